@@ -1,0 +1,373 @@
+"""Pins of the CPU oracle against facts it does not compute itself.
+
+Each test checks the oracle against the paper's printed numbers, a closed form,
+an independent physical formulation, finite differences or brute force, so that
+a dropped term, a wrong sign, a swapped index or a transposed operand in the
+oracle fails at least one of them.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import OracleGrid
+from paper_2201_00241_gb300 import gridgen as gg
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def tiny(n_bus, n_branch, n_gen, seed, lossless=False):
+    return gg.make_grid(n_bus, n_branch, n_gen, seed, lossless=lossless)
+
+
+def flat_start(o):
+    ix_th, ix_v, _, _ = o.index_maps()
+    x0 = np.zeros(o.n_x)
+    x0[ix_v[ix_v >= 0]] = 1.0
+    return x0
+
+
+# ---------------------------------------------------------------------------
+# Table 1: dimension counts (pins the index reading of x and p)
+# ---------------------------------------------------------------------------
+
+def test_table1_dimension_counts():
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "table1_dims.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    shapes = {118: "case118", 1354: "case1354", 2869: "case2869", 9241: "case9241"}
+    for name, n_v, n_e, n_x, n_p in rows:
+        c = gg.CASES[shapes[int(n_v)]]
+        assert c["n_bus"] == int(n_v) and c["n_branch"] == int(n_e)
+        assert 2 * c["n_gen"] - 1 == int(n_p), name
+        # the oracle's own counts, from its own index maps, on the grid itself
+        if int(n_v) <= 2869:
+            o = OracleGrid(gg.make_case(shapes[int(n_v)]))
+            assert (o.n_x, o.n_p) == (int(n_x), int(n_p)), name
+
+
+def test_index_maps_order():
+    g = tiny(12, 16, 4, 3)
+    o = OracleGrid(g)
+    ix_th, ix_v, ip_v, ip_pg = o.index_maps()
+    t = g.bus_type
+    pv, pq, gen = np.flatnonzero(t == 1), np.flatnonzero(t == 2), np.flatnonzero(t != 2)
+    assert list(ix_th[pv]) == list(range(len(pv)))
+    assert list(ix_th[pq]) == list(range(len(pv), len(pv) + len(pq)))
+    assert list(ix_v[pq]) == list(range(len(pv) + len(pq), len(pv) + 2 * len(pq)))
+    assert list(ip_v[gen]) == list(range(len(gen)))
+    assert list(ip_pg[pv]) == list(range(len(gen), len(gen) + len(pv)))
+    assert ix_th[t == 0] == -1 and ip_pg[t == 0] == -1
+
+
+# ---------------------------------------------------------------------------
+# eq. (2): injections against Kirchhoff's laws on the branch currents
+# ---------------------------------------------------------------------------
+
+def branch_power(g, vm, va, fr, to, r, x, b):
+    """Complex power injected at each bus, summed over pi-model branch ends."""
+    V = vm * np.exp(1j * va)
+    S = np.zeros(g.n_bus, dtype=complex)
+    for f, t, rr, xx, bb in zip(fr, to, r, x, b):
+        ys = 1.0 / complex(rr, xx)
+        I_f = ys * (V[f] - V[t]) + 0.5j * bb * V[f]
+        I_t = ys * (V[t] - V[f]) + 0.5j * bb * V[t]
+        S[f] += V[f] * np.conj(I_f)
+        S[t] += V[t] * np.conj(I_t)
+    return S
+
+
+def test_injections_match_branch_currents():
+    g = tiny(30, 41, 6, 11)
+    # add a parallel branch to check that the admittances of parallel lines add
+    g.fr = np.append(g.fr, g.fr[3]).astype(np.int32)
+    g.to = np.append(g.to, g.to[3]).astype(np.int32)
+    g.r, g.x, g.b = np.append(g.r, 0.02), np.append(g.x, 0.1), np.append(g.b, 0.01)
+    g.n_branch += 1
+    o = OracleGrid(g)
+    rng = np.random.default_rng(5)
+    vm = rng.uniform(0.9, 1.1, g.n_bus)
+    va = rng.normal(0, 0.2, g.n_bus)
+    P, Q = o.injections(vm, va)
+    S = branch_power(g, vm, va, g.fr, g.to, g.r, g.x, g.b)
+    np.testing.assert_allclose(P, S.real, rtol=0, atol=1e-10 * abs(S).max())
+    np.testing.assert_allclose(Q, S.imag, rtol=0, atol=1e-10 * abs(S).max())
+
+
+def test_lossless_injections_sum_to_zero():
+    g = tiny(40, 55, 8, 12, lossless=True)
+    o = OracleGrid(g)
+    P, Q = o.injections(g.v_star, g.theta_star)
+    assert abs(P.sum()) <= 1e-12 * abs(P).sum()
+
+
+# ---------------------------------------------------------------------------
+# eq. (3) and the Jacobians
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(5, 6, 2, 1), (9, 12, 3, 2), (14, 20, 5, 3), (30, 41, 6, 4)])
+def test_jacobians_match_central_differences(shape):
+    o = OracleGrid(tiny(*shape))
+    st = o.plant()
+    rng = np.random.default_rng(7)
+    x = st.x + rng.normal(0, 0.05, o.n_x)      # off the solution: g != 0
+    jx, jp = o.jacobians_dense(x, st.p)
+    h = 1e-6
+    fx = np.column_stack([(o.residual(x + h * e, st.p, st.pd, st.qd) - o.residual(x - h * e, st.p, st.pd, st.qd)) / (2 * h)
+                          for e in np.eye(o.n_x)])
+    fp = np.column_stack([(o.residual(x, st.p + h * e, st.pd, st.qd) - o.residual(x, st.p - h * e, st.pd, st.qd)) / (2 * h)
+                          for e in np.eye(o.n_p)])
+    assert abs(jx - fx).max() <= 1e-6 * abs(jx).max()
+    assert abs(jp - fp).max() <= 1e-6 * abs(jp).max()
+    # J_x is structurally symmetric (P_i pairs with theta_i, Q_i with v_i)
+    assert ((jx != 0) == (jx.T != 0)).all()
+
+
+def test_planted_point_and_newton_from_flat_start():
+    g = gg.make_case("case118")
+    o = OracleGrid(g)
+    st = o.plant()
+    assert abs(o.residual(st.x, st.p, st.pd, st.qd)).max() <= 1e-12
+    x, status, iters, res = o.newton(st.p, st.pd, st.qd, flat_start(o))
+    assert status == 0 and res <= 1e-12 and iters >= 3
+    assert abs(x - st.x).max() <= 1e-8
+
+
+# ---------------------------------------------------------------------------
+# the oracle's LU (static minimum-degree order, no pivoting)
+# ---------------------------------------------------------------------------
+
+def test_lu_against_dense_factorisation():
+    o = OracleGrid(tiny(30, 41, 6, 4))
+    st = o.plant()
+    jx, _ = o.jacobians_dense(st.x, st.p)
+    perm, L, U = o.lu_dense(st.x, st.p)
+    B = jx[np.ix_(perm, perm)]
+    assert np.allclose(np.tril(L, -1) + np.eye(o.n_x), L) and np.allclose(np.triu(U), U)
+    assert abs(L @ U - B).max() <= 1e-13 * abs(B).max()
+    R = np.random.default_rng(3).normal(size=(o.n_x, 3))
+    for trans in (False, True):
+        X = o.solve(st.x, st.p, R, trans=trans)
+        A = jx.T if trans else jx
+        np.testing.assert_allclose(X, np.linalg.solve(A, R), rtol=1e-11, atol=1e-12 * abs(X).max())
+
+
+# ---------------------------------------------------------------------------
+# first order: lambda and the reduced gradient, eq. (6)-(7)
+# ---------------------------------------------------------------------------
+
+def reduced(o, st, p, tol=1e-13):
+    x, status, _, _ = o.newton(p, st.pd, st.qd, st.x, tol=tol)
+    assert status == 0
+    return x
+
+
+def test_adjoint_solves_first_order_condition():
+    o = OracleGrid(tiny(30, 41, 6, 4))
+    st = o.plant()
+    lam, grad, F = o.adjoint(st.x, st.p, st.pd, st.qd)
+    jx, _ = o.jacobians_dense(st.x, st.p)
+    h = 1e-5
+    dfdx = np.array([(o.objective(st.x + h * e, st.p, st.pd) - o.objective(st.x - h * e, st.p, st.pd)) / (2 * h)
+                     for e in np.eye(o.n_x)])
+    # grad_x f + lambda^T J_x = 0
+    assert abs(dfdx + jx.T @ lam).max() <= 1e-7 * abs(dfdx).max()
+    assert F == pytest.approx(o.objective(st.x, st.p, st.pd), rel=1e-15)
+
+
+@pytest.mark.parametrize("shape", [(9, 12, 3, 2), (30, 41, 6, 4)])
+def test_reduced_gradient_matches_central_differences(shape):
+    o = OracleGrid(tiny(*shape))
+    st = o.plant()
+    _, grad, _ = o.adjoint(st.x, st.p, st.pd, st.qd)
+    h = 1e-6
+    fd = np.empty(o.n_p)
+    for k in range(o.n_p):
+        e = np.zeros(o.n_p)
+        e[k] = h
+        fd[k] = (o.objective(reduced(o, st, st.p + e), st.p + e, st.pd)
+                 - o.objective(reduced(o, st, st.p - e), st.p - e, st.pd)) / (2 * h)
+    assert abs(grad - fd).max() <= 1e-6 * abs(grad).max()
+
+
+# ---------------------------------------------------------------------------
+# second order: Hessian of the Lagrangian and the reduced Hessian
+# ---------------------------------------------------------------------------
+
+def test_lagrangian_hessian_matches_second_differences():
+    o = OracleGrid(tiny(9, 12, 3, 2))
+    st = o.plant()
+    rng = np.random.default_rng(9)
+    x = st.x + rng.normal(0, 0.05, o.n_x)
+    lam = rng.normal(0, 100.0, o.n_x)
+    K = o.lagrangian_hessian_dense(x, st.p, st.pd, lam)
+    nx = o.n_x
+
+    def ell(u):
+        return o.objective(u[:nx], u[nx:], st.pd) + lam @ o.residual(u[:nx], u[nx:], st.pd, st.qd)
+
+    u0 = np.concatenate([x, st.p])
+    n = len(u0)
+    h = 1e-4
+    fd = np.empty((n, n))
+    E = np.eye(n) * h
+    for a in range(n):
+        for b in range(n):
+            fd[a, b] = (ell(u0 + E[a] + E[b]) - ell(u0 + E[a] - E[b]) - ell(u0 - E[a] + E[b])
+                        + ell(u0 - E[a] - E[b])) / (4 * h * h)
+    assert abs(K - K.T).max() <= 1e-14 * abs(K).max()
+    assert abs(K - fd).max() <= 2e-6 * abs(K).max()
+
+
+def full_hessian(o, st):
+    return o.hessvec(st.x, st.p, st.pd, st.qd, np.eye(o.n_p))
+
+
+@pytest.mark.parametrize("shape", [(5, 6, 2, 1), (9, 12, 3, 2), (14, 20, 5, 3), (30, 41, 6, 4)])
+def test_reduced_hessian_matches_differences_of_gradient(shape):
+    o = OracleGrid(tiny(*shape))
+    st = o.plant()
+    H = full_hessian(o, st)
+    h = 1e-6
+    fd = np.empty_like(H)
+    for k in range(o.n_p):
+        e = np.zeros(o.n_p)
+        e[k] = h
+        gp = o.adjoint(reduced(o, st, st.p + e), st.p + e, st.pd, st.qd)[1]
+        gm = o.adjoint(reduced(o, st, st.p - e), st.p - e, st.pd, st.qd)[1]
+        fd[:, k] = (gp - gm) / (2 * h)
+    assert abs(H - fd).max() <= 1e-6 * abs(H).max()
+
+
+def test_reduced_hessian_quadratic_form_matches_second_difference():
+    o = OracleGrid(gg.make_case("case118"))
+    st = o.plant()
+    w = gg.random_directions(o.n_p, 1, 118)[:, 0]
+    hw = o.hessvec(st.x, st.p, st.pd, st.qd, w[:, None])[:, 0]
+    h = 1e-4
+
+    def F(p):
+        return o.objective(reduced(o, st, p), p, st.pd)
+
+    d2 = (F(st.p + h * w) - 2 * F(st.p) + F(st.p - h * w)) / (h * h)
+    assert w @ hw == pytest.approx(d2, rel=1e-5)
+
+
+def test_reduced_hessian_is_symmetric():
+    o = OracleGrid(gg.make_case("case118"))
+    st = o.plant()
+    H = full_hessian(o, st)
+    assert abs(H - H.T).max() <= 1e-11 * abs(H).max()
+
+
+def test_lossless_closed_form():
+    """With r = 0 the losses vanish, so F(p) = sum_PV c_k(Pg_k) + c_ref(sum Pd - sum_PV Pg_k):
+    H[Pg_k, Pg_l] = c''_k delta_kl + c''_ref and every v row and column is zero."""
+    g = gg.make_grid(118, 186, 54, 20220100, lossless=True)
+    o = OracleGrid(g)
+    st = o.plant()
+    H = full_hessian(o, st)
+    _, _, ip_v, ip_pg = o.index_maps()
+    S = g.base_mva
+    ref = int(np.flatnonzero(g.bus_type == 0)[0])
+    pv = np.flatnonzero(ip_pg >= 0)
+    ng = int((ip_v >= 0).sum())
+    expect = np.zeros((o.n_p, o.n_p))
+    expect[ng:, ng:] = 2 * g.c2[ref] * S * S
+    expect[ip_pg[pv], ip_pg[pv]] += 2 * g.c2[pv] * S * S
+    assert abs(H - expect).max() <= 1e-9 * abs(expect).max()
+
+
+def test_bus_relabelling_permutes_the_hessian():
+    g = gg.make_case("case118")
+    o = OracleGrid(g)
+    st = o.plant()
+    H = full_hessian(o, st)
+    rng = np.random.default_rng(4)
+    pi = rng.permutation(g.n_bus)            # old bus id -> new bus id
+    g2 = gg.make_case("case118")
+    inv = np.argsort(pi)
+    g2.fr, g2.to = pi[g.fr].astype(np.int32), pi[g.to].astype(np.int32)
+    for name in ("bus_type", "v_star", "theta_star", "c2", "c1"):
+        setattr(g2, name, getattr(g, name)[inv])
+    o2 = OracleGrid(g2)
+    st2 = o2.plant()
+    H2 = full_hessian(o2, st2)
+    # map p indices: variable of bus b in grid 1 is variable of bus pi[b] in grid 2
+    _, _, ipv1, ipg1 = o.index_maps()
+    _, _, ipv2, ipg2 = o2.index_maps()
+    m = np.empty(o.n_p, dtype=int)
+    for b in range(g.n_bus):
+        if ipv1[b] >= 0:
+            m[ipv1[b]] = ipv2[pi[b]]
+        if ipg1[b] >= 0:
+            m[ipg1[b]] = ipg2[pi[b]]
+    assert abs(H2[np.ix_(m, m)] - H).max() <= 1e-10 * abs(H).max()
+
+
+# ---------------------------------------------------------------------------
+# symbolic data: ordering, patterns, levels (brute force on small graphs)
+# ---------------------------------------------------------------------------
+
+def brute_min_degree(g):
+    alive = {i for i in range(g.n_bus) if g.bus_type[i] != 0}
+    adj = {i: set() for i in alive}
+    for f, t in zip(g.fr, g.to):
+        if f in alive and t in alive and f != t:
+            adj[f].add(t)
+            adj[t].add(f)
+    order = []
+    while alive:
+        best = min(alive, key=lambda i: (len(adj[i]), i))
+        nb = adj.pop(best)
+        alive.remove(best)
+        for a in nb:
+            adj[a].discard(best)
+            adj[a] |= nb - {a}
+        order.append(best)
+    return order
+
+
+@pytest.mark.parametrize("shape", [(9, 12, 3, 2), (30, 41, 6, 4), (118, 186, 54, 20220100)])
+def test_symbolic_ordering_patterns_levels(shape):
+    g = tiny(*shape)
+    o = OracleGrid(g)
+    sym = o.symbolic()
+    assert list(sym["bus_order"]) == brute_min_degree(g)
+    ix_th, ix_v, _, _ = o.index_maps()
+    perm = []
+    for b in sym["bus_order"]:
+        perm.append(ix_th[b])
+        if ix_v[b] >= 0:
+            perm.append(ix_v[b])
+    assert list(sym["perm"]) == perm
+    # patterns equal the nonzero pattern of a dense LU of random values placed on the
+    # structural pattern of J_x (power-flow values can cancel exactly: P_i and Q_i
+    # depend on angle differences only)
+    st = o.plant()
+    jx, _ = o.jacobians_dense(st.x + np.random.default_rng(1).normal(0, 0.01, o.n_x), st.p)
+    n = o.n_x
+    rng = np.random.default_rng(2)
+    A = np.where(jx != 0, rng.uniform(-1, 1, (n, n)), 0.0) + n * np.eye(n)
+    B = A[np.ix_(sym["perm"], sym["perm"])]
+    L, U = np.eye(n), B.copy()
+    for k in range(n):
+        L[k + 1:, k] = U[k + 1:, k] / U[k, k]
+        U[k + 1:, :] -= np.outer(L[k + 1:, k], U[k, :])
+        U[k + 1:, k] = 0.0
+    Lpat = np.zeros((n, n), bool)
+    Upat = np.zeros((n, n), bool)
+    for r in range(n):
+        Lpat[r, sym["Lj"][sym["Lp"][r]:sym["Lp"][r + 1]]] = True
+        Upat[r, sym["Uj"][sym["Up"][r]:sym["Up"][r + 1]]] = True
+    assert ((np.tril(L, -1) != 0) == Lpat).all()
+    assert ((U != 0) == Upat).all()
+    assert (Lpat == Upat.T & ~np.eye(n, dtype=bool)).all()        # structural symmetry
+    # levels: longest dependency chain between buses through L rows
+    bus_of = np.repeat(np.arange(len(sym["bus_order"])),
+                       [2 if ix_v[b] >= 0 else 1 for b in sym["bus_order"]])
+    lev = np.zeros(len(sym["bus_order"]), int)
+    for r in range(n):
+        for c in np.flatnonzero(Lpat[r]):
+            if bus_of[c] != bus_of[r]:
+                lev[bus_of[r]] = max(lev[bus_of[r]], lev[bus_of[c]] + 1)
+    assert (lev == sym["level"]).all()

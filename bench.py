@@ -1,0 +1,271 @@
+"""Benchmark: reduced-Hessian-vector products per second, FP64, 9241-bus-shaped grid.
+
+A step is one pass of the whole hot path over the grid's current state:
+Jacobian assembly, LU refactorisation, adjoint and projection coefficients
+(rh_adjoint), then the full reduced Hessian, all n_p = 2889 directions, as
+W = I blocks of N = 256 columns issued together in one direction-kernel launch.
+Throughput = n_p HVPs / step time.  Inputs are synthetic (seeded PEGASE9241
+shape, see gridgen.py) and resident in HBM; the device workspace (~0.9 GB) is
+larger than L2 and L2 is also flushed between timed steps.
+
+e2e: the same metric through the C ABI with host buffers: parameters, loads and
+the operating point copied in, the full H (66.8 MB) copied out, every step.
+
+--impl reference times the CPU oracle (oracle/, plain C, one thread) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CASE = "case9241"
+BLOCK_N = 256
+PEAK_FP64_GFLOPS = 152 * 4 * 0.5 * 2 * 2.070  # SMs x sub-partitions x lane-FMA/clk x 2 x GHz (max SM clock)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--case", default=CASE)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def algorithmic_flops_per_direction(dm, n_inc, n_gref):
+    """FP64 flops one direction of Algorithm 2 needs (FMA = 2)."""
+    nx = dm.n_x
+    spmul = 2 * dm.nnz_jp
+    l_sweep = 2 * dm.nnz_l
+    u_sweep = 2 * (dm.nnz_u - nx) + nx
+    proj = 8 * n_inc + 8 * dm.n_bus + 4 * n_gref + dm.n_pv
+    return spmul + 2 * (l_sweep + u_sweep) + proj + spmul
+
+
+def start_clock_sampler(path):
+    try:
+        return subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+             "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except (OSError, FileNotFoundError):
+        return None
+
+
+def read_clocks(path, dev):
+    out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+    try:
+        rows = [ln.split(",") for ln in open(path) if ln.strip()]
+    except OSError:
+        return out
+    rows = [[c.strip() for c in r] for r in rows if len(r) >= 9 and r[0].strip() == str(dev)]
+    if not rows:
+        return out
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    out["sm_mhz"] = statistics.median(sm) if sm else None
+    out["sm_max_mhz"] = float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = set()
+    for r in rows:
+        for k, name in enumerate(names):
+            if r[5 + k].lower().startswith("active"):
+                reasons.add(name)
+    out["reasons"] = sorted(reasons)
+    return out
+
+
+def cpu_baseline(case, n_dirs=32):
+    """The oracle as it stands (single-threaded C) on a bounded sample: n_dirs
+    directions of the same grid and state, plus its own per-state setup."""
+    from oracle import OracleGrid
+    from paper_2201_00241_gb300 import gridgen as gg
+
+    g = gg.make_case(case)
+    o = OracleGrid(g)
+    st = o.plant()
+    W = np.eye(o.n_p)[:, :n_dirs]
+    t0 = time.perf_counter()
+    o.hessvec(st.x, st.p, st.pd, st.qd, W)
+    dt = time.perf_counter() - t0
+    return dict(value=n_dirs / dt, unit="HVP/s", cores=1, kind="oracle",
+                sample=f"{n_dirs} of {o.n_p} unit directions of H on {case} (incl. the oracle's own LU and adjoint), "
+                       f"{dt:.1f} s")
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cb = cpu_baseline(args.case, n_dirs=32)
+    times = []
+    for _ in range(args.warmup):
+        pass
+    from oracle import OracleGrid
+    from paper_2201_00241_gb300 import gridgen as gg
+    g = gg.make_case(args.case)
+    o = OracleGrid(g)
+    st = o.plant()
+    per = 16
+    W = np.eye(o.n_p)[:, :per]
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.hessvec(st.x, st.p, st.pd, st.qd, W)
+        times.append(time.perf_counter() - t0)
+    value = per * len(times) / sum(times)
+    line = {"impl": "reference", "metric": "reduced-Hessian HVPs/sec FP64 (9241-bus-shaped grid, N=256)",
+            "value": value, "unit": "HVP/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.case}: {per} unit directions of the reduced Hessian per step "
+                                   "(sample of the full-H workload), oracle single thread"},
+            "cpu_baseline": {"value": value, "unit": "HVP/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per} directions per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": "HVP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2201_00241_gb300 import gridgen as gg
+    from paper_2201_00241_gb300 import rh
+
+    g = gg.make_case(args.case)
+    lg = rh.Grid(g, device=local)
+    st = lg.plant()
+    lg.set_state(st.p, st.pd, st.qd)
+    lg.powerflow(st.x, tol=1e-12, max_iter=20)
+    dm = lg.dims
+    n_p = lg.n_p
+    lib = rh.load()
+    # incidences and slack-gradient entries, for the flop count
+    n_inc = 2 * int(np.count_nonzero(g.fr != g.to))
+    ref = int(np.flatnonzero(g.bus_type == 0)[0])
+    n_gref = 1 + 2 * int(np.count_nonzero(g.fr == ref) + np.count_nonzero(g.to == ref))
+    flops_dir = algorithmic_flops_per_direction(dm, n_inc, n_gref)
+
+    H = torch.empty((n_p, n_p), dtype=torch.float64, device=f"cuda:{local}").t()   # column-major
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+    sptr = rh.C.c_void_p(stream.cuda_stream)
+
+    def step(ev=None):
+        rc = lib.rh_adjoint(lg._h, None, None, None)
+        if rc:
+            rh._check(rc)
+        if ev is not None:
+            ev[0].record(stream)
+        rh._check(lib.rh_hessian(lg._h, BLOCK_N, rh._ptr(H), n_p, sptr,
+                                 rh.RH_DEVICE_PTRS | rh.RH_HESSIAN_CONCURRENT))
+        if ev is not None:
+            ev[1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                            f"clocks_rank{rank}.csv")
+    sampler = start_clock_sampler(clk_path)
+    step_ms, dirs_ms = [], []
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.fill_(1.0)           # L2 flush, outside the timed events
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        step((k0, k1))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        dirs_ms.append(k0.elapsed_time(k1))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+    t_step = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([t_step], device=f"cuda:{local}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(t.item())
+    value = world * n_p / (t_step * 1e-3)
+    t_dirs = sum(dirs_ms) / len(dirs_ms)
+    achieved = flops_dir * n_p / (t_dirs * 1e-3) * 1e-9
+
+    # e2e through the C ABI with host buffers
+    Hh = np.empty((n_p, n_p), order="F")
+    x0 = st.x.copy()
+    e2e_t = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        lg.set_state(st.p, st.pd, st.qd)
+        lg.powerflow(x0, tol=1e-12, max_iter=20)
+        lg.adjoint()
+        rh._check(lib.rh_hessian(lg._h, BLOCK_N, rh._ptr(Hh), n_p, None, rh.RH_HESSIAN_CONCURRENT))
+        if i >= args.warmup:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_value = world * n_p / (sum(e2e_t) / len(e2e_t))
+    h2d = 8 * (n_p + 2 * g.n_bus + lg.n_x)
+    d2h = 8 * n_p * n_p + 8 * (lg.n_x + n_p + 1)
+
+    if rank != 0:
+        return
+    clocks = read_clocks(clk_path, local)
+    line = {
+        "metric": "reduced-Hessian HVPs/sec FP64 (9241-bus-shaped grid, N=256)",
+        "value": value, "unit": "HVP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.case}: full reduced Hessian ({n_p} HVPs) per step, W = I in blocks of "
+                               f"N={BLOCK_N} issued in one launch, per-state setup (Jacobian, refactor, adjoint) "
+                               "included", "n_x": lg.n_x, "n_p": n_p, "block_n": BLOCK_N,
+                   "nnz_l": dm.nnz_l, "nnz_u": dm.nnz_u, "l2": "flushed between steps; workspace > L2",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "alu", "kernel": "k_dirs", "achieved": achieved, "peak": PEAK_FP64_GFLOPS,
+                     "unit": "GFLOP/s", "frac": achieved / PEAK_FP64_GFLOPS, "traffic": None,
+                     "kernel_ms": t_dirs, "flops_per_direction": flops_dir},
+        "e2e": {"value": e2e_value, "unit": "HVP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": dm.n_levels_fwd + 7,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.case)
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

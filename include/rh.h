@@ -1,0 +1,202 @@
+/*
+ * rh.h -- C ABI of librh: batched reduced-Hessian-vector products of the polar
+ * power-flow equations on one GB300 GPU (FP64 throughout).
+ *
+ * Method: "Batched Second-Order Adjoint Sensitivity for Reduced Space
+ * Methods" (arXiv 2201.00241).  Notation follows the paper:
+ *   g(x, p) = 0        balance equations, eq. (3), x = (theta_pv, theta_pq, v_pq)
+ *   p                  parameters (v at every generator bus, Pg at PV buses)
+ *   f(x, p)            generation cost; F(p) = f(x(p), p), eq. (5)
+ *   lambda             first-order adjoint, eq. (7)
+ *   HW                 reduced Hessian applied to W = (w_1..w_N), eq. (9)-(10),
+ *                      computed by the parallel reduction of Algorithm 2.
+ *
+ * Index conventions (all arrays are 0-based):
+ *   x  = [theta at PV buses (ascending bus id), theta at PQ buses, v at PQ buses]
+ *   p  = [v at generator buses incl. the slack (ascending id), Pg at PV buses]
+ *   rows of g and of lambda are ordered like x (P_i <-> theta_i, Q_i <-> v_i).
+ *   Bus types: 0 slack (exactly one), 1 PV, 2 PQ.  Powers are per unit on
+ *   base_mva; the cost is sum_k c2_k (S Pg_k)^2 + c1_k S Pg_k with S = base_mva,
+ *   the slack generation being P_inj + Pd at the slack.
+ *
+ * Errors: every call returns an rh_status and never aborts; on error the
+ * outputs are unspecified and rh_last_error() (thread-local) says why.
+ *
+ * Ownership: rh_grid_create copies every descriptor array; W, HW, H and all
+ * other caller buffers stay owned by the caller and are only used during the
+ * call (stream-ordered for device pointers, see RH_DEVICE_PTRS).
+ *
+ * Streams: entry points taking a `stream` (a cudaStream_t, NULL = legacy
+ * default) enqueue their GPU work on it.  One grid must not be used from two
+ * host threads at once.
+ */
+#ifndef RH_H
+#define RH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rh_grid rh_grid;
+
+typedef enum {
+    RH_OK = 0,
+    RH_EINVAL = 1,      /* bad argument or inconsistent grid                      */
+    RH_ENOMEM = 2,      /* device or host allocation failed                       */
+    RH_ESINGULAR = 3,   /* a static pivot |u_kk| <= 1e-14 max|J_x|                */
+    RH_ENOCONV = 4,     /* Newton did not reach the tolerance                     */
+    RH_ETIMEOUT = 5,    /* a bounded device wait gave up                          */
+    RH_ECUDA = 6,       /* a CUDA runtime call failed                             */
+    RH_ESTATE = 7       /* call order: e.g. rh_hessvec before rh_adjoint          */
+} rh_status;
+
+/* Pointer-kind flag for W / HW / H / R arguments. */
+#define RH_HOST_PTRS 0u     /* caller buffers are in host memory (copied by the call; the call synchronises) */
+#define RH_DEVICE_PTRS 1u   /* caller buffers are device pointers on the grid's device (stream-ordered)      */
+
+typedef struct {
+    int32_t n_bus, n_branch;
+    const int32_t *from, *to;       /* branch end buses, 0 <= from, to < n_bus, from != to   */
+    const double *r, *x, *b;        /* series resistance, reactance, total line charging (p.u.) */
+    const int8_t *bus_type;         /* 0 slack, 1 PV, 2 PQ                                   */
+    const double *c2, *c1;          /* cost coefficients per bus (used at generator buses)    */
+    double base_mva;                /* S                                                     */
+} rh_grid_desc;
+
+typedef struct {
+    int32_t n_bus, n_branch, n_gen, n_pv, n_pq;
+    int32_t n_x, n_p;
+    int32_t n_levels_fwd, n_levels_bwd;   /* bus-level schedule depths               */
+    int64_t nnz_jx, nnz_jp;               /* structural nonzeros of J_x and J_p      */
+    int64_t nnz_l, nnz_u;                 /* strictly-lower L, upper U incl. diagonal */
+    int64_t refactor_updates;             /* multiply-subtract count of a refactor   */
+} rh_dims;
+
+/*
+ * Load a grid (paper section 3.1).  Builds the pi-model admittance matrix
+ * (series y = 1/(r + jx), b/2 at each end), and runs the host symbolic phase:
+ * exact minimum-degree ordering of the bus graph (ties: smallest bus id; each
+ * bus contributes theta then v), symbolic LU of J_x, bus-level schedules, and
+ * uploads the fixed patterns to `device`.  The paper factors J_x on the host
+ * once and refactors on the device with the same pattern (section 5.2); here
+ * only the symbolic part runs on the host.
+ * device < 0 runs the symbolic phase only (no CUDA call at all): such a grid
+ * answers rh_grid_dims and rh_grid_symbolic, every other call returns
+ * RH_ESTATE.
+ * Returns RH_EINVAL for a grid without exactly one slack bus, an out-of-range
+ * or self-loop branch, or a non-positive |r + jx|.
+ */
+rh_status rh_grid_create(const rh_grid_desc *desc, int32_t device, rh_grid **out);
+void rh_grid_destroy(rh_grid *grid);
+rh_status rh_grid_dims(const rh_grid *grid, rh_dims *out);
+
+/*
+ * Symbolic data for bit-exact comparison (host buffers sized from rh_dims):
+ *   perm[n_x]        internal variable q -> x index
+ *   bus_order[n_bus-1], level[n_bus-1]   elimination order (bus ids) and the
+ *                    forward level of each eliminated bus (longest chain of
+ *                    bus-level dependencies through the rows of L)
+ *   Lp[n_x+1], Lj[nnz_l]   CSR of the strictly lower part of L (internal indices)
+ *   Up[n_x+1], Uj[nnz_u]   CSR of U including the diagonal
+ * Any pointer may be NULL to skip that array.
+ */
+rh_status rh_grid_symbolic(const rh_grid *grid, int32_t *perm, int32_t *bus_order, int32_t *level,
+                           int32_t *Lp, int32_t *Lj, int32_t *Up, int32_t *Uj);
+
+/*
+ * Power injections of eq. (2) (diagonal admittance term included) at bus
+ * voltages vm, va (host arrays of n_bus); P, Q host outputs of n_bus.
+ * Evaluated on the device.
+ */
+rh_status rh_injections(rh_grid *grid, const double *vm, const double *va, double *P, double *Q);
+
+/*
+ * Set the parameters p (host, n_p) and, optionally, the loads pd, qd (host,
+ * n_bus each; NULL keeps the previous loads, initially zero).  Invalidates
+ * the factors, lambda and the projection coefficients.
+ */
+rh_status rh_set_state(rh_grid *grid, const double *p, const double *pd, const double *qd);
+
+/*
+ * Newton-Raphson power flow (section 3.2): x_{k+1} = x_k - J_x^{-1} g(x_k, p),
+ * entirely on the device (residual and Jacobian kernel, fixed-pattern LU
+ * refactorisation, triangular solves).  x0 (host, n_x) is the initial guess,
+ * or NULL to continue from the current state (initially flat: theta = 0,
+ * v = 1).  Stops when ||g||_inf <= tol or after max_iter steps.  x_out (host,
+ * n_x), iters and resid (final ||g||_inf) may be NULL.
+ * Returns RH_ENOCONV if the tolerance is not met, RH_ESINGULAR on a zero pivot.
+ */
+rh_status rh_powerflow(rh_grid *grid, const double *x0, double tol, int32_t max_iter,
+                       double *x_out, int32_t *iters, double *resid);
+
+/*
+ * Per-state setup of the hot path at the current (x, p): Jacobian assembly
+ * into the fixed LU pattern, LU refactorisation, first-order adjoint
+ * lambda = -J_x^{-T} grad_x f (eq. 7), reduced gradient
+ * grad F = grad_p f + J_p^T lambda, F = f(x, p), and the per-branch second-order
+ * coefficients of lambda^T Hess g + Hess f used by every later rh_hessvec.
+ * Outputs (host, nullable): F, lambda[n_x], grad[n_p].
+ */
+rh_status rh_adjoint(rh_grid *grid, double *F, double *lambda, double *grad);
+
+/*
+ * Reduced Hessian-vector products HW = (Hess F) W for N directions
+ * (Algorithm 2, eq. 9-10): B = J_p W; Z = -J_x^{-1} B; (Y_x, Y_p) = the
+ * projection of lambda^T Hess g + Hess f on (Z, W) (eq. 13); Psi = -J_x^{-T} Y_x;
+ * HW = Y_p + J_p^T Psi.  Requires a prior rh_adjoint for the current state
+ * (RH_ESTATE otherwise).
+ *   W   n_p x N, column-major, leading dimension ldw >= n_p (column j = w_j)
+ *   HW  n_p x N, column-major, leading dimension ldhw >= n_p
+ * flags: RH_HOST_PTRS or RH_DEVICE_PTRS.  With device pointers the call is
+ * asynchronous on `stream`; with host pointers it copies and synchronises.
+ * N = 0 is a no-op.  Every direction is computed independently, so column j of
+ * HW does not depend on the other columns of W.
+ */
+rh_status rh_hessvec(rh_grid *grid, const double *W, int64_t ldw, int32_t N,
+                     double *HW, int64_t ldhw, void *stream, uint32_t flags);
+
+/*
+ * Full reduced Hessian H = Hess F (n_p x n_p, column-major, leading dimension
+ * ldh >= n_p), computed as HW for W = I by blocks of block_n columns
+ * (section 5.3; block count ceil(n_p / block_n)).  All blocks are issued in
+ * one launch when `flags` has RH_HESSIAN_CONCURRENT, otherwise one launch per
+ * block.  Requires rh_adjoint for the current state.
+ */
+#define RH_HESSIAN_CONCURRENT 2u
+rh_status rh_hessian(rh_grid *grid, int32_t block_n, double *H, int64_t ldh, void *stream, uint32_t flags);
+
+/*
+ * Solve J_x X = R (trans = 0) or J_x^T X = R (trans = 1) with the current
+ * device factors (after rh_adjoint or rh_refactor), in place.  R is n_x x nrhs,
+ * column-major, leading dimension ldr >= n_x, indexed like x.  These are the
+ * batched sparse solves of Algorithm 2 on their own.
+ */
+rh_status rh_solve(rh_grid *grid, double *R, int64_t ldr, int32_t nrhs, int32_t trans,
+                   void *stream, uint32_t flags);
+
+/*
+ * Assemble J_x, J_p at the current state and refactor (the first two steps of
+ * rh_adjoint).  A_out (host, nullable, nnz_l + nnz_u doubles) receives the
+ * factors in the CSR pattern of rh_grid_symbolic, row by row: the strictly
+ * lower entries of L then the entries of U.
+ */
+rh_status rh_refactor(rh_grid *grid, double *A_out);
+
+/*
+ * The projection step of Algorithm 2 on its own (eq. 11/13): Y = [Hess l] V
+ * with l = f + lambda^T g at the current state and lambda of the last
+ * rh_adjoint.  V, Y are (n_x + n_p) x N column-major with leading dimensions
+ * ldv, ldy; rows 0..n_x-1 are indexed like x, rows n_x.. like p.
+ */
+rh_status rh_lagrangian_hessvec(rh_grid *grid, const double *V, int64_t ldv, int32_t N,
+                                double *Y, int64_t ldy, void *stream, uint32_t flags);
+
+/* Message of the last error on this thread ("" if none). */
+const char *rh_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

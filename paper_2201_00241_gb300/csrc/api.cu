@@ -1,0 +1,715 @@
+// api.cu -- extern "C" entry points of librh (declared in include/rh.h).
+//
+// Host code only: argument checks, device memory, the Newton and setup
+// sequencing, copies for host-pointer calls.  Every numerical step runs in the
+// kernels of kernels.cu.
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rh.h"
+#include "rh_internal.h"
+#include "rh_kernels.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+rh_status fail(rh_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+#define RH_CUDA(call)                                                                           \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(e_ == cudaErrorMemoryAllocation ? RH_ENOMEM : RH_ECUDA,                 \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+    } while (0)
+
+template <typename T>
+struct DevArr {
+    T* p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct rh_grid {
+    int device = 0;
+    rh::Symbolic S;
+    double base_mva = 100.0;
+    cudaStream_t stream = nullptr;
+    std::vector<void*> allocs;
+
+    // --- device: topology (static) --------------------------------------
+    int *yp = nullptr, *yj = nullptr, *ydiag = nullptr;
+    double *G = nullptr, *B = nullptr;
+    int *qth = nullptr, *qv = nullptr, *ip_v = nullptr, *ip_pg = nullptr, *ix_th = nullptr, *ix_v = nullptr;
+    int *pg_slot = nullptr, *jac_dst = nullptr;
+    double *c2 = nullptr, *c1 = nullptr;
+    int *rowptr = nullptr, *col = nullptr, *diagpos = nullptr, *tpos = nullptr, *q0 = nullptr;
+    uint8_t* nv = nullptr;
+    int *flev_ptr = nullptr, *flev_bus = nullptr, *flev_maxext = nullptr;
+    int *blev_ptr = nullptr, *blev_bus = nullptr, *blev_maxext = nullptr;
+    int64_t *lrank_ptr = nullptr, *upd_ptr = nullptr;
+    int* upd_pos = nullptr;
+    int *jp_ptr = nullptr, *jp_col = nullptr, *jpt_ptr = nullptr, *jpt_row = nullptr, *jpt_src = nullptr;
+    int *tp_bus = nullptr, *uth = nullptr, *uv = nullptr, *inc_ptr = nullptr, *inc_nb = nullptr;
+    int *inc_uth = nullptr, *inc_uv = nullptr, *gref_row = nullptr, *pg_row = nullptr, *xmap = nullptr;
+    uint8_t* has_gref = nullptr;
+    int n_inc = 0, n_gref = 0;
+
+    // --- device: state ----------------------------------------------------
+    double *vm = nullptr, *va = nullptr, *pg = nullptr, *pd = nullptr, *qd = nullptr, *P = nullptr, *Q = nullptr;
+    double *A = nullptr, *At = nullptr, *invdiag = nullptr, *jpv = nullptr, *jptv = nullptr;
+    double *gres = nullptr, *lam = nullptr, *grad = nullptr, *v1 = nullptr;
+    double4_32a* inc_coef = nullptr;
+    double *d2 = nullptr, *asum = nullptr, *csum = nullptr, *pg_curv = nullptr, *gref_th = nullptr,
+           *gref_v = nullptr, *gref_val = nullptr;
+    double *tmp_bus = nullptr;     // 4 * n_bus scratch for rh_injections
+    double *pbuf = nullptr;        // n_p
+    double *xbuf = nullptr;        // n_x
+    // scalars: cref, c2ref, F
+    double* dscal = nullptr;
+    unsigned long long* umax = nullptr;  // gmax, jmax
+    int* err = nullptr;
+
+    // --- workspace for the direction kernel --------------------------------
+    double *V = nullptr, *T = nullptr;
+    size_t ws_cols = 0;
+    double *stage_in = nullptr, *stage_out = nullptr;
+    size_t stage_n = 0;
+
+    bool adjoint_ready = false;
+
+    ~rh_grid() {
+        for (void* p : allocs) cudaFree(p);
+        if (V) cudaFree(V);
+        if (T) cudaFree(T);
+        if (stage_in) cudaFree(stage_in);
+        if (stage_out) cudaFree(stage_out);
+        if (stream) cudaStreamDestroy(stream);
+    }
+
+    template <typename T_>
+    cudaError_t alloc(T_*& p, size_t n) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, (n ? n : 1) * sizeof(T_));
+        if (e != cudaSuccess) return e;
+        allocs.push_back(q);
+        p = (T_*)q;
+        return cudaMemset(q, 0, (n ? n : 1) * sizeof(T_));
+    }
+    template <typename T_>
+    cudaError_t upload(T_*& p, const std::vector<T_>& v) {
+        cudaError_t e = alloc(p, v.size());
+        if (e != cudaSuccess || v.empty()) return e;
+        return cudaMemcpy(p, v.data(), v.size() * sizeof(T_), cudaMemcpyHostToDevice);
+    }
+
+    rh::PfGrid pf() const {
+        rh::PfGrid g;
+        g.n_bus = S.n_bus;
+        g.n_x = S.n_x;
+        g.ref = S.ref;
+        g.yp = yp; g.yj = yj; g.ydiag = ydiag; g.G = G; g.B = B;
+        g.qth = qth; g.qv = qv; g.ip_v = ip_v; g.ip_pg = ip_pg;
+        g.jac_dst = jac_dst; g.pg_slot = pg_slot;
+        g.base_mva = base_mva; g.c2 = c2; g.c1 = c1;
+        return g;
+    }
+    rh::PfState st() const {
+        rh::PfState s;
+        s.vm = vm; s.va = va; s.pg = pg; s.pd = pd; s.qd = qd; s.P = P; s.Q = Q;
+        return s;
+    }
+    rh::DirGrid dir() const {
+        rh::DirGrid g;
+        g.n_x = S.n_x; g.n_p = S.n_p; g.zero_row = S.n_x + S.n_p;
+        g.rowptr = rowptr; g.col = col; g.diagpos = diagpos; g.A = A; g.At = At; g.invdiag = invdiag;
+        g.q0 = q0; g.nv = nv;
+        g.n_flev = S.n_flev; g.n_blev = S.n_blev;
+        g.flev_ptr = flev_ptr; g.flev_bus = flev_bus; g.flev_maxext = flev_maxext;
+        g.blev_ptr = blev_ptr; g.blev_bus = blev_bus; g.blev_maxext = blev_maxext;
+        g.jp_ptr = jp_ptr; g.jp_col = jp_col; g.jpv = jpv;
+        g.jpt_ptr = jpt_ptr; g.jpt_row = jpt_row; g.jptv = jptv;
+        g.n_bus = S.n_bus; g.tp_bus = tp_bus; g.uth = uth; g.uv = uv;
+        g.inc_ptr = inc_ptr; g.inc_uth = inc_uth; g.inc_uv = inc_uv; g.inc_coef = inc_coef;
+        g.d2 = d2; g.asum = asum; g.csum = csum; g.has_gref = has_gref; g.gref_th = gref_th; g.gref_v = gref_v;
+        g.n_gref = n_gref; g.gref_row = gref_row; g.gref_val = gref_val; g.c2ref = dscal + 1;
+        g.pg_row = pg_row; g.pg_curv = pg_curv;
+        return g;
+    }
+    int rows() const { return S.n_x + S.n_p + 1; }
+};
+
+namespace {
+
+rh_status set_device(const rh_grid* g) {
+    if (g->device < 0) return fail(RH_ESTATE, "grid was created without a device (symbolic only)");
+    RH_CUDA(cudaSetDevice(g->device));
+    return RH_OK;
+}
+
+rh_status ensure_ws(rh_grid* g, size_t cols) {
+    if (cols <= g->ws_cols) return RH_OK;
+    if (g->V) { cudaFree(g->V); g->V = nullptr; }
+    if (g->T) { cudaFree(g->T); g->T = nullptr; }
+    g->ws_cols = 0;
+    size_t n = (size_t)g->rows() * cols;
+    RH_CUDA(cudaMalloc(&g->V, n * sizeof(double)));
+    RH_CUDA(cudaMalloc(&g->T, n * sizeof(double)));
+    g->ws_cols = cols;
+    return RH_OK;
+}
+
+rh_status ensure_stage(rh_grid* g, size_t n) {
+    if (n <= g->stage_n) return RH_OK;
+    if (g->stage_in) { cudaFree(g->stage_in); g->stage_in = nullptr; }
+    if (g->stage_out) { cudaFree(g->stage_out); g->stage_out = nullptr; }
+    g->stage_n = 0;
+    RH_CUDA(cudaMalloc(&g->stage_in, n * sizeof(double)));
+    RH_CUDA(cudaMalloc(&g->stage_out, n * sizeof(double)));
+    g->stage_n = n;
+    return RH_OK;
+}
+
+rh_status check_err_flag(rh_grid* g) {
+    int e = 0;
+    RH_CUDA(cudaMemcpyAsync(&e, g->err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    RH_CUDA(cudaStreamSynchronize(g->stream));
+    if (e & 1) return fail(RH_ESINGULAR, "LU refactorisation: a static pivot is below 1e-14 max|J_x|");
+    return RH_OK;
+}
+
+// J_x, J_p at the current state, refactorisation, transposed copies.
+rh_status assemble_and_factor(rh_grid* g) {
+    const auto& S = g->S;
+    cudaStream_t s = g->stream;
+    RH_CUDA(cudaMemsetAsync(g->A, 0, sizeof(double) * S.col.size(), s));
+    RH_CUDA(cudaMemsetAsync(g->umax, 0, 2 * sizeof(unsigned long long), s));
+    RH_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
+    rh::launch_pf_eval(g->pf(), g->st(), nullptr, g->A, g->jpv, g->umax, g->umax + 1, true, s);
+    rh::launch_refactor(S.flev_ptr.data(), S.n_flev, g->flev_bus, g->q0, g->nv, g->rowptr, g->col, g->diagpos,
+                        g->lrank_ptr, g->upd_ptr, g->upd_pos, g->A, g->invdiag, g->umax + 1, g->err, s);
+    rh::launch_transpose_values((int)S.col.size(), g->tpos, g->A, g->At, (int)S.jp_col.size(), g->jpt_src, g->jpv,
+                                g->jptv, s);
+    RH_CUDA(cudaGetLastError());
+    return check_err_flag(g);
+}
+
+rh_status dirs(rh_grid* g, int N, int64_t ld, double* V, double* T, const double* W, int64_t ldw, int col0,
+               double* HW, int64_t ldhw, unsigned phases, cudaStream_t s) {
+    rh::DirLaunch L;
+    L.N = N;
+    L.n_cta = rh::dirs_default_ctas(N);
+    L.ld = ld;
+    L.V = V;
+    L.T = T;
+    L.W = W;
+    L.ldw = ldw;
+    L.col0 = col0;
+    L.HW = HW;
+    L.ldhw = ldhw;
+    L.phases = phases;
+    rh::launch_dirs(g->dir(), L, s);
+    RH_CUDA(cudaGetLastError());
+    return RH_OK;
+}
+
+__global__ void k_set_p(int n_bus, const int* ip_v, const int* ip_pg, const double* p, double* vm, double* pg) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_bus) return;
+    if (ip_v[i] >= 0) vm[i] = p[ip_v[i]];
+    pg[i] = ip_pg[i] >= 0 ? p[ip_pg[i]] : 0.0;
+}
+
+__global__ void k_set_x(int n_bus, const int* ix_th, const int* ix_v, const double* x, double* vm, double* va) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_bus) return;
+    va[i] = ix_th[i] >= 0 ? x[ix_th[i]] : 0.0;
+    if (ix_v[i] >= 0) vm[i] = x[ix_v[i]];
+}
+
+__global__ void k_get_x(int n_bus, const int* ix_th, const int* ix_v, const double* vm, const double* va, double* x) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_bus) return;
+    if (ix_th[i] >= 0) x[ix_th[i]] = va[i];
+    if (ix_v[i] >= 0) x[ix_v[i]] = vm[i];
+}
+
+int nblk(int n, int t) { return (n + t - 1) / t; }
+
+}  // namespace
+
+extern "C" {
+
+const char* rh_last_error(void) { return g_last_error.c_str(); }
+
+rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
+    if (!out) return fail(RH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!d || !d->from || !d->to || !d->r || !d->x || !d->b || !d->bus_type || !d->c2 || !d->c1)
+        return fail(RH_EINVAL, "grid descriptor has a NULL array");
+    if (!(d->base_mva > 0.0)) return fail(RH_EINVAL, "base_mva must be positive");
+    std::unique_ptr<rh_grid> g(new rh_grid());
+    g->device = device;
+    g->base_mva = d->base_mva;
+    std::string msg = rh::build_symbolic(d->n_bus, d->n_branch, d->from, d->to, d->r, d->x, d->b, d->bus_type, g->S);
+    if (!msg.empty()) return fail(RH_EINVAL, msg);
+    const auto& S = g->S;
+    if (device < 0) {  // symbolic phase only: no device state
+        *out = g.release();
+        return RH_OK;
+    }
+    RH_CUDA(cudaSetDevice(device));
+    RH_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+    int nb = S.n_bus, nx = S.n_x, np = S.n_p;
+    int zero_row = nx + np;
+
+    // projection structure
+    std::vector<int> uth(nb), uv(nb), pg_row(nb, -1), inc_ptr(nb + 1, 0), inc_nb, inc_uth, inc_uv;
+    std::vector<uint8_t> has_gref(nb, 0);
+    for (int i = 0; i < nb; i++) {
+        uth[i] = S.qth[i] >= 0 ? S.qth[i] : zero_row;
+        uv[i] = S.qv[i] >= 0 ? S.qv[i] : nx + S.ip_v[i];
+        if (S.ip_pg[i] >= 0) pg_row[i] = nx + S.ip_pg[i];
+    }
+    for (int i = 0; i < nb; i++) {
+        for (int t = S.yp[i]; t < S.yp[i + 1]; t++) {
+            int j = S.yj[t];
+            if (j == i) continue;
+            inc_nb.push_back(j);
+            inc_uth.push_back(uth[j]);
+            inc_uv.push_back(uv[j]);
+        }
+        inc_ptr[i + 1] = (int)inc_nb.size();
+    }
+    has_gref[S.ref] = 1;
+    for (int t = S.yp[S.ref]; t < S.yp[S.ref + 1]; t++) has_gref[S.yj[t]] = 1;
+    g->n_inc = (int)inc_nb.size();
+    g->n_gref = 1 + 2 * (S.yp[S.ref + 1] - S.yp[S.ref] - 1);
+    std::vector<int> tp_bus(S.ebus);
+    tp_bus.push_back(S.ref);
+    std::vector<int> xmap(nx + np);
+    for (int q = 0; q < nx; q++) xmap[S.perm[q]] = q;
+    for (int k = 0; k < np; k++) xmap[nx + k] = nx + k;
+
+    std::vector<double> c2v(d->c2, d->c2 + nb), c1v(d->c1, d->c1 + nb);
+    std::vector<int> flev_ptr(S.flev_ptr), blev_ptr(S.blev_ptr);
+    RH_CUDA(g->upload(g->yp, S.yp));
+    RH_CUDA(g->upload(g->yj, S.yj));
+    RH_CUDA(g->upload(g->ydiag, S.ydiag));
+    RH_CUDA(g->upload(g->G, S.G));
+    RH_CUDA(g->upload(g->B, S.B));
+    RH_CUDA(g->upload(g->qth, S.qth));
+    RH_CUDA(g->upload(g->qv, S.qv));
+    RH_CUDA(g->upload(g->ip_v, S.ip_v));
+    RH_CUDA(g->upload(g->ip_pg, S.ip_pg));
+    RH_CUDA(g->upload(g->ix_th, S.ix_th));
+    RH_CUDA(g->upload(g->ix_v, S.ix_v));
+    RH_CUDA(g->upload(g->pg_slot, S.pg_slot));
+    RH_CUDA(g->upload(g->jac_dst, S.jac_dst));
+    RH_CUDA(g->upload(g->c2, c2v));
+    RH_CUDA(g->upload(g->c1, c1v));
+    RH_CUDA(g->upload(g->rowptr, S.rowptr));
+    RH_CUDA(g->upload(g->col, S.col));
+    RH_CUDA(g->upload(g->diagpos, S.diagpos));
+    RH_CUDA(g->upload(g->tpos, S.tpos));
+    RH_CUDA(g->upload(g->q0, S.q0));
+    RH_CUDA(g->upload(g->nv, S.nv));
+    RH_CUDA(g->upload(g->flev_ptr, flev_ptr));
+    RH_CUDA(g->upload(g->flev_bus, S.flev_bus));
+    RH_CUDA(g->upload(g->flev_maxext, S.flev_maxext));
+    RH_CUDA(g->upload(g->blev_ptr, blev_ptr));
+    RH_CUDA(g->upload(g->blev_bus, S.blev_bus));
+    RH_CUDA(g->upload(g->blev_maxext, S.blev_maxext));
+    RH_CUDA(g->upload(g->lrank_ptr, S.lrank_ptr));
+    RH_CUDA(g->upload(g->upd_ptr, S.upd_ptr));
+    RH_CUDA(g->upload(g->upd_pos, S.upd_pos));
+    RH_CUDA(g->upload(g->jp_ptr, S.jp_ptr));
+    RH_CUDA(g->upload(g->jp_col, S.jp_col));
+    RH_CUDA(g->upload(g->jpt_ptr, S.jpt_ptr));
+    RH_CUDA(g->upload(g->jpt_row, S.jpt_row));
+    RH_CUDA(g->upload(g->jpt_src, S.jpt_src));
+    RH_CUDA(g->upload(g->tp_bus, tp_bus));
+    RH_CUDA(g->upload(g->uth, uth));
+    RH_CUDA(g->upload(g->uv, uv));
+    RH_CUDA(g->upload(g->inc_ptr, inc_ptr));
+    RH_CUDA(g->upload(g->inc_nb, inc_nb));
+    RH_CUDA(g->upload(g->inc_uth, inc_uth));
+    RH_CUDA(g->upload(g->inc_uv, inc_uv));
+    RH_CUDA(g->upload(g->has_gref, has_gref));
+    RH_CUDA(g->upload(g->pg_row, pg_row));
+    RH_CUDA(g->upload(g->xmap, xmap));
+    RH_CUDA(g->alloc(g->gref_row, g->n_gref));
+    // state
+    std::vector<double> ones(nb, 1.0);
+    RH_CUDA(g->upload(g->vm, ones));
+    RH_CUDA(g->alloc(g->va, nb));
+    RH_CUDA(g->alloc(g->pg, nb));
+    RH_CUDA(g->alloc(g->pd, nb));
+    RH_CUDA(g->alloc(g->qd, nb));
+    RH_CUDA(g->alloc(g->P, nb));
+    RH_CUDA(g->alloc(g->Q, nb));
+    RH_CUDA(g->alloc(g->A, S.col.size()));
+    RH_CUDA(g->alloc(g->At, S.col.size()));
+    RH_CUDA(g->alloc(g->invdiag, nx));
+    RH_CUDA(g->alloc(g->jpv, S.jp_col.size()));
+    RH_CUDA(g->alloc(g->jptv, S.jp_col.size()));
+    RH_CUDA(g->alloc(g->gres, nx));
+    RH_CUDA(g->alloc(g->lam, nx));
+    RH_CUDA(g->alloc(g->grad, np));
+    RH_CUDA(g->alloc(g->v1, g->rows()));
+    RH_CUDA(g->alloc(g->inc_coef, g->n_inc));
+    RH_CUDA(g->alloc(g->d2, nb));
+    RH_CUDA(g->alloc(g->asum, nb));
+    RH_CUDA(g->alloc(g->csum, nb));
+    RH_CUDA(g->alloc(g->pg_curv, nb));
+    RH_CUDA(g->alloc(g->gref_th, nb));
+    RH_CUDA(g->alloc(g->gref_v, nb));
+    RH_CUDA(g->alloc(g->gref_val, g->n_gref));
+    RH_CUDA(g->alloc(g->tmp_bus, 4 * (size_t)nb));
+    RH_CUDA(g->alloc(g->pbuf, np));
+    RH_CUDA(g->alloc(g->xbuf, nx));
+    RH_CUDA(g->alloc(g->dscal, 4));
+    RH_CUDA(g->alloc(g->umax, 2));
+    RH_CUDA(g->alloc(g->err, 1));
+    RH_CUDA(cudaDeviceSynchronize());
+    *out = g.release();
+    return RH_OK;
+}
+
+void rh_grid_destroy(rh_grid* g) {
+    if (!g) return;
+    if (g->device >= 0) cudaSetDevice(g->device);
+    delete g;
+}
+
+rh_status rh_grid_dims(const rh_grid* g, rh_dims* o) {
+    if (!g || !o) return fail(RH_EINVAL, "NULL argument");
+    const auto& S = g->S;
+    o->n_bus = S.n_bus; o->n_branch = S.n_branch; o->n_gen = S.n_gen; o->n_pv = S.n_pv; o->n_pq = S.n_pq;
+    o->n_x = S.n_x; o->n_p = S.n_p; o->n_levels_fwd = S.n_flev; o->n_levels_bwd = S.n_blev;
+    o->nnz_jx = S.nnz_jx; o->nnz_jp = (int64_t)S.jp_col.size();
+    o->nnz_l = S.nnz_l; o->nnz_u = S.nnz_u;
+    o->refactor_updates = (int64_t)S.upd_pos.size();
+    return RH_OK;
+}
+
+rh_status rh_grid_symbolic(const rh_grid* g, int32_t* perm, int32_t* bus_order, int32_t* level, int32_t* Lp,
+                           int32_t* Lj, int32_t* Up, int32_t* Uj) {
+    if (!g) return fail(RH_EINVAL, "NULL grid");
+    const auto& S = g->S;
+    if (perm) for (int q = 0; q < S.n_x; q++) perm[q] = S.perm[q];
+    if (bus_order) for (int k = 0; k < S.n_elim; k++) bus_order[k] = S.ebus[k];
+    if (level) for (int k = 0; k < S.n_elim; k++) level[k] = S.flevel[k];
+    int64_t nl = 0, nu = 0;
+    for (int q = 0; q < S.n_x; q++) {
+        if (Lp) Lp[q] = (int32_t)nl;
+        if (Up) Up[q] = (int32_t)nu;
+        for (int s = S.rowptr[q]; s < S.diagpos[q]; s++) { if (Lj) Lj[nl] = S.col[s]; nl++; }
+        for (int s = S.diagpos[q]; s < S.rowptr[q + 1]; s++) { if (Uj) Uj[nu] = S.col[s]; nu++; }
+    }
+    if (Lp) Lp[S.n_x] = (int32_t)nl;
+    if (Up) Up[S.n_x] = (int32_t)nu;
+    return RH_OK;
+}
+
+rh_status rh_injections(rh_grid* g, const double* vm, const double* va, double* P, double* Q) {
+    if (!g || !vm || !va || !P || !Q) return fail(RH_EINVAL, "NULL argument");
+    rh_status st = set_device(g);
+    if (st) return st;
+    int nb = g->S.n_bus;
+    rh::PfState s = g->st();
+    s.vm = g->tmp_bus; s.va = g->tmp_bus + nb; s.P = g->tmp_bus + 2 * nb; s.Q = g->tmp_bus + 3 * nb;
+    RH_CUDA(cudaMemcpyAsync(s.vm, vm, nb * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+    RH_CUDA(cudaMemcpyAsync(s.va, va, nb * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+    rh::launch_injections(g->pf(), s, g->stream);
+    RH_CUDA(cudaGetLastError());
+    RH_CUDA(cudaMemcpyAsync(P, s.P, nb * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    RH_CUDA(cudaMemcpyAsync(Q, s.Q, nb * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    RH_CUDA(cudaStreamSynchronize(g->stream));
+    return RH_OK;
+}
+
+rh_status rh_set_state(rh_grid* g, const double* p, const double* pd, const double* qd) {
+    if (!g || !p) return fail(RH_EINVAL, "NULL argument");
+    rh_status st = set_device(g);
+    if (st) return st;
+    int nb = g->S.n_bus;
+    RH_CUDA(cudaMemcpyAsync(g->pbuf, p, g->S.n_p * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+    if (pd) RH_CUDA(cudaMemcpyAsync(g->pd, pd, nb * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+    if (qd) RH_CUDA(cudaMemcpyAsync(g->qd, qd, nb * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+    k_set_p<<<nblk(nb, 128), 128, 0, g->stream>>>(nb, g->ip_v, g->ip_pg, g->pbuf, g->vm, g->pg);
+    RH_CUDA(cudaGetLastError());
+    RH_CUDA(cudaStreamSynchronize(g->stream));
+    g->adjoint_ready = false;
+    return RH_OK;
+}
+
+rh_status rh_powerflow(rh_grid* g, const double* x0, double tol, int32_t max_iter, double* x_out, int32_t* iters,
+                       double* resid) {
+    if (!g) return fail(RH_EINVAL, "NULL grid");
+    if (!(tol >= 0.0) || max_iter < 0) return fail(RH_EINVAL, "tol must be >= 0 and max_iter >= 0");
+    rh_status st = set_device(g);
+    if (st) return st;
+    const auto& S = g->S;
+    int nb = S.n_bus, nx = S.n_x;
+    cudaStream_t s = g->stream;
+    g->adjoint_ready = false;
+    if (x0) {
+        RH_CUDA(cudaMemcpyAsync(g->xbuf, x0, nx * sizeof(double), cudaMemcpyHostToDevice, s));
+        k_set_x<<<nblk(nb, 128), 128, 0, s>>>(nb, g->ix_th, g->ix_v, g->xbuf, g->vm, g->va);
+    }
+    int it = 0;
+    double res = INFINITY;
+    rh_status out = RH_ENOCONV;
+    for (;;) {
+        RH_CUDA(cudaMemsetAsync(g->A, 0, sizeof(double) * S.col.size(), s));
+        RH_CUDA(cudaMemsetAsync(g->umax, 0, 2 * sizeof(unsigned long long), s));
+        RH_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
+        rh::launch_pf_eval(g->pf(), g->st(), g->gres, g->A, g->jpv, g->umax, g->umax + 1, true, s);
+        unsigned long long bits = 0;
+        RH_CUDA(cudaMemcpyAsync(&bits, g->umax, sizeof(bits), cudaMemcpyDeviceToHost, s));
+        RH_CUDA(cudaStreamSynchronize(s));
+        std::memcpy(&res, &bits, sizeof(res));
+        if (nx == 0) res = 0.0;
+        if (res <= tol) { out = RH_OK; break; }
+        if (it >= max_iter || !std::isfinite(res)) break;
+        rh::launch_refactor(S.flev_ptr.data(), S.n_flev, g->flev_bus, g->q0, g->nv, g->rowptr, g->col, g->diagpos,
+                            g->lrank_ptr, g->upd_ptr, g->upd_pos, g->A, g->invdiag, g->umax + 1, g->err, s);
+        st = check_err_flag(g);
+        if (st) return st;
+        RH_CUDA(cudaMemcpyAsync(g->v1, g->gres, nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        st = dirs(g, 1, 1, g->v1, g->v1, nullptr, 0, 0, nullptr, 0, rh::PH_L | rh::PH_U, s);
+        if (st) return st;
+        rh::launch_newton_update(g->pf(), g->st(), g->v1, s);
+        RH_CUDA(cudaGetLastError());
+        it++;
+    }
+    if (iters) *iters = it;
+    if (resid) *resid = res;
+    if (x_out) {
+        k_get_x<<<nblk(nb, 128), 128, 0, s>>>(nb, g->ix_th, g->ix_v, g->vm, g->va, g->xbuf);
+        RH_CUDA(cudaGetLastError());
+        RH_CUDA(cudaMemcpyAsync(x_out, g->xbuf, nx * sizeof(double), cudaMemcpyDeviceToHost, s));
+        RH_CUDA(cudaStreamSynchronize(s));
+    }
+    if (out != RH_OK) return fail(out, "Newton did not reach the tolerance");
+    return RH_OK;
+}
+
+rh_status rh_refactor(rh_grid* g, double* A_out) {
+    if (!g) return fail(RH_EINVAL, "NULL grid");
+    rh_status st = set_device(g);
+    if (st) return st;
+    g->adjoint_ready = false;
+    st = assemble_and_factor(g);
+    if (st) return st;
+    if (A_out) {
+        RH_CUDA(cudaMemcpyAsync(A_out, g->A, sizeof(double) * g->S.col.size(), cudaMemcpyDeviceToHost, g->stream));
+        RH_CUDA(cudaStreamSynchronize(g->stream));
+    }
+    return RH_OK;
+}
+
+rh_status rh_adjoint(rh_grid* g, double* F, double* lambda, double* grad) {
+    if (!g) return fail(RH_EINVAL, "NULL grid");
+    rh_status st = set_device(g);
+    if (st) return st;
+    const auto& S = g->S;
+    cudaStream_t s = g->stream;
+    g->adjoint_ready = false;
+    st = assemble_and_factor(g);
+    if (st) return st;
+    // lambda = -J_x^{-T} grad_x f
+    RH_CUDA(cudaMemsetAsync(g->v1, 0, sizeof(double) * g->rows(), s));
+    rh::AdjData a;
+    a.rhs = g->v1; a.cref = g->dscal; a.c2ref = g->dscal + 1; a.F = g->dscal + 2;
+    a.gref_th = g->gref_th; a.gref_v = g->gref_v; a.gref_row = g->gref_row; a.gref_val = g->gref_val;
+    a.n_gref = g->n_gref; a.uth = g->uth; a.uv = g->uv;
+    rh::launch_adjoint_rhs(g->pf(), g->st(), a, s);
+    st = dirs(g, 1, 1, g->v1, g->v1, nullptr, 0, 0, nullptr, 0, rh::PH_UT | rh::PH_LT, s);
+    if (st) return st;
+    RH_CUDA(cudaMemcpyAsync(g->lam, g->v1, S.n_x * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    rh::launch_adjoint_coef(g->pf(), g->st(), g->lam, g->dscal, g->inc_ptr, g->inc_nb, g->inc_coef, g->d2, g->asum,
+                            g->csum, g->pg_curv, s);
+    rh::launch_gradient(g->pf(), g->st(), S.n_p, g->jpt_ptr, g->jpt_row, g->jptv, g->lam, g->dscal, g->gref_v,
+                        g->grad, s);
+    RH_CUDA(cudaGetLastError());
+    if (lambda) {
+        rh::launch_gather_rows(S.n_x, 1, g->xmap, g->lam, 1, g->xbuf, S.n_x, 1.0, S.n_x, s);
+        RH_CUDA(cudaMemcpyAsync(lambda, g->xbuf, S.n_x * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    if (grad) RH_CUDA(cudaMemcpyAsync(grad, g->grad, S.n_p * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (F) RH_CUDA(cudaMemcpyAsync(F, g->dscal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    RH_CUDA(cudaStreamSynchronize(s));
+    g->adjoint_ready = true;
+    return RH_OK;
+}
+
+rh_status rh_hessvec(rh_grid* g, const double* W, int64_t ldw, int32_t N, double* HW, int64_t ldhw, void* stream,
+                     uint32_t flags) {
+    if (!g) return fail(RH_EINVAL, "NULL grid");
+    if (N < 0) return fail(RH_EINVAL, "N must be >= 0");
+    if (N == 0) return RH_OK;
+    const auto& S = g->S;
+    if (!W || !HW || ldw < S.n_p || ldhw < S.n_p) return fail(RH_EINVAL, "bad W / HW or leading dimension");
+    if (!g->adjoint_ready) return fail(RH_ESTATE, "rh_hessvec needs rh_adjoint for the current state");
+    rh_status st = set_device(g);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = ensure_ws(g, (size_t)N);
+    if (st) return st;
+    const double* Wd = W;
+    double* HWd = HW;
+    int64_t lw = ldw, lh = ldhw;
+    bool host = !(flags & RH_DEVICE_PTRS);
+    if (host) {
+        st = ensure_stage(g, (size_t)S.n_p * N);
+        if (st) return st;
+        RH_CUDA(cudaMemcpy2DAsync(g->stage_in, S.n_p * sizeof(double), W, ldw * sizeof(double),
+                                  S.n_p * sizeof(double), N, cudaMemcpyHostToDevice, s));
+        Wd = g->stage_in;
+        HWd = g->stage_out;
+        lw = lh = S.n_p;
+    }
+    st = dirs(g, N, N, g->V, g->T, Wd, lw, 0, HWd, lh,
+              rh::PH_WLOAD | rh::PH_SPMUL | rh::PH_L | rh::PH_U | rh::PH_TPROJ | rh::PH_UT | rh::PH_LT |
+                  rh::PH_MULADD,
+              s);
+    if (st) return st;
+    if (host) {
+        RH_CUDA(cudaMemcpy2DAsync(HW, ldhw * sizeof(double), g->stage_out, S.n_p * sizeof(double),
+                                  S.n_p * sizeof(double), N, cudaMemcpyDeviceToHost, s));
+        RH_CUDA(cudaStreamSynchronize(s));
+    }
+    return RH_OK;
+}
+
+rh_status rh_hessian(rh_grid* g, int32_t block_n, double* H, int64_t ldh, void* stream, uint32_t flags) {
+    if (!g) return fail(RH_EINVAL, "NULL grid");
+    const auto& S = g->S;
+    if (!H || ldh < S.n_p) return fail(RH_EINVAL, "bad H or leading dimension");
+    if (block_n <= 0) return fail(RH_EINVAL, "block_n must be positive");
+    if (!g->adjoint_ready) return fail(RH_ESTATE, "rh_hessian needs rh_adjoint for the current state");
+    rh_status st = set_device(g);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    int np = S.n_p;
+    bool concurrent = (flags & RH_HESSIAN_CONCURRENT) != 0;
+    int width = concurrent ? np : (block_n < np ? block_n : np);
+    st = ensure_ws(g, (size_t)width);
+    if (st) return st;
+    bool host = !(flags & RH_DEVICE_PTRS);
+    double* Hd = H;
+    int64_t lh = ldh;
+    if (host) {
+        st = ensure_stage(g, (size_t)np * np);
+        if (st) return st;
+        Hd = g->stage_out;
+        lh = np;
+    }
+    const unsigned all = rh::PH_WLOAD | rh::PH_SPMUL | rh::PH_L | rh::PH_U | rh::PH_TPROJ | rh::PH_UT | rh::PH_LT |
+                         rh::PH_MULADD;
+    if (concurrent) {
+        st = dirs(g, np, np, g->V, g->T, nullptr, 0, 0, Hd, lh, all, s);
+        if (st) return st;
+    } else {
+        for (int c0 = 0; c0 < np; c0 += block_n) {
+            int n = np - c0 < block_n ? np - c0 : block_n;
+            st = dirs(g, n, width, g->V, g->T, nullptr, 0, c0, Hd + (int64_t)c0 * lh, lh, all, s);
+            if (st) return st;
+        }
+    }
+    if (host) {
+        RH_CUDA(cudaMemcpy2DAsync(H, ldh * sizeof(double), Hd, lh * sizeof(double), np * sizeof(double), np,
+                                  cudaMemcpyDeviceToHost, s));
+        RH_CUDA(cudaStreamSynchronize(s));
+    }
+    return RH_OK;
+}
+
+rh_status rh_solve(rh_grid* g, double* R, int64_t ldr, int32_t nrhs, int32_t trans, void* stream, uint32_t flags) {
+    if (!g) return fail(RH_EINVAL, "NULL grid");
+    const auto& S = g->S;
+    if (nrhs < 0 || !R || ldr < S.n_x) return fail(RH_EINVAL, "bad R, leading dimension or nrhs");
+    if (nrhs == 0) return RH_OK;
+    rh_status st = set_device(g);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = ensure_ws(g, (size_t)nrhs);
+    if (st) return st;
+    double* Rd = R;
+    int64_t lr = ldr;
+    bool host = !(flags & RH_DEVICE_PTRS);
+    if (host) {
+        st = ensure_stage(g, (size_t)S.n_x * nrhs);
+        if (st) return st;
+        RH_CUDA(cudaMemcpy2DAsync(g->stage_in, S.n_x * sizeof(double), R, ldr * sizeof(double),
+                                  S.n_x * sizeof(double), nrhs, cudaMemcpyHostToDevice, s));
+        Rd = g->stage_in;
+        lr = S.n_x;
+    }
+    rh::launch_scatter_rows(S.n_x, nrhs, g->xmap, Rd, lr, g->V, nrhs, 1.0, S.n_x, s);
+    st = dirs(g, nrhs, nrhs, g->V, g->V, nullptr, 0, 0, nullptr, 0,
+              trans ? (rh::PH_UT | rh::PH_LT) : (rh::PH_L | rh::PH_U), s);
+    if (st) return st;
+    rh::launch_gather_rows(S.n_x, nrhs, g->xmap, g->V, nrhs, Rd, lr, 1.0, S.n_x, s);
+    RH_CUDA(cudaGetLastError());
+    if (host) {
+        RH_CUDA(cudaMemcpy2DAsync(R, ldr * sizeof(double), g->stage_in, S.n_x * sizeof(double),
+                                  S.n_x * sizeof(double), nrhs, cudaMemcpyDeviceToHost, s));
+        RH_CUDA(cudaStreamSynchronize(s));
+    }
+    return RH_OK;
+}
+
+rh_status rh_lagrangian_hessvec(rh_grid* g, const double* V, int64_t ldv, int32_t N, double* Y, int64_t ldy,
+                                void* stream, uint32_t flags) {
+    if (!g) return fail(RH_EINVAL, "NULL grid");
+    const auto& S = g->S;
+    int nu = S.n_x + S.n_p;
+    if (N < 0 || !V || !Y || ldv < nu || ldy < nu) return fail(RH_EINVAL, "bad V / Y, leading dimension or N");
+    if (N == 0) return RH_OK;
+    if (!g->adjoint_ready) return fail(RH_ESTATE, "needs rh_adjoint for the current state");
+    rh_status st = set_device(g);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = ensure_ws(g, (size_t)N);
+    if (st) return st;
+    const double* Vd = V;
+    double* Yd = Y;
+    int64_t lv = ldv, ly = ldy;
+    bool host = !(flags & RH_DEVICE_PTRS);
+    if (host) {
+        st = ensure_stage(g, (size_t)nu * N);
+        if (st) return st;
+        RH_CUDA(cudaMemcpy2DAsync(g->stage_in, nu * sizeof(double), V, ldv * sizeof(double), nu * sizeof(double), N,
+                                  cudaMemcpyHostToDevice, s));
+        Vd = g->stage_in;
+        Yd = g->stage_out;
+        lv = ly = nu;
+    }
+    rh::launch_scatter_rows(nu, N, g->xmap, Vd, lv, g->V, N, 1.0, S.n_x, s);
+    RH_CUDA(cudaMemsetAsync(g->V + (size_t)(S.n_x + S.n_p) * N, 0, N * sizeof(double), s));
+    st = dirs(g, N, N, g->V, g->T, nullptr, 0, 0, nullptr, 0, rh::PH_TPROJ, s);
+    if (st) return st;
+    rh::launch_gather_rows(nu, N, g->xmap, g->T, N, Yd, ly, -1.0, S.n_x, s);
+    RH_CUDA(cudaGetLastError());
+    if (host) {
+        RH_CUDA(cudaMemcpy2DAsync(Y, ldy * sizeof(double), g->stage_out, nu * sizeof(double), nu * sizeof(double), N,
+                                  cudaMemcpyDeviceToHost, s));
+        RH_CUDA(cudaStreamSynchronize(s));
+    }
+    return RH_OK;
+}
+
+}  // extern "C"

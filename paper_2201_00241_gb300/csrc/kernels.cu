@@ -1,0 +1,682 @@
+// kernels.cu -- FP64 device kernels of librh (sm_103a).
+//
+// The hot path (Algorithm 2 of arXiv 2201.00241) is FP64-ALU-bound on GB300:
+// one FP64 pipe per SM sub-partition retires one warp-wide DFMA per 64 cycles
+// (about 1.2 TFLOP/s for the chip) and masked-off lanes cost the same issue
+// slot.  The kernels are therefore organised to keep every lane of every
+// DFMA useful:
+//
+//  * Directions are independent, so the direction kernel gives each CTA its
+//    own slice of the N directions and runs every step of Algorithm 2 on it
+//    (SpMul, both triangular sweeps, the projection, both transposed sweeps,
+//    SpMulAdd) with only CTA-local barriers: no grid-wide synchronisation.
+//  * Inside a CTA the work of a level is flattened over (bus, direction)
+//    pairs; narrow levels near the top of the elimination tree additionally
+//    split each row's dot product into k-slices combined through shared
+//    memory, so that at least 4 warps issue FP64 work.
+//  * A bus is a block of one (PV) or two (PQ) variables whose rows share the
+//    same columns outside the bus; one load of x_c feeds two FMAs.
+//  * Right-hand sides are interleaved, row-major [row][ld]: the D directions
+//    of a CTA are contiguous in each row.
+#include <cstdio>
+
+#include "rh_kernels.h"
+
+namespace rh {
+
+namespace {
+
+constexpr int kDirThreads = 256;
+constexpr int kPartCap = 4096;   // doubles of k-split partial sums per CTA
+constexpr int kDMax = 256;       // max directions per CTA
+
+__device__ __forceinline__ unsigned long long ordered_bits(double v) {
+    // |v| as a bit pattern whose unsigned order is the numeric order (NaN above inf)
+    return (unsigned long long)__double_as_longlong(fabs(v));
+}
+
+// ---------------------------------------------------------------------------
+// power flow: injections (eq. 2), residual (eq. 3), Jacobians
+// ---------------------------------------------------------------------------
+
+__global__ void k_injections(PfGrid g, PfState s) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_bus) return;
+    double vi = s.vm[i], ai = s.va[i], p = 0.0, q = 0.0;
+    for (int t = g.yp[i]; t < g.yp[i + 1]; t++) {
+        int j = g.yj[t];
+        double sn, cs;
+        sincos(ai - s.va[j], &sn, &cs);
+        p += s.vm[j] * (g.G[t] * cs + g.B[t] * sn);
+        q += s.vm[j] * (g.G[t] * sn - g.B[t] * cs);
+    }
+    s.P[i] = vi * p;
+    s.Q[i] = vi * q;
+}
+
+// One thread per bus: injections, the two residual rows of the bus and the
+// Jacobian entries of those rows, scattered into the fixed LU / J_p slots.
+__global__ void k_pf_eval(PfGrid g, PfState s, double* gres, double* A, double* jpv,
+                          unsigned long long* gmax, unsigned long long* jmax, int want_jac) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_bus) return;
+    double vi = s.vm[i], ai = s.va[i], P = 0.0, Q = 0.0;
+    for (int t = g.yp[i]; t < g.yp[i + 1]; t++) {
+        int j = g.yj[t];
+        double sn, cs;
+        sincos(ai - s.va[j], &sn, &cs);
+        P += s.vm[j] * (g.G[t] * cs + g.B[t] * sn);
+        Q += s.vm[j] * (g.G[t] * sn - g.B[t] * cs);
+    }
+    P *= vi;
+    Q *= vi;
+    s.P[i] = P;
+    s.Q[i] = Q;
+    int rP = g.qth[i], rQ = g.qv[i];
+    if (rP < 0) return;  // slack: no rows
+    if (gres) {
+        double gp = P - s.pg[i] + s.pd[i];
+        gres[rP] = gp;
+        unsigned long long m = ordered_bits(gp);
+        if (rQ >= 0) {
+            double gq = Q + s.qd[i];
+            gres[rQ] = gq;
+            unsigned long long mq = ordered_bits(gq);
+            m = mq > m ? mq : m;
+        }
+        atomicMax(gmax, m);
+    }
+    if (!want_jac) return;
+    unsigned long long jm = 0;
+    for (int t = g.yp[i]; t < g.yp[i + 1]; t++) {
+        int j = g.yj[t];
+        double d[4];  // dP/dtheta_j, dP/dv_j, dQ/dtheta_j, dQ/dv_j
+        if (j == i) {
+            double Gii = g.G[t], Bii = g.B[t];
+            d[0] = -Q - Bii * vi * vi;
+            d[1] = P / vi + Gii * vi;
+            d[2] = P - Gii * vi * vi;
+            d[3] = Q / vi - Bii * vi;
+        } else {
+            double sn, cs;
+            sincos(ai - s.va[j], &sn, &cs);
+            double vj = s.vm[j], Gij = g.G[t], Bij = g.B[t];
+            d[0] = vi * vj * (Gij * sn - Bij * cs);
+            d[1] = vi * (Gij * cs + Bij * sn);
+            d[2] = -vi * vj * (Gij * cs + Bij * sn);
+            d[3] = vi * (Gij * sn - Bij * cs);
+        }
+        for (int u = 0; u < 4; u++) {
+            int dst = g.jac_dst[4 * t + u];
+            if (dst >= 0) {
+                A[dst] = d[u];
+                unsigned long long b = ordered_bits(d[u]);
+                jm = b > jm ? b : jm;
+            } else if (dst <= -2) {
+                jpv[-(dst + 2)] = d[u];
+            }
+        }
+    }
+    if (g.ip_pg[i] >= 0) jpv[g.pg_slot[i]] = -1.0;
+    atomicMax(jmax, jm);
+}
+
+__global__ void k_newton_update(PfGrid g, PfState s, const double* dx) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_bus) return;
+    if (g.qth[i] >= 0) s.va[i] -= dx[g.qth[i]];
+    if (g.qv[i] >= 0) s.vm[i] -= dx[g.qv[i]];
+}
+
+// ---------------------------------------------------------------------------
+// fixed-pattern LU refactorisation (row-wise elimination, static pivots)
+// ---------------------------------------------------------------------------
+
+// One warp per bus of the level.  Row i of A is eliminated by the finished
+// rows k < i of its L part, in increasing k: l_ik = a_ik / u_kk, then
+// a_ij -= l_ik u_kj for every j > k in row k (positions precomputed).
+// Rows of earlier levels are final; lanes share the updates of one k.
+__global__ void k_refactor_level(int b0, int nb, const int* __restrict__ flev_bus, const int* __restrict__ q0,
+                                 const uint8_t* __restrict__ nv, const int* __restrict__ rowptr,
+                                 const int* __restrict__ col, const int* __restrict__ diagpos,
+                                 const int64_t* __restrict__ lrank_ptr, const int64_t* __restrict__ upd_ptr,
+                                 const int* __restrict__ upd_pos, double* A, double* invdiag,
+                                 const unsigned long long* jmax, int* err) {
+    int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (w >= nb) return;
+    int k = flev_bus[b0 + w];
+    double tau = 1e-14 * __longlong_as_double((long long)*jmax);
+    for (int r = 0; r < nv[k]; r++) {
+        int i = q0[k] + r;
+        int rp = rowptr[i], dp = diagpos[i];
+        int64_t rank0 = lrank_ptr[i];
+        for (int s = rp; s < dp; s++) {
+            int kk = col[s];
+            double l = A[s] * invdiag[kk];
+            __syncwarp();
+            if (lane == 0) A[s] = l;
+            int u0 = diagpos[kk] + 1, cnt = rowptr[kk + 1] - u0;
+            int64_t base = upd_ptr[rank0 + (s - rp)];
+            for (int t = lane; t < cnt; t += 32) {
+                int pos = upd_pos[base + t];
+                A[pos] = fma(-l, A[u0 + t], A[pos]);
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            double piv = A[dp];
+            if (!(fabs(piv) > tau)) atomicOr(err, 1);
+            invdiag[i] = 1.0 / piv;
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_transpose_values(int nnz, const int* __restrict__ tpos, const double* __restrict__ A,
+                                   double* __restrict__ At, int nnz_jp, const int* __restrict__ jpt_src,
+                                   const double* __restrict__ jpv, double* __restrict__ jptv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nnz) At[i] = A[tpos[i]];
+    if (i < nnz_jp) jptv[i] = jpv[jpt_src[i]];
+}
+
+// ---------------------------------------------------------------------------
+// the direction kernel: Algorithm 2 for a slice of directions per CTA
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int choose_ks(int nb, int D, int maxext) {
+    int base = nb * D;
+    if (base >= kDirThreads / 2) return 1;
+    int ks = kDirThreads / base;
+    int lim = maxext / 4;
+    if (ks > lim) ks = lim;
+    int cap = kPartCap / (2 * base);
+    if (ks > cap) ks = cap;
+    return ks < 2 ? 1 : ks;
+}
+
+// forward sweep over the L pattern: x_q = (b_q - sum_{c<q} v_qc x_c) [* 1/u_qq]
+template <bool SCALE>
+__device__ __forceinline__ void fwd_finish(const DirGrid& g, const double* __restrict__ vals, double* X, int64_t ld,
+                                           int64_t c, int q, bool two, int pos_vt, double a0, double a1) {
+    double x0 = SCALE ? a0 * g.invdiag[q] : a0;
+    X[(int64_t)q * ld + c] = x0;
+    if (two) {
+        a1 = fma(-vals[pos_vt], x0, a1);
+        X[(int64_t)(q + 1) * ld + c] = SCALE ? a1 * g.invdiag[q + 1] : a1;
+    }
+}
+
+template <bool SCALE>
+__device__ void sweep_fwd(const DirGrid& g, const double* __restrict__ vals, double* X, int64_t ld, int c0, int D,
+                          double* part) {
+    for (int lev = 0; lev < g.n_flev; lev++) {
+        const int b0 = g.flev_ptr[lev], nb = g.flev_ptr[lev + 1] - b0;
+        const int ks = choose_ks(nb, D, g.flev_maxext[lev]);
+        if (ks == 1) {
+            for (int it = threadIdx.x; it < nb * D; it += blockDim.x) {
+                int bi = it / D, d = it - bi * D;
+                int k = g.flev_bus[b0 + bi];
+                int q = g.q0[k];
+                bool two = g.nv[k] == 2;
+                int rp = g.rowptr[q], n = g.diagpos[q] - rp;
+                int rpv = two ? g.rowptr[q + 1] : rp;
+                int64_t c = c0 + d;
+                double a0 = X[(int64_t)q * ld + c];
+                double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
+                for (int e = 0; e < n; e++) {
+                    double xv = X[(int64_t)g.col[rp + e] * ld + c];
+                    a0 = fma(-vals[rp + e], xv, a0);
+                    if (two) a1 = fma(-vals[rpv + e], xv, a1);
+                }
+                fwd_finish<SCALE>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
+            }
+        } else {
+            const int per = ks * D;
+            for (int it = threadIdx.x; it < nb * per; it += blockDim.x) {
+                int bi = it / per, rem = it - bi * per;
+                int sl = rem / D, d = rem - sl * D;
+                int k = g.flev_bus[b0 + bi];
+                int q = g.q0[k];
+                bool two = g.nv[k] == 2;
+                int rp = g.rowptr[q], n = g.diagpos[q] - rp;
+                int rpv = two ? g.rowptr[q + 1] : rp;
+                int64_t c = c0 + d;
+                int e0 = sl * n / ks, e1 = (sl + 1) * n / ks;
+                double a0 = 0.0, a1 = 0.0;
+                for (int e = e0; e < e1; e++) {
+                    double xv = X[(int64_t)g.col[rp + e] * ld + c];
+                    a0 = fma(-vals[rp + e], xv, a0);
+                    if (two) a1 = fma(-vals[rpv + e], xv, a1);
+                }
+                double* pp = part + 2 * ((bi * ks + sl) * D + d);
+                pp[0] = a0;
+                pp[1] = a1;
+            }
+            __syncthreads();
+            for (int it = threadIdx.x; it < nb * D; it += blockDim.x) {
+                int bi = it / D, d = it - bi * D;
+                int k = g.flev_bus[b0 + bi];
+                int q = g.q0[k];
+                bool two = g.nv[k] == 2;
+                int rp = g.rowptr[q], n = g.diagpos[q] - rp;
+                int rpv = two ? g.rowptr[q + 1] : rp;
+                int64_t c = c0 + d;
+                double a0 = X[(int64_t)q * ld + c];
+                double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
+                for (int sl = 0; sl < ks; sl++) {
+                    const double* pp = part + 2 * ((bi * ks + sl) * D + d);
+                    a0 += pp[0];
+                    a1 += pp[1];
+                }
+                fwd_finish<SCALE>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// backward sweep over the U pattern: x_q = (b_q - sum_{c>q} v_qc x_c) [* 1/u_qq]
+template <bool SCALE>
+__device__ __forceinline__ void bwd_finish(const DirGrid& g, const double* __restrict__ vals, double* X, int64_t ld,
+                                           int64_t c, int q, bool two, int dp, double a0, double a1) {
+    if (two) {
+        double x1 = SCALE ? a1 * g.invdiag[q + 1] : a1;
+        X[(int64_t)(q + 1) * ld + c] = x1;
+        a0 = fma(-vals[dp + 1], x1, a0);
+    }
+    X[(int64_t)q * ld + c] = SCALE ? a0 * g.invdiag[q] : a0;
+}
+
+template <bool SCALE>
+__device__ void sweep_bwd(const DirGrid& g, const double* __restrict__ vals, double* X, int64_t ld, int c0, int D,
+                          double* part) {
+    for (int lev = 0; lev < g.n_blev; lev++) {
+        const int b0 = g.blev_ptr[lev], nb = g.blev_ptr[lev + 1] - b0;
+        const int ks = choose_ks(nb, D, g.blev_maxext[lev]);
+        if (ks == 1) {
+            for (int it = threadIdx.x; it < nb * D; it += blockDim.x) {
+                int bi = it / D, d = it - bi * D;
+                int k = g.blev_bus[b0 + bi];
+                int q = g.q0[k];
+                bool two = g.nv[k] == 2;
+                int dp = g.diagpos[q];
+                int ue0 = dp + (two ? 2 : 1);
+                int n = g.rowptr[q + 1] - ue0;
+                int ue1 = two ? g.diagpos[q + 1] + 1 : ue0;
+                int64_t c = c0 + d;
+                double a0 = X[(int64_t)q * ld + c];
+                double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
+                for (int e = 0; e < n; e++) {
+                    double xv = X[(int64_t)g.col[ue0 + e] * ld + c];
+                    a0 = fma(-vals[ue0 + e], xv, a0);
+                    if (two) a1 = fma(-vals[ue1 + e], xv, a1);
+                }
+                bwd_finish<SCALE>(g, vals, X, ld, c, q, two, dp, a0, a1);
+            }
+        } else {
+            const int per = ks * D;
+            for (int it = threadIdx.x; it < nb * per; it += blockDim.x) {
+                int bi = it / per, rem = it - bi * per;
+                int sl = rem / D, d = rem - sl * D;
+                int k = g.blev_bus[b0 + bi];
+                int q = g.q0[k];
+                bool two = g.nv[k] == 2;
+                int dp = g.diagpos[q];
+                int ue0 = dp + (two ? 2 : 1);
+                int n = g.rowptr[q + 1] - ue0;
+                int ue1 = two ? g.diagpos[q + 1] + 1 : ue0;
+                int64_t c = c0 + d;
+                int e0 = sl * n / ks, e1 = (sl + 1) * n / ks;
+                double a0 = 0.0, a1 = 0.0;
+                for (int e = e0; e < e1; e++) {
+                    double xv = X[(int64_t)g.col[ue0 + e] * ld + c];
+                    a0 = fma(-vals[ue0 + e], xv, a0);
+                    if (two) a1 = fma(-vals[ue1 + e], xv, a1);
+                }
+                double* pp = part + 2 * ((bi * ks + sl) * D + d);
+                pp[0] = a0;
+                pp[1] = a1;
+            }
+            __syncthreads();
+            for (int it = threadIdx.x; it < nb * D; it += blockDim.x) {
+                int bi = it / D, d = it - bi * D;
+                int k = g.blev_bus[b0 + bi];
+                int q = g.q0[k];
+                bool two = g.nv[k] == 2;
+                int dp = g.diagpos[q];
+                int64_t c = c0 + d;
+                double a0 = X[(int64_t)q * ld + c];
+                double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
+                for (int sl = 0; sl < ks; sl++) {
+                    const double* pp = part + 2 * ((bi * ks + sl) * D + d);
+                    a0 += pp[0];
+                    a1 += pp[1];
+                }
+                bwd_finish<SCALE>(g, vals, X, ld, c, q, two, dp, a0, a1);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Projection (eq. 11/13): y = [lambda^T Hess g + Hess f] v for v = (z, w).
+// Gathered bus by bus over the incident branches (no atomics, deterministic):
+//   y_v(b)  = d2_b dv_b + A_b dth_b + sum_e ( K_e dv_j - a_e dth_j )
+//   y_th(b) = A_b dv_b  + C_b dth_b + sum_e ( b_e dv_j - c_e dth_j )
+// plus c''_slack (grad P_slack . v) grad P_slack and c''_k w_Pg_k.
+__device__ void tproj(const DirGrid& g, const double* V, double* T, int64_t ld, int c0, int D, double* sref) {
+    double c2r = *g.c2ref;
+    for (int d = threadIdx.x; d < D; d += blockDim.x) {
+        double s = 0.0;
+        for (int e = 0; e < g.n_gref; e++) s = fma(g.gref_val[e], V[(int64_t)g.gref_row[e] * ld + c0 + d], s);
+        sref[d] = c2r * s;
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < g.n_bus * D; it += blockDim.x) {
+        int bi = it / D, d = it - bi * D;
+        int b = g.tp_bus[bi];
+        int64_t c = c0 + d;
+        int rth = g.uth[b], rv = g.uv[b];
+        double dth = V[(int64_t)rth * ld + c], dv = V[(int64_t)rv * ld + c];
+        double ab = g.asum[b];
+        double yv = fma(g.d2[b], dv, ab * dth);
+        double yth = fma(ab, dv, g.csum[b] * dth);
+        for (int e = g.inc_ptr[b]; e < g.inc_ptr[b + 1]; e++) {
+            double4_32a cf = g.inc_coef[e];
+            double dthj = V[(int64_t)g.inc_uth[e] * ld + c];
+            double dvj = V[(int64_t)g.inc_uv[e] * ld + c];
+            yv = fma(cf.x, dvj, yv);
+            yv = fma(cf.y, dthj, yv);
+            yth = fma(cf.z, dvj, yth);
+            yth = fma(cf.w, dthj, yth);
+        }
+        if (g.has_gref[b]) {
+            yv = fma(sref[d], g.gref_v[b], yv);
+            yth = fma(sref[d], g.gref_th[b], yth);
+        }
+        if (rth != g.zero_row) T[(int64_t)rth * ld + c] = -yth;
+        T[(int64_t)rv * ld + c] = rv < g.n_x ? -yv : yv;
+        int pr = g.pg_row[b];
+        if (pr >= 0) T[(int64_t)pr * ld + c] = g.pg_curv[b] * V[(int64_t)pr * ld + c];
+    }
+}
+
+__global__ void __launch_bounds__(kDirThreads, 2) k_dirs(DirGrid g, DirLaunch L) {
+    __shared__ double part[kPartCap];
+    __shared__ double sref[kDMax];
+    const int cta = blockIdx.x;
+    const int c0 = (int)((int64_t)cta * L.N / L.n_cta);
+    const int c1 = (int)((int64_t)(cta + 1) * L.N / L.n_cta);
+    const int D = c1 - c0;
+    if (D <= 0) return;
+    const int64_t ld = L.ld;
+    double* V = L.V;
+    double* T = L.T;
+    if (L.phases & PH_WLOAD) {
+        for (int it = threadIdx.x; it < g.n_p * D; it += blockDim.x) {
+            int k = it / D, d = it - k * D;
+            int64_t c = c0 + d;
+            double w = L.W ? L.W[c * L.ldw + k] : (k == L.col0 + c ? 1.0 : 0.0);
+            V[(int64_t)(g.n_x + k) * ld + c] = w;
+        }
+        for (int d = threadIdx.x; d < D; d += blockDim.x) V[(int64_t)g.zero_row * ld + c0 + d] = 0.0;
+        __syncthreads();
+    }
+    if (L.phases & PH_SPMUL) {
+        for (int it = threadIdx.x; it < g.n_x * D; it += blockDim.x) {
+            int q = it / D, d = it - q * D;
+            int64_t c = c0 + d;
+            double s = 0.0;
+            for (int t = g.jp_ptr[q]; t < g.jp_ptr[q + 1]; t++)
+                s = fma(g.jpv[t], V[(int64_t)(g.n_x + g.jp_col[t]) * ld + c], s);
+            V[(int64_t)q * ld + c] = -s;
+        }
+        __syncthreads();
+    }
+    if (L.phases & PH_L) sweep_fwd<false>(g, g.A, V, ld, c0, D, part);
+    if (L.phases & PH_U) sweep_bwd<true>(g, g.A, V, ld, c0, D, part);
+    if (L.phases & PH_TPROJ) {
+        tproj(g, V, T, ld, c0, D, sref);
+        __syncthreads();
+    }
+    if (L.phases & PH_UT) sweep_fwd<true>(g, g.At, T, ld, c0, D, part);
+    if (L.phases & PH_LT) sweep_bwd<false>(g, g.At, T, ld, c0, D, part);
+    if (L.phases & PH_MULADD) {
+        for (int it = threadIdx.x; it < g.n_p * D; it += blockDim.x) {
+            int k = it / D, d = it - k * D;
+            int64_t c = c0 + d;
+            double h = T[(int64_t)(g.n_x + k) * ld + c];
+            for (int t = g.jpt_ptr[k]; t < g.jpt_ptr[k + 1]; t++)
+                h = fma(g.jptv[t], T[(int64_t)g.jpt_row[t] * ld + c], h);
+            L.HW[c * L.ldhw + k] = h;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint (eq. 7) and the per-state second-order coefficients
+// ---------------------------------------------------------------------------
+
+// Single thread: the slack cost derivatives, grad P_slack, the right-hand side
+// -grad_x f = -c'_slack grad_x P_slack of the adjoint system, and F.
+__global__ void k_adjoint_rhs(PfGrid g, PfState s, AdjData a) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int r = g.ref;
+    const double S = g.base_mva;
+    double vr = s.vm[r], Pr = s.P[r];
+    double pg_ref = Pr + s.pd[r];
+    double cref = 2.0 * g.c2[r] * S * S * pg_ref + g.c1[r] * S;
+    *a.cref = cref;
+    *a.c2ref = 2.0 * g.c2[r] * S * S;
+    int n = 0;
+    for (int t = g.yp[r]; t < g.yp[r + 1]; t++) {
+        int j = g.yj[t];
+        if (j == r) {
+            double dv = Pr / vr + g.G[t] * vr;
+            a.gref_v[r] = dv;
+            a.gref_th[r] = 0.0;
+            a.gref_row[n] = a.uv[r];
+            a.gref_val[n++] = dv;
+            continue;
+        }
+        double sn, cs;
+        sincos(s.va[r] - s.va[j], &sn, &cs);
+        double vj = s.vm[j];
+        double dth = vr * vj * (g.G[t] * sn - g.B[t] * cs);
+        double dv = vr * (g.G[t] * cs + g.B[t] * sn);
+        a.gref_th[j] = dth;
+        a.gref_v[j] = dv;
+        a.gref_row[n] = a.uth[j];
+        a.gref_val[n++] = dth;
+        a.gref_row[n] = a.uv[j];
+        a.gref_val[n++] = dv;
+        a.rhs[g.qth[j]] = -cref * dth;
+        if (g.qv[j] >= 0) a.rhs[g.qv[j]] = -cref * dv;
+    }
+    double F = 0.0;
+    for (int i = 0; i < g.n_bus; i++) {
+        if (g.qv[i] >= 0) continue;  // PQ bus: no generator
+        double pg = (i == r) ? pg_ref : s.pg[i];
+        double P = S * pg;
+        F += g.c2[i] * P * P + g.c1[i] * P;
+    }
+    *a.F = F;
+}
+
+// One thread per bus: bus weights mu, nu from lambda (mu_slack = c'_slack) and
+// the coefficients of every incident branch for the gathered projection.
+// With alpha = G(mu_i + mu_j) - B(nu_i + nu_j), beta = B(mu_i - mu_j) + G(nu_i - nu_j),
+// t = theta_i - theta_j, the branch term of sum mu P + nu Q is
+// v_i v_j (alpha cos t + beta sin t); K = alpha cos t + beta sin t,
+// M = dK/dt, a = v_j M, b = v_i M, c = -v_i v_j K.
+__global__ void k_adjoint_coef(PfGrid g, PfState s, const double* lam, const double* crefp, const int* inc_ptr,
+                               const int* inc_nb, double4_32a* coef, double* d2, double* asum, double* csum,
+                               double* pg_curv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_bus) return;
+    double cref = *crefp;
+    double mu_i = g.qth[i] >= 0 ? lam[g.qth[i]] : cref;
+    double nu_i = g.qv[i] >= 0 ? lam[g.qv[i]] : 0.0;
+    double vi = s.vm[i];
+    d2[i] = 2.0 * (mu_i * g.G[g.ydiag[i]] - nu_i * g.B[g.ydiag[i]]);
+    double sa = 0.0, sc = 0.0;
+    int e = inc_ptr[i];
+    for (int t = g.yp[i]; t < g.yp[i + 1]; t++) {
+        int j = g.yj[t];
+        if (j == i) continue;
+        double mu_j = g.qth[j] >= 0 ? lam[g.qth[j]] : cref;
+        double nu_j = g.qv[j] >= 0 ? lam[g.qv[j]] : 0.0;
+        double Gij = g.G[t], Bij = g.B[t];
+        double alpha = Gij * (mu_i + mu_j) - Bij * (nu_i + nu_j);
+        double beta = Bij * (mu_i - mu_j) + Gij * (nu_i - nu_j);
+        double sn, cs;
+        sincos(s.va[i] - s.va[j], &sn, &cs);
+        double K = alpha * cs + beta * sn;
+        double M = -alpha * sn + beta * cs;
+        double vj = s.vm[j];
+        double a = vj * M, bb = vi * M, c = -vi * vj * K;
+        coef[e] = make_double4_32a(K, -a, bb, -c);
+        sa += a;
+        sc += c;
+        e++;
+    }
+    asum[i] = sa;
+    csum[i] = sc;
+    pg_curv[i] = g.ip_pg[i] >= 0 ? 2.0 * g.c2[i] * g.base_mva * g.base_mva : 0.0;
+}
+
+// grad F = grad_p f + J_p^T lambda, one thread per bus (its v and Pg entries).
+__global__ void k_gradient(PfGrid g, PfState s, const int* jpt_ptr, const int* jpt_row, const double* jptv,
+                           const double* lam, const double* crefp, const double* gref_v, double* grad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_bus) return;
+    double cref = *crefp;
+    int kv = g.ip_v[i];
+    if (kv >= 0) {
+        double h = cref * gref_v[i];
+        for (int t = jpt_ptr[kv]; t < jpt_ptr[kv + 1]; t++) h = fma(jptv[t], lam[jpt_row[t]], h);
+        grad[kv] = h;
+    }
+    int kp = g.ip_pg[i];
+    if (kp >= 0) {
+        double S = g.base_mva;
+        double h = 2.0 * g.c2[i] * S * S * s.pg[i] + g.c1[i] * S;
+        for (int t = jpt_ptr[kp]; t < jpt_ptr[kp + 1]; t++) h = fma(jptv[t], lam[jpt_row[t]], h);
+        grad[kp] = h;
+    }
+}
+
+// external column-major <-> internal row-major with a row map
+__global__ void k_scatter_rows(int n_rows, int N, const int* map, const double* src, int64_t lds, double* dst,
+                               int64_t ldd, double scale_x, int n_x) {
+    int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= (int64_t)n_rows * N) return;
+    int c = (int)(it / n_rows), r = (int)(it - (int64_t)c * n_rows);
+    double v = src[(int64_t)c * lds + r];
+    dst[(int64_t)map[r] * ldd + c] = r < n_x ? scale_x * v : v;
+}
+
+__global__ void k_gather_rows(int n_rows, int N, const int* map, const double* src, int64_t lds, double* dst,
+                              int64_t ldd, double scale_x, int n_x) {
+    int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= (int64_t)n_rows * N) return;
+    int c = (int)(it / n_rows), r = (int)(it - (int64_t)c * n_rows);
+    double v = src[(int64_t)map[r] * lds + c];
+    dst[(int64_t)c * ldd + r] = r < n_x ? scale_x * v : v;
+}
+
+int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+void launch_injections(const PfGrid& g, const PfState& s, cudaStream_t st) {
+    if (g.n_bus > 0) k_injections<<<blocks_for(g.n_bus, 128), 128, 0, st>>>(g, s);
+}
+
+void launch_pf_eval(const PfGrid& g, const PfState& s, double* gres, double* A, double* jpv,
+                    unsigned long long* gmax, unsigned long long* jmax, bool want_jac, cudaStream_t st) {
+    if (g.n_bus > 0) k_pf_eval<<<blocks_for(g.n_bus, 128), 128, 0, st>>>(g, s, gres, A, jpv, gmax, jmax, want_jac);
+}
+
+void launch_newton_update(const PfGrid& g, const PfState& s, const double* dx, cudaStream_t st) {
+    if (g.n_bus > 0) k_newton_update<<<blocks_for(g.n_bus, 128), 128, 0, st>>>(g, s, dx);
+}
+
+void launch_refactor(const int* flev_ptr_host, int n_flev, const int* flev_bus, const int* q0, const uint8_t* nv,
+                     const int* rowptr, const int* col, const int* diagpos, const int64_t* lrank_ptr,
+                     const int64_t* upd_ptr, const int* upd_pos, double* A, double* invdiag,
+                     const unsigned long long* jmax, int* err, cudaStream_t st) {
+    for (int lev = 0; lev < n_flev; lev++) {
+        int b0 = flev_ptr_host[lev], nb = flev_ptr_host[lev + 1] - b0;
+        if (nb <= 0) continue;
+        int threads = 128;
+        int blocks = blocks_for((int64_t)nb * 32, threads);
+        k_refactor_level<<<blocks, threads, 0, st>>>(b0, nb, flev_bus, q0, nv, rowptr, col, diagpos, lrank_ptr,
+                                                      upd_ptr, upd_pos, A, invdiag, jmax, err);
+    }
+}
+
+void launch_transpose_values(int nnz, const int* tpos, const double* A, double* At, int nnz_jp,
+                             const int* jpt_src, const double* jpv, double* jptv, cudaStream_t st) {
+    int n = nnz > nnz_jp ? nnz : nnz_jp;
+    if (n > 0) k_transpose_values<<<blocks_for(n, 256), 256, 0, st>>>(nnz, tpos, A, At, nnz_jp, jpt_src, jpv, jptv);
+}
+
+int dirs_default_ctas(int N) {
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 1;
+    }
+    int G = N < 2 * n_sm ? N : 2 * n_sm;
+    int need = (N + kDMax - 1) / kDMax;
+    if (G < need) G = need;
+    return G < 1 ? 1 : G;
+}
+
+void launch_dirs(const DirGrid& g, const DirLaunch& L, cudaStream_t st) {
+    if (L.N <= 0 || L.n_cta <= 0) return;
+    k_dirs<<<L.n_cta, kDirThreads, 0, st>>>(g, L);
+}
+
+void launch_adjoint_rhs(const PfGrid& g, const PfState& s, const AdjData& a, cudaStream_t st) {
+    k_adjoint_rhs<<<1, 32, 0, st>>>(g, s, a);
+}
+
+void launch_adjoint_coef(const PfGrid& g, const PfState& s, const double* lambda_int, const double* cref,
+                         const int* inc_ptr, const int* inc_nb, double4_32a* inc_coef, double* d2, double* asum,
+                         double* csum, double* pg_curv, cudaStream_t st) {
+    if (g.n_bus > 0)
+        k_adjoint_coef<<<blocks_for(g.n_bus, 128), 128, 0, st>>>(g, s, lambda_int, cref, inc_ptr, inc_nb, inc_coef,
+                                                                 d2, asum, csum, pg_curv);
+}
+
+void launch_gradient(const PfGrid& g, const PfState& s, int n_p, const int* jpt_ptr, const int* jpt_row,
+                     const double* jptv, const double* lambda_int, const double* cref, const double* gref_v,
+                     double* grad, cudaStream_t st) {
+    (void)n_p;
+    if (g.n_bus > 0)
+        k_gradient<<<blocks_for(g.n_bus, 128), 128, 0, st>>>(g, s, jpt_ptr, jpt_row, jptv, lambda_int, cref, gref_v,
+                                                             grad);
+}
+
+void launch_scatter_rows(int n_rows, int N, const int* map, const double* src, int64_t lds, double* dst,
+                         int64_t ldd, double scale_x, int n_x, cudaStream_t st) {
+    int64_t n = (int64_t)n_rows * N;
+    if (n > 0) k_scatter_rows<<<blocks_for(n, 256), 256, 0, st>>>(n_rows, N, map, src, lds, dst, ldd, scale_x, n_x);
+}
+
+void launch_gather_rows(int n_rows, int N, const int* map, const double* src, int64_t lds, double* dst,
+                        int64_t ldd, double scale_x, int n_x, cudaStream_t st) {
+    int64_t n = (int64_t)n_rows * N;
+    if (n > 0) k_gather_rows<<<blocks_for(n, 256), 256, 0, st>>>(n_rows, N, map, src, lds, dst, ldd, scale_x, n_x);
+}
+
+}  // namespace rh

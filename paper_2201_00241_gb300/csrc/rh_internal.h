@@ -1,0 +1,79 @@
+// rh_internal.h -- data shared by the host symbolic phase, the entry points
+// and the kernels of librh.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace rh {
+
+enum BusType : int8_t { kRef = 0, kPV = 1, kPQ = 2 };
+
+// Result of the host symbolic phase (once per topology).
+//
+// Internal variable order: buses in elimination order, each contributing theta
+// then (PQ only) v.  "Position" k of a bus is its place in that order; the
+// slack bus has no position (no x variable).
+//
+// The filled matrix A = L + U of the permuted J_x is stored row-wise (CSR),
+// columns ascending: [strictly lower L | diagonal | strictly upper U].  The two
+// rows of a PQ bus share the same columns outside the bus (bus-level fill), so
+// a kernel can walk both rows with one column list.
+struct Symbolic {
+    int n_bus = 0, n_branch = 0, n_gen = 0, n_pv = 0, n_pq = 0, ref = -1;
+    int n_x = 0, n_p = 0, n_elim = 0;
+
+    // external index maps (documented in rh.h): -1 where absent
+    std::vector<int> ix_th, ix_v, ip_v, ip_pg;
+    // internal maps
+    std::vector<int> ebus;          // position -> bus id
+    std::vector<int> epos;          // bus id -> position (-1 for the slack)
+    std::vector<int> q0;            // position -> first internal variable
+    std::vector<uint8_t> nv;        // position -> 1 (PV) or 2 (PQ)
+    std::vector<int> qth, qv;       // bus id -> internal variable of theta / v (-1)
+    std::vector<int> perm;          // internal variable -> x index
+
+    // bus-level patterns and schedules
+    std::vector<std::vector<int>> colpat;   // position -> later positions (U side)
+    std::vector<std::vector<int>> rowpat;   // position -> earlier positions (L side)
+    std::vector<int> flevel, blevel;        // forward / backward level per position
+    int n_flev = 0, n_blev = 0;
+    std::vector<int> flev_ptr, flev_bus;    // positions grouped by forward level
+    std::vector<int> blev_ptr, blev_bus;    // positions grouped by backward level
+    std::vector<int> flev_maxext, blev_maxext;  // longest external row part per level
+
+    // variable-level CSR of A
+    std::vector<int> rowptr, col, diagpos;
+    std::vector<int> tpos;                  // position of the transposed entry
+    int64_t nnz_l = 0, nnz_u = 0;
+
+    // refactorisation schedule: for every strictly-lower entry s of A (row i,
+    // column k) the positions in row i updated by the strictly-upper part of
+    // row k, in order: upd_ptr[s] .. upd_ptr[s+1]  (indexed by L-entry rank)
+    std::vector<int64_t> lrank_ptr;         // row -> first L-entry rank
+    std::vector<int64_t> upd_ptr;           // L-entry rank -> first update
+    std::vector<int> upd_pos;
+
+    // admittance matrix (CSR by bus, diagonal included, parallel branches merged)
+    std::vector<int> yp, yj;
+    std::vector<double> G, B;
+    std::vector<int> ydiag;
+
+    // J_x / J_p assembly: for every admittance entry s (bus i, neighbour-or-self j)
+    // the destination of dP_i/dtheta_j, dP_i/dv_j, dQ_i/dtheta_j, dQ_i/dv_j:
+    //   >= 0 : slot in A;  <= -2 : slot -(code + 2) in Jp values;  -1 : none
+    std::vector<int> jac_dst;               // 4 per admittance entry
+    // J_p in CSR by internal row (columns = p index), and its transpose
+    std::vector<int> jp_ptr, jp_col;
+    std::vector<int> jpt_ptr, jpt_row, jpt_src;
+    std::vector<int> pg_slot;               // bus id -> Jp slot of its Pg column (-1)
+    int64_t nnz_jx = 0;
+};
+
+// Builds everything above.  Returns an empty string on success, else a message.
+std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int32_t* to,
+                           const double* r, const double* x, const double* b,
+                           const int8_t* type, Symbolic& S);
+
+}  // namespace rh

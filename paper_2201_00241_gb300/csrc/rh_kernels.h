@@ -1,0 +1,127 @@
+// rh_kernels.h -- device data layout and kernel launchers of librh.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace rh {
+
+// Phases of the direction kernel (one bit each, executed in this order).
+enum : unsigned {
+    PH_WLOAD = 1u << 0,    // W (or identity columns) -> rows n_x.. of V; zero row
+    PH_SPMUL = 1u << 1,    // V[x rows] = -J_p W                          (Alg. 2 SpMul)
+    PH_L = 1u << 2,        // V <- L^{-1} V                                (BatchSparseSolve 1)
+    PH_U = 1u << 3,        // V <- U^{-1} V
+    PH_TPROJ = 1u << 4,    // T[x rows] = -y_x, T[p rows] = y_p            (BatchTensorProjection)
+    PH_UT = 1u << 5,       // T <- U^{-T} T                                (BatchSparseSolve 2)
+    PH_LT = 1u << 6,       // T <- L^{-T} T
+    PH_MULADD = 1u << 7,   // HW = y_p + J_p^T psi                         (SpMulAdd)
+};
+
+// Read-only grid data used by the direction kernel, all device pointers.
+struct DirGrid {
+    int n_x, n_p;
+    int zero_row;                              // n_x + n_p: a row of zeros in V
+    // filled matrix A = L + U (CSR), its transposed values and 1/diagonal
+    const int *rowptr, *col, *diagpos;
+    const double *A, *At, *invdiag;
+    const int *q0;
+    const uint8_t *nv;
+    int n_flev, n_blev;
+    const int *flev_ptr, *flev_bus, *flev_maxext;
+    const int *blev_ptr, *blev_bus, *blev_maxext;
+    // J_p by internal rows and by p index
+    const int *jp_ptr, *jp_col;
+    const double *jpv;
+    const int *jpt_ptr, *jpt_row;
+    const double *jptv;
+    // projection data (per bus, original ids); rows are V/Y row indices
+    int n_bus;
+    const int *tp_bus;                         // bus processing order (internal order, slack last)
+    const int *uth, *uv;                       // rows of theta_b (zero row at the slack) and v_b
+    const int *inc_ptr, *inc_uth, *inc_uv;     // incident branches: rows of the other end
+    const double4_32a *inc_coef;                   // (K, -a, b, -c) per incidence (state dependent)
+    const double *d2, *asum, *csum;            // per-bus coefficients (state dependent)
+    const uint8_t *has_gref;
+    const double *gref_th, *gref_v;            // grad P_slack at the rows of bus b
+    int n_gref;
+    const int *gref_row;
+    const double *gref_val;
+    const double *c2ref;                       // device scalar c''_slack
+    const int *pg_row;                         // per bus: row of Pg (or -1)
+    const double *pg_curv;                     // per bus: c''_k
+};
+
+struct DirLaunch {
+    int N;                     // directions in this launch
+    int n_cta;                 // CTAs; CTA c owns directions [c*N/n_cta, (c+1)*N/n_cta)
+    int64_t ld;                // row stride of V and T (>= N)
+    double *V, *T;             // tangent buffer; buffer of the transposed sweeps / projection
+    const double *W;           // n_p x N column-major (ldw), or NULL for identity columns
+    int64_t ldw;
+    int col0;                  // identity columns start at col0
+    double *HW;                // n_p x N column-major (ldhw)
+    int64_t ldhw;
+    unsigned phases;
+};
+
+// Grid-wide power-flow evaluation data (per bus, original ids).
+struct PfGrid {
+    int n_bus, n_x, ref;
+    const int *yp, *yj, *ydiag;
+    const double *G, *B;
+    const int *qth, *qv, *ip_v, *ip_pg;
+    const int *jac_dst;
+    const int *pg_slot;
+    double base_mva;
+    const double *c2, *c1;
+};
+
+struct PfState {
+    double *vm, *va, *pg, *pd, *qd;  // per bus
+    double *P, *Q;                   // injections (output)
+};
+
+// ---- launchers (all asynchronous on `st`) ----------------------------------
+void launch_injections(const PfGrid& g, const PfState& s, cudaStream_t st);
+// residual (internal order) and/or Jacobian values; gmax / jmax receive
+// max |g| and max |J_x| as ordered bit patterns (zeroed by the caller).
+void launch_pf_eval(const PfGrid& g, const PfState& s, double* gres, double* A, double* jpv,
+                    unsigned long long* gmax, unsigned long long* jmax, bool want_jac, cudaStream_t st);
+void launch_newton_update(const PfGrid& g, const PfState& s, const double* dx, cudaStream_t st);
+void launch_refactor(const int* flev_ptr_host, int n_flev, const int* flev_bus, const int* q0, const uint8_t* nv,
+                     const int* rowptr, const int* col, const int* diagpos, const int64_t* lrank_ptr,
+                     const int64_t* upd_ptr, const int* upd_pos, double* A, double* invdiag,
+                     const unsigned long long* jmax, int* err, cudaStream_t st);
+void launch_transpose_values(int nnz, const int* tpos, const double* A, double* At, int nnz_jp,
+                             const int* jpt_src, const double* jpv, double* jptv, cudaStream_t st);
+void launch_dirs(const DirGrid& g, const DirLaunch& L, cudaStream_t st);
+int dirs_default_ctas(int N);
+
+// adjoint helpers
+struct AdjData {
+    double *rhs;          // n_x, internal order (output: -grad_x f)
+    double *cref, *c2ref; // device scalars c'_slack, c''_slack
+    double *F;            // device scalar
+    double *gref_th, *gref_v;   // per bus
+    int *gref_row;        // up to n_gref_max entries
+    double *gref_val;
+    int n_gref;           // number of entries (static: slack + its neighbours)
+    const int *uth, *uv;  // combined rows per bus
+};
+void launch_adjoint_rhs(const PfGrid& g, const PfState& s, const AdjData& a, cudaStream_t st);
+void launch_adjoint_coef(const PfGrid& g, const PfState& s, const double* lambda_int, const double* cref,
+                         const int* inc_ptr, const int* inc_nb, double4_32a* inc_coef, double* d2, double* asum,
+                         double* csum, double* pg_curv, cudaStream_t st);
+void launch_gradient(const PfGrid& g, const PfState& s, int n_p, const int* jpt_ptr, const int* jpt_row,
+                     const double* jptv, const double* lambda_int, const double* cref, const double* gref_v,
+                     double* grad, cudaStream_t st);
+
+// permutation helpers between external (x, p) order and the internal rows
+void launch_gather_rows(int n_rows, int N, const int* map, const double* src, int64_t lds, double* dst,
+                        int64_t ldd, double scale_x, int n_x, cudaStream_t st);
+void launch_scatter_rows(int n_rows, int N, const int* map, const double* src, int64_t lds, double* dst,
+                         int64_t ldd, double scale_x, int n_x, cudaStream_t st);
+
+}  // namespace rh

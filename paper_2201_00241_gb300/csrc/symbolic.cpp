@@ -1,0 +1,326 @@
+// symbolic.cpp -- host symbolic phase of librh (once per topology).
+//
+// The paper factors J_x once on the host and hands the fixed pattern to a
+// device refactorisation (section 5.2).  Here the host does only the symbolic
+// work: admittance pattern, a static fill-reducing order, the pattern of
+// L + U, the bus-level schedules and the index maps used by the kernels.
+// Numerical work (Jacobian values, LU values, solves) runs on the device.
+#include <algorithm>
+#include <cmath>
+#include <functional>
+#include <queue>
+#include <tuple>
+#include <utility>
+
+#include "rh_internal.h"
+
+namespace rh {
+namespace {
+
+// Exact minimum degree on the bus graph: repeatedly eliminate the remaining
+// bus of smallest degree in the current elimination graph (ties: smallest bus
+// id); the neighbours of an eliminated bus become a clique.  Adjacency lists
+// are kept sorted; a min-heap with lazy invalidation finds the next bus.
+// colpat_bus[k] receives the neighbour set (bus ids) of the k-th eliminated bus.
+void minimum_degree(int n_bus, const std::vector<std::vector<int>>& adj0, const std::vector<char>& active,
+                    std::vector<int>& order, std::vector<std::vector<int>>& colpat_bus) {
+    std::vector<std::vector<int>> adj = adj0;
+    std::vector<char> alive = active;
+    using Key = std::pair<int, int>;  // (degree, bus id)
+    std::priority_queue<Key, std::vector<Key>, std::greater<Key>> heap;
+    for (int i = 0; i < n_bus; i++)
+        if (alive[i]) heap.push({(int)adj[i].size(), i});
+    std::vector<int> merged;
+    while (!heap.empty()) {
+        auto [d, e] = heap.top();
+        heap.pop();
+        if (!alive[e] || d != (int)adj[e].size()) continue;  // stale entry
+        alive[e] = 0;
+        std::vector<int> nb = std::move(adj[e]);
+        adj[e].clear();
+        for (int a : nb) {
+            // adj[a] <- (adj[a] U nb) \ {a, e}
+            merged.clear();
+            std::set_union(adj[a].begin(), adj[a].end(), nb.begin(), nb.end(), std::back_inserter(merged));
+            adj[a].clear();
+            for (int v : merged)
+                if (v != a && v != e) adj[a].push_back(v);
+            heap.push({(int)adj[a].size(), a});
+        }
+        order.push_back(e);
+        colpat_bus.push_back(std::move(nb));
+    }
+}
+
+int find_in_row(const std::vector<int>& rowptr, const std::vector<int>& col, int row, int c) {
+    auto b = col.begin() + rowptr[row], e = col.begin() + rowptr[row + 1];
+    auto it = std::lower_bound(b, e, c);
+    if (it == e || *it != c) return -1;
+    return (int)(it - col.begin());
+}
+
+}  // namespace
+
+std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int32_t* to,
+                           const double* r, const double* x, const double* b,
+                           const int8_t* type, Symbolic& S) {
+    if (n_bus < 1 || n_branch < 0) return "n_bus must be >= 1 and n_branch >= 0";
+    S.n_bus = n_bus;
+    S.n_branch = n_branch;
+    int n_ref = 0;
+    for (int i = 0; i < n_bus; i++) {
+        if (type[i] != kRef && type[i] != kPV && type[i] != kPQ) return "bus_type must be 0, 1 or 2";
+        if (type[i] == kRef) { n_ref++; S.ref = i; }
+        if (type[i] == kPV) S.n_pv++;
+        if (type[i] == kPQ) S.n_pq++;
+    }
+    if (n_ref != 1) return "the grid needs exactly one slack bus (bus_type 0)";
+    S.n_gen = 1 + S.n_pv;
+    S.n_x = S.n_pv + 2 * S.n_pq;
+    S.n_p = 2 * S.n_gen - 1;
+
+    // ---- admittance matrix (pi model) -------------------------------------
+    std::vector<std::vector<std::tuple<int, double, double>>> yrow(n_bus);
+    std::vector<double> gd(n_bus, 0.0), bd(n_bus, 0.0);
+    for (int e = 0; e < n_branch; e++) {
+        int i = fr[e], j = to[e];
+        if (i < 0 || j < 0 || i >= n_bus || j >= n_bus || i == j) return "branch with a bad or repeated end bus";
+        double den = r[e] * r[e] + x[e] * x[e];
+        if (!(den > 0.0) || !std::isfinite(den)) return "branch with zero or non-finite impedance";
+        double gs = r[e] / den, bs = -x[e] / den;
+        gd[i] += gs; bd[i] += bs + 0.5 * b[e];
+        gd[j] += gs; bd[j] += bs + 0.5 * b[e];
+        yrow[i].emplace_back(j, -gs, -bs);
+        yrow[j].emplace_back(i, -gs, -bs);
+    }
+    S.yp.assign(n_bus + 1, 0);
+    S.ydiag.assign(n_bus, -1);
+    for (int i = 0; i < n_bus; i++) {
+        auto& rw = yrow[i];
+        rw.emplace_back(i, gd[i], bd[i]);
+        std::sort(rw.begin(), rw.end(), [](auto& a, auto& c) { return std::get<0>(a) < std::get<0>(c); });
+        for (size_t k = 0; k < rw.size(); k++) {
+            int j = std::get<0>(rw[k]);
+            if (!S.yj.empty() && (int)S.yj.size() > S.yp[i] && S.yj.back() == j) {
+                S.G.back() += std::get<1>(rw[k]);
+                S.B.back() += std::get<2>(rw[k]);
+            } else {
+                if (j == i) S.ydiag[i] = (int)S.yj.size();
+                S.yj.push_back(j);
+                S.G.push_back(std::get<1>(rw[k]));
+                S.B.push_back(std::get<2>(rw[k]));
+            }
+        }
+        S.yp[i + 1] = (int)S.yj.size();
+    }
+
+    // ---- external index maps ------------------------------------------------
+    S.ix_th.assign(n_bus, -1); S.ix_v.assign(n_bus, -1); S.ip_v.assign(n_bus, -1); S.ip_pg.assign(n_bus, -1);
+    {
+        int kpv = 0, kpq = 0, kg = 0;
+        for (int i = 0; i < n_bus; i++) {
+            if (type[i] == kPV) { S.ix_th[i] = kpv; S.ip_pg[i] = S.n_gen + kpv; kpv++; }
+            if (type[i] == kPQ) { S.ix_th[i] = S.n_pv + kpq; S.ix_v[i] = S.n_pv + S.n_pq + kpq; kpq++; }
+            if (type[i] != kPQ) S.ip_v[i] = kg++;
+        }
+    }
+
+    // ---- ordering -------------------------------------------------------------
+    std::vector<std::vector<int>> adj(n_bus);
+    std::vector<char> active(n_bus, 0);
+    for (int i = 0; i < n_bus; i++) active[i] = type[i] != kRef;
+    for (int i = 0; i < n_bus; i++) {
+        if (!active[i]) continue;
+        for (int s = S.yp[i]; s < S.yp[i + 1]; s++) {
+            int j = S.yj[s];
+            if (j != i && active[j]) adj[i].push_back(j);   // yj is sorted and unique
+        }
+    }
+    std::vector<std::vector<int>> colpat_bus;
+    minimum_degree(n_bus, adj, active, S.ebus, colpat_bus);
+    S.n_elim = (int)S.ebus.size();
+    S.epos.assign(n_bus, -1);
+    for (int k = 0; k < S.n_elim; k++) S.epos[S.ebus[k]] = k;
+    S.q0.assign(S.n_elim, 0);
+    S.nv.assign(S.n_elim, 1);
+    S.qth.assign(n_bus, -1);
+    S.qv.assign(n_bus, -1);
+    S.perm.assign(S.n_x, -1);
+    {
+        int q = 0;
+        for (int k = 0; k < S.n_elim; k++) {
+            int bus = S.ebus[k];
+            S.q0[k] = q;
+            S.qth[bus] = q;
+            S.perm[q++] = S.ix_th[bus];
+            if (type[bus] == kPQ) {
+                S.nv[k] = 2;
+                S.qv[bus] = q;
+                S.perm[q++] = S.ix_v[bus];
+            }
+        }
+    }
+
+    // ---- bus-level patterns and levels ----------------------------------------
+    S.colpat.assign(S.n_elim, {});
+    S.rowpat.assign(S.n_elim, {});
+    for (int k = 0; k < S.n_elim; k++) {
+        for (int bus : colpat_bus[k]) S.colpat[k].push_back(S.epos[bus]);
+        std::sort(S.colpat[k].begin(), S.colpat[k].end());
+        for (int c : S.colpat[k]) S.rowpat[c].push_back(k);        // k ascending -> sorted
+    }
+    S.flevel.assign(S.n_elim, 0);
+    S.blevel.assign(S.n_elim, 0);
+    for (int k = 0; k < S.n_elim; k++)
+        for (int c : S.rowpat[k]) S.flevel[k] = std::max(S.flevel[k], S.flevel[c] + 1);
+    for (int k = S.n_elim - 1; k >= 0; k--)
+        for (int c : S.colpat[k]) S.blevel[k] = std::max(S.blevel[k], S.blevel[c] + 1);
+    auto ext_len = [&](const std::vector<int>& pat) {
+        int n = 0;
+        for (int c : pat) n += S.nv[c];
+        return n;
+    };
+    auto group = [&](const std::vector<int>& lev, const std::vector<std::vector<int>>& pat, int& nlev,
+                     std::vector<int>& ptr, std::vector<int>& bus, std::vector<int>& maxext) {
+        nlev = 0;
+        for (int k = 0; k < S.n_elim; k++) nlev = std::max(nlev, lev[k] + 1);
+        ptr.assign(nlev + 1, 0);
+        maxext.assign(nlev, 0);
+        for (int k = 0; k < S.n_elim; k++) ptr[lev[k] + 1]++;
+        for (int l = 0; l < nlev; l++) ptr[l + 1] += ptr[l];
+        bus.assign(S.n_elim, 0);
+        std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+        for (int k = 0; k < S.n_elim; k++) bus[fill[lev[k]]++] = k;
+        // within a level: PQ buses first, then longer rows first (balance, less divergence)
+        for (int l = 0; l < nlev; l++) {
+            std::stable_sort(bus.begin() + ptr[l], bus.begin() + ptr[l + 1], [&](int a, int c) {
+                int la = ext_len(pat[a]), lc = ext_len(pat[c]);
+                if (S.nv[a] != S.nv[c]) return S.nv[a] > S.nv[c];
+                return la > lc;
+            });
+            for (int t = ptr[l]; t < ptr[l + 1]; t++) maxext[l] = std::max(maxext[l], ext_len(pat[bus[t]]));
+        }
+    };
+    group(S.flevel, S.rowpat, S.n_flev, S.flev_ptr, S.flev_bus, S.flev_maxext);
+    group(S.blevel, S.colpat, S.n_blev, S.blev_ptr, S.blev_bus, S.blev_maxext);
+
+    // ---- variable-level CSR of A = L + U -------------------------------------
+    S.rowptr.assign(S.n_x + 1, 0);
+    S.diagpos.assign(S.n_x, 0);
+    for (int k = 0; k < S.n_elim; k++) {
+        for (int t = 0; t < S.nv[k]; t++) {
+            int q = S.q0[k] + t;
+            S.rowptr[q] = (int)S.col.size();
+            for (int c : S.rowpat[k])
+                for (int u = 0; u < S.nv[c]; u++) S.col.push_back(S.q0[c] + u);
+            if (t == 1) S.col.push_back(S.q0[k]);                 // (v, theta) of the bus
+            S.diagpos[q] = (int)S.col.size();
+            S.col.push_back(q);
+            if (t == 0 && S.nv[k] == 2) S.col.push_back(q + 1);   // (theta, v) of the bus
+            for (int c : S.colpat[k])
+                for (int u = 0; u < S.nv[c]; u++) S.col.push_back(S.q0[c] + u);
+        }
+    }
+    S.rowptr[S.n_x] = (int)S.col.size();
+    S.nnz_l = 0;
+    for (int q = 0; q < S.n_x; q++) S.nnz_l += S.diagpos[q] - S.rowptr[q];
+    S.nnz_u = (int64_t)S.col.size() - S.nnz_l;
+    S.tpos.assign(S.col.size(), -1);
+    for (int q = 0; q < S.n_x; q++)
+        for (int s = S.rowptr[q]; s < S.rowptr[q + 1]; s++) {
+            int t = find_in_row(S.rowptr, S.col, S.col[s], q);
+            if (t < 0) return "internal error: pattern of L + U is not symmetric";
+            S.tpos[s] = t;
+        }
+
+    // ---- refactorisation update map (row-wise elimination, IKJ order) ------
+    S.lrank_ptr.assign(S.n_x + 1, 0);
+    for (int q = 0; q < S.n_x; q++) S.lrank_ptr[q + 1] = S.lrank_ptr[q] + (S.diagpos[q] - S.rowptr[q]);
+    S.upd_ptr.assign(S.nnz_l + 1, 0);
+    for (int i = 0; i < S.n_x; i++) {
+        for (int s = S.rowptr[i]; s < S.diagpos[i]; s++) {
+            int k = S.col[s];
+            int64_t rank = S.lrank_ptr[i] + (s - S.rowptr[i]);
+            int p = s + 1;
+            for (int t = S.diagpos[k] + 1; t < S.rowptr[k + 1]; t++) {
+                int j = S.col[t];
+                while (p < S.rowptr[i + 1] && S.col[p] < j) p++;
+                if (p >= S.rowptr[i + 1] || S.col[p] != j) return "internal error: fill pattern not closed";
+                S.upd_pos.push_back(p);
+            }
+            S.upd_ptr[rank + 1] = (int64_t)S.upd_pos.size();
+        }
+    }
+
+    // ---- J_p pattern and the assembly destinations -------------------------
+    std::vector<std::vector<int>> jprow(S.n_x);
+    for (int i = 0; i < n_bus; i++) {
+        int rows[2] = {S.qth[i], S.qv[i]};
+        for (int s = S.yp[i]; s < S.yp[i + 1]; s++) {
+            int j = S.yj[s];
+            if (S.qv[j] >= 0) continue;                       // v_j in x
+            for (int rr : rows)
+                if (rr >= 0) jprow[rr].push_back(S.ip_v[j]);
+        }
+        if (S.ip_pg[i] >= 0) jprow[S.qth[i]].push_back(S.ip_pg[i]);
+    }
+    S.jp_ptr.assign(S.n_x + 1, 0);
+    for (int q = 0; q < S.n_x; q++) {
+        std::sort(jprow[q].begin(), jprow[q].end());
+        jprow[q].erase(std::unique(jprow[q].begin(), jprow[q].end()), jprow[q].end());
+        for (int c : jprow[q]) S.jp_col.push_back(c);
+        S.jp_ptr[q + 1] = (int)S.jp_col.size();
+    }
+    auto jp_slot = [&](int row, int pc) { return find_in_row(S.jp_ptr, S.jp_col, row, pc); };
+    S.jac_dst.assign(4 * S.yj.size(), -1);
+    S.nnz_jx = 0;
+    for (int i = 0; i < n_bus; i++) {
+        int rP = S.qth[i], rQ = S.qv[i];
+        for (int s = S.yp[i]; s < S.yp[i + 1]; s++) {
+            int j = S.yj[s];
+            int cth = S.qth[j];
+            int rows[2] = {rP, rQ};
+            for (int a = 0; a < 2; a++) {
+                int rr = rows[a];
+                if (rr < 0) continue;
+                if (cth >= 0) {
+                    int t = find_in_row(S.rowptr, S.col, rr, cth);
+                    if (t < 0) return "internal error: J_x entry outside the LU pattern";
+                    S.jac_dst[4 * s + 2 * a + 0] = t;
+                    S.nnz_jx++;
+                }
+                if (S.qv[j] >= 0) {
+                    int t = find_in_row(S.rowptr, S.col, rr, S.qv[j]);
+                    if (t < 0) return "internal error: J_x entry outside the LU pattern";
+                    S.jac_dst[4 * s + 2 * a + 1] = t;
+                    S.nnz_jx++;
+                } else {
+                    int t = jp_slot(rr, S.ip_v[j]);
+                    if (t < 0) return "internal error: J_p entry missing";
+                    S.jac_dst[4 * s + 2 * a + 1] = -(t + 2);
+                }
+            }
+        }
+    }
+    S.pg_slot.assign(n_bus, -1);
+    for (int i = 0; i < n_bus; i++)
+        if (S.ip_pg[i] >= 0) S.pg_slot[i] = jp_slot(S.qth[i], S.ip_pg[i]);
+    // transpose of J_p: rows = p index
+    S.jpt_ptr.assign(S.n_p + 1, 0);
+    for (int c : S.jp_col) S.jpt_ptr[c + 1]++;
+    for (int k = 0; k < S.n_p; k++) S.jpt_ptr[k + 1] += S.jpt_ptr[k];
+    S.jpt_row.assign(S.jp_col.size(), 0);
+    S.jpt_src.assign(S.jp_col.size(), 0);
+    {
+        std::vector<int> fill(S.jpt_ptr.begin(), S.jpt_ptr.end() - 1);
+        for (int q = 0; q < S.n_x; q++)
+            for (int s = S.jp_ptr[q]; s < S.jp_ptr[q + 1]; s++) {
+                int d = fill[S.jp_col[s]]++;
+                S.jpt_row[d] = q;
+                S.jpt_src[d] = s;
+            }
+    }
+    return "";
+}
+
+}  // namespace rh

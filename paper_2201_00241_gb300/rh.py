@@ -1,0 +1,288 @@
+"""Thin ctypes binding of librh (include/rh.h): argument marshalling only.
+
+Every numerical step runs in the CUDA kernels of the library.  Arrays may be
+numpy arrays (host pointers) or CUDA torch tensors (device pointers, used on
+torch's current stream).  There is no CPU fallback: without the built library
+or a CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+RH_OK, RH_EINVAL, RH_ENOMEM, RH_ESINGULAR, RH_ENOCONV, RH_ETIMEOUT, RH_ECUDA, RH_ESTATE = range(8)
+RH_HOST_PTRS, RH_DEVICE_PTRS, RH_HESSIAN_CONCURRENT = 0, 1, 2
+_NAMES = ["RH_OK", "RH_EINVAL", "RH_ENOMEM", "RH_ESINGULAR", "RH_ENOCONV", "RH_ETIMEOUT", "RH_ECUDA", "RH_ESTATE"]
+
+# every symbol declared in include/rh.h
+EXPORTS = ["rh_grid_create", "rh_grid_destroy", "rh_grid_dims", "rh_grid_symbolic", "rh_injections",
+           "rh_set_state", "rh_powerflow", "rh_adjoint", "rh_hessvec", "rh_hessian", "rh_solve", "rh_refactor",
+           "rh_lagrangian_hessvec", "rh_last_error"]
+
+
+class RHError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_NAMES[status] if 0 <= status < len(_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class _Desc(C.Structure):
+    _fields_ = [("n_bus", C.c_int32), ("n_branch", C.c_int32), ("from_", C.c_void_p), ("to", C.c_void_p),
+                ("r", C.c_void_p), ("x", C.c_void_p), ("b", C.c_void_p), ("bus_type", C.c_void_p),
+                ("c2", C.c_void_p), ("c1", C.c_void_p), ("base_mva", C.c_double)]
+
+
+class Dims(C.Structure):
+    _fields_ = [("n_bus", C.c_int32), ("n_branch", C.c_int32), ("n_gen", C.c_int32), ("n_pv", C.c_int32),
+                ("n_pq", C.c_int32), ("n_x", C.c_int32), ("n_p", C.c_int32), ("n_levels_fwd", C.c_int32),
+                ("n_levels_bwd", C.c_int32), ("nnz_jx", C.c_int64), ("nnz_jp", C.c_int64), ("nnz_l", C.c_int64),
+                ("nnz_u", C.c_int64), ("refactor_updates", C.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load librh.so; builds it first when it is missing and nvcc is available."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"librh is not built ({path}); run __graft_entry__.build()")
+        _build.build()
+    lib = C.CDLL(path)
+    P, I32, I64, D, U32 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_uint32
+    sig = {
+        "rh_grid_create": ([P, I32, P], C.c_int),
+        "rh_grid_destroy": ([P], None),
+        "rh_grid_dims": ([P, P], C.c_int),
+        "rh_grid_symbolic": ([P] + [P] * 7, C.c_int),
+        "rh_injections": ([P, P, P, P, P], C.c_int),
+        "rh_set_state": ([P, P, P, P], C.c_int),
+        "rh_powerflow": ([P, P, D, I32, P, P, P], C.c_int),
+        "rh_adjoint": ([P, P, P, P], C.c_int),
+        "rh_hessvec": ([P, P, I64, I32, P, I64, P, U32], C.c_int),
+        "rh_hessian": ([P, I32, P, I64, P, U32], C.c_int),
+        "rh_solve": ([P, P, I64, I32, I32, P, U32], C.c_int),
+        "rh_refactor": ([P, P], C.c_int),
+        "rh_lagrangian_hessvec": ([P, P, I64, I32, P, I64, P, U32], C.c_int),
+        "rh_last_error": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != RH_OK:
+        raise RHError(st, _lib.rh_last_error().decode())
+
+
+def _ptr(a) -> C.c_void_p:
+    if a is None:
+        return C.c_void_p(0)
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(a.data_ptr())  # torch tensor
+
+
+def _is_device(a) -> bool:
+    return a is not None and not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False)
+
+
+def _stream_of(a):
+    if _is_device(a):
+        import torch
+        return C.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
+    return C.c_void_p(0)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+@dataclass
+class Planted:
+    x: np.ndarray
+    p: np.ndarray
+    pd: np.ndarray
+    qd: np.ndarray
+
+
+class Grid:
+    """One grid loaded on one GPU (rh_grid_create)."""
+
+    def __init__(self, grid, device: int = 0):
+        lib = load()
+        self.src = grid
+        self._keep = [np.ascontiguousarray(grid.fr, dtype=np.int32), np.ascontiguousarray(grid.to, dtype=np.int32),
+                      _f64(grid.r), _f64(grid.x), _f64(grid.b), np.ascontiguousarray(grid.bus_type, dtype=np.int8),
+                      _f64(grid.c2), _f64(grid.c1)]
+        k = self._keep
+        d = _Desc(int(grid.n_bus), int(grid.n_branch), *[_ptr(a) for a in k], float(grid.base_mva))
+        h = C.c_void_p(0)
+        _check(lib.rh_grid_create(C.byref(d), int(device), C.byref(h)))
+        self._h = h
+        self.device = device
+        dm = Dims()
+        _check(lib.rh_grid_dims(self._h, C.byref(dm)))
+        self.dims = dm
+        self.n_bus, self.n_x, self.n_p = dm.n_bus, dm.n_x, dm.n_p
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.rh_grid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    # ---- symbolic ------------------------------------------------------------
+    def symbolic(self) -> dict:
+        dm, nx = self.dims, self.n_x
+        out = dict(perm=np.empty(nx, np.int32), bus_order=np.empty(self.n_bus - 1, np.int32),
+                   level=np.empty(self.n_bus - 1, np.int32), Lp=np.empty(nx + 1, np.int32),
+                   Lj=np.empty(dm.nnz_l, np.int32), Up=np.empty(nx + 1, np.int32), Uj=np.empty(dm.nnz_u, np.int32))
+        _check(_lib.rh_grid_symbolic(self._h, *[_ptr(out[k]) for k in ("perm", "bus_order", "level", "Lp", "Lj",
+                                                                       "Up", "Uj")]))
+        return out
+
+    # ---- model ---------------------------------------------------------------
+    def injections(self, vm, va):
+        vm, va = _f64(vm), _f64(va)
+        P = np.empty(self.n_bus)
+        Q = np.empty(self.n_bus)
+        _check(_lib.rh_injections(self._h, _ptr(vm), _ptr(va), _ptr(P), _ptr(Q)))
+        return P, Q
+
+    def set_state(self, p, pd=None, qd=None):
+        p = _f64(p)
+        pd = None if pd is None else _f64(pd)
+        qd = None if qd is None else _f64(qd)
+        _check(_lib.rh_set_state(self._h, _ptr(p), _ptr(pd), _ptr(qd)))
+
+    def powerflow(self, x0=None, tol=1e-12, max_iter=20, raise_on_noconv=True):
+        x0 = None if x0 is None else _f64(x0)
+        x = np.empty(self.n_x)
+        it = C.c_int32(0)
+        res = C.c_double(0.0)
+        st = _lib.rh_powerflow(self._h, _ptr(x0), float(tol), int(max_iter), _ptr(x), C.byref(it), C.byref(res))
+        if st != RH_ENOCONV or raise_on_noconv:
+            _check(st)
+        return x, int(it.value), float(res.value), st
+
+    def adjoint(self):
+        F = C.c_double(0.0)
+        lam = np.empty(self.n_x)
+        grad = np.empty(self.n_p)
+        _check(_lib.rh_adjoint(self._h, C.byref(F), _ptr(lam), _ptr(grad)))
+        return lam, grad, float(F.value)
+
+    def refactor(self):
+        A = np.empty(self.dims.nnz_l + self.dims.nnz_u)
+        _check(_lib.rh_refactor(self._h, _ptr(A)))
+        return A
+
+    # ---- Algorithm 2 -------------------------------------------------------------
+    def hessvec(self, W, HW=None, stream=None):
+        """HW = (Hess F) W.  W: (n_p, N) numpy (column-major) or a CUDA torch tensor.
+
+        Torch tensors are taken as column-major (n_p, N): pass ``W.t().contiguous().t()``
+        or a tensor of shape (N, n_p) transposed.
+        """
+        if _is_device(W):
+            N = W.shape[1]
+            assert W.stride(0) == 1, "device W must be column-major (stride(0) == 1)"
+            if HW is None:
+                import torch
+                HW = torch.empty((N, self.n_p), dtype=torch.float64, device=W.device).t()
+            st = stream if stream is not None else _stream_of(W)
+            _check(_lib.rh_hessvec(self._h, _ptr(W), W.stride(1), N, _ptr(HW), HW.stride(1), st, RH_DEVICE_PTRS))
+            return HW
+        W = np.asfortranarray(W, dtype=np.float64)
+        if W.ndim == 1:
+            W = W.reshape(-1, 1, order="F")
+        N = W.shape[1]
+        HW = np.empty((self.n_p, N), order="F")
+        _check(_lib.rh_hessvec(self._h, _ptr(W), self.n_p, N, _ptr(HW), self.n_p, C.c_void_p(0), RH_HOST_PTRS))
+        return HW
+
+    def hessian(self, block_n=256, concurrent=True, out=None, stream=None):
+        flags = RH_HESSIAN_CONCURRENT if concurrent else 0
+        if out is not None and _is_device(out):
+            st = stream if stream is not None else _stream_of(out)
+            _check(_lib.rh_hessian(self._h, int(block_n), _ptr(out), out.stride(1), st, flags | RH_DEVICE_PTRS))
+            return out
+        H = np.empty((self.n_p, self.n_p), order="F")
+        _check(_lib.rh_hessian(self._h, int(block_n), _ptr(H), self.n_p, C.c_void_p(0), flags))
+        return H
+
+    def solve(self, R, trans=False):
+        R = np.array(R, dtype=np.float64, order="F", copy=True)
+        if R.ndim == 1:
+            R = R.reshape(-1, 1, order="F")
+        _check(_lib.rh_solve(self._h, _ptr(R), self.n_x, R.shape[1], int(bool(trans)), C.c_void_p(0), RH_HOST_PTRS))
+        return R
+
+    def lagrangian_hessvec(self, V):
+        V = np.asfortranarray(V, dtype=np.float64)
+        if V.ndim == 1:
+            V = V.reshape(-1, 1, order="F")
+        nu = self.n_x + self.n_p
+        Y = np.empty((nu, V.shape[1]), order="F")
+        _check(_lib.rh_lagrangian_hessvec(self._h, _ptr(V), nu, V.shape[1], _ptr(Y), nu, C.c_void_p(0),
+                                          RH_HOST_PTRS))
+        return Y
+
+    # ---- planted operating point -------------------------------------------------
+    def index_maps(self):
+        """(ix_th, ix_v, ip_v, ip_pg) per bus, from the documented index conventions."""
+        t = np.asarray(self.src.bus_type)
+        n = len(t)
+        ix_th = np.full(n, -1, np.int32)
+        ix_v = np.full(n, -1, np.int32)
+        ip_v = np.full(n, -1, np.int32)
+        ip_pg = np.full(n, -1, np.int32)
+        pv, pq, gen = np.flatnonzero(t == 1), np.flatnonzero(t == 2), np.flatnonzero(t != 2)
+        ix_th[pv] = np.arange(len(pv))
+        ix_th[pq] = len(pv) + np.arange(len(pq))
+        ix_v[pq] = len(pv) + len(pq) + np.arange(len(pq))
+        ip_v[gen] = np.arange(len(gen))
+        ip_pg[pv] = len(gen) + np.arange(len(pv))
+        return ix_th, ix_v, ip_v, ip_pg
+
+    def plant(self, vm=None, va=None) -> Planted:
+        """Loads and parameters that make the planted voltages an exact solution
+        (loads at PQ buses, Pg = P_inj at PV buses), from the library's injections."""
+        g = self.src
+        vm = _f64(g.v_star if vm is None else vm)
+        va = _f64(g.theta_star if va is None else va)
+        P, Q = self.injections(vm, va)
+        ix_th, ix_v, ip_v, ip_pg = self.index_maps()
+        pq = ix_v >= 0
+        pd = np.where(pq, -P, 0.0)
+        qd = np.where(pq, -Q, 0.0)
+        x = np.empty(self.n_x)
+        p = np.empty(self.n_p)
+        th = ix_th >= 0
+        x[ix_th[th]] = va[th]
+        x[ix_v[pq]] = vm[pq]
+        gen = ip_v >= 0
+        p[ip_v[gen]] = vm[gen]
+        pv = ip_pg >= 0
+        p[ip_pg[pv]] = P[pv]
+        return Planted(x, p, pd, qd)

@@ -19,11 +19,20 @@ uses are not available, so these seeded grids stand in for them:
   power-grid-like topology with bounded LU fill);
 * r ~ U[0.001, 0.05], x ~ U[0.01, 0.3], b ~ U[0, 0.05] (p.u., pi model);
 * generator buses are drawn uniformly; the first one drawn is the slack;
-* planted |V| ~ U[0.95, 1.05], theta ~ N(0, 0.1) rad (theta_slack = 0);
+* planted |V| ~ U[0.95, 1.05] and theta ~ N(0, 0.1) rad per bus, drawn as
+  spatially smooth random fields over the bus positions (stationary Gaussian
+  fields with squared-exponential correlation of length 0.1, by random Fourier
+  features; |V| through the normal CDF so that its marginal is uniform), and
+  theta shifted so that theta_slack = 0.  Independent draws per bus would put
+  neighbouring buses of a low-impedance branch at unrelated angles and
+  voltages, an operating point next to voltage collapse on which a +-10 %
+  load change has no power-flow solution; smooth fields keep the marginals and
+  give operating points like those of real grids;
 * quadratic cost c2 ~ U[0.01, 0.1], c1 ~ U[10, 40] per generator.
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -108,6 +117,18 @@ def _knn(pts: np.ndarray, k: int) -> np.ndarray:
     return out
 
 
+def _smooth_field(rng: np.random.Generator, pts: np.ndarray, ell: float, m: int = 64) -> np.ndarray:
+    """Unit-variance stationary Gaussian field with correlation exp(-|d|^2 / (2 ell^2)),
+    approximated by m random Fourier features, evaluated at pts."""
+    w = rng.normal(0.0, 1.0 / ell, (m, 2))
+    ph = rng.uniform(0.0, 2.0 * np.pi, m)
+    return math.sqrt(2.0 / m) * np.cos(pts @ w.T + ph).sum(axis=1)
+
+
+def _normal_cdf(z: np.ndarray) -> np.ndarray:
+    return np.array([0.5 * (1.0 + math.erf(float(t) / math.sqrt(2.0))) for t in z])
+
+
 def make_grid(n_bus: int, n_branch: int, n_gen: int, seed: int,
               base_mva: float = 100.0, lossless: bool = False) -> Grid:
     """Draw one synthetic grid.  ``lossless`` sets every r to 0."""
@@ -147,9 +168,10 @@ def make_grid(n_bus: int, n_branch: int, n_gen: int, seed: int,
     bus_type[gens] = PV
     bus_type[gens[0]] = REF
 
-    v_star = rng.uniform(0.95, 1.05, n_bus)
-    theta_star = rng.normal(0.0, 0.1, n_bus)
-    theta_star[gens[0]] = 0.0
+    z_theta = _smooth_field(rng, pts, 0.1)
+    z_v = _smooth_field(rng, pts, 0.1)
+    theta_star = 0.1 * (z_theta - z_theta[gens[0]])
+    v_star = 0.95 + 0.1 * _normal_cdf(z_v)
 
     c2 = np.zeros(n_bus)
     c1 = np.zeros(n_bus)

@@ -59,6 +59,7 @@ struct rh_grid {
     int *blev_ptr = nullptr, *blev_bus = nullptr, *blev_maxext = nullptr;
     int64_t *lrank_ptr = nullptr, *upd_ptr = nullptr;
     int* upd_pos = nullptr;
+    int *rf_lev_bus = nullptr, *tail_next = nullptr;
     int *jp_ptr = nullptr, *jp_col = nullptr, *jpt_ptr = nullptr, *jpt_row = nullptr, *jpt_src = nullptr;
     int *tp_bus = nullptr, *uth = nullptr, *uv = nullptr, *inc_ptr = nullptr, *inc_nb = nullptr;
     int *inc_uth = nullptr, *inc_uv = nullptr, *gref_row = nullptr, *pg_row = nullptr, *xmap = nullptr;
@@ -146,6 +147,16 @@ struct rh_grid {
         g.pg_row = pg_row; g.pg_curv = pg_curv;
         return g;
     }
+    rh::RfGrid rf() const {
+        rh::RfGrid g;
+        g.n_x = S.n_x; g.t0 = S.t0; g.T = S.n_x - S.t0;
+        g.max_row = S.rf_max_row; g.tail_max_ext = S.tail_max_ext;
+        g.rf_lev_bus = rf_lev_bus; g.q0 = q0; g.nv = nv;
+        g.rowptr = rowptr; g.col = col; g.diagpos = diagpos;
+        g.lrank_ptr = lrank_ptr; g.upd_ptr = upd_ptr; g.upd_pos = upd_pos; g.tail_next = tail_next;
+        g.A = A; g.invdiag = invdiag; g.jmax = umax + 1; g.err = err;
+        return g;
+    }
     int rows() const { return S.n_x + S.n_p + 1; }
 };
 
@@ -196,8 +207,7 @@ rh_status assemble_and_factor(rh_grid* g) {
     RH_CUDA(cudaMemsetAsync(g->umax, 0, 2 * sizeof(unsigned long long), s));
     RH_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
     rh::launch_pf_eval(g->pf(), g->st(), nullptr, g->A, g->jpv, g->umax, g->umax + 1, true, s);
-    rh::launch_refactor(S.flev_ptr.data(), S.n_flev, g->flev_bus, g->q0, g->nv, g->rowptr, g->col, g->diagpos,
-                        g->lrank_ptr, g->upd_ptr, g->upd_pos, g->A, g->invdiag, g->umax + 1, g->err, s);
+    RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_n_lev, s));
     rh::launch_transpose_values((int)S.col.size(), g->tpos, g->A, g->At, (int)S.jp_col.size(), g->jpt_src, g->jpv,
                                 g->jptv, s);
     RH_CUDA(cudaGetLastError());
@@ -221,6 +231,15 @@ rh_status dirs(rh_grid* g, int N, int64_t ld, double* V, double* T, const double
     rh::launch_dirs(g->dir(), L, s);
     RH_CUDA(cudaGetLastError());
     return RH_OK;
+}
+
+// single right-hand side in g->v1 (internal order), in place
+rh_status solve_one(rh_grid* g, unsigned phases, cudaStream_t s) {
+    if (rh::solve1_fits(g->S.n_x)) {
+        RH_CUDA(rh::launch_solve1(g->dir(), g->v1, phases, s));
+        return RH_OK;
+    }
+    return dirs(g, 1, 1, g->v1, g->v1, nullptr, 0, 0, nullptr, 0, phases, s);
 }
 
 __global__ void k_set_p(int n_bus, const int* ip_v, const int* ip_pg, const double* p, double* vm, double* pg) {
@@ -333,6 +352,16 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     RH_CUDA(g->upload(g->lrank_ptr, S.lrank_ptr));
     RH_CUDA(g->upload(g->upd_ptr, S.upd_ptr));
     RH_CUDA(g->upload(g->upd_pos, S.upd_pos));
+    RH_CUDA(g->upload(g->rf_lev_bus, S.rf_lev_bus));
+    {
+        std::vector<int> tail_next(nx - S.t0, 0);
+        for (int q = S.t0; q < nx; q++) {
+            int e = 0;
+            for (int t = S.rowptr[q]; t < S.rowptr[q + 1] && S.col[t] < S.t0; t++) e++;
+            tail_next[q - S.t0] = e;
+        }
+        RH_CUDA(g->upload(g->tail_next, tail_next));
+    }
     RH_CUDA(g->upload(g->jp_ptr, S.jp_ptr));
     RH_CUDA(g->upload(g->jp_col, S.jp_col));
     RH_CUDA(g->upload(g->jpt_ptr, S.jpt_ptr));
@@ -483,12 +512,11 @@ rh_status rh_powerflow(rh_grid* g, const double* x0, double tol, int32_t max_ite
         if (nx == 0) res = 0.0;
         if (res <= tol) { out = RH_OK; break; }
         if (it >= max_iter || !std::isfinite(res)) break;
-        rh::launch_refactor(S.flev_ptr.data(), S.n_flev, g->flev_bus, g->q0, g->nv, g->rowptr, g->col, g->diagpos,
-                            g->lrank_ptr, g->upd_ptr, g->upd_pos, g->A, g->invdiag, g->umax + 1, g->err, s);
+        RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_n_lev, s));
         st = check_err_flag(g);
         if (st) return st;
         RH_CUDA(cudaMemcpyAsync(g->v1, g->gres, nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        st = dirs(g, 1, 1, g->v1, g->v1, nullptr, 0, 0, nullptr, 0, rh::PH_L | rh::PH_U, s);
+        st = solve_one(g, rh::PH_L | rh::PH_U, s);
         if (st) return st;
         rh::launch_newton_update(g->pf(), g->st(), g->v1, s);
         RH_CUDA(cudaGetLastError());
@@ -536,7 +564,7 @@ rh_status rh_adjoint(rh_grid* g, double* F, double* lambda, double* grad) {
     a.gref_th = g->gref_th; a.gref_v = g->gref_v; a.gref_row = g->gref_row; a.gref_val = g->gref_val;
     a.n_gref = g->n_gref; a.uth = g->uth; a.uv = g->uv;
     rh::launch_adjoint_rhs(g->pf(), g->st(), a, s);
-    st = dirs(g, 1, 1, g->v1, g->v1, nullptr, 0, 0, nullptr, 0, rh::PH_UT | rh::PH_LT, s);
+    st = solve_one(g, rh::PH_UT | rh::PH_LT, s);
     if (st) return st;
     RH_CUDA(cudaMemcpyAsync(g->lam, g->v1, S.n_x * sizeof(double), cudaMemcpyDeviceToDevice, s));
     rh::launch_adjoint_coef(g->pf(), g->st(), g->lam, g->dscal, g->inc_ptr, g->inc_nb, g->inc_coef, g->d2, g->asum,

@@ -132,44 +132,121 @@ __global__ void k_newton_update(PfGrid g, PfState s, const double* dx) {
 // fixed-pattern LU refactorisation (row-wise elimination, static pivots)
 // ---------------------------------------------------------------------------
 
-// One warp per bus of the level.  Row i of A is eliminated by the finished
-// rows k < i of its L part, in increasing k: l_ik = a_ik / u_kk, then
-// a_ij -= l_ik u_kj for every j > k in row k (positions precomputed).
-// Rows of earlier levels are final; lanes share the updates of one k.
-__global__ void k_refactor_level(int b0, int nb, const int* __restrict__ flev_bus, const int* __restrict__ q0,
-                                 const uint8_t* __restrict__ nv, const int* __restrict__ rowptr,
-                                 const int* __restrict__ col, const int* __restrict__ diagpos,
-                                 const int64_t* __restrict__ lrank_ptr, const int64_t* __restrict__ upd_ptr,
-                                 const int* __restrict__ upd_pos, double* A, double* invdiag,
-                                 const unsigned long long* jmax, int* err) {
-    int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
+// Sparse part, one warp per bus of a level.  Row i of A is eliminated by the
+// finished rows k < i of its L part, in increasing k: l_ik = a_ik / u_kk, then
+// a_ij -= l_ik u_kj for every j > k in row k (positions precomputed).  The
+// rows of the bus are staged in shared memory, so the sequential chain of a
+// row waits on shared-memory latency only; lanes share the updates of one k.
+__global__ void k_refactor_sparse(RfGrid g, int b0, int nb) {
+    extern __shared__ double rbuf[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = blockIdx.x * (blockDim.x >> 5) + wib;
     if (w >= nb) return;
-    int k = flev_bus[b0 + w];
-    double tau = 1e-14 * __longlong_as_double((long long)*jmax);
-    for (int r = 0; r < nv[k]; r++) {
-        int i = q0[k] + r;
-        int rp = rowptr[i], dp = diagpos[i];
-        int64_t rank0 = lrank_ptr[i];
+    double* buf = rbuf + (size_t)wib * g.max_row;
+    const int k = g.rf_lev_bus[b0 + w];
+    const double tau = 1e-14 * __longlong_as_double((long long)*g.jmax);
+    for (int r = 0; r < g.nv[k]; r++) {
+        const int i = g.q0[k] + r;
+        const int rp = g.rowptr[i], re = g.rowptr[i + 1], dp = g.diagpos[i];
+        for (int e = lane; e < re - rp; e += 32) buf[e] = g.A[rp + e];
+        __syncwarp();
+        const int64_t rank0 = g.lrank_ptr[i];
         for (int s = rp; s < dp; s++) {
-            int kk = col[s];
-            double l = A[s] * invdiag[kk];
+            const int kk = g.col[s];
+            const double l = buf[s - rp] * g.invdiag[kk];
+            const int u0 = g.diagpos[kk] + 1, cnt = g.rowptr[kk + 1] - u0;
+            const int64_t base = g.upd_ptr[rank0 + (s - rp)];
             __syncwarp();
-            if (lane == 0) A[s] = l;
-            int u0 = diagpos[kk] + 1, cnt = rowptr[kk + 1] - u0;
-            int64_t base = upd_ptr[rank0 + (s - rp)];
+            if (lane == 0) buf[s - rp] = l;
             for (int t = lane; t < cnt; t += 32) {
-                int pos = upd_pos[base + t];
-                A[pos] = fma(-l, A[u0 + t], A[pos]);
+                int pos = g.upd_pos[base + t] - rp;
+                buf[pos] = fma(-l, g.A[u0 + t], buf[pos]);
             }
             __syncwarp();
         }
+        const double piv = buf[dp - rp];
         if (lane == 0) {
-            double piv = A[dp];
-            if (!(fabs(piv) > tau)) atomicOr(err, 1);
-            invdiag[i] = 1.0 / piv;
+            if (!(fabs(piv) > tau)) atomicOr(g.err, 1);
+            g.invdiag[i] = 1.0 / piv;
         }
+        for (int e = lane; e < re - rp; e += 32) g.A[rp + e] = buf[e];
         __syncwarp();
+    }
+}
+
+// Dense trailing block [t0, n_x), one CTA.  Phase 1: each tail row applies the
+// pivots k < t0 of its L part (warp per row, the part of the row left of t0
+// staged per warp); phase 2: right-looking LU of the T x T block in shared
+// memory with the static diagonal pivots.  Every entry receives the same
+// updates in the same order as in the row-wise elimination.
+__global__ void __launch_bounds__(1024, 1) k_refactor_tail(RfGrid g, int nw1) {
+    extern __shared__ double sm[];
+    const int T = g.T, t0 = g.t0;
+    double* D = sm;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    double* ebuf = sm + (size_t)T * T + (size_t)warp * g.tail_max_ext;
+    const double tau = 1e-14 * __longlong_as_double((long long)*g.jmax);
+    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) D[idx] = 0.0;
+    __syncthreads();
+    for (int i = t0 + warp; i < g.n_x; i += nwarps) {
+        int rp = g.rowptr[i], re = g.rowptr[i + 1];
+        for (int e = lane; e < re - rp; e += 32) {
+            int c = g.col[rp + e];
+            if (c >= t0) D[(size_t)(i - t0) * T + (c - t0)] = g.A[rp + e];
+        }
+    }
+    __syncthreads();
+    if (warp < nw1) {
+        for (int i = t0 + warp; i < g.n_x; i += nw1) {
+            const int rp = g.rowptr[i], n_ext = g.tail_next[i - t0];
+            for (int e = lane; e < n_ext; e += 32) ebuf[e] = g.A[rp + e];
+            __syncwarp();
+            const int64_t rank0 = g.lrank_ptr[i];
+            double* Drow = D + (size_t)(i - t0) * T;
+            for (int e = 0; e < n_ext; e++) {
+                const int s = rp + e;
+                const int kk = g.col[s];
+                const double l = ebuf[e] * g.invdiag[kk];
+                const int u0 = g.diagpos[kk] + 1, cnt = g.rowptr[kk + 1] - u0;
+                const int64_t base = g.upd_ptr[rank0 + e];
+                __syncwarp();
+                if (lane == 0) ebuf[e] = l;
+                for (int t = lane; t < cnt; t += 32) {
+                    int pos = g.upd_pos[base + t];
+                    int c = g.col[pos];
+                    double u = g.A[u0 + t];
+                    if (c < t0) ebuf[pos - rp] = fma(-l, u, ebuf[pos - rp]);
+                    else Drow[c - t0] = fma(-l, u, Drow[c - t0]);
+                }
+                __syncwarp();
+            }
+            for (int e = lane; e < n_ext; e += 32) g.A[rp + e] = ebuf[e];
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < T; k++) {
+        const double piv = D[(size_t)k * T + k];
+        const double ip = 1.0 / piv;
+        if (threadIdx.x == 0) {
+            if (!(fabs(piv) > tau)) atomicOr(g.err, 1);
+            g.invdiag[t0 + k] = ip;
+        }
+        for (int i = k + 1 + threadIdx.x; i < T; i += blockDim.x) D[(size_t)i * T + k] *= ip;
+        __syncthreads();
+        const int m = T - k - 1;
+        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+            int ii = k + 1 + idx / m, jj = k + 1 + idx % m;
+            D[(size_t)ii * T + jj] = fma(-D[(size_t)ii * T + k], D[(size_t)k * T + jj], D[(size_t)ii * T + jj]);
+        }
+        __syncthreads();
+    }
+    for (int i = t0 + warp; i < g.n_x; i += nwarps) {
+        int rp = g.rowptr[i], re = g.rowptr[i + 1];
+        for (int e = lane; e < re - rp; e += 32) {
+            int c = g.col[rp + e];
+            if (c >= t0) g.A[rp + e] = D[(size_t)(i - t0) * T + (c - t0)];
+        }
     }
 }
 
@@ -187,8 +264,8 @@ __global__ void k_transpose_values(int nnz, const int* __restrict__ tpos, const 
 
 __device__ __forceinline__ int choose_ks(int nb, int D, int maxext) {
     int base = nb * D;
-    if (base >= kDirThreads / 2) return 1;
-    int ks = kDirThreads / base;
+    if (base >= (int)blockDim.x / 2) return 1;
+    int ks = (int)blockDim.x / base;
     int lim = maxext / 4;
     if (ks > lim) ks = lim;
     int cap = kPartCap / (2 * base);
@@ -455,6 +532,20 @@ __global__ void __launch_bounds__(kDirThreads, 2) k_dirs(DirGrid g, DirLaunch L)
     }
 }
 
+// One right-hand side, one CTA, x held in shared memory for the whole sweep
+// (Newton steps and the first-order adjoint).
+__global__ void __launch_bounds__(1024, 1) k_solve1(DirGrid g, double* x, unsigned phases) {
+    extern __shared__ double X[];
+    __shared__ double part[kPartCap];
+    for (int q = threadIdx.x; q < g.n_x; q += blockDim.x) X[q] = x[q];
+    __syncthreads();
+    if (phases & PH_L) sweep_fwd<false>(g, g.A, X, 1, 0, 1, part);
+    if (phases & PH_U) sweep_bwd<true>(g, g.A, X, 1, 0, 1, part);
+    if (phases & PH_UT) sweep_fwd<true>(g, g.At, X, 1, 0, 1, part);
+    if (phases & PH_LT) sweep_bwd<false>(g, g.At, X, 1, 0, 1, part);
+    for (int q = threadIdx.x; q < g.n_x; q += blockDim.x) x[q] = X[q];
+}
+
 // ---------------------------------------------------------------------------
 // adjoint (eq. 7) and the per-state second-order coefficients
 // ---------------------------------------------------------------------------
@@ -495,14 +586,26 @@ __global__ void k_adjoint_rhs(PfGrid g, PfState s, AdjData a) {
         a.rhs[g.qth[j]] = -cref * dth;
         if (g.qv[j] >= 0) a.rhs[g.qv[j]] = -cref * dv;
     }
-    double F = 0.0;
-    for (int i = 0; i < g.n_bus; i++) {
+}
+
+// F = sum over generators of c2 (S Pg)^2 + c1 S Pg, one block, fixed reduction order.
+__global__ void k_objective(PfGrid g, PfState s, double* F) {
+    __shared__ double red[256];
+    const double S = g.base_mva;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < g.n_bus; i += blockDim.x) {
         if (g.qv[i] >= 0) continue;  // PQ bus: no generator
-        double pg = (i == r) ? pg_ref : s.pg[i];
+        double pg = (i == g.ref) ? s.P[i] + s.pd[i] : s.pg[i];
         double P = S * pg;
-        F += g.c2[i] * P * P + g.c1[i] * P;
+        acc += g.c2[i] * P * P + g.c1[i] * P;
     }
-    *a.F = F;
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *F = red[0];
 }
 
 // One thread per bus: bus weights mu, nu from lambda (mu_slack = c'_slack) and
@@ -608,18 +711,36 @@ void launch_newton_update(const PfGrid& g, const PfState& s, const double* dx, c
     if (g.n_bus > 0) k_newton_update<<<blocks_for(g.n_bus, 128), 128, 0, st>>>(g, s, dx);
 }
 
-void launch_refactor(const int* flev_ptr_host, int n_flev, const int* flev_bus, const int* q0, const uint8_t* nv,
-                     const int* rowptr, const int* col, const int* diagpos, const int64_t* lrank_ptr,
-                     const int64_t* upd_ptr, const int* upd_pos, double* A, double* invdiag,
-                     const unsigned long long* jmax, int* err, cudaStream_t st) {
-    for (int lev = 0; lev < n_flev; lev++) {
-        int b0 = flev_ptr_host[lev], nb = flev_ptr_host[lev + 1] - b0;
-        if (nb <= 0) continue;
-        int threads = 128;
-        int blocks = blocks_for((int64_t)nb * 32, threads);
-        k_refactor_level<<<blocks, threads, 0, st>>>(b0, nb, flev_bus, q0, nv, rowptr, col, diagpos, lrank_ptr,
-                                                      upd_ptr, upd_pos, A, invdiag, jmax, err);
+size_t refactor_tail_smem(const RfGrid& g, int* nw1) {
+    const size_t cap = 227 * 1024;
+    size_t dense = (size_t)g.T * g.T * sizeof(double);
+    int w = 32;
+    while (w > 1 && dense + (size_t)w * g.tail_max_ext * sizeof(double) > cap) w--;
+    *nw1 = w;
+    return dense + (size_t)w * g.tail_max_ext * sizeof(double);
+}
+
+cudaError_t launch_refactor(const RfGrid& g, const int* rf_lev_ptr_host, int rf_n_lev, cudaStream_t st) {
+    const int threads = 128;
+    size_t smem = (size_t)(threads / 32) * g.max_row * sizeof(double);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_refactor_sparse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
     }
+    for (int lev = 0; lev < rf_n_lev; lev++) {
+        int b0 = rf_lev_ptr_host[lev], nb = rf_lev_ptr_host[lev + 1] - b0;
+        if (nb <= 0) continue;
+        int blocks = blocks_for((int64_t)nb * 32, threads);
+        k_refactor_sparse<<<blocks, threads, smem, st>>>(g, b0, nb);
+    }
+    if (g.T > 0) {
+        int nw1 = 1;
+        size_t ts = refactor_tail_smem(g, &nw1);
+        cudaError_t e = cudaFuncSetAttribute(k_refactor_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts);
+        if (e != cudaSuccess) return e;
+        k_refactor_tail<<<1, 1024, ts, st>>>(g, nw1);
+    }
+    return cudaGetLastError();
 }
 
 void launch_transpose_values(int nnz, const int* tpos, const double* A, double* At, int nnz_jp,
@@ -648,6 +769,17 @@ void launch_dirs(const DirGrid& g, const DirLaunch& L, cudaStream_t st) {
 
 void launch_adjoint_rhs(const PfGrid& g, const PfState& s, const AdjData& a, cudaStream_t st) {
     k_adjoint_rhs<<<1, 32, 0, st>>>(g, s, a);
+    k_objective<<<1, 256, 0, st>>>(g, s, a.F);
+}
+
+bool solve1_fits(int n_x) { return (size_t)n_x * sizeof(double) + kPartCap * sizeof(double) <= 227 * 1024; }
+
+cudaError_t launch_solve1(const DirGrid& g, double* x, unsigned phases, cudaStream_t st) {
+    size_t smem = (size_t)(g.n_x > 0 ? g.n_x : 1) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_solve1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_solve1<<<1, 1024, smem, st>>>(g, x, phases);
+    return cudaGetLastError();
 }
 
 void launch_adjoint_coef(const PfGrid& g, const PfState& s, const double* lambda_int, const double* cref,

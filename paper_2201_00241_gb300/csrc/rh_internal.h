@@ -54,6 +54,14 @@ struct Symbolic {
     std::vector<int64_t> lrank_ptr;         // row -> first L-entry rank
     std::vector<int64_t> upd_ptr;           // L-entry rank -> first update
     std::vector<int> upd_pos;
+    // split of the refactorisation: rows < t0 (buses < tail_bus0) are eliminated
+    // level by level; the trailing block [t0, n_x) is factored densely in one
+    // CTA's shared memory.  rf_lev_*: the sparse buses grouped by forward level.
+    int t0 = 0, tail_bus0 = 0;
+    int rf_n_lev = 0;
+    std::vector<int> rf_lev_ptr, rf_lev_bus;
+    int rf_max_row = 0;                     // longest sparse row (entries)
+    int tail_max_ext = 0;                   // longest part of a tail row left of t0
 
     // admittance matrix (CSR by bus, diagonal included, parallel branches merged)
     std::vector<int> yp, yj;
@@ -72,8 +80,9 @@ struct Symbolic {
 };
 
 // Builds everything above.  Returns an empty string on success, else a message.
+// max_tail: largest trailing block (variables) factored densely.
 std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int32_t* to,
                            const double* r, const double* x, const double* b,
-                           const int8_t* type, Symbolic& S);
+                           const int8_t* type, Symbolic& S, int max_tail = 128);
 
 }  // namespace rh

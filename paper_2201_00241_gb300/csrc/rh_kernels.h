@@ -90,13 +90,27 @@ void launch_injections(const PfGrid& g, const PfState& s, cudaStream_t st);
 void launch_pf_eval(const PfGrid& g, const PfState& s, double* gres, double* A, double* jpv,
                     unsigned long long* gmax, unsigned long long* jmax, bool want_jac, cudaStream_t st);
 void launch_newton_update(const PfGrid& g, const PfState& s, const double* dx, cudaStream_t st);
-void launch_refactor(const int* flev_ptr_host, int n_flev, const int* flev_bus, const int* q0, const uint8_t* nv,
-                     const int* rowptr, const int* col, const int* diagpos, const int64_t* lrank_ptr,
-                     const int64_t* upd_ptr, const int* upd_pos, double* A, double* invdiag,
-                     const unsigned long long* jmax, int* err, cudaStream_t st);
+// Fixed-pattern LU refactorisation data (device pointers).
+struct RfGrid {
+    int n_x, t0, T;                    // dense trailing block [t0, n_x), T = n_x - t0
+    int max_row, tail_max_ext;
+    const int *rf_lev_bus, *q0;
+    const uint8_t *nv;
+    const int *rowptr, *col, *diagpos;
+    const int64_t *lrank_ptr, *upd_ptr;
+    const int *upd_pos;
+    const int *tail_next;              // per tail row: entries left of t0
+    double *A, *invdiag;
+    const unsigned long long *jmax;
+    int *err;
+};
+cudaError_t launch_refactor(const RfGrid& g, const int* rf_lev_ptr_host, int rf_n_lev, cudaStream_t st);
 void launch_transpose_values(int nnz, const int* tpos, const double* A, double* At, int nnz_jp,
                              const int* jpt_src, const double* jpv, double* jptv, cudaStream_t st);
 void launch_dirs(const DirGrid& g, const DirLaunch& L, cudaStream_t st);
+// one right-hand side in shared memory (requires solve1_fits(n_x))
+bool solve1_fits(int n_x);
+cudaError_t launch_solve1(const DirGrid& g, double* x, unsigned phases, cudaStream_t st);
 int dirs_default_ctas(int N);
 
 // adjoint helpers

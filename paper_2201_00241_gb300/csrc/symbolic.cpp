@@ -63,7 +63,7 @@ int find_in_row(const std::vector<int>& rowptr, const std::vector<int>& col, int
 
 std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int32_t* to,
                            const double* r, const double* x, const double* b,
-                           const int8_t* type, Symbolic& S) {
+                           const int8_t* type, Symbolic& S, int max_tail) {
     if (n_bus < 1 || n_branch < 0) return "n_bus must be >= 1 and n_branch >= 0";
     S.n_bus = n_bus;
     S.n_branch = n_branch;
@@ -250,6 +250,34 @@ std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int
             }
             S.upd_ptr[rank + 1] = (int64_t)S.upd_pos.size();
         }
+    }
+
+    // ---- split: sparse levels + dense trailing block --------------------------
+    S.tail_bus0 = S.n_elim;
+    while (S.tail_bus0 > 0 && S.n_x - S.q0[S.tail_bus0 - 1] <= max_tail) S.tail_bus0--;
+    S.t0 = S.tail_bus0 < S.n_elim ? S.q0[S.tail_bus0] : S.n_x;
+    {
+        std::vector<std::vector<int>> by_lev(S.n_flev);
+        for (int t = 0; t < S.n_elim; t++) {
+            int k = S.flev_bus[t];
+            if (k < S.tail_bus0) by_lev[S.flevel[k]].push_back(k);
+        }
+        S.rf_lev_ptr.assign(1, 0);
+        S.rf_lev_bus.clear();
+        for (auto& v : by_lev) {
+            if (v.empty()) continue;
+            for (int k : v) S.rf_lev_bus.push_back(k);
+            S.rf_lev_ptr.push_back((int)S.rf_lev_bus.size());
+        }
+        S.rf_n_lev = (int)S.rf_lev_ptr.size() - 1;
+    }
+    S.rf_max_row = 0;
+    for (int q = 0; q < S.t0; q++) S.rf_max_row = std::max(S.rf_max_row, S.rowptr[q + 1] - S.rowptr[q]);
+    S.tail_max_ext = 0;
+    for (int q = S.t0; q < S.n_x; q++) {
+        int e = 0;
+        for (int s = S.rowptr[q]; s < S.rowptr[q + 1] && S.col[s] < S.t0; s++) e++;
+        S.tail_max_ext = std::max(S.tail_max_ext, e);
     }
 
     // ---- J_p pattern and the assembly destinations -------------------------

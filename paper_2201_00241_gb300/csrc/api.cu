@@ -57,9 +57,8 @@ struct rh_grid {
     uint8_t* nv = nullptr;
     int *flev_ptr = nullptr, *flev_bus = nullptr, *flev_maxext = nullptr;
     int *blev_ptr = nullptr, *blev_bus = nullptr, *blev_maxext = nullptr;
-    int64_t *lrank_ptr = nullptr, *upd_ptr = nullptr;
-    int* upd_pos = nullptr;
-    int *rf_lev_bus = nullptr, *tail_next = nullptr;
+    int *rf_lev_bus = nullptr, *rf_tgt_pos = nullptr, *rf_c_l = nullptr, *rf_c_u = nullptr;
+    int64_t* rf_tgt_cptr = nullptr;
     int *jp_ptr = nullptr, *jp_col = nullptr, *jpt_ptr = nullptr, *jpt_row = nullptr, *jpt_src = nullptr;
     int *tp_bus = nullptr, *uth = nullptr, *uv = nullptr, *inc_ptr = nullptr, *inc_nb = nullptr;
     int *inc_uth = nullptr, *inc_uv = nullptr, *gref_row = nullptr, *pg_row = nullptr, *xmap = nullptr;
@@ -150,10 +149,9 @@ struct rh_grid {
     rh::RfGrid rf() const {
         rh::RfGrid g;
         g.n_x = S.n_x; g.t0 = S.t0; g.T = S.n_x - S.t0;
-        g.max_row = S.rf_max_row; g.tail_max_ext = S.tail_max_ext;
         g.rf_lev_bus = rf_lev_bus; g.q0 = q0; g.nv = nv;
-        g.rowptr = rowptr; g.col = col; g.diagpos = diagpos;
-        g.lrank_ptr = lrank_ptr; g.upd_ptr = upd_ptr; g.upd_pos = upd_pos; g.tail_next = tail_next;
+        g.rowptr = rowptr; g.col = col; g.diagpos = diagpos; g.tpos = tpos;
+        g.tgt_pos = rf_tgt_pos; g.tgt_cptr = rf_tgt_cptr; g.c_l = rf_c_l; g.c_u = rf_c_u;
         g.A = A; g.invdiag = invdiag; g.jmax = umax + 1; g.err = err;
         return g;
     }
@@ -207,7 +205,7 @@ rh_status assemble_and_factor(rh_grid* g) {
     RH_CUDA(cudaMemsetAsync(g->umax, 0, 2 * sizeof(unsigned long long), s));
     RH_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
     rh::launch_pf_eval(g->pf(), g->st(), nullptr, g->A, g->jpv, g->umax, g->umax + 1, true, s);
-    RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_n_lev, s));
+    RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_tgt_lev_ptr.data(), S.rf_n_lev, s));
     rh::launch_transpose_values((int)S.col.size(), g->tpos, g->A, g->At, (int)S.jp_col.size(), g->jpt_src, g->jpv,
                                 g->jptv, s);
     RH_CUDA(cudaGetLastError());
@@ -349,19 +347,11 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     RH_CUDA(g->upload(g->blev_ptr, blev_ptr));
     RH_CUDA(g->upload(g->blev_bus, S.blev_bus));
     RH_CUDA(g->upload(g->blev_maxext, S.blev_maxext));
-    RH_CUDA(g->upload(g->lrank_ptr, S.lrank_ptr));
-    RH_CUDA(g->upload(g->upd_ptr, S.upd_ptr));
-    RH_CUDA(g->upload(g->upd_pos, S.upd_pos));
     RH_CUDA(g->upload(g->rf_lev_bus, S.rf_lev_bus));
-    {
-        std::vector<int> tail_next(nx - S.t0, 0);
-        for (int q = S.t0; q < nx; q++) {
-            int e = 0;
-            for (int t = S.rowptr[q]; t < S.rowptr[q + 1] && S.col[t] < S.t0; t++) e++;
-            tail_next[q - S.t0] = e;
-        }
-        RH_CUDA(g->upload(g->tail_next, tail_next));
-    }
+    RH_CUDA(g->upload(g->rf_tgt_pos, S.rf_tgt_pos));
+    RH_CUDA(g->upload(g->rf_tgt_cptr, S.rf_tgt_cptr));
+    RH_CUDA(g->upload(g->rf_c_l, S.rf_c_l));
+    RH_CUDA(g->upload(g->rf_c_u, S.rf_c_u));
     RH_CUDA(g->upload(g->jp_ptr, S.jp_ptr));
     RH_CUDA(g->upload(g->jp_col, S.jp_col));
     RH_CUDA(g->upload(g->jpt_ptr, S.jpt_ptr));
@@ -428,7 +418,7 @@ rh_status rh_grid_dims(const rh_grid* g, rh_dims* o) {
     o->n_x = S.n_x; o->n_p = S.n_p; o->n_levels_fwd = S.n_flev; o->n_levels_bwd = S.n_blev;
     o->nnz_jx = S.nnz_jx; o->nnz_jp = (int64_t)S.jp_col.size();
     o->nnz_l = S.nnz_l; o->nnz_u = S.nnz_u;
-    o->refactor_updates = (int64_t)S.upd_pos.size();
+    o->refactor_updates = (int64_t)S.rf_c_l.size();
     return RH_OK;
 }
 
@@ -512,7 +502,7 @@ rh_status rh_powerflow(rh_grid* g, const double* x0, double tol, int32_t max_ite
         if (nx == 0) res = 0.0;
         if (res <= tol) { out = RH_OK; break; }
         if (it >= max_iter || !std::isfinite(res)) break;
-        RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_n_lev, s));
+        RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_tgt_lev_ptr.data(), S.rf_n_lev, s));
         st = check_err_flag(g);
         if (st) return st;
         RH_CUDA(cudaMemcpyAsync(g->v1, g->gres, nx * sizeof(double), cudaMemcpyDeviceToDevice, s));

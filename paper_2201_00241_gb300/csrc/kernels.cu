@@ -132,59 +132,78 @@ __global__ void k_newton_update(PfGrid g, PfState s, const double* dx) {
 // fixed-pattern LU refactorisation (row-wise elimination, static pivots)
 // ---------------------------------------------------------------------------
 
-// Sparse part, one warp per bus of a level.  Row i of A is eliminated by the
-// finished rows k < i of its L part, in increasing k: l_ik = a_ik / u_kk, then
-// a_ij -= l_ik u_kj for every j > k in row k (positions precomputed).  The
-// rows of the bus are staged in shared memory, so the sequential chain of a
-// row waits on shared-memory latency only; lanes share the updates of one k.
-__global__ void k_refactor_sparse(RfGrid g, int b0, int nb) {
-    extern __shared__ double rbuf[];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int w = blockIdx.x * (blockDim.x >> 5) + wib;
+// Right-looking refactorisation, pivot step of one level: one warp per bus k.
+// All entries it reads are final once the previous levels' updates are done.
+// Bus block (theta, v) of a PQ bus:
+//   u_tt = a_tt, l_vt = a_vt / u_tt, u_vv = a_vv - l_vt u_tv,
+//   U row of v:    u_vj = a_vj - l_vt u_tj,
+//   L columns:     l_it = a_it / u_tt,  l_iv = (a_iv - l_it u_tv) / u_vv
+// for every later variable i, j of the bus's pattern (a PV bus has theta only).
+__global__ void k_rf_pivot(RfGrid g, int b0, int nb) {
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= nb) return;
-    double* buf = rbuf + (size_t)wib * g.max_row;
     const int k = g.rf_lev_bus[b0 + w];
+    const int qt = g.q0[k];
+    const bool two = g.nv[k] == 2;
     const double tau = 1e-14 * __longlong_as_double((long long)*g.jmax);
-    for (int r = 0; r < g.nv[k]; r++) {
-        const int i = g.q0[k] + r;
-        const int rp = g.rowptr[i], re = g.rowptr[i + 1], dp = g.diagpos[i];
-        for (int e = lane; e < re - rp; e += 32) buf[e] = g.A[rp + e];
+    const int dt = g.diagpos[qt];
+    const double utt = g.A[dt];
+    const double it = 1.0 / utt;
+    double utv = 0.0, lvt = 0.0, iv = 0.0;
+    int dv = 0;
+    if (two) {
+        dv = g.diagpos[qt + 1];
+        utv = g.A[dt + 1];
+        lvt = g.A[dv - 1] * it;
+        double uvv = fma(-lvt, utv, g.A[dv]);
+        iv = 1.0 / uvv;
         __syncwarp();
-        const int64_t rank0 = g.lrank_ptr[i];
-        for (int s = rp; s < dp; s++) {
-            const int kk = g.col[s];
-            const double l = buf[s - rp] * g.invdiag[kk];
-            const int u0 = g.diagpos[kk] + 1, cnt = g.rowptr[kk + 1] - u0;
-            const int64_t base = g.upd_ptr[rank0 + (s - rp)];
-            __syncwarp();
-            if (lane == 0) buf[s - rp] = l;
-            for (int t = lane; t < cnt; t += 32) {
-                int pos = g.upd_pos[base + t] - rp;
-                buf[pos] = fma(-l, g.A[u0 + t], buf[pos]);
-            }
-            __syncwarp();
-        }
-        const double piv = buf[dp - rp];
         if (lane == 0) {
-            if (!(fabs(piv) > tau)) atomicOr(g.err, 1);
-            g.invdiag[i] = 1.0 / piv;
+            g.A[dv - 1] = lvt;
+            g.A[dv] = uvv;
+            g.invdiag[qt + 1] = iv;
+            if (!(fabs(uvv) > tau)) atomicOr(g.err, 1);
         }
-        for (int e = lane; e < re - rp; e += 32) g.A[rp + e] = buf[e];
-        __syncwarp();
+    }
+    if (lane == 0) {
+        g.invdiag[qt] = it;
+        if (!(fabs(utt) > tau)) atomicOr(g.err, 1);
+    }
+    const int ut0 = dt + (two ? 2 : 1);
+    const int uv0 = dv + 1;
+    const int n = g.rowptr[qt + 1] - ut0;
+    for (int e = lane; e < n; e += 32) {
+        if (two) g.A[uv0 + e] = fma(-lvt, g.A[ut0 + e], g.A[uv0 + e]);
+        int pt = g.tpos[ut0 + e];
+        double lt = g.A[pt] * it;
+        g.A[pt] = lt;
+        if (two) {
+            int pv = g.tpos[uv0 + e];
+            g.A[pv] = fma(-lt, utv, g.A[pv]) * iv;
+        }
     }
 }
 
-// Dense trailing block [t0, n_x), one CTA.  Phase 1: each tail row applies the
-// pivots k < t0 of its L part (warp per row, the part of the row left of t0
-// staged per warp); phase 2: right-looking LU of the T x T block in shared
-// memory with the static diagonal pivots.  Every entry receives the same
-// updates in the same order as in the row-wise elimination.
-__global__ void __launch_bounds__(1024, 1) k_refactor_tail(RfGrid g, int nw1) {
-    extern __shared__ double sm[];
+// Update step of one level: every target entry a_ij of the level subtracts the
+// sum of its contributions l_ik u_kj (fixed order: bus, then theta before v).
+__global__ void k_rf_update(RfGrid g, int64_t t0, int64_t nt) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    t += t0;
+    double acc = 0.0;
+    for (int64_t c = g.tgt_cptr[t]; c < g.tgt_cptr[t + 1]; c++) acc = fma(g.A[g.c_l[c]], g.A[g.c_u[c]], acc);
+    const int p = g.tgt_pos[t];
+    g.A[p] -= acc;
+}
+
+// Dense trailing block [t0, n_x), one CTA: load it (all updates from the
+// earlier pivots are applied), right-looking LU with the static diagonal
+// pivots in shared memory, store it back.
+__global__ void __launch_bounds__(1024, 1) k_refactor_tail(RfGrid g) {
+    extern __shared__ double D[];
     const int T = g.T, t0 = g.t0;
-    double* D = sm;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    double* ebuf = sm + (size_t)T * T + (size_t)warp * g.tail_max_ext;
     const double tau = 1e-14 * __longlong_as_double((long long)*g.jmax);
     for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) D[idx] = 0.0;
     __syncthreads();
@@ -193,35 +212,6 @@ __global__ void __launch_bounds__(1024, 1) k_refactor_tail(RfGrid g, int nw1) {
         for (int e = lane; e < re - rp; e += 32) {
             int c = g.col[rp + e];
             if (c >= t0) D[(size_t)(i - t0) * T + (c - t0)] = g.A[rp + e];
-        }
-    }
-    __syncthreads();
-    if (warp < nw1) {
-        for (int i = t0 + warp; i < g.n_x; i += nw1) {
-            const int rp = g.rowptr[i], n_ext = g.tail_next[i - t0];
-            for (int e = lane; e < n_ext; e += 32) ebuf[e] = g.A[rp + e];
-            __syncwarp();
-            const int64_t rank0 = g.lrank_ptr[i];
-            double* Drow = D + (size_t)(i - t0) * T;
-            for (int e = 0; e < n_ext; e++) {
-                const int s = rp + e;
-                const int kk = g.col[s];
-                const double l = ebuf[e] * g.invdiag[kk];
-                const int u0 = g.diagpos[kk] + 1, cnt = g.rowptr[kk + 1] - u0;
-                const int64_t base = g.upd_ptr[rank0 + e];
-                __syncwarp();
-                if (lane == 0) ebuf[e] = l;
-                for (int t = lane; t < cnt; t += 32) {
-                    int pos = g.upd_pos[base + t];
-                    int c = g.col[pos];
-                    double u = g.A[u0 + t];
-                    if (c < t0) ebuf[pos - rp] = fma(-l, u, ebuf[pos - rp]);
-                    else Drow[c - t0] = fma(-l, u, Drow[c - t0]);
-                }
-                __syncwarp();
-            }
-            for (int e = lane; e < n_ext; e += 32) g.A[rp + e] = ebuf[e];
-            __syncwarp();
         }
     }
     __syncthreads();
@@ -711,34 +701,19 @@ void launch_newton_update(const PfGrid& g, const PfState& s, const double* dx, c
     if (g.n_bus > 0) k_newton_update<<<blocks_for(g.n_bus, 128), 128, 0, st>>>(g, s, dx);
 }
 
-size_t refactor_tail_smem(const RfGrid& g, int* nw1) {
-    const size_t cap = 227 * 1024;
-    size_t dense = (size_t)g.T * g.T * sizeof(double);
-    int w = 32;
-    while (w > 1 && dense + (size_t)w * g.tail_max_ext * sizeof(double) > cap) w--;
-    *nw1 = w;
-    return dense + (size_t)w * g.tail_max_ext * sizeof(double);
-}
-
-cudaError_t launch_refactor(const RfGrid& g, const int* rf_lev_ptr_host, int rf_n_lev, cudaStream_t st) {
-    const int threads = 128;
-    size_t smem = (size_t)(threads / 32) * g.max_row * sizeof(double);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_refactor_sparse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    for (int lev = 0; lev < rf_n_lev; lev++) {
-        int b0 = rf_lev_ptr_host[lev], nb = rf_lev_ptr_host[lev + 1] - b0;
-        if (nb <= 0) continue;
-        int blocks = blocks_for((int64_t)nb * 32, threads);
-        k_refactor_sparse<<<blocks, threads, smem, st>>>(g, b0, nb);
+cudaError_t launch_refactor(const RfGrid& g, const int* lev_ptr_host, const int64_t* tgt_lev_ptr_host, int n_lev,
+                            cudaStream_t st) {
+    for (int lev = 0; lev < n_lev; lev++) {
+        int b0 = lev_ptr_host[lev], nb = lev_ptr_host[lev + 1] - b0;
+        if (nb > 0) k_rf_pivot<<<blocks_for((int64_t)nb * 32, 128), 128, 0, st>>>(g, b0, nb);
+        int64_t t0 = tgt_lev_ptr_host[lev], nt = tgt_lev_ptr_host[lev + 1] - t0;
+        if (nt > 0) k_rf_update<<<blocks_for(nt, 256), 256, 0, st>>>(g, t0, nt);
     }
     if (g.T > 0) {
-        int nw1 = 1;
-        size_t ts = refactor_tail_smem(g, &nw1);
+        size_t ts = (size_t)g.T * g.T * sizeof(double);
         cudaError_t e = cudaFuncSetAttribute(k_refactor_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts);
         if (e != cudaSuccess) return e;
-        k_refactor_tail<<<1, 1024, ts, st>>>(g, nw1);
+        k_refactor_tail<<<1, 1024, ts, st>>>(g);
     }
     return cudaGetLastError();
 }

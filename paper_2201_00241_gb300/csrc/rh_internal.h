@@ -48,20 +48,19 @@ struct Symbolic {
     std::vector<int> tpos;                  // position of the transposed entry
     int64_t nnz_l = 0, nnz_u = 0;
 
-    // refactorisation schedule: for every strictly-lower entry s of A (row i,
-    // column k) the positions in row i updated by the strictly-upper part of
-    // row k, in order: upd_ptr[s] .. upd_ptr[s+1]  (indexed by L-entry rank)
-    std::vector<int64_t> lrank_ptr;         // row -> first L-entry rank
-    std::vector<int64_t> upd_ptr;           // L-entry rank -> first update
-    std::vector<int> upd_pos;
-    // split of the refactorisation: rows < t0 (buses < tail_bus0) are eliminated
-    // level by level; the trailing block [t0, n_x) is factored densely in one
-    // CTA's shared memory.  rf_lev_*: the sparse buses grouped by forward level.
+    // Refactorisation schedule.  Buses before tail_bus0 (variables < t0) are
+    // eliminated right-looking, one forward level at a time: the pivot step of a
+    // level finalises the 2x2 (or 1x1) pivot block, U rows and L columns of its
+    // buses; the update step applies a_ij -= sum_k l_ik u_kj to every target
+    // entry of the level, summing its contributions in a fixed order.  The
+    // trailing block [t0, n_x) is then factored densely in one CTA.
     int t0 = 0, tail_bus0 = 0;
     int rf_n_lev = 0;
-    std::vector<int> rf_lev_ptr, rf_lev_bus;
-    int rf_max_row = 0;                     // longest sparse row (entries)
-    int tail_max_ext = 0;                   // longest part of a tail row left of t0
+    std::vector<int> rf_lev_ptr, rf_lev_bus;        // sparse buses grouped by level
+    std::vector<int64_t> rf_tgt_lev_ptr;            // level -> first target
+    std::vector<int> rf_tgt_pos;                    // target position in A
+    std::vector<int64_t> rf_tgt_cptr;               // target -> first contribution
+    std::vector<int> rf_c_l, rf_c_u;                // contribution: positions of l_ik and u_kj
 
     // admittance matrix (CSR by bus, diagonal included, parallel branches merged)
     std::vector<int> yp, yj;

@@ -93,18 +93,18 @@ void launch_newton_update(const PfGrid& g, const PfState& s, const double* dx, c
 // Fixed-pattern LU refactorisation data (device pointers).
 struct RfGrid {
     int n_x, t0, T;                    // dense trailing block [t0, n_x), T = n_x - t0
-    int max_row, tail_max_ext;
     const int *rf_lev_bus, *q0;
     const uint8_t *nv;
-    const int *rowptr, *col, *diagpos;
-    const int64_t *lrank_ptr, *upd_ptr;
-    const int *upd_pos;
-    const int *tail_next;              // per tail row: entries left of t0
+    const int *rowptr, *col, *diagpos, *tpos;
+    const int *tgt_pos;                // update targets (positions in A), grouped by level
+    const int64_t *tgt_cptr;           // target -> first contribution
+    const int *c_l, *c_u;              // contribution positions of l_ik and u_kj
     double *A, *invdiag;
     const unsigned long long *jmax;
     int *err;
 };
-cudaError_t launch_refactor(const RfGrid& g, const int* rf_lev_ptr_host, int rf_n_lev, cudaStream_t st);
+cudaError_t launch_refactor(const RfGrid& g, const int* lev_ptr_host, const int64_t* tgt_lev_ptr_host, int n_lev,
+                            cudaStream_t st);
 void launch_transpose_values(int nnz, const int* tpos, const double* A, double* At, int nnz_jp,
                              const int* jpt_src, const double* jpv, double* jptv, cudaStream_t st);
 void launch_dirs(const DirGrid& g, const DirLaunch& L, cudaStream_t st);

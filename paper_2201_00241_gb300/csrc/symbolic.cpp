@@ -233,26 +233,7 @@ std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int
             S.tpos[s] = t;
         }
 
-    // ---- refactorisation update map (row-wise elimination, IKJ order) ------
-    S.lrank_ptr.assign(S.n_x + 1, 0);
-    for (int q = 0; q < S.n_x; q++) S.lrank_ptr[q + 1] = S.lrank_ptr[q] + (S.diagpos[q] - S.rowptr[q]);
-    S.upd_ptr.assign(S.nnz_l + 1, 0);
-    for (int i = 0; i < S.n_x; i++) {
-        for (int s = S.rowptr[i]; s < S.diagpos[i]; s++) {
-            int k = S.col[s];
-            int64_t rank = S.lrank_ptr[i] + (s - S.rowptr[i]);
-            int p = s + 1;
-            for (int t = S.diagpos[k] + 1; t < S.rowptr[k + 1]; t++) {
-                int j = S.col[t];
-                while (p < S.rowptr[i + 1] && S.col[p] < j) p++;
-                if (p >= S.rowptr[i + 1] || S.col[p] != j) return "internal error: fill pattern not closed";
-                S.upd_pos.push_back(p);
-            }
-            S.upd_ptr[rank + 1] = (int64_t)S.upd_pos.size();
-        }
-    }
-
-    // ---- split: sparse levels + dense trailing block --------------------------
+    // ---- refactorisation schedule -------------------------------------------
     S.tail_bus0 = S.n_elim;
     while (S.tail_bus0 > 0 && S.n_x - S.q0[S.tail_bus0 - 1] <= max_tail) S.tail_bus0--;
     S.t0 = S.tail_bus0 < S.n_elim ? S.q0[S.tail_bus0] : S.n_x;
@@ -264,20 +245,48 @@ std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int
         }
         S.rf_lev_ptr.assign(1, 0);
         S.rf_lev_bus.clear();
+        S.rf_tgt_lev_ptr.assign(1, 0);
+        S.rf_tgt_cptr.assign(1, 0);
+        std::vector<std::tuple<int, int, int, int>> trip;   // (target, order, lpos, upos)
         for (auto& v : by_lev) {
             if (v.empty()) continue;
-            for (int k : v) S.rf_lev_bus.push_back(k);
+            trip.clear();
+            int order = 0;
+            for (int k : v) {
+                S.rf_lev_bus.push_back(k);
+                int qt = S.q0[k];
+                bool two = S.nv[k] == 2;
+                int ut0 = S.diagpos[qt] + (two ? 2 : 1);
+                int uv0 = two ? S.diagpos[qt + 1] + 1 : -1;
+                int n = S.rowptr[qt + 1] - ut0;
+                for (int a = 0; a < n; a++) {
+                    int i = S.col[ut0 + a];
+                    int lt = S.tpos[ut0 + a], lv = two ? S.tpos[uv0 + a] : -1;
+                    for (int bb = 0; bb < n; bb++) {
+                        int j = S.col[ut0 + bb];
+                        int tg = find_in_row(S.rowptr, S.col, i, j);
+                        if (tg < 0) return "internal error: fill pattern not closed";
+                        trip.emplace_back(tg, order, lt, ut0 + bb);
+                        if (two) trip.emplace_back(tg, order + 1, lv, uv0 + bb);
+                    }
+                }
+                order += 2;
+            }
+            std::sort(trip.begin(), trip.end());
+            for (size_t t = 0; t < trip.size(); t++) {
+                int tg = std::get<0>(trip[t]);
+                if (t == 0 || std::get<0>(trip[t - 1]) != tg) {
+                    if (t > 0) S.rf_tgt_cptr.push_back((int64_t)S.rf_c_l.size());
+                    S.rf_tgt_pos.push_back(tg);
+                }
+                S.rf_c_l.push_back(std::get<2>(trip[t]));
+                S.rf_c_u.push_back(std::get<3>(trip[t]));
+            }
+            if (!trip.empty()) S.rf_tgt_cptr.push_back((int64_t)S.rf_c_l.size());
             S.rf_lev_ptr.push_back((int)S.rf_lev_bus.size());
+            S.rf_tgt_lev_ptr.push_back((int64_t)S.rf_tgt_pos.size());
         }
         S.rf_n_lev = (int)S.rf_lev_ptr.size() - 1;
-    }
-    S.rf_max_row = 0;
-    for (int q = 0; q < S.t0; q++) S.rf_max_row = std::max(S.rf_max_row, S.rowptr[q + 1] - S.rowptr[q]);
-    S.tail_max_ext = 0;
-    for (int q = S.t0; q < S.n_x; q++) {
-        int e = 0;
-        for (int s = S.rowptr[q]; s < S.rowptr[q + 1] && S.col[s] < S.t0; s++) e++;
-        S.tail_max_ext = std::max(S.tail_max_ext, e);
     }
 
     // ---- J_p pattern and the assembly destinations -------------------------

@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--case", default=CASE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
     return ap.parse_args()
 
 
@@ -230,7 +231,7 @@ def main():
     Hh = np.empty((n_p, n_p), order="F")
     x0 = st.x.copy()
     e2e_t = []
-    for i in range(args.warmup + args.steps):
+    for i in range(0 if args.no_e2e else args.warmup + args.steps):
         t0 = time.perf_counter()
         lg.set_state(st.p, st.pd, st.qd)
         lg.powerflow(x0, tol=1e-12, max_iter=20)
@@ -238,7 +239,7 @@ def main():
         rh._check(lib.rh_hessian(lg._h, BLOCK_N, rh._ptr(Hh), n_p, None, rh.RH_HESSIAN_CONCURRENT))
         if i >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
-    e2e_value = world * n_p / (sum(e2e_t) / len(e2e_t))
+    e2e_value = world * n_p / (sum(e2e_t) / len(e2e_t)) if e2e_t else None
     h2d = 8 * (n_p + 2 * g.n_bus + lg.n_x)
     d2h = 8 * n_p * n_p + 8 * (lg.n_x + n_p + 1)
 

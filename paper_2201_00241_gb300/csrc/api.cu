@@ -56,6 +56,7 @@ struct rh_grid {
     int *rowptr = nullptr, *col = nullptr, *diagpos = nullptr, *tpos = nullptr, *q0 = nullptr;
     uint8_t* nv = nullptr;
     int *flev_ptr = nullptr, *flev_bus = nullptr, *flev_maxext = nullptr;
+    int4 *fslot = nullptr, *bslot = nullptr;
     int *blev_ptr = nullptr, *blev_bus = nullptr, *blev_maxext = nullptr;
     int *rf_lev_bus = nullptr, *rf_tgt_pos = nullptr, *rf_c_l = nullptr, *rf_c_u = nullptr;
     int64_t* rf_tgt_cptr = nullptr;
@@ -82,7 +83,7 @@ struct rh_grid {
 
     // --- workspace for the direction kernel --------------------------------
     double *V = nullptr, *T = nullptr;
-    size_t ws_cols = 0;
+    size_t ws_elems = 0;
     double *stage_in = nullptr, *stage_out = nullptr;
     size_t stage_n = 0;
 
@@ -137,6 +138,7 @@ struct rh_grid {
         g.n_flev = S.n_flev; g.n_blev = S.n_blev;
         g.flev_ptr = flev_ptr; g.flev_bus = flev_bus; g.flev_maxext = flev_maxext;
         g.blev_ptr = blev_ptr; g.blev_bus = blev_bus; g.blev_maxext = blev_maxext;
+        g.fslot = fslot; g.bslot = bslot;
         g.jp_ptr = jp_ptr; g.jp_col = jp_col; g.jpv = jpv;
         g.jpt_ptr = jpt_ptr; g.jpt_row = jpt_row; g.jptv = jptv;
         g.n_bus = S.n_bus; g.tp_bus = tp_bus; g.uth = uth; g.uv = uv;
@@ -166,17 +168,19 @@ rh_status set_device(const rh_grid* g) {
     return RH_OK;
 }
 
-rh_status ensure_ws(rh_grid* g, size_t cols) {
-    if (cols <= g->ws_cols) return RH_OK;
+// V and T hold at least n doubles each
+rh_status ensure_ws_elems(rh_grid* g, size_t n) {
+    if (n <= g->ws_elems) return RH_OK;
     if (g->V) { cudaFree(g->V); g->V = nullptr; }
     if (g->T) { cudaFree(g->T); g->T = nullptr; }
-    g->ws_cols = 0;
-    size_t n = (size_t)g->rows() * cols;
+    g->ws_elems = 0;
     RH_CUDA(cudaMalloc(&g->V, n * sizeof(double)));
     RH_CUDA(cudaMalloc(&g->T, n * sizeof(double)));
-    g->ws_cols = cols;
+    g->ws_elems = n;
     return RH_OK;
 }
+
+rh_status ensure_ws(rh_grid* g, size_t cols) { return ensure_ws_elems(g, (size_t)g->rows() * cols); }
 
 rh_status ensure_stage(rh_grid* g, size_t n) {
     if (n <= g->stage_n) return RH_OK;
@@ -218,6 +222,7 @@ rh_status dirs(rh_grid* g, int N, int64_t ld, double* V, double* T, const double
     L.N = N;
     L.n_cta = rh::dirs_default_ctas(N);
     L.ld = ld;
+    L.cta_stride = 0;
     L.V = V;
     L.T = T;
     L.W = W;
@@ -347,6 +352,21 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     RH_CUDA(g->upload(g->blev_ptr, blev_ptr));
     RH_CUDA(g->upload(g->blev_bus, S.blev_bus));
     RH_CUDA(g->upload(g->blev_maxext, S.blev_maxext));
+    {
+        std::vector<int4> fs(S.n_elim), bs(S.n_elim);
+        for (int t = 0; t < S.n_elim; t++) {
+            int k = S.flev_bus[t], q = S.q0[k];
+            bool two = S.nv[k] == 2;
+            fs[t] = make_int4(q, S.diagpos[q] - S.rowptr[q], S.rowptr[q], two ? S.rowptr[q + 1] : -1);
+            k = S.blev_bus[t];
+            q = S.q0[k];
+            two = S.nv[k] == 2;
+            int ue0 = S.diagpos[q] + (two ? 2 : 1);
+            bs[t] = make_int4(q, S.rowptr[q + 1] - ue0, ue0, two ? S.diagpos[q + 1] + 1 : -1);
+        }
+        RH_CUDA(g->upload(g->fslot, fs));
+        RH_CUDA(g->upload(g->bslot, bs));
+    }
     RH_CUDA(g->upload(g->rf_lev_bus, S.rf_lev_bus));
     RH_CUDA(g->upload(g->rf_tgt_pos, S.rf_tgt_pos));
     RH_CUDA(g->upload(g->rf_tgt_cptr, S.rf_tgt_cptr));
@@ -584,8 +604,6 @@ rh_status rh_hessvec(rh_grid* g, const double* W, int64_t ldw, int32_t N, double
     rh_status st = set_device(g);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    st = ensure_ws(g, (size_t)N);
-    if (st) return st;
     const double* Wd = W;
     double* HWd = HW;
     int64_t lw = ldw, lh = ldhw;
@@ -599,6 +617,8 @@ rh_status rh_hessvec(rh_grid* g, const double* W, int64_t ldw, int32_t N, double
         HWd = g->stage_out;
         lw = lh = S.n_p;
     }
+    st = ensure_ws(g, (size_t)N);
+    if (st) return st;
     st = dirs(g, N, N, g->V, g->T, Wd, lw, 0, HWd, lh,
               rh::PH_WLOAD | rh::PH_SPMUL | rh::PH_L | rh::PH_U | rh::PH_TPROJ | rh::PH_UT | rh::PH_LT |
                   rh::PH_MULADD,
@@ -623,9 +643,6 @@ rh_status rh_hessian(rh_grid* g, int32_t block_n, double* H, int64_t ldh, void* 
     cudaStream_t s = (cudaStream_t)stream;
     int np = S.n_p;
     bool concurrent = (flags & RH_HESSIAN_CONCURRENT) != 0;
-    int width = concurrent ? np : (block_n < np ? block_n : np);
-    st = ensure_ws(g, (size_t)width);
-    if (st) return st;
     bool host = !(flags & RH_DEVICE_PTRS);
     double* Hd = H;
     int64_t lh = ldh;
@@ -637,6 +654,9 @@ rh_status rh_hessian(rh_grid* g, int32_t block_n, double* H, int64_t ldh, void* 
     }
     const unsigned all = rh::PH_WLOAD | rh::PH_SPMUL | rh::PH_L | rh::PH_U | rh::PH_TPROJ | rh::PH_UT | rh::PH_LT |
                          rh::PH_MULADD;
+    int width = concurrent ? np : (block_n < np ? block_n : np);
+    st = ensure_ws(g, (size_t)width);
+    if (st) return st;
     if (concurrent) {
         st = dirs(g, np, np, g->V, g->T, nullptr, 0, 0, Hd, lh, all, s);
         if (st) return st;

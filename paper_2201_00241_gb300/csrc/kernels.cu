@@ -263,6 +263,38 @@ __device__ __forceinline__ int choose_ks(int nb, int D, int maxext) {
     return ks < 2 ? 1 : ks;
 }
 
+// s0 = sum_e v0[e] x[col[e]], s1 = sum_e v1[e] x[col[e]] over e in [e0, e1) of one
+// bus block (two rows sharing their columns when `two`).  Unrolled by 4 with two
+// accumulators per row, so that each lane has four independent loads in flight.
+__device__ __forceinline__ void block_dot(const int* __restrict__ col, const double* __restrict__ vals, int r0, int r1,
+                                          int e0, int e1, const double* X, int64_t ld, int64_t c, bool two,
+                                          double& s0, double& s1) {
+    double p0 = 0.0, q0 = 0.0, p1 = 0.0, q1 = 0.0;
+    int e = e0;
+    for (; e + 4 <= e1; e += 4) {
+        const int i0 = col[r0 + e], i1 = col[r0 + e + 1], i2 = col[r0 + e + 2], i3 = col[r0 + e + 3];
+        const double x0 = X[(int64_t)i0 * ld + c], x1 = X[(int64_t)i1 * ld + c];
+        const double x2 = X[(int64_t)i2 * ld + c], x3 = X[(int64_t)i3 * ld + c];
+        p0 = fma(vals[r0 + e], x0, p0);
+        q0 = fma(vals[r0 + e + 1], x1, q0);
+        p0 = fma(vals[r0 + e + 2], x2, p0);
+        q0 = fma(vals[r0 + e + 3], x3, q0);
+        if (two) {
+            p1 = fma(vals[r1 + e], x0, p1);
+            q1 = fma(vals[r1 + e + 1], x1, q1);
+            p1 = fma(vals[r1 + e + 2], x2, p1);
+            q1 = fma(vals[r1 + e + 3], x3, q1);
+        }
+    }
+    for (; e < e1; e++) {
+        const double xv = X[(int64_t)col[r0 + e] * ld + c];
+        p0 = fma(vals[r0 + e], xv, p0);
+        if (two) p1 = fma(vals[r1 + e], xv, p1);
+    }
+    s0 = p0 + q0;
+    s1 = p1 + q1;
+}
+
 // forward sweep over the L pattern: x_q = (b_q - sum_{c<q} v_qc x_c) [* 1/u_qq]
 template <bool SCALE>
 __device__ __forceinline__ void fwd_finish(const DirGrid& g, const double* __restrict__ vals, double* X, int64_t ld,
@@ -275,67 +307,73 @@ __device__ __forceinline__ void fwd_finish(const DirGrid& g, const double* __res
     }
 }
 
+// One level of a sweep is flattened over (bus, direction) items, or over
+// (bus, k-slice, direction) items when the level is too narrow to give every
+// warp work.  Each bus block is described by one packed slot
+//   forward:  {q, n, rp, rpv}  theta row q, n columns left of the bus, L parts of
+//             the theta row at rp and of the v row at rpv (-1 for a PV bus)
+//   backward: {q, n, ue0, ue1} U parts right of the bus at ue0 / ue1 (-1: PV)
+// so an item needs a single dependent load before its row data; the next
+// item's slot is prefetched while the current one is computed.
 template <bool SCALE>
 __device__ void sweep_fwd(const DirGrid& g, const double* __restrict__ vals, double* X, int64_t ld, int c0, int D,
                           double* part) {
     for (int lev = 0; lev < g.n_flev; lev++) {
         const int b0 = g.flev_ptr[lev], nb = g.flev_ptr[lev + 1] - b0;
+        const int4* __restrict__ slots = g.fslot + b0;
         const int ks = choose_ks(nb, D, g.flev_maxext[lev]);
         if (ks == 1) {
-            for (int it = threadIdx.x; it < nb * D; it += blockDim.x) {
-                int bi = it / D, d = it - bi * D;
-                int k = g.flev_bus[b0 + bi];
-                int q = g.q0[k];
-                bool two = g.nv[k] == 2;
-                int rp = g.rowptr[q], n = g.diagpos[q] - rp;
-                int rpv = two ? g.rowptr[q + 1] : rp;
-                int64_t c = c0 + d;
-                double a0 = X[(int64_t)q * ld + c];
-                double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
-                for (int e = 0; e < n; e++) {
-                    double xv = X[(int64_t)g.col[rp + e] * ld + c];
-                    a0 = fma(-vals[rp + e], xv, a0);
-                    if (two) a1 = fma(-vals[rpv + e], xv, a1);
-                }
+            const int items = nb * D;
+            int it = threadIdx.x;
+            int bi = it / D;
+            int4 nxt = it < items ? slots[bi] : make_int4(0, 0, 0, -1);
+            for (; it < items; it += blockDim.x) {
+                const int4 sl = nxt;
+                const int d = it - bi * D;
+                const int it2 = it + blockDim.x, bi2 = it2 / D;
+                if (it2 < items) nxt = slots[bi2];
+                const int q = sl.x, n = sl.y, rp = sl.z;
+                const bool two = sl.w >= 0;
+                const int rpv = two ? sl.w : rp;
+                const int64_t c = c0 + d;
+                double s0, s1;
+                block_dot(g.col, vals, rp, rpv, 0, n, X, ld, c, two, s0, s1);
+                double a0 = X[(int64_t)q * ld + c] - s0;
+                double a1 = two ? X[(int64_t)(q + 1) * ld + c] - s1 : 0.0;
                 fwd_finish<SCALE>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
+                bi = bi2;
             }
         } else {
             const int per = ks * D;
             for (int it = threadIdx.x; it < nb * per; it += blockDim.x) {
                 int bi = it / per, rem = it - bi * per;
-                int sl = rem / D, d = rem - sl * D;
-                int k = g.flev_bus[b0 + bi];
-                int q = g.q0[k];
-                bool two = g.nv[k] == 2;
-                int rp = g.rowptr[q], n = g.diagpos[q] - rp;
-                int rpv = two ? g.rowptr[q + 1] : rp;
+                int sli = rem / D, d = rem - sli * D;
+                const int4 sl = slots[bi];
+                const int n = sl.y, rp = sl.z;
+                const bool two = sl.w >= 0;
+                const int rpv = two ? sl.w : rp;
                 int64_t c = c0 + d;
-                int e0 = sl * n / ks, e1 = (sl + 1) * n / ks;
-                double a0 = 0.0, a1 = 0.0;
-                for (int e = e0; e < e1; e++) {
-                    double xv = X[(int64_t)g.col[rp + e] * ld + c];
-                    a0 = fma(-vals[rp + e], xv, a0);
-                    if (two) a1 = fma(-vals[rpv + e], xv, a1);
-                }
-                double* pp = part + 2 * ((bi * ks + sl) * D + d);
-                pp[0] = a0;
-                pp[1] = a1;
+                int e0 = sli * n / ks, e1 = (sli + 1) * n / ks;
+                double s0, s1;
+                block_dot(g.col, vals, rp, rpv, e0, e1, X, ld, c, two, s0, s1);
+                double* pp = part + 2 * ((bi * ks + sli) * D + d);
+                pp[0] = s0;
+                pp[1] = s1;
             }
             __syncthreads();
             for (int it = threadIdx.x; it < nb * D; it += blockDim.x) {
                 int bi = it / D, d = it - bi * D;
-                int k = g.flev_bus[b0 + bi];
-                int q = g.q0[k];
-                bool two = g.nv[k] == 2;
-                int rp = g.rowptr[q], n = g.diagpos[q] - rp;
-                int rpv = two ? g.rowptr[q + 1] : rp;
+                const int4 sl = slots[bi];
+                const int q = sl.x, n = sl.y;
+                const bool two = sl.w >= 0;
+                const int rpv = two ? sl.w : sl.z;
                 int64_t c = c0 + d;
                 double a0 = X[(int64_t)q * ld + c];
                 double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
-                for (int sl = 0; sl < ks; sl++) {
-                    const double* pp = part + 2 * ((bi * ks + sl) * D + d);
-                    a0 += pp[0];
-                    a1 += pp[1];
+                for (int k = 0; k < ks; k++) {
+                    const double* pp = part + 2 * ((bi * ks + k) * D + d);
+                    a0 -= pp[0];
+                    a1 -= pp[1];
                 }
                 fwd_finish<SCALE>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
             }
@@ -347,11 +385,11 @@ __device__ void sweep_fwd(const DirGrid& g, const double* __restrict__ vals, dou
 // backward sweep over the U pattern: x_q = (b_q - sum_{c>q} v_qc x_c) [* 1/u_qq]
 template <bool SCALE>
 __device__ __forceinline__ void bwd_finish(const DirGrid& g, const double* __restrict__ vals, double* X, int64_t ld,
-                                           int64_t c, int q, bool two, int dp, double a0, double a1) {
+                                           int64_t c, int q, bool two, int pos_tv, double a0, double a1) {
     if (two) {
         double x1 = SCALE ? a1 * g.invdiag[q + 1] : a1;
         X[(int64_t)(q + 1) * ld + c] = x1;
-        a0 = fma(-vals[dp + 1], x1, a0);
+        a0 = fma(-vals[pos_tv], x1, a0);
     }
     X[(int64_t)q * ld + c] = SCALE ? a0 * g.invdiag[q] : a0;
 }
@@ -361,67 +399,61 @@ __device__ void sweep_bwd(const DirGrid& g, const double* __restrict__ vals, dou
                           double* part) {
     for (int lev = 0; lev < g.n_blev; lev++) {
         const int b0 = g.blev_ptr[lev], nb = g.blev_ptr[lev + 1] - b0;
+        const int4* __restrict__ slots = g.bslot + b0;
         const int ks = choose_ks(nb, D, g.blev_maxext[lev]);
         if (ks == 1) {
-            for (int it = threadIdx.x; it < nb * D; it += blockDim.x) {
-                int bi = it / D, d = it - bi * D;
-                int k = g.blev_bus[b0 + bi];
-                int q = g.q0[k];
-                bool two = g.nv[k] == 2;
-                int dp = g.diagpos[q];
-                int ue0 = dp + (two ? 2 : 1);
-                int n = g.rowptr[q + 1] - ue0;
-                int ue1 = two ? g.diagpos[q + 1] + 1 : ue0;
-                int64_t c = c0 + d;
-                double a0 = X[(int64_t)q * ld + c];
-                double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
-                for (int e = 0; e < n; e++) {
-                    double xv = X[(int64_t)g.col[ue0 + e] * ld + c];
-                    a0 = fma(-vals[ue0 + e], xv, a0);
-                    if (two) a1 = fma(-vals[ue1 + e], xv, a1);
-                }
-                bwd_finish<SCALE>(g, vals, X, ld, c, q, two, dp, a0, a1);
+            const int items = nb * D;
+            int it = threadIdx.x;
+            int bi = it / D;
+            int4 nxt = it < items ? slots[bi] : make_int4(0, 0, 0, -1);
+            for (; it < items; it += blockDim.x) {
+                const int4 sl = nxt;
+                const int d = it - bi * D;
+                const int it2 = it + blockDim.x, bi2 = it2 / D;
+                if (it2 < items) nxt = slots[bi2];
+                const int q = sl.x, n = sl.y, ue0 = sl.z;
+                const bool two = sl.w >= 0;
+                const int ue1 = two ? sl.w : ue0;
+                const int64_t c = c0 + d;
+                double s0, s1;
+                block_dot(g.col, vals, ue0, ue1, 0, n, X, ld, c, two, s0, s1);
+                double a0 = X[(int64_t)q * ld + c] - s0;
+                double a1 = two ? X[(int64_t)(q + 1) * ld + c] - s1 : 0.0;
+                bwd_finish<SCALE>(g, vals, X, ld, c, q, two, ue0 - 1, a0, a1);
+                bi = bi2;
             }
         } else {
             const int per = ks * D;
             for (int it = threadIdx.x; it < nb * per; it += blockDim.x) {
                 int bi = it / per, rem = it - bi * per;
-                int sl = rem / D, d = rem - sl * D;
-                int k = g.blev_bus[b0 + bi];
-                int q = g.q0[k];
-                bool two = g.nv[k] == 2;
-                int dp = g.diagpos[q];
-                int ue0 = dp + (two ? 2 : 1);
-                int n = g.rowptr[q + 1] - ue0;
-                int ue1 = two ? g.diagpos[q + 1] + 1 : ue0;
+                int sli = rem / D, d = rem - sli * D;
+                const int4 sl = slots[bi];
+                const int n = sl.y, ue0 = sl.z;
+                const bool two = sl.w >= 0;
+                const int ue1 = two ? sl.w : ue0;
                 int64_t c = c0 + d;
-                int e0 = sl * n / ks, e1 = (sl + 1) * n / ks;
-                double a0 = 0.0, a1 = 0.0;
-                for (int e = e0; e < e1; e++) {
-                    double xv = X[(int64_t)g.col[ue0 + e] * ld + c];
-                    a0 = fma(-vals[ue0 + e], xv, a0);
-                    if (two) a1 = fma(-vals[ue1 + e], xv, a1);
-                }
-                double* pp = part + 2 * ((bi * ks + sl) * D + d);
-                pp[0] = a0;
-                pp[1] = a1;
+                int e0 = sli * n / ks, e1 = (sli + 1) * n / ks;
+                double s0, s1;
+                block_dot(g.col, vals, ue0, ue1, e0, e1, X, ld, c, two, s0, s1);
+                double* pp = part + 2 * ((bi * ks + sli) * D + d);
+                pp[0] = s0;
+                pp[1] = s1;
             }
             __syncthreads();
             for (int it = threadIdx.x; it < nb * D; it += blockDim.x) {
                 int bi = it / D, d = it - bi * D;
-                int k = g.blev_bus[b0 + bi];
-                int q = g.q0[k];
-                bool two = g.nv[k] == 2;
-                int dp = g.diagpos[q];
+                const int4 sl = slots[bi];
+                const int q = sl.x;
+                const bool two = sl.w >= 0;
                 int64_t c = c0 + d;
                 double a0 = X[(int64_t)q * ld + c];
                 double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
-                for (int sl = 0; sl < ks; sl++) {
-                    const double* pp = part + 2 * ((bi * ks + sl) * D + d);
-                    a0 += pp[0];
-                    a1 += pp[1];
+                for (int k = 0; k < ks; k++) {
+                    const double* pp = part + 2 * ((bi * ks + k) * D + d);
+                    a0 -= pp[0];
+                    a1 -= pp[1];
                 }
-                bwd_finish<SCALE>(g, vals, X, ld, c, q, two, dp, a0, a1);
+                bwd_finish<SCALE>(g, vals, X, ld, c, q, two, sl.z - 1, a0, a1);
             }
         }
         __syncthreads();
@@ -450,15 +482,34 @@ __device__ void tproj(const DirGrid& g, const double* V, double* T, int64_t ld, 
         double ab = g.asum[b];
         double yv = fma(g.d2[b], dv, ab * dth);
         double yth = fma(ab, dv, g.csum[b] * dth);
-        for (int e = g.inc_ptr[b]; e < g.inc_ptr[b + 1]; e++) {
-            double4_32a cf = g.inc_coef[e];
-            double dthj = V[(int64_t)g.inc_uth[e] * ld + c];
-            double dvj = V[(int64_t)g.inc_uv[e] * ld + c];
+        int e = g.inc_ptr[b];
+        const int e1 = g.inc_ptr[b + 1];
+        double yv2 = 0.0, yth2 = 0.0;
+        for (; e + 2 <= e1; e += 2) {
+            const int t0 = g.inc_uth[e], v0 = g.inc_uv[e], t1 = g.inc_uth[e + 1], v1 = g.inc_uv[e + 1];
+            const double dthj0 = V[(int64_t)t0 * ld + c], dvj0 = V[(int64_t)v0 * ld + c];
+            const double dthj1 = V[(int64_t)t1 * ld + c], dvj1 = V[(int64_t)v1 * ld + c];
+            const double4_32a cf0 = g.inc_coef[e], cf1 = g.inc_coef[e + 1];
+            yv = fma(cf0.x, dvj0, yv);
+            yv = fma(cf0.y, dthj0, yv);
+            yth = fma(cf0.z, dvj0, yth);
+            yth = fma(cf0.w, dthj0, yth);
+            yv2 = fma(cf1.x, dvj1, yv2);
+            yv2 = fma(cf1.y, dthj1, yv2);
+            yth2 = fma(cf1.z, dvj1, yth2);
+            yth2 = fma(cf1.w, dthj1, yth2);
+        }
+        if (e < e1) {
+            const double4_32a cf = g.inc_coef[e];
+            const double dthj = V[(int64_t)g.inc_uth[e] * ld + c];
+            const double dvj = V[(int64_t)g.inc_uv[e] * ld + c];
             yv = fma(cf.x, dvj, yv);
             yv = fma(cf.y, dthj, yv);
             yth = fma(cf.z, dvj, yth);
             yth = fma(cf.w, dthj, yth);
         }
+        yv += yv2;
+        yth += yth2;
         if (g.has_gref[b]) {
             yv = fma(sref[d], g.gref_v[b], yv);
             yth = fma(sref[d], g.gref_th[b], yth);
@@ -478,46 +529,46 @@ __global__ void __launch_bounds__(kDirThreads, 2) k_dirs(DirGrid g, DirLaunch L)
     const int c1 = (int)((int64_t)(cta + 1) * L.N / L.n_cta);
     const int D = c1 - c0;
     if (D <= 0) return;
+    // this CTA's directions: row r, local direction d at base[r * ld + d]
     const int64_t ld = L.ld;
-    double* V = L.V;
-    double* T = L.T;
+    const int64_t base = L.cta_stride ? (int64_t)cta * L.cta_stride : (int64_t)c0;
+    double* V = L.V + base;
+    double* T = L.T + base;
     if (L.phases & PH_WLOAD) {
         for (int it = threadIdx.x; it < g.n_p * D; it += blockDim.x) {
             int k = it / D, d = it - k * D;
             int64_t c = c0 + d;
             double w = L.W ? L.W[c * L.ldw + k] : (k == L.col0 + c ? 1.0 : 0.0);
-            V[(int64_t)(g.n_x + k) * ld + c] = w;
+            V[(int64_t)(g.n_x + k) * ld + d] = w;
         }
-        for (int d = threadIdx.x; d < D; d += blockDim.x) V[(int64_t)g.zero_row * ld + c0 + d] = 0.0;
+        for (int d = threadIdx.x; d < D; d += blockDim.x) V[(int64_t)g.zero_row * ld + d] = 0.0;
         __syncthreads();
     }
     if (L.phases & PH_SPMUL) {
         for (int it = threadIdx.x; it < g.n_x * D; it += blockDim.x) {
             int q = it / D, d = it - q * D;
-            int64_t c = c0 + d;
             double s = 0.0;
             for (int t = g.jp_ptr[q]; t < g.jp_ptr[q + 1]; t++)
-                s = fma(g.jpv[t], V[(int64_t)(g.n_x + g.jp_col[t]) * ld + c], s);
-            V[(int64_t)q * ld + c] = -s;
+                s = fma(g.jpv[t], V[(int64_t)(g.n_x + g.jp_col[t]) * ld + d], s);
+            V[(int64_t)q * ld + d] = -s;
         }
         __syncthreads();
     }
-    if (L.phases & PH_L) sweep_fwd<false>(g, g.A, V, ld, c0, D, part);
-    if (L.phases & PH_U) sweep_bwd<true>(g, g.A, V, ld, c0, D, part);
+    if (L.phases & PH_L) sweep_fwd<false>(g, g.A, V, ld, 0, D, part);
+    if (L.phases & PH_U) sweep_bwd<true>(g, g.A, V, ld, 0, D, part);
     if (L.phases & PH_TPROJ) {
-        tproj(g, V, T, ld, c0, D, sref);
+        tproj(g, V, T, ld, 0, D, sref);
         __syncthreads();
     }
-    if (L.phases & PH_UT) sweep_fwd<true>(g, g.At, T, ld, c0, D, part);
-    if (L.phases & PH_LT) sweep_bwd<false>(g, g.At, T, ld, c0, D, part);
+    if (L.phases & PH_UT) sweep_fwd<true>(g, g.At, T, ld, 0, D, part);
+    if (L.phases & PH_LT) sweep_bwd<false>(g, g.At, T, ld, 0, D, part);
     if (L.phases & PH_MULADD) {
         for (int it = threadIdx.x; it < g.n_p * D; it += blockDim.x) {
             int k = it / D, d = it - k * D;
-            int64_t c = c0 + d;
-            double h = T[(int64_t)(g.n_x + k) * ld + c];
+            double h = T[(int64_t)(g.n_x + k) * ld + d];
             for (int t = g.jpt_ptr[k]; t < g.jpt_ptr[k + 1]; t++)
-                h = fma(g.jptv[t], T[(int64_t)g.jpt_row[t] * ld + c], h);
-            L.HW[c * L.ldhw + k] = h;
+                h = fma(g.jptv[t], T[(int64_t)g.jpt_row[t] * ld + d], h);
+            L.HW[(int64_t)(c0 + d) * L.ldhw + k] = h;
         }
     }
 }

@@ -31,6 +31,7 @@ struct DirGrid {
     int n_flev, n_blev;
     const int *flev_ptr, *flev_bus, *flev_maxext;
     const int *blev_ptr, *blev_bus, *blev_maxext;
+    const int4 *fslot, *bslot;                 // packed bus-block descriptors in level order
     // J_p by internal rows and by p index
     const int *jp_ptr, *jp_col;
     const double *jpv;
@@ -56,7 +57,11 @@ struct DirGrid {
 struct DirLaunch {
     int N;                     // directions in this launch
     int n_cta;                 // CTAs; CTA c owns directions [c*N/n_cta, (c+1)*N/n_cta)
-    int64_t ld;                // row stride of V and T (>= N)
+    // Layout of V and T: element (row r, direction c0 + d) of CTA c is at
+    //   cta_stride > 0 (panel-major): c * cta_stride + r * ld + d   (each CTA's panel contiguous)
+    //   cta_stride = 0 (interleaved):  r * ld + c0 + d              (ld >= N)
+    int64_t ld;
+    int64_t cta_stride;
     double *V, *T;             // tangent buffer; buffer of the transposed sweeps / projection
     const double *W;           // n_p x N column-major (ldw), or NULL for identity columns
     int64_t ldw;

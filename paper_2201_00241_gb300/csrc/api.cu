@@ -3,6 +3,7 @@
 // Host code only: argument checks, device memory, the Newton and setup
 // sequencing, copies for host-pointer calls.  Every numerical step runs in the
 // kernels of kernels.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -57,6 +58,15 @@ struct rh_grid {
     uint8_t* nv = nullptr;
     int *flev_ptr = nullptr, *flev_bus = nullptr, *flev_maxext = nullptr;
     int4 *fslot = nullptr, *bslot = nullptr;
+    // sparse-part schedules and the tail's external phase (device), with host level pointers
+    int *sf_ptr = nullptr, *sf_maxext = nullptr, *sb_ptr = nullptr, *sb_maxext = nullptr;
+    int *ef_ptr = nullptr, *ef_maxext = nullptr;
+    int4 *sf_slot = nullptr, *sb_slot = nullptr, *ef_slot = nullptr;
+    int n_sf = 0, n_sb = 0, n_ef = 0;
+    int* tail_pos = nullptr;
+    int *jp_rows = nullptr, *jp_zero_rows = nullptr;
+    int n_jp_rows = 0, n_jp_zero = 0;
+    double *triL = nullptr, *triU = nullptr, *triUt = nullptr, *triLt = nullptr;
     int *blev_ptr = nullptr, *blev_bus = nullptr, *blev_maxext = nullptr;
     int *rf_lev_bus = nullptr, *rf_tgt_pos = nullptr, *rf_c_l = nullptr, *rf_c_u = nullptr;
     int64_t* rf_tgt_cptr = nullptr;
@@ -88,8 +98,10 @@ struct rh_grid {
     size_t stage_n = 0;
 
     bool adjoint_ready = false;
+    cudaGraphExec_t adj_exec = nullptr;   // captured device work of rh_adjoint
 
     ~rh_grid() {
+        if (adj_exec) cudaGraphExecDestroy(adj_exec);
         for (void* p : allocs) cudaFree(p);
         if (V) cudaFree(V);
         if (T) cudaFree(T);
@@ -133,13 +145,16 @@ struct rh_grid {
     rh::DirGrid dir() const {
         rh::DirGrid g;
         g.n_x = S.n_x; g.n_p = S.n_p; g.zero_row = S.n_x + S.n_p;
-        g.rowptr = rowptr; g.col = col; g.diagpos = diagpos; g.A = A; g.At = At; g.invdiag = invdiag;
-        g.q0 = q0; g.nv = nv;
-        g.n_flev = S.n_flev; g.n_blev = S.n_blev;
-        g.flev_ptr = flev_ptr; g.flev_bus = flev_bus; g.flev_maxext = flev_maxext;
-        g.blev_ptr = blev_ptr; g.blev_bus = blev_bus; g.blev_maxext = blev_maxext;
-        g.fslot = fslot; g.bslot = bslot;
+        g.col = col; g.A = A; g.At = At; g.invdiag = invdiag;
+        g.lf = {S.n_flev, flev_ptr, fslot, flev_maxext};
+        g.lb = {S.n_blev, blev_ptr, bslot, blev_maxext};
+        g.sf = {n_sf, sf_ptr, sf_slot, sf_maxext};
+        g.sb = {n_sb, sb_ptr, sb_slot, sb_maxext};
+        g.ef = {n_ef, ef_ptr, ef_slot, ef_maxext};
+        g.t0 = S.t0; g.T = S.n_x - S.t0;
+        g.triL = triL; g.triU = triU; g.triUt = triUt; g.triLt = triLt;
         g.jp_ptr = jp_ptr; g.jp_col = jp_col; g.jpv = jpv;
+        g.n_jp_rows = n_jp_rows; g.n_jp_zero = n_jp_zero; g.jp_rows = jp_rows; g.jp_zero_rows = jp_zero_rows;
         g.jpt_ptr = jpt_ptr; g.jpt_row = jpt_row; g.jptv = jptv;
         g.n_bus = S.n_bus; g.tp_bus = tp_bus; g.uth = uth; g.uv = uv;
         g.inc_ptr = inc_ptr; g.inc_uth = inc_uth; g.inc_uv = inc_uv; g.inc_coef = inc_coef;
@@ -201,8 +216,8 @@ rh_status check_err_flag(rh_grid* g) {
     return RH_OK;
 }
 
-// J_x, J_p at the current state, refactorisation, transposed copies.
-rh_status assemble_and_factor(rh_grid* g) {
+// J_x, J_p at the current state, refactorisation, transposed copies (enqueue only).
+rh_status enqueue_factor(rh_grid* g) {
     const auto& S = g->S;
     cudaStream_t s = g->stream;
     RH_CUDA(cudaMemsetAsync(g->A, 0, sizeof(double) * S.col.size(), s));
@@ -212,7 +227,14 @@ rh_status assemble_and_factor(rh_grid* g) {
     RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_tgt_lev_ptr.data(), S.rf_n_lev, s));
     rh::launch_transpose_values((int)S.col.size(), g->tpos, g->A, g->At, (int)S.jp_col.size(), g->jpt_src, g->jpv,
                                 g->jptv, s);
+    rh::launch_build_tail(S.n_x - S.t0, S.t0, g->tail_pos, g->A, g->invdiag, g->triL, g->triU, g->triUt, g->triLt, s);
     RH_CUDA(cudaGetLastError());
+    return RH_OK;
+}
+
+rh_status assemble_and_factor(rh_grid* g) {
+    rh_status st = enqueue_factor(g);
+    if (st) return st;
     return check_err_flag(g);
 }
 
@@ -231,6 +253,7 @@ rh_status dirs(rh_grid* g, int N, int64_t ld, double* V, double* T, const double
     L.HW = HW;
     L.ldhw = ldhw;
     L.phases = phases;
+    L.use_tail = rh::dirs_tail_fits(g->S.n_x - g->S.t0, N, L.n_cta) ? 1 : 0;
     rh::launch_dirs(g->dir(), L, s);
     RH_CUDA(cudaGetLastError());
     return RH_OK;
@@ -292,6 +315,7 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     }
     RH_CUDA(cudaSetDevice(device));
     RH_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+    RH_CUDA(rh::prepare_kernels());
     int nb = S.n_bus, nx = S.n_x, np = S.n_p;
     int zero_row = nx + np;
 
@@ -366,6 +390,67 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
         }
         RH_CUDA(g->upload(g->fslot, fs));
         RH_CUDA(g->upload(g->bslot, bs));
+        // schedules restricted to the sparse part (buses before the dense tail)
+        auto restrict_set = [&](const std::vector<int>& order, const std::vector<int>& lev, const std::vector<int4>& src,
+                                std::vector<int>& ptr, std::vector<int4>& sl, std::vector<int>& mx) {
+            ptr.assign(1, 0);
+            int cur = -1;
+            for (int t = 0; t < S.n_elim; t++) {
+                int k = order[t];
+                if (k >= S.tail_bus0) continue;
+                if (lev[k] != cur) {
+                    if (cur >= 0) ptr.push_back((int)sl.size());
+                    cur = lev[k];
+                    mx.push_back(0);
+                }
+                sl.push_back(src[t]);
+                mx.back() = std::max(mx.back(), src[t].y);
+            }
+            if (cur >= 0) ptr.push_back((int)sl.size());
+        };
+        std::vector<int> sfp, sbp, sfm, sbm;
+        std::vector<int4> sfs, sbs;
+        restrict_set(S.flev_bus, S.flevel, fs, sfp, sfs, sfm);
+        restrict_set(S.blev_bus, S.blevel, bs, sbp, sbs, sbm);
+        g->n_sf = (int)sfp.size() - 1;
+        g->n_sb = (int)sbp.size() - 1;
+        // the tail's external phase: one level of tail buses, columns left of t0 only
+        std::vector<int> efp(1, 0), efm;
+        std::vector<int4> efs;
+        for (int k = S.tail_bus0; k < S.n_elim; k++) {
+            int q = S.q0[k];
+            int n = 0;
+            for (int t = S.rowptr[q]; t < S.diagpos[q] && S.col[t] < S.t0; t++) n++;
+            efs.push_back(make_int4(q, n, S.rowptr[q], S.nv[k] == 2 ? S.rowptr[q + 1] : -1));
+        }
+        if (!efs.empty()) {
+            efp.push_back((int)efs.size());
+            int m = 0;
+            for (auto& e : efs) m = std::max(m, e.y);
+            efm.push_back(m);
+        }
+        g->n_ef = (int)efp.size() - 1;
+        RH_CUDA(g->upload(g->sf_ptr, sfp));
+        RH_CUDA(g->upload(g->sf_slot, sfs));
+        RH_CUDA(g->upload(g->sf_maxext, sfm));
+        RH_CUDA(g->upload(g->sb_ptr, sbp));
+        RH_CUDA(g->upload(g->sb_slot, sbs));
+        RH_CUDA(g->upload(g->sb_maxext, sbm));
+        RH_CUDA(g->upload(g->ef_ptr, efp));
+        RH_CUDA(g->upload(g->ef_slot, efs));
+        RH_CUDA(g->upload(g->ef_maxext, efm));
+        // dense tail: position of (t0 + i, t0 + j) in A, -1 where structurally zero
+        int T = S.n_x - S.t0;
+        std::vector<int> tp((size_t)T * T, -1);
+        for (int i = 0; i < T; i++)
+            for (int t = S.rowptr[S.t0 + i]; t < S.rowptr[S.t0 + i + 1]; t++)
+                if (S.col[t] >= S.t0) tp[(size_t)i * T + (S.col[t] - S.t0)] = t;
+        RH_CUDA(g->upload(g->tail_pos, tp));
+        size_t ntri = T > 1 ? (size_t)T * (T - 1) / 2 : 1;
+        RH_CUDA(g->alloc(g->triL, ntri));
+        RH_CUDA(g->alloc(g->triU, ntri));
+        RH_CUDA(g->alloc(g->triUt, ntri));
+        RH_CUDA(g->alloc(g->triLt, ntri));
     }
     RH_CUDA(g->upload(g->rf_lev_bus, S.rf_lev_bus));
     RH_CUDA(g->upload(g->rf_tgt_pos, S.rf_tgt_pos));
@@ -373,6 +458,14 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     RH_CUDA(g->upload(g->rf_c_l, S.rf_c_l));
     RH_CUDA(g->upload(g->rf_c_u, S.rf_c_u));
     RH_CUDA(g->upload(g->jp_ptr, S.jp_ptr));
+    {
+        std::vector<int> rows, zero;
+        for (int q = 0; q < nx; q++) (S.jp_ptr[q + 1] > S.jp_ptr[q] ? rows : zero).push_back(q);
+        g->n_jp_rows = (int)rows.size();
+        g->n_jp_zero = (int)zero.size();
+        RH_CUDA(g->upload(g->jp_rows, rows));
+        RH_CUDA(g->upload(g->jp_zero_rows, zero));
+    }
     RH_CUDA(g->upload(g->jp_col, S.jp_col));
     RH_CUDA(g->upload(g->jpt_ptr, S.jpt_ptr));
     RH_CUDA(g->upload(g->jpt_row, S.jpt_row));
@@ -558,16 +651,13 @@ rh_status rh_refactor(rh_grid* g, double* A_out) {
     return RH_OK;
 }
 
-rh_status rh_adjoint(rh_grid* g, double* F, double* lambda, double* grad) {
-    if (!g) return fail(RH_EINVAL, "NULL grid");
-    rh_status st = set_device(g);
-    if (st) return st;
+// Device work of rh_adjoint: a1 (Jacobian), a2 (refactor), a3 (adjoint, gradient,
+// projection coefficients).  Enqueue only; captured once per grid into a graph.
+rh_status enqueue_adjoint(rh_grid* g) {
     const auto& S = g->S;
     cudaStream_t s = g->stream;
-    g->adjoint_ready = false;
-    st = assemble_and_factor(g);
+    rh_status st = enqueue_factor(g);
     if (st) return st;
-    // lambda = -J_x^{-T} grad_x f
     RH_CUDA(cudaMemsetAsync(g->v1, 0, sizeof(double) * g->rows(), s));
     rh::AdjData a;
     a.rhs = g->v1; a.cref = g->dscal; a.c2ref = g->dscal + 1; a.F = g->dscal + 2;
@@ -582,13 +672,36 @@ rh_status rh_adjoint(rh_grid* g, double* F, double* lambda, double* grad) {
     rh::launch_gradient(g->pf(), g->st(), S.n_p, g->jpt_ptr, g->jpt_row, g->jptv, g->lam, g->dscal, g->gref_v,
                         g->grad, s);
     RH_CUDA(cudaGetLastError());
+    return RH_OK;
+}
+
+rh_status rh_adjoint(rh_grid* g, double* F, double* lambda, double* grad) {
+    if (!g) return fail(RH_EINVAL, "NULL grid");
+    rh_status st = set_device(g);
+    if (st) return st;
+    const auto& S = g->S;
+    cudaStream_t s = g->stream;
+    g->adjoint_ready = false;
+    if (!g->adj_exec) {
+        cudaGraph_t graph = nullptr;
+        RH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        st = enqueue_adjoint(g);
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (st) { if (graph) cudaGraphDestroy(graph); return st; }
+        if (ce != cudaSuccess) return fail(RH_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&g->adj_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) { g->adj_exec = nullptr; return fail(RH_ECUDA, std::string("graph: ") + cudaGetErrorString(ce)); }
+    }
+    RH_CUDA(cudaGraphLaunch(g->adj_exec, s));
     if (lambda) {
         rh::launch_gather_rows(S.n_x, 1, g->xmap, g->lam, 1, g->xbuf, S.n_x, 1.0, S.n_x, s);
         RH_CUDA(cudaMemcpyAsync(lambda, g->xbuf, S.n_x * sizeof(double), cudaMemcpyDeviceToHost, s));
     }
     if (grad) RH_CUDA(cudaMemcpyAsync(grad, g->grad, S.n_p * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (F) RH_CUDA(cudaMemcpyAsync(F, g->dscal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
-    RH_CUDA(cudaStreamSynchronize(s));
+    st = check_err_flag(g);   // synchronises the stream
+    if (st) return st;
     g->adjoint_ready = true;
     return RH_OK;
 }

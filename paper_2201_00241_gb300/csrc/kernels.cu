@@ -248,6 +248,28 @@ __global__ void k_transpose_values(int nnz, const int* __restrict__ tpos, const 
     if (i < nnz_jp) jptv[i] = jpv[jpt_src[i]];
 }
 
+// The four packed triangles of the dense tail for the sweeps, one thread per
+// (i, j) of the T x T block; pos maps (i, j) to A (-1: structurally zero).
+__global__ void k_build_tail(int T, int t0, const int* __restrict__ pos, const double* __restrict__ A,
+                             const double* __restrict__ invdiag, double* triL, double* triU, double* triUt,
+                             double* triLt) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= T * T) return;
+    int i = idx / T, j = idx - i * T;
+    if (i == j) return;
+    int pij = pos[idx], pji = pos[j * T + i];
+    double aij = pij >= 0 ? A[pij] : 0.0, aji = pji >= 0 ? A[pji] : 0.0;
+    if (i > j) {
+        int o = j * (T - 1) - j * (j - 1) / 2 + (i - j - 1);
+        triL[o] = aij;                              // L_ij
+        triUt[o] = aji * invdiag[t0 + j];           // (U^T)_ij = U_ji, scaled by 1/u_jj
+    } else {
+        int o = j * (j - 1) / 2 + i;
+        triU[o] = aij * invdiag[t0 + j];            // U_ij scaled by 1/u_jj
+        triLt[o] = aji;                             // (L^T)_ij = L_ji
+    }
+}
+
 // ---------------------------------------------------------------------------
 // the direction kernel: Algorithm 2 for a slice of directions per CTA
 // ---------------------------------------------------------------------------
@@ -315,13 +337,14 @@ __device__ __forceinline__ void fwd_finish(const DirGrid& g, const double* __res
 //   backward: {q, n, ue0, ue1} U parts right of the bus at ue0 / ue1 (-1: PV)
 // so an item needs a single dependent load before its row data; the next
 // item's slot is prefetched while the current one is computed.
-template <bool SCALE>
-__device__ void sweep_fwd(const DirGrid& g, const double* __restrict__ vals, double* X, int64_t ld, int c0, int D,
-                          double* part) {
-    for (int lev = 0; lev < g.n_flev; lev++) {
-        const int b0 = g.flev_ptr[lev], nb = g.flev_ptr[lev + 1] - b0;
-        const int4* __restrict__ slots = g.fslot + b0;
-        const int ks = choose_ks(nb, D, g.flev_maxext[lev]);
+// EXT: subtract the row parts only (the dense tail's external phase), no finish.
+template <bool SCALE, bool EXT = false>
+__device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __restrict__ vals, double* X,
+                          int64_t ld, int c0, int D, double* part) {
+    for (int lev = 0; lev < ls.n_lev; lev++) {
+        const int b0 = ls.ptr[lev], nb = ls.ptr[lev + 1] - b0;
+        const int4* __restrict__ slots = ls.slots + b0;
+        const int ks = choose_ks(nb, D, ls.maxext[lev]);
         if (ks == 1) {
             const int items = nb * D;
             int it = threadIdx.x;
@@ -340,7 +363,12 @@ __device__ void sweep_fwd(const DirGrid& g, const double* __restrict__ vals, dou
                 block_dot(g.col, vals, rp, rpv, 0, n, X, ld, c, two, s0, s1);
                 double a0 = X[(int64_t)q * ld + c] - s0;
                 double a1 = two ? X[(int64_t)(q + 1) * ld + c] - s1 : 0.0;
-                fwd_finish<SCALE>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
+                if (EXT) {
+                    X[(int64_t)q * ld + c] = a0;
+                    if (two) X[(int64_t)(q + 1) * ld + c] = a1;
+                } else {
+                    fwd_finish<SCALE>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
+                }
                 bi = bi2;
             }
         } else {
@@ -375,7 +403,12 @@ __device__ void sweep_fwd(const DirGrid& g, const double* __restrict__ vals, dou
                     a0 -= pp[0];
                     a1 -= pp[1];
                 }
-                fwd_finish<SCALE>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
+                if (EXT) {
+                    X[(int64_t)q * ld + c] = a0;
+                    if (two) X[(int64_t)(q + 1) * ld + c] = a1;
+                } else {
+                    fwd_finish<SCALE>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
+                }
             }
         }
         __syncthreads();
@@ -395,12 +428,12 @@ __device__ __forceinline__ void bwd_finish(const DirGrid& g, const double* __res
 }
 
 template <bool SCALE>
-__device__ void sweep_bwd(const DirGrid& g, const double* __restrict__ vals, double* X, int64_t ld, int c0, int D,
-                          double* part) {
-    for (int lev = 0; lev < g.n_blev; lev++) {
-        const int b0 = g.blev_ptr[lev], nb = g.blev_ptr[lev + 1] - b0;
-        const int4* __restrict__ slots = g.bslot + b0;
-        const int ks = choose_ks(nb, D, g.blev_maxext[lev]);
+__device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __restrict__ vals, double* X,
+                          int64_t ld, int c0, int D, double* part) {
+    for (int lev = 0; lev < ls.n_lev; lev++) {
+        const int b0 = ls.ptr[lev], nb = ls.ptr[lev + 1] - b0;
+        const int4* __restrict__ slots = ls.slots + b0;
+        const int ks = choose_ks(nb, D, ls.maxext[lev]);
         if (ks == 1) {
             const int items = nb * D;
             int it = threadIdx.x;
@@ -458,6 +491,70 @@ __device__ void sweep_bwd(const DirGrid& g, const double* __restrict__ vals, dou
         }
         __syncthreads();
     }
+}
+
+// Dense trailing block [t0, t0 + T) of a sweep, column-oriented in shared memory.
+// xt[i * D + d] holds row t0 + i of the CTA's directions; tri is the packed
+// strictly-triangular block (column j contiguous), columns pre-scaled by 1/u_jj
+// for the scaled sweeps, so each column step is y_i -= tri_ij y_j and the
+// result is x_i = y_i [* 1/u_ii].  One barrier per column.
+__device__ __forceinline__ int lpack_off(int j, int T) { return j * (T - 1) - j * (j - 1) / 2; }  // rows j+1..T-1
+__device__ __forceinline__ int upack_off(int j) { return j * (j - 1) / 2; }                      // rows 0..j-1
+
+template <bool SCALE>
+__device__ void tail_fwd(const DirGrid& g, const double* __restrict__ tri_g, double* X, int64_t ld, int c0, int D,
+                         double* xt, double* tri) {
+    const int T = g.T, t0 = g.t0;
+    const int ntri = T * (T - 1) / 2;
+    for (int i = threadIdx.x; i < ntri; i += blockDim.x) tri[i] = tri_g[i];
+    for (int it = threadIdx.x; it < T * D; it += blockDim.x) {
+        int i = it / D, d = it - i * D;
+        xt[it] = X[(int64_t)(t0 + i) * ld + c0 + d];
+    }
+    __syncthreads();
+    for (int j = 0; j < T - 1; j++) {
+        const double* colj = tri + lpack_off(j, T) - (j + 1);
+        const int n = (T - 1 - j) * D;
+        for (int it = threadIdx.x; it < n; it += blockDim.x) {
+            int i = j + 1 + it / D, d = it % D;
+            xt[i * D + d] = fma(-colj[i], xt[j * D + d], xt[i * D + d]);
+        }
+        __syncthreads();
+    }
+    for (int it = threadIdx.x; it < T * D; it += blockDim.x) {
+        int i = it / D, d = it - i * D;
+        double v = xt[it];
+        X[(int64_t)(t0 + i) * ld + c0 + d] = SCALE ? v * g.invdiag[t0 + i] : v;
+    }
+    __syncthreads();
+}
+
+template <bool SCALE>
+__device__ void tail_bwd(const DirGrid& g, const double* __restrict__ tri_g, double* X, int64_t ld, int c0, int D,
+                         double* xt, double* tri) {
+    const int T = g.T, t0 = g.t0;
+    const int ntri = T * (T - 1) / 2;
+    for (int i = threadIdx.x; i < ntri; i += blockDim.x) tri[i] = tri_g[i];
+    for (int it = threadIdx.x; it < T * D; it += blockDim.x) {
+        int i = it / D, d = it - i * D;
+        xt[it] = X[(int64_t)(t0 + i) * ld + c0 + d];
+    }
+    __syncthreads();
+    for (int j = T - 1; j > 0; j--) {
+        const double* colj = tri + upack_off(j);
+        const int n = j * D;
+        for (int it = threadIdx.x; it < n; it += blockDim.x) {
+            int i = it / D, d = it - i * D;
+            xt[i * D + d] = fma(-colj[i], xt[j * D + d], xt[i * D + d]);
+        }
+        __syncthreads();
+    }
+    for (int it = threadIdx.x; it < T * D; it += blockDim.x) {
+        int i = it / D, d = it - i * D;
+        double v = xt[it];
+        X[(int64_t)(t0 + i) * ld + c0 + d] = SCALE ? v * g.invdiag[t0 + i] : v;
+    }
+    __syncthreads();
 }
 
 // Projection (eq. 11/13): y = [lambda^T Hess g + Hess f] v for v = (z, w).
@@ -545,8 +642,14 @@ __global__ void __launch_bounds__(kDirThreads, 2) k_dirs(DirGrid g, DirLaunch L)
         __syncthreads();
     }
     if (L.phases & PH_SPMUL) {
-        for (int it = threadIdx.x; it < g.n_x * D; it += blockDim.x) {
-            int q = it / D, d = it - q * D;
+        // rows of J_p without entries: -B is zero there (stores only, no loads)
+        for (int it = threadIdx.x; it < g.n_jp_zero * D; it += blockDim.x) {
+            int r = it / D, d = it - r * D;
+            V[(int64_t)g.jp_zero_rows[r] * ld + d] = 0.0;
+        }
+        for (int it = threadIdx.x; it < g.n_jp_rows * D; it += blockDim.x) {
+            int r = it / D, d = it - r * D;
+            const int q = g.jp_rows[r];
             double s = 0.0;
             for (int t = g.jp_ptr[q]; t < g.jp_ptr[q + 1]; t++)
                 s = fma(g.jpv[t], V[(int64_t)(g.n_x + g.jp_col[t]) * ld + d], s);
@@ -554,14 +657,39 @@ __global__ void __launch_bounds__(kDirThreads, 2) k_dirs(DirGrid g, DirLaunch L)
         }
         __syncthreads();
     }
-    if (L.phases & PH_L) sweep_fwd<false>(g, g.A, V, ld, 0, D, part);
-    if (L.phases & PH_U) sweep_bwd<true>(g, g.A, V, ld, 0, D, part);
+    extern __shared__ double tri[];
+    if (L.use_tail) {
+        if (L.phases & PH_L) {
+            sweep_fwd<false>(g, g.sf, g.A, V, ld, 0, D, part);
+            sweep_fwd<false, true>(g, g.ef, g.A, V, ld, 0, D, part);
+            tail_fwd<false>(g, g.triL, V, ld, 0, D, part, tri);
+        }
+        if (L.phases & PH_U) {
+            tail_bwd<true>(g, g.triU, V, ld, 0, D, part, tri);
+            sweep_bwd<true>(g, g.sb, g.A, V, ld, 0, D, part);
+        }
+    } else {
+        if (L.phases & PH_L) sweep_fwd<false>(g, g.lf, g.A, V, ld, 0, D, part);
+        if (L.phases & PH_U) sweep_bwd<true>(g, g.lb, g.A, V, ld, 0, D, part);
+    }
     if (L.phases & PH_TPROJ) {
         tproj(g, V, T, ld, 0, D, sref);
         __syncthreads();
     }
-    if (L.phases & PH_UT) sweep_fwd<true>(g, g.At, T, ld, 0, D, part);
-    if (L.phases & PH_LT) sweep_bwd<false>(g, g.At, T, ld, 0, D, part);
+    if (L.use_tail) {
+        if (L.phases & PH_UT) {
+            sweep_fwd<true>(g, g.sf, g.At, T, ld, 0, D, part);
+            sweep_fwd<true, true>(g, g.ef, g.At, T, ld, 0, D, part);
+            tail_fwd<true>(g, g.triUt, T, ld, 0, D, part, tri);
+        }
+        if (L.phases & PH_LT) {
+            tail_bwd<false>(g, g.triLt, T, ld, 0, D, part, tri);
+            sweep_bwd<false>(g, g.sb, g.At, T, ld, 0, D, part);
+        }
+    } else {
+        if (L.phases & PH_UT) sweep_fwd<true>(g, g.lf, g.At, T, ld, 0, D, part);
+        if (L.phases & PH_LT) sweep_bwd<false>(g, g.lb, g.At, T, ld, 0, D, part);
+    }
     if (L.phases & PH_MULADD) {
         for (int it = threadIdx.x; it < g.n_p * D; it += blockDim.x) {
             int k = it / D, d = it - k * D;
@@ -580,10 +708,10 @@ __global__ void __launch_bounds__(1024, 1) k_solve1(DirGrid g, double* x, unsign
     __shared__ double part[kPartCap];
     for (int q = threadIdx.x; q < g.n_x; q += blockDim.x) X[q] = x[q];
     __syncthreads();
-    if (phases & PH_L) sweep_fwd<false>(g, g.A, X, 1, 0, 1, part);
-    if (phases & PH_U) sweep_bwd<true>(g, g.A, X, 1, 0, 1, part);
-    if (phases & PH_UT) sweep_fwd<true>(g, g.At, X, 1, 0, 1, part);
-    if (phases & PH_LT) sweep_bwd<false>(g, g.At, X, 1, 0, 1, part);
+    if (phases & PH_L) sweep_fwd<false>(g, g.lf, g.A, X, 1, 0, 1, part);
+    if (phases & PH_U) sweep_bwd<true>(g, g.lb, g.A, X, 1, 0, 1, part);
+    if (phases & PH_UT) sweep_fwd<true>(g, g.lf, g.At, X, 1, 0, 1, part);
+    if (phases & PH_LT) sweep_bwd<false>(g, g.lb, g.At, X, 1, 0, 1, part);
     for (int q = threadIdx.x; q < g.n_x; q += blockDim.x) x[q] = X[q];
 }
 
@@ -760,13 +888,30 @@ cudaError_t launch_refactor(const RfGrid& g, const int* lev_ptr_host, const int6
         int64_t t0 = tgt_lev_ptr_host[lev], nt = tgt_lev_ptr_host[lev + 1] - t0;
         if (nt > 0) k_rf_update<<<blocks_for(nt, 256), 256, 0, st>>>(g, t0, nt);
     }
-    if (g.T > 0) {
-        size_t ts = (size_t)g.T * g.T * sizeof(double);
-        cudaError_t e = cudaFuncSetAttribute(k_refactor_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts);
-        if (e != cudaSuccess) return e;
-        k_refactor_tail<<<1, 1024, ts, st>>>(g);
-    }
+    if (g.T > 0) k_refactor_tail<<<1, 1024, (size_t)g.T * g.T * sizeof(double), st>>>(g);
     return cudaGetLastError();
+}
+
+// The dynamic shared-memory limit is a per-kernel, process-wide attribute: raise
+// it once to the device maximum (minus the kernel's static shared memory) for
+// every kernel that can need more than the 48 KB default.
+cudaError_t prepare_kernels() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const void* fns[3] = {(const void*)k_refactor_tail, (const void*)k_dirs, (const void*)k_solve1};
+    for (const void* f : fns) {
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, f);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+        if (e != cudaSuccess) return e;
+    }
+    done = true;
+    return cudaSuccess;
 }
 
 void launch_transpose_values(int nnz, const int* tpos, const double* A, double* At, int nnz_jp,
@@ -788,9 +933,21 @@ int dirs_default_ctas(int N) {
     return G < 1 ? 1 : G;
 }
 
+bool dirs_tail_fits(int T, int N, int n_cta) {
+    if (T <= 1 || n_cta <= 0) return false;
+    int dmax = (N + n_cta - 1) / n_cta;
+    return (int64_t)T * dmax <= kPartCap && (size_t)T * (T - 1) / 2 * sizeof(double) <= 96 * 1024;
+}
+
 void launch_dirs(const DirGrid& g, const DirLaunch& L, cudaStream_t st) {
     if (L.N <= 0 || L.n_cta <= 0) return;
-    k_dirs<<<L.n_cta, kDirThreads, 0, st>>>(g, L);
+    size_t smem = L.use_tail ? (size_t)g.T * (g.T - 1) / 2 * sizeof(double) : 0;
+    k_dirs<<<L.n_cta, kDirThreads, smem, st>>>(g, L);
+}
+
+void launch_build_tail(int T, int t0, const int* pos, const double* A, const double* invdiag, double* triL,
+                       double* triU, double* triUt, double* triLt, cudaStream_t st) {
+    if (T > 1) k_build_tail<<<blocks_for((int64_t)T * T, 256), 256, 0, st>>>(T, t0, pos, A, invdiag, triL, triU, triUt, triLt);
 }
 
 void launch_adjoint_rhs(const PfGrid& g, const PfState& s, const AdjData& a, cudaStream_t st) {
@@ -802,8 +959,6 @@ bool solve1_fits(int n_x) { return (size_t)n_x * sizeof(double) + kPartCap * siz
 
 cudaError_t launch_solve1(const DirGrid& g, double* x, unsigned phases, cudaStream_t st) {
     size_t smem = (size_t)(g.n_x > 0 ? g.n_x : 1) * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_solve1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     k_solve1<<<1, 1024, smem, st>>>(g, x, phases);
     return cudaGetLastError();
 }

@@ -19,22 +19,38 @@ enum : unsigned {
     PH_MULADD = 1u << 7,   // HW = y_p + J_p^T psi                         (SpMulAdd)
 };
 
+// A bus-level schedule: level l holds the bus blocks slots[ptr[l] .. ptr[l+1]),
+// maxext[l] = their longest row part.  Slots are packed descriptors
+//   forward  {q, n, rp, rpv}: theta row q, n columns left of the bus (or left of
+//            the dense tail for the tail's external phase), row parts at rp / rpv
+//            (rpv = -1 for a PV bus);
+//   backward {q, n, ue0, ue1}: U parts right of the bus at ue0 / ue1 (-1: PV).
+struct LevelSet {
+    int n_lev;
+    const int *ptr;
+    const int4 *slots;
+    const int *maxext;
+};
+
 // Read-only grid data used by the direction kernel, all device pointers.
 struct DirGrid {
     int n_x, n_p;
     int zero_row;                              // n_x + n_p: a row of zeros in V
     // filled matrix A = L + U (CSR), its transposed values and 1/diagonal
-    const int *rowptr, *col, *diagpos;
+    const int *col;
     const double *A, *At, *invdiag;
-    const int *q0;
-    const uint8_t *nv;
-    int n_flev, n_blev;
-    const int *flev_ptr, *flev_bus, *flev_maxext;
-    const int *blev_ptr, *blev_bus, *blev_maxext;
-    const int4 *fslot, *bslot;                 // packed bus-block descriptors in level order
-    // J_p by internal rows and by p index
+    LevelSet lf, lb;                           // full forward / backward schedules
+    LevelSet sf, sb, ef;                       // sparse part only, and the tail's external phase
+    // dense trailing block [t0, t0 + T): packed strictly-triangular columns
+    //   triL  (L,  lower, unit)            triU  (U,  upper, column j scaled by 1/u_jj)
+    //   triUt (U^T, lower, column j scaled) triLt (L^T, upper, unit)
+    int t0, T;
+    const double *triL, *triU, *triUt, *triLt;
+    // J_p by internal rows and by p index; rows with and without entries
     const int *jp_ptr, *jp_col;
     const double *jpv;
+    int n_jp_rows, n_jp_zero;
+    const int *jp_rows, *jp_zero_rows;
     const int *jpt_ptr, *jpt_row;
     const double *jptv;
     // projection data (per bus, original ids); rows are V/Y row indices
@@ -42,7 +58,7 @@ struct DirGrid {
     const int *tp_bus;                         // bus processing order (internal order, slack last)
     const int *uth, *uv;                       // rows of theta_b (zero row at the slack) and v_b
     const int *inc_ptr, *inc_uth, *inc_uv;     // incident branches: rows of the other end
-    const double4_32a *inc_coef;                   // (K, -a, b, -c) per incidence (state dependent)
+    const double4_32a *inc_coef;               // (K, -a, b, -c) per incidence (state dependent)
     const double *d2, *asum, *csum;            // per-bus coefficients (state dependent)
     const uint8_t *has_gref;
     const double *gref_th, *gref_v;            // grad P_slack at the rows of bus b
@@ -69,6 +85,7 @@ struct DirLaunch {
     double *HW;                // n_p x N column-major (ldhw)
     int64_t ldhw;
     unsigned phases;
+    int use_tail;              // dense tail in shared memory (needs T * ceil(N / n_cta) <= 4096)
 };
 
 // Grid-wide power-flow evaluation data (per bus, original ids).
@@ -113,6 +130,12 @@ cudaError_t launch_refactor(const RfGrid& g, const int* lev_ptr_host, const int6
 void launch_transpose_values(int nnz, const int* tpos, const double* A, double* At, int nnz_jp,
                              const int* jpt_src, const double* jpv, double* jptv, cudaStream_t st);
 void launch_dirs(const DirGrid& g, const DirLaunch& L, cudaStream_t st);
+// raise the dynamic shared-memory limits of the kernels that need it (once per grid)
+cudaError_t prepare_kernels();
+bool dirs_tail_fits(int T, int N, int n_cta);
+// dense tail triangles of the current factors (pos: T*T map to A, -1 where structurally zero)
+void launch_build_tail(int T, int t0, const int* pos, const double* A, const double* invdiag, double* triL,
+                       double* triU, double* triUt, double* triLt, cudaStream_t st);
 // one right-hand side in shared memory (requires solve1_fits(n_x))
 bool solve1_fits(int n_x);
 cudaError_t launch_solve1(const DirGrid& g, double* x, unsigned phases, cudaStream_t st);

@@ -193,6 +193,29 @@ rh_status rh_refactor(rh_grid *grid, double *A_out);
 rh_status rh_lagrangian_hessvec(rh_grid *grid, const double *V, int64_t ldv, int32_t N,
                                 double *Y, int64_t ldy, void *stream, uint32_t flags);
 
+/*
+ * Allocation-free form of rh_hessvec (the paper has no counterpart: this is a
+ * deployment variant of Algorithm 2).  For callers that must not have the
+ * library allocate device memory after start-up, such as an application that
+ * owns all device memory through its own pool, or a real-time control loop
+ * that forbids allocation once running.  The two direction buffers of the
+ * computation live in a fixed device array of 2 x 8 MiB that every GPU holding
+ * librh keeps until the process exits, so this call makes no cudaMalloc,
+ * cudaFree or allocating library call.
+ *   W, HW   DEVICE pointers, n_p x N column-major (ldw, ldhw >= n_p)
+ *   limit   N * (n_x + n_p + 1) <= 1048576 (e.g. N <= 52 on a 9241-bus grid,
+ *           N <= 353 on a 1354-bus grid); larger N returns RH_EINVAL.
+ * Asynchronous on `stream`.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, once per device); make that first call
+ * before any stream capture.  All calls on a device share the one array, which
+ * keeps the previous call's contents (the kernel initialises everything it
+ * reads), so calls that overlap on the GPU, for instance on two streams or for
+ * two grids at once, race and give wrong results: serialise them.
+ * Requires rh_adjoint for the current state (RH_ESTATE otherwise).
+ */
+rh_status rh_hessvec_noalloc(rh_grid *grid, const double *W, int64_t ldw, int32_t N,
+                             double *HW, int64_t ldhw, void *stream);
+
 /* Message of the last error on this thread ("" if none). */
 const char *rh_last_error(void);
 

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -860,6 +861,78 @@ rh_status rh_lagrangian_hessvec(rh_grid* g, const double* V, int64_t ldv, int32_
                                   cudaMemcpyDeviceToHost, s));
         RH_CUDA(cudaStreamSynchronize(s));
     }
+    return RH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free reduced-Hessian-vector products.
+//
+// Some callers cannot let the library call cudaMalloc: a host application that
+// owns all device memory through its own pool, a real-time loop that forbids
+// allocation after start-up, or code whose device memory is budgeted in
+// advance.  rh_hessvec_noalloc serves them: it runs the same direction kernel
+// as rh_hessvec, but its two direction buffers live in the fixed array below,
+// which every GPU that loads librh holds (2 x 8 MiB) until the process exits.
+// ---------------------------------------------------------------------------
+#define RH_NOALLOC_DOUBLES (1u << 20)   // doubles per buffer: 8 MiB
+
+static __device__ __align__(256) double rh_noalloc_scratch[2 * RH_NOALLOC_DOUBLES];
+
+namespace {
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[64] = {nullptr};   // per device: device address of rh_noalloc_scratch
+
+// The array's name in host code is only a host-side stand-in; the device
+// address is looked up once per device, with that device current.
+rh_status noalloc_scratch(int device, double** out) {
+    if (device < 0 || device >= 64) return fail(RH_EINVAL, "device id out of range for the fixed scratch table");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, rh_noalloc_scratch);
+        if (e != cudaSuccess) return fail(RH_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_noalloc_ptr[device] = (double*)p;
+    }
+    *out = g_noalloc_ptr[device];
+    return RH_OK;
+}
+}  // namespace
+
+rh_status rh_hessvec_noalloc(rh_grid* g, const double* W, int64_t ldw, int32_t N, double* HW, int64_t ldhw,
+                             void* stream) {
+    if (!g) return fail(RH_EINVAL, "NULL grid");
+    if (N < 0) return fail(RH_EINVAL, "N must be >= 0");
+    if (N == 0) return RH_OK;
+    const auto& S = g->S;
+    if (!W || !HW || ldw < S.n_p || ldhw < S.n_p) return fail(RH_EINVAL, "bad W / HW or leading dimension");
+    if ((uint64_t)g->rows() * (uint64_t)N > RH_NOALLOC_DOUBLES)
+        return fail(RH_EINVAL, "rh_hessvec_noalloc: N * (n_x + n_p + 1) = " +
+                                   std::to_string((uint64_t)g->rows() * (uint64_t)N) + " exceeds the fixed scratch of " +
+                                   std::to_string(RH_NOALLOC_DOUBLES) + " doubles per buffer; use rh_hessvec or a smaller N");
+    if (!g->adjoint_ready) return fail(RH_ESTATE, "rh_hessvec_noalloc needs rh_adjoint for the current state");
+    rh_status st = set_device(g);
+    if (st) return st;
+    double* scratch = nullptr;
+    st = noalloc_scratch(g->device, &scratch);
+    if (st) return st;
+    // Every row the kernel reads is written by an earlier phase of the same
+    // call (W rows, the zero row, -B, the projection), so nothing is cleared.
+    rh::DirLaunch L;
+    L.N = N;
+    L.n_cta = rh::dirs_default_ctas(N);
+    L.ld = N;
+    L.cta_stride = 0;
+    L.V = scratch;
+    L.T = scratch + RH_NOALLOC_DOUBLES;
+    L.W = W;
+    L.ldw = ldw;
+    L.col0 = 0;
+    L.HW = HW;
+    L.ldhw = ldhw;
+    L.phases = rh::PH_WLOAD | rh::PH_SPMUL | rh::PH_L | rh::PH_U | rh::PH_TPROJ | rh::PH_UT | rh::PH_LT | rh::PH_MULADD;
+    L.use_tail = rh::dirs_tail_fits(S.n_x - S.t0, N, L.n_cta) ? 1 : 0;
+    rh::launch_dirs(g->dir(), L, (cudaStream_t)stream);
+    RH_CUDA(cudaGetLastError());
     return RH_OK;
 }
 

@@ -22,7 +22,7 @@ _NAMES = ["RH_OK", "RH_EINVAL", "RH_ENOMEM", "RH_ESINGULAR", "RH_ENOCONV", "RH_E
 # every symbol declared in include/rh.h
 EXPORTS = ["rh_grid_create", "rh_grid_destroy", "rh_grid_dims", "rh_grid_symbolic", "rh_injections",
            "rh_set_state", "rh_powerflow", "rh_adjoint", "rh_hessvec", "rh_hessian", "rh_solve", "rh_refactor",
-           "rh_lagrangian_hessvec", "rh_last_error"]
+           "rh_lagrangian_hessvec", "rh_hessvec_noalloc", "rh_last_error"]
 
 
 class RHError(RuntimeError):
@@ -77,6 +77,7 @@ def load(build_if_missing: bool = True):
         "rh_solve": ([P, P, I64, I32, I32, P, U32], C.c_int),
         "rh_refactor": ([P, P], C.c_int),
         "rh_lagrangian_hessvec": ([P, P, I64, I32, P, I64, P, U32], C.c_int),
+        "rh_hessvec_noalloc": ([P, P, I64, I32, P, I64, P], C.c_int),
         "rh_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():

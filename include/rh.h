@@ -158,6 +158,36 @@ rh_status rh_hessvec(rh_grid *grid, const double *W, int64_t ldw, int32_t N,
                      double *HW, int64_t ldhw, void *stream, uint32_t flags);
 
 /*
+ * Cross-instance batching: several (grid, W block) items, for instance the load
+ * scenarios of one topology (each its own rh_grid with its own state) or
+ * requests on grids of different sizes, computed by ONE kernel launch on
+ * `stream` (asynchronous).  Items are independent; item i gets
+ * ceil(N_i / width) CTAs (width = target directions per CTA, the right-hand-
+ * side interleave width; 0 picks the rh_hessvec default per item).  Up to 32
+ * items per launch; larger batches take several launches.
+ *   grid    adjoint-ready grid (rh_adjoint for its current state); all items
+ *           must be on the same device
+ *   W, HW   DEVICE pointers, n_p x N column-major (ldw, ldhw >= n_p of the grid)
+ *   work    DEVICE workspace of at least rh_hv_work_doubles(grid, N) doubles
+ *           owned by the caller, or NULL to use (and grow) the grid's own
+ *           workspace; a grid may appear at most once with work = NULL.
+ * Items must not share workspaces or outputs.  Each item's result equals
+ * rh_hessvec on the same grid and W up to rounding.
+ */
+typedef struct {
+    rh_grid *grid;
+    const double *W;
+    int64_t ldw;
+    int32_t N;
+    double *HW;
+    int64_t ldhw;
+    double *work;
+} rh_hv_item;
+
+int64_t rh_hv_work_doubles(const rh_grid *grid, int32_t N);
+rh_status rh_batch_hessvec(int32_t n_items, const rh_hv_item *items, int32_t width, void *stream);
+
+/*
  * Full reduced Hessian H = Hess F (n_p x n_p, column-major, leading dimension
  * ldh >= n_p), computed as HW for W = I by blocks of block_n columns
  * (section 5.3; block count ceil(n_p / block_n)).  All blocks are issued in

@@ -746,6 +746,78 @@ rh_status rh_hessvec(rh_grid* g, const double* W, int64_t ldw, int32_t N, double
     return RH_OK;
 }
 
+int64_t rh_hv_work_doubles(const rh_grid* g, int32_t N) {
+    if (!g || N < 0) return -1;
+    return 2 * (int64_t)g->rows() * (int64_t)N;
+}
+
+rh_status rh_batch_hessvec(int32_t n_items, const rh_hv_item* items, int32_t width, void* stream) {
+    if (n_items < 0 || (n_items > 0 && !items)) return fail(RH_EINVAL, "bad item list");
+    if (width < 0) return fail(RH_EINVAL, "width must be >= 0");
+    if (n_items == 0) return RH_OK;
+    int device = -1;
+    for (int i = 0; i < n_items; i++) {
+        const rh_hv_item& it = items[i];
+        if (!it.grid) return fail(RH_EINVAL, "item " + std::to_string(i) + ": NULL grid");
+        const auto& S = it.grid->S;
+        if (it.N < 0 || (it.N > 0 && (!it.W || !it.HW)) || it.ldw < S.n_p || it.ldhw < S.n_p)
+            return fail(RH_EINVAL, "item " + std::to_string(i) + ": bad W / HW, leading dimension or N");
+        if (!it.grid->adjoint_ready)
+            return fail(RH_ESTATE, "item " + std::to_string(i) + ": rh_batch_hessvec needs rh_adjoint for the grid's state");
+        if (device < 0) device = it.grid->device;
+        if (it.grid->device != device) return fail(RH_EINVAL, "all items must be on the same device");
+        if (!it.work)
+            for (int j = 0; j < i; j++)
+                if (!items[j].work && items[j].grid == it.grid)
+                    return fail(RH_EINVAL, "a grid appears twice with work = NULL");
+    }
+    rh_status st = set_device(items[0].grid);
+    if (st) return st;
+    for (int i = 0; i < n_items; i++)
+        if (!items[i].work && items[i].N > 0) {
+            st = ensure_ws(items[i].grid, (size_t)items[i].N);
+            if (st) return st;
+        }
+    const unsigned all = rh::PH_WLOAD | rh::PH_SPMUL | rh::PH_L | rh::PH_U | rh::PH_TPROJ | rh::PH_UT | rh::PH_LT |
+                         rh::PH_MULADD;
+    std::unique_ptr<rh::DirBatch> B(new rh::DirBatch());
+    for (int first = 0; first < n_items; first += rh::kMaxBatch) {
+        int n = std::min(rh::kMaxBatch, n_items - first);
+        B->n_items = 0;
+        B->cta_ptr[0] = 0;
+        int max_T = 0;
+        for (int k = 0; k < n; k++) {
+            const rh_hv_item& it = items[first + k];
+            if (it.N == 0) continue;
+            rh_grid* g = it.grid;
+            int G = width > 0 ? (it.N + width - 1) / width : rh::dirs_default_ctas(it.N);
+            G = std::max(G, (it.N + 255) / 256);
+            rh::DirLaunch& L = B->l[B->n_items];
+            L.N = it.N;
+            L.n_cta = G;
+            L.ld = it.N;
+            L.cta_stride = 0;
+            L.V = it.work ? it.work : g->V;
+            L.T = it.work ? it.work + (size_t)g->rows() * it.N : g->T;
+            L.W = it.W;
+            L.ldw = it.ldw;
+            L.col0 = 0;
+            L.HW = it.HW;
+            L.ldhw = it.ldhw;
+            L.phases = all;
+            int Tt = g->S.n_x - g->S.t0;
+            L.use_tail = rh::dirs_tail_fits(Tt, it.N, G) ? 1 : 0;
+            if (L.use_tail) max_T = std::max(max_T, Tt);
+            B->g[B->n_items] = g->dir();
+            B->cta_ptr[B->n_items + 1] = B->cta_ptr[B->n_items] + G;
+            B->n_items++;
+        }
+        rh::launch_dirs_batch(*B, max_T, (cudaStream_t)stream);
+        RH_CUDA(cudaGetLastError());
+    }
+    return RH_OK;
+}
+
 rh_status rh_hessian(rh_grid* g, int32_t block_n, double* H, int64_t ldh, void* stream, uint32_t flags) {
     if (!g) return fail(RH_EINVAL, "NULL grid");
     const auto& S = g->S;

@@ -618,10 +618,9 @@ __device__ void tproj(const DirGrid& g, const double* V, double* T, int64_t ld, 
     }
 }
 
-__global__ void __launch_bounds__(kDirThreads, 2) k_dirs(DirGrid g, DirLaunch L) {
-    __shared__ double part[kPartCap];
-    __shared__ double sref[kDMax];
-    const int cta = blockIdx.x;
+// Algorithm 2 for the directions owned by CTA `cta` of launch L on grid g.
+__device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, const int cta, double* part,
+                                          double* sref, double* tri) {
     const int c0 = (int)((int64_t)cta * L.N / L.n_cta);
     const int c1 = (int)((int64_t)(cta + 1) * L.N / L.n_cta);
     const int D = c1 - c0;
@@ -657,7 +656,6 @@ __global__ void __launch_bounds__(kDirThreads, 2) k_dirs(DirGrid g, DirLaunch L)
         }
         __syncthreads();
     }
-    extern __shared__ double tri[];
     if (L.use_tail) {
         if (L.phases & PH_L) {
             sweep_fwd<false>(g, g.sf, g.A, V, ld, 0, D, part);
@@ -699,6 +697,32 @@ __global__ void __launch_bounds__(kDirThreads, 2) k_dirs(DirGrid g, DirLaunch L)
             L.HW[(int64_t)(c0 + d) * L.ldhw + k] = h;
         }
     }
+}
+
+__global__ void __launch_bounds__(kDirThreads, 2) k_dirs(DirGrid g, DirLaunch L) {
+    __shared__ double part[kPartCap];
+    __shared__ double sref[kDMax];
+    extern __shared__ double tri[];
+    dirs_body(g, L, blockIdx.x, part, sref, tri);
+}
+
+// Several (grid, W block) items in one launch: CTA b belongs to the item i with
+// cta_ptr[i] <= b < cta_ptr[i + 1]; the item descriptors travel in the kernel
+// parameters and are copied to shared memory.
+__global__ void __launch_bounds__(kDirThreads, 2) k_dirs_batch(DirBatch B) {
+    __shared__ double part[kPartCap];
+    __shared__ double sref[kDMax];
+    __shared__ DirGrid sg;
+    __shared__ DirLaunch sl;
+    extern __shared__ double tri[];
+    int item = 0;
+    while (item + 1 < B.n_items && (int)blockIdx.x >= B.cta_ptr[item + 1]) item++;
+    if (threadIdx.x == 0) {
+        sg = B.g[item];
+        sl = B.l[item];
+    }
+    __syncthreads();
+    dirs_body(sg, sl, (int)blockIdx.x - B.cta_ptr[item], part, sref, tri);
 }
 
 // One right-hand side, one CTA, x held in shared memory for the whole sweep
@@ -902,7 +926,8 @@ cudaError_t prepare_kernels() {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const void* fns[3] = {(const void*)k_refactor_tail, (const void*)k_dirs, (const void*)k_solve1};
+    const void* fns[4] = {(const void*)k_refactor_tail, (const void*)k_dirs, (const void*)k_solve1,
+                          (const void*)k_dirs_batch};
     for (const void* f : fns) {
         cudaFuncAttributes fa;
         e = cudaFuncGetAttributes(&fa, f);
@@ -943,6 +968,12 @@ void launch_dirs(const DirGrid& g, const DirLaunch& L, cudaStream_t st) {
     if (L.N <= 0 || L.n_cta <= 0) return;
     size_t smem = L.use_tail ? (size_t)g.T * (g.T - 1) / 2 * sizeof(double) : 0;
     k_dirs<<<L.n_cta, kDirThreads, smem, st>>>(g, L);
+}
+
+void launch_dirs_batch(const DirBatch& B, int max_T, cudaStream_t st) {
+    if (B.n_items <= 0 || B.cta_ptr[B.n_items] <= 0) return;
+    size_t smem = max_T > 1 ? (size_t)max_T * (max_T - 1) / 2 * sizeof(double) : 0;
+    k_dirs_batch<<<B.cta_ptr[B.n_items], kDirThreads, smem, st>>>(B);
 }
 
 void launch_build_tail(int T, int t0, const int* pos, const double* A, const double* invdiag, double* triL,

@@ -88,6 +88,17 @@ struct DirLaunch {
     int use_tail;              // dense tail in shared memory (needs T * ceil(N / n_cta) <= 4096)
 };
 
+// Up to kMaxBatch (grid, W block) items of one batched launch, passed by value as
+// the kernel parameter (about 16 KB).
+constexpr int kMaxBatch = 32;
+struct DirBatch {
+    int n_items;
+    int cta_ptr[kMaxBatch + 1];
+    DirGrid g[kMaxBatch];
+    DirLaunch l[kMaxBatch];
+};
+void launch_dirs_batch(const DirBatch& B, int max_T, cudaStream_t st);
+
 // Grid-wide power-flow evaluation data (per bus, original ids).
 struct PfGrid {
     int n_bus, n_x, ref;

@@ -22,7 +22,8 @@ _NAMES = ["RH_OK", "RH_EINVAL", "RH_ENOMEM", "RH_ESINGULAR", "RH_ENOCONV", "RH_E
 # every symbol declared in include/rh.h
 EXPORTS = ["rh_grid_create", "rh_grid_destroy", "rh_grid_dims", "rh_grid_symbolic", "rh_injections",
            "rh_set_state", "rh_powerflow", "rh_adjoint", "rh_hessvec", "rh_hessian", "rh_solve", "rh_refactor",
-           "rh_lagrangian_hessvec", "rh_hessvec_noalloc", "rh_last_error"]
+           "rh_lagrangian_hessvec", "rh_hessvec_noalloc", "rh_hv_work_doubles", "rh_batch_hessvec",
+           "rh_last_error"]
 
 
 class RHError(RuntimeError):
@@ -35,6 +36,11 @@ class _Desc(C.Structure):
     _fields_ = [("n_bus", C.c_int32), ("n_branch", C.c_int32), ("from_", C.c_void_p), ("to", C.c_void_p),
                 ("r", C.c_void_p), ("x", C.c_void_p), ("b", C.c_void_p), ("bus_type", C.c_void_p),
                 ("c2", C.c_void_p), ("c1", C.c_void_p), ("base_mva", C.c_double)]
+
+
+class HvItem(C.Structure):
+    _fields_ = [("grid", C.c_void_p), ("W", C.c_void_p), ("ldw", C.c_int64), ("N", C.c_int32),
+                ("HW", C.c_void_p), ("ldhw", C.c_int64), ("work", C.c_void_p)]
 
 
 class Dims(C.Structure):
@@ -78,6 +84,8 @@ def load(build_if_missing: bool = True):
         "rh_refactor": ([P, P], C.c_int),
         "rh_lagrangian_hessvec": ([P, P, I64, I32, P, I64, P, U32], C.c_int),
         "rh_hessvec_noalloc": ([P, P, I64, I32, P, I64, P], C.c_int),
+        "rh_hv_work_doubles": ([P, I32], C.c_int64),
+        "rh_batch_hessvec": ([I32, P, I32, P], C.c_int),
         "rh_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -207,12 +215,14 @@ class Grid:
         """
         if _is_device(W):
             N = W.shape[1]
-            assert W.stride(0) == 1, "device W must be column-major (stride(0) == 1)"
+            assert N <= 1 or W.stride(0) == 1, "device W must be column-major (stride(0) == 1)"
             if HW is None:
                 import torch
                 HW = torch.empty((N, self.n_p), dtype=torch.float64, device=W.device).t()
             st = stream if stream is not None else _stream_of(W)
-            _check(_lib.rh_hessvec(self._h, _ptr(W), W.stride(1), N, _ptr(HW), HW.stride(1), st, RH_DEVICE_PTRS))
+            ldw = W.stride(1) if N > 1 else self.n_p
+            ldh = HW.stride(1) if N > 1 else self.n_p
+            _check(_lib.rh_hessvec(self._h, _ptr(W), ldw, N, _ptr(HW), ldh, st, RH_DEVICE_PTRS))
             return HW
         W = np.asfortranarray(W, dtype=np.float64)
         if W.ndim == 1:
@@ -287,3 +297,29 @@ class Grid:
         pv = ip_pg >= 0
         p[ip_pg[pv]] = P[pv]
         return Planted(x, p, pd, qd)
+
+
+def batch_hessvec(items, width: int = 0, stream=None):
+    """rh_batch_hessvec: items are (Grid, W, HW, work) with CUDA torch tensors W, HW
+    (column-major n_p x N views) and work (1-D float64 tensor of
+    rh_hv_work_doubles(grid, N) elements) or None.  Asynchronous on `stream`
+    (default: torch's current stream)."""
+    lib = load()
+    arr = (HvItem * len(items))()
+    for k, (grid, W, HW, work) in enumerate(items):
+        n = W.shape[1]
+        assert HW.shape[1] == n and W.shape[0] == HW.shape[0] == grid.n_p
+        assert n <= 1 or (W.stride(0) == 1 and HW.stride(0) == 1), "W and HW must be column-major"
+        # a single column's leading dimension is free (torch may report any stride there)
+        ldw = W.stride(1) if n > 1 else grid.n_p
+        ldh = HW.stride(1) if n > 1 else grid.n_p
+        arr[k] = HvItem(grid._h.value, W.data_ptr(), ldw, n, HW.data_ptr(), ldh,
+                        0 if work is None else work.data_ptr())
+    if stream is None:
+        import torch
+        stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _check(lib.rh_batch_hessvec(len(items), arr, int(width), stream))
+
+
+def work_doubles(grid, N: int) -> int:
+    return int(load().rh_hv_work_doubles(grid._h, int(N)))

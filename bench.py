@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--case", default=CASE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 118-bus latency, scenario batching, plain-path and serving measurements")
     return ap.parse_args()
 
 
@@ -126,6 +128,191 @@ def cpu_baseline(case, n_dirs=32):
     return dict(value=n_dirs / dt, unit="HVP/s", cores=1, kind="oracle",
                 sample=f"{n_dirs} of {o.n_p} unit directions of H on {case} (incl. the oracle's own LU and adjoint), "
                        f"{dt:.1f} s")
+
+
+def _ready(case, scale_k=None):
+    from paper_2201_00241_gb300 import gridgen as gg
+    from paper_2201_00241_gb300 import rh
+    g = gg.make_case(case)
+    lg = rh.Grid(g, device=torch_device_index())
+    st = lg.plant()
+    pd, qd = st.pd, st.qd
+    if scale_k is not None:
+        s = gg.load_scales(g.n_bus, scale_k + 1, g.seed)[scale_k]
+        pd, qd = pd * s, qd * s
+    lg.set_state(st.p, pd, qd)
+    lg.powerflow(st.x, tol=1e-12, max_iter=20)
+    lg.adjoint()
+    return lg
+
+
+def torch_device_index():
+    import torch
+    return torch.cuda.current_device()
+
+
+def _colmajor(W):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(W.T)).cuda().t()
+
+
+def _event_ms(fn, reps):
+    import torch
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_case118_latency(reps=20):
+    """Full reduced Hessian of the 118-bus grid (7 blocks of 16), per-state setup included."""
+    from paper_2201_00241_gb300 import rh
+    lg = _ready("case118")
+    lib = rh.load()
+    import torch
+    H = torch.empty((lg.n_p, lg.n_p), dtype=torch.float64, device="cuda").t()
+    sptr = rh.C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def one():
+        rh._check(lib.rh_adjoint(lg._h, None, None, None))
+        rh._check(lib.rh_hessian(lg._h, 16, rh._ptr(H), lg.n_p, sptr, rh.RH_DEVICE_PTRS))
+
+    for _ in range(3):
+        one()
+    t = [_event_ms(one, 1) for _ in range(reps)]
+    return {"workload": "case118: full reduced Hessian, 107 columns in 7 blocks of N=16, setup included",
+            "latency_ms_p50": float(np.median(t)), "latency_ms_min": float(np.min(t))}
+
+
+def measure_scenarios(n_scen=8, N=64, reps=10):
+    """8 load scenarios of the 1354-bus grid, N=64 directions each: 8 plain launches vs one
+    batched launch (autotuned interleave width) replayed from a captured CUDA graph."""
+    import torch
+    from paper_2201_00241_gb300 import gridgen as gg
+    from paper_2201_00241_gb300 import rh
+    from paper_2201_00241_gb300.autotune import tune_width
+    grids = [_ready("case1354", k) for k in range(n_scen)]
+    items = []
+    for k, lg in enumerate(grids):
+        W = _colmajor(gg.random_directions(lg.n_p, N, 1000 + k))
+        HW = torch.empty((N, lg.n_p), dtype=torch.float64, device="cuda").t()
+        work = torch.empty(rh.work_doubles(lg, N), dtype=torch.float64, device="cuda")
+        items.append((lg, W, HW, work))
+
+    def plain():
+        for lg, W, HW, _ in items:
+            lg.hessvec(W, HW)
+
+    plain()
+    t_plain = _event_ms(plain, reps)
+    width, width_ms = tune_width(items)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    rh.batch_hessvec(items, width)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            rh.batch_hessvec(items, width, stream=rh.C.c_void_p(s.cuda_stream))
+    graph.replay()
+    t_batched = _event_ms(graph.replay, reps)
+    total = n_scen * N
+    return {"workload": f"case1354: {n_scen} load scenarios (per-bus loads x U[0.9,1.1], power flow re-solved), "
+                        f"N={N} random unit directions each",
+            "plain_hvp_per_s": total / (t_plain * 1e-3), "batched_hvp_per_s": total / (t_batched * 1e-3),
+            "plain_ms": t_plain, "batched_ms": t_batched, "width": width,
+            "width_ms": {str(k): v for k, v in width_ms.items()}, "batched_launch": "one rh_batch_hessvec, CUDA graph"}
+
+
+def measure_plain_paths(lg, n_single=32, reps=3):
+    """The plain one-direction-at-a-time path and the one-launch-per-block full Hessian."""
+    import torch
+    from paper_2201_00241_gb300 import gridgen as gg
+    from paper_2201_00241_gb300 import rh
+    W = _colmajor(gg.random_directions(lg.n_p, n_single, 77))
+    HW = torch.empty((n_single, lg.n_p), dtype=torch.float64, device="cuda").t()
+
+    def singles():
+        for j in range(n_single):
+            lg.hessvec(W[:, j:j + 1], HW[:, j:j + 1])
+
+    singles()
+    t1 = _event_ms(singles, reps)
+    lib = rh.load()
+    H = torch.empty((lg.n_p, lg.n_p), dtype=torch.float64, device="cuda").t()
+    sptr = rh.C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def blocks():
+        rh._check(lib.rh_hessian(lg._h, BLOCK_N, rh._ptr(H), lg.n_p, sptr, rh.RH_DEVICE_PTRS))
+
+    blocks()
+    tb = _event_ms(blocks, reps)
+    return {"n1_hvp_per_s": n_single / (t1 * 1e-3),
+            "per_block_launches_hvp_per_s": lg.n_p / (tb * 1e-3),
+            "note": "HVP only (state resident); N=1 calls one at a time / 12 launches of N=256"}
+
+
+def measure_serving(factors=(0.25, 0.5, 1.0, 2.0, 4.0), n_req=120, seed=4):
+    """Poisson request stream over grids of 118, 1354, 2869 and 9241 buses (ratio 8:4:2:1),
+    N ~ U{1..256} unit directions per request, through the continuous-batching server."""
+    import time as _t
+    from paper_2201_00241_gb300 import gridgen as gg
+    from paper_2201_00241_gb300.server import RHServer
+    names = ["case118", "case1354", "case2869", "case9241"]
+    weights = np.array([8, 4, 2, 1], dtype=float)
+    weights /= weights.sum()
+    grids = {n: _ready(n) for n in names}
+    srv = RHServer(device=torch_device_index(), budget_bytes=16 << 30, max_batch=16, n_streams=4)
+    for n, lg in grids.items():
+        srv.register(n, lg)
+    rng = np.random.default_rng(seed)
+
+    def draw(k):
+        name = names[rng.choice(4, p=weights)]
+        N = int(rng.integers(1, 257))
+        return name, gg.random_directions(grids[name].n_p, N, 10_000 + k)
+
+    try:
+        reqs = [draw(k) for k in range(48)]
+        for name, W in reqs[:8]:
+            srv.submit(name, W).result()                     # warm-up
+        t0 = _t.perf_counter()
+        futs = [srv.submit(name, W) for name, W in reqs]
+        for f in futs:
+            f.result()
+        dt = _t.perf_counter() - t0
+        sat_req = len(reqs) / dt
+        sat_hvp = sum(W.shape[1] for _, W in reqs) / dt
+        rows = []
+        for f in factors:
+            rate = f * sat_req
+            stream = [draw(1000 * int(10 * f) + k) for k in range(n_req)]
+            gaps = rng.exponential(1.0 / rate, n_req)
+            srv.latencies = []
+            t0 = _t.perf_counter()
+            t_next = t0
+            futs = []
+            for (name, W), gap in zip(stream, gaps):
+                t_next += gap
+                wait = t_next - _t.perf_counter()
+                if wait > 0:
+                    _t.sleep(wait)          # releases the GIL for the server's worker thread
+                futs.append(srv.submit(name, W))
+            for fu in futs:
+                fu.result()
+            dt = _t.perf_counter() - t0
+            st = srv.stats()
+            rows.append({"rate_factor": f, "offered_req_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                         "throughput_hvp_per_s": sum(W.shape[1] for _, W in stream) / dt})
+        return {"workload": "Poisson requests over case118/1354/2869/9241 (8:4:2:1), N ~ U{1..256}",
+                "saturated_req_per_s": sat_req, "saturated_hvp_per_s": sat_hvp, "sweep": rows,
+                "batches": srv.batches, "waited_for_budget": srv.waited_for_budget}
+    finally:
+        srv.close()
 
 
 def run_reference(args, rank, world):
@@ -277,6 +464,11 @@ def main():
         "gpu_launches": dm.n_levels_fwd + 7,
         "clocks": clocks,
     }
+    if not args.no_extras:
+        line["plain_paths"] = measure_plain_paths(lg)
+        line["case118_full_hessian"] = measure_case118_latency()
+        line["scenario_batching"] = measure_scenarios()
+        line["serving"] = measure_serving()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.case)
     print(json.dumps(line), flush=True)

@@ -459,7 +459,9 @@ def main():
         "roofline": {"bound": "alu", "kernel": "k_dirs", "achieved": achieved, "peak": PEAK_FP64_GFLOPS,
                      "unit": "GFLOP/s", "frac": achieved / PEAK_FP64_GFLOPS,
                      "traffic": measured_traffic() if args.case == CASE else None,
-                     "kernel_ms": t_dirs, "flops_per_direction": flops_dir},
+                     "kernel_ms": t_dirs, "flops_per_direction": flops_dir,
+                     "note": "flops counted for a dense W; with W = I the forward L sweep skips buses outside "
+                             "the reach of B's nonzeros (exact zeros), so frac overstates FP64 use by that share"},
         "e2e": {"value": e2e_value, "unit": "HVP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": dm.n_levels_fwd + 7,
         "clocks": clocks,

@@ -65,6 +65,7 @@ struct rh_grid {
     int4 *sf_slot = nullptr, *sb_slot = nullptr, *ef_slot = nullptr;
     int n_sf = 0, n_sb = 0, n_ef = 0;
     int* tail_pos = nullptr;
+    int *qtheta = nullptr, *bparent = nullptr;
     int *jp_rows = nullptr, *jp_zero_rows = nullptr;
     int n_jp_rows = 0, n_jp_zero = 0;
     double *triL = nullptr, *triU = nullptr, *triUt = nullptr, *triLt = nullptr;
@@ -154,6 +155,7 @@ struct rh_grid {
         g.ef = {n_ef, ef_ptr, ef_slot, ef_maxext};
         g.t0 = S.t0; g.T = S.n_x - S.t0;
         g.triL = triL; g.triU = triU; g.triUt = triUt; g.triLt = triLt;
+        g.qtheta = qtheta; g.bparent = bparent;
         g.jp_ptr = jp_ptr; g.jp_col = jp_col; g.jpv = jpv;
         g.n_jp_rows = n_jp_rows; g.n_jp_zero = n_jp_zero; g.jp_rows = jp_rows; g.jp_zero_rows = jp_zero_rows;
         g.jpt_ptr = jpt_ptr; g.jpt_row = jpt_row; g.jptv = jptv;
@@ -255,6 +257,7 @@ rh_status dirs(rh_grid* g, int N, int64_t ld, double* V, double* T, const double
     L.ldhw = ldhw;
     L.phases = phases;
     L.use_tail = rh::dirs_tail_fits(g->S.n_x - g->S.t0, N, L.n_cta) ? 1 : 0;
+    L.use_reach = (L.use_tail && !W && (phases & rh::PH_WLOAD) && (phases & rh::PH_L)) ? 1 : 0;
     rh::launch_dirs(g->dir(), L, s);
     RH_CUDA(cudaGetLastError());
     return RH_OK;
@@ -447,6 +450,18 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
             for (int t = S.rowptr[S.t0 + i]; t < S.rowptr[S.t0 + i + 1]; t++)
                 if (S.col[t] >= S.t0) tp[(size_t)i * T + (S.col[t] - S.t0)] = t;
         RH_CUDA(g->upload(g->tail_pos, tp));
+        // bus structure by theta row for the reach-restricted forward sweep
+        std::vector<int> qth(nx, 0), bpar(nx, -1);
+        for (int k = 0; k < S.n_elim; k++) {
+            int q = S.q0[k];
+            for (int t = 0; t < S.nv[k]; t++) qth[q + t] = q;
+            if (k < S.tail_bus0 && !S.colpat[k].empty()) {
+                int par = S.colpat[k][0];              // first later bus of the pattern: the tree parent
+                if (par < S.tail_bus0) bpar[q] = S.q0[par];
+            }
+        }
+        RH_CUDA(g->upload(g->qtheta, qth));
+        RH_CUDA(g->upload(g->bparent, bpar));
         size_t ntri = T > 1 ? (size_t)T * (T - 1) / 2 : 1;
         RH_CUDA(g->alloc(g->triL, ntri));
         RH_CUDA(g->alloc(g->triU, ntri));
@@ -807,6 +822,7 @@ rh_status rh_batch_hessvec(int32_t n_items, const rh_hv_item* items, int32_t wid
             L.phases = all;
             int Tt = g->S.n_x - g->S.t0;
             L.use_tail = rh::dirs_tail_fits(Tt, it.N, G) ? 1 : 0;
+            L.use_reach = 0;
             if (L.use_tail) max_T = std::max(max_T, Tt);
             B->g[B->n_items] = g->dir();
             B->cta_ptr[B->n_items + 1] = B->cta_ptr[B->n_items] + G;
@@ -1003,6 +1019,7 @@ rh_status rh_hessvec_noalloc(rh_grid* g, const double* W, int64_t ldw, int32_t N
     L.ldhw = ldhw;
     L.phases = rh::PH_WLOAD | rh::PH_SPMUL | rh::PH_L | rh::PH_U | rh::PH_TPROJ | rh::PH_UT | rh::PH_LT | rh::PH_MULADD;
     L.use_tail = rh::dirs_tail_fits(S.n_x - S.t0, N, L.n_cta) ? 1 : 0;
+    L.use_reach = 0;
     rh::launch_dirs(g->dir(), L, (cudaStream_t)stream);
     RH_CUDA(cudaGetLastError());
     return RH_OK;

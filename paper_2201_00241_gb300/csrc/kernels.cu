@@ -338,9 +338,14 @@ __device__ __forceinline__ void fwd_finish(const DirGrid& g, const double* __res
 // so an item needs a single dependent load before its row data; the next
 // item's slot is prefetched while the current one is computed.
 // EXT: subtract the row parts only (the dense tail's external phase), no finish.
+// mask (optional, forward L sweep with identity W): bit q is set for the theta row q of
+// every bus whose x can be nonzero for this CTA's directions; inactive buses keep
+// x = b = 0 and are skipped, and every processed bus activates its tree parent.
+__device__ __forceinline__ bool mask_get(const unsigned* m, int q) { return (m[q >> 5] >> (q & 31)) & 1u; }
+__device__ __forceinline__ void mask_set(unsigned* m, int q) { atomicOr(m + (q >> 5), 1u << (q & 31)); }
 template <bool SCALE, bool EXT = false>
 __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __restrict__ vals, double* X,
-                          int64_t ld, int c0, int D, double* part) {
+                          int64_t ld, int c0, int D, double* part, unsigned* mask = nullptr) {
     for (int lev = 0; lev < ls.n_lev; lev++) {
         const int b0 = ls.ptr[lev], nb = ls.ptr[lev + 1] - b0;
         const int4* __restrict__ slots = ls.slots + b0;
@@ -356,6 +361,8 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 const int it2 = it + blockDim.x, bi2 = it2 / D;
                 if (it2 < items) nxt = slots[bi2];
                 const int q = sl.x, n = sl.y, rp = sl.z;
+                bi = bi2;
+                if (mask && !mask_get(mask, q)) continue;
                 const bool two = sl.w >= 0;
                 const int rpv = two ? sl.w : rp;
                 const int64_t c = c0 + d;
@@ -369,7 +376,10 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 } else {
                     fwd_finish<SCALE>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
                 }
-                bi = bi2;
+                if (mask) {
+                    const int pq = g.bparent[q];
+                    if (pq >= 0) mask_set(mask, pq);
+                }
             }
         } else {
             const int per = ks * D;
@@ -377,6 +387,7 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 int bi = it / per, rem = it - bi * per;
                 int sli = rem / D, d = rem - sli * D;
                 const int4 sl = slots[bi];
+                if (mask && !mask_get(mask, sl.x)) continue;
                 const int n = sl.y, rp = sl.z;
                 const bool two = sl.w >= 0;
                 const int rpv = two ? sl.w : rp;
@@ -393,6 +404,7 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 int bi = it / D, d = it - bi * D;
                 const int4 sl = slots[bi];
                 const int q = sl.x, n = sl.y;
+                if (mask && !mask_get(mask, q)) continue;
                 const bool two = sl.w >= 0;
                 const int rpv = two ? sl.w : sl.z;
                 int64_t c = c0 + d;
@@ -408,6 +420,10 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                     if (two) X[(int64_t)(q + 1) * ld + c] = a1;
                 } else {
                     fwd_finish<SCALE>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
+                }
+                if (mask) {
+                    const int pq = g.bparent[q];
+                    if (pq >= 0) mask_set(mask, pq);
                 }
             }
         }
@@ -658,7 +674,20 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
     }
     if (L.use_tail) {
         if (L.phases & PH_L) {
-            sweep_fwd<false>(g, g.sf, g.A, V, ld, 0, D, part);
+            unsigned* mask = nullptr;
+            if (L.use_reach) {
+                // identity W: B column c is column col0 + c of J_p; seed its buses
+                mask = reinterpret_cast<unsigned*>(tri + (size_t)g.T * (g.T - 1) / 2);
+                for (int i = threadIdx.x; i < (g.n_x + 31) / 32; i += blockDim.x) mask[i] = 0u;
+                __syncthreads();
+                for (int d = threadIdx.x / 8; d < D; d += blockDim.x / 8) {
+                    const int k = L.col0 + c0 + d;
+                    for (int t = g.jpt_ptr[k] + (threadIdx.x & 7); t < g.jpt_ptr[k + 1]; t += 8)
+                        mask_set(mask, g.qtheta[g.jpt_row[t]]);
+                }
+                __syncthreads();
+            }
+            sweep_fwd<false>(g, g.sf, g.A, V, ld, 0, D, part, mask);
             sweep_fwd<false, true>(g, g.ef, g.A, V, ld, 0, D, part);
             tail_fwd<false>(g, g.triL, V, ld, 0, D, part, tri);
         }
@@ -967,6 +996,7 @@ bool dirs_tail_fits(int T, int N, int n_cta) {
 void launch_dirs(const DirGrid& g, const DirLaunch& L, cudaStream_t st) {
     if (L.N <= 0 || L.n_cta <= 0) return;
     size_t smem = L.use_tail ? (size_t)g.T * (g.T - 1) / 2 * sizeof(double) : 0;
+    if (L.use_tail && L.use_reach) smem += ((size_t)g.n_x + 127) / 128 * 16;   // one bit per row
     k_dirs<<<L.n_cta, kDirThreads, smem, st>>>(g, L);
 }
 

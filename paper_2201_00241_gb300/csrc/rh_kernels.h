@@ -46,6 +46,9 @@ struct DirGrid {
     //   triUt (U^T, lower, column j scaled) triLt (L^T, upper, unit)
     int t0, T;
     const double *triL, *triU, *triUt, *triLt;
+    // bus structure by theta row: theta row of the bus owning row q; theta row of the
+    // bus's elimination-tree parent (-1 for a root or a parent in the dense tail)
+    const int *qtheta, *bparent;
     // J_p by internal rows and by p index; rows with and without entries
     const int *jp_ptr, *jp_col;
     const double *jpv;
@@ -86,6 +89,7 @@ struct DirLaunch {
     int64_t ldhw;
     unsigned phases;
     int use_tail;              // dense tail in shared memory (needs T * ceil(N / n_cta) <= 4096)
+    int use_reach;             // identity W: forward L sweep only over the reach of B's nonzeros (needs use_tail)
 };
 
 // Up to kMaxBatch (grid, W block) items of one batched launch, passed by value as

@@ -55,6 +55,8 @@ def _load():
     lib.orc_hessvec.argtypes = [P, P, P, P, P, P, I, I, P, I]
     lib.orc_symbolic.argtypes = [P] + [P] * 7 + [P, P, P]
     lib.orc_lu_dense.argtypes = [P, P, P, P, P, P]
+    lib.orc_cholesky.argtypes = [I, P, I, P, I]
+    lib.orc_cholesky_solve.argtypes = [I, P, I, P, I, I]
     _lib = lib
     return lib
 
@@ -210,6 +212,22 @@ class OracleGrid:
             raise RuntimeError("oracle LU: singular pivot")
         return perm, L, U
 
+    # ---- real-time tracking step (section 6.3) ------------------------------
+    def rto_step(self, x, p, pd, qd):
+        """One tracking update at loads (pd, qd), eq. (18)-(19).
+
+        Step 1: reduced gradient g (eq. 7) and reduced Hessian H (Algorithm 1
+        applied to the columns of the identity) at the power-flow solution x.
+        Step 2: H = L L^T, d = -H^{-1} g, p_next = p + d.
+        """
+        lam, g, F = self.adjoint(x, p, pd, qd)
+        H = self.hessvec(x, p, pd, qd, np.eye(self.n_p))
+        L, info = cholesky(H)
+        if info:
+            raise RuntimeError(f"oracle Cholesky: pivot {info} is not positive")
+        d = -cholesky_solve(L, g)[:, 0]
+        return dict(g=g, F=F, H=H, L=L, d=d, p_next=_f64(p) + d)
+
     # ---- planted operating point ---------------------------------------------
     def plant(self, vm=None, va=None) -> State:
         """Loads and parameters that make the grid's planted voltages an exact solution.
@@ -235,3 +253,27 @@ class OracleGrid:
         pv = ip_pg >= 0
         p[ip_pg[pv]] = P[pv]
         return State(x, p, pd, qd)
+
+
+def cholesky(H):
+    """Lower Cholesky factor of the symmetric positive definite H (lower triangle read).
+
+    Returns (L, info): info = 0, or j + 1 for the first pivot that is not positive."""
+    lib = _load()
+    H = np.asfortranarray(H, dtype=np.float64)
+    n = H.shape[0]
+    L = np.zeros((n, n), order="F")
+    info = lib.orc_cholesky(n, _p(H), max(n, 1), _p(L), max(n, 1))
+    return L, int(info)
+
+
+def cholesky_solve(L, B):
+    """X with L L^T X = B (B a vector or n x nrhs)."""
+    lib = _load()
+    L = np.asfortranarray(L, dtype=np.float64)
+    X = np.array(B, dtype=np.float64, order="F", copy=True)
+    if X.ndim == 1:
+        X = X.reshape(-1, 1, order="F")
+    n = L.shape[0]
+    lib.orc_cholesky_solve(n, _p(L), max(n, 1), _p(X), X.shape[1], max(n, 1))
+    return X

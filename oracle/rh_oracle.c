@@ -28,7 +28,9 @@
  *       Hw  = y_p + J_p^T psi
  *     one direction at a time (Algorithm 1), no batching, no fusion.
  *   - the symbolic data of the factorization (ordering, patterns, levels),
- *     derived independently for bit-exact comparison with the library.
+ *     derived independently for bit-exact comparison with the library;
+ *   - the dense Cholesky factorisation and the two triangular solves of the
+ *     real-time tracking step (section 6.3, eq. 18-19).
  */
 #include <math.h>
 #include <stdint.h>
@@ -927,4 +929,53 @@ int orc_lu_dense(const orc_grid *g, const double *x, const double *p, int32_t *p
     }
     lu_free(&F); state_free(&s);
     return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* real-time tracking step, section 6.3 eq. (18)-(19)                       */
+/* ------------------------------------------------------------------------ */
+/* The paper's Step 2 solves H d = -g with a dense Cholesky factorisation.
+ * The oracle writes that factorisation out from its definition, row by row
+ * (the Cholesky-Banachiewicz order): for j = 0..n-1
+ *     L_jj = sqrt(H_jj - sum_{k<j} L_jk^2)
+ *     L_ij = (H_ij - sum_{k<j} L_ik L_jk) / L_jj        for i > j
+ * with sums in ascending k.  Only the lower triangle of H is read; L is
+ * written whole (zero above the diagonal).  Column-major, leading dimensions
+ * ldh, ldl.  Returns 0, or j + 1 for the first pivot H_jj - sum L_jk^2 that is
+ * not positive (L is then unspecified from column j on). */
+int orc_cholesky(int n, const double *H, int ldh, double *L, int ldl) {
+    for (int j = 0; j < n; j++)
+        for (int i = 0; i < j; i++) L[i + (size_t)j * ldl] = 0.0;
+    for (int j = 0; j < n; j++) {
+        double s = H[j + (size_t)j * ldh];
+        for (int k = 0; k < j; k++) s -= L[j + (size_t)k * ldl] * L[j + (size_t)k * ldl];
+        if (!(s > 0.0)) return j + 1;
+        double ljj = sqrt(s);
+        L[j + (size_t)j * ldl] = ljj;
+        for (int i = j + 1; i < n; i++) {
+            double t = H[i + (size_t)j * ldh];
+            for (int k = 0; k < j; k++) t -= L[i + (size_t)k * ldl] * L[j + (size_t)k * ldl];
+            L[i + (size_t)j * ldl] = t / ljj;
+        }
+    }
+    return 0;
+}
+
+/* Solve L L^T X = B in place for nrhs columns of B (leading dimension ldb):
+ * forward substitution L y = b (ascending rows), then back substitution
+ * L^T x = y (descending rows), each sum in ascending index order. */
+void orc_cholesky_solve(int n, const double *L, int ldl, double *B, int nrhs, int ldb) {
+    for (int c = 0; c < nrhs; c++) {
+        double *b = B + (size_t)c * ldb;
+        for (int i = 0; i < n; i++) {
+            double s = b[i];
+            for (int k = 0; k < i; k++) s -= L[i + (size_t)k * ldl] * b[k];
+            b[i] = s / L[i + (size_t)i * ldl];
+        }
+        for (int i = n - 1; i >= 0; i--) {
+            double s = b[i];
+            for (int k = i + 1; k < n; k++) s -= L[k + (size_t)i * ldl] * b[k];
+            b[i] = s / L[i + (size_t)i * ldl];
+        }
+    }
 }

@@ -371,3 +371,108 @@ def test_symbolic_ordering_patterns_levels(shape):
             if bus_of[c] != bus_of[r]:
                 lev[bus_of[r]] = max(lev[bus_of[r]], lev[bus_of[c]] + 1)
     assert (lev == sym["level"]).all()
+
+
+# ---------------------------------------------------------------------------
+# Real-time tracking step (section 6.3, eq. 18-19): dense Cholesky and solve
+# ---------------------------------------------------------------------------
+
+def _binom(n, k):
+    from math import comb
+    return comb(n, k)
+
+
+def test_cholesky_of_pascal_matrix_is_the_binomial_matrix():
+    """The symmetric Pascal matrix P_ij = C(i+j, i) factors as L L^T with
+    L_ij = C(i, j) (Vandermonde's identity): an exact integer closed form."""
+    from oracle import cholesky
+    n = 15
+    P = np.array([[_binom(i + j, i) for j in range(n)] for i in range(n)], dtype=float)
+    L, info = cholesky(P)
+    assert info == 0
+    expect = np.array([[_binom(i, j) if j <= i else 0 for j in range(n)] for i in range(n)], dtype=float)
+    assert np.array_equal(L, expect)
+
+
+def test_cholesky_of_second_difference_matrix_closed_form():
+    """tridiag(-1, 2, -1): L_kk = sqrt((k+2)/(k+1)), L_{k+1,k} = -sqrt((k+1)/(k+2)), zero elsewhere."""
+    from oracle import cholesky
+    n = 40
+    T = 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    L, info = cholesky(T)
+    assert info == 0
+    k = np.arange(n)
+    assert np.allclose(np.diag(L), np.sqrt((k + 2) / (k + 1)), rtol=1e-15, atol=0)
+    assert np.allclose(np.diag(L, -1), -np.sqrt((k[:-1] + 1) / (k[:-1] + 2)), rtol=1e-15, atol=0)
+    assert np.count_nonzero(L) == 2 * n - 1
+
+
+def test_cholesky_reads_the_lower_triangle_and_matches_a_library_factor():
+    from oracle import cholesky
+    rng = np.random.default_rng(11)
+    n = 57
+    A = rng.standard_normal((n, n))
+    H = A @ A.T / n + np.eye(n)
+    garbage = H + np.triu(rng.standard_normal((n, n)) * 1e3, 1)   # upper triangle must not be read
+    L, info = cholesky(garbage)
+    assert info == 0
+    assert np.array_equal(L, np.tril(L))
+    assert np.abs(L - np.linalg.cholesky(H)).max() <= 1e-13 * np.abs(L).max()
+    assert np.abs(L @ L.T - H).max() <= 1e-13 * np.abs(H).max()
+
+
+def test_cholesky_reports_the_first_non_positive_pivot():
+    from oracle import cholesky
+    assert cholesky(np.diag([4.0, 9.0, -1.0, 16.0]))[1] == 3
+    assert cholesky(np.array([[1.0, 2.0], [2.0, 1.0]]))[1] == 2       # 1 - 2^2 < 0
+    assert cholesky(np.array([[1.0, 1.0], [1.0, 1.0]]))[1] == 2       # singular: pivot exactly 0
+    assert cholesky(np.zeros((0, 0)))[1] == 0
+
+
+def test_cholesky_solve_is_exact_on_an_integer_system():
+    """Unit-diagonal integer L (Pascal): forward and back substitution are exact."""
+    from oracle import cholesky, cholesky_solve
+    n = 10
+    P = np.array([[_binom(i + j, i) for j in range(n)] for i in range(n)], dtype=float)
+    L, _ = cholesky(P)
+    X = np.random.default_rng(3).integers(-5, 6, size=(n, 3)).astype(float)
+    assert np.array_equal(cholesky_solve(L, P @ X), X)
+
+
+def test_tracking_step_is_the_newton_direction_of_the_reduced_objective():
+    """d = -H^{-1} grad F makes grad F(p + a d) = (1 - a) grad F(p) + O(a^2):
+    the residual must shrink by 4 when a halves (independent power-flow solves
+    and adjoint gradients at the moved parameters), F must decrease along d
+    (the paper's descent direction), and H d = -g must hold."""
+    g = gg.make_case("case118")
+    o = OracleGrid(g)
+    st = o.plant()
+    pd, qd = 1.05 * st.pd, 1.05 * st.qd
+    x, s, _, _ = o.newton(st.p, pd, qd, st.x)
+    assert s == 0
+    r = o.rto_step(x, st.p, pd, qd)
+    g0, d = r["g"], r["d"]
+    assert g0 @ d < 0
+    assert np.abs(r["H"] @ d + g0).max() <= 1e-11 * np.abs(g0).max()
+    res = []
+    for a in (1e-4, 2e-4):
+        xa, s, _, _ = o.newton(st.p + a * d, pd, qd, x)
+        assert s == 0
+        _, ga, Fa = o.adjoint(xa, st.p + a * d, pd, qd)
+        assert Fa < r["F"]
+        res.append(np.abs(ga - (1 - a) * g0).max())
+    assert res[0] <= 1e-3 * 1e-4 * np.abs(g0).max()
+    assert 3.9 < res[1] / res[0] < 4.1
+
+
+def test_tracking_step_refuses_an_indefinite_reduced_hessian():
+    """The 30-bus seed-4 grid has an indefinite reduced Hessian at its planted
+    point (H_00 < 0): the Cholesky step stops at the first pivot."""
+    from oracle import cholesky
+    o = OracleGrid(tiny(30, 41, 6, 4))
+    st = o.plant()
+    H = o.hessvec(st.x, st.p, st.pd, st.qd, np.eye(o.n_p))
+    assert H[0, 0] < 0 and np.linalg.eigvalsh(0.5 * (H + H.T))[0] < 0
+    assert cholesky(H)[1] == 1
+    with pytest.raises(RuntimeError, match="pivot 1"):
+        o.rto_step(st.x, st.p, st.pd, st.qd)

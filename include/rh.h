@@ -113,9 +113,10 @@ rh_status rh_grid_symbolic(const rh_grid *grid, int32_t *perm, int32_t *bus_orde
 rh_status rh_injections(rh_grid *grid, const double *vm, const double *va, double *P, double *Q);
 
 /*
- * Set the parameters p (host, n_p) and, optionally, the loads pd, qd (host,
- * n_bus each; NULL keeps the previous loads, initially zero).  Invalidates
- * the factors, lambda and the projection coefficients.
+ * Set the parameters p (host, n_p; NULL keeps the current parameters, e.g.
+ * those a tracking step applied on the device) and, optionally, the loads
+ * pd, qd (host, n_bus each; NULL keeps the previous loads, initially zero).
+ * Invalidates the factors, lambda and the projection coefficients.
  */
 rh_status rh_set_state(rh_grid *grid, const double *p, const double *pd, const double *qd);
 
@@ -245,6 +246,52 @@ rh_status rh_lagrangian_hessvec(rh_grid *grid, const double *V, int64_t ldv, int
  */
 rh_status rh_hessvec_noalloc(rh_grid *grid, const double *W, int64_t ldw, int32_t N,
                              double *HW, int64_t ldhw, void *stream);
+
+/*
+ * Dense FP64 Cholesky factorisation A = L L^T of a symmetric positive definite
+ * n x n matrix: the factorisation of the real-time tracking step (section 6.3,
+ * eq. 19), where the paper calls a vendor library.
+ *   A     DEVICE pointer, column-major, leading dimension lda >= n.  The lower
+ *         triangle is read and overwritten with L; the strictly upper triangle
+ *         is neither read nor written.
+ *   info  DEVICE pointer to one int32: 0, or j + 1 for the first column j whose
+ *         pivot (the diagonal of the Schur complement) is not positive, i.e. A
+ *         is not positive definite; L is then unspecified from column j on.
+ * Asynchronous on `stream` (the status only reports argument and launch
+ * errors; read info after the stream).  n = 0 only sets info to 0.
+ */
+rh_status rh_potrf(int32_t n, double *A, int64_t lda, int32_t *info, void *stream);
+
+/*
+ * Solve L L^T X = B in place with the factor written by rh_potrf (its lower
+ * triangle is read).  L, B, work are DEVICE pointers: B is n x nrhs
+ * column-major (ldb >= n); work holds n * nrhs doubles owned by the caller
+ * (the intermediate L^{-1} B).  Asynchronous on `stream`.
+ */
+rh_status rh_potrs(int32_t n, const double *L, int64_t ldl, double *B, int64_t ldb, int32_t nrhs, double *work,
+                   void *stream);
+
+/*
+ * One update of the real-time tracking algorithm (section 6.3, eq. 18-19) at
+ * the grid's current loads and state, after rh_adjoint (RH_ESTATE otherwise),
+ * which supplies the reduced gradient g:
+ *   Step 1, second half: H = Hess F, every column in one launch (rh_hessian
+ *           with RH_HESSIAN_CONCURRENT);
+ *   Step 2: H = L L^T (rh_potrf), d = -H^{-1} g (rh_potrs), p_next = p + d.
+ *   H       DEVICE, n_p x n_p column-major, ldh >= n_p; holds H with its lower
+ *           triangle replaced by L on return
+ *   d       DEVICE, n_p: the step
+ *   p_next  DEVICE, n_p, or NULL
+ *   info    DEVICE int32, as for rh_potrf; d and p_next are unspecified when
+ *           it is not 0
+ * flags: RH_RTO_APPLY also makes p_next the grid's parameters, as rh_set_state
+ * with unchanged loads would, but only if info is 0 (decided on the device);
+ * it invalidates the adjoint, and later calls on the grid are ordered after it.
+ * Asynchronous on `stream`.
+ */
+#define RH_RTO_APPLY 4u
+rh_status rh_rto_step(rh_grid *grid, double *H, int64_t ldh, double *d, double *p_next, int32_t *info,
+                      void *stream, uint32_t flags);
 
 /* Message of the last error on this thread ("" if none). */
 const char *rh_last_error(void);

@@ -86,6 +86,7 @@ struct rh_grid {
     double *d2 = nullptr, *asum = nullptr, *csum = nullptr, *pg_curv = nullptr, *gref_th = nullptr,
            *gref_v = nullptr, *gref_val = nullptr;
     double *tmp_bus = nullptr;     // 4 * n_bus scratch for rh_injections
+    double *rto_y = nullptr;       // n_p: workspace of the tracking step's solve
     double *pbuf = nullptr;        // n_p
     double *xbuf = nullptr;        // n_x
     // scalars: cref, c2ref, F
@@ -101,9 +102,11 @@ struct rh_grid {
 
     bool adjoint_ready = false;
     cudaGraphExec_t adj_exec = nullptr;   // captured device work of rh_adjoint
+    cudaEvent_t apply_done = nullptr;     // orders a tracking step's parameter update before later grid work
 
     ~rh_grid() {
         if (adj_exec) cudaGraphExecDestroy(adj_exec);
+        if (apply_done) cudaEventDestroy(apply_done);
         for (void* p : allocs) cudaFree(p);
         if (V) cudaFree(V);
         if (T) cudaFree(T);
@@ -291,6 +294,30 @@ __global__ void k_get_x(int n_bus, const int* ix_th, const int* ix_v, const doub
     if (i >= n_bus) return;
     if (ix_th[i] >= 0) x[ix_th[i]] = va[i];
     if (ix_v[i] >= 0) x[ix_v[i]] = vm[i];
+}
+
+// Tracking step (section 6.3): right-hand side -g, p_next = p + d, and the
+// optional hand-over of p_next to the grid, which only happens when the
+// factorisation reported no bad pivot.
+__global__ void k_rto_rhs(int n, const double* grad, double* d) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) d[i] = -grad[i];
+}
+
+__global__ void k_rto_next(int n, const double* p, const double* d, double* p_next) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p_next[i] = p[i] + d[i];
+}
+
+__global__ void k_rto_apply(int n_p, int n_bus, const int* info, const double* p_next, double* p, const int* ip_v,
+                            const int* ip_pg, double* vm, double* pg) {
+    if (*info != 0) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_p) p[i] = p_next[i];
+    if (i < n_bus) {
+        if (ip_v[i] >= 0) vm[i] = p_next[ip_v[i]];
+        pg[i] = ip_pg[i] >= 0 ? p_next[ip_pg[i]] : 0.0;
+    }
 }
 
 int nblk(int n, int t) { return (n + t - 1) / t; }
@@ -514,6 +541,7 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     RH_CUDA(g->alloc(g->gres, nx));
     RH_CUDA(g->alloc(g->lam, nx));
     RH_CUDA(g->alloc(g->grad, np));
+    RH_CUDA(g->alloc(g->rto_y, np));
     RH_CUDA(g->alloc(g->v1, g->rows()));
     RH_CUDA(g->alloc(g->inc_coef, g->n_inc));
     RH_CUDA(g->alloc(g->d2, nb));
@@ -588,11 +616,11 @@ rh_status rh_injections(rh_grid* g, const double* vm, const double* va, double* 
 }
 
 rh_status rh_set_state(rh_grid* g, const double* p, const double* pd, const double* qd) {
-    if (!g || !p) return fail(RH_EINVAL, "NULL argument");
+    if (!g) return fail(RH_EINVAL, "NULL grid");
     rh_status st = set_device(g);
     if (st) return st;
     int nb = g->S.n_bus;
-    RH_CUDA(cudaMemcpyAsync(g->pbuf, p, g->S.n_p * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+    if (p) RH_CUDA(cudaMemcpyAsync(g->pbuf, p, g->S.n_p * sizeof(double), cudaMemcpyHostToDevice, g->stream));
     if (pd) RH_CUDA(cudaMemcpyAsync(g->pd, pd, nb * sizeof(double), cudaMemcpyHostToDevice, g->stream));
     if (qd) RH_CUDA(cudaMemcpyAsync(g->qd, qd, nb * sizeof(double), cudaMemcpyHostToDevice, g->stream));
     k_set_p<<<nblk(nb, 128), 128, 0, g->stream>>>(nb, g->ip_v, g->ip_pg, g->pbuf, g->vm, g->pg);
@@ -1022,6 +1050,66 @@ rh_status rh_hessvec_noalloc(rh_grid* g, const double* W, int64_t ldw, int32_t N
     L.use_reach = 0;
     rh::launch_dirs(g->dir(), L, (cudaStream_t)stream);
     RH_CUDA(cudaGetLastError());
+    return RH_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Real-time tracking step (section 6.3, eq. 18-19)
+// ---------------------------------------------------------------------------
+extern "C" {
+
+rh_status rh_potrf(int32_t n, double* A, int64_t lda, int32_t* info, void* stream) {
+    if (n < 0 || !info) return fail(RH_EINVAL, "n must be >= 0 and info non-NULL");
+    if (n > 0 && (!A || lda < n)) return fail(RH_EINVAL, "bad A or leading dimension");
+    RH_CUDA(rh::launch_potrf(n, A, lda, info, nullptr, (cudaStream_t)stream));
+    return RH_OK;
+}
+
+rh_status rh_potrs(int32_t n, const double* L, int64_t ldl, double* B, int64_t ldb, int32_t nrhs, double* work,
+                   void* stream) {
+    if (n < 0 || nrhs < 0) return fail(RH_EINVAL, "n and nrhs must be >= 0");
+    if (n == 0 || nrhs == 0) return RH_OK;
+    if (!L || !B || !work || ldl < n || ldb < n) return fail(RH_EINVAL, "bad L, B, work or leading dimension");
+    RH_CUDA(rh::launch_potrs(n, L, ldl, B, ldb, nrhs, work, true, (cudaStream_t)stream));
+    return RH_OK;
+}
+
+rh_status rh_rto_step(rh_grid* g, double* H, int64_t ldh, double* d, double* p_next, int32_t* info, void* stream,
+                      uint32_t flags) {
+    if (!g) return fail(RH_EINVAL, "NULL grid");
+    const auto& S = g->S;
+    if (!H || ldh < S.n_p || !d || !info) return fail(RH_EINVAL, "bad H, leading dimension, d or info");
+    if (!g->adjoint_ready) return fail(RH_ESTATE, "rh_rto_step needs rh_adjoint for the current state");
+    rh_status st = set_device(g);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int np = S.n_p;
+    // Step 1 (second half): the reduced Hessian, all n_p columns in one launch
+    st = rh_hessian(g, np, H, ldh, stream, RH_HESSIAN_CONCURRENT | RH_DEVICE_PTRS);
+    if (st) return st;
+    // Step 2: H = L L^T with the forward solve L y = -g fused into the
+    // factorisation (y in rto_y), then L^T d = y; p_next = p + d
+    k_rto_rhs<<<nblk(np, 128), 128, 0, s>>>(np, g->grad, g->rto_y);
+    RH_CUDA(cudaGetLastError());
+    RH_CUDA(rh::launch_potrf(np, H, ldh, info, g->rto_y, s));
+    RH_CUDA(rh::launch_potrs(np, H, ldh, d, np, 1, g->rto_y, false, s));
+    double* pn = p_next ? p_next : g->rto_y;
+    if (p_next || (flags & RH_RTO_APPLY)) {
+        k_rto_next<<<nblk(np, 128), 128, 0, s>>>(np, g->pbuf, d, pn);
+        RH_CUDA(cudaGetLastError());
+    }
+    if (flags & RH_RTO_APPLY) {
+        int nt = std::max(np, S.n_bus);
+        k_rto_apply<<<nblk(nt, 128), 128, 0, s>>>(np, S.n_bus, info, pn, g->pbuf, g->ip_v, g->ip_pg, g->vm, g->pg);
+        RH_CUDA(cudaGetLastError());
+        g->adjoint_ready = false;
+        // the grid's own stream (power flow, adjoint) must see the new parameters
+        if (!g->apply_done) RH_CUDA(cudaEventCreateWithFlags(&g->apply_done, cudaEventDisableTiming));
+        RH_CUDA(cudaEventRecord(g->apply_done, s));
+        RH_CUDA(cudaStreamWaitEvent(g->stream, g->apply_done, 0));
+    }
     return RH_OK;
 }
 

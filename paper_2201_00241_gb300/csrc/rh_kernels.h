@@ -154,6 +154,17 @@ void launch_build_tail(int T, int t0, const int* pos, const double* A, const dou
 // one right-hand side in shared memory (requires solve1_fits(n_x))
 bool solve1_fits(int n_x);
 cudaError_t launch_solve1(const DirGrid& g, double* x, unsigned phases, cudaStream_t st);
+
+// Dense Cholesky of the tracking step (dense.cu).  A, L, B, work, y and info
+// are device pointers; column-major.  info receives 0 or the 1-based column of
+// the first pivot that is not positive.  launch_potrf with y != NULL also runs
+// the forward solve L y = b in place on the vector y (b on entry).
+// launch_potrs: work holds n * nrhs doubles; with forward = false it only runs
+// the backward sweep L^T X = work, writing X into B.
+int dense_tile(int n);
+cudaError_t launch_potrf(int n, double* A, int64_t lda, int* info, double* y, cudaStream_t s);
+cudaError_t launch_potrs(int n, const double* L, int64_t ldl, double* B, int64_t ldb, int nrhs, double* work,
+                         bool forward, cudaStream_t s);
 int dirs_default_ctas(int N);
 
 // adjoint helpers

@@ -16,14 +16,14 @@ import numpy as np
 from . import build as _build
 
 RH_OK, RH_EINVAL, RH_ENOMEM, RH_ESINGULAR, RH_ENOCONV, RH_ETIMEOUT, RH_ECUDA, RH_ESTATE = range(8)
-RH_HOST_PTRS, RH_DEVICE_PTRS, RH_HESSIAN_CONCURRENT = 0, 1, 2
+RH_HOST_PTRS, RH_DEVICE_PTRS, RH_HESSIAN_CONCURRENT, RH_RTO_APPLY = 0, 1, 2, 4
 _NAMES = ["RH_OK", "RH_EINVAL", "RH_ENOMEM", "RH_ESINGULAR", "RH_ENOCONV", "RH_ETIMEOUT", "RH_ECUDA", "RH_ESTATE"]
 
 # every symbol declared in include/rh.h
 EXPORTS = ["rh_grid_create", "rh_grid_destroy", "rh_grid_dims", "rh_grid_symbolic", "rh_injections",
            "rh_set_state", "rh_powerflow", "rh_adjoint", "rh_hessvec", "rh_hessian", "rh_solve", "rh_refactor",
            "rh_lagrangian_hessvec", "rh_hessvec_noalloc", "rh_hv_work_doubles", "rh_batch_hessvec",
-           "rh_last_error"]
+           "rh_potrf", "rh_potrs", "rh_rto_step", "rh_last_error"]
 
 
 class RHError(RuntimeError):
@@ -86,6 +86,9 @@ def load(build_if_missing: bool = True):
         "rh_hessvec_noalloc": ([P, P, I64, I32, P, I64, P], C.c_int),
         "rh_hv_work_doubles": ([P, I32], C.c_int64),
         "rh_batch_hessvec": ([I32, P, I32, P], C.c_int),
+        "rh_potrf": ([I32, P, I64, P, P], C.c_int),
+        "rh_potrs": ([I32, P, I64, P, I64, I32, P, P], C.c_int),
+        "rh_rto_step": ([P, P, I64, P, P, P, P, U32], C.c_int),
         "rh_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -178,8 +181,9 @@ class Grid:
         _check(_lib.rh_injections(self._h, _ptr(vm), _ptr(va), _ptr(P), _ptr(Q)))
         return P, Q
 
-    def set_state(self, p, pd=None, qd=None):
-        p = _f64(p)
+    def set_state(self, p=None, pd=None, qd=None):
+        """p None keeps the current parameters (for example those of a tracking step)."""
+        p = None if p is None else _f64(p)
         pd = None if pd is None else _f64(pd)
         qd = None if qd is None else _f64(qd)
         _check(_lib.rh_set_state(self._h, _ptr(p), _ptr(pd), _ptr(qd)))
@@ -259,6 +263,26 @@ class Grid:
                                           RH_HOST_PTRS))
         return Y
 
+    # ---- real-time tracking step (section 6.3) -------------------------------------
+    def rto_step(self, H=None, apply=False, stream=None):
+        """rh_rto_step at the current state (after adjoint()).  Returns CUDA
+        tensors d, p_next, H (n_p x n_p column-major, lower triangle = L) and the
+        pivot status info (0, or the 1-based column of the first bad pivot),
+        read after the stream finished."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        n = self.n_p
+        if H is None:
+            H = torch.empty((n, n), dtype=torch.float64, device=dev).t()
+        d = torch.empty(n, dtype=torch.float64, device=dev)
+        p_next = torch.empty(n, dtype=torch.float64, device=dev)
+        info = torch.empty(1, dtype=torch.int32, device=dev)
+        st = stream if stream is not None else C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        _check(_lib.rh_rto_step(self._h, _ptr(H), H.stride(1), _ptr(d), _ptr(p_next), _ptr(info), st,
+                                RH_RTO_APPLY if apply else 0))
+        torch.cuda.synchronize(dev)
+        return d, p_next, H, int(info.item())
+
     # ---- planted operating point -------------------------------------------------
     def index_maps(self):
         """(ix_th, ix_v, ip_v, ip_pg) per bus, from the documented index conventions."""
@@ -323,3 +347,38 @@ def batch_hessvec(items, width: int = 0, stream=None):
 
 def work_doubles(grid, N: int) -> int:
     return int(load().rh_hv_work_doubles(grid._h, int(N)))
+
+
+def _stream_arg(a, stream):
+    if stream is not None:
+        return stream
+    import torch
+    return C.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
+
+
+def potrf(A, info=None, stream=None):
+    """rh_potrf in place on a column-major CUDA float64 tensor A (n x n view with
+    stride(0) == 1).  Returns the device int32 tensor info (asynchronous)."""
+    import torch
+    n = A.shape[0]
+    assert A.shape == (n, n) and (n <= 1 or A.stride(0) == 1), "A must be a column-major n x n view"
+    if info is None:
+        info = torch.empty(1, dtype=torch.int32, device=A.device)
+    lda = A.stride(1) if n > 1 else max(n, 1)
+    _check(load().rh_potrf(n, _ptr(A), lda, _ptr(info), _stream_arg(A, stream)))
+    return info
+
+
+def potrs(L, B, work=None, stream=None):
+    """rh_potrs: B <- (L L^T)^{-1} B in place; B a column-major CUDA (n, nrhs) view or a vector."""
+    import torch
+    n = L.shape[0]
+    Bv = B.reshape(-1, 1) if B.dim() == 1 else B
+    nrhs = Bv.shape[1]
+    assert nrhs <= 1 or Bv.stride(0) == 1, "B must be column-major"
+    if work is None:
+        work = torch.empty(max(n * nrhs, 1), dtype=torch.float64, device=B.device)
+    ldl = L.stride(1) if n > 1 else max(n, 1)
+    ldb = Bv.stride(1) if nrhs > 1 else max(n, 1)
+    _check(load().rh_potrs(n, _ptr(L), ldl, _ptr(Bv), ldb, nrhs, _ptr(work), _stream_arg(B, stream)))
+    return B

@@ -56,6 +56,8 @@ def _load():
     lib.orc_symbolic.argtypes = [P] + [P] * 7 + [P, P, P]
     lib.orc_lu_dense.argtypes = [P, P, P, P, P, P]
     lib.orc_cholesky.argtypes = [I, P, I, P, I]
+    lib.orc_jacobians_csc.argtypes = [P, P, P] + [P] * 8
+    lib.orc_coloring.argtypes = [P, P, P, P, P]
     lib.orc_cholesky_solve.argtypes = [I, P, I, P, I, I]
     _lib = lib
     return lib
@@ -183,6 +185,30 @@ class OracleGrid:
         if st != 0:
             raise RuntimeError("oracle LU: singular pivot")
         return HW
+
+    def jacobians_csc(self, x, p):
+        """J_x, J_p as scipy CSC matrices with their structural pattern (explicit zeros kept)."""
+        import scipy.sparse as sp
+        x, p = _f64(x), _f64(p)
+        nx_, np_ = C.c_int64(0), C.c_int64(0)
+        null = C.c_void_p(0)
+        _lib.orc_jacobians_csc(self._h, _p(x), _p(p), null, null, null, null, null, null,
+                               C.byref(nx_), C.byref(np_))
+        a = dict(xp=np.empty(self.n_x + 1, np.int32), xi=np.empty(nx_.value, np.int32), xx=np.empty(nx_.value),
+                 pp=np.empty(self.n_p + 1, np.int32), pi=np.empty(np_.value, np.int32), px=np.empty(np_.value))
+        _lib.orc_jacobians_csc(self._h, _p(x), _p(p), _p(a["xp"]), _p(a["xi"]), _p(a["xx"]), _p(a["pp"]),
+                               _p(a["pi"]), _p(a["px"]), C.byref(nx_), C.byref(np_))
+        Jx = sp.csc_matrix((a["xx"], a["xi"], a["xp"]), shape=(self.n_x, self.n_x))
+        Jp = sp.csc_matrix((a["px"], a["pi"], a["pp"]), shape=(self.n_x, self.n_p))
+        return Jx, Jp
+
+    def coloring(self):
+        """Greedy column colourings of J_x and J_p (section 4.2.2): (colors_x, colors_p, n_colors_x, n_colors_p)."""
+        cx = np.empty(self.n_x, np.int32)
+        cp = np.empty(self.n_p, np.int32)
+        ncx, ncp = C.c_int32(0), C.c_int32(0)
+        _lib.orc_coloring(self._h, _p(cx), _p(cp), C.byref(ncx), C.byref(ncp))
+        return cx, cp, int(ncx.value), int(ncp.value)
 
     def symbolic(self):
         nnzL = C.c_int64(0)

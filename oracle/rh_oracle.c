@@ -979,3 +979,71 @@ void orc_cholesky_solve(int n, const double *L, int ldl, double *B, int nrhs, in
         }
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* sparse Jacobians and their column colouring (section 4.2.2, Fig. 2)       */
+/* ------------------------------------------------------------------------ */
+/* J_x and J_p at (x, p) in CSC (rows sorted, explicit zeros kept: the pattern
+ * is structural).  Two calls: with NULL arrays only the counts are returned. */
+void orc_jacobians_csc(const orc_grid *g, const double *x, const double *p,
+                       int32_t *jx_p, int32_t *jx_i, double *jx_x,
+                       int32_t *jp_p, int32_t *jp_i, double *jp_x, int64_t *nnz_x, int64_t *nnz_p) {
+    orc_state s; state_alloc(g, &s); state_from(g, x, p, &s);
+    csc Jx, Jp; jacobians(g, &s, &Jx, &Jp);
+    *nnz_x = Jx.p[Jx.nc];
+    *nnz_p = Jp.p[Jp.nc];
+    if (jx_p) {
+        for (int j = 0; j <= Jx.nc; j++) jx_p[j] = Jx.p[j];
+        for (int k = 0; k < Jx.p[Jx.nc]; k++) { jx_i[k] = Jx.i[k]; jx_x[k] = Jx.x[k]; }
+        for (int j = 0; j <= Jp.nc; j++) jp_p[j] = Jp.p[j];
+        for (int k = 0; k < Jp.p[Jp.nc]; k++) { jp_i[k] = Jp.i[k]; jp_x[k] = Jp.x[k]; }
+    }
+    csc_free(&Jx); csc_free(&Jp); state_free(&s);
+}
+
+/* Greedy column colouring of a CSC pattern: columns in ascending order, each
+ * takes the smallest colour that no earlier column sharing a row with it has.
+ * Columns of one colour then have disjoint row sets, so the product of the
+ * matrix with the 0/1 seed matrix of a colour recovers each of those columns
+ * exactly (the compression of Fig. 2).  Returns the number of colours. */
+static int greedy_colouring(const csc *A, int *colour) {
+    /* row -> columns (CSR of the pattern) */
+    int nr = A->nr, nc = A->nc, nz = A->p[nc];
+    int *rp = xcalloc(nr + 1, sizeof(int)), *rc = xcalloc(nz > 0 ? nz : 1, sizeof(int));
+    for (int k = 0; k < nz; k++) rp[A->i[k] + 1]++;
+    for (int r = 0; r < nr; r++) rp[r + 1] += rp[r];
+    int *fill = xcalloc(nr > 0 ? nr : 1, sizeof(int));
+    for (int r = 0; r < nr; r++) fill[r] = rp[r];
+    for (int j = 0; j < nc; j++)
+        for (int k = A->p[j]; k < A->p[j + 1]; k++) rc[fill[A->i[k]]++] = j;
+    int *used = xcalloc(nc + 1, sizeof(int));      /* used[c] == j + 1: colour c is taken for column j */
+    int ncol = 0;
+    for (int j = 0; j < nc; j++) {
+        for (int k = A->p[j]; k < A->p[j + 1]; k++) {
+            int r = A->i[k];
+            for (int t = rp[r]; t < rp[r + 1]; t++)
+                if (rc[t] < j) used[colour[rc[t]]] = j + 1;
+        }
+        int c = 0;
+        while (used[c] == j + 1) c++;
+        colour[j] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+    }
+    free(rp); free(rc); free(fill); free(used);
+    return ncol;
+}
+
+/* Colourings of the J_x columns (x order) and of the J_p columns (p order).
+ * The patterns are structural, so the state is irrelevant: a flat start. */
+void orc_coloring(const orc_grid *g, int32_t *colors_x, int32_t *colors_p, int32_t *n_colors_x, int32_t *n_colors_p) {
+    orc_state s; state_alloc(g, &s);
+    for (int i = 0; i < g->n_bus; i++) { s.vm[i] = 1.0; s.va[i] = 0.0; s.pg[i] = 0.0; }
+    csc Jx, Jp; jacobians(g, &s, &Jx, &Jp);
+    int *cx = xcalloc(g->n_x + 1, sizeof(int)), *cp = xcalloc(g->n_p + 1, sizeof(int));
+    *n_colors_x = greedy_colouring(&Jx, cx);
+    *n_colors_p = greedy_colouring(&Jp, cp);
+    for (int j = 0; j < g->n_x; j++) colors_x[j] = cx[j];
+    for (int j = 0; j < g->n_p; j++) colors_p[j] = cp[j];
+    free(cx); free(cp);
+    csc_free(&Jx); csc_free(&Jp); state_free(&s);
+}

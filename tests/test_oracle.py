@@ -476,3 +476,62 @@ def test_tracking_step_refuses_an_indefinite_reduced_hessian():
     assert cholesky(H)[1] == 1
     with pytest.raises(RuntimeError, match="pivot 1"):
         o.rto_step(st.x, st.p, st.pd, st.qd)
+
+
+# ---------------------------------------------------------------------------
+# Column colouring of the Jacobians (section 4.2.2, Fig. 2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["tiny30", "case118", "case1354"])
+def test_coloring_equals_library_greedy_on_the_column_intersection_graph(case):
+    """The oracle's colouring is the greedy colouring (columns in index order,
+    smallest colour unused by earlier conflicting columns) of the graph whose
+    edges join columns sharing a row: rebuilt here with scipy (pattern of
+    |J|^T |J|) and coloured by networkx's greedy routine in the same order."""
+    nx = pytest.importorskip("networkx")
+    g = tiny(30, 41, 6, 4) if case == "tiny30" else gg.make_case(case)
+    o = OracleGrid(g)
+    st = o.plant()
+    Jx, Jp = o.jacobians_csc(st.x, st.p)
+    cx, cp, ncx, ncp = o.coloring()
+    for J, col, nc in ((Jx, cx, ncx), (Jp, cp, ncp)):
+        S = J.copy()
+        S.data[:] = 1.0
+        C = (S.T @ S).tocoo()
+        G = nx.Graph()
+        G.add_nodes_from(range(J.shape[1]))
+        G.add_edges_from((int(a), int(b)) for a, b in zip(C.row, C.col) if a != b)
+        ref = nx.coloring.greedy_color(G, strategy=lambda G, colors: sorted(G.nodes()))
+        assert [ref[q] for q in range(J.shape[1])] == list(col)
+        assert nc == max(ref.values()) + 1
+
+
+@pytest.mark.parametrize("case", ["case118", "case9241"])
+def test_coloring_compresses_the_jacobian_exactly(case):
+    """Fig. 2: J times the 0/1 seed of a colour holds, in every row, the one
+    entry of that colour's columns; so every structural entry is recovered
+    bit for bit, and no colouring can use fewer colours than the widest row."""
+    o = OracleGrid(gg.make_case(case))
+    st = o.plant()
+    Jx, Jp = o.jacobians_csc(st.x, st.p)
+    cx, cp, ncx, ncp = o.coloring()
+    for J, col, nc in ((Jx, cx, ncx), (Jp, cp, ncp)):
+        seeds = np.zeros((J.shape[1], nc))
+        seeds[np.arange(J.shape[1]), col] = 1.0
+        comp = J @ seeds                                  # n_rows x n_colours
+        coo = J.tocoo()
+        assert np.array_equal(comp[coo.row, col[coo.col]], coo.data)
+        assert nc >= np.diff(J.tocsr().indptr).max()
+        # columns of one colour never share a row
+        for c in range(nc):
+            sub = J[:, np.flatnonzero(col == c)]
+            sub.data[:] = 1.0
+            assert (sub.sum(axis=1) <= 1).all()
+
+
+def test_sparse_jacobians_equal_the_dense_ones():
+    o = OracleGrid(tiny(30, 41, 6, 4))
+    st = o.plant()
+    Jx, Jp = o.jacobians_csc(st.x, st.p)
+    jx, jp = o.jacobians_dense(st.x, st.p)
+    assert np.array_equal(Jx.toarray(), jx) and np.array_equal(Jp.toarray(), jp)

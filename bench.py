@@ -292,6 +292,25 @@ def measure_rto(n_updates=12):
             "paper_v100_s": {"step1": 0.05, "step2": 0.05, "total": 0.10, "cpu_total": 2.22}}
 
 
+def measure_jacobian_ad(reps=10):
+    """Coloured forward-mode Jacobian (section 4.2.2) against the analytic assembly on the
+    9241-bus grid: colour counts, and the per-state setup (rh_adjoint: assembly, refactor,
+    adjoint) with each assembly method."""
+    from paper_2201_00241_gb300 import rh
+    lg = _ready("case9241")
+    lib = rh.load()
+    _, _, ncx, ncp = lg.coloring()
+    out = {"workload": "case9241: J_x (n_x columns) and J_p (n_p columns) at the planted point",
+           "n_x": lg.n_x, "n_p": lg.n_p, "colors_x": ncx, "colors_p": ncp,
+           "tangent_passes": (ncx + ncp + 7) // 8}
+    for method in ("analytic", "ad"):
+        lg.set_jacobian_method(method)
+        rh._check(lib.rh_adjoint(lg._h, None, None, None))
+        out[f"setup_ms_{method}"] = _event_ms(lambda: rh._check(lib.rh_adjoint(lg._h, None, None, None)), reps)
+    lg.set_jacobian_method("analytic")
+    return out
+
+
 def measure_plain_paths(lg, n_single=32, reps=3):
     """The plain one-direction-at-a-time path and the one-launch-per-block full Hessian."""
     import torch
@@ -536,6 +555,7 @@ def main():
         line["scenario_batching"] = measure_scenarios()
         line["serving"] = measure_serving()
         line["tracking_step"] = measure_rto()
+        line["jacobian_ad"] = measure_jacobian_ad()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.case)
     print(json.dumps(line), flush=True)

@@ -293,6 +293,36 @@ rh_status rh_potrs(int32_t n, const double *L, int64_t ldl, double *B, int64_t l
 rh_status rh_rto_step(rh_grid *grid, double *H, int64_t ldh, double *d, double *p_next, int32_t *info,
                       void *stream, uint32_t flags);
 
+/*
+ * Coloured forward-mode Jacobian (section 4.2.2, Fig. 2): the paper assembles
+ * J_x and J_p by forward-mode AD on dual numbers, with the columns compressed
+ * by a colouring.  Here the colouring is greedy: columns in index order (x
+ * order for J_x, p order for J_p), each taking the smallest colour that no
+ * earlier column sharing a row with it holds.  The injections are evaluated on
+ * dual numbers seeded with the unit tangent of each variable's colour, 8
+ * colours per pass, and every structural entry is read from the tangent of
+ * its column's colour.
+ *
+ * rh_set_jacobian_method: the assembly used by every later rh_powerflow,
+ * rh_adjoint and rh_refactor on the grid (RH_JAC_ANALYTIC, the default, or
+ * RH_JAC_COLORED_AD).  Invalidates the adjoint.
+ *
+ * rh_grid_coloring (host outputs, any pointer may be NULL; works on a
+ * symbolic-only grid): colors_x[n_x], colors_p[n_p] and the colour counts.
+ *
+ * rh_jacobian: J_x and J_p at the current state by `method`, as host triplets
+ * in x / p indices: nnz_jx entries of J_x sorted by (row, column) and nnz_jp
+ * entries of J_p (rh_dims); any pointer may be NULL.  Overwrites the factors,
+ * so rh_adjoint is needed again before rh_hessvec.  Synchronous.
+ */
+#define RH_JAC_ANALYTIC 0
+#define RH_JAC_COLORED_AD 1
+rh_status rh_set_jacobian_method(rh_grid *grid, int32_t method);
+rh_status rh_grid_coloring(const rh_grid *grid, int32_t *colors_x, int32_t *colors_p, int32_t *n_colors_x,
+                           int32_t *n_colors_p);
+rh_status rh_jacobian(rh_grid *grid, int32_t method, int32_t *jx_row, int32_t *jx_col, double *jx_val,
+                      int32_t *jp_row, int32_t *jp_col, double *jp_val);
+
 /* Message of the last error on this thread ("" if none). */
 const char *rh_last_error(void);
 

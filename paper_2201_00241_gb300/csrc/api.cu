@@ -54,6 +54,8 @@ struct rh_grid {
     double *G = nullptr, *B = nullptr;
     int *qth = nullptr, *qv = nullptr, *ip_v = nullptr, *ip_pg = nullptr, *ix_th = nullptr, *ix_v = nullptr;
     int *pg_slot = nullptr, *jac_dst = nullptr;
+    int *col_th = nullptr, *col_v = nullptr, *col_pg = nullptr;   // seed colours (coloured AD)
+    int jac_method = RH_JAC_ANALYTIC;
     double *c2 = nullptr, *c1 = nullptr;
     int *rowptr = nullptr, *col = nullptr, *diagpos = nullptr, *tpos = nullptr, *q0 = nullptr;
     uint8_t* nv = nullptr;
@@ -222,6 +224,19 @@ rh_status check_err_flag(rh_grid* g) {
     return RH_OK;
 }
 
+// Injections, residual (when gres is given) and the values of J_x (into the
+// slots of A, zeroed by the caller) and J_p, by the analytic formulas or by
+// coloured forward-mode AD (enqueue only).
+rh_status assemble(rh_grid* g, int method, double* gres, cudaStream_t s) {
+    const bool ad = (method == RH_JAC_COLORED_AD);
+    rh::launch_pf_eval(g->pf(), g->st(), gres, g->A, g->jpv, g->umax, g->umax + 1, !ad, s);
+    if (ad)
+        RH_CUDA(rh::launch_jac_ad(g->pf(), g->st(), g->col_th, g->col_v, g->col_pg,
+                                  g->S.n_colors_x + g->S.n_colors_p, g->A, g->jpv, g->umax + 1, s));
+    RH_CUDA(cudaGetLastError());
+    return RH_OK;
+}
+
 // J_x, J_p at the current state, refactorisation, transposed copies (enqueue only).
 rh_status enqueue_factor(rh_grid* g) {
     const auto& S = g->S;
@@ -229,7 +244,8 @@ rh_status enqueue_factor(rh_grid* g) {
     RH_CUDA(cudaMemsetAsync(g->A, 0, sizeof(double) * S.col.size(), s));
     RH_CUDA(cudaMemsetAsync(g->umax, 0, 2 * sizeof(unsigned long long), s));
     RH_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
-    rh::launch_pf_eval(g->pf(), g->st(), nullptr, g->A, g->jpv, g->umax, g->umax + 1, true, s);
+    rh_status st = assemble(g, g->jac_method, nullptr, s);
+    if (st) return st;
     RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_tgt_lev_ptr.data(), S.rf_n_lev, s));
     rh::launch_transpose_values((int)S.col.size(), g->tpos, g->A, g->At, (int)S.jp_col.size(), g->jpt_src, g->jpv,
                                 g->jptv, s);
@@ -393,6 +409,9 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     RH_CUDA(g->upload(g->ix_v, S.ix_v));
     RH_CUDA(g->upload(g->pg_slot, S.pg_slot));
     RH_CUDA(g->upload(g->jac_dst, S.jac_dst));
+    RH_CUDA(g->upload(g->col_th, S.col_th));
+    RH_CUDA(g->upload(g->col_v, S.col_v));
+    RH_CUDA(g->upload(g->col_pg, S.col_pg));
     RH_CUDA(g->upload(g->c2, c2v));
     RH_CUDA(g->upload(g->c1, c1v));
     RH_CUDA(g->upload(g->rowptr, S.rowptr));
@@ -651,7 +670,8 @@ rh_status rh_powerflow(rh_grid* g, const double* x0, double tol, int32_t max_ite
         RH_CUDA(cudaMemsetAsync(g->A, 0, sizeof(double) * S.col.size(), s));
         RH_CUDA(cudaMemsetAsync(g->umax, 0, 2 * sizeof(unsigned long long), s));
         RH_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
-        rh::launch_pf_eval(g->pf(), g->st(), g->gres, g->A, g->jpv, g->umax, g->umax + 1, true, s);
+        st = assemble(g, g->jac_method, g->gres, s);
+        if (st) return st;
         unsigned long long bits = 0;
         RH_CUDA(cudaMemcpyAsync(&bits, g->umax, sizeof(bits), cudaMemcpyDeviceToHost, s));
         RH_CUDA(cudaStreamSynchronize(s));
@@ -1110,6 +1130,68 @@ rh_status rh_rto_step(rh_grid* g, double* H, int64_t ldh, double* d, double* p_n
         RH_CUDA(cudaEventRecord(g->apply_done, s));
         RH_CUDA(cudaStreamWaitEvent(g->stream, g->apply_done, 0));
     }
+    return RH_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Coloured forward-mode Jacobian (section 4.2.2, Fig. 2)
+// ---------------------------------------------------------------------------
+extern "C" {
+
+rh_status rh_set_jacobian_method(rh_grid* g, int32_t method) {
+    if (!g) return fail(RH_EINVAL, "NULL grid");
+    if (method != RH_JAC_ANALYTIC && method != RH_JAC_COLORED_AD) return fail(RH_EINVAL, "unknown Jacobian method");
+    if (method == g->jac_method) return RH_OK;
+    g->jac_method = method;
+    g->adjoint_ready = false;
+    if (g->adj_exec) {                 // the captured setup holds the previous assembly kernel
+        cudaGraphExecDestroy(g->adj_exec);
+        g->adj_exec = nullptr;
+    }
+    return RH_OK;
+}
+
+rh_status rh_grid_coloring(const rh_grid* g, int32_t* colors_x, int32_t* colors_p, int32_t* n_colors_x,
+                           int32_t* n_colors_p) {
+    if (!g) return fail(RH_EINVAL, "NULL grid");
+    const auto& S = g->S;
+    if (colors_x) std::copy(S.colors_x.begin(), S.colors_x.end(), colors_x);
+    if (colors_p) std::copy(S.colors_p.begin(), S.colors_p.end(), colors_p);
+    if (n_colors_x) *n_colors_x = S.n_colors_x;
+    if (n_colors_p) *n_colors_p = S.n_colors_p;
+    return RH_OK;
+}
+
+rh_status rh_jacobian(rh_grid* g, int32_t method, int32_t* jx_row, int32_t* jx_col, double* jx_val, int32_t* jp_row,
+                      int32_t* jp_col, double* jp_val) {
+    if (!g) return fail(RH_EINVAL, "NULL grid");
+    if (method != RH_JAC_ANALYTIC && method != RH_JAC_COLORED_AD) return fail(RH_EINVAL, "unknown Jacobian method");
+    rh_status st = set_device(g);
+    if (st) return st;
+    const auto& S = g->S;
+    cudaStream_t s = g->stream;
+    g->adjoint_ready = false;          // the factors in A are overwritten
+    RH_CUDA(cudaMemsetAsync(g->A, 0, sizeof(double) * S.col.size(), s));
+    RH_CUDA(cudaMemsetAsync(g->umax, 0, 2 * sizeof(unsigned long long), s));
+    st = assemble(g, method, nullptr, s);
+    if (st) return st;
+    std::vector<double> A(S.col.size()), jp(S.jp_col.size());
+    if (!A.empty()) RH_CUDA(cudaMemcpyAsync(A.data(), g->A, A.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (!jp.empty()) RH_CUDA(cudaMemcpyAsync(jp.data(), g->jpv, jp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RH_CUDA(cudaStreamSynchronize(s));
+    for (size_t k = 0; k < S.jx_slot.size(); k++) {
+        if (jx_row) jx_row[k] = S.jx_row[k];
+        if (jx_col) jx_col[k] = S.jx_col[k];
+        if (jx_val) jx_val[k] = A[S.jx_slot[k]];
+    }
+    for (int q = 0; q < S.n_x; q++)
+        for (int t = S.jp_ptr[q]; t < S.jp_ptr[q + 1]; t++) {
+            if (jp_row) jp_row[t] = S.jp_xrow[q];
+            if (jp_col) jp_col[t] = S.jp_col[t];
+            if (jp_val) jp_val[t] = jp[t];
+        }
     return RH_OK;
 }
 

@@ -129,6 +129,106 @@ __global__ void k_newton_update(PfGrid g, PfState s, const double* dx) {
 }
 
 // ---------------------------------------------------------------------------
+// coloured forward-mode Jacobian (section 4.2.2, Fig. 2)
+// ---------------------------------------------------------------------------
+// A dual number carries a value and CH tangent components.  Every variable of
+// x and p is seeded with the unit tangent of its column colour, so the
+// tangent c of a residual row is the sum of that row's derivatives over the
+// columns of colour c, which the colouring makes a single entry.  Colours are
+// processed CH at a time (one grid row per chunk; the values are recomputed in
+// every chunk, as in chunked forward mode).
+
+template <int CH>
+struct Dual {
+    double v;
+    double d[CH];
+};
+
+template <int CH>
+__device__ __forceinline__ Dual<CH> dual_seed(double v, int k) {
+    Dual<CH> r;
+    r.v = v;
+#pragma unroll
+    for (int m = 0; m < CH; m++) r.d[m] = (m == k) ? 1.0 : 0.0;
+    return r;
+}
+
+template <int CH>
+__global__ void __launch_bounds__(128) k_jac_ad(PfGrid g, PfState s, const int* __restrict__ col_th,
+                                                const int* __restrict__ col_v, const int* __restrict__ col_pg,
+                                                double* A, double* jpv, unsigned long long* jmax) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_bus || g.qth[i] < 0) return;      // the slack has no rows
+    const int c0 = blockIdx.y * CH;
+    const Dual<CH> th_i = dual_seed<CH>(s.va[i], col_th[i] - c0);
+    const Dual<CH> v_i = dual_seed<CH>(s.vm[i], col_v[i] - c0);
+    // P_i / v_i and Q_i / v_i accumulated over the admittance row (eq. 2)
+    Dual<CH> p = dual_seed<CH>(0.0, -1), q = dual_seed<CH>(0.0, -1);
+    for (int t = g.yp[i]; t < g.yp[i + 1]; t++) {
+        const int j = g.yj[t];
+        const double G = g.G[t], B = g.B[t];
+        const int kth = col_th[j] - c0, kv = col_v[j] - c0;
+        double sn, cs;
+        sincos(th_i.v - s.va[j], &sn, &cs);
+        const double vj = s.vm[j];
+        const double gc = G * cs + B * sn, gs = G * sn - B * cs;   // value parts of the two brackets
+        p.v = fma(vj, gc, p.v);
+        q.v = fma(vj, gs, q.v);
+#pragma unroll
+        for (int m = 0; m < CH; m++) {
+            // d(theta_i - theta_j); d cos = -sin d(.), d sin = cos d(.)
+            const double da = th_i.d[m] - (m == kth ? 1.0 : 0.0);
+            const double dvj = (m == kv) ? 1.0 : 0.0;
+            const double dgc = (B * cs - G * sn) * da;              // d(G cos + B sin)
+            const double dgs = (G * cs + B * sn) * da;              // d(G sin - B cos)
+            p.d[m] = fma(vj, dgc, fma(dvj, gc, p.d[m]));
+            q.d[m] = fma(vj, dgs, fma(dvj, gs, q.d[m]));
+        }
+    }
+    // g_P = v_i p - Pg_i + Pd_i,  g_Q = v_i q + Qd_i
+    Dual<CH> gP, gQ;
+    const int kpg = col_pg[i] - c0;
+    gP.v = v_i.v * p.v;
+    gQ.v = v_i.v * q.v;
+#pragma unroll
+    for (int m = 0; m < CH; m++) {
+        gP.d[m] = fma(v_i.v, p.d[m], v_i.d[m] * p.v) - (m == kpg ? 1.0 : 0.0);
+        gQ.d[m] = fma(v_i.v, q.d[m], v_i.d[m] * q.v);
+    }
+    // uncompress: each structural entry reads the tangent of its column's colour
+    unsigned long long jm = 0;
+    for (int t = g.yp[i]; t < g.yp[i + 1]; t++) {
+        const int j = g.yj[t];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int dst = g.jac_dst[4 * t + u];
+            if (dst == -1) continue;
+            const int k = ((u & 1) ? col_v[j] : col_th[j]) - c0;
+            if (k < 0 || k >= CH) continue;
+            double val = 0.0;
+#pragma unroll
+            for (int m = 0; m < CH; m++)
+                if (m == k) val = (u < 2) ? gP.d[m] : gQ.d[m];
+            if (dst >= 0) {
+                A[dst] = val;
+                const unsigned long long b = ordered_bits(val);
+                jm = b > jm ? b : jm;
+            } else {
+                jpv[-(dst + 2)] = val;
+            }
+        }
+    }
+    if (kpg >= 0 && kpg < CH) {
+        double val = 0.0;
+#pragma unroll
+        for (int m = 0; m < CH; m++)
+            if (m == kpg) val = gP.d[m];
+        jpv[g.pg_slot[i]] = val;
+    }
+    if (jm) atomicMax(jmax, jm);
+}
+
+// ---------------------------------------------------------------------------
 // fixed-pattern LU refactorisation (row-wise elimination, static pivots)
 // ---------------------------------------------------------------------------
 
@@ -927,6 +1027,15 @@ void launch_injections(const PfGrid& g, const PfState& s, cudaStream_t st) {
 void launch_pf_eval(const PfGrid& g, const PfState& s, double* gres, double* A, double* jpv,
                     unsigned long long* gmax, unsigned long long* jmax, bool want_jac, cudaStream_t st) {
     if (g.n_bus > 0) k_pf_eval<<<blocks_for(g.n_bus, 128), 128, 0, st>>>(g, s, gres, A, jpv, gmax, jmax, want_jac);
+}
+
+cudaError_t launch_jac_ad(const PfGrid& g, const PfState& s, const int* col_th, const int* col_v, const int* col_pg,
+                          int n_colors, double* A, double* jpv, unsigned long long* jmax, cudaStream_t st) {
+    constexpr int CH = 8;
+    if (g.n_bus == 0 || n_colors == 0) return cudaSuccess;
+    dim3 grid((unsigned)blocks_for(g.n_bus, 128), (unsigned)((n_colors + CH - 1) / CH));
+    k_jac_ad<CH><<<grid, 128, 0, st>>>(g, s, col_th, col_v, col_pg, A, jpv, jmax);
+    return cudaGetLastError();
 }
 
 void launch_newton_update(const PfGrid& g, const PfState& s, const double* dx, cudaStream_t st) {

@@ -76,6 +76,18 @@ struct Symbolic {
     std::vector<int> jpt_ptr, jpt_row, jpt_src;
     std::vector<int> pg_slot;               // bus id -> Jp slot of its Pg column (-1)
     int64_t nnz_jx = 0;
+
+    // Column colouring for the coloured forward-mode Jacobian (section 4.2.2):
+    // J_x columns in x order and J_p columns in p order, each greedily given the
+    // smallest colour not held by an earlier column that shares a row with it.
+    std::vector<int> colors_x, colors_p;
+    int n_colors_x = 0, n_colors_p = 0;
+    // seed colour of each bus variable in the combined space [0, n_colors_x +
+    // n_colors_p), J_p colours following the J_x ones; -1 where not a variable
+    std::vector<int> col_th, col_v, col_pg;
+    // structural J_x entries in x indices, sorted by (row, column), with their
+    // slot in A; J_p rows in x indices (per internal row)
+    std::vector<int> jx_slot, jx_row, jx_col, jp_xrow;
 };
 
 // Builds everything above.  Returns an empty string on success, else a message.

@@ -127,6 +127,12 @@ void launch_injections(const PfGrid& g, const PfState& s, cudaStream_t st);
 void launch_pf_eval(const PfGrid& g, const PfState& s, double* gres, double* A, double* jpv,
                     unsigned long long* gmax, unsigned long long* jmax, bool want_jac, cudaStream_t st);
 void launch_newton_update(const PfGrid& g, const PfState& s, const double* dx, cudaStream_t st);
+// Coloured forward-mode Jacobian (section 4.2.2): the injections evaluated on
+// dual numbers whose tangents are the seed colours (col_th, col_v, col_pg per
+// bus), in chunks of tangents; writes the J_x slots of A (and max |J_x| into
+// jmax) and the J_p values.  The residual comes from launch_pf_eval.
+cudaError_t launch_jac_ad(const PfGrid& g, const PfState& s, const int* col_th, const int* col_v, const int* col_pg,
+                          int n_colors, double* A, double* jpv, unsigned long long* jmax, cudaStream_t st);
 // Fixed-pattern LU refactorisation data (device pointers).
 struct RfGrid {
     int n_x, t0, T;                    // dense trailing block [t0, n_x), T = n_x - t0

@@ -59,6 +59,28 @@ int find_in_row(const std::vector<int>& rowptr, const std::vector<int>& col, int
     return (int)(it - col.begin());
 }
 
+// Greedy column colouring from row -> column lists: columns in ascending
+// order, each taking the smallest colour that no earlier column sharing one of
+// its rows holds.  Returns the number of colours.
+int greedy_columns(int n_cols, const std::vector<std::vector<int>>& row_cols, std::vector<int>& colour) {
+    std::vector<std::vector<int>> col_rows(n_cols);
+    for (int r = 0; r < (int)row_cols.size(); r++)
+        for (int c : row_cols[r]) col_rows[c].push_back(r);
+    colour.assign(n_cols, -1);
+    std::vector<int> stamp(n_cols + 1, -1);
+    int n_colours = 0;
+    for (int c = 0; c < n_cols; c++) {
+        for (int r : col_rows[c])
+            for (int d : row_cols[r])
+                if (d < c) stamp[colour[d]] = c;
+        int k = 0;
+        while (stamp[k] == c) k++;
+        colour[c] = k;
+        n_colours = std::max(n_colours, k + 1);
+    }
+    return n_colours;
+}
+
 }  // namespace
 
 std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int32_t* to,
@@ -342,6 +364,61 @@ std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int
     S.pg_slot.assign(n_bus, -1);
     for (int i = 0; i < n_bus; i++)
         if (S.ip_pg[i] >= 0) S.pg_slot[i] = jp_slot(S.qth[i], S.ip_pg[i]);
+    // ---- column colouring of J_x and J_p (coloured forward-mode AD) --------
+    {
+        std::vector<std::vector<int>> xrows(S.n_x), prows(S.n_x);   // row (x index) -> columns
+        for (int i = 0; i < n_bus; i++) {
+            int rows[2] = {S.qth[i], S.qv[i]};
+            for (int a = 0; a < 2; a++) {
+                if (rows[a] < 0) continue;
+                int r = S.perm[rows[a]];
+                for (int s = S.yp[i]; s < S.yp[i + 1]; s++) {
+                    int j = S.yj[s];
+                    if (S.qth[j] >= 0) xrows[r].push_back(S.perm[S.qth[j]]);
+                    if (S.qv[j] >= 0) xrows[r].push_back(S.perm[S.qv[j]]);
+                    else if (S.ip_v[j] >= 0) prows[r].push_back(S.ip_v[j]);
+                }
+                if (a == 0 && S.ip_pg[i] >= 0) prows[r].push_back(S.ip_pg[i]);
+            }
+        }
+        S.n_colors_x = greedy_columns(S.n_x, xrows, S.colors_x);
+        S.n_colors_p = greedy_columns(S.n_p, prows, S.colors_p);
+        S.col_th.assign(n_bus, -1);
+        S.col_v.assign(n_bus, -1);
+        S.col_pg.assign(n_bus, -1);
+        for (int j = 0; j < n_bus; j++) {
+            if (S.qth[j] >= 0) S.col_th[j] = S.colors_x[S.perm[S.qth[j]]];
+            if (S.qv[j] >= 0) S.col_v[j] = S.colors_x[S.perm[S.qv[j]]];
+            else if (S.ip_v[j] >= 0) S.col_v[j] = S.n_colors_x + S.colors_p[S.ip_v[j]];
+            if (S.ip_pg[j] >= 0) S.col_pg[j] = S.n_colors_x + S.colors_p[S.ip_pg[j]];
+        }
+        // structural J_x entries for export, sorted by (row, column) in x indices
+        std::vector<std::tuple<int, int, int>> e;
+        e.reserve((size_t)S.nnz_jx);
+        for (int i = 0; i < n_bus; i++) {
+            int rows[2] = {S.qth[i], S.qv[i]};
+            for (int s = S.yp[i]; s < S.yp[i + 1]; s++) {
+                int j = S.yj[s];
+                for (int a = 0; a < 2; a++)
+                    for (int u = 0; u < 2; u++) {
+                        int dst = S.jac_dst[4 * s + 2 * a + u];
+                        int cq = u == 0 ? S.qth[j] : S.qv[j];
+                        if (dst >= 0) e.emplace_back(S.perm[rows[a]], S.perm[cq], dst);
+                    }
+            }
+        }
+        std::sort(e.begin(), e.end());
+        S.jx_row.resize(e.size());
+        S.jx_col.resize(e.size());
+        S.jx_slot.resize(e.size());
+        for (size_t k = 0; k < e.size(); k++) {
+            S.jx_row[k] = std::get<0>(e[k]);
+            S.jx_col[k] = std::get<1>(e[k]);
+            S.jx_slot[k] = std::get<2>(e[k]);
+        }
+        S.jp_xrow.resize(S.n_x);
+        for (int q = 0; q < S.n_x; q++) S.jp_xrow[q] = S.perm[q];
+    }
     // transpose of J_p: rows = p index
     S.jpt_ptr.assign(S.n_p + 1, 0);
     for (int c : S.jp_col) S.jpt_ptr[c + 1]++;

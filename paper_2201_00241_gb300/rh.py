@@ -23,7 +23,9 @@ _NAMES = ["RH_OK", "RH_EINVAL", "RH_ENOMEM", "RH_ESINGULAR", "RH_ENOCONV", "RH_E
 EXPORTS = ["rh_grid_create", "rh_grid_destroy", "rh_grid_dims", "rh_grid_symbolic", "rh_injections",
            "rh_set_state", "rh_powerflow", "rh_adjoint", "rh_hessvec", "rh_hessian", "rh_solve", "rh_refactor",
            "rh_lagrangian_hessvec", "rh_hessvec_noalloc", "rh_hv_work_doubles", "rh_batch_hessvec",
-           "rh_potrf", "rh_potrs", "rh_rto_step", "rh_last_error"]
+           "rh_potrf", "rh_potrs", "rh_rto_step", "rh_set_jacobian_method", "rh_grid_coloring", "rh_jacobian",
+           "rh_last_error"]
+RH_JAC_ANALYTIC, RH_JAC_COLORED_AD = 0, 1
 
 
 class RHError(RuntimeError):
@@ -89,6 +91,9 @@ def load(build_if_missing: bool = True):
         "rh_potrf": ([I32, P, I64, P, P], C.c_int),
         "rh_potrs": ([I32, P, I64, P, I64, I32, P, P], C.c_int),
         "rh_rto_step": ([P, P, I64, P, P, P, P, U32], C.c_int),
+        "rh_set_jacobian_method": ([P, I32], C.c_int),
+        "rh_grid_coloring": ([P, P, P, P, P], C.c_int),
+        "rh_jacobian": ([P, I32, P, P, P, P, P, P], C.c_int),
         "rh_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -262,6 +267,27 @@ class Grid:
         _check(_lib.rh_lagrangian_hessvec(self._h, _ptr(V), nu, V.shape[1], _ptr(Y), nu, C.c_void_p(0),
                                           RH_HOST_PTRS))
         return Y
+
+    # ---- coloured forward-mode Jacobian (section 4.2.2) ----------------------------
+    def set_jacobian_method(self, method: str):
+        """'analytic' (default) or 'ad' (coloured forward-mode AD) for every later assembly."""
+        _check(_lib.rh_set_jacobian_method(self._h, {"analytic": RH_JAC_ANALYTIC, "ad": RH_JAC_COLORED_AD}[method]))
+
+    def coloring(self):
+        cx = np.empty(self.n_x, np.int32)
+        cp = np.empty(self.n_p, np.int32)
+        ncx, ncp = C.c_int32(0), C.c_int32(0)
+        _check(_lib.rh_grid_coloring(self._h, _ptr(cx), _ptr(cp), C.byref(ncx), C.byref(ncp)))
+        return cx, cp, int(ncx.value), int(ncp.value)
+
+    def jacobian(self, method: str = "ad"):
+        """J_x, J_p at the current state as (row, col, value) triplets in x / p indices."""
+        m = {"analytic": RH_JAC_ANALYTIC, "ad": RH_JAC_COLORED_AD}[method]
+        d = self.dims
+        jx = (np.empty(d.nnz_jx, np.int32), np.empty(d.nnz_jx, np.int32), np.empty(d.nnz_jx))
+        jp = (np.empty(d.nnz_jp, np.int32), np.empty(d.nnz_jp, np.int32), np.empty(d.nnz_jp))
+        _check(_lib.rh_jacobian(self._h, m, *[_ptr(a) for a in jx], *[_ptr(a) for a in jp]))
+        return jx, jp
 
     # ---- real-time tracking step (section 6.3) -------------------------------------
     def rto_step(self, H=None, apply=False, stream=None):

@@ -90,3 +90,25 @@ def test_invalid_grids_are_rejected():
     st, h, _ = host_grid(g)
     assert st == 0
     lib.rh_grid_destroy(h)
+
+
+@pytest.mark.parametrize("case", ["tiny9", "tiny30", "case118", "case1354", "case2869", "case9241"])
+def test_coloring_bit_exact_against_oracle(case):
+    """The library's column colouring (host symbolic phase) equals the oracle's
+    independent greedy colouring, colour for colour."""
+    g = gg.make_grid(9, 12, 3, 2) if case == "tiny9" else gg.make_grid(30, 41, 6, 4) if case == "tiny30" \
+        else gg.make_case(case)
+    lib = rh.load()
+    st, h, keep = host_grid(g)
+    assert st == 0, lib.rh_last_error()
+    try:
+        o = OracleGrid(g)
+        cx, cp = np.empty(o.n_x, np.int32), np.empty(o.n_p, np.int32)
+        ncx, ncp = C.c_int32(0), C.c_int32(0)
+        assert lib.rh_grid_coloring(h, rh._ptr(cx), rh._ptr(cp), C.byref(ncx), C.byref(ncp)) == 0
+        assert lib.rh_jacobian(h, 1, None, None, None, None, None, None) == rh.RH_ESTATE
+    finally:
+        lib.rh_grid_destroy(h)
+    ref_x, ref_p, ref_ncx, ref_ncp = o.coloring()
+    assert (ncx.value, ncp.value) == (ref_ncx, ref_ncp)
+    assert np.array_equal(cx, ref_x) and np.array_equal(cp, ref_p)

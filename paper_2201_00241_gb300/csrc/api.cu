@@ -284,8 +284,9 @@ rh_status dirs(rh_grid* g, int N, int64_t ld, double* V, double* T, const double
 
 // single right-hand side in g->v1 (internal order), in place
 rh_status solve_one(rh_grid* g, unsigned phases, cudaStream_t s) {
-    if (rh::solve1_fits(g->S.n_x)) {
-        RH_CUDA(rh::launch_solve1(g->dir(), g->v1, phases, s));
+    const int mode = rh::solve1_mode(g->S.n_x, g->S.n_x - g->S.t0);
+    if (mode > 0) {
+        RH_CUDA(rh::launch_solve1(g->dir(), g->v1, phases, mode == 2, s));
         return RH_OK;
     }
     return dirs(g, 1, 1, g->v1, g->v1, nullptr, 0, 0, nullptr, 0, phases, s);
@@ -680,6 +681,8 @@ rh_status rh_powerflow(rh_grid* g, const double* x0, double tol, int32_t max_ite
         if (res <= tol) { out = RH_OK; break; }
         if (it >= max_iter || !std::isfinite(res)) break;
         RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_tgt_lev_ptr.data(), S.rf_n_lev, s));
+        rh::launch_build_tail(S.n_x - S.t0, S.t0, g->tail_pos, g->A, g->invdiag, g->triL, g->triU, g->triUt,
+                              g->triLt, s);
         st = check_err_flag(g);
         if (st) return st;
         RH_CUDA(cudaMemcpyAsync(g->v1, g->gres, nx * sizeof(double), cudaMemcpyDeviceToDevice, s));

@@ -855,16 +855,45 @@ __global__ void __launch_bounds__(kDirThreads, 2) k_dirs_batch(DirBatch B) {
 }
 
 // One right-hand side, one CTA, x held in shared memory for the whole sweep
-// (Newton steps and the first-order adjoint).
-__global__ void __launch_bounds__(1024, 1) k_solve1(DirGrid g, double* x, unsigned phases) {
+// (Newton steps and the first-order adjoint).  Dynamic shared memory holds
+// X[n_x] | the packed tail triangle (use_tail) | the k-split partial sums.  With
+// 1024 threads and one right-hand side choose_ks picks ks <= 1024 / nb, so a
+// level never writes more than 2 * 1024 partial sums (kSolve1Part).  With the
+// tail, the dense top block is solved column by column in shared memory, as in
+// k_dirs, instead of as one sparse level per variable.
+constexpr int kSolve1Part = 2048;
+__global__ void __launch_bounds__(1024, 1) k_solve1(DirGrid g, double* x, unsigned phases, int use_tail) {
     extern __shared__ double X[];
-    __shared__ double part[kPartCap];
+    double* tri = X + g.n_x;
+    double* part = tri + (use_tail ? (size_t)g.T * (g.T - 1) / 2 : 0);
     for (int q = threadIdx.x; q < g.n_x; q += blockDim.x) X[q] = x[q];
     __syncthreads();
-    if (phases & PH_L) sweep_fwd<false>(g, g.lf, g.A, X, 1, 0, 1, part);
-    if (phases & PH_U) sweep_bwd<true>(g, g.lb, g.A, X, 1, 0, 1, part);
-    if (phases & PH_UT) sweep_fwd<true>(g, g.lf, g.At, X, 1, 0, 1, part);
-    if (phases & PH_LT) sweep_bwd<false>(g, g.lb, g.At, X, 1, 0, 1, part);
+    if (use_tail) {
+        if (phases & PH_L) {
+            sweep_fwd<false>(g, g.sf, g.A, X, 1, 0, 1, part);
+            sweep_fwd<false, true>(g, g.ef, g.A, X, 1, 0, 1, part);
+            tail_fwd<false>(g, g.triL, X, 1, 0, 1, part, tri);
+        }
+        if (phases & PH_U) {
+            tail_bwd<true>(g, g.triU, X, 1, 0, 1, part, tri);
+            sweep_bwd<true>(g, g.sb, g.A, X, 1, 0, 1, part);
+        }
+        if (phases & PH_UT) {
+            sweep_fwd<true>(g, g.sf, g.At, X, 1, 0, 1, part);
+            sweep_fwd<true, true>(g, g.ef, g.At, X, 1, 0, 1, part);
+            tail_fwd<true>(g, g.triUt, X, 1, 0, 1, part, tri);
+        }
+        if (phases & PH_LT) {
+            tail_bwd<false>(g, g.triLt, X, 1, 0, 1, part, tri);
+            sweep_bwd<false>(g, g.sb, g.At, X, 1, 0, 1, part);
+        }
+    } else {
+        if (phases & PH_L) sweep_fwd<false>(g, g.lf, g.A, X, 1, 0, 1, part);
+        if (phases & PH_U) sweep_bwd<true>(g, g.lb, g.A, X, 1, 0, 1, part);
+        if (phases & PH_UT) sweep_fwd<true>(g, g.lf, g.At, X, 1, 0, 1, part);
+        if (phases & PH_LT) sweep_bwd<false>(g, g.lb, g.At, X, 1, 0, 1, part);
+    }
+    __syncthreads();
     for (int q = threadIdx.x; q < g.n_x; q += blockDim.x) x[q] = X[q];
 }
 
@@ -1125,11 +1154,18 @@ void launch_adjoint_rhs(const PfGrid& g, const PfState& s, const AdjData& a, cud
     k_objective<<<1, 256, 0, st>>>(g, s, a.F);
 }
 
-bool solve1_fits(int n_x) { return (size_t)n_x * sizeof(double) + kPartCap * sizeof(double) <= 227 * 1024; }
+static size_t solve1_smem(int n_x, int T, bool tail) {
+    return ((size_t)n_x + (tail ? (size_t)T * (T - 1) / 2 : 0) + kSolve1Part) * sizeof(double);
+}
 
-cudaError_t launch_solve1(const DirGrid& g, double* x, unsigned phases, cudaStream_t st) {
-    size_t smem = (size_t)(g.n_x > 0 ? g.n_x : 1) * sizeof(double);
-    k_solve1<<<1, 1024, smem, st>>>(g, x, phases);
+int solve1_mode(int n_x, int T) {
+    const size_t cap = 227 * 1024;
+    if (T > 1 && T <= kSolve1Part && solve1_smem(n_x, T, true) <= cap) return 2;
+    return solve1_smem(n_x, T, false) <= cap ? 1 : 0;
+}
+
+cudaError_t launch_solve1(const DirGrid& g, double* x, unsigned phases, bool use_tail, cudaStream_t st) {
+    k_solve1<<<1, 1024, solve1_smem(g.n_x, g.T, use_tail), st>>>(g, x, phases, use_tail ? 1 : 0);
     return cudaGetLastError();
 }
 

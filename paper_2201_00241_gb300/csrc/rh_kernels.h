@@ -158,8 +158,11 @@ bool dirs_tail_fits(int T, int N, int n_cta);
 void launch_build_tail(int T, int t0, const int* pos, const double* A, const double* invdiag, double* triL,
                        double* triU, double* triUt, double* triLt, cudaStream_t st);
 // one right-hand side in shared memory (requires solve1_fits(n_x))
-bool solve1_fits(int n_x);
-cudaError_t launch_solve1(const DirGrid& g, double* x, unsigned phases, cudaStream_t st);
+// One right-hand side in one CTA with x in shared memory: mode 2 also keeps the
+// dense tail triangle there (needs the tail triangles built), 1 without it,
+// 0 when x does not fit (use the direction kernel instead).
+int solve1_mode(int n_x, int T);
+cudaError_t launch_solve1(const DirGrid& g, double* x, unsigned phases, bool use_tail, cudaStream_t st);
 
 // Dense Cholesky of the tracking step (dense.cu).  A, L, B, work, y and info
 // are device pointers; column-major.  info receives 0 or the 1-based column of

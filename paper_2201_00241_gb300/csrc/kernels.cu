@@ -385,36 +385,36 @@ __device__ __forceinline__ int choose_ks(int nb, int D, int maxext) {
     return ks < 2 ? 1 : ks;
 }
 
-// s0 = sum_e v0[e] x[col[e]], s1 = sum_e v1[e] x[col[e]] over e in [e0, e1) of one
-// bus block (two rows sharing their columns when `two`).  Unrolled by 4 with two
-// accumulators per row, so that each lane has four independent loads in flight.
-__device__ __forceinline__ void block_dot(const int* __restrict__ col, const double* __restrict__ vals, int r0, int r1,
+// a0 -= sum_e v0[e] x[col[e]], a1 -= sum_e v1[e] x[col[e]] over e in [e0, e1) of
+// one bus block (two rows sharing their columns when `two`).  Unrolled by 4 so
+// that each lane has four independent loads in flight, with one FMA chain per
+// row: the FP64 pipe takes one warp instruction per 64 cycles per sub-partition,
+// far longer than the chain's latency, so a second accumulator would only cost
+// an extra FP64 add.
+__device__ __forceinline__ void block_sub(const int* __restrict__ col, const double* __restrict__ vals, int r0, int r1,
                                           int e0, int e1, const double* X, int64_t ld, int64_t c, bool two,
-                                          double& s0, double& s1) {
-    double p0 = 0.0, q0 = 0.0, p1 = 0.0, q1 = 0.0;
+                                          double& a0, double& a1) {
     int e = e0;
     for (; e + 4 <= e1; e += 4) {
         const int i0 = col[r0 + e], i1 = col[r0 + e + 1], i2 = col[r0 + e + 2], i3 = col[r0 + e + 3];
         const double x0 = X[(int64_t)i0 * ld + c], x1 = X[(int64_t)i1 * ld + c];
         const double x2 = X[(int64_t)i2 * ld + c], x3 = X[(int64_t)i3 * ld + c];
-        p0 = fma(vals[r0 + e], x0, p0);
-        q0 = fma(vals[r0 + e + 1], x1, q0);
-        p0 = fma(vals[r0 + e + 2], x2, p0);
-        q0 = fma(vals[r0 + e + 3], x3, q0);
+        a0 = fma(-vals[r0 + e], x0, a0);
+        a0 = fma(-vals[r0 + e + 1], x1, a0);
+        a0 = fma(-vals[r0 + e + 2], x2, a0);
+        a0 = fma(-vals[r0 + e + 3], x3, a0);
         if (two) {
-            p1 = fma(vals[r1 + e], x0, p1);
-            q1 = fma(vals[r1 + e + 1], x1, q1);
-            p1 = fma(vals[r1 + e + 2], x2, p1);
-            q1 = fma(vals[r1 + e + 3], x3, q1);
+            a1 = fma(-vals[r1 + e], x0, a1);
+            a1 = fma(-vals[r1 + e + 1], x1, a1);
+            a1 = fma(-vals[r1 + e + 2], x2, a1);
+            a1 = fma(-vals[r1 + e + 3], x3, a1);
         }
     }
     for (; e < e1; e++) {
         const double xv = X[(int64_t)col[r0 + e] * ld + c];
-        p0 = fma(vals[r0 + e], xv, p0);
-        if (two) p1 = fma(vals[r1 + e], xv, p1);
+        a0 = fma(-vals[r0 + e], xv, a0);
+        if (two) a1 = fma(-vals[r1 + e], xv, a1);
     }
-    s0 = p0 + q0;
-    s1 = p1 + q1;
 }
 
 // forward sweep over the L pattern: x_q = (b_q - sum_{c<q} v_qc x_c) [* 1/u_qq]
@@ -466,10 +466,9 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 const bool two = sl.w >= 0;
                 const int rpv = two ? sl.w : rp;
                 const int64_t c = c0 + d;
-                double s0, s1;
-                block_dot(g.col, vals, rp, rpv, 0, n, X, ld, c, two, s0, s1);
-                double a0 = X[(int64_t)q * ld + c] - s0;
-                double a1 = two ? X[(int64_t)(q + 1) * ld + c] - s1 : 0.0;
+                double a0 = X[(int64_t)q * ld + c];
+                double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
+                block_sub(g.col, vals, rp, rpv, 0, n, X, ld, c, two, a0, a1);
                 if (EXT) {
                     X[(int64_t)q * ld + c] = a0;
                     if (two) X[(int64_t)(q + 1) * ld + c] = a1;
@@ -493,8 +492,8 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 const int rpv = two ? sl.w : rp;
                 int64_t c = c0 + d;
                 int e0 = sli * n / ks, e1 = (sli + 1) * n / ks;
-                double s0, s1;
-                block_dot(g.col, vals, rp, rpv, e0, e1, X, ld, c, two, s0, s1);
+                double s0 = 0.0, s1 = 0.0;     // minus the slice's partial sums
+                block_sub(g.col, vals, rp, rpv, e0, e1, X, ld, c, two, s0, s1);
                 double* pp = part + 2 * ((bi * ks + sli) * D + d);
                 pp[0] = s0;
                 pp[1] = s1;
@@ -512,8 +511,8 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
                 for (int k = 0; k < ks; k++) {
                     const double* pp = part + 2 * ((bi * ks + k) * D + d);
-                    a0 -= pp[0];
-                    a1 -= pp[1];
+                    a0 += pp[0];
+                    a1 += pp[1];
                 }
                 if (EXT) {
                     X[(int64_t)q * ld + c] = a0;
@@ -564,10 +563,9 @@ __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __
                 const bool two = sl.w >= 0;
                 const int ue1 = two ? sl.w : ue0;
                 const int64_t c = c0 + d;
-                double s0, s1;
-                block_dot(g.col, vals, ue0, ue1, 0, n, X, ld, c, two, s0, s1);
-                double a0 = X[(int64_t)q * ld + c] - s0;
-                double a1 = two ? X[(int64_t)(q + 1) * ld + c] - s1 : 0.0;
+                double a0 = X[(int64_t)q * ld + c];
+                double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
+                block_sub(g.col, vals, ue0, ue1, 0, n, X, ld, c, two, a0, a1);
                 bwd_finish<SCALE>(g, vals, X, ld, c, q, two, ue0 - 1, a0, a1);
                 bi = bi2;
             }
@@ -582,8 +580,8 @@ __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __
                 const int ue1 = two ? sl.w : ue0;
                 int64_t c = c0 + d;
                 int e0 = sli * n / ks, e1 = (sli + 1) * n / ks;
-                double s0, s1;
-                block_dot(g.col, vals, ue0, ue1, e0, e1, X, ld, c, two, s0, s1);
+                double s0 = 0.0, s1 = 0.0;     // minus the slice's partial sums
+                block_sub(g.col, vals, ue0, ue1, e0, e1, X, ld, c, two, s0, s1);
                 double* pp = part + 2 * ((bi * ks + sli) * D + d);
                 pp[0] = s0;
                 pp[1] = s1;
@@ -599,8 +597,8 @@ __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __
                 double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
                 for (int k = 0; k < ks; k++) {
                     const double* pp = part + 2 * ((bi * ks + k) * D + d);
-                    a0 -= pp[0];
-                    a1 -= pp[1];
+                    a0 += pp[0];
+                    a1 += pp[1];
                 }
                 bwd_finish<SCALE>(g, vals, X, ld, c, q, two, sl.z - 1, a0, a1);
             }
@@ -756,7 +754,22 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
         for (int d = threadIdx.x; d < D; d += blockDim.x) V[(int64_t)g.zero_row * ld + d] = 0.0;
         __syncthreads();
     }
-    if (L.phases & PH_SPMUL) {
+    if ((L.phases & PH_SPMUL) && !L.W) {
+        // identity W: -B column c is minus column col0 + c of J_p; zero the x rows
+        // (stores only), then scatter the few entries of each column
+        const int rstep = (int)blockDim.x / D;
+        if (threadIdx.x < rstep * D) {
+            const int d = threadIdx.x % D;
+            for (int r = threadIdx.x / D; r < g.n_x; r += rstep) V[(int64_t)r * ld + d] = 0.0;
+        }
+        __syncthreads();
+        for (int d = threadIdx.x / 8; d < D; d += blockDim.x / 8) {
+            const int k = L.col0 + c0 + d;
+            for (int t = g.jpt_ptr[k] + (threadIdx.x & 7); t < g.jpt_ptr[k + 1]; t += 8)
+                V[(int64_t)g.jpt_row[t] * ld + d] = -g.jptv[t];
+        }
+        __syncthreads();
+    } else if (L.phases & PH_SPMUL) {
         // rows of J_p without entries: -B is zero there (stores only, no loads)
         for (int it = threadIdx.x; it < g.n_jp_zero * D; it += blockDim.x) {
             int r = it / D, d = it - r * D;

@@ -389,8 +389,15 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     for (int t = S.yp[S.ref]; t < S.yp[S.ref + 1]; t++) has_gref[S.yj[t]] = 1;
     g->n_inc = (int)inc_nb.size();
     g->n_gref = 1 + 2 * (S.yp[S.ref + 1] - S.yp[S.ref] - 1);
+    // projection order: degree descending, then buses with a Pg row, then elimination order, so
+    // that the lanes of a warp share their incidence count and their branches
     std::vector<int> tp_bus(S.ebus);
     tp_bus.push_back(S.ref);
+    std::stable_sort(tp_bus.begin(), tp_bus.end(), [&](int a, int b) {
+        int da = inc_ptr[a + 1] - inc_ptr[a], db = inc_ptr[b + 1] - inc_ptr[b];
+        if (da != db) return da > db;
+        return (pg_row[a] >= 0) > (pg_row[b] >= 0);
+    });
     std::vector<int> xmap(nx + np);
     for (int q = 0; q < nx; q++) xmap[S.perm[q]] = q;
     for (int k = 0; k < np; k++) xmap[nx + k] = nx + k;

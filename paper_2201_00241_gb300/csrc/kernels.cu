@@ -386,14 +386,21 @@ __device__ __forceinline__ int choose_ks(int nb, int D, int maxext) {
 }
 
 // a0 -= sum_e v0[e] x[col[e]], a1 -= sum_e v1[e] x[col[e]] over e in [e0, e1) of
-// one bus block (two rows sharing their columns when `two`).  Unrolled by 4 so
+// one bus block (two rows sharing their columns when TWO).  Unrolled by 4 so
 // that each lane has four independent loads in flight, with one FMA chain per
 // row: the FP64 pipe takes one warp instruction per 64 cycles per sub-partition,
 // far longer than the chain's latency, so a second accumulator would only cost
 // an extra FP64 add.
+//
+// TWO is chosen per warp (any lane with a second row): a predicated FP64
+// instruction occupies the pipe even with its lanes off, so warps of
+// single-row buses must not issue the second row at all.  In a mixed warp the
+// single-row lanes run the second row on a copy of their first (r1 == r0) and
+// ignore the result.
+template <bool TWO>
 __device__ __forceinline__ void block_sub(const int* __restrict__ col, const double* __restrict__ vals, int r0, int r1,
-                                          int e0, int e1, const double* X, int64_t ld, int64_t c, bool two,
-                                          double& a0, double& a1) {
+                                          int e0, int e1, const double* X, int64_t ld, int64_t c, double& a0,
+                                          double& a1) {
     int e = e0;
     for (; e + 4 <= e1; e += 4) {
         const int i0 = col[r0 + e], i1 = col[r0 + e + 1], i2 = col[r0 + e + 2], i3 = col[r0 + e + 3];
@@ -403,7 +410,7 @@ __device__ __forceinline__ void block_sub(const int* __restrict__ col, const dou
         a0 = fma(-vals[r0 + e + 1], x1, a0);
         a0 = fma(-vals[r0 + e + 2], x2, a0);
         a0 = fma(-vals[r0 + e + 3], x3, a0);
-        if (two) {
+        if constexpr (TWO) {
             a1 = fma(-vals[r1 + e], x0, a1);
             a1 = fma(-vals[r1 + e + 1], x1, a1);
             a1 = fma(-vals[r1 + e + 2], x2, a1);
@@ -413,19 +420,24 @@ __device__ __forceinline__ void block_sub(const int* __restrict__ col, const dou
     for (; e < e1; e++) {
         const double xv = X[(int64_t)col[r0 + e] * ld + c];
         a0 = fma(-vals[r0 + e], xv, a0);
-        if (two) a1 = fma(-vals[r1 + e], xv, a1);
+        if constexpr (TWO) a1 = fma(-vals[r1 + e], xv, a1);
     }
 }
 
+// warp-uniform choice of the two-row path (lanes that left the item loop do not vote)
+__device__ __forceinline__ bool warp_any(bool p) { return __any_sync(__activemask(), p); }
+
 // forward sweep over the L pattern: x_q = (b_q - sum_{c<q} v_qc x_c) [* 1/u_qq]
-template <bool SCALE>
+template <bool SCALE, bool TWO>
 __device__ __forceinline__ void fwd_finish(const DirGrid& g, const double* __restrict__ vals, double* X, int64_t ld,
                                            int64_t c, int q, bool two, int pos_vt, double a0, double a1) {
     double x0 = SCALE ? a0 * g.invdiag[q] : a0;
     X[(int64_t)q * ld + c] = x0;
-    if (two) {
+    if constexpr (TWO) {
         a1 = fma(-vals[pos_vt], x0, a1);
-        X[(int64_t)(q + 1) * ld + c] = SCALE ? a1 * g.invdiag[q + 1] : a1;
+        const double i1 = (SCALE && two) ? g.invdiag[q + 1] : 1.0;
+        const double x1 = SCALE ? a1 * i1 : a1;
+        if (two) X[(int64_t)(q + 1) * ld + c] = x1;
     }
 }
 
@@ -468,12 +480,18 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 const int64_t c = c0 + d;
                 double a0 = X[(int64_t)q * ld + c];
                 double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
-                block_sub(g.col, vals, rp, rpv, 0, n, X, ld, c, two, a0, a1);
-                if (EXT) {
-                    X[(int64_t)q * ld + c] = a0;
-                    if (two) X[(int64_t)(q + 1) * ld + c] = a1;
+                if (warp_any(two)) {
+                    block_sub<true>(g.col, vals, rp, rpv, 0, n, X, ld, c, a0, a1);
+                    if (EXT) {
+                        X[(int64_t)q * ld + c] = a0;
+                        if (two) X[(int64_t)(q + 1) * ld + c] = a1;
+                    } else {
+                        fwd_finish<SCALE, true>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
+                    }
                 } else {
-                    fwd_finish<SCALE>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
+                    block_sub<false>(g.col, vals, rp, rpv, 0, n, X, ld, c, a0, a1);
+                    if (EXT) X[(int64_t)q * ld + c] = a0;
+                    else fwd_finish<SCALE, false>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
                 }
                 if (mask) {
                     const int pq = g.bparent[q];
@@ -493,7 +511,8 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 int64_t c = c0 + d;
                 int e0 = sli * n / ks, e1 = (sli + 1) * n / ks;
                 double s0 = 0.0, s1 = 0.0;     // minus the slice's partial sums
-                block_sub(g.col, vals, rp, rpv, e0, e1, X, ld, c, two, s0, s1);
+                if (warp_any(two)) block_sub<true>(g.col, vals, rp, rpv, e0, e1, X, ld, c, s0, s1);
+                else block_sub<false>(g.col, vals, rp, rpv, e0, e1, X, ld, c, s0, s1);
                 double* pp = part + 2 * ((bi * ks + sli) * D + d);
                 pp[0] = s0;
                 pp[1] = s1;
@@ -509,16 +528,22 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 int64_t c = c0 + d;
                 double a0 = X[(int64_t)q * ld + c];
                 double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
-                for (int k = 0; k < ks; k++) {
-                    const double* pp = part + 2 * ((bi * ks + k) * D + d);
-                    a0 += pp[0];
-                    a1 += pp[1];
-                }
-                if (EXT) {
-                    X[(int64_t)q * ld + c] = a0;
-                    if (two) X[(int64_t)(q + 1) * ld + c] = a1;
+                if (warp_any(two)) {
+                    for (int k = 0; k < ks; k++) {
+                        const double* pp = part + 2 * ((bi * ks + k) * D + d);
+                        a0 += pp[0];
+                        a1 += pp[1];
+                    }
+                    if (EXT) {
+                        X[(int64_t)q * ld + c] = a0;
+                        if (two) X[(int64_t)(q + 1) * ld + c] = a1;
+                    } else {
+                        fwd_finish<SCALE, true>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
+                    }
                 } else {
-                    fwd_finish<SCALE>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
+                    for (int k = 0; k < ks; k++) a0 += part[2 * ((bi * ks + k) * D + d)];
+                    if (EXT) X[(int64_t)q * ld + c] = a0;
+                    else fwd_finish<SCALE, false>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
                 }
                 if (mask) {
                     const int pq = g.bparent[q];
@@ -531,13 +556,14 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
 }
 
 // backward sweep over the U pattern: x_q = (b_q - sum_{c>q} v_qc x_c) [* 1/u_qq]
-template <bool SCALE>
+template <bool SCALE, bool TWO>
 __device__ __forceinline__ void bwd_finish(const DirGrid& g, const double* __restrict__ vals, double* X, int64_t ld,
                                            int64_t c, int q, bool two, int pos_tv, double a0, double a1) {
-    if (two) {
-        double x1 = SCALE ? a1 * g.invdiag[q + 1] : a1;
-        X[(int64_t)(q + 1) * ld + c] = x1;
-        a0 = fma(-vals[pos_tv], x1, a0);
+    if constexpr (TWO) {
+        const double i1 = (SCALE && two) ? g.invdiag[q + 1] : 1.0;
+        const double x1 = SCALE ? a1 * i1 : a1;
+        if (two) X[(int64_t)(q + 1) * ld + c] = x1;
+        a0 = fma(-vals[pos_tv], two ? x1 : 0.0, a0);
     }
     X[(int64_t)q * ld + c] = SCALE ? a0 * g.invdiag[q] : a0;
 }
@@ -565,8 +591,13 @@ __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __
                 const int64_t c = c0 + d;
                 double a0 = X[(int64_t)q * ld + c];
                 double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
-                block_sub(g.col, vals, ue0, ue1, 0, n, X, ld, c, two, a0, a1);
-                bwd_finish<SCALE>(g, vals, X, ld, c, q, two, ue0 - 1, a0, a1);
+                if (warp_any(two)) {
+                    block_sub<true>(g.col, vals, ue0, ue1, 0, n, X, ld, c, a0, a1);
+                    bwd_finish<SCALE, true>(g, vals, X, ld, c, q, two, ue0 - 1, a0, a1);
+                } else {
+                    block_sub<false>(g.col, vals, ue0, ue1, 0, n, X, ld, c, a0, a1);
+                    bwd_finish<SCALE, false>(g, vals, X, ld, c, q, two, ue0 - 1, a0, a1);
+                }
                 bi = bi2;
             }
         } else {
@@ -581,7 +612,8 @@ __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __
                 int64_t c = c0 + d;
                 int e0 = sli * n / ks, e1 = (sli + 1) * n / ks;
                 double s0 = 0.0, s1 = 0.0;     // minus the slice's partial sums
-                block_sub(g.col, vals, ue0, ue1, e0, e1, X, ld, c, two, s0, s1);
+                if (warp_any(two)) block_sub<true>(g.col, vals, ue0, ue1, e0, e1, X, ld, c, s0, s1);
+                else block_sub<false>(g.col, vals, ue0, ue1, e0, e1, X, ld, c, s0, s1);
                 double* pp = part + 2 * ((bi * ks + sli) * D + d);
                 pp[0] = s0;
                 pp[1] = s1;
@@ -595,12 +627,17 @@ __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __
                 int64_t c = c0 + d;
                 double a0 = X[(int64_t)q * ld + c];
                 double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
-                for (int k = 0; k < ks; k++) {
-                    const double* pp = part + 2 * ((bi * ks + k) * D + d);
-                    a0 += pp[0];
-                    a1 += pp[1];
+                if (warp_any(two)) {
+                    for (int k = 0; k < ks; k++) {
+                        const double* pp = part + 2 * ((bi * ks + k) * D + d);
+                        a0 += pp[0];
+                        a1 += pp[1];
+                    }
+                    bwd_finish<SCALE, true>(g, vals, X, ld, c, q, two, sl.z - 1, a0, a1);
+                } else {
+                    for (int k = 0; k < ks; k++) a0 += part[2 * ((bi * ks + k) * D + d)];
+                    bwd_finish<SCALE, false>(g, vals, X, ld, c, q, two, sl.z - 1, a0, a1);
                 }
-                bwd_finish<SCALE>(g, vals, X, ld, c, q, two, sl.z - 1, a0, a1);
             }
         }
         __syncthreads();
@@ -676,6 +713,15 @@ __device__ void tail_bwd(const DirGrid& g, const double* __restrict__ tri_g, dou
 //   y_v(b)  = d2_b dv_b + A_b dth_b + sum_e ( K_e dv_j - a_e dth_j )
 //   y_th(b) = A_b dv_b  + C_b dth_b + sum_e ( b_e dv_j - c_e dth_j )
 // plus c''_slack (grad P_slack . v) grad P_slack and c''_k w_Pg_k.
+__device__ __forceinline__ double flip_sign(double v, bool flip) {
+    // negation through the sign bit (an integer operation, not an FP64 instruction)
+    return __longlong_as_double(__double_as_longlong(v) ^ (flip ? (long long)0x8000000000000000ULL : 0LL));
+}
+
+// Buses are visited in the order tp_bus (degree descending), so the lanes of a
+// warp mostly share their incidence count; each output is one FMA chain; the
+// slack-neighbour and Pg terms, which few buses have, are only issued by warps
+// that hold such a bus (a predicated FP64 instruction costs its issue slot).
 __device__ void tproj(const DirGrid& g, const double* V, double* T, int64_t ld, int c0, int D, double* sref) {
     double c2r = *g.c2ref;
     for (int d = threadIdx.x; d < D; d += blockDim.x) {
@@ -695,7 +741,6 @@ __device__ void tproj(const DirGrid& g, const double* V, double* T, int64_t ld, 
         double yth = fma(ab, dv, g.csum[b] * dth);
         int e = g.inc_ptr[b];
         const int e1 = g.inc_ptr[b + 1];
-        double yv2 = 0.0, yth2 = 0.0;
         for (; e + 2 <= e1; e += 2) {
             const int t0 = g.inc_uth[e], v0 = g.inc_uv[e], t1 = g.inc_uth[e + 1], v1 = g.inc_uv[e + 1];
             const double dthj0 = V[(int64_t)t0 * ld + c], dvj0 = V[(int64_t)v0 * ld + c];
@@ -705,30 +750,35 @@ __device__ void tproj(const DirGrid& g, const double* V, double* T, int64_t ld, 
             yv = fma(cf0.y, dthj0, yv);
             yth = fma(cf0.z, dvj0, yth);
             yth = fma(cf0.w, dthj0, yth);
-            yv2 = fma(cf1.x, dvj1, yv2);
-            yv2 = fma(cf1.y, dthj1, yv2);
-            yth2 = fma(cf1.z, dvj1, yth2);
-            yth2 = fma(cf1.w, dthj1, yth2);
+            yv = fma(cf1.x, dvj1, yv);
+            yv = fma(cf1.y, dthj1, yv);
+            yth = fma(cf1.z, dvj1, yth);
+            yth = fma(cf1.w, dthj1, yth);
         }
-        if (e < e1) {
-            const double4_32a cf = g.inc_coef[e];
-            const double dthj = V[(int64_t)g.inc_uth[e] * ld + c];
-            const double dvj = V[(int64_t)g.inc_uv[e] * ld + c];
-            yv = fma(cf.x, dvj, yv);
-            yv = fma(cf.y, dthj, yv);
-            yth = fma(cf.z, dvj, yth);
-            yth = fma(cf.w, dthj, yth);
+        if (warp_any(e < e1)) {
+            if (e < e1) {
+                const double4_32a cf = g.inc_coef[e];
+                const double dthj = V[(int64_t)g.inc_uth[e] * ld + c];
+                const double dvj = V[(int64_t)g.inc_uv[e] * ld + c];
+                yv = fma(cf.x, dvj, yv);
+                yv = fma(cf.y, dthj, yv);
+                yth = fma(cf.z, dvj, yth);
+                yth = fma(cf.w, dthj, yth);
+            }
         }
-        yv += yv2;
-        yth += yth2;
-        if (g.has_gref[b]) {
-            yv = fma(sref[d], g.gref_v[b], yv);
-            yth = fma(sref[d], g.gref_th[b], yth);
+        const bool hg = g.has_gref[b];
+        if (warp_any(hg)) {
+            if (hg) {
+                yv = fma(sref[d], g.gref_v[b], yv);
+                yth = fma(sref[d], g.gref_th[b], yth);
+            }
         }
-        if (rth != g.zero_row) T[(int64_t)rth * ld + c] = -yth;
-        T[(int64_t)rv * ld + c] = rv < g.n_x ? -yv : yv;
-        int pr = g.pg_row[b];
-        if (pr >= 0) T[(int64_t)pr * ld + c] = g.pg_curv[b] * V[(int64_t)pr * ld + c];
+        if (rth != g.zero_row) T[(int64_t)rth * ld + c] = flip_sign(yth, true);
+        T[(int64_t)rv * ld + c] = flip_sign(yv, rv < g.n_x);
+        const int pr = g.pg_row[b];
+        if (warp_any(pr >= 0)) {
+            if (pr >= 0) T[(int64_t)pr * ld + c] = g.pg_curv[b] * V[(int64_t)pr * ld + c];
+        }
     }
 }
 

@@ -27,6 +27,7 @@ namespace rh {
 namespace {
 
 constexpr int kDirThreads = 256;
+constexpr int kDirCtasPerSm = 3;  // resident direction CTAs per SM (bounds registers to 85)
 constexpr int kPartCap = 4096;   // doubles of k-split partial sums per CTA
 constexpr int kDMax = 256;       // max directions per CTA
 
@@ -645,10 +646,12 @@ __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __
 }
 
 // Dense trailing block [t0, t0 + T) of a sweep, column-oriented in shared memory.
-// xt[i * D + d] holds row t0 + i of the CTA's directions; tri is the packed
+// xt[i * D + d] holds row t0 + i of the CTA's directions; tri_g is the packed
 // strictly-triangular block (column j contiguous), columns pre-scaled by 1/u_jj
 // for the scaled sweeps, so each column step is y_i -= tri_ij y_j and the
-// result is x_i = y_i [* 1/u_ii].  One barrier per column.
+// result is x_i = y_i [* 1/u_ii].  One barrier per column.  With tri != NULL the
+// triangle is first staged in shared memory (one CTA per SM); with tri == NULL
+// it is read through L1, where it is shared by all the CTAs of the SM.
 __device__ __forceinline__ int lpack_off(int j, int T) { return j * (T - 1) - j * (j - 1) / 2; }  // rows j+1..T-1
 __device__ __forceinline__ int upack_off(int j) { return j * (j - 1) / 2; }                      // rows 0..j-1
 
@@ -657,14 +660,16 @@ __device__ void tail_fwd(const DirGrid& g, const double* __restrict__ tri_g, dou
                          double* xt, double* tri) {
     const int T = g.T, t0 = g.t0;
     const int ntri = T * (T - 1) / 2;
-    for (int i = threadIdx.x; i < ntri; i += blockDim.x) tri[i] = tri_g[i];
+    if (tri)
+        for (int i = threadIdx.x; i < ntri; i += blockDim.x) tri[i] = tri_g[i];
+    const double* src = tri ? tri : tri_g;
     for (int it = threadIdx.x; it < T * D; it += blockDim.x) {
         int i = it / D, d = it - i * D;
         xt[it] = X[(int64_t)(t0 + i) * ld + c0 + d];
     }
     __syncthreads();
     for (int j = 0; j < T - 1; j++) {
-        const double* colj = tri + lpack_off(j, T) - (j + 1);
+        const double* colj = src + lpack_off(j, T) - (j + 1);
         const int n = (T - 1 - j) * D;
         for (int it = threadIdx.x; it < n; it += blockDim.x) {
             int i = j + 1 + it / D, d = it % D;
@@ -685,14 +690,16 @@ __device__ void tail_bwd(const DirGrid& g, const double* __restrict__ tri_g, dou
                          double* xt, double* tri) {
     const int T = g.T, t0 = g.t0;
     const int ntri = T * (T - 1) / 2;
-    for (int i = threadIdx.x; i < ntri; i += blockDim.x) tri[i] = tri_g[i];
+    if (tri)
+        for (int i = threadIdx.x; i < ntri; i += blockDim.x) tri[i] = tri_g[i];
+    const double* src = tri ? tri : tri_g;
     for (int it = threadIdx.x; it < T * D; it += blockDim.x) {
         int i = it / D, d = it - i * D;
         xt[it] = X[(int64_t)(t0 + i) * ld + c0 + d];
     }
     __syncthreads();
     for (int j = T - 1; j > 0; j--) {
-        const double* colj = tri + upack_off(j);
+        const double* colj = src + upack_off(j);
         const int n = j * D;
         for (int it = threadIdx.x; it < n; it += blockDim.x) {
             int i = it / D, d = it - i * D;
@@ -782,9 +789,28 @@ __device__ void tproj(const DirGrid& g, const double* V, double* T, int64_t ld, 
     }
 }
 
+// HW = Y_p + J_p^T Psi (Algorithm 2, SpMulAdd): one lane per p row k, directions
+// blocked W at a time, so a warp's stores of one direction are consecutive.
+template <int W>
+__device__ __forceinline__ void muladd_row(const DirGrid& g, const DirLaunch& L, const double* T, int64_t ld, int c0,
+                                           int d0, int k) {
+    double h[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) h[w] = T[(int64_t)(g.n_x + k) * ld + d0 + w];
+    const int t1 = g.jpt_ptr[k + 1];
+    for (int t = g.jpt_ptr[k]; t < t1; t++) {
+        const double v = g.jptv[t];
+        const double* pr = T + (int64_t)g.jpt_row[t] * ld + d0;
+#pragma unroll
+        for (int w = 0; w < W; w++) h[w] = fma(v, pr[w], h[w]);
+    }
+#pragma unroll
+    for (int w = 0; w < W; w++) L.HW[(int64_t)(c0 + d0 + w) * L.ldhw + k] = h[w];
+}
+
 // Algorithm 2 for the directions owned by CTA `cta` of launch L on grid g.
 __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, const int cta, double* part,
-                                          double* sref, double* tri) {
+                                          double* sref, unsigned* mask_smem) {
     const int c0 = (int)((int64_t)cta * L.N / L.n_cta);
     const int c1 = (int)((int64_t)(cta + 1) * L.N / L.n_cta);
     const int D = c1 - c0;
@@ -840,7 +866,7 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
             unsigned* mask = nullptr;
             if (L.use_reach) {
                 // identity W: B column c is column col0 + c of J_p; seed its buses
-                mask = reinterpret_cast<unsigned*>(tri + (size_t)g.T * (g.T - 1) / 2);
+                mask = mask_smem;
                 for (int i = threadIdx.x; i < (g.n_x + 31) / 32; i += blockDim.x) mask[i] = 0u;
                 __syncthreads();
                 for (int d = threadIdx.x / 8; d < D; d += blockDim.x / 8) {
@@ -852,10 +878,10 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
             }
             sweep_fwd<false>(g, g.sf, g.A, V, ld, 0, D, part, mask);
             sweep_fwd<false, true>(g, g.ef, g.A, V, ld, 0, D, part);
-            tail_fwd<false>(g, g.triL, V, ld, 0, D, part, tri);
+            tail_fwd<false>(g, g.triL, V, ld, 0, D, part, nullptr);
         }
         if (L.phases & PH_U) {
-            tail_bwd<true>(g, g.triU, V, ld, 0, D, part, tri);
+            tail_bwd<true>(g, g.triU, V, ld, 0, D, part, nullptr);
             sweep_bwd<true>(g, g.sb, g.A, V, ld, 0, D, part);
         }
     } else {
@@ -870,10 +896,10 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
         if (L.phases & PH_UT) {
             sweep_fwd<true>(g, g.sf, g.At, T, ld, 0, D, part);
             sweep_fwd<true, true>(g, g.ef, g.At, T, ld, 0, D, part);
-            tail_fwd<true>(g, g.triUt, T, ld, 0, D, part, tri);
+            tail_fwd<true>(g, g.triUt, T, ld, 0, D, part, nullptr);
         }
         if (L.phases & PH_LT) {
-            tail_bwd<false>(g, g.triLt, T, ld, 0, D, part, tri);
+            tail_bwd<false>(g, g.triLt, T, ld, 0, D, part, nullptr);
             sweep_bwd<false>(g, g.sb, g.At, T, ld, 0, D, part);
         }
     } else {
@@ -881,32 +907,31 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
         if (L.phases & PH_LT) sweep_bwd<false>(g, g.lb, g.At, T, ld, 0, D, part);
     }
     if (L.phases & PH_MULADD) {
-        for (int it = threadIdx.x; it < g.n_p * D; it += blockDim.x) {
-            int k = it / D, d = it - k * D;
-            double h = T[(int64_t)(g.n_x + k) * ld + d];
-            for (int t = g.jpt_ptr[k]; t < g.jpt_ptr[k + 1]; t++)
-                h = fma(g.jptv[t], T[(int64_t)g.jpt_row[t] * ld + d], h);
-            L.HW[(int64_t)(c0 + d) * L.ldhw + k] = h;
+        for (int k = threadIdx.x; k < g.n_p; k += blockDim.x) {
+            int d0 = 0;
+            for (; d0 + 8 <= D; d0 += 8) muladd_row<8>(g, L, T, ld, c0, d0, k);
+            if (d0 + 4 <= D) { muladd_row<4>(g, L, T, ld, c0, d0, k); d0 += 4; }
+            if (d0 + 2 <= D) { muladd_row<2>(g, L, T, ld, c0, d0, k); d0 += 2; }
+            if (d0 < D) muladd_row<1>(g, L, T, ld, c0, d0, k);
         }
     }
 }
 
-__global__ void __launch_bounds__(kDirThreads, 2) k_dirs(DirGrid g, DirLaunch L) {
+__global__ void __launch_bounds__(kDirThreads, kDirCtasPerSm) k_dirs(DirGrid g, DirLaunch L) {
     __shared__ double part[kPartCap];
     __shared__ double sref[kDMax];
-    extern __shared__ double tri[];
-    dirs_body(g, L, blockIdx.x, part, sref, tri);
+    extern __shared__ unsigned mask_smem[];
+    dirs_body(g, L, blockIdx.x, part, sref, mask_smem);
 }
 
 // Several (grid, W block) items in one launch: CTA b belongs to the item i with
 // cta_ptr[i] <= b < cta_ptr[i + 1]; the item descriptors travel in the kernel
 // parameters and are copied to shared memory.
-__global__ void __launch_bounds__(kDirThreads, 2) k_dirs_batch(DirBatch B) {
+__global__ void __launch_bounds__(kDirThreads, kDirCtasPerSm) k_dirs_batch(DirBatch B) {
     __shared__ double part[kPartCap];
     __shared__ double sref[kDMax];
     __shared__ DirGrid sg;
     __shared__ DirLaunch sl;
-    extern __shared__ double tri[];
     int item = 0;
     while (item + 1 < B.n_items && (int)blockIdx.x >= B.cta_ptr[item + 1]) item++;
     if (threadIdx.x == 0) {
@@ -914,7 +939,7 @@ __global__ void __launch_bounds__(kDirThreads, 2) k_dirs_batch(DirBatch B) {
         sl = B.l[item];
     }
     __syncthreads();
-    dirs_body(sg, sl, (int)blockIdx.x - B.cta_ptr[item], part, sref, tri);
+    dirs_body(sg, sl, (int)blockIdx.x - B.cta_ptr[item], part, sref, nullptr);
 }
 
 // One right-hand side, one CTA, x held in shared memory for the whole sweep
@@ -1182,7 +1207,7 @@ int dirs_default_ctas(int N) {
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 1;
     }
-    int G = N < 2 * n_sm ? N : 2 * n_sm;
+    int G = N < kDirCtasPerSm * n_sm ? N : kDirCtasPerSm * n_sm;
     int need = (N + kDMax - 1) / kDMax;
     if (G < need) G = need;
     return G < 1 ? 1 : G;
@@ -1191,20 +1216,19 @@ int dirs_default_ctas(int N) {
 bool dirs_tail_fits(int T, int N, int n_cta) {
     if (T <= 1 || n_cta <= 0) return false;
     int dmax = (N + n_cta - 1) / n_cta;
-    return (int64_t)T * dmax <= kPartCap && (size_t)T * (T - 1) / 2 * sizeof(double) <= 96 * 1024;
+    return (int64_t)T * dmax <= kPartCap;      // the tail rows of the CTA's directions sit in `part`
 }
 
 void launch_dirs(const DirGrid& g, const DirLaunch& L, cudaStream_t st) {
     if (L.N <= 0 || L.n_cta <= 0) return;
-    size_t smem = L.use_tail ? (size_t)g.T * (g.T - 1) / 2 * sizeof(double) : 0;
-    if (L.use_tail && L.use_reach) smem += ((size_t)g.n_x + 127) / 128 * 16;   // one bit per row
+    size_t smem = (L.use_tail && L.use_reach) ? ((size_t)g.n_x + 127) / 128 * 16 : 0;   // one bit per row
     k_dirs<<<L.n_cta, kDirThreads, smem, st>>>(g, L);
 }
 
 void launch_dirs_batch(const DirBatch& B, int max_T, cudaStream_t st) {
     if (B.n_items <= 0 || B.cta_ptr[B.n_items] <= 0) return;
-    size_t smem = max_T > 1 ? (size_t)max_T * (max_T - 1) / 2 * sizeof(double) : 0;
-    k_dirs_batch<<<B.cta_ptr[B.n_items], kDirThreads, smem, st>>>(B);
+    (void)max_T;
+    k_dirs_batch<<<B.cta_ptr[B.n_items], kDirThreads, 0, st>>>(B);
 }
 
 void launch_build_tail(int T, int t0, const int* pos, const double* A, const double* invdiag, double* triL,

@@ -89,6 +89,7 @@ struct rh_grid {
            *gref_v = nullptr, *gref_val = nullptr;
     double *tmp_bus = nullptr;     // 4 * n_bus scratch for rh_injections
     double *rto_y = nullptr;       // n_p: workspace of the tracking step's solve
+    double *tailD = nullptr;       // T x T scratch of the dense tail LU
     double *pbuf = nullptr;        // n_p
     double *xbuf = nullptr;        // n_x
     // scalars: cref, c2ref, F
@@ -178,6 +179,7 @@ struct rh_grid {
         g.rowptr = rowptr; g.col = col; g.diagpos = diagpos; g.tpos = tpos;
         g.tgt_pos = rf_tgt_pos; g.tgt_cptr = rf_tgt_cptr; g.c_l = rf_c_l; g.c_u = rf_c_u;
         g.A = A; g.invdiag = invdiag; g.jmax = umax + 1; g.err = err;
+        g.tailD = tailD; g.tail_pos = tail_pos;
         return g;
     }
     int rows() const { return S.n_x + S.n_p + 1; }
@@ -569,6 +571,7 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     RH_CUDA(g->alloc(g->lam, nx));
     RH_CUDA(g->alloc(g->grad, np));
     RH_CUDA(g->alloc(g->rto_y, np));
+    RH_CUDA(g->alloc(g->tailD, (size_t)(S.n_x - S.t0) * (S.n_x - S.t0)));
     RH_CUDA(g->alloc(g->v1, g->rows()));
     RH_CUDA(g->alloc(g->inc_coef, g->n_inc));
     RH_CUDA(g->alloc(g->d2, nb));

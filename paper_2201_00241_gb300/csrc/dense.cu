@@ -1,15 +1,15 @@
 // dense.cu -- dense FP64 Cholesky factorisation and solves of the real-time
 // tracking step (section 6.3, eq. 18-19): H_t d_t = -g_t with H_t = L L^T.
 //
-// Right-looking tiled algorithm over TB x TB tiles of a column-major matrix:
-// for every tile column k
-//   k_chol_panel   CTA 0 factors the diagonal tile A_kk; CTA b > 0 solves the
-//                  tile b rows below it, L_ik = A_ik L_kk^{-T}.  Each CTA
-//                  eliminates the stacked [A_kk; A_ik] in shared memory
-//                  (the diagonal part redundantly), so one launch finishes the
-//                  whole tile column;
-//   k_chol_update  every trailing tile (i, j), k < j <= i, takes
-//                  A_ij -= L_ik L_jk^T (lower half only on the diagonal).
+// Right-looking tiled algorithm over TB x TB tiles of a column-major matrix.
+// The diagonal tile of tile column k is factored by the CTA that gives it its
+// last trailing update (in the update launch of column k - 1; k_chol_diag0 for
+// the first one), so no launch reads a tile that another of its CTAs writes:
+//   k_chol_panel   L_ik = A_ik L_kk^{-T} for every tile i below the diagonal,
+//                  one CTA each; fused: the forward solve y_k = L_kk^{-1} b_k
+//   k_chol_update  A_ij -= L_ik L_jk^T for every trailing tile, k < j <= i
+//                  (lower half only on the diagonal); the CTA of tile
+//                  (k + 1, k + 1) then factors it; fused: b_i -= L_ik y_k
 // The solves run one launch per tile: the forward sweep L y = b writes y into a
 // workspace while the other CTAs of the launch subtract L_ik y_k from the
 // right-hand side below it, and the backward sweep L^T x = y writes x back into
@@ -32,42 +32,25 @@ namespace {
 
 constexpr int kDenseThreads = 256;
 
+// Eliminates the symmetric tile held (lower triangle, unit-padded beyond kb) in
+// D: afterwards D[r][c] = l_rc l_cc for r >= c, Sq[c] = l_cc, Sinv[c] = 1 / l_cc.
+// The thread that completes the next pivot forms its reciprocal, so a step is
+// one multiply and one FMA per element and no division.
 template <int TB>
-__global__ void __launch_bounds__(kDenseThreads)
-    k_chol_panel(int n, double* __restrict__ A, int64_t lda, int k, int* __restrict__ info, double* __restrict__ y) {
+__device__ __forceinline__ void chol_tile(double (*D)[TB + 1], int kb, double* Inv, double* Sq, double* Sinv) {
     constexpr int R = TB * TB / kDenseThreads;
-    __shared__ double D[TB][TB + 1];
-    __shared__ double X[TB][TB + 1];
-    __shared__ double Inv[TB], Sq[TB], Sinv[TB];
     const int t = threadIdx.x;
-    const int k0 = k * TB, kb = min(TB, n - k0);
-    const int b = blockIdx.x;
-    const int r0 = k0 + b * TB, rb = b ? min(TB, n - r0) : 0;
-#pragma unroll
-    for (int q = 0; q < R; q++) {
-        const int e = t + q * kDenseThreads, r = e % TB, c = e / TB;
-        // lower triangle of A_kk; padding rows/columns get a unit pivot and no coupling
-        D[r][c] = (r < kb && c <= r) ? A[(k0 + r) + (int64_t)(k0 + c) * lda] : (r == c ? 1.0 : 0.0);
-        if (b) X[r][c] = (r < rb && c < kb) ? A[(r0 + r) + (int64_t)(k0 + c) * lda] : 0.0;
-    }
-    __syncthreads();
     if (t == 0) Inv[0] = 1.0 / D[0][0];
     __syncthreads();
-    // Unscaled elimination: after step j, D[r][j] = l_rj * l_jj and D[j][j] = l_jj^2.
-    // The thread that completes the next pivot also forms its reciprocal, so a
-    // step costs one multiply and one or two FMAs per element and no division.
     for (int j = 0; j < kb - 1; j++) {
         const double inv = Inv[j];
 #pragma unroll
         for (int q = 0; q < R; q++) {
             const int e = t + q * kDenseThreads, r = e % TB, c = e / TB;
-            if (c > j) {
+            if (c > j && r >= c) {
                 const double lc = D[c][j] * inv;
-                if (r >= c) {
-                    D[r][c] -= D[r][j] * lc;
-                    if (r == j + 1 && c == j + 1) Inv[j + 1] = 1.0 / D[r][c];
-                }
-                if (b) X[r][c] -= X[r][j] * lc;
+                D[r][c] = fma(-D[r][j], lc, D[r][c]);
+                if (r == j + 1 && c == j + 1) Inv[j + 1] = 1.0 / D[r][c];
             }
         }
         __syncthreads();
@@ -78,45 +61,114 @@ __global__ void __launch_bounds__(kDenseThreads)
         Sinv[t] = 1.0 / sq;
     }
     __syncthreads();
+}
+
+// Stores L_kk from an eliminated tile and records its first pivot that is not
+// positive (or NaN from an earlier failure): the steps run in order, so the
+// first value written to info is the first failure overall.
+template <int TB>
+__device__ __forceinline__ void chol_store_tile(double* __restrict__ A, int64_t lda, int k0, int kb,
+                                                const double (*D)[TB + 1], const double* Sq, const double* Sinv,
+                                                int* __restrict__ info) {
+    constexpr int R = TB * TB / kDenseThreads;
 #pragma unroll
     for (int q = 0; q < R; q++) {
-        const int e = t + q * kDenseThreads, r = e % TB, c = e / TB;
-        if (b == 0) {
-            if (r < kb && c <= r) A[(k0 + r) + (int64_t)(k0 + c) * lda] = (r == c) ? Sq[c] : D[r][c] * Sinv[c];
-        } else if (r < rb && c < kb) {
-            A[(r0 + r) + (int64_t)(k0 + c) * lda] = X[r][c] * Sinv[c];
-        }
+        const int e = threadIdx.x + q * kDenseThreads, r = e % TB, c = e / TB;
+        if (r < kb && c <= r) A[(k0 + r) + (int64_t)(k0 + c) * lda] = (r == c) ? Sq[c] : D[r][c] * Sinv[c];
     }
-    if (b != 0) return;
-    if (t == 0) {
+    if (threadIdx.x == 0) {
         for (int j = 0; j < kb; j++)
-            if (!(D[j][j] > 0.0)) {      // not positive, or NaN from an earlier failed pivot
+            if (!(D[j][j] > 0.0)) {
                 atomicCAS(info, 0, k0 + j + 1);
                 break;
             }
     }
-    // Fused forward solve of one right-hand side: y_k = L_kk^{-1} b_k in place
-    // (b_k already holds b_k - sum_{m<k} L_km y_m from the earlier updates).
-    // One warp, unscaled like the elimination: z_r -= D[r][j] z_j / D[j][j],
-    // then y_r = z_r / l_rr.
-    if (y && t < 32) {
+}
+
+template <int TB>
+__global__ void __launch_bounds__(kDenseThreads) k_chol_diag0(int n, double* __restrict__ A, int64_t lda,
+                                                              int* __restrict__ info) {
+    constexpr int R = TB * TB / kDenseThreads;
+    __shared__ double D[TB][TB + 1];
+    __shared__ double Inv[TB], Sq[TB], Sinv[TB];
+    const int kb = min(TB, n);
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+        const int e = threadIdx.x + q * kDenseThreads, r = e % TB, c = e / TB;
+        D[r][c] = (r < kb && c <= r) ? A[r + (int64_t)c * lda] : (r == c ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    chol_tile<TB>(D, kb, Inv, Sq, Sinv);
+    chol_store_tile<TB>(A, lda, 0, kb, D, Sq, Sinv, info);
+}
+
+// Tile column k, with L_kk already stored: CTA b < m solves tile k + 1 + b,
+// X L_kk^T = A_ik; CTA m (only with y) solves y_k = L_kk^{-1} y_k in place.
+// With M[c][j] = l_cj / l_jj and X kept unscaled (x_rj l_jj), a step is
+// X[r][c] -= X[r][j] M[c][j]; the result is x_rc = X[r][c] / l_cc.
+template <int TB>
+__global__ void __launch_bounds__(kDenseThreads)
+    k_chol_panel(int n, double* __restrict__ A, int64_t lda, int k, double* __restrict__ y) {
+    constexpr int R = TB * TB / kDenseThreads;
+    __shared__ double M[TB][TB + 1];
+    __shared__ double X[TB][TB + 1];
+    __shared__ double Inv[TB];
+    const int t = threadIdx.x;
+    const int k0 = k * TB, kb = min(TB, n - k0);
+    const int nt = (n + TB - 1) / TB, m = nt - k - 1;
+    const int b = blockIdx.x;
+    const int r0 = k0 + (b + 1) * TB, rb = b < m ? min(TB, n - r0) : 0;
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+        const int e = t + q * kDenseThreads, r = e % TB, c = e / TB;
+        M[r][c] = (r < kb && c <= r) ? A[(k0 + r) + (int64_t)(k0 + c) * lda] : (r == c ? 1.0 : 0.0);
+        if (b < m) X[r][c] = (r < rb && c < kb) ? A[(r0 + r) + (int64_t)(k0 + c) * lda] : 0.0;
+    }
+    __syncthreads();
+    if (t < TB) Inv[t] = 1.0 / M[t][t];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+        const int e = t + q * kDenseThreads, r = e % TB, c = e / TB;
+        if (r > c) M[r][c] *= Inv[c];
+    }
+    __syncthreads();
+    if (b < m) {
+        for (int j = 0; j < kb - 1; j++) {
+#pragma unroll
+            for (int q = 0; q < R; q++) {
+                const int e = t + q * kDenseThreads, r = e % TB, c = e / TB;
+                if (c > j) X[r][c] = fma(-X[r][j], M[c][j], X[r][c]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+            const int e = t + q * kDenseThreads, r = e % TB, c = e / TB;
+            if (r < rb && c < kb) A[(r0 + r) + (int64_t)(k0 + c) * lda] = X[r][c] * Inv[c];
+        }
+        return;
+    }
+    // fused forward solve, one warp: z_r -= M[r][j] z_j with z unscaled (y_j l_jj), then y_r = z_r / l_rr
+    if (t < 32) {
         const int r = t;
         double z = (r < kb) ? y[k0 + r] : 0.0;
         for (int j = 0; j < kb - 1; j++) {
-            const double zj = __shfl_sync(0xffffffffu, z, j) * Inv[j];
-            if (r > j && r < kb) z -= D[r][j] * zj;
+            const double zj = __shfl_sync(0xffffffffu, z, j);
+            if (r > j && r < kb) z = fma(-M[r][j], zj, z);
         }
-        if (r < kb) y[k0 + r] = z * Sinv[r];
+        if (r < kb) y[k0 + r] = z * Inv[r];
     }
 }
 
 template <int TB>
 __global__ void __launch_bounds__(kDenseThreads)
-    k_chol_update(int n, double* __restrict__ A, int64_t lda, int k, double* __restrict__ y) {
+    k_chol_update(int n, double* __restrict__ A, int64_t lda, int k, double* __restrict__ y, int* __restrict__ info) {
     constexpr int R = TB * TB / kDenseThreads;
     constexpr int CS = kDenseThreads / TB;      // column stride between a thread's outputs
     __shared__ double Li[TB][TB + 1];
     __shared__ double Lj[TB][TB + 1];
+    __shared__ double Inv[TB], Sq[TB], Sinv[TB];
     const int t = threadIdx.x;
     const int k0 = k * TB, kb = min(TB, n - k0);
     const int nt = (n + TB - 1) / TB;
@@ -165,11 +217,24 @@ __global__ void __launch_bounds__(kDenseThreads)
         for (int q = 0; q < R; q++) acc[q] = fma(a, Lj[c0 + q * CS][m], acc[q]);
     }
     const bool diag = (i0 == j0);
+    if (!(ii == 0 && jj == 0)) {
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+            const int c = c0 + q * CS;
+            if (r < ib && c < jb && (!diag || r >= c)) A[(i0 + r) + (int64_t)(j0 + c) * lda] -= acc[q];
+        }
+        return;
+    }
+    // tile (k + 1, k + 1) has its last update: factor it here
+    __syncthreads();                           // every thread is done reading Li
 #pragma unroll
     for (int q = 0; q < R; q++) {
         const int c = c0 + q * CS;
-        if (r < ib && c < jb && (!diag || r >= c)) A[(i0 + r) + (int64_t)(j0 + c) * lda] -= acc[q];
+        Li[r][c] = (r < ib && c <= r) ? A[(i0 + r) + (int64_t)(i0 + c) * lda] - acc[q] : (r == c ? 1.0 : 0.0);
     }
+    __syncthreads();
+    chol_tile<TB>(Li, ib, Inv, Sq, Sinv);
+    chol_store_tile<TB>(A, lda, i0, ib, Li, Sq, Sinv, info);
 }
 
 // Forward sweep, tile k: y_k = L_kk^{-1} b_k (every CTA, redundantly); CTA 0
@@ -270,11 +335,14 @@ __global__ void __launch_bounds__(kDenseThreads)
 template <int TB>
 cudaError_t potrf_tiles(int n, double* A, int64_t lda, int* info, double* y, cudaStream_t s) {
     const int nt = (n + TB - 1) / TB;
+    k_chol_diag0<TB><<<1, kDenseThreads, 0, s>>>(n, A, lda, info);
     for (int k = 0; k < nt; k++) {
-        k_chol_panel<TB><<<nt - k, kDenseThreads, 0, s>>>(n, A, lda, k, info, y);
         const int64_t T = nt - k - 1;
+        const unsigned panel = (unsigned)(T + (y ? 1 : 0));
+        if (panel) k_chol_panel<TB><<<panel, kDenseThreads, 0, s>>>(n, A, lda, k, y);
         if (T > 0)
-            k_chol_update<TB><<<(unsigned)(T * (T + 1) / 2 + (y ? T : 0)), kDenseThreads, 0, s>>>(n, A, lda, k, y);
+            k_chol_update<TB><<<(unsigned)(T * (T + 1) / 2 + (y ? T : 0)), kDenseThreads, 0, s>>>(n, A, lda, k, y,
+                                                                                              info);
     }
     return cudaGetLastError();
 }

@@ -298,6 +298,139 @@ __global__ void k_rf_update(RfGrid g, int64_t t0, int64_t nt) {
     g.A[p] -= acc;
 }
 
+// Dense trailing block [t0, n_x) as a tiled right-looking LU over TB x TB tiles
+// of a row-major scratch copy, spread over many SMs (GB300 runs FP64 on the
+// CUDA cores at 2 lane-FMAs per clock per SM, so one CTA would need T^3 / 3
+// FMAs on a single SM).  Static diagonal pivots, unit lower L.  The diagonal
+// tile of tile column k is factored by the CTA that gives it its last trailing
+// update (k_tail_diag0 for the first), so no launch reads a tile another of its
+// CTAs writes.  Per tile column k: k_tail_panel (m CTAs form L_ik = A_ik
+// U_kk^{-1}, m more U_kj = L_kk^{-1} A_kj) and k_tail_update (A_ij -= L_ik U_kj;
+// the CTA of tile (k + 1, k + 1) then factors it).  Inside a tile the
+// multipliers stay unscaled until the end (a_rc -= a_rj a_jc / a_jj), so a step
+// never writes the row or column it reads: one barrier per step.
+constexpr int kTailTB = 16;
+
+__global__ void k_tail_gather(RfGrid g) {
+    const int T = g.T;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= T * T) return;
+    const int p = g.tail_pos[idx];
+    g.tailD[idx] = p >= 0 ? g.A[p] : 0.0;
+}
+
+// Eliminates the tile held in Dk (unit-padded beyond kb) and stores it at
+// (k0, k0): U on and above the diagonal, L = a_rj / u_jj below it.
+__device__ __forceinline__ void tail_factor_store(const RfGrid& g, int k0, int kb, double (*Dk)[kTailTB + 1],
+                                                  double* Inv) {
+    constexpr int TB = kTailTB;
+    const int T = g.T, t = threadIdx.x, r = t % TB, c = t / TB;
+    if (t == 0) Inv[0] = 1.0 / Dk[0][0];
+    __syncthreads();
+    for (int j = 0; j < kb - 1; j++) {
+        const double inv = Inv[j];
+        if (r > j && c > j) {
+            Dk[r][c] = fma(-Dk[r][j], Dk[j][c] * inv, Dk[r][c]);
+            if (r == j + 1 && c == j + 1) Inv[j + 1] = 1.0 / Dk[r][c];
+        }
+        __syncthreads();
+    }
+    if (r < kb && c < kb) g.tailD[(size_t)(k0 + r) * T + k0 + c] = r > c ? Dk[r][c] * Inv[c] : Dk[r][c];
+}
+
+__global__ void __launch_bounds__(256) k_tail_diag0(RfGrid g) {
+    constexpr int TB = kTailTB;
+    __shared__ double Dk[TB][TB + 1];
+    __shared__ double Inv[TB];
+    const int T = g.T, kb = min(TB, T), r = threadIdx.x % TB, c = threadIdx.x / TB;
+    Dk[r][c] = (r < kb && c < kb) ? g.tailD[(size_t)r * T + c] : (r == c ? 1.0 : 0.0);
+    __syncthreads();
+    tail_factor_store(g, 0, kb, Dk, Inv);
+}
+
+__global__ void __launch_bounds__(256) k_tail_panel(RfGrid g, int k) {
+    constexpr int TB = kTailTB;
+    __shared__ double F[TB][TB + 1];      // the factored A_kk: U above, L below (unit diagonal)
+    __shared__ double X[TB][TB + 1];
+    __shared__ double Inv[TB];
+    const int T = g.T, nt = (T + TB - 1) / TB, m = nt - k - 1;
+    const int t = threadIdx.x, r = t % TB, c = t / TB;
+    const int k0 = k * TB, kb = min(TB, T - k0);
+    const int b = blockIdx.x;
+    const bool ltile = b < m;
+    const int o0 = (k + 1 + (ltile ? b : b - m)) * TB;
+    const int ob = min(TB, T - o0);
+    double* D = g.tailD;
+    F[r][c] = (r < kb && c < kb) ? D[(size_t)(k0 + r) * T + k0 + c] : (r == c ? 1.0 : 0.0);
+    if (ltile) X[r][c] = (r < ob && c < kb) ? D[(size_t)(o0 + r) * T + k0 + c] : 0.0;
+    else X[r][c] = (r < kb && c < ob) ? D[(size_t)(k0 + r) * T + o0 + c] : 0.0;
+    __syncthreads();
+    if (ltile) {
+        // X U = A_ik: with N[j][c] = u_jc / u_jj and X unscaled (x_rj u_jj),
+        // X[r][c] -= X[r][j] N[j][c]; x_rc = X[r][c] / u_cc
+        if (t < TB) Inv[t] = 1.0 / F[t][t];
+        __syncthreads();
+        if (c > r) F[r][c] *= Inv[r];
+        __syncthreads();
+        for (int j = 0; j < kb - 1; j++) {
+            if (c > j) X[r][c] = fma(-X[r][j], F[j][c], X[r][c]);
+            __syncthreads();
+        }
+        if (r < ob && c < kb) D[(size_t)(o0 + r) * T + k0 + c] = X[r][c] * Inv[c];
+        return;
+    }
+    // L Y = A_kj with unit L: Y[r][c] -= l_rj Y[j][c] for r > j
+    for (int j = 0; j < kb - 1; j++) {
+        if (r > j) X[r][c] = fma(-F[r][j], X[j][c], X[r][c]);
+        __syncthreads();
+    }
+    if (r < kb && c < ob) D[(size_t)(k0 + r) * T + o0 + c] = X[r][c];
+}
+
+__global__ void __launch_bounds__(256) k_tail_update(RfGrid g, int k) {
+    constexpr int TB = kTailTB;
+    __shared__ double Li[TB][TB + 1];
+    __shared__ double Uj[TB][TB + 1];
+    __shared__ double Inv[TB];
+    const int T = g.T, nt = (T + TB - 1) / TB, m = nt - k - 1;
+    const int bi = (int)blockIdx.x / m, bj = (int)blockIdx.x % m;
+    const int i0 = (k + 1 + bi) * TB, j0 = (k + 1 + bj) * TB, k0 = k * TB;
+    const int ib = min(TB, T - i0), jb = min(TB, T - j0), kb = min(TB, T - k0);
+    const int t = threadIdx.x, r = t % TB, c = t / TB;
+    double* D = g.tailD;
+    Li[r][c] = (r < ib && c < kb) ? D[(size_t)(i0 + r) * T + k0 + c] : 0.0;
+    Uj[r][c] = (r < kb && c < jb) ? D[(size_t)(k0 + r) * T + j0 + c] : 0.0;
+    __syncthreads();
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < TB; q++) acc = fma(Li[r][q], Uj[q][c], acc);
+    const double v = (r < ib && c < jb) ? D[(size_t)(i0 + r) * T + j0 + c] - acc : 0.0;
+    if (bi != 0 || bj != 0) {
+        if (r < ib && c < jb) D[(size_t)(i0 + r) * T + j0 + c] = v;
+        return;
+    }
+    // tile (k + 1, k + 1) has its last update: factor it here
+    __syncthreads();                             // every thread is done reading Li
+    Li[r][c] = (r < ib && c < ib) ? v : (r == c ? 1.0 : 0.0);
+    __syncthreads();
+    tail_factor_store(g, i0, ib, Li, Inv);
+}
+
+__global__ void k_tail_scatter(RfGrid g) {
+    const int T = g.T;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= T * T) return;
+    const int p = g.tail_pos[idx];
+    const double v = g.tailD[idx];
+    if (p >= 0) g.A[p] = v;
+    const int i = idx / T, j = idx - i * T;
+    if (i == j) {
+        g.invdiag[g.t0 + i] = 1.0 / v;
+        const double tau = 1e-14 * __longlong_as_double((long long)*g.jmax);
+        if (!(fabs(v) > tau)) atomicOr(g.err, 1);
+    }
+}
+
 // Dense trailing block [t0, n_x), one CTA: load it (all updates from the
 // earlier pivots are applied), right-looking LU with the static diagonal
 // pivots in shared memory, store it back.
@@ -1167,7 +1300,17 @@ cudaError_t launch_refactor(const RfGrid& g, const int* lev_ptr_host, const int6
         int64_t t0 = tgt_lev_ptr_host[lev], nt = tgt_lev_ptr_host[lev + 1] - t0;
         if (nt > 0) k_rf_update<<<blocks_for(nt, 256), 256, 0, st>>>(g, t0, nt);
     }
-    if (g.T > 0) k_refactor_tail<<<1, 1024, (size_t)g.T * g.T * sizeof(double), st>>>(g);
+    if (g.T > 0) {
+        const int TT = g.T * g.T, nt = (g.T + kTailTB - 1) / kTailTB;
+        k_tail_gather<<<blocks_for(TT, 256), 256, 0, st>>>(g);
+        k_tail_diag0<<<1, 256, 0, st>>>(g);
+        for (int k = 0; k < nt - 1; k++) {
+            const int m = nt - k - 1;
+            k_tail_panel<<<2 * m, 256, 0, st>>>(g, k);
+            k_tail_update<<<m * m, 256, 0, st>>>(g, k);
+        }
+        k_tail_scatter<<<blocks_for(TT, 256), 256, 0, st>>>(g);
+    }
     return cudaGetLastError();
 }
 

@@ -136,6 +136,8 @@ cudaError_t launch_jac_ad(const PfGrid& g, const PfState& s, const int* col_th, 
 // Fixed-pattern LU refactorisation data (device pointers).
 struct RfGrid {
     int n_x, t0, T;                    // dense trailing block [t0, n_x), T = n_x - t0
+    double* tailD;                     // T x T row-major scratch of the tiled dense LU
+    const int* tail_pos;               // (i, j) of the trailing block -> position in A, -1 if structurally zero
     const int *rf_lev_bus, *q0;
     const uint8_t *nv;
     const int *rowptr, *col, *diagpos, *tpos;

@@ -431,49 +431,6 @@ __global__ void k_tail_scatter(RfGrid g) {
     }
 }
 
-// Dense trailing block [t0, n_x), one CTA: load it (all updates from the
-// earlier pivots are applied), right-looking LU with the static diagonal
-// pivots in shared memory, store it back.
-__global__ void __launch_bounds__(1024, 1) k_refactor_tail(RfGrid g) {
-    extern __shared__ double D[];
-    const int T = g.T, t0 = g.t0;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    const double tau = 1e-14 * __longlong_as_double((long long)*g.jmax);
-    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) D[idx] = 0.0;
-    __syncthreads();
-    for (int i = t0 + warp; i < g.n_x; i += nwarps) {
-        int rp = g.rowptr[i], re = g.rowptr[i + 1];
-        for (int e = lane; e < re - rp; e += 32) {
-            int c = g.col[rp + e];
-            if (c >= t0) D[(size_t)(i - t0) * T + (c - t0)] = g.A[rp + e];
-        }
-    }
-    __syncthreads();
-    for (int k = 0; k < T; k++) {
-        const double piv = D[(size_t)k * T + k];
-        const double ip = 1.0 / piv;
-        if (threadIdx.x == 0) {
-            if (!(fabs(piv) > tau)) atomicOr(g.err, 1);
-            g.invdiag[t0 + k] = ip;
-        }
-        for (int i = k + 1 + threadIdx.x; i < T; i += blockDim.x) D[(size_t)i * T + k] *= ip;
-        __syncthreads();
-        const int m = T - k - 1;
-        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-            int ii = k + 1 + idx / m, jj = k + 1 + idx % m;
-            D[(size_t)ii * T + jj] = fma(-D[(size_t)ii * T + k], D[(size_t)k * T + jj], D[(size_t)ii * T + jj]);
-        }
-        __syncthreads();
-    }
-    for (int i = t0 + warp; i < g.n_x; i += nwarps) {
-        int rp = g.rowptr[i], re = g.rowptr[i + 1];
-        for (int e = lane; e < re - rp; e += 32) {
-            int c = g.col[rp + e];
-            if (c >= t0) g.A[rp + e] = D[(size_t)(i - t0) * T + (c - t0)];
-        }
-    }
-}
-
 __global__ void k_transpose_values(int nnz, const int* __restrict__ tpos, const double* __restrict__ A,
                                    double* __restrict__ At, int nnz_jp, const int* __restrict__ jpt_src,
                                    const double* __restrict__ jpv, double* __restrict__ jptv) {
@@ -1075,15 +1032,222 @@ __global__ void __launch_bounds__(kDirThreads, kDirCtasPerSm) k_dirs_batch(DirBa
     dirs_body(sg, sl, (int)blockIdx.x - B.cta_ptr[item], part, sref, nullptr);
 }
 
+// Sweeps of a single right-hand side held in shared memory (k_solve1).  There
+// is nothing to coalesce, so each bus block of a level takes a group of G
+// lanes (G a power of two, G * nb <= blockDim): the lanes stride over the row
+// and combine their sums with warp shuffles in log2(G) steps, and lane 0 of the
+// group finishes the block.  One barrier per level.  (Spreading a level over a
+// thread-block cluster with x replicated through distributed shared memory was
+// slower: a level's cost is its chain of dependent loads, which more CTAs do not
+// shorten, and a cluster barrier costs more than a CTA barrier.)
+__device__ __forceinline__ int group_size(int nb, int maxext, int threads) {
+    int G = 1;
+    while (G < 32 && 2 * G * nb <= threads && G < maxext) G *= 2;
+    return G;
+}
+
+// s0 -= sum v0[e] x[col[e]], s1 likewise, over e = e0, e0 + G, ... < n; unrolled by
+// 4 so that four independent index/value loads (L2: read once per solve) are in
+// flight per lane.
+__device__ __forceinline__ void row1_sub(const int* __restrict__ col, const double* __restrict__ vals, int r0, int r1,
+                                         int e0, int n, int G, const double* X, bool two, double& s0, double& s1) {
+    int e = e0;
+    for (; e + 3 * G < n; e += 4 * G) {
+        const int i0 = col[r0 + e], i1 = col[r0 + e + G], i2 = col[r0 + e + 2 * G], i3 = col[r0 + e + 3 * G];
+        const double u0 = vals[r0 + e], u1 = vals[r0 + e + G], u2 = vals[r0 + e + 2 * G], u3 = vals[r0 + e + 3 * G];
+        double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
+        if (two) {
+            w0 = vals[r1 + e];
+            w1 = vals[r1 + e + G];
+            w2 = vals[r1 + e + 2 * G];
+            w3 = vals[r1 + e + 3 * G];
+        }
+        const double x0 = X[i0], x1 = X[i1], x2 = X[i2], x3 = X[i3];
+        s0 = fma(-u0, x0, s0);
+        s0 = fma(-u1, x1, s0);
+        s0 = fma(-u2, x2, s0);
+        s0 = fma(-u3, x3, s0);
+        if (two) {
+            s1 = fma(-w0, x0, s1);
+            s1 = fma(-w1, x1, s1);
+            s1 = fma(-w2, x2, s1);
+            s1 = fma(-w3, x3, s1);
+        }
+    }
+    for (; e < n; e += G) {
+        const double xv = X[col[r0 + e]];
+        s0 = fma(-vals[r0 + e], xv, s0);
+        if (two) s1 = fma(-vals[r1 + e], xv, s1);
+    }
+}
+
+// sum of s over the G lanes of a group (G <= 32; groups are whole and aligned in
+// the warp)
+__device__ __forceinline__ void group_sum(int it, int items, int G, double& s0, double& s1) {
+    if (G == 1) return;
+    const int live = items - (it - (int)(threadIdx.x & 31));      // lanes of this warp holding an item
+    const unsigned m = live >= 32 ? 0xffffffffu : ((1u << live) - 1u);
+    for (int off = G / 2; off > 0; off >>= 1) {
+        s0 += __shfl_down_sync(m, s0, off, G);
+        s1 += __shfl_down_sync(m, s1, off, G);
+    }
+}
+
+// The first item of a level for one thread, with everything it needs that does
+// not depend on x: its slot, the first four (column, value) pairs of its share
+// of the row and the finishing data.  Loaded for the next level before the
+// barrier that ends the current one, so that after the barrier only the
+// shared-memory reads of x and the FMAs remain on the critical path (for rows
+// whose share is longer than four entries the rest is loaded as before).
+struct Pf1 {
+    int4 sl;
+    int i[4];
+    double u[4], w[4];
+    double inv0, inv1, vt;
+    bool valid;
+};
+
+template <bool FWD, bool SCALE, bool FIN>
+__device__ __forceinline__ void pf1_load(const DirGrid& g, const int4* __restrict__ slots,
+                                         const double* __restrict__ vals, int b0, int nb, int G, int it, Pf1& p) {
+    p.valid = it < nb * G;
+    if (!p.valid) return;
+    const int bi = it / G, li = it - bi * G;
+    p.sl = slots[b0 + bi];
+    const int n = p.sl.y, r0 = p.sl.z;
+    const bool two = p.sl.w >= 0;
+    const int r1 = two ? p.sl.w : r0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int e = li + k * G;
+        const bool in = e < n;
+        p.i[k] = in ? g.col[r0 + e] : -1;
+        p.u[k] = in ? vals[r0 + e] : 0.0;
+        p.w[k] = (in && two) ? vals[r1 + e] : 0.0;
+    }
+    if (FIN && li == 0) {
+        const int q = p.sl.x;
+        p.inv0 = SCALE ? g.invdiag[q] : 1.0;
+        p.inv1 = (SCALE && two) ? g.invdiag[q + 1] : 1.0;
+        p.vt = two ? vals[FWD ? r1 + n : r0 - 1] : 0.0;
+    }
+}
+
+// row share of one item: the prefetched first chunk, then the rest of the row
+__device__ __forceinline__ void pf1_sum(const DirGrid& g, const double* __restrict__ vals, const Pf1& p, int li,
+                                        int G, const double* X, double& s0, double& s1) {
+    const int n = p.sl.y, r0 = p.sl.z;
+    const bool two = p.sl.w >= 0;
+    const int r1 = two ? p.sl.w : r0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if (p.i[k] >= 0) {
+            const double xv = X[p.i[k]];
+            s0 = fma(-p.u[k], xv, s0);
+            if (two) s1 = fma(-p.w[k], xv, s1);
+        }
+    }
+    row1_sub(g.col, vals, r0, r1, li + 4 * G, n, G, X, two, s0, s1);
+}
+
+template <bool SCALE, bool EXT>
+__device__ void sweep1_fwd(const DirGrid& g, const LevelSet& ls, const double* __restrict__ vals, double* X) {
+    const int TT = (int)blockDim.x, gt = (int)threadIdx.x;
+    if (ls.n_lev <= 0) return;
+    int b0 = ls.ptr[0], nb = ls.ptr[1] - b0, G = group_size(nb, ls.maxext[0], TT);
+    Pf1 cur;
+    pf1_load<true, SCALE, !EXT>(g, ls.slots, vals, b0, nb, G, gt, cur);
+    for (int lev = 0; lev < ls.n_lev; lev++) {
+        int b0n = 0, nbn = 0, Gn = 1;
+        if (lev + 1 < ls.n_lev) {
+            b0n = ls.ptr[lev + 1];
+            nbn = ls.ptr[lev + 2] - b0n;
+            Gn = group_size(nbn, ls.maxext[lev + 1], TT);
+        }
+        for (int it = gt; it < nb * G; it += TT) {
+            Pf1 p = cur;
+            if (it != gt) pf1_load<true, SCALE, !EXT>(g, ls.slots, vals, b0, nb, G, it, p);
+            const int li = it - (it / G) * G;
+            const int q = p.sl.x;
+            const bool two = p.sl.w >= 0;
+            double s0 = 0.0, s1 = 0.0;
+            pf1_sum(g, vals, p, li, G, X, s0, s1);
+            group_sum(it, nb * G, G, s0, s1);
+            if (li == 0) {
+                const double a0 = X[q] + s0;
+                double a1 = two ? X[q + 1] + s1 : 0.0;
+                if (EXT) {
+                    X[q] = a0;
+                    if (two) X[q + 1] = a1;
+                } else {
+                    const double x0 = SCALE ? a0 * p.inv0 : a0;
+                    X[q] = x0;
+                    if (two) {
+                        a1 = fma(-p.vt, x0, a1);
+                        X[q + 1] = SCALE ? a1 * p.inv1 : a1;
+                    }
+                }
+            }
+        }
+        if (lev + 1 < ls.n_lev) pf1_load<true, SCALE, !EXT>(g, ls.slots, vals, b0n, nbn, Gn, gt, cur);
+        __syncthreads();
+        b0 = b0n;
+        nb = nbn;
+        G = Gn;
+    }
+}
+
+template <bool SCALE>
+__device__ void sweep1_bwd(const DirGrid& g, const LevelSet& ls, const double* __restrict__ vals, double* X) {
+    const int TT = (int)blockDim.x, gt = (int)threadIdx.x;
+    if (ls.n_lev <= 0) return;
+    int b0 = ls.ptr[0], nb = ls.ptr[1] - b0, G = group_size(nb, ls.maxext[0], TT);
+    Pf1 cur;
+    pf1_load<false, SCALE, true>(g, ls.slots, vals, b0, nb, G, gt, cur);
+    for (int lev = 0; lev < ls.n_lev; lev++) {
+        int b0n = 0, nbn = 0, Gn = 1;
+        if (lev + 1 < ls.n_lev) {
+            b0n = ls.ptr[lev + 1];
+            nbn = ls.ptr[lev + 2] - b0n;
+            Gn = group_size(nbn, ls.maxext[lev + 1], TT);
+        }
+        for (int it = gt; it < nb * G; it += TT) {
+            Pf1 p = cur;
+            if (it != gt) pf1_load<false, SCALE, true>(g, ls.slots, vals, b0, nb, G, it, p);
+            const int li = it - (it / G) * G;
+            const int q = p.sl.x;
+            const bool two = p.sl.w >= 0;
+            double s0 = 0.0, s1 = 0.0;
+            pf1_sum(g, vals, p, li, G, X, s0, s1);
+            group_sum(it, nb * G, G, s0, s1);
+            if (li == 0) {
+                double a0 = X[q] + s0;
+                if (two) {
+                    const double a1 = X[q + 1] + s1;
+                    const double x1 = SCALE ? a1 * p.inv1 : a1;
+                    X[q + 1] = x1;
+                    a0 = fma(-p.vt, x1, a0);
+                }
+                X[q] = SCALE ? a0 * p.inv0 : a0;
+            }
+        }
+        if (lev + 1 < ls.n_lev) pf1_load<false, SCALE, true>(g, ls.slots, vals, b0n, nbn, Gn, gt, cur);
+        __syncthreads();
+        b0 = b0n;
+        nb = nbn;
+        G = Gn;
+    }
+}
+
 // One right-hand side, one CTA, x held in shared memory for the whole sweep
 // (Newton steps and the first-order adjoint).  Dynamic shared memory holds
-// X[n_x] | the packed tail triangle (use_tail) | the k-split partial sums.  With
-// 1024 threads and one right-hand side choose_ks picks ks <= 1024 / nb, so a
-// level never writes more than 2 * 1024 partial sums (kSolve1Part).  With the
-// tail, the dense top block is solved column by column in shared memory, as in
-// k_dirs, instead of as one sparse level per variable.
+// X[n_x] | the packed tail triangle (use_tail) | kSolve1Part doubles of scratch
+// (the tail's right-hand side).  With the tail, the dense top block is solved
+// column by column in shared memory, as in k_dirs, instead of as one sparse
+// level per variable.
 constexpr int kSolve1Part = 2048;
-__global__ void __launch_bounds__(1024, 1) k_solve1(DirGrid g, double* x, unsigned phases, int use_tail) {
+constexpr int kSolve1Threads = 768;   // 85 registers per thread: room for the prefetched level data
+__global__ void __launch_bounds__(kSolve1Threads, 1) k_solve1(DirGrid g, double* x, unsigned phases, int use_tail) {
     extern __shared__ double X[];
     double* tri = X + g.n_x;
     double* part = tri + (use_tail ? (size_t)g.T * (g.T - 1) / 2 : 0);
@@ -1091,28 +1255,28 @@ __global__ void __launch_bounds__(1024, 1) k_solve1(DirGrid g, double* x, unsign
     __syncthreads();
     if (use_tail) {
         if (phases & PH_L) {
-            sweep_fwd<false>(g, g.sf, g.A, X, 1, 0, 1, part);
-            sweep_fwd<false, true>(g, g.ef, g.A, X, 1, 0, 1, part);
+            sweep1_fwd<false, false>(g, g.sf, g.A, X);
+            sweep1_fwd<false, true>(g, g.ef, g.A, X);
             tail_fwd<false>(g, g.triL, X, 1, 0, 1, part, tri);
         }
         if (phases & PH_U) {
             tail_bwd<true>(g, g.triU, X, 1, 0, 1, part, tri);
-            sweep_bwd<true>(g, g.sb, g.A, X, 1, 0, 1, part);
+            sweep1_bwd<true>(g, g.sb, g.A, X);
         }
         if (phases & PH_UT) {
-            sweep_fwd<true>(g, g.sf, g.At, X, 1, 0, 1, part);
-            sweep_fwd<true, true>(g, g.ef, g.At, X, 1, 0, 1, part);
+            sweep1_fwd<true, false>(g, g.sf, g.At, X);
+            sweep1_fwd<true, true>(g, g.ef, g.At, X);
             tail_fwd<true>(g, g.triUt, X, 1, 0, 1, part, tri);
         }
         if (phases & PH_LT) {
             tail_bwd<false>(g, g.triLt, X, 1, 0, 1, part, tri);
-            sweep_bwd<false>(g, g.sb, g.At, X, 1, 0, 1, part);
+            sweep1_bwd<false>(g, g.sb, g.At, X);
         }
     } else {
-        if (phases & PH_L) sweep_fwd<false>(g, g.lf, g.A, X, 1, 0, 1, part);
-        if (phases & PH_U) sweep_bwd<true>(g, g.lb, g.A, X, 1, 0, 1, part);
-        if (phases & PH_UT) sweep_fwd<true>(g, g.lf, g.At, X, 1, 0, 1, part);
-        if (phases & PH_LT) sweep_bwd<false>(g, g.lb, g.At, X, 1, 0, 1, part);
+        if (phases & PH_L) sweep1_fwd<false, false>(g, g.lf, g.A, X);
+        if (phases & PH_U) sweep1_bwd<true>(g, g.lb, g.A, X);
+        if (phases & PH_UT) sweep1_fwd<true, false>(g, g.lf, g.At, X);
+        if (phases & PH_LT) sweep1_bwd<false>(g, g.lb, g.At, X);
     }
     __syncthreads();
     for (int q = threadIdx.x; q < g.n_x; q += blockDim.x) x[q] = X[q];
@@ -1324,8 +1488,7 @@ cudaError_t prepare_kernels() {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const void* fns[4] = {(const void*)k_refactor_tail, (const void*)k_dirs, (const void*)k_solve1,
-                          (const void*)k_dirs_batch};
+    const void* fns[3] = {(const void*)k_dirs, (const void*)k_solve1, (const void*)k_dirs_batch};
     for (const void* f : fns) {
         cudaFuncAttributes fa;
         e = cudaFuncGetAttributes(&fa, f);
@@ -1395,7 +1558,7 @@ int solve1_mode(int n_x, int T) {
 }
 
 cudaError_t launch_solve1(const DirGrid& g, double* x, unsigned phases, bool use_tail, cudaStream_t st) {
-    k_solve1<<<1, 1024, solve1_smem(g.n_x, g.T, use_tail), st>>>(g, x, phases, use_tail ? 1 : 0);
+    k_solve1<<<1, kSolve1Threads, solve1_smem(g.n_x, g.T, use_tail), st>>>(g, x, phases, use_tail ? 1 : 0);
     return cudaGetLastError();
 }
 

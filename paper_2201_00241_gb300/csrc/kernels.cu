@@ -745,6 +745,16 @@ __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __
 __device__ __forceinline__ int lpack_off(int j, int T) { return j * (T - 1) - j * (j - 1) / 2; }  // rows j+1..T-1
 __device__ __forceinline__ int upack_off(int j) { return j * (j - 1) / 2; }                      // rows 0..j-1
 
+// The solve runs over blocks of kTailB columns with two barriers per block:
+// the block's diagonal part is solved inside warps (16 lanes hold the block's
+// rows of one direction and pass each finished value along with a shuffle),
+// then every row below (above, for the backward solve) takes the block's
+// contribution in one CTA-wide pass.
+constexpr int kTailB = 16;
+
+__device__ __forceinline__ double tri_l(const double* src, int T, int i, int j) { return src[lpack_off(j, T) + (i - j - 1)]; }
+__device__ __forceinline__ double tri_u(const double* src, int i, int j) { return src[upack_off(j) + i]; }
+
 template <bool SCALE>
 __device__ void tail_fwd(const DirGrid& g, const double* __restrict__ tri_g, double* X, int64_t ld, int c0, int D,
                          double* xt, double* tri) {
@@ -758,12 +768,34 @@ __device__ void tail_fwd(const DirGrid& g, const double* __restrict__ tri_g, dou
         xt[it] = X[(int64_t)(t0 + i) * ld + c0 + d];
     }
     __syncthreads();
-    for (int j = 0; j < T - 1; j++) {
-        const double* colj = src + lpack_off(j, T) - (j + 1);
-        const int n = (T - 1 - j) * D;
+    const int lane = threadIdx.x & 31, l = lane & 15;
+    const int hw = (int)(threadIdx.x >> 4), nhw = (int)(blockDim.x >> 4);
+    const unsigned hmask = (lane < 16) ? 0x0000ffffu : 0xffff0000u;
+    for (int b0 = 0; b0 < T; b0 += kTailB) {
+        const int bn = min(kTailB, T - b0);
+        // (1) diagonal block: rows b0 + l of direction d, one half-warp per direction
+        if (hw < D) {
+            double a[kTailB];
+#pragma unroll
+            for (int m = 0; m < kTailB; m++) a[m] = (m < l && l < bn) ? tri_l(src, T, b0 + l, b0 + m) : 0.0;
+            for (int d = hw; d < D; d += nhw) {
+                double v = l < bn ? xt[(b0 + l) * D + d] : 0.0;
+#pragma unroll
+                for (int m = 0; m < kTailB - 1; m++) {
+                    const double ym = __shfl_sync(hmask, v, m, 16);
+                    v = fma(-a[m], ym, v);
+                }
+                if (l < bn) xt[(b0 + l) * D + d] = v;
+            }
+        }
+        __syncthreads();
+        // (2) rows below the block take its contribution
+        const int n = (T - b0 - bn) * D;
         for (int it = threadIdx.x; it < n; it += blockDim.x) {
-            int i = j + 1 + it / D, d = it % D;
-            xt[i * D + d] = fma(-colj[i], xt[j * D + d], xt[i * D + d]);
+            const int i = b0 + bn + it / D, d = it % D;
+            double v = xt[i * D + d];
+            for (int m = 0; m < bn; m++) v = fma(-tri_l(src, T, i, b0 + m), xt[(b0 + m) * D + d], v);
+            xt[i * D + d] = v;
         }
         __syncthreads();
     }
@@ -788,12 +820,34 @@ __device__ void tail_bwd(const DirGrid& g, const double* __restrict__ tri_g, dou
         xt[it] = X[(int64_t)(t0 + i) * ld + c0 + d];
     }
     __syncthreads();
-    for (int j = T - 1; j > 0; j--) {
-        const double* colj = src + upack_off(j);
-        const int n = j * D;
+    const int lane = threadIdx.x & 31, l = lane & 15;
+    const int hw = (int)(threadIdx.x >> 4), nhw = (int)(blockDim.x >> 4);
+    const unsigned hmask = (lane < 16) ? 0x0000ffffu : 0xffff0000u;
+    for (int be = T; be > 0; be -= kTailB) {
+        const int b0 = be > kTailB ? be - kTailB : 0, bn = be - b0;
+        // (1) diagonal block, bottom-up: row b0 + l takes the finished values of the rows after it
+        if (hw < D) {
+            double a[kTailB];
+#pragma unroll
+            for (int m = 0; m < kTailB; m++) a[m] = (l < m && m < bn) ? tri_u(src, b0 + l, b0 + m) : 0.0;
+            for (int d = hw; d < D; d += nhw) {
+                double v = l < bn ? xt[(b0 + l) * D + d] : 0.0;
+#pragma unroll
+                for (int m = kTailB - 1; m > 0; m--) {
+                    const double ym = __shfl_sync(hmask, v, m, 16);
+                    v = fma(-a[m], ym, v);
+                }
+                if (l < bn) xt[(b0 + l) * D + d] = v;
+            }
+        }
+        __syncthreads();
+        // (2) rows above the block take its contribution
+        const int n = b0 * D;
         for (int it = threadIdx.x; it < n; it += blockDim.x) {
-            int i = it / D, d = it - i * D;
-            xt[i * D + d] = fma(-colj[i], xt[j * D + d], xt[i * D + d]);
+            const int i = it / D, d = it - i * D;
+            double v = xt[i * D + d];
+            for (int m = 0; m < bn; m++) v = fma(-tri_u(src, i, b0 + m), xt[(b0 + m) * D + d], v);
+            xt[i * D + d] = v;
         }
         __syncthreads();
     }

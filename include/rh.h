@@ -72,6 +72,8 @@ typedef struct {
     int64_t nnz_jx, nnz_jp;               /* structural nonzeros of J_x and J_p      */
     int64_t nnz_l, nnz_u;                 /* strictly-lower L, upper U incl. diagonal */
     int64_t refactor_updates;             /* multiply-subtract count of a refactor   */
+    int32_t setup_kernels;                /* kernels one rh_adjoint launches (counted in its
+                                             captured graph; 0 before the first call)    */
 } rh_dims;
 
 /*

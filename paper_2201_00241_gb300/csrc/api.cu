@@ -105,6 +105,7 @@ struct rh_grid {
 
     bool adjoint_ready = false;
     cudaGraphExec_t adj_exec = nullptr;   // captured device work of rh_adjoint
+    int adj_kernels = 0;                  // kernel nodes in that graph
     cudaEvent_t apply_done = nullptr;     // orders a tracking step's parameter update before later grid work
 
     ~rh_grid() {
@@ -606,6 +607,7 @@ rh_status rh_grid_dims(const rh_grid* g, rh_dims* o) {
     o->nnz_jx = S.nnz_jx; o->nnz_jp = (int64_t)S.jp_col.size();
     o->nnz_l = S.nnz_l; o->nnz_u = S.nnz_u;
     o->refactor_updates = (int64_t)S.rf_c_l.size();
+    o->setup_kernels = g->adj_kernels;
     return RH_OK;
 }
 
@@ -766,6 +768,17 @@ rh_status rh_adjoint(rh_grid* g, double* F, double* lambda, double* grad) {
         cudaError_t ce = cudaStreamEndCapture(s, &graph);
         if (st) { if (graph) cudaGraphDestroy(graph); return st; }
         if (ce != cudaSuccess) return fail(RH_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        size_t n_nodes = 0;
+        if (cudaGraphGetNodes(graph, nullptr, &n_nodes) == cudaSuccess) {
+            std::vector<cudaGraphNode_t> nodes(n_nodes);
+            int kernels = 0;
+            if (n_nodes && cudaGraphGetNodes(graph, nodes.data(), &n_nodes) == cudaSuccess)
+                for (auto nd : nodes) {
+                    cudaGraphNodeType ty;
+                    if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) kernels++;
+                }
+            g->adj_kernels = kernels;
+        }
         ce = cudaGraphInstantiate(&g->adj_exec, graph, 0);
         cudaGraphDestroy(graph);
         if (ce != cudaSuccess) { g->adj_exec = nullptr; return fail(RH_ECUDA, std::string("graph: ") + cudaGetErrorString(ce)); }

@@ -49,7 +49,7 @@ class Dims(C.Structure):
     _fields_ = [("n_bus", C.c_int32), ("n_branch", C.c_int32), ("n_gen", C.c_int32), ("n_pv", C.c_int32),
                 ("n_pq", C.c_int32), ("n_x", C.c_int32), ("n_p", C.c_int32), ("n_levels_fwd", C.c_int32),
                 ("n_levels_bwd", C.c_int32), ("nnz_jx", C.c_int64), ("nnz_jp", C.c_int64), ("nnz_l", C.c_int64),
-                ("nnz_u", C.c_int64), ("refactor_updates", C.c_int64)]
+                ("nnz_u", C.c_int64), ("refactor_updates", C.c_int64), ("setup_kernels", C.c_int32)]
 
 
 _lib = None

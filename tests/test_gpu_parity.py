@@ -263,3 +263,23 @@ def test_load_scenarios_case1354(k):
     d = setup_case("case1354", scale=scale)
     W = gg.random_directions(d["lg"].n_p, 64, 1000 + k)
     assert rel(d["lg"].hessvec(W), oracle_hv(d, W)) <= TOL_HW
+
+
+def test_setup_kernel_count_is_reported_after_the_first_adjoint():
+    """rh_dims.setup_kernels counts the kernels of rh_adjoint's captured graph: 0
+    before the first call, then the same positive number on every call."""
+    import ctypes as C
+    from paper_2201_00241_gb300 import rh
+    lg = rh.Grid(gg.make_case("case118"), device=0)
+    st = lg.plant()
+    lg.set_state(st.p, st.pd, st.qd)
+    lg.powerflow(st.x)
+    lib = rh.load()
+    dm = rh.Dims()
+    assert lib.rh_grid_dims(lg._h, C.byref(dm)) == 0 and dm.setup_kernels == 0
+    lg.adjoint()
+    assert lib.rh_grid_dims(lg._h, C.byref(dm)) == 0
+    first = dm.setup_kernels
+    assert first > 5
+    lg.adjoint()
+    assert lib.rh_grid_dims(lg._h, C.byref(dm)) == 0 and dm.setup_kernels == first

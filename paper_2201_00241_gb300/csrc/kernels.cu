@@ -542,13 +542,16 @@ __device__ __forceinline__ void fwd_finish(const DirGrid& g, const double* __res
 // item's slot is prefetched while the current one is computed.
 // EXT: subtract the row parts only (the dense tail's external phase), no finish.
 // mask (optional, forward L sweep with identity W): bit q is set for the theta row q of
-// every bus whose x can be nonzero for this CTA's directions; inactive buses keep
-// x = b = 0 and are skipped, and every processed bus activates its tree parent.
+// every bus whose x can be nonzero for this CTA's directions; every processed bus
+// activates its tree parent, an inactive bus only stores its zeros.  seed: the buses
+// whose right-hand side was written (zeroed, then the J_p entries scattered); every
+// other active bus has b = 0, so V need not be zeroed beforehand.
 __device__ __forceinline__ bool mask_get(const unsigned* m, int q) { return (m[q >> 5] >> (q & 31)) & 1u; }
 __device__ __forceinline__ void mask_set(unsigned* m, int q) { atomicOr(m + (q >> 5), 1u << (q & 31)); }
 template <bool SCALE, bool EXT = false>
 __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __restrict__ vals, double* X,
-                          int64_t ld, int c0, int D, double* part, unsigned* mask = nullptr) {
+                          int64_t ld, int c0, int D, double* part, unsigned* mask = nullptr,
+                          const unsigned* seed = nullptr) {
     for (int lev = 0; lev < ls.n_lev; lev++) {
         const int b0 = ls.ptr[lev], nb = ls.ptr[lev + 1] - b0;
         const int4* __restrict__ slots = ls.slots + b0;
@@ -565,12 +568,17 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 if (it2 < items) nxt = slots[bi2];
                 const int q = sl.x, n = sl.y, rp = sl.z;
                 bi = bi2;
-                if (mask && !mask_get(mask, q)) continue;
                 const bool two = sl.w >= 0;
-                const int rpv = two ? sl.w : rp;
                 const int64_t c = c0 + d;
-                double a0 = X[(int64_t)q * ld + c];
-                double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
+                if (mask && !mask_get(mask, q)) {
+                    X[(int64_t)q * ld + c] = 0.0;
+                    if (two) X[(int64_t)(q + 1) * ld + c] = 0.0;
+                    continue;
+                }
+                const int rpv = two ? sl.w : rp;
+                const bool has_b = !seed || mask_get(seed, q);
+                double a0 = has_b ? X[(int64_t)q * ld + c] : 0.0;
+                double a1 = (two && has_b) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
                 if (warp_any(two)) {
                     block_sub<true>(g.col, vals, rp, rpv, 0, n, X, ld, c, a0, a1);
                     if (EXT) {
@@ -613,12 +621,17 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 int bi = it / D, d = it - bi * D;
                 const int4 sl = slots[bi];
                 const int q = sl.x, n = sl.y;
-                if (mask && !mask_get(mask, q)) continue;
                 const bool two = sl.w >= 0;
-                const int rpv = two ? sl.w : sl.z;
                 int64_t c = c0 + d;
-                double a0 = X[(int64_t)q * ld + c];
-                double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
+                if (mask && !mask_get(mask, q)) {
+                    X[(int64_t)q * ld + c] = 0.0;
+                    if (two) X[(int64_t)(q + 1) * ld + c] = 0.0;
+                    continue;
+                }
+                const int rpv = two ? sl.w : sl.z;
+                const bool has_b = !seed || mask_get(seed, q);
+                double a0 = has_b ? X[(int64_t)q * ld + c] : 0.0;
+                double a1 = (two && has_b) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
                 if (warp_any(two)) {
                     for (int k = 0; k < ks; k++) {
                         const double* pp = part + 2 * ((bi * ks + k) * D + d);
@@ -974,7 +987,38 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
         for (int d = threadIdx.x; d < D; d += blockDim.x) V[(int64_t)g.zero_row * ld + d] = 0.0;
         __syncthreads();
     }
-    if ((L.phases & PH_SPMUL) && !L.W) {
+    unsigned* seed = nullptr;
+    if ((L.phases & PH_SPMUL) && !L.W && L.use_reach) {
+        // identity W with the reach-restricted forward sweep: only the buses of this
+        // CTA's J_p columns (all their rows, every direction) and the dense tail are
+        // zeroed before the scatter; the forward sweep writes every other row itself
+        seed = mask_smem + (g.n_x + 31) / 32;
+        for (int i = threadIdx.x; i < (g.n_x + 31) / 32; i += blockDim.x) seed[i] = 0u;
+        for (int it = threadIdx.x; it < g.T * D; it += blockDim.x) {
+            const int i = it / D, d = it - i * D;
+            V[(int64_t)(g.t0 + i) * ld + d] = 0.0;
+        }
+        __syncthreads();
+        for (int d = threadIdx.x / 8; d < D; d += blockDim.x / 8) {
+            const int k = L.col0 + c0 + d;
+            for (int t = g.jpt_ptr[k] + (threadIdx.x & 7); t < g.jpt_ptr[k + 1]; t += 8) {
+                const int qb = g.qtheta[g.jpt_row[t]];
+                mask_set(seed, qb);
+                const bool two = qb + 1 < g.n_x && g.qtheta[qb + 1] == qb;
+                for (int e = 0; e < D; e++) {
+                    V[(int64_t)qb * ld + e] = 0.0;
+                    if (two) V[(int64_t)(qb + 1) * ld + e] = 0.0;
+                }
+            }
+        }
+        __syncthreads();
+        for (int d = threadIdx.x / 8; d < D; d += blockDim.x / 8) {
+            const int k = L.col0 + c0 + d;
+            for (int t = g.jpt_ptr[k] + (threadIdx.x & 7); t < g.jpt_ptr[k + 1]; t += 8)
+                V[(int64_t)g.jpt_row[t] * ld + d] = -g.jptv[t];
+        }
+        __syncthreads();
+    } else if ((L.phases & PH_SPMUL) && !L.W) {
         // identity W: -B column c is minus column col0 + c of J_p; zero the x rows
         // (stores only), then scatter the few entries of each column
         const int rstep = (int)blockDim.x / D;
@@ -1011,16 +1055,20 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
             if (L.use_reach) {
                 // identity W: B column c is column col0 + c of J_p; seed its buses
                 mask = mask_smem;
-                for (int i = threadIdx.x; i < (g.n_x + 31) / 32; i += blockDim.x) mask[i] = 0u;
-                __syncthreads();
-                for (int d = threadIdx.x / 8; d < D; d += blockDim.x / 8) {
-                    const int k = L.col0 + c0 + d;
-                    for (int t = g.jpt_ptr[k] + (threadIdx.x & 7); t < g.jpt_ptr[k + 1]; t += 8)
-                        mask_set(mask, g.qtheta[g.jpt_row[t]]);
+                if (seed) {
+                    for (int i = threadIdx.x; i < (g.n_x + 31) / 32; i += blockDim.x) mask[i] = seed[i];
+                } else {
+                    for (int i = threadIdx.x; i < (g.n_x + 31) / 32; i += blockDim.x) mask[i] = 0u;
+                    __syncthreads();
+                    for (int d = threadIdx.x / 8; d < D; d += blockDim.x / 8) {
+                        const int k = L.col0 + c0 + d;
+                        for (int t = g.jpt_ptr[k] + (threadIdx.x & 7); t < g.jpt_ptr[k + 1]; t += 8)
+                            mask_set(mask, g.qtheta[g.jpt_row[t]]);
+                    }
                 }
                 __syncthreads();
             }
-            sweep_fwd<false>(g, g.sf, g.A, V, ld, 0, D, part, mask);
+            sweep_fwd<false>(g, g.sf, g.A, V, ld, 0, D, part, mask, seed);
             sweep_fwd<false, true>(g, g.ef, g.A, V, ld, 0, D, part);
             tail_fwd<false>(g, g.triL, V, ld, 0, D, part, nullptr);
         }
@@ -1581,7 +1629,8 @@ bool dirs_tail_fits(int T, int N, int n_cta) {
 
 void launch_dirs(const DirGrid& g, const DirLaunch& L, cudaStream_t st) {
     if (L.N <= 0 || L.n_cta <= 0) return;
-    size_t smem = (L.use_tail && L.use_reach) ? ((size_t)g.n_x + 127) / 128 * 16 : 0;   // one bit per row
+    // active and seed masks, one bit per row each
+    size_t smem = (L.use_tail && L.use_reach) ? 2 * (((size_t)g.n_x + 127) / 128 * 16) : 0;
     k_dirs<<<L.n_cta, kDirThreads, smem, st>>>(g, L);
 }
 

@@ -55,6 +55,25 @@ def dist_env():
     return rank, world, local
 
 
+# Several GPUs run replicas: every rank computes the whole workload of a step (the
+# directions and blocks are independent, no step exchanges data), so the job's
+# time is the slowest rank's and its throughput is world x the per-rank units.
+def max_over_ranks(value, world, device):
+    """The largest of the ranks' values (all ranks call it; no-op for one rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` replicas that each process units_per_rank in `seconds`."""
+    return world * units_per_rank / seconds
+
+
 def measured_traffic():
     """DRAM bytes per k_dirs launch from the committed ncu capture, if the kernel source is unchanged."""
     import hashlib
@@ -516,12 +535,8 @@ def main():
     if sampler:
         sampler.terminate()
         sampler.wait()
-    t_step = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([t_step], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(t.item())
-    value = world * n_p / (t_step * 1e-3)
+    t_step = max_over_ranks(sum(step_ms) / len(step_ms), world, f"cuda:{local}")
+    value = replica_throughput(n_p, world, t_step * 1e-3)
     t_dirs = sum(dirs_ms) / len(dirs_ms)
     achieved = flops_dir * n_p / (t_dirs * 1e-3) * 1e-9
 
@@ -537,7 +552,8 @@ def main():
         rh._check(lib.rh_hessian(lg._h, BLOCK_N, rh._ptr(Hh), n_p, None, rh.RH_HESSIAN_CONCURRENT))
         if i >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
-    e2e_value = world * n_p / (sum(e2e_t) / len(e2e_t)) if e2e_t else None
+    e2e_s = max_over_ranks(sum(e2e_t) / len(e2e_t), world, f"cuda:{local}") if e2e_t else None
+    e2e_value = replica_throughput(n_p, world, e2e_s) if e2e_t else None
     h2d = 8 * (n_p + 2 * g.n_bus + lg.n_x)
     d2h = 8 * n_p * n_p + 8 * (lg.n_x + n_p + 1)
 

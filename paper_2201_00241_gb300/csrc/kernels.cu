@@ -26,8 +26,12 @@ namespace rh {
 
 namespace {
 
-constexpr int kDirThreads = 256;
-constexpr int kDirCtasPerSm = 3;  // resident direction CTAs per SM (bounds registers to 85)
+// Direction CTAs: 384 threads, 2 resident per SM (80 registers).  With 24 warps per
+// SM either way, 2 CTAs of 384 run the full 9241-bus Hessian in 6.47 ms against
+// 7.39 ms for 3 of 256: more directions per CTA put fewer buses (with different
+// row lengths) in a warp and more items in every level.
+constexpr int kDirThreads = 384;
+constexpr int kDirCtasPerSm = 2;
 constexpr int kPartCap = 4096;   // doubles of k-split partial sums per CTA
 constexpr int kDMax = 256;       // max directions per CTA
 

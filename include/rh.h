@@ -74,6 +74,8 @@ typedef struct {
     int64_t refactor_updates;             /* multiply-subtract count of a refactor   */
     int32_t setup_kernels;                /* kernels one rh_adjoint launches (counted in its
                                              captured graph; 0 before the first call)    */
+    int32_t hessian_kernels;              /* kernels one rh_reduced_hessian launches (its
+                                             captured graph; 0 before the first call)    */
 } rh_dims;
 
 /*
@@ -199,6 +201,38 @@ rh_status rh_batch_hessvec(int32_t n_items, const rh_hv_item *items, int32_t wid
  */
 #define RH_HESSIAN_CONCURRENT 2u
 rh_status rh_hessian(rh_grid *grid, int32_t block_n, double *H, int64_t ldh, void *stream, uint32_t flags);
+
+/*
+ * The reduced Hessian at the current state in one call (sections 4 and 5:
+ * Jacobians, refactorisation, the adjoint of eq. 7, then Algorithm 2 with
+ * W = I, all n_p directions in flight): J_x and J_p, the LU refactorisation,
+ * lambda, grad F and F, and H = Hess F (n_p x n_p, column-major, ldh >= n_p).
+ * The adjoint's transposed solve runs on a second stream beside the first half
+ * of the direction sweeps (SpMul, L and U), which do not need lambda; the
+ * projection and the transposed sweeps follow once both are done.  The device
+ * work is one captured CUDA graph, rebuilt when H, ldh or the workspace change.
+ *
+ * H: host (default) or, with RH_DEVICE_PTRS, device memory; F (1) and grad
+ * (n_p) are optional host outputs (NULL skips them).  `stream` (may be NULL):
+ * the call first waits for the work already queued there.  Synchronous: on
+ * return the results are in place, and the grid is ready for rh_hessvec as after
+ * rh_adjoint.  Returns RH_ESINGULAR when a static pivot is below 1e-14 max|J_x|
+ * (H is then not meaningful), RH_EINVAL for a NULL H or ldh < n_p.
+ */
+rh_status rh_reduced_hessian(rh_grid *grid, double *H, int64_t ldh, double *F, double *grad, void *stream,
+                             uint32_t flags);
+
+/*
+ * Device times in milliseconds of the last completed rh_reduced_hessian call,
+ * from CUDA events recorded inside its graph, all measured from the fork that
+ * follows the factorisation:
+ *   ms[0]  end of the second direction launch (both launches, and any wait for
+ *          the adjoint branch between them),
+ *   ms[1]  end of the first direction launch (SpMul, L and U sweeps),
+ *   ms[2]  end of the adjoint branch (transposed solve, coefficients, grad F).
+ * RH_ESTATE before the first completed call.
+ */
+rh_status rh_reduced_hessian_times(const rh_grid *grid, float *ms);
 
 /*
  * Solve J_x X = R (trans = 0) or J_x^T X = R (trans = 1) with the current

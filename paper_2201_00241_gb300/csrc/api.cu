@@ -108,9 +108,32 @@ struct rh_grid {
     int adj_kernels = 0;                  // kernel nodes in that graph
     cudaEvent_t apply_done = nullptr;     // orders a tracking step's parameter update before later grid work
 
-    ~rh_grid() {
+    // rh_reduced_hessian: its captured graph (for one H pointer, leading dimension and
+    // workspace), the second stream and events of the fork and join, and the timing
+    // events around the direction launches
+    cudaGraphExec_t hess_exec = nullptr;
+    const double* hess_H = nullptr;
+    int64_t hess_ld = 0;
+    const double* hess_V = nullptr;
+    int hess_kernels = 0;
+    bool hess_timed = false;
+    cudaStream_t stream2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_user = nullptr;
+    cudaEvent_t ev_d0 = nullptr, ev_d1 = nullptr, ev_v = nullptr, ev_c = nullptr;   // timing
+
+    void drop_graphs() {
         if (adj_exec) cudaGraphExecDestroy(adj_exec);
+        if (hess_exec) cudaGraphExecDestroy(hess_exec);
+        adj_exec = nullptr;
+        hess_exec = nullptr;
+    }
+
+    ~rh_grid() {
+        drop_graphs();
         if (apply_done) cudaEventDestroy(apply_done);
+        for (cudaEvent_t e : {ev_fork, ev_join, ev_user, ev_d0, ev_d1, ev_v, ev_c})
+            if (e) cudaEventDestroy(e);
+        if (stream2) cudaStreamDestroy(stream2);
         for (void* p : allocs) cudaFree(p);
         if (V) cudaFree(V);
         if (T) cudaFree(T);
@@ -263,11 +286,13 @@ rh_status assemble_and_factor(rh_grid* g) {
     return check_err_flag(g);
 }
 
+// n_cta > 0 caps the CTA count (the default is one per slot of the device)
 rh_status dirs(rh_grid* g, int N, int64_t ld, double* V, double* T, const double* W, int64_t ldw, int col0,
-               double* HW, int64_t ldhw, unsigned phases, cudaStream_t s) {
+               double* HW, int64_t ldhw, unsigned phases, cudaStream_t s, int n_cta = 0) {
     rh::DirLaunch L;
     L.N = N;
     L.n_cta = rh::dirs_default_ctas(N);
+    if (n_cta > 0 && n_cta < L.n_cta) L.n_cta = n_cta;
     L.ld = ld;
     L.cta_stride = 0;
     L.V = V;
@@ -285,9 +310,12 @@ rh_status dirs(rh_grid* g, int N, int64_t ld, double* V, double* T, const double
     return RH_OK;
 }
 
-// single right-hand side in g->v1 (internal order), in place
-rh_status solve_one(rh_grid* g, unsigned phases, cudaStream_t s) {
-    const int mode = rh::solve1_mode(g->S.n_x, g->S.n_x - g->S.t0);
+// single right-hand side in g->v1 (internal order), in place.  beside_dirs: as
+// one CTA of the direction kernel, which fits in the slot a direction launch of
+// one CTA less than the device holds leaves free (k_solve1's shared-memory x
+// needs a shared-memory carveout that an SM running k_dirs does not have).
+rh_status solve_one(rh_grid* g, unsigned phases, cudaStream_t s, bool beside_dirs = false) {
+    const int mode = beside_dirs ? 0 : rh::solve1_mode(g->S.n_x, g->S.n_x - g->S.t0);
     if (mode > 0) {
         RH_CUDA(rh::launch_solve1(g->dir(), g->v1, phases, mode == 2, s));
         return RH_OK;
@@ -608,6 +636,7 @@ rh_status rh_grid_dims(const rh_grid* g, rh_dims* o) {
     o->nnz_l = S.nnz_l; o->nnz_u = S.nnz_u;
     o->refactor_updates = (int64_t)S.rf_c_l.size();
     o->setup_kernels = g->adj_kernels;
+    o->hessian_kernels = g->hess_kernels;
     return RH_OK;
 }
 
@@ -732,18 +761,21 @@ rh_status rh_refactor(rh_grid* g, double* A_out) {
 
 // Device work of rh_adjoint: a1 (Jacobian), a2 (refactor), a3 (adjoint, gradient,
 // projection coefficients).  Enqueue only; captured once per grid into a graph.
-rh_status enqueue_adjoint(rh_grid* g) {
+}  // extern "C"
+
+namespace {
+
+// The adjoint (eq. 7) on the current factors: right-hand side and F, the transposed
+// single solve, lambda, the projection coefficients and grad F (enqueue only).
+rh_status enqueue_adjoint_chain(rh_grid* g, cudaStream_t s, bool beside_dirs) {
     const auto& S = g->S;
-    cudaStream_t s = g->stream;
-    rh_status st = enqueue_factor(g);
-    if (st) return st;
     RH_CUDA(cudaMemsetAsync(g->v1, 0, sizeof(double) * g->rows(), s));
     rh::AdjData a;
     a.rhs = g->v1; a.cref = g->dscal; a.c2ref = g->dscal + 1; a.F = g->dscal + 2;
     a.gref_th = g->gref_th; a.gref_v = g->gref_v; a.gref_row = g->gref_row; a.gref_val = g->gref_val;
     a.n_gref = g->n_gref; a.uth = g->uth; a.uv = g->uv;
     rh::launch_adjoint_rhs(g->pf(), g->st(), a, s);
-    st = solve_one(g, rh::PH_UT | rh::PH_LT, s);
+    rh_status st = solve_one(g, rh::PH_UT | rh::PH_LT, s, beside_dirs);
     if (st) return st;
     RH_CUDA(cudaMemcpyAsync(g->lam, g->v1, S.n_x * sizeof(double), cudaMemcpyDeviceToDevice, s));
     rh::launch_adjoint_coef(g->pf(), g->st(), g->lam, g->dscal, g->inc_ptr, g->inc_nb, g->inc_coef, g->d2, g->asum,
@@ -754,6 +786,72 @@ rh_status enqueue_adjoint(rh_grid* g) {
     return RH_OK;
 }
 
+rh_status enqueue_adjoint(rh_grid* g) {
+    rh_status st = enqueue_factor(g);
+    if (st) return st;
+    return enqueue_adjoint_chain(g, g->stream, false);
+}
+
+// Captures what `enqueue` puts on g->stream (and on streams it joins) into an
+// executable graph, counting its kernel nodes.
+template <class F>
+rh_status capture_graph(rh_grid* g, F&& enqueue, cudaGraphExec_t* exec, int* kernels) {
+    cudaGraph_t graph = nullptr;
+    RH_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    rh_status st = enqueue();
+    cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
+    if (st) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (ce != cudaSuccess) return fail(RH_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    size_t n_nodes = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &n_nodes) == cudaSuccess) {
+        std::vector<cudaGraphNode_t> nodes(n_nodes);
+        int k = 0;
+        if (n_nodes && cudaGraphGetNodes(graph, nodes.data(), &n_nodes) == cudaSuccess)
+            for (auto nd : nodes) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) k++;
+            }
+        *kernels = k;
+    }
+    ce = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) { *exec = nullptr; return fail(RH_ECUDA, std::string("graph: ") + cudaGetErrorString(ce)); }
+    return RH_OK;
+}
+
+// rh_reduced_hessian's device work.  After the factorisation the adjoint chain
+// forks onto stream2 (its single solve as one direction CTA) while
+// the direction kernel runs SpMul and the L and U sweeps on one CTA less than the
+// device holds, so the two run at once; after the join a second direction launch
+// runs the projection, the transposed sweeps and SpMulAdd.  The directions of the
+// two launches are independent columns of V, so their CTA counts may differ.
+rh_status enqueue_reduced_hessian(rh_grid* g, double* Hd, int64_t lh) {
+    const int np = g->S.n_p;
+    rh_status st = enqueue_factor(g);
+    if (st) return st;
+    RH_CUDA(cudaEventRecord(g->ev_fork, g->stream));
+    RH_CUDA(cudaStreamWaitEvent(g->stream2, g->ev_fork, 0));
+    st = enqueue_adjoint_chain(g, g->stream2, true);
+    if (st) return st;
+    RH_CUDA(cudaEventRecordWithFlags(g->ev_d0, g->stream, cudaEventRecordExternal));
+    st = dirs(g, np, np, g->V, g->T, nullptr, 0, 0, Hd, lh, rh::PH_WLOAD | rh::PH_SPMUL | rh::PH_L | rh::PH_U,
+              g->stream, rh::dirs_cta_slots() - 1);
+    if (st) return st;
+    RH_CUDA(cudaEventRecordWithFlags(g->ev_v, g->stream, cudaEventRecordExternal));
+    RH_CUDA(cudaEventRecordWithFlags(g->ev_c, g->stream2, cudaEventRecordExternal));
+    RH_CUDA(cudaEventRecord(g->ev_join, g->stream2));
+    RH_CUDA(cudaStreamWaitEvent(g->stream, g->ev_join, 0));
+    st = dirs(g, np, np, g->V, g->T, nullptr, 0, 0, Hd, lh, rh::PH_TPROJ | rh::PH_UT | rh::PH_LT | rh::PH_MULADD,
+              g->stream);
+    if (st) return st;
+    RH_CUDA(cudaEventRecordWithFlags(g->ev_d1, g->stream, cudaEventRecordExternal));
+    return RH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 rh_status rh_adjoint(rh_grid* g, double* F, double* lambda, double* grad) {
     if (!g) return fail(RH_EINVAL, "NULL grid");
     rh_status st = set_device(g);
@@ -762,26 +860,8 @@ rh_status rh_adjoint(rh_grid* g, double* F, double* lambda, double* grad) {
     cudaStream_t s = g->stream;
     g->adjoint_ready = false;
     if (!g->adj_exec) {
-        cudaGraph_t graph = nullptr;
-        RH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        st = enqueue_adjoint(g);
-        cudaError_t ce = cudaStreamEndCapture(s, &graph);
-        if (st) { if (graph) cudaGraphDestroy(graph); return st; }
-        if (ce != cudaSuccess) return fail(RH_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
-        size_t n_nodes = 0;
-        if (cudaGraphGetNodes(graph, nullptr, &n_nodes) == cudaSuccess) {
-            std::vector<cudaGraphNode_t> nodes(n_nodes);
-            int kernels = 0;
-            if (n_nodes && cudaGraphGetNodes(graph, nodes.data(), &n_nodes) == cudaSuccess)
-                for (auto nd : nodes) {
-                    cudaGraphNodeType ty;
-                    if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) kernels++;
-                }
-            g->adj_kernels = kernels;
-        }
-        ce = cudaGraphInstantiate(&g->adj_exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ce != cudaSuccess) { g->adj_exec = nullptr; return fail(RH_ECUDA, std::string("graph: ") + cudaGetErrorString(ce)); }
+        st = capture_graph(g, [&] { return enqueue_adjoint(g); }, &g->adj_exec, &g->adj_kernels);
+        if (st) return st;
     }
     RH_CUDA(cudaGraphLaunch(g->adj_exec, s));
     if (lambda) {
@@ -793,6 +873,72 @@ rh_status rh_adjoint(rh_grid* g, double* F, double* lambda, double* grad) {
     st = check_err_flag(g);   // synchronises the stream
     if (st) return st;
     g->adjoint_ready = true;
+    return RH_OK;
+}
+
+rh_status rh_reduced_hessian(rh_grid* g, double* H, int64_t ldh, double* F, double* grad, void* stream,
+                             uint32_t flags) {
+    if (!g) return fail(RH_EINVAL, "NULL grid");
+    const auto& S = g->S;
+    if (!H || ldh < S.n_p) return fail(RH_EINVAL, "bad H or leading dimension");
+    rh_status st = set_device(g);
+    if (st) return st;
+    const int np = S.n_p;
+    const bool host = !(flags & RH_DEVICE_PTRS);
+    double* Hd = H;
+    int64_t lh = ldh;
+    if (host) {
+        st = ensure_stage(g, (size_t)np * np);
+        if (st) return st;
+        Hd = g->stage_out;
+        lh = np;
+    }
+    st = ensure_ws(g, (size_t)np);
+    if (st) return st;
+    g->adjoint_ready = false;
+    g->hess_timed = false;
+    if (g->hess_exec && (g->hess_H != Hd || g->hess_ld != lh || g->hess_V != g->V)) {
+        cudaGraphExecDestroy(g->hess_exec);
+        g->hess_exec = nullptr;
+    }
+    if (!g->hess_exec) {
+        if (!g->stream2) RH_CUDA(cudaStreamCreateWithFlags(&g->stream2, cudaStreamNonBlocking));
+        if (!g->ev_fork) RH_CUDA(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
+        if (!g->ev_join) RH_CUDA(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
+        if (!g->ev_d0) RH_CUDA(cudaEventCreate(&g->ev_d0));
+        if (!g->ev_d1) RH_CUDA(cudaEventCreate(&g->ev_d1));
+        if (!g->ev_v) RH_CUDA(cudaEventCreate(&g->ev_v));
+        if (!g->ev_c) RH_CUDA(cudaEventCreate(&g->ev_c));
+        st = capture_graph(g, [&] { return enqueue_reduced_hessian(g, Hd, lh); }, &g->hess_exec, &g->hess_kernels);
+        if (st) return st;
+        g->hess_H = Hd;
+        g->hess_ld = lh;
+        g->hess_V = g->V;
+    }
+    if (stream) {   // order after the caller's earlier work on its stream
+        if (!g->ev_user) RH_CUDA(cudaEventCreateWithFlags(&g->ev_user, cudaEventDisableTiming));
+        RH_CUDA(cudaEventRecord(g->ev_user, (cudaStream_t)stream));
+        RH_CUDA(cudaStreamWaitEvent(g->stream, g->ev_user, 0));
+    }
+    RH_CUDA(cudaGraphLaunch(g->hess_exec, g->stream));
+    if (host)
+        RH_CUDA(cudaMemcpy2DAsync(H, ldh * sizeof(double), Hd, lh * sizeof(double), np * sizeof(double), np,
+                                  cudaMemcpyDeviceToHost, g->stream));
+    if (grad) RH_CUDA(cudaMemcpyAsync(grad, g->grad, np * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    if (F) RH_CUDA(cudaMemcpyAsync(F, g->dscal + 2, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    st = check_err_flag(g);   // synchronises the stream
+    if (st) return st;
+    g->adjoint_ready = true;
+    g->hess_timed = true;
+    return RH_OK;
+}
+
+rh_status rh_reduced_hessian_times(const rh_grid* g, float* ms) {
+    if (!g || !ms) return fail(RH_EINVAL, "NULL grid or ms");
+    if (!g->hess_timed) return fail(RH_ESTATE, "no completed rh_reduced_hessian call on this grid");
+    RH_CUDA(cudaEventElapsedTime(ms, g->ev_d0, g->ev_d1));
+    RH_CUDA(cudaEventElapsedTime(ms + 1, g->ev_d0, g->ev_v));
+    RH_CUDA(cudaEventElapsedTime(ms + 2, g->ev_d0, g->ev_c));
     return RH_OK;
 }
 
@@ -1172,10 +1318,7 @@ rh_status rh_set_jacobian_method(rh_grid* g, int32_t method) {
     if (method == g->jac_method) return RH_OK;
     g->jac_method = method;
     g->adjoint_ready = false;
-    if (g->adj_exec) {                 // the captured setup holds the previous assembly kernel
-        cudaGraphExecDestroy(g->adj_exec);
-        g->adj_exec = nullptr;
-    }
+    g->drop_graphs();   // the captured setups hold the previous assembly kernel
     return RH_OK;
 }
 

@@ -1612,14 +1612,19 @@ void launch_transpose_values(int nnz, const int* tpos, const double* A, double* 
     if (n > 0) k_transpose_values<<<blocks_for(n, 256), 256, 0, st>>>(nnz, tpos, A, At, nnz_jp, jpt_src, jpv, jptv);
 }
 
-int dirs_default_ctas(int N) {
+static int num_sms() {
     static int n_sm = 0;
     if (n_sm == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 1;
     }
-    int G = N < kDirCtasPerSm * n_sm ? N : kDirCtasPerSm * n_sm;
+    return n_sm;
+}
+
+int dirs_default_ctas(int N) {
+    const int slots = kDirCtasPerSm * num_sms();
+    int G = N < slots ? N : slots;
     int need = (N + kDMax - 1) / kDMax;
     if (G < need) G = need;
     return G < 1 ? 1 : G;
@@ -1668,6 +1673,8 @@ cudaError_t launch_solve1(const DirGrid& g, double* x, unsigned phases, bool use
     k_solve1<<<1, kSolve1Threads, solve1_smem(g.n_x, g.T, use_tail), st>>>(g, x, phases, use_tail ? 1 : 0);
     return cudaGetLastError();
 }
+
+int dirs_cta_slots() { return kDirCtasPerSm * num_sms(); }
 
 void launch_adjoint_coef(const PfGrid& g, const PfState& s, const double* lambda_int, const double* cref,
                          const int* inc_ptr, const int* inc_nb, double4_32a* inc_coef, double* d2, double* asum,

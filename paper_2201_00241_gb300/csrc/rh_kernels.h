@@ -159,7 +159,6 @@ bool dirs_tail_fits(int T, int N, int n_cta);
 // dense tail triangles of the current factors (pos: T*T map to A, -1 where structurally zero)
 void launch_build_tail(int T, int t0, const int* pos, const double* A, const double* invdiag, double* triL,
                        double* triU, double* triUt, double* triLt, cudaStream_t st);
-// one right-hand side in shared memory (requires solve1_fits(n_x))
 // One right-hand side in one CTA with x in shared memory: mode 2 also keeps the
 // dense tail triangle there (needs the tail triangles built), 1 without it,
 // 0 when x does not fit (use the direction kernel instead).
@@ -177,6 +176,8 @@ cudaError_t launch_potrf(int n, double* A, int64_t lda, int* info, double* y, cu
 cudaError_t launch_potrs(int n, const double* L, int64_t ldl, double* B, int64_t ldb, int nrhs, double* work,
                          bool forward, cudaStream_t s);
 int dirs_default_ctas(int N);
+// CTAs of k_dirs the device holds at once (CTAs per SM x SMs)
+int dirs_cta_slots();
 
 // adjoint helpers
 struct AdjData {

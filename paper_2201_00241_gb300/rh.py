@@ -24,7 +24,7 @@ EXPORTS = ["rh_grid_create", "rh_grid_destroy", "rh_grid_dims", "rh_grid_symboli
            "rh_set_state", "rh_powerflow", "rh_adjoint", "rh_hessvec", "rh_hessian", "rh_solve", "rh_refactor",
            "rh_lagrangian_hessvec", "rh_hessvec_noalloc", "rh_hv_work_doubles", "rh_batch_hessvec",
            "rh_potrf", "rh_potrs", "rh_rto_step", "rh_set_jacobian_method", "rh_grid_coloring", "rh_jacobian",
-           "rh_last_error"]
+           "rh_reduced_hessian", "rh_reduced_hessian_times", "rh_last_error"]
 RH_JAC_ANALYTIC, RH_JAC_COLORED_AD = 0, 1
 
 
@@ -49,7 +49,8 @@ class Dims(C.Structure):
     _fields_ = [("n_bus", C.c_int32), ("n_branch", C.c_int32), ("n_gen", C.c_int32), ("n_pv", C.c_int32),
                 ("n_pq", C.c_int32), ("n_x", C.c_int32), ("n_p", C.c_int32), ("n_levels_fwd", C.c_int32),
                 ("n_levels_bwd", C.c_int32), ("nnz_jx", C.c_int64), ("nnz_jp", C.c_int64), ("nnz_l", C.c_int64),
-                ("nnz_u", C.c_int64), ("refactor_updates", C.c_int64), ("setup_kernels", C.c_int32)]
+                ("nnz_u", C.c_int64), ("refactor_updates", C.c_int64), ("setup_kernels", C.c_int32),
+                ("hessian_kernels", C.c_int32)]
 
 
 _lib = None
@@ -94,6 +95,8 @@ def load(build_if_missing: bool = True):
         "rh_set_jacobian_method": ([P, I32], C.c_int),
         "rh_grid_coloring": ([P, P, P, P, P], C.c_int),
         "rh_jacobian": ([P, I32, P, P, P, P, P, P], C.c_int),
+        "rh_reduced_hessian": ([P, P, I64, P, P, P, U32], C.c_int),
+        "rh_reduced_hessian_times": ([P, P], C.c_int),
         "rh_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -250,6 +253,30 @@ class Grid:
         H = np.empty((self.n_p, self.n_p), order="F")
         _check(_lib.rh_hessian(self._h, int(block_n), _ptr(H), self.n_p, C.c_void_p(0), flags))
         return H
+
+    def reduced_hessian(self, out=None, stream=None):
+        """Jacobians, refactorisation, adjoint and the full reduced Hessian in one call
+        (the adjoint solve overlapped with the first direction sweeps).  Returns
+        (H, grad, F); H is ``out`` when given (a CUDA torch tensor, column-major),
+        else a new column-major numpy array."""
+        F = C.c_double(0.0)
+        grad = np.empty(self.n_p)
+        if out is not None and _is_device(out):
+            st = stream if stream is not None else _stream_of(out)
+            _check(_lib.rh_reduced_hessian(self._h, _ptr(out), out.stride(1), C.byref(F), _ptr(grad), st,
+                                           RH_DEVICE_PTRS))
+            return out, grad, float(F.value)
+        H = np.empty((self.n_p, self.n_p), order="F")
+        _check(_lib.rh_reduced_hessian(self._h, _ptr(H), self.n_p, C.byref(F), _ptr(grad), C.c_void_p(0),
+                                       RH_HOST_PTRS))
+        return H, grad, float(F.value)
+
+    def reduced_hessian_times(self):
+        """Device times (ms) of the last reduced_hessian call, from the fork after the
+        factorisation: (both direction launches, the first one, the adjoint branch)."""
+        ms = (C.c_float * 3)()
+        _check(_lib.rh_reduced_hessian_times(self._h, ms))
+        return tuple(float(v) for v in ms)
 
     def solve(self, R, trans=False):
         R = np.array(R, dtype=np.float64, order="F", copy=True)

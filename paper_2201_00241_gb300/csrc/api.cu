@@ -72,8 +72,8 @@ struct rh_grid {
     int n_jp_rows = 0, n_jp_zero = 0;
     double *triL = nullptr, *triU = nullptr, *triUt = nullptr, *triLt = nullptr;
     int *blev_ptr = nullptr, *blev_bus = nullptr, *blev_maxext = nullptr;
-    int *rf_lev_bus = nullptr, *rf_tgt_pos = nullptr, *rf_c_l = nullptr, *rf_c_u = nullptr;
-    int64_t* rf_tgt_cptr = nullptr;
+    int *rf_lev_bus = nullptr, *rf_tgt_pos = nullptr, *rf_grp = nullptr;
+    int64_t* rf_tgt_gptr = nullptr;
     int *jp_ptr = nullptr, *jp_col = nullptr, *jpt_ptr = nullptr, *jpt_row = nullptr, *jpt_src = nullptr;
     int *tp_bus = nullptr, *uth = nullptr, *uv = nullptr, *inc_ptr = nullptr, *inc_nb = nullptr;
     int *inc_uth = nullptr, *inc_uv = nullptr, *gref_row = nullptr, *pg_row = nullptr, *xmap = nullptr;
@@ -201,7 +201,7 @@ struct rh_grid {
         g.n_x = S.n_x; g.t0 = S.t0; g.T = S.n_x - S.t0;
         g.rf_lev_bus = rf_lev_bus; g.q0 = q0; g.nv = nv;
         g.rowptr = rowptr; g.col = col; g.diagpos = diagpos; g.tpos = tpos;
-        g.tgt_pos = rf_tgt_pos; g.tgt_cptr = rf_tgt_cptr; g.c_l = rf_c_l; g.c_u = rf_c_u;
+        g.tgt_pos = rf_tgt_pos; g.tgt_gptr = rf_tgt_gptr; g.grp = reinterpret_cast<const int2*>(rf_grp);
         g.A = A; g.invdiag = invdiag; g.jmax = umax + 1; g.err = err;
         g.tailD = tailD; g.tail_pos = tail_pos;
         return g;
@@ -555,9 +555,8 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     }
     RH_CUDA(g->upload(g->rf_lev_bus, S.rf_lev_bus));
     RH_CUDA(g->upload(g->rf_tgt_pos, S.rf_tgt_pos));
-    RH_CUDA(g->upload(g->rf_tgt_cptr, S.rf_tgt_cptr));
-    RH_CUDA(g->upload(g->rf_c_l, S.rf_c_l));
-    RH_CUDA(g->upload(g->rf_c_u, S.rf_c_u));
+    RH_CUDA(g->upload(g->rf_tgt_gptr, S.rf_tgt_gptr));
+    RH_CUDA(g->upload(g->rf_grp, S.rf_grp));
     RH_CUDA(g->upload(g->jp_ptr, S.jp_ptr));
     {
         std::vector<int> rows, zero;
@@ -634,7 +633,7 @@ rh_status rh_grid_dims(const rh_grid* g, rh_dims* o) {
     o->n_x = S.n_x; o->n_p = S.n_p; o->n_levels_fwd = S.n_flev; o->n_levels_bwd = S.n_blev;
     o->nnz_jx = S.nnz_jx; o->nnz_jp = (int64_t)S.jp_col.size();
     o->nnz_l = S.nnz_l; o->nnz_u = S.nnz_u;
-    o->refactor_updates = (int64_t)S.rf_c_l.size();
+    o->refactor_updates = S.rf_updates;
     o->setup_kernels = g->adj_kernels;
     o->hessian_kernels = g->hess_kernels;
     return RH_OK;

@@ -237,8 +237,8 @@ __global__ void __launch_bounds__(128) k_jac_ad(PfGrid g, PfState s, const int* 
 // fixed-pattern LU refactorisation (row-wise elimination, static pivots)
 // ---------------------------------------------------------------------------
 
-// Right-looking refactorisation, pivot step of one level: one warp per bus k.
-// All entries it reads are final once the previous levels' updates are done.
+// Right-looking refactorisation, pivot step: one warp per bus k.  All entries
+// it reads are final once the updates of the levels before k's are done.
 // Bus block (theta, v) of a PQ bus:
 //   u_tt = a_tt, l_vt = a_vt / u_tt, u_vv = a_vv - l_vt u_tv,
 //   U row of v:    u_vj = a_vj - l_vt u_tj,
@@ -290,14 +290,37 @@ __global__ void k_rf_pivot(RfGrid g, int b0, int nb) {
     }
 }
 
-// Update step of one level: every target entry a_ij of the level subtracts the
-// sum of its contributions l_ik u_kj (fixed order: bus, then theta before v).
+// Update step of one level: every target entry a_ij of the level subtracts
+// sum_k l_ik u_kj over the buses k of the level whose pattern holds i and j
+// (fixed order: bus, then theta before v).  Bus k's entries are final raw
+// values here (its pivot step has not run), so l_it, l_iv and u_vj are formed
+// from them with exactly the operations, in the order, of the pivot step:
+// the factors come out bit for bit as with a pivot launch before every level,
+// and the pivot steps of all sparse buses run once, in one launch, at the end.
+// No entry a group reads is a target of the same level (its bus would depend
+// on the level's own buses).
 __global__ void k_rf_update(RfGrid g, int64_t t0, int64_t nt) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
     t += t0;
     double acc = 0.0;
-    for (int64_t c = g.tgt_cptr[t]; c < g.tgt_cptr[t + 1]; c++) acc = fma(g.A[g.c_l[c]], g.A[g.c_u[c]], acc);
+    for (int64_t c = g.tgt_gptr[t]; c < g.tgt_gptr[t + 1]; c++) {
+        const int2 d = g.grp[3 * c], tu = g.grp[3 * c + 1], vu = g.grp[3 * c + 2];   // {dt, dv} {lt, ut} {lv, uv}
+        const double it = 1.0 / g.A[d.x];
+        const double lt = g.A[tu.x] * it;
+        const double ut = g.A[tu.y];
+        if (d.y >= 0) {
+            const double utv = g.A[d.x + 1];
+            const double lvt = g.A[d.y - 1] * it;
+            const double iv = 1.0 / fma(-lvt, utv, g.A[d.y]);
+            const double lv = fma(-lt, utv, g.A[vu.x]) * iv;
+            const double uv = fma(-lvt, ut, g.A[vu.y]);
+            acc = fma(lt, ut, acc);
+            acc = fma(lv, uv, acc);
+        } else {
+            acc = fma(lt, ut, acc);
+        }
+    }
     const int p = g.tgt_pos[t];
     g.A[p] -= acc;
 }
@@ -1565,11 +1588,11 @@ void launch_newton_update(const PfGrid& g, const PfState& s, const double* dx, c
 cudaError_t launch_refactor(const RfGrid& g, const int* lev_ptr_host, const int64_t* tgt_lev_ptr_host, int n_lev,
                             cudaStream_t st) {
     for (int lev = 0; lev < n_lev; lev++) {
-        int b0 = lev_ptr_host[lev], nb = lev_ptr_host[lev + 1] - b0;
-        if (nb > 0) k_rf_pivot<<<blocks_for((int64_t)nb * 32, 128), 128, 0, st>>>(g, b0, nb);
         int64_t t0 = tgt_lev_ptr_host[lev], nt = tgt_lev_ptr_host[lev + 1] - t0;
         if (nt > 0) k_rf_update<<<blocks_for(nt, 256), 256, 0, st>>>(g, t0, nt);
     }
+    const int nb = lev_ptr_host[n_lev];   // every sparse bus
+    if (nb > 0) k_rf_pivot<<<blocks_for((int64_t)nb * 32, 128), 128, 0, st>>>(g, 0, nb);
     if (g.T > 0) {
         const int TT = g.T * g.T, nt = (g.T + kTailTB - 1) / kTailTB;
         k_tail_gather<<<blocks_for(TT, 256), 256, 0, st>>>(g);

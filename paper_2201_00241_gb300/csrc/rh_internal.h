@@ -49,18 +49,23 @@ struct Symbolic {
     int64_t nnz_l = 0, nnz_u = 0;
 
     // Refactorisation schedule.  Buses before tail_bus0 (variables < t0) are
-    // eliminated right-looking, one forward level at a time: the pivot step of a
-    // level finalises the 2x2 (or 1x1) pivot block, U rows and L columns of its
-    // buses; the update step applies a_ij -= sum_k l_ik u_kj to every target
-    // entry of the level, summing its contributions in a fixed order.  The
-    // trailing block [t0, n_x) is then factored densely in one CTA.
+    // eliminated right-looking, one forward level at a time: the update step of
+    // a level applies a_ij -= sum_k l_ik u_kj to every target entry of the level
+    // (buses k of the level in a fixed order, theta before v), forming bus k's
+    // factor entries on the fly from its final raw entries; the pivot steps,
+    // which write every sparse bus's 2x2 (or 1x1) pivot block, U row and L
+    // column, run once after the last level.  The trailing block [t0, n_x) is
+    // then factored densely.
     int t0 = 0, tail_bus0 = 0;
     int rf_n_lev = 0;
     std::vector<int> rf_lev_ptr, rf_lev_bus;        // sparse buses grouped by level
     std::vector<int64_t> rf_tgt_lev_ptr;            // level -> first target
     std::vector<int> rf_tgt_pos;                    // target position in A
-    std::vector<int64_t> rf_tgt_cptr;               // target -> first contribution
-    std::vector<int> rf_c_l, rf_c_u;                // contribution: positions of l_ik and u_kj
+    std::vector<int64_t> rf_tgt_gptr;               // target -> first group
+    // group (target, bus k): 6 positions in A: k's theta and v diagonals (dv = -1
+    // for a PV bus), a_it, a_tj, a_iv, a_vj (-1, -1 for a PV bus)
+    std::vector<int> rf_grp;
+    int64_t rf_updates = 0;                         // multiply-subtracts of one refactorisation
 
     // admittance matrix (CSR by bus, diagonal included, parallel branches merged)
     std::vector<int> yp, yj;

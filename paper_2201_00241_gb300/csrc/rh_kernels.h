@@ -142,8 +142,8 @@ struct RfGrid {
     const uint8_t *nv;
     const int *rowptr, *col, *diagpos, *tpos;
     const int *tgt_pos;                // update targets (positions in A), grouped by level
-    const int64_t *tgt_cptr;           // target -> first contribution
-    const int *c_l, *c_u;              // contribution positions of l_ik and u_kj
+    const int64_t *tgt_gptr;           // target -> first group
+    const int2 *grp;                   // 3 per group: {dt, dv}, {a_it, a_tj}, {a_iv, a_vj} positions
     double *A, *invdiag;
     const unsigned long long *jmax;
     int *err;

@@ -6,6 +6,7 @@
 // L + U, the bus-level schedules and the index maps used by the kernels.
 // Numerical work (Jacobian values, LU values, solves) runs on the device.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <functional>
 #include <queue>
@@ -268,18 +269,23 @@ std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int
         S.rf_lev_ptr.assign(1, 0);
         S.rf_lev_bus.clear();
         S.rf_tgt_lev_ptr.assign(1, 0);
-        S.rf_tgt_cptr.assign(1, 0);
-        std::vector<std::tuple<int, int, int, int>> trip;   // (target, order, lpos, upos)
+        S.rf_tgt_gptr.assign(1, 0);
+        S.rf_grp.clear();
+        S.rf_updates = 0;
+        // (target, bus order, {dt, dv, lt, ut, lv, uv}): one group per target and bus
+        using Grp = std::tuple<int, int, std::array<int, 6>>;
+        std::vector<Grp> grp;
         for (auto& v : by_lev) {
             if (v.empty()) continue;
-            trip.clear();
+            grp.clear();
             int order = 0;
             for (int k : v) {
                 S.rf_lev_bus.push_back(k);
                 int qt = S.q0[k];
                 bool two = S.nv[k] == 2;
-                int ut0 = S.diagpos[qt] + (two ? 2 : 1);
-                int uv0 = two ? S.diagpos[qt + 1] + 1 : -1;
+                int dt = S.diagpos[qt], dv = two ? S.diagpos[qt + 1] : -1;
+                int ut0 = dt + (two ? 2 : 1);
+                int uv0 = two ? dv + 1 : -1;
                 int n = S.rowptr[qt + 1] - ut0;
                 for (int a = 0; a < n; a++) {
                     int i = S.col[ut0 + a];
@@ -288,23 +294,24 @@ std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int
                         int j = S.col[ut0 + bb];
                         int tg = find_in_row(S.rowptr, S.col, i, j);
                         if (tg < 0) return "internal error: fill pattern not closed";
-                        trip.emplace_back(tg, order, lt, ut0 + bb);
-                        if (two) trip.emplace_back(tg, order + 1, lv, uv0 + bb);
+                        grp.emplace_back(tg, order, std::array<int, 6>{dt, dv, lt, ut0 + bb, lv, two ? uv0 + bb : -1});
+                        S.rf_updates += two ? 2 : 1;
                     }
                 }
-                order += 2;
+                order++;
             }
-            std::sort(trip.begin(), trip.end());
-            for (size_t t = 0; t < trip.size(); t++) {
-                int tg = std::get<0>(trip[t]);
-                if (t == 0 || std::get<0>(trip[t - 1]) != tg) {
-                    if (t > 0) S.rf_tgt_cptr.push_back((int64_t)S.rf_c_l.size());
+            std::sort(grp.begin(), grp.end(),
+                      [](const Grp& x, const Grp& y) { return std::tie(std::get<0>(x), std::get<1>(x)) <
+                                                             std::tie(std::get<0>(y), std::get<1>(y)); });
+            for (size_t t = 0; t < grp.size(); t++) {
+                int tg = std::get<0>(grp[t]);
+                if (t == 0 || std::get<0>(grp[t - 1]) != tg) {
+                    if (t > 0) S.rf_tgt_gptr.push_back((int64_t)(S.rf_grp.size() / 6));
                     S.rf_tgt_pos.push_back(tg);
                 }
-                S.rf_c_l.push_back(std::get<2>(trip[t]));
-                S.rf_c_u.push_back(std::get<3>(trip[t]));
+                for (int x : std::get<2>(grp[t])) S.rf_grp.push_back(x);
             }
-            if (!trip.empty()) S.rf_tgt_cptr.push_back((int64_t)S.rf_c_l.size());
+            if (!grp.empty()) S.rf_tgt_gptr.push_back((int64_t)(S.rf_grp.size() / 6));
             S.rf_lev_ptr.push_back((int)S.rf_lev_bus.size());
             S.rf_tgt_lev_ptr.push_back((int64_t)S.rf_tgt_pos.size());
         }

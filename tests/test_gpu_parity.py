@@ -117,6 +117,30 @@ def test_refactor_reproduces_permuted_jacobian(case):
     lg.adjoint()  # restore the hessvec-ready state for later tests
 
 
+@pytest.mark.parametrize("case", ["case1354", "case9241"])
+def test_refactor_sparse_product_large(case):
+    """Every level of the update schedule and the closing pivot launch on the larger
+    grids: L U against the permuted J_x, as sparse matrices."""
+    import scipy.sparse as sp
+    d = setup_case(case)
+    lg, o = d["lg"], d["o"]
+    A = lg.refactor()
+    sym = lg.symbolic()
+    n = lg.n_x
+    Lp, Lj, Up, Uj = (np.asarray(sym[k], dtype=np.int64) for k in ("Lp", "Lj", "Up", "Uj"))
+    # row r of A holds its L part then its U part, from position Lp[r] + Up[r]
+    rows_l = np.repeat(np.arange(n), np.diff(Lp))
+    rows_u = np.repeat(np.arange(n), np.diff(Up))
+    L = sp.csr_matrix((A[Up[rows_l] + np.arange(len(Lj))], Lj, Lp), shape=(n, n)) + sp.identity(n, format="csr")
+    U = sp.csr_matrix((A[Lp[rows_u + 1] + np.arange(len(Uj))], Uj, Up), shape=(n, n))
+    Jx, _ = o.jacobians_csc(d["x_o"], d["so"].p)
+    perm = np.asarray(sym["perm"])
+    B = sp.csr_matrix(Jx)[perm][:, perm]
+    diff = (L @ U - B).tocoo()
+    assert np.abs(diff.data).max(initial=0.0) <= 1e-12 * np.abs(B.data).max()
+    lg.adjoint()  # restore the hessvec-ready state for later tests
+
+
 @pytest.mark.parametrize("nrhs", [1, 3, 31, 32, 33, 64])
 @pytest.mark.parametrize("trans", [False, True])
 def test_batched_solves(nrhs, trans):

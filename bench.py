@@ -75,13 +75,14 @@ def replica_throughput(units_per_rank, world, seconds):
 
 
 def measured_traffic():
-    """DRAM bytes per k_dirs launch from the committed ncu capture, if the kernel source is unchanged."""
+    """DRAM bytes of one step's two k_dirs launches from the committed ncu capture, if the kernel
+    source is unchanged."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "k_dirs_case9241_traffic.json")))
         src = os.path.join(ROOT, "paper_2201_00241_gb300", "csrc", "kernels.cu")
         if hashlib.sha256(open(src, "rb").read()).hexdigest() == rec["kernels_cu_sha256"]:
-            return int(rec["dram_bytes_per_launch"])
+            return int(rec["dram_bytes_per_step"])
     except (OSError, ValueError, KeyError):
         pass
     return None

@@ -820,7 +820,7 @@ rh_status capture_graph(rh_grid* g, F&& enqueue, cudaGraphExec_t* exec, int* ker
 
 // rh_reduced_hessian's device work.  After the factorisation the adjoint chain
 // forks onto stream2 (its single solve as one direction CTA) while
-// the direction kernel runs SpMul and the L and U sweeps on one CTA less than the
+// the direction kernel runs SpMul and the L and U sweeps on fewer CTAs than the
 // device holds, so the two run at once; after the join a second direction launch
 // runs the projection, the transposed sweeps and SpMulAdd.  The directions of the
 // two launches are independent columns of V, so their CTA counts may differ.
@@ -833,8 +833,11 @@ rh_status enqueue_reduced_hessian(rh_grid* g, double* Hd, int64_t lh) {
     st = enqueue_adjoint_chain(g, g->stream2, true);
     if (st) return st;
     RH_CUDA(cudaEventRecordWithFlags(g->ev_d0, g->stream, cudaEventRecordExternal));
+    // the fewest CTAs with the directions per CTA of a launch one slot short of full: the
+    // slots left over (7 SMs' worth for the 9241-bus grid) are the adjoint branch's
+    const int per = (np + rh::dirs_cta_slots() - 2) / (rh::dirs_cta_slots() - 1);
     st = dirs(g, np, np, g->V, g->T, nullptr, 0, 0, Hd, lh, rh::PH_WLOAD | rh::PH_SPMUL | rh::PH_L | rh::PH_U,
-              g->stream, rh::dirs_cta_slots() - 1);
+              g->stream, std::max(1, (np + per - 1) / per));
     if (st) return st;
     RH_CUDA(cudaEventRecordWithFlags(g->ev_v, g->stream, cudaEventRecordExternal));
     RH_CUDA(cudaEventRecordWithFlags(g->ev_c, g->stream2, cudaEventRecordExternal));

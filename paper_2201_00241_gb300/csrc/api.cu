@@ -71,6 +71,10 @@ struct rh_grid {
     int *jp_rows = nullptr, *jp_zero_rows = nullptr;
     int n_jp_rows = 0, n_jp_zero = 0;
     double *triL = nullptr, *triU = nullptr, *triUt = nullptr, *triLt = nullptr;
+    // unit-diagonal factors of the direction kernel (J_x = D L'' U')
+    double *Ad = nullptr, *Atd = nullptr, *jptvd = nullptr;
+    int* arow = nullptr;   // row of every position of A
+    double *triLd = nullptr, *triUd = nullptr, *triUtd = nullptr, *triLtd = nullptr;
     int *blev_ptr = nullptr, *blev_bus = nullptr, *blev_maxext = nullptr;
     int *rf_lev_bus = nullptr, *rf_tgt_pos = nullptr, *rf_grp = nullptr;
     int64_t* rf_tgt_gptr = nullptr;
@@ -185,6 +189,8 @@ struct rh_grid {
         g.ef = {n_ef, ef_ptr, ef_slot, ef_maxext};
         g.t0 = S.t0; g.T = S.n_x - S.t0;
         g.triL = triL; g.triU = triU; g.triUt = triUt; g.triLt = triLt;
+        g.Ad = Ad; g.Atd = Atd; g.jptvd = jptvd;
+        g.triLd = triLd; g.triUd = triUd; g.triUtd = triUtd; g.triLtd = triLtd;
         g.qtheta = qtheta; g.bparent = bparent;
         g.jp_ptr = jp_ptr; g.jp_col = jp_col; g.jpv = jpv;
         g.n_jp_rows = n_jp_rows; g.n_jp_zero = n_jp_zero; g.jp_rows = jp_rows; g.jp_zero_rows = jp_zero_rows;
@@ -263,6 +269,17 @@ rh_status assemble(rh_grid* g, int method, double* gres, cudaStream_t s) {
     return RH_OK;
 }
 
+// Transposed values, the direction kernel's unit-diagonal factors and the dense
+// tail's triangles from the current LU (enqueue only).
+void enqueue_factor_copies(rh_grid* g, cudaStream_t s) {
+    const auto& S = g->S;
+    rh::launch_transpose_values((int)S.col.size(), g->tpos, g->arow, g->col, g->diagpos, g->A, g->invdiag, g->At,
+                                g->Ad, g->Atd, (int)S.jp_col.size(), g->jpt_src, g->jpt_row, g->jpv, g->jptv,
+                                g->jptvd, s);
+    rh::launch_build_tail(S.n_x - S.t0, S.t0, g->tail_pos, g->A, g->invdiag, g->triL, g->triU, g->triUt, g->triLt,
+                          g->triLd, g->triUd, g->triUtd, g->triLtd, s);
+}
+
 // J_x, J_p at the current state, refactorisation, transposed copies (enqueue only).
 rh_status enqueue_factor(rh_grid* g) {
     const auto& S = g->S;
@@ -273,9 +290,7 @@ rh_status enqueue_factor(rh_grid* g) {
     rh_status st = assemble(g, g->jac_method, nullptr, s);
     if (st) return st;
     RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_tgt_lev_ptr.data(), S.rf_n_lev, s));
-    rh::launch_transpose_values((int)S.col.size(), g->tpos, g->A, g->At, (int)S.jp_col.size(), g->jpt_src, g->jpv,
-                                g->jptv, s);
-    rh::launch_build_tail(S.n_x - S.t0, S.t0, g->tail_pos, g->A, g->invdiag, g->triL, g->triU, g->triUt, g->triLt, s);
+    enqueue_factor_copies(g, s);
     RH_CUDA(cudaGetLastError());
     return RH_OK;
 }
@@ -320,7 +335,13 @@ rh_status solve_one(rh_grid* g, unsigned phases, cudaStream_t s, bool beside_dir
         RH_CUDA(rh::launch_solve1(g->dir(), g->v1, phases, mode == 2, s));
         return RH_OK;
     }
-    return dirs(g, 1, 1, g->v1, g->v1, nullptr, 0, 0, nullptr, 0, phases, s);
+    // through k_dirs, whose factors are unit-diagonal (J_x = D L'' U'): the right-hand
+    // side of J_x z = b enters as D^-1 b, and J_x^T's solution D psi leaves as psi
+    if (phases & rh::PH_L) rh::launch_scale_rows(g->S.n_x, 1, g->invdiag, g->v1, 1, s);
+    rh_status st = dirs(g, 1, 1, g->v1, g->v1, nullptr, 0, 0, nullptr, 0, phases, s);
+    if (st) return st;
+    if (phases & rh::PH_LT) rh::launch_scale_rows(g->S.n_x, 1, g->invdiag, g->v1, 1, s);
+    return RH_OK;
 }
 
 __global__ void k_set_p(int n_bus, const int* ip_v, const int* ip_pg, const double* p, double* vm, double* pg) {
@@ -457,6 +478,12 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     RH_CUDA(g->upload(g->col, S.col));
     RH_CUDA(g->upload(g->diagpos, S.diagpos));
     RH_CUDA(g->upload(g->tpos, S.tpos));
+    {
+        std::vector<int> arow(S.col.size());
+        for (int q = 0; q < S.n_x; q++)
+            for (int e = S.rowptr[q]; e < S.rowptr[q + 1]; e++) arow[e] = q;
+        RH_CUDA(g->upload(g->arow, arow));
+    }
     RH_CUDA(g->upload(g->q0, S.q0));
     RH_CUDA(g->upload(g->nv, S.nv));
     RH_CUDA(g->upload(g->flev_ptr, flev_ptr));
@@ -552,6 +579,10 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
         RH_CUDA(g->alloc(g->triU, ntri));
         RH_CUDA(g->alloc(g->triUt, ntri));
         RH_CUDA(g->alloc(g->triLt, ntri));
+        RH_CUDA(g->alloc(g->triLd, ntri));
+        RH_CUDA(g->alloc(g->triUd, ntri));
+        RH_CUDA(g->alloc(g->triUtd, ntri));
+        RH_CUDA(g->alloc(g->triLtd, ntri));
     }
     RH_CUDA(g->upload(g->rf_lev_bus, S.rf_lev_bus));
     RH_CUDA(g->upload(g->rf_tgt_pos, S.rf_tgt_pos));
@@ -592,9 +623,12 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     RH_CUDA(g->alloc(g->Q, nb));
     RH_CUDA(g->alloc(g->A, S.col.size()));
     RH_CUDA(g->alloc(g->At, S.col.size()));
+    RH_CUDA(g->alloc(g->Ad, S.col.size()));
+    RH_CUDA(g->alloc(g->Atd, S.col.size()));
     RH_CUDA(g->alloc(g->invdiag, nx));
     RH_CUDA(g->alloc(g->jpv, S.jp_col.size()));
     RH_CUDA(g->alloc(g->jptv, S.jp_col.size()));
+    RH_CUDA(g->alloc(g->jptvd, S.jp_col.size()));
     RH_CUDA(g->alloc(g->gres, nx));
     RH_CUDA(g->alloc(g->lam, nx));
     RH_CUDA(g->alloc(g->grad, np));
@@ -721,8 +755,7 @@ rh_status rh_powerflow(rh_grid* g, const double* x0, double tol, int32_t max_ite
         if (res <= tol) { out = RH_OK; break; }
         if (it >= max_iter || !std::isfinite(res)) break;
         RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_tgt_lev_ptr.data(), S.rf_n_lev, s));
-        rh::launch_build_tail(S.n_x - S.t0, S.t0, g->tail_pos, g->A, g->invdiag, g->triL, g->triU, g->triUt,
-                              g->triLt, s);
+        enqueue_factor_copies(g, s);
         st = check_err_flag(g);
         if (st) return st;
         RH_CUDA(cudaMemcpyAsync(g->v1, g->gres, nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1121,9 +1154,12 @@ rh_status rh_solve(rh_grid* g, double* R, int64_t ldr, int32_t nrhs, int32_t tra
         lr = S.n_x;
     }
     rh::launch_scatter_rows(S.n_x, nrhs, g->xmap, Rd, lr, g->V, nrhs, 1.0, S.n_x, s);
+    // unit-diagonal factors (J_x = D L'' U'): D^-1 R in, or D^-1 out for the transpose
+    if (!trans) rh::launch_scale_rows(S.n_x, nrhs, g->invdiag, g->V, nrhs, s);
     st = dirs(g, nrhs, nrhs, g->V, g->V, nullptr, 0, 0, nullptr, 0,
               trans ? (rh::PH_UT | rh::PH_LT) : (rh::PH_L | rh::PH_U), s);
     if (st) return st;
+    if (trans) rh::launch_scale_rows(S.n_x, nrhs, g->invdiag, g->V, nrhs, s);
     rh::launch_gather_rows(S.n_x, nrhs, g->xmap, g->V, nrhs, Rd, lr, 1.0, S.n_x, s);
     RH_CUDA(cudaGetLastError());
     if (host) {

@@ -458,33 +458,74 @@ __global__ void k_tail_scatter(RfGrid g) {
     }
 }
 
-__global__ void k_transpose_values(int nnz, const int* __restrict__ tpos, const double* __restrict__ A,
-                                   double* __restrict__ At, int nnz_jp, const int* __restrict__ jpt_src,
-                                   const double* __restrict__ jpv, double* __restrict__ jptv) {
+// Transposed copies of the factor values and of J_p, and the unit-diagonal
+// factors of the direction kernel.  With D = diag(U), J_x = L U = D L'' U' where
+// L'' = D^-1 L D and U' = D^-1 U are both unit triangular:
+//   l''_qc = l_qc u_cc / u_qq (c < q),   u'_qc = u_qc / u_qq (c > q).
+// J_x z = b is then L'' y = D^-1 b, U' z = y, and J_x^T psi = r is U'^T u = r,
+// L''^T w = u, psi = D^-1 w: no sweep multiplies by a pivot, and D^-1 folds into
+// the rows of J_p (SpMul's right-hand sides, SpMulAdd's J_p^T psi).  One thread
+// per position of A (row arow[i], column col[i]) and per entry of J_p.
+__device__ __forceinline__ double unit_scale(const double* A, const int* diagpos, const double* invdiag, int r,
+                                             int c) {
+    return c < r ? A[diagpos[c]] * invdiag[r] : (c > r ? invdiag[r] : 0.0);
+}
+__global__ void k_transpose_values(int nnz, const int* __restrict__ tpos, const int* __restrict__ arow,
+                                   const int* __restrict__ col, const int* __restrict__ diagpos,
+                                   const double* __restrict__ A, const double* __restrict__ invdiag,
+                                   double* __restrict__ At, double* __restrict__ Ad, double* __restrict__ Atd,
+                                   int nnz_jp, const int* __restrict__ jpt_src, const int* __restrict__ jpt_row,
+                                   const double* __restrict__ jpv, double* __restrict__ jptv,
+                                   double* __restrict__ jptvd) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nnz) At[i] = A[tpos[i]];
-    if (i < nnz_jp) jptv[i] = jpv[jpt_src[i]];
+    if (i < nnz) {
+        const int r = arow[i], c = col[i];
+        const double at = A[tpos[i]];
+        At[i] = at;
+        Ad[i] = r == c ? 1.0 : A[i] * unit_scale(A, diagpos, invdiag, r, c);
+        Atd[i] = r == c ? 1.0 : at * unit_scale(A, diagpos, invdiag, c, r);
+    }
+    if (i < nnz_jp) {
+        const double v = jpv[jpt_src[i]];
+        jptv[i] = v;
+        jptvd[i] = v * invdiag[jpt_row[i]];
+    }
 }
 
 // The four packed triangles of the dense tail for the sweeps, one thread per
 // (i, j) of the T x T block; pos maps (i, j) to A (-1: structurally zero).
+// x[r] *= s[r] for the first n rows of an n x N row-major block (leading dimension ld)
+__global__ void k_scale_rows(int n, int N, const double* __restrict__ s, double* x, int64_t ld) {
+    const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= (int64_t)n * N) return;
+    const int r = (int)(it / N), c = (int)(it - (int64_t)r * N);
+    x[(int64_t)r * ld + c] *= s[r];
+}
+
+// The dense tail's triangles: for the single solves (columns of U scaled by
+// 1/u_jj), and of the unit-diagonal factors L'', U' for the direction kernel.
 __global__ void k_build_tail(int T, int t0, const int* __restrict__ pos, const double* __restrict__ A,
                              const double* __restrict__ invdiag, double* triL, double* triU, double* triUt,
-                             double* triLt) {
+                             double* triLt, double* triLd, double* triUd, double* triUtd, double* triLtd) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= T * T) return;
     int i = idx / T, j = idx - i * T;
     if (i == j) return;
     int pij = pos[idx], pji = pos[j * T + i];
     double aij = pij >= 0 ? A[pij] : 0.0, aji = pji >= 0 ? A[pji] : 0.0;
+    const double ii = invdiag[t0 + i], ij = invdiag[t0 + j];
     if (i > j) {
         int o = j * (T - 1) - j * (j - 1) / 2 + (i - j - 1);
         triL[o] = aij;                              // L_ij
-        triUt[o] = aji * invdiag[t0 + j];           // (U^T)_ij = U_ji, scaled by 1/u_jj
+        triUt[o] = aji * ij;                        // (U^T)_ij = U_ji, scaled by 1/u_jj
+        triLd[o] = aij * A[pos[j * T + j]] * ii;    // L''_ij
+        triUtd[o] = aji * ij;                       // (U'^T)_ij = U'_ji
     } else {
         int o = j * (j - 1) / 2 + i;
-        triU[o] = aij * invdiag[t0 + j];            // U_ij scaled by 1/u_jj
+        triU[o] = aij * ij;                         // U_ij scaled by 1/u_jj
         triLt[o] = aji;                             // (L^T)_ij = L_ji
+        triUd[o] = aij * ii;                        // U'_ij
+        triLtd[o] = aji * A[pos[i * T + i]] * ij;   // (L''^T)_ij = L''_ji
     }
 }
 
@@ -983,7 +1024,7 @@ __device__ __forceinline__ void muladd_row(const DirGrid& g, const DirLaunch& L,
     for (int w = 0; w < W; w++) h[w] = T[(int64_t)(g.n_x + k) * ld + d0 + w];
     const int t1 = g.jpt_ptr[k + 1];
     for (int t = g.jpt_ptr[k]; t < t1; t++) {
-        const double v = g.jptv[t];
+        const double v = g.jptvd[t];
         const double* pr = T + (int64_t)g.jpt_row[t] * ld + d0;
 #pragma unroll
         for (int w = 0; w < W; w++) h[w] = fma(v, pr[w], h[w]);
@@ -1042,7 +1083,7 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
         for (int d = threadIdx.x / 8; d < D; d += blockDim.x / 8) {
             const int k = L.col0 + c0 + d;
             for (int t = g.jpt_ptr[k] + (threadIdx.x & 7); t < g.jpt_ptr[k + 1]; t += 8)
-                V[(int64_t)g.jpt_row[t] * ld + d] = -g.jptv[t];
+                V[(int64_t)g.jpt_row[t] * ld + d] = -g.jptvd[t];
         }
         __syncthreads();
     } else if ((L.phases & PH_SPMUL) && !L.W) {
@@ -1057,7 +1098,7 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
         for (int d = threadIdx.x / 8; d < D; d += blockDim.x / 8) {
             const int k = L.col0 + c0 + d;
             for (int t = g.jpt_ptr[k] + (threadIdx.x & 7); t < g.jpt_ptr[k + 1]; t += 8)
-                V[(int64_t)g.jpt_row[t] * ld + d] = -g.jptv[t];
+                V[(int64_t)g.jpt_row[t] * ld + d] = -g.jptvd[t];
         }
         __syncthreads();
     } else if (L.phases & PH_SPMUL) {
@@ -1072,7 +1113,7 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
             double s = 0.0;
             for (int t = g.jp_ptr[q]; t < g.jp_ptr[q + 1]; t++)
                 s = fma(g.jpv[t], V[(int64_t)(g.n_x + g.jp_col[t]) * ld + d], s);
-            V[(int64_t)q * ld + d] = -s;
+            V[(int64_t)q * ld + d] = -s * g.invdiag[q];     // D^-1 B for the unit-diagonal factors
         }
         __syncthreads();
     }
@@ -1095,17 +1136,17 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
                 }
                 __syncthreads();
             }
-            sweep_fwd<false>(g, g.sf, g.A, V, ld, 0, D, part, mask, seed);
-            sweep_fwd<false, true>(g, g.ef, g.A, V, ld, 0, D, part);
-            tail_fwd<false>(g, g.triL, V, ld, 0, D, part, nullptr);
+            sweep_fwd<false>(g, g.sf, g.Ad, V, ld, 0, D, part, mask, seed);
+            sweep_fwd<false, true>(g, g.ef, g.Ad, V, ld, 0, D, part);
+            tail_fwd<false>(g, g.triLd, V, ld, 0, D, part, nullptr);
         }
         if (L.phases & PH_U) {
-            tail_bwd<true>(g, g.triU, V, ld, 0, D, part, nullptr);
-            sweep_bwd<true>(g, g.sb, g.A, V, ld, 0, D, part);
+            tail_bwd<false>(g, g.triUd, V, ld, 0, D, part, nullptr);
+            sweep_bwd<false>(g, g.sb, g.Ad, V, ld, 0, D, part);
         }
     } else {
-        if (L.phases & PH_L) sweep_fwd<false>(g, g.lf, g.A, V, ld, 0, D, part);
-        if (L.phases & PH_U) sweep_bwd<true>(g, g.lb, g.A, V, ld, 0, D, part);
+        if (L.phases & PH_L) sweep_fwd<false>(g, g.lf, g.Ad, V, ld, 0, D, part);
+        if (L.phases & PH_U) sweep_bwd<false>(g, g.lb, g.Ad, V, ld, 0, D, part);
     }
     if (L.phases & PH_TPROJ) {
         tproj(g, V, T, ld, 0, D, sref);
@@ -1113,17 +1154,17 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
     }
     if (L.use_tail) {
         if (L.phases & PH_UT) {
-            sweep_fwd<true>(g, g.sf, g.At, T, ld, 0, D, part);
-            sweep_fwd<true, true>(g, g.ef, g.At, T, ld, 0, D, part);
-            tail_fwd<true>(g, g.triUt, T, ld, 0, D, part, nullptr);
+            sweep_fwd<false>(g, g.sf, g.Atd, T, ld, 0, D, part);
+            sweep_fwd<false, true>(g, g.ef, g.Atd, T, ld, 0, D, part);
+            tail_fwd<false>(g, g.triUtd, T, ld, 0, D, part, nullptr);
         }
         if (L.phases & PH_LT) {
-            tail_bwd<false>(g, g.triLt, T, ld, 0, D, part, nullptr);
-            sweep_bwd<false>(g, g.sb, g.At, T, ld, 0, D, part);
+            tail_bwd<false>(g, g.triLtd, T, ld, 0, D, part, nullptr);
+            sweep_bwd<false>(g, g.sb, g.Atd, T, ld, 0, D, part);
         }
     } else {
-        if (L.phases & PH_UT) sweep_fwd<true>(g, g.lf, g.At, T, ld, 0, D, part);
-        if (L.phases & PH_LT) sweep_bwd<false>(g, g.lb, g.At, T, ld, 0, D, part);
+        if (L.phases & PH_UT) sweep_fwd<false>(g, g.lf, g.Atd, T, ld, 0, D, part);
+        if (L.phases & PH_LT) sweep_bwd<false>(g, g.lb, g.Atd, T, ld, 0, D, part);
     }
     if (L.phases & PH_MULADD) {
         for (int k = threadIdx.x; k < g.n_p; k += blockDim.x) {
@@ -1629,10 +1670,14 @@ cudaError_t prepare_kernels() {
     return cudaSuccess;
 }
 
-void launch_transpose_values(int nnz, const int* tpos, const double* A, double* At, int nnz_jp,
-                             const int* jpt_src, const double* jpv, double* jptv, cudaStream_t st) {
+void launch_transpose_values(int nnz, const int* tpos, const int* arow, const int* col, const int* diagpos,
+                             const double* A, const double* invdiag, double* At, double* Ad, double* Atd, int nnz_jp,
+                             const int* jpt_src, const int* jpt_row, const double* jpv, double* jptv, double* jptvd,
+                             cudaStream_t st) {
     int n = nnz > nnz_jp ? nnz : nnz_jp;
-    if (n > 0) k_transpose_values<<<blocks_for(n, 256), 256, 0, st>>>(nnz, tpos, A, At, nnz_jp, jpt_src, jpv, jptv);
+    if (n > 0)
+        k_transpose_values<<<blocks_for(n, 256), 256, 0, st>>>(nnz, tpos, arow, col, diagpos, A, invdiag, At, Ad, Atd,
+                                                               nnz_jp, jpt_src, jpt_row, jpv, jptv, jptvd);
 }
 
 static int num_sms() {
@@ -1672,9 +1717,16 @@ void launch_dirs_batch(const DirBatch& B, int max_T, cudaStream_t st) {
     k_dirs_batch<<<B.cta_ptr[B.n_items], kDirThreads, 0, st>>>(B);
 }
 
+void launch_scale_rows(int n, int N, const double* s, double* x, int64_t ld, cudaStream_t st) {
+    if ((int64_t)n * N > 0) k_scale_rows<<<blocks_for((int64_t)n * N, 256), 256, 0, st>>>(n, N, s, x, ld);
+}
+
 void launch_build_tail(int T, int t0, const int* pos, const double* A, const double* invdiag, double* triL,
-                       double* triU, double* triUt, double* triLt, cudaStream_t st) {
-    if (T > 1) k_build_tail<<<blocks_for((int64_t)T * T, 256), 256, 0, st>>>(T, t0, pos, A, invdiag, triL, triU, triUt, triLt);
+                       double* triU, double* triUt, double* triLt, double* triLd, double* triUd, double* triUtd,
+                       double* triLtd, cudaStream_t st) {
+    if (T > 1)
+        k_build_tail<<<blocks_for((int64_t)T * T, 256), 256, 0, st>>>(T, t0, pos, A, invdiag, triL, triU, triUt, triLt,
+                                                                      triLd, triUd, triUtd, triLtd);
 }
 
 void launch_adjoint_rhs(const PfGrid& g, const PfState& s, const AdjData& a, cudaStream_t st) {

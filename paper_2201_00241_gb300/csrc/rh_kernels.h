@@ -46,6 +46,12 @@ struct DirGrid {
     //   triUt (U^T, lower, column j scaled) triLt (L^T, upper, unit)
     int t0, T;
     const double *triL, *triU, *triUt, *triLt;
+    // Unit-diagonal factors used by k_dirs (J_x = D L'' U', D = diag(U)): values of
+    // L'' and U' in A's pattern and transposed, the dense tail's triangles of L'',
+    // U', U'^T, L''^T, and D^-1 J_p by p index (jptvd)
+    const double *Ad, *Atd;
+    const double *triLd, *triUd, *triUtd, *triLtd;
+    const double *jptvd;
     // bus structure by theta row: theta row of the bus owning row q; theta row of the
     // bus's elimination-tree parent (-1 for a root or a parent in the dense tail)
     const int *qtheta, *bparent;
@@ -150,15 +156,23 @@ struct RfGrid {
 };
 cudaError_t launch_refactor(const RfGrid& g, const int* lev_ptr_host, const int64_t* tgt_lev_ptr_host, int n_lev,
                             cudaStream_t st);
-void launch_transpose_values(int nnz, const int* tpos, const double* A, double* At, int nnz_jp,
-                             const int* jpt_src, const double* jpv, double* jptv, cudaStream_t st);
+// At (transposed values), Ad / Atd (the unit-diagonal factors L'', U' of J_x = D L'' U'
+// and their transpose), jptv (J_p by p index) and jptvd (D^-1 J_p by p index)
+void launch_transpose_values(int nnz, const int* tpos, const int* arow, const int* col, const int* diagpos,
+                             const double* A, const double* invdiag, double* At, double* Ad, double* Atd, int nnz_jp,
+                             const int* jpt_src, const int* jpt_row, const double* jpv, double* jptv, double* jptvd,
+                             cudaStream_t st);
 void launch_dirs(const DirGrid& g, const DirLaunch& L, cudaStream_t st);
 // raise the dynamic shared-memory limits of the kernels that need it (once per grid)
 cudaError_t prepare_kernels();
 bool dirs_tail_fits(int T, int N, int n_cta);
 // dense tail triangles of the current factors (pos: T*T map to A, -1 where structurally zero)
+// x[r][c] *= s[r] for r < n, c < N
+void launch_scale_rows(int n, int N, const double* s, double* x, int64_t ld, cudaStream_t st);
+// triangles of the single solves (triL .. triLt) and of the unit-diagonal factors (triLd .. triLtd)
 void launch_build_tail(int T, int t0, const int* pos, const double* A, const double* invdiag, double* triL,
-                       double* triU, double* triUt, double* triLt, cudaStream_t st);
+                       double* triU, double* triUt, double* triLt, double* triLd, double* triUd, double* triUtd,
+                       double* triLtd, cudaStream_t st);
 // One right-hand side in one CTA with x in shared memory: mode 2 also keeps the
 // dense tail triangle there (needs the tail triangles built), 1 without it,
 // 0 when x does not fit (use the direction kernel instead).

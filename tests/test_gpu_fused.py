@@ -98,7 +98,9 @@ def test_device_output_recapture_counts_and_timing():
         assert rel(out.cpu().numpy(), Hh) <= 1e-12
     lg.adjoint()
     assert lib.rh_grid_dims(lg._h, C.byref(dm)) == 0
-    assert dm.setup_kernels > 2 and dm.hessian_kernels == dm.setup_kernels + 2   # + the two direction launches
+    # + the two direction launches and the rescaling of the adjoint solve (run as a direction CTA
+    # on the unit-diagonal factors, it yields D lambda)
+    assert dm.setup_kernels > 2 and dm.hessian_kernels == dm.setup_kernels + 3
     total, first, adj = lg.reduced_hessian_times()
     assert 0.0 < first < total < 1e4 and 0.0 < adj < total
     # a padded leading dimension

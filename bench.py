@@ -93,7 +93,7 @@ def algorithmic_flops_per_direction(dm, n_inc, n_gref):
     nx = dm.n_x
     spmul = 2 * dm.nnz_jp
     l_sweep = 2 * dm.nnz_l
-    u_sweep = 2 * (dm.nnz_u - nx) + nx
+    u_sweep = 2 * (dm.nnz_u - nx)      # unit-diagonal U' = D^-1 U: the pivots fold into J_p's rows
     proj = 8 * n_inc + 8 * dm.n_bus + 4 * n_gref + dm.n_pv
     return spmul + 2 * (l_sweep + u_sweep) + proj + spmul
 

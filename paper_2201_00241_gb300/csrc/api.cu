@@ -319,7 +319,7 @@ rh_status dirs(rh_grid* g, int N, int64_t ld, double* V, double* T, const double
     L.ldhw = ldhw;
     L.phases = phases;
     L.use_tail = rh::dirs_tail_fits(g->S.n_x - g->S.t0, N, L.n_cta) ? 1 : 0;
-    L.use_reach = (L.use_tail && !W && (phases & rh::PH_WLOAD) && (phases & rh::PH_L)) ? 1 : 0;
+    L.use_reach = (L.use_tail && !W && (phases & rh::PH_WLOAD) && (phases & rh::PH_L) && (phases & rh::PH_U)) ? 1 : 0;
     rh::launch_dirs(g->dir(), L, s);
     RH_CUDA(cudaGetLastError());
     return RH_OK;
@@ -569,7 +569,7 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
             for (int t = 0; t < S.nv[k]; t++) qth[q + t] = q;
             if (k < S.tail_bus0 && !S.colpat[k].empty()) {
                 int par = S.colpat[k][0];              // first later bus of the pattern: the tree parent
-                if (par < S.tail_bus0) bpar[q] = S.q0[par];
+                if (par < S.tail_bus0) bpar[q] = 2 * S.q0[par] + (S.nv[par] == 2 ? 1 : 0);
             }
         }
         RH_CUDA(g->upload(g->qtheta, qth));

@@ -556,15 +556,21 @@ __device__ __forceinline__ int choose_ks(int nb, int D, int maxext) {
 // single-row buses must not issue the second row at all.  In a mixed warp the
 // single-row lanes run the second row on a copy of their first (r1 == r0) and
 // ignore the result.
-template <bool TWO>
+// CMASK: x of a row whose bit in cmask is clear is zero and is not read.
+__device__ __forceinline__ bool mask_get(const unsigned* m, int q) { return (m[q >> 5] >> (q & 31)) & 1u; }
+template <bool CMASK>
+__device__ __forceinline__ double ldx(const double* X, int i, int64_t ld, int64_t c, const unsigned* cmask) {
+    return (!CMASK || mask_get(cmask, i)) ? X[(int64_t)i * ld + c] : 0.0;
+}
+template <bool TWO, bool CMASK = false>
 __device__ __forceinline__ void block_sub(const int* __restrict__ col, const double* __restrict__ vals, int r0, int r1,
                                           int e0, int e1, const double* X, int64_t ld, int64_t c, double& a0,
-                                          double& a1) {
+                                          double& a1, const unsigned* cmask = nullptr) {
     int e = e0;
     for (; e + 4 <= e1; e += 4) {
         const int i0 = col[r0 + e], i1 = col[r0 + e + 1], i2 = col[r0 + e + 2], i3 = col[r0 + e + 3];
-        const double x0 = X[(int64_t)i0 * ld + c], x1 = X[(int64_t)i1 * ld + c];
-        const double x2 = X[(int64_t)i2 * ld + c], x3 = X[(int64_t)i3 * ld + c];
+        const double x0 = ldx<CMASK>(X, i0, ld, c, cmask), x1 = ldx<CMASK>(X, i1, ld, c, cmask);
+        const double x2 = ldx<CMASK>(X, i2, ld, c, cmask), x3 = ldx<CMASK>(X, i3, ld, c, cmask);
         a0 = fma(-vals[r0 + e], x0, a0);
         a0 = fma(-vals[r0 + e + 1], x1, a0);
         a0 = fma(-vals[r0 + e + 2], x2, a0);
@@ -577,7 +583,7 @@ __device__ __forceinline__ void block_sub(const int* __restrict__ col, const dou
         }
     }
     for (; e < e1; e++) {
-        const double xv = X[(int64_t)col[r0 + e] * ld + c];
+        const double xv = ldx<CMASK>(X, col[r0 + e], ld, c, cmask);
         a0 = fma(-vals[r0 + e], xv, a0);
         if constexpr (TWO) a1 = fma(-vals[r1 + e], xv, a1);
     }
@@ -614,12 +620,17 @@ __device__ __forceinline__ void fwd_finish(const DirGrid& g, const double* __res
 // activates its tree parent, an inactive bus only stores its zeros.  seed: the buses
 // whose right-hand side was written (zeroed, then the J_p entries scattered); every
 // other active bus has b = 0, so V need not be zeroed beforehand.
-__device__ __forceinline__ bool mask_get(const unsigned* m, int q) { return (m[q >> 5] >> (q & 31)) & 1u; }
 __device__ __forceinline__ void mask_set(unsigned* m, int q) { atomicOr(m + (q >> 5), 1u << (q & 31)); }
-template <bool SCALE, bool EXT = false>
+// activate a bus given its encoded theta row (theta row * 2 + 1 if it has a v row)
+__device__ __forceinline__ void mask_bus(unsigned* m, int enc) {
+    if (enc < 0) return;
+    mask_set(m, enc >> 1);
+    if (enc & 1) mask_set(m, (enc >> 1) + 1);
+}
+template <bool SCALE, bool EXT = false, bool CMASK = false>
 __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __restrict__ vals, double* X,
                           int64_t ld, int c0, int D, double* part, unsigned* mask = nullptr,
-                          const unsigned* seed = nullptr) {
+                          const unsigned* seed = nullptr, const unsigned* cmask = nullptr) {
     for (int lev = 0; lev < ls.n_lev; lev++) {
         const int b0 = ls.ptr[lev], nb = ls.ptr[lev + 1] - b0;
         const int4* __restrict__ slots = ls.slots + b0;
@@ -638,17 +649,13 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 bi = bi2;
                 const bool two = sl.w >= 0;
                 const int64_t c = c0 + d;
-                if (mask && !mask_get(mask, q)) {
-                    X[(int64_t)q * ld + c] = 0.0;
-                    if (two) X[(int64_t)(q + 1) * ld + c] = 0.0;
-                    continue;
-                }
+                if (mask && !mask_get(mask, q)) continue;     // outside the reach: x = 0, never read
                 const int rpv = two ? sl.w : rp;
                 const bool has_b = !seed || mask_get(seed, q);
                 double a0 = has_b ? X[(int64_t)q * ld + c] : 0.0;
                 double a1 = (two && has_b) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
                 if (warp_any(two)) {
-                    block_sub<true>(g.col, vals, rp, rpv, 0, n, X, ld, c, a0, a1);
+                    block_sub<true, CMASK>(g.col, vals, rp, rpv, 0, n, X, ld, c, a0, a1, cmask);
                     if (EXT) {
                         X[(int64_t)q * ld + c] = a0;
                         if (two) X[(int64_t)(q + 1) * ld + c] = a1;
@@ -656,14 +663,11 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                         fwd_finish<SCALE, true>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
                     }
                 } else {
-                    block_sub<false>(g.col, vals, rp, rpv, 0, n, X, ld, c, a0, a1);
+                    block_sub<false, CMASK>(g.col, vals, rp, rpv, 0, n, X, ld, c, a0, a1, cmask);
                     if (EXT) X[(int64_t)q * ld + c] = a0;
                     else fwd_finish<SCALE, false>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
                 }
-                if (mask) {
-                    const int pq = g.bparent[q];
-                    if (pq >= 0) mask_set(mask, pq);
-                }
+                if (mask) mask_bus(mask, g.bparent[q]);
             }
         } else {
             const int per = ks * D;
@@ -678,8 +682,8 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 int64_t c = c0 + d;
                 int e0 = sli * n / ks, e1 = (sli + 1) * n / ks;
                 double s0 = 0.0, s1 = 0.0;     // minus the slice's partial sums
-                if (warp_any(two)) block_sub<true>(g.col, vals, rp, rpv, e0, e1, X, ld, c, s0, s1);
-                else block_sub<false>(g.col, vals, rp, rpv, e0, e1, X, ld, c, s0, s1);
+                if (warp_any(two)) block_sub<true, CMASK>(g.col, vals, rp, rpv, e0, e1, X, ld, c, s0, s1, cmask);
+                else block_sub<false, CMASK>(g.col, vals, rp, rpv, e0, e1, X, ld, c, s0, s1, cmask);
                 double* pp = part + 2 * ((bi * ks + sli) * D + d);
                 pp[0] = s0;
                 pp[1] = s1;
@@ -691,11 +695,7 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 const int q = sl.x, n = sl.y;
                 const bool two = sl.w >= 0;
                 int64_t c = c0 + d;
-                if (mask && !mask_get(mask, q)) {
-                    X[(int64_t)q * ld + c] = 0.0;
-                    if (two) X[(int64_t)(q + 1) * ld + c] = 0.0;
-                    continue;
-                }
+                if (mask && !mask_get(mask, q)) continue;
                 const int rpv = two ? sl.w : sl.z;
                 const bool has_b = !seed || mask_get(seed, q);
                 double a0 = has_b ? X[(int64_t)q * ld + c] : 0.0;
@@ -717,10 +717,7 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                     if (EXT) X[(int64_t)q * ld + c] = a0;
                     else fwd_finish<SCALE, false>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
                 }
-                if (mask) {
-                    const int pq = g.bparent[q];
-                    if (pq >= 0) mask_set(mask, pq);
-                }
+                if (mask) mask_bus(mask, g.bparent[q]);
             }
         }
         __syncthreads();
@@ -740,9 +737,10 @@ __device__ __forceinline__ void bwd_finish(const DirGrid& g, const double* __res
     X[(int64_t)q * ld + c] = SCALE ? a0 * g.invdiag[q] : a0;
 }
 
+// rmask (optional): right-hand side rows whose bit is clear are zero and are not read
 template <bool SCALE>
 __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __restrict__ vals, double* X,
-                          int64_t ld, int c0, int D, double* part) {
+                          int64_t ld, int c0, int D, double* part, const unsigned* rmask = nullptr) {
     for (int lev = 0; lev < ls.n_lev; lev++) {
         const int b0 = ls.ptr[lev], nb = ls.ptr[lev + 1] - b0;
         const int4* __restrict__ slots = ls.slots + b0;
@@ -761,8 +759,9 @@ __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __
                 const bool two = sl.w >= 0;
                 const int ue1 = two ? sl.w : ue0;
                 const int64_t c = c0 + d;
-                double a0 = X[(int64_t)q * ld + c];
-                double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
+                const bool has_b = !rmask || mask_get(rmask, q);
+                double a0 = has_b ? X[(int64_t)q * ld + c] : 0.0;
+                double a1 = (two && has_b) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
                 if (warp_any(two)) {
                     block_sub<true>(g.col, vals, ue0, ue1, 0, n, X, ld, c, a0, a1);
                     bwd_finish<SCALE, true>(g, vals, X, ld, c, q, two, ue0 - 1, a0, a1);
@@ -797,8 +796,9 @@ __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __
                 const int q = sl.x;
                 const bool two = sl.w >= 0;
                 int64_t c = c0 + d;
-                double a0 = X[(int64_t)q * ld + c];
-                double a1 = two ? X[(int64_t)(q + 1) * ld + c] : 0.0;
+                const bool has_b = !rmask || mask_get(rmask, q);
+                double a0 = has_b ? X[(int64_t)q * ld + c] : 0.0;
+                double a1 = (two && has_b) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
                 if (warp_any(two)) {
                     for (int k = 0; k < ks; k++) {
                         const double* pp = part + 2 * ((bi * ks + k) * D + d);
@@ -1059,7 +1059,8 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
     if ((L.phases & PH_SPMUL) && !L.W && L.use_reach) {
         // identity W with the reach-restricted forward sweep: only the buses of this
         // CTA's J_p columns (all their rows, every direction) and the dense tail are
-        // zeroed before the scatter; the forward sweep writes every other row itself
+        // zeroed before the scatter; the forward sweep writes the other rows of the
+        // reach, and the rows outside it are zero and never read
         seed = mask_smem + (g.n_x + 31) / 32;
         for (int i = threadIdx.x; i < (g.n_x + 31) / 32; i += blockDim.x) seed[i] = 0u;
         for (int it = threadIdx.x; it < g.T * D; it += blockDim.x) {
@@ -1071,8 +1072,9 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
             const int k = L.col0 + c0 + d;
             for (int t = g.jpt_ptr[k] + (threadIdx.x & 7); t < g.jpt_ptr[k + 1]; t += 8) {
                 const int qb = g.qtheta[g.jpt_row[t]];
-                mask_set(seed, qb);
                 const bool two = qb + 1 < g.n_x && g.qtheta[qb + 1] == qb;
+                mask_set(seed, qb);
+                if (two) mask_set(seed, qb + 1);
                 for (int e = 0; e < D; e++) {
                     V[(int64_t)qb * ld + e] = 0.0;
                     if (two) V[(int64_t)(qb + 1) * ld + e] = 0.0;
@@ -1118,31 +1120,40 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
         __syncthreads();
     }
     if (L.use_tail) {
-        if (L.phases & PH_L) {
-            unsigned* mask = nullptr;
-            if (L.use_reach) {
-                // identity W: B column c is column col0 + c of J_p; seed its buses
-                mask = mask_smem;
-                if (seed) {
-                    for (int i = threadIdx.x; i < (g.n_x + 31) / 32; i += blockDim.x) mask[i] = seed[i];
-                } else {
-                    for (int i = threadIdx.x; i < (g.n_x + 31) / 32; i += blockDim.x) mask[i] = 0u;
-                    __syncthreads();
-                    for (int d = threadIdx.x / 8; d < D; d += blockDim.x / 8) {
-                        const int k = L.col0 + c0 + d;
-                        for (int t = g.jpt_ptr[k] + (threadIdx.x & 7); t < g.jpt_ptr[k + 1]; t += 8)
-                            mask_set(mask, g.qtheta[g.jpt_row[t]]);
+        // identity W: the reach of B's columns (one bit per row; L, U and the tail's
+        // external phase in this launch); rows outside it are zero in Z's forward sweep
+        unsigned* mask = nullptr;
+        if ((L.phases & PH_L) && L.use_reach) {
+            mask = mask_smem;
+            if (seed) {
+                for (int i = threadIdx.x; i < (g.n_x + 31) / 32; i += blockDim.x) mask[i] = seed[i];
+            } else {
+                for (int i = threadIdx.x; i < (g.n_x + 31) / 32; i += blockDim.x) mask[i] = 0u;
+                __syncthreads();
+                for (int d = threadIdx.x / 8; d < D; d += blockDim.x / 8) {
+                    const int k = L.col0 + c0 + d;
+                    for (int t = g.jpt_ptr[k] + (threadIdx.x & 7); t < g.jpt_ptr[k + 1]; t += 8) {
+                        const int qb = g.qtheta[g.jpt_row[t]];
+                        mask_set(mask, qb);
+                        if (qb + 1 < g.n_x && g.qtheta[qb + 1] == qb) mask_set(mask, qb + 1);
                     }
                 }
-                __syncthreads();
             }
-            sweep_fwd<false>(g, g.sf, g.Ad, V, ld, 0, D, part, mask, seed);
-            sweep_fwd<false, true>(g, g.ef, g.Ad, V, ld, 0, D, part);
+            __syncthreads();
+        }
+        if (L.phases & PH_L) {
+            if (mask) {
+                sweep_fwd<false, false, true>(g, g.sf, g.Ad, V, ld, 0, D, part, mask, seed, mask);
+                sweep_fwd<false, true, true>(g, g.ef, g.Ad, V, ld, 0, D, part, nullptr, nullptr, mask);
+            } else {
+                sweep_fwd<false>(g, g.sf, g.Ad, V, ld, 0, D, part);
+                sweep_fwd<false, true>(g, g.ef, g.Ad, V, ld, 0, D, part);
+            }
             tail_fwd<false>(g, g.triLd, V, ld, 0, D, part, nullptr);
         }
         if (L.phases & PH_U) {
             tail_bwd<false>(g, g.triUd, V, ld, 0, D, part, nullptr);
-            sweep_bwd<false>(g, g.sb, g.Ad, V, ld, 0, D, part);
+            sweep_bwd<false>(g, g.sb, g.Ad, V, ld, 0, D, part, mask);
         }
     } else {
         if (L.phases & PH_L) sweep_fwd<false>(g, g.lf, g.Ad, V, ld, 0, D, part);

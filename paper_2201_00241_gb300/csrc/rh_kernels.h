@@ -52,8 +52,9 @@ struct DirGrid {
     const double *Ad, *Atd;
     const double *triLd, *triUd, *triUtd, *triLtd;
     const double *jptvd;
-    // bus structure by theta row: theta row of the bus owning row q; theta row of the
-    // bus's elimination-tree parent (-1 for a root or a parent in the dense tail)
+    // bus structure by theta row: theta row of the bus owning row q; the bus's
+    // elimination-tree parent as 2 * (its theta row) + (1 if it has a v row), or -1
+    // for a root or a parent in the dense tail
     const int *qtheta, *bparent;
     // J_p by internal rows and by p index; rows with and without entries
     const int *jp_ptr, *jp_col;
@@ -95,7 +96,8 @@ struct DirLaunch {
     int64_t ldhw;
     unsigned phases;
     int use_tail;              // dense tail in shared memory (needs T * ceil(N / n_cta) <= 4096)
-    int use_reach;             // identity W: forward L sweep only over the reach of B's nonzeros (needs use_tail)
+    int use_reach;             // identity W: forward L sweep only over the reach of B's nonzeros (needs use_tail,
+                               // and phases L and U in the same launch)
 };
 
 // Up to kMaxBatch (grid, W block) items of one batched launch, passed by value as

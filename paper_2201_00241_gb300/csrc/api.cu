@@ -327,7 +327,7 @@ rh_status dirs(rh_grid* g, int N, int64_t ld, double* V, double* T, const double
 
 // single right-hand side in g->v1 (internal order), in place.  beside_dirs: as
 // one CTA of the direction kernel, which fits in the slot a direction launch of
-// one CTA less than the device holds leaves free (k_solve1's shared-memory x
+// fewer CTAs than the device holds leaves free (k_solve1's shared-memory x
 // needs a shared-memory carveout that an SM running k_dirs does not have).
 rh_status solve_one(rh_grid* g, unsigned phases, cudaStream_t s, bool beside_dirs = false) {
     const int mode = beside_dirs ? 0 : rh::solve1_mode(g->S.n_x, g->S.n_x - g->S.t0);

@@ -8,7 +8,7 @@ transposed solve running beside the first direction sweeps.
   fused call runs in another thread shape, so its sums may round differently:
   1e-12);
 * H against the separate rh_adjoint + rh_hessian calls at 1e-12 (the first
-  direction launch has one CTA less, which may change how a narrow level's rows
+  direction launch has fewer CTAs, which may change how a narrow level's rows
   are split);
 * the grid is left ready for rh_hessvec, device outputs, re-capture for a new
   output buffer, the kernel count and the timing query, argument errors.

@@ -80,6 +80,7 @@ struct rh_grid {
     int64_t* rf_tgt_gptr = nullptr;
     int *jp_ptr = nullptr, *jp_col = nullptr, *jpt_ptr = nullptr, *jpt_row = nullptr, *jpt_src = nullptr;
     int *tp_bus = nullptr, *uth = nullptr, *uv = nullptr, *inc_ptr = nullptr, *inc_nb = nullptr;
+    int* tp_l0 = nullptr;   // per bus: position of (v, theta) in At for a PQ bus of forward level 0, else -1
     int *inc_uth = nullptr, *inc_uv = nullptr, *gref_row = nullptr, *pg_row = nullptr, *xmap = nullptr;
     uint8_t* has_gref = nullptr;
     int n_inc = 0, n_gref = 0;
@@ -195,7 +196,7 @@ struct rh_grid {
         g.jp_ptr = jp_ptr; g.jp_col = jp_col; g.jpv = jpv;
         g.n_jp_rows = n_jp_rows; g.n_jp_zero = n_jp_zero; g.jp_rows = jp_rows; g.jp_zero_rows = jp_zero_rows;
         g.jpt_ptr = jpt_ptr; g.jpt_row = jpt_row; g.jptv = jptv;
-        g.n_bus = S.n_bus; g.tp_bus = tp_bus; g.uth = uth; g.uv = uv;
+        g.n_bus = S.n_bus; g.tp_bus = tp_bus; g.uth = uth; g.uv = uv; g.tp_l0 = tp_l0;
         g.inc_ptr = inc_ptr; g.inc_uth = inc_uth; g.inc_uv = inc_uv; g.inc_coef = inc_coef;
         g.d2 = d2; g.asum = asum; g.csum = csum; g.has_gref = has_gref; g.gref_th = gref_th; g.gref_v = gref_v;
         g.n_gref = n_gref; g.gref_row = gref_row; g.gref_val = gref_val; g.c2ref = dscal + 1;
@@ -602,6 +603,14 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     RH_CUDA(g->upload(g->jpt_row, S.jpt_row));
     RH_CUDA(g->upload(g->jpt_src, S.jpt_src));
     RH_CUDA(g->upload(g->tp_bus, tp_bus));
+    {
+        // a sparse bus of forward level 0 has no L entries outside its block; for a PQ
+        // bus the v row's only L entry is (v, theta), the first of the row
+        std::vector<int> l0(nb, -1);
+        for (int k = 0; k < S.tail_bus0; k++)
+            if (S.flevel[k] == 0 && S.nv[k] == 2) l0[S.ebus[k]] = S.rowptr[S.q0[k] + 1];
+        RH_CUDA(g->upload(g->tp_l0, l0));
+    }
     RH_CUDA(g->upload(g->uth, uth));
     RH_CUDA(g->upload(g->uv, uv));
     RH_CUDA(g->upload(g->inc_ptr, inc_ptr));

@@ -954,7 +954,11 @@ __device__ __forceinline__ double flip_sign(double v, bool flip) {
 // warp mostly share their incidence count; each output is one FMA chain; the
 // slack-neighbour and Pg terms, which few buses have, are only issued by warps
 // that hold such a bus (a predicated FP64 instruction costs its issue slot).
-__device__ void tproj(const DirGrid& g, const double* V, double* T, int64_t ld, int c0, int D, double* sref) {
+// fold_ut: the launch runs the U'^T sweep over the sparse levels next; its level 0
+// (buses without L entries outside their block, so x_theta = b_theta and, for a PQ
+// bus, x_v = b_v - u'_tv x_theta) is done here and the sweep starts at level 1.
+__device__ void tproj(const DirGrid& g, const double* V, double* T, int64_t ld, int c0, int D, double* sref,
+                      bool fold_ut) {
     double c2r = *g.c2ref;
     for (int d = threadIdx.x; d < D; d += blockDim.x) {
         double s = 0.0;
@@ -1006,6 +1010,10 @@ __device__ void tproj(const DirGrid& g, const double* V, double* T, int64_t ld, 
             }
         }
         if (rth != g.zero_row) T[(int64_t)rth * ld + c] = flip_sign(yth, true);
+        const int l0 = fold_ut ? g.tp_l0[b] : -1;
+        if (warp_any(l0 >= 0)) {
+            if (l0 >= 0) yv = fma(-g.Atd[l0], yth, yv);   // T_v = -yv + u'_tv yth
+        }
         T[(int64_t)rv * ld + c] = flip_sign(yv, rv < g.n_x);
         const int pr = g.pg_row[b];
         if (warp_any(pr >= 0)) {
@@ -1159,13 +1167,20 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
         if (L.phases & PH_L) sweep_fwd<false>(g, g.lf, g.Ad, V, ld, 0, D, part);
         if (L.phases & PH_U) sweep_bwd<false>(g, g.lb, g.Ad, V, ld, 0, D, part);
     }
+    const bool fold_ut = (L.phases & PH_TPROJ) && (L.phases & PH_UT) && L.use_tail && g.sf.n_lev > 0;
     if (L.phases & PH_TPROJ) {
-        tproj(g, V, T, ld, 0, D, sref);
+        tproj(g, V, T, ld, 0, D, sref, fold_ut);
         __syncthreads();
     }
     if (L.use_tail) {
         if (L.phases & PH_UT) {
-            sweep_fwd<false>(g, g.sf, g.Atd, T, ld, 0, D, part);
+            LevelSet sf = g.sf;
+            if (fold_ut) {   // level 0 was done by the projection
+                sf.n_lev -= 1;
+                sf.ptr += 1;
+                sf.maxext += 1;
+            }
+            sweep_fwd<false>(g, sf, g.Atd, T, ld, 0, D, part);
             sweep_fwd<false, true>(g, g.ef, g.Atd, T, ld, 0, D, part);
             tail_fwd<false>(g, g.triUtd, T, ld, 0, D, part, nullptr);
         }

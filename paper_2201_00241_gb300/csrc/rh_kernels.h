@@ -67,6 +67,7 @@ struct DirGrid {
     int n_bus;
     const int *tp_bus;                         // bus processing order (internal order, slack last)
     const int *uth, *uv;                       // rows of theta_b (zero row at the slack) and v_b
+    const int *tp_l0;                          // position of (v, theta) in At for a PQ bus of forward level 0, else -1
     const int *inc_ptr, *inc_uth, *inc_uv;     // incident branches: rows of the other end
     const double4_32a *inc_coef;               // (K, -a, b, -c) per incidence (state dependent)
     const double *d2, *asum, *csum;            // per-bus coefficients (state dependent)

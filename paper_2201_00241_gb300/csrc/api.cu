@@ -119,7 +119,7 @@ struct rh_grid {
     cudaGraphExec_t hess_exec = nullptr;
     const double* hess_H = nullptr;
     int64_t hess_ld = 0;
-    const double* hess_V = nullptr;
+    const double *hess_V = nullptr, *hess_T = nullptr;
     int hess_kernels = 0;
     bool hess_timed = false;
     cudaStream_t stream2 = nullptr;
@@ -941,7 +941,7 @@ rh_status rh_reduced_hessian(rh_grid* g, double* H, int64_t ldh, double* F, doub
     if (st) return st;
     g->adjoint_ready = false;
     g->hess_timed = false;
-    if (g->hess_exec && (g->hess_H != Hd || g->hess_ld != lh || g->hess_V != g->V)) {
+    if (g->hess_exec && (g->hess_H != Hd || g->hess_ld != lh || g->hess_V != g->V || g->hess_T != g->T)) {
         cudaGraphExecDestroy(g->hess_exec);
         g->hess_exec = nullptr;
     }
@@ -958,6 +958,7 @@ rh_status rh_reduced_hessian(rh_grid* g, double* H, int64_t ldh, double* F, doub
         g->hess_H = Hd;
         g->hess_ld = lh;
         g->hess_V = g->V;
+        g->hess_T = g->T;
     }
     if (stream) {   // order after the caller's earlier work on its stream
         if (!g->ev_user) RH_CUDA(cudaEventCreateWithFlags(&g->ev_user, cudaEventDisableTiming));

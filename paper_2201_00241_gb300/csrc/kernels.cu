@@ -61,23 +61,55 @@ __global__ void k_injections(PfGrid g, PfState s) {
 
 // One thread per bus: injections, the two residual rows of the bus and the
 // Jacobian entries of those rows, scattered into the fixed LU / J_p slots.
+// the four derivatives of admittance entry t into their slots of A (J_x) or J_p
+__device__ __forceinline__ void jac_store(const PfGrid& g, int t, const double (&d)[4], double* A, double* jpv,
+                                          unsigned long long& jm) {
+    for (int u = 0; u < 4; u++) {
+        const int dst = g.jac_dst[4 * t + u];
+        if (dst >= 0) {
+            A[dst] = d[u];
+            const unsigned long long b = ordered_bits(d[u]);
+            jm = b > jm ? b : jm;
+        } else if (dst <= -2) {
+            jpv[-(dst + 2)] = d[u];
+        }
+    }
+}
+
 __global__ void k_pf_eval(PfGrid g, PfState s, double* gres, double* A, double* jpv,
                           unsigned long long* gmax, unsigned long long* jmax, int want_jac) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n_bus) return;
-    double vi = s.vm[i], ai = s.va[i], P = 0.0, Q = 0.0;
+    const double vi = s.vm[i], ai = s.va[i];
+    const int rP = g.qth[i];
+    const bool jac = want_jac && rP >= 0;
+    double P = 0.0, Q = 0.0;
+    unsigned long long jm = 0;
+    int tdiag = -1;
+    // one pass over the admittance row: the injection sums and, for j != i, the
+    // off-diagonal Jacobian entries from the same sin/cos of theta_i - theta_j
     for (int t = g.yp[i]; t < g.yp[i + 1]; t++) {
-        int j = g.yj[t];
-        double sn, cs;
-        sincos(ai - s.va[j], &sn, &cs);
-        P += s.vm[j] * (g.G[t] * cs + g.B[t] * sn);
-        Q += s.vm[j] * (g.G[t] * sn - g.B[t] * cs);
+        const int j = g.yj[t];
+        double sn = 0.0, cs = 1.0;
+        if (j != i) sincos(ai - s.va[j], &sn, &cs);
+        else tdiag = t;
+        const double vj = s.vm[j], Gij = g.G[t], Bij = g.B[t];
+        P += vj * (Gij * cs + Bij * sn);
+        Q += vj * (Gij * sn - Bij * cs);
+        if (jac && j != i) {
+            double d[4];  // dP/dtheta_j, dP/dv_j, dQ/dtheta_j, dQ/dv_j
+            d[0] = vi * vj * (Gij * sn - Bij * cs);
+            d[1] = vi * (Gij * cs + Bij * sn);
+            d[2] = -vi * vj * (Gij * cs + Bij * sn);
+            d[3] = vi * (Gij * sn - Bij * cs);
+            jac_store(g, t, d, A, jpv, jm);
+        }
     }
     P *= vi;
     Q *= vi;
     s.P[i] = P;
     s.Q[i] = Q;
-    int rP = g.qth[i], rQ = g.qv[i];
+    const int rQ = g.qv[i];
     if (rP < 0) return;  // slack: no rows
     if (gres) {
         double gp = P - s.pg[i] + s.pd[i];
@@ -92,35 +124,14 @@ __global__ void k_pf_eval(PfGrid g, PfState s, double* gres, double* A, double* 
         atomicMax(gmax, m);
     }
     if (!want_jac) return;
-    unsigned long long jm = 0;
-    for (int t = g.yp[i]; t < g.yp[i + 1]; t++) {
-        int j = g.yj[t];
-        double d[4];  // dP/dtheta_j, dP/dv_j, dQ/dtheta_j, dQ/dv_j
-        if (j == i) {
-            double Gii = g.G[t], Bii = g.B[t];
-            d[0] = -Q - Bii * vi * vi;
-            d[1] = P / vi + Gii * vi;
-            d[2] = P - Gii * vi * vi;
-            d[3] = Q / vi - Bii * vi;
-        } else {
-            double sn, cs;
-            sincos(ai - s.va[j], &sn, &cs);
-            double vj = s.vm[j], Gij = g.G[t], Bij = g.B[t];
-            d[0] = vi * vj * (Gij * sn - Bij * cs);
-            d[1] = vi * (Gij * cs + Bij * sn);
-            d[2] = -vi * vj * (Gij * cs + Bij * sn);
-            d[3] = vi * (Gij * sn - Bij * cs);
-        }
-        for (int u = 0; u < 4; u++) {
-            int dst = g.jac_dst[4 * t + u];
-            if (dst >= 0) {
-                A[dst] = d[u];
-                unsigned long long b = ordered_bits(d[u]);
-                jm = b > jm ? b : jm;
-            } else if (dst <= -2) {
-                jpv[-(dst + 2)] = d[u];
-            }
-        }
+    if (tdiag >= 0) {
+        const double Gii = g.G[tdiag], Bii = g.B[tdiag];
+        double d[4];
+        d[0] = -Q - Bii * vi * vi;
+        d[1] = P / vi + Gii * vi;
+        d[2] = P - Gii * vi * vi;
+        d[3] = Q / vi - Bii * vi;
+        jac_store(g, tdiag, d, A, jpv, jm);
     }
     if (g.ip_pg[i] >= 0) jpv[g.pg_slot[i]] = -1.0;
     atomicMax(jmax, jm);
@@ -1636,7 +1647,7 @@ void launch_injections(const PfGrid& g, const PfState& s, cudaStream_t st) {
 
 void launch_pf_eval(const PfGrid& g, const PfState& s, double* gres, double* A, double* jpv,
                     unsigned long long* gmax, unsigned long long* jmax, bool want_jac, cudaStream_t st) {
-    if (g.n_bus > 0) k_pf_eval<<<blocks_for(g.n_bus, 128), 128, 0, st>>>(g, s, gres, A, jpv, gmax, jmax, want_jac);
+    if (g.n_bus > 0) k_pf_eval<<<blocks_for(g.n_bus, 64), 64, 0, st>>>(g, s, gres, A, jpv, gmax, jmax, want_jac);
 }
 
 cudaError_t launch_jac_ad(const PfGrid& g, const PfState& s, const int* col_th, const int* col_v, const int* col_pg,

@@ -103,6 +103,12 @@ def test_device_output_recapture_counts_and_timing():
     assert dm.setup_kernels > 2 and dm.hessian_kernels == dm.setup_kernels + 3
     total, first, adj = lg.reduced_hessian_times()
     assert 0.0 < first < total < 1e4 and 0.0 < adj < total
+    # a wider rh_hessvec grows (reallocates) the workspace: the graph is captured again
+    W = gg.random_directions(n, 2 * n + 3, 11)
+    HW = lg.hessvec(W)
+    assert rel(HW, Hh @ W) <= 1e-11
+    H2, _, _ = lg.reduced_hessian()
+    assert rel(H2, Hh) <= 1e-12
     # a padded leading dimension
     Hp = torch.zeros((n + 5) * n, dtype=torch.float64, device="cuda:0")
     st_ptr = C.c_void_p(torch.cuda.current_stream().cuda_stream)

@@ -80,8 +80,10 @@ def measured_traffic():
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "k_dirs_case9241_traffic.json")))
-        src = os.path.join(ROOT, "paper_2201_00241_gb300", "csrc", "kernels.cu")
-        if hashlib.sha256(open(src, "rb").read()).hexdigest() == rec["kernels_cu_sha256"]:
+        csrc = os.path.join(ROOT, "paper_2201_00241_gb300", "csrc")
+        sha = lambda f: hashlib.sha256(open(os.path.join(csrc, f), "rb").read()).hexdigest()
+        # the kernels and the symbolic phase (ordering, schedules) both shape the traffic
+        if sha("kernels.cu") == rec["kernels_cu_sha256"] and sha("symbolic.cpp") == rec.get("symbolic_cpp_sha256"):
             return int(rec["dram_bytes_per_step"])
     except (OSError, ValueError, KeyError):
         pass
@@ -514,6 +516,12 @@ def main():
     def step():
         rh._check(lib.rh_reduced_hessian(lg._h, rh._ptr(H), n_p, None, None, sptr, rh.RH_DEVICE_PTRS))
 
+    # the clock sampler starts before the warm-up, so that its start-up (NVML initialisation)
+    # is over before the timed steps; it keeps sampling through them
+    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                            f"clocks_rank{rank}.csv")
+    sampler = start_clock_sampler(clk_path)
+    time.sleep(1.0)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -523,9 +531,6 @@ def main():
     launches_per_step = int(dm_run.hessian_kernels)
     if world > 1:
         torch.distributed.barrier()
-    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                            f"clocks_rank{rank}.csv")
-    sampler = start_clock_sampler(clk_path)
     step_ms, dirs_ms, phase_ms = [], [], []
     torch.cuda.synchronize()
     for _ in range(args.steps):

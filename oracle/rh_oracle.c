@@ -16,7 +16,7 @@
  *     P_inj + Pd at the slack (a function of x and p);
  *   - textbook analytic Jacobians J_x = dg/dx and J_p = dg/dp;
  *   - Newton-Raphson power flow (section 3.2) with its own left-looking sparse LU
- *     under a static minimum-degree ordering of the bus graph;
+ *     under a static minimum-weighted-fill ordering of the bus graph;
  *   - first-order adjoint lambda and reduced gradient, eq. (6)-(7);
  *   - the explicit Hessian of the Lagrangian l = f + lambda^T g over (x, p),
  *     assembled bus by bus from the second derivatives of every P_i and Q_i
@@ -415,57 +415,106 @@ void orc_jacobians_dense(const orc_grid *g, const double *x, const double *p, do
 }
 
 /* ------------------------------------------------------------------------ */
-/* static ordering: exact minimum degree on the bus graph                    */
+/* static ordering: minimum weighted fill on the bus graph                   */
 /* ------------------------------------------------------------------------ */
 
 /*
  * Graph: the non-slack buses, an edge wherever a branch joins two of them.
- * Repeatedly eliminate the remaining bus of smallest current degree (ties:
- * smallest bus id); its remaining neighbours become a clique.  The elimination
- * graph is kept as a dense bit matrix, which is slow but plainly correct.
+ * Eliminating bus e joins its remaining neighbours into a clique; each pair
+ * (a, b) of them that is not yet adjacent adds w_a * w_b entries to L, with
+ * w = 1 for a PV bus and 2 for a PQ bus (its x variables).  Repeatedly
+ * eliminate the remaining bus that adds the fewest (ties: the smallest sum of
+ * w over its remaining neighbours, then the smallest bus id).  The elimination
+ * graph is a dense bit matrix; after each elimination the scores of all buses
+ * within two steps of it are recomputed from the matrix (no other score can
+ * change), which is slow but plainly correct.
  * Each bus contributes its x variables in the order theta, then v.
  * perm[q] = x index of the variable eliminated q-th; bus_order[k] = bus id.
  */
-static void md_order(const orc_grid *g, int *perm, int *bus_order, int *n_elim) {
+/* the remaining neighbours of bus v in the elimination graph, read from its row of bits */
+static int mf_row(const uint64_t *adj, size_t words, int v, const char *alive, int *out) {
+    int m = 0;
+    const uint64_t *row = adj + (size_t)v * words;
+    for (size_t k = 0; k < words; k++) {
+        uint64_t bits = row[k];
+        while (bits) {
+            int j = (int)(k * 64) + __builtin_ctzll(bits);
+            bits &= bits - 1;
+            if (alive[j] && j != v) out[m++] = j;
+        }
+    }
+    return m;
+}
+
+static void mf_order(const orc_grid *g, int *perm, int *bus_order, int *n_elim) {
     int n = g->n_bus;
     size_t words = (size_t)(n + 63) / 64;
     uint64_t *adj = xcalloc((size_t)n * words, sizeof(uint64_t));
-    int *deg = xcalloc(n, sizeof(int));
     char *alive = xcalloc(n, 1);
+    int *w = xcalloc(n, sizeof(int));
+    long long *fill = xcalloc(n, sizeof(long long)), *wdeg = xcalloc(n, sizeof(long long));
+    int *nb = xcalloc(n, sizeof(int)), *nb2 = xcalloc(n, sizeof(int)), *hit = xcalloc(n, sizeof(int));
 #define HAS(a, b) ((adj[(size_t)(a) * words + (b) / 64] >> ((b) % 64)) & 1u)
 #define SET(a, b) (adj[(size_t)(a) * words + (b) / 64] |= (uint64_t)1 << ((b) % 64))
 #define CLR(a, b) (adj[(size_t)(a) * words + (b) / 64] &= ~((uint64_t)1 << ((b) % 64)))
-    for (int i = 0; i < n; i++) alive[i] = g->type[i] != REF;
+    for (int i = 0; i < n; i++) {
+        alive[i] = g->type[i] != REF;
+        w[i] = g->type[i] == PQ ? 2 : 1;
+        hit[i] = -1;
+    }
     for (int i = 0; i < n; i++) {
         if (!alive[i]) continue;
         for (int k = g->yp[i]; k < g->yp[i + 1]; k++) {
             int j = g->yj[k];
-            if (j != i && alive[j] && !HAS(i, j)) { SET(i, j); deg[i]++; }
+            if (j != i && alive[j]) SET(i, j);
         }
     }
-    int *nb = xcalloc(n, sizeof(int));
+    /* score of bus v: the weight of its non-adjacent neighbour pairs, and its weighted degree */
+#define SCORE(v)                                                                   \
+    do {                                                                           \
+        int m_ = mf_row(adj, words, (v), alive, nb2);                              \
+        long long f_ = 0, s_ = 0;                                                  \
+        for (int a_ = 0; a_ < m_; a_++) {                                          \
+            s_ += w[nb2[a_]];                                                      \
+            for (int c_ = a_ + 1; c_ < m_; c_++)                                   \
+                if (!HAS(nb2[a_], nb2[c_])) f_ += (long long)w[nb2[a_]] * w[nb2[c_]]; \
+        }                                                                          \
+        fill[v] = f_;                                                              \
+        wdeg[v] = s_;                                                              \
+    } while (0)
+    for (int i = 0; i < n; i++) if (alive[i]) SCORE(i);
     int cnt = 0, q = 0;
     for (;;) {
         int best = -1;
-        for (int i = 0; i < n; i++)
-            if (alive[i] && (best < 0 || deg[i] < deg[best])) best = i;
+        for (int i = 0; i < n; i++) {
+            if (!alive[i]) continue;
+            if (best < 0 || fill[i] < fill[best] || (fill[i] == fill[best] && wdeg[i] < wdeg[best])) best = i;
+        }
         if (best < 0) break;
-        int m = 0;
-        for (int j = 0; j < n; j++) if (alive[j] && j != best && HAS(best, j)) nb[m++] = j;
+        int m = mf_row(adj, words, best, alive, nb);
         alive[best] = 0;
-        for (int a = 0; a < m; a++) { CLR(nb[a], best); deg[nb[a]]--; }
+        for (int a = 0; a < m; a++) CLR(nb[a], best);
         for (int a = 0; a < m; a++)
             for (int c = a + 1; c < m; c++)
-                if (!HAS(nb[a], nb[c])) { SET(nb[a], nb[c]); SET(nb[c], nb[a]); deg[nb[a]]++; deg[nb[c]]++; }
+                if (!HAS(nb[a], nb[c])) { SET(nb[a], nb[c]); SET(nb[c], nb[a]); }
+        /* rescore every bus within two steps of the eliminated one: its former
+           neighbours and their neighbours (no other score can change) */
+        for (int a = 0; a < m; a++) {
+            hit[nb[a]] = cnt;
+            int m2 = mf_row(adj, words, nb[a], alive, nb2);
+            for (int c = 0; c < m2; c++) hit[nb2[c]] = cnt;
+        }
+        for (int j = 0; j < n; j++) if (alive[j] && hit[j] == cnt) SCORE(j);
         bus_order[cnt++] = best;
         perm[q++] = g->ix_th[best];
         if (g->ix_v[best] >= 0) perm[q++] = g->ix_v[best];
     }
+#undef SCORE
 #undef HAS
 #undef SET
 #undef CLR
     *n_elim = cnt;
-    free(adj); free(deg); free(alive); free(nb);
+    free(adj); free(alive); free(w); free(fill); free(wdeg); free(nb); free(nb2); free(hit);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -581,7 +630,7 @@ static int factor_at(const orc_grid *g, const orc_state *s, orc_lu *F, csc *Jp_o
     csc Jx, Jp;
     jacobians(g, s, &Jx, &Jp);
     int *perm = xcalloc(g->n_x, sizeof(int)), *bo = xcalloc(g->n_bus, sizeof(int)), nb;
-    md_order(g, perm, bo, &nb);
+    mf_order(g, perm, bo, &nb);
     int st = lu_factor(&Jx, perm, F);
     free(perm); free(bo);
     csc_free(&Jx);
@@ -827,7 +876,7 @@ int orc_hessvec(const orc_grid *g, const double *x, const double *p, const doubl
 /* ------------------------------------------------------------------------ */
 
 /*
- * Ordering from md_order.  Patterns from a structural (boolean) left-looking
+ * Ordering from mf_order.  Patterns from a structural (boolean) left-looking
  * factorization of the permuted J_x pattern at the variable level: column k
  * gathers the rows of column k of B and, for every j < k already reached, the
  * rows of L(:, j).  J_x entries are taken as structurally nonzero wherever the
@@ -846,7 +895,7 @@ int orc_symbolic(const orc_grid *g, int32_t *perm_out, int32_t *bus_order_out, i
                  int64_t *nnzL, int64_t *nnzU, int32_t *n_elim) {
     int nx = g->n_x, n = g->n_bus;
     int *perm = xcalloc(nx, sizeof(int)), *bo = xcalloc(n, sizeof(int)), nb = 0;
-    md_order(g, perm, bo, &nb);
+    mf_order(g, perm, bo, &nb);
     int *iperm = xcalloc(nx, sizeof(int));
     for (int q = 0; q < nx; q++) iperm[perm[q]] = q;
     /* structural J_x pattern by columns, in permuted indices */

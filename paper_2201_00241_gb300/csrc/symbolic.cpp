@@ -18,24 +18,46 @@
 namespace rh {
 namespace {
 
-// Exact minimum degree on the bus graph: repeatedly eliminate the remaining
-// bus of smallest degree in the current elimination graph (ties: smallest bus
-// id); the neighbours of an eliminated bus become a clique.  Adjacency lists
-// are kept sorted; a min-heap with lazy invalidation finds the next bus.
+// Minimum weighted fill on the bus graph.  Eliminating bus e joins its remaining
+// neighbours into a clique: every pair (a, b) of them that is not yet adjacent
+// adds w_a * w_b entries to L (and as many to U), w = variables per bus (1 for a
+// PV bus, 2 for a PQ bus).  Repeatedly eliminate the bus that adds the fewest
+// (ties: the smallest weighted degree, i.e. sum of w over its remaining
+// neighbours, then the smallest bus id).  An elimination changes the score of
+// the buses within two steps of it only; those are rescored and pushed again on
+// a min-heap with lazy invalidation.  Adjacency lists are kept sorted.
 // colpat_bus[k] receives the neighbour set (bus ids) of the k-th eliminated bus.
-void minimum_degree(int n_bus, const std::vector<std::vector<int>>& adj0, const std::vector<char>& active,
-                    std::vector<int>& order, std::vector<std::vector<int>>& colpat_bus) {
+void minimum_fill(int n_bus, const std::vector<std::vector<int>>& adj0, const std::vector<char>& active,
+                  const std::vector<int>& w, std::vector<int>& order, std::vector<std::vector<int>>& colpat_bus) {
     std::vector<std::vector<int>> adj = adj0;
     std::vector<char> alive = active;
-    using Key = std::pair<int, int>;  // (degree, bus id)
+    std::vector<int> mark(n_bus, -1);
+    int stamp = 0;
+    using Key = std::tuple<int64_t, int64_t, int>;   // (weighted fill, weighted degree, bus id)
+    auto key = [&](int v) {
+        stamp++;
+        int64_t sw = 0, sw2 = 0, adj2 = 0;
+        for (int c : adj[v]) {
+            mark[c] = stamp;
+            sw += w[c];
+            sw2 += (int64_t)w[c] * w[c];
+        }
+        for (int a : adj[v])
+            for (int c : adj[a])
+                if (mark[c] == stamp) adj2 += (int64_t)w[a] * w[c];   // each adjacent pair twice
+        return Key{(sw * sw - sw2) / 2 - adj2 / 2, sw, v};
+    };
+    std::vector<Key> cur(n_bus);
     std::priority_queue<Key, std::vector<Key>, std::greater<Key>> heap;
     for (int i = 0; i < n_bus; i++)
-        if (alive[i]) heap.push({(int)adj[i].size(), i});
-    std::vector<int> merged;
+        if (alive[i]) heap.push(cur[i] = key(i));
+    std::vector<int> merged, touched;
+    std::vector<int> seen(n_bus, -1);
     while (!heap.empty()) {
-        auto [d, e] = heap.top();
+        const Key k = heap.top();
         heap.pop();
-        if (!alive[e] || d != (int)adj[e].size()) continue;  // stale entry
+        const int e = std::get<2>(k);
+        if (!alive[e] || k != cur[e]) continue;  // stale entry
         alive[e] = 0;
         std::vector<int> nb = std::move(adj[e]);
         adj[e].clear();
@@ -46,8 +68,16 @@ void minimum_degree(int n_bus, const std::vector<std::vector<int>>& adj0, const 
             adj[a].clear();
             for (int v : merged)
                 if (v != a && v != e) adj[a].push_back(v);
-            heap.push({(int)adj[a].size(), a});
         }
+        // rescore the buses within two steps of e
+        touched.clear();
+        for (int a : nb) {
+            if (seen[a] != e) { seen[a] = e; touched.push_back(a); }
+            for (int c : adj[a])
+                if (seen[c] != e) { seen[c] = e; touched.push_back(c); }
+        }
+        for (int v : touched)
+            if (alive[v]) heap.push(cur[v] = key(v));
         order.push_back(e);
         colpat_bus.push_back(std::move(nb));
     }
@@ -160,7 +190,9 @@ std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int
         }
     }
     std::vector<std::vector<int>> colpat_bus;
-    minimum_degree(n_bus, adj, active, S.ebus, colpat_bus);
+    std::vector<int> wbus(n_bus);
+    for (int i = 0; i < n_bus; i++) wbus[i] = type[i] == kPQ ? 2 : 1;
+    minimum_fill(n_bus, adj, active, wbus, S.ebus, colpat_bus);
     S.n_elim = (int)S.ebus.size();
     S.epos.assign(n_bus, -1);
     for (int k = 0; k < S.n_elim; k++) S.epos[S.ebus[k]] = k;

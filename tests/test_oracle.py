@@ -133,7 +133,7 @@ def test_planted_point_and_newton_from_flat_start():
 
 
 # ---------------------------------------------------------------------------
-# the oracle's LU (static minimum-degree order, no pivoting)
+# the oracle's LU (static minimum-weighted-fill order, no pivoting)
 # ---------------------------------------------------------------------------
 
 def test_lu_against_dense_factorisation():
@@ -308,16 +308,27 @@ def test_bus_relabelling_permutes_the_hessian():
 # symbolic data: ordering, patterns, levels (brute force on small graphs)
 # ---------------------------------------------------------------------------
 
-def brute_min_degree(g):
+def brute_min_weighted_fill(g):
+    """The ordering by its definition: at every step, score every remaining bus from
+    scratch (the weight w_a * w_b of each pair of its neighbours that is not yet
+    adjacent, w = 1 for a PV bus and 2 for a PQ bus; ties: the sum of w over its
+    neighbours, then the bus id) and eliminate the smallest."""
     alive = {i for i in range(g.n_bus) if g.bus_type[i] != 0}
+    w = {i: 2 if g.bus_type[i] == 2 else 1 for i in alive}
     adj = {i: set() for i in alive}
     for f, t in zip(g.fr, g.to):
         if f in alive and t in alive and f != t:
             adj[f].add(t)
             adj[t].add(f)
+
+    def score(i):
+        nb = sorted(adj[i])
+        fill = sum(w[a] * w[b] for x, a in enumerate(nb) for b in nb[x + 1:] if b not in adj[a])
+        return fill, sum(w[a] for a in nb), i
+
     order = []
     while alive:
-        best = min(alive, key=lambda i: (len(adj[i]), i))
+        best = min(alive, key=score)
         nb = adj.pop(best)
         alive.remove(best)
         for a in nb:
@@ -327,12 +338,52 @@ def brute_min_degree(g):
     return order
 
 
+def test_weighted_fill_order_beats_minimum_degree_on_fill():
+    """A property the heuristic is chosen for: on the 118-bus grid the factor it gives
+    holds no more entries than the one of exact minimum degree."""
+    g = tiny(118, 186, 54, 20220100)
+
+    def factor_entries(order):
+        alive = {i for i in range(g.n_bus) if g.bus_type[i] != 0}
+        w = {i: 2 if g.bus_type[i] == 2 else 1 for i in alive}
+        adj = {i: set() for i in alive}
+        for f, t in zip(g.fr, g.to):
+            if f in alive and t in alive and f != t:
+                adj[f].add(t)
+                adj[t].add(f)
+        total = 0
+        for b in order:
+            nb = adj.pop(b)
+            total += w[b] * sum(w[c] for c in nb)
+            for a in nb:
+                adj[a].discard(b)
+                adj[a] |= nb - {a}
+        return total
+
+    alive = {i for i in range(g.n_bus) if g.bus_type[i] != 0}
+    adj = {i: set() for i in alive}
+    for f, t in zip(g.fr, g.to):
+        if f in alive and t in alive and f != t:
+            adj[f].add(t)
+            adj[t].add(f)
+    md = []
+    while alive:
+        best = min(alive, key=lambda i: (len(adj[i]), i))
+        nb = adj.pop(best)
+        alive.remove(best)
+        for a in nb:
+            adj[a].discard(best)
+            adj[a] |= nb - {a}
+        md.append(best)
+    assert factor_entries(brute_min_weighted_fill(g)) <= factor_entries(md)
+
+
 @pytest.mark.parametrize("shape", [(9, 12, 3, 2), (30, 41, 6, 4), (118, 186, 54, 20220100)])
 def test_symbolic_ordering_patterns_levels(shape):
     g = tiny(*shape)
     o = OracleGrid(g)
     sym = o.symbolic()
-    assert list(sym["bus_order"]) == brute_min_degree(g)
+    assert list(sym["bus_order"]) == brute_min_weighted_fill(g)
     ix_th, ix_v, _, _ = o.index_maps()
     perm = []
     for b in sym["bus_order"]:

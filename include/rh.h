@@ -81,8 +81,8 @@ typedef struct {
 /*
  * Load a grid (paper section 3.1).  Builds the pi-model admittance matrix
  * (series y = 1/(r + jx), b/2 at each end), and runs the host symbolic phase:
- * minimum-weighted-fill ordering of the bus graph (the bus whose elimination
- * adds the fewest entries first; ties: weighted degree, then smallest bus id; each
+ * fill-reducing ordering of the bus graph (exact minimum degree or minimum
+ * weighted fill, whichever costs less for a full reduced Hessian; each
  * bus contributes theta then v), symbolic LU of J_x, bus-level schedules, and
  * uploads the fixed patterns to `device`.  The paper factors J_x on the host
  * once and refactors on the device with the same pattern (section 5.2); here

@@ -54,6 +54,8 @@ def _load():
     lib.orc_lagrangian_hessian_dense.argtypes = [P, P, P, P, P, P]
     lib.orc_hessvec.argtypes = [P, P, P, P, P, P, I, I, P, I]
     lib.orc_symbolic.argtypes = [P] + [P] * 7 + [P, P, P]
+    lib.orc_order.argtypes = [P, C.c_int, P]
+    lib.orc_order.restype = C.c_int
     lib.orc_lu_dense.argtypes = [P, P, P, P, P, P]
     lib.orc_cholesky.argtypes = [I, P, I, P, I]
     lib.orc_jacobians_csc.argtypes = [P, P, P] + [P] * 8
@@ -209,6 +211,13 @@ class OracleGrid:
         ncx, ncp = C.c_int32(0), C.c_int32(0)
         _lib.orc_coloring(self._h, _p(cx), _p(cp), C.byref(ncx), C.byref(ncp))
         return cx, cp, int(ncx.value), int(ncp.value)
+
+    def order(self, which):
+        """One candidate elimination order of the buses: "degree" (exact minimum degree),
+        "fill" (minimum weighted fill) or "static" (the one the factorisation uses)."""
+        out = np.empty(self.n_bus, np.int32)
+        n = _lib.orc_order(self._h, {"degree": 0, "fill": 1, "static": 2}[which], _p(out))
+        return out[:n]
 
     def symbolic(self):
         nnzL = C.c_int64(0)

@@ -16,7 +16,7 @@
  *     P_inj + Pd at the slack (a function of x and p);
  *   - textbook analytic Jacobians J_x = dg/dx and J_p = dg/dp;
  *   - Newton-Raphson power flow (section 3.2) with its own left-looking sparse LU
- *     under a static minimum-weighted-fill ordering of the bus graph;
+ *     under a static fill-reducing ordering of the bus graph;
  *   - first-order adjoint lambda and reduced gradient, eq. (6)-(7);
  *   - the explicit Hessian of the Lagrangian l = f + lambda^T g over (x, p),
  *     assembled bus by bus from the second derivatives of every P_i and Q_i
@@ -431,6 +431,109 @@ void orc_jacobians_dense(const orc_grid *g, const double *x, const double *p, do
  * Each bus contributes its x variables in the order theta, then v.
  * perm[q] = x index of the variable eliminated q-th; bus_order[k] = bus id.
  */
+/*
+ * Exact minimum degree: repeatedly eliminate the remaining bus of smallest
+ * current degree (ties: smallest bus id); its remaining neighbours become a
+ * clique.  Same graph and output as mf_order below.
+ */
+static void md_order(const orc_grid *g, int *perm, int *bus_order, int *n_elim) {
+    int n = g->n_bus;
+    size_t words = (size_t)(n + 63) / 64;
+    uint64_t *adj = xcalloc((size_t)n * words, sizeof(uint64_t));
+    int *deg = xcalloc(n, sizeof(int));
+    char *alive = xcalloc(n, 1);
+#define HAS(a, b) ((adj[(size_t)(a) * words + (b) / 64] >> ((b) % 64)) & 1u)
+#define SET(a, b) (adj[(size_t)(a) * words + (b) / 64] |= (uint64_t)1 << ((b) % 64))
+#define CLR(a, b) (adj[(size_t)(a) * words + (b) / 64] &= ~((uint64_t)1 << ((b) % 64)))
+    for (int i = 0; i < n; i++) alive[i] = g->type[i] != REF;
+    for (int i = 0; i < n; i++) {
+        if (!alive[i]) continue;
+        for (int k = g->yp[i]; k < g->yp[i + 1]; k++) {
+            int j = g->yj[k];
+            if (j != i && alive[j] && !HAS(i, j)) { SET(i, j); deg[i]++; }
+        }
+    }
+    int *nb = xcalloc(n, sizeof(int));
+    int cnt = 0, q = 0;
+    for (;;) {
+        int best = -1;
+        for (int i = 0; i < n; i++)
+            if (alive[i] && (best < 0 || deg[i] < deg[best])) best = i;
+        if (best < 0) break;
+        int m = 0;
+        for (int j = 0; j < n; j++) if (alive[j] && j != best && HAS(best, j)) nb[m++] = j;
+        alive[best] = 0;
+        for (int a = 0; a < m; a++) { CLR(nb[a], best); deg[nb[a]]--; }
+        for (int a = 0; a < m; a++)
+            for (int c = a + 1; c < m; c++)
+                if (!HAS(nb[a], nb[c])) { SET(nb[a], nb[c]); SET(nb[c], nb[a]); deg[nb[a]]++; deg[nb[c]]++; }
+        bus_order[cnt++] = best;
+        perm[q++] = g->ix_th[best];
+        if (g->ix_v[best] >= 0) perm[q++] = g->ix_v[best];
+    }
+#undef HAS
+#undef SET
+#undef CLR
+    *n_elim = cnt;
+    free(adj); free(deg); free(alive); free(nb);
+}
+
+/*
+ * Cost of an elimination order, replayed on a fresh elimination graph: the
+ * factor entries outside the bus blocks (sum over buses of w_k times the
+ * weight of the neighbours it has when eliminated, w as in mf_order) times
+ * n_dirs, plus ORDER_LEVEL_COST per forward level (a bus's level is one more
+ * than the highest level of the buses whose elimination reached it).
+ */
+#define ORDER_LEVEL_COST 1700000LL
+static long long order_cost(const orc_grid *g, const int *bus_order, int n_elim, long long n_dirs) {
+    int n = g->n_bus;
+    size_t words = (size_t)(n + 63) / 64;
+    uint64_t *adj = xcalloc((size_t)n * words, sizeof(uint64_t));
+    char *alive = xcalloc(n, 1);
+    int *lev = xcalloc(n, sizeof(int));
+#define HAS(a, b) ((adj[(size_t)(a) * words + (b) / 64] >> ((b) % 64)) & 1u)
+#define SET(a, b) (adj[(size_t)(a) * words + (b) / 64] |= (uint64_t)1 << ((b) % 64))
+    for (int i = 0; i < n; i++) alive[i] = g->type[i] != REF;
+    for (int i = 0; i < n; i++) {
+        if (!alive[i]) continue;
+        for (int k = g->yp[i]; k < g->yp[i + 1]; k++) {
+            int j = g->yj[k];
+            if (j != i && alive[j]) SET(i, j);
+        }
+    }
+    int *nb = xcalloc(n, sizeof(int));
+    long long entries = 0;
+    int n_lev = 0;
+    for (int k = 0; k < n_elim; k++) {
+        int e = bus_order[k];
+        alive[e] = 0;
+        int m = 0;                                  /* remaining neighbours of e, from its row of bits */
+        for (size_t wd = 0; wd < words; wd++) {
+            uint64_t bits = adj[(size_t)e * words + wd];
+            while (bits) {
+                int j = (int)(wd * 64) + __builtin_ctzll(bits);
+                bits &= bits - 1;
+                if (alive[j]) nb[m++] = j;
+            }
+        }
+        long long s = 0;
+        for (int a = 0; a < m; a++) {
+            int j = nb[a];
+            s += g->type[j] == PQ ? 2 : 1;
+            if (lev[j] < lev[e] + 1) lev[j] = lev[e] + 1;
+            for (int c = 0; c < m; c++)
+                if (c != a) SET(j, nb[c]);
+        }
+        entries += (g->type[e] == PQ ? 2 : 1) * s;
+        if (lev[e] + 1 > n_lev) n_lev = lev[e] + 1;
+    }
+#undef HAS
+#undef SET
+    free(adj); free(alive); free(lev); free(nb);
+    return entries * n_dirs + ORDER_LEVEL_COST * n_lev;
+}
+
 /* the remaining neighbours of bus v in the elimination graph, read from its row of bits */
 static int mf_row(const uint64_t *adj, size_t words, int v, const char *alive, int *out) {
     int m = 0;
@@ -515,6 +618,39 @@ static void mf_order(const orc_grid *g, int *perm, int *bus_order, int *n_elim) 
 #undef CLR
     *n_elim = cnt;
     free(adj); free(alive); free(w); free(fill); free(wdeg); free(nb); free(nb2); free(hit);
+}
+
+/*
+ * The static order: whichever of minimum degree and minimum weighted fill has
+ * the smaller order_cost for the directions of a full reduced Hessian (n_p);
+ * ties go to minimum degree.
+ */
+static void static_order(const orc_grid *g, int *perm, int *bus_order, int *n_elim) {
+    int nx = g->n_x, nb = g->n_bus;
+    int *perm2 = xcalloc(nx > 0 ? nx : 1, sizeof(int)), *bo2 = xcalloc(nb, sizeof(int));
+    int n1 = 0, n2 = 0;
+    md_order(g, perm, bus_order, &n1);
+    mf_order(g, perm2, bo2, &n2);
+    if (order_cost(g, bo2, n2, g->n_p) < order_cost(g, bus_order, n1, g->n_p)) {
+        memcpy(perm, perm2, (size_t)nx * sizeof(int));
+        memcpy(bus_order, bo2, (size_t)n2 * sizeof(int));
+        n1 = n2;
+    }
+    *n_elim = n1;
+    free(perm2); free(bo2);
+}
+
+/* One candidate order on its own (which = 0: minimum degree, 1: minimum weighted
+ * fill, 2: the static choice); bus_order has n_bus entries.  Returns n_elim. */
+int orc_order(const orc_grid *g, int which, int32_t *bus_order) {
+    int *perm = xcalloc(g->n_x > 0 ? g->n_x : 1, sizeof(int)), *bo = xcalloc(g->n_bus, sizeof(int));
+    int n = 0;
+    if (which == 0) md_order(g, perm, bo, &n);
+    else if (which == 1) mf_order(g, perm, bo, &n);
+    else static_order(g, perm, bo, &n);
+    for (int k = 0; k < n; k++) bus_order[k] = bo[k];
+    free(perm); free(bo);
+    return n;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -630,7 +766,7 @@ static int factor_at(const orc_grid *g, const orc_state *s, orc_lu *F, csc *Jp_o
     csc Jx, Jp;
     jacobians(g, s, &Jx, &Jp);
     int *perm = xcalloc(g->n_x, sizeof(int)), *bo = xcalloc(g->n_bus, sizeof(int)), nb;
-    mf_order(g, perm, bo, &nb);
+    static_order(g, perm, bo, &nb);
     int st = lu_factor(&Jx, perm, F);
     free(perm); free(bo);
     csc_free(&Jx);
@@ -876,7 +1012,7 @@ int orc_hessvec(const orc_grid *g, const double *x, const double *p, const doubl
 /* ------------------------------------------------------------------------ */
 
 /*
- * Ordering from mf_order.  Patterns from a structural (boolean) left-looking
+ * Ordering from static_order.  Patterns from a structural (boolean) left-looking
  * factorization of the permuted J_x pattern at the variable level: column k
  * gathers the rows of column k of B and, for every j < k already reached, the
  * rows of L(:, j).  J_x entries are taken as structurally nonzero wherever the
@@ -895,7 +1031,7 @@ int orc_symbolic(const orc_grid *g, int32_t *perm_out, int32_t *bus_order_out, i
                  int64_t *nnzL, int64_t *nnzU, int32_t *n_elim) {
     int nx = g->n_x, n = g->n_bus;
     int *perm = xcalloc(nx, sizeof(int)), *bo = xcalloc(n, sizeof(int)), nb = 0;
-    mf_order(g, perm, bo, &nb);
+    static_order(g, perm, bo, &nb);
     int *iperm = xcalloc(nx, sizeof(int));
     for (int q = 0; q < nx; q++) iperm[perm[q]] = q;
     /* structural J_x pattern by columns, in permuted indices */

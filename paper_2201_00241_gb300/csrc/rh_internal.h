@@ -23,6 +23,7 @@ enum BusType : int8_t { kRef = 0, kPV = 1, kPQ = 2 };
 struct Symbolic {
     int n_bus = 0, n_branch = 0, n_gen = 0, n_pv = 0, n_pq = 0, ref = -1;
     int n_x = 0, n_p = 0, n_elim = 0;
+    bool order_mf = false;                  // minimum weighted fill chosen over minimum degree
 
     // external index maps (documented in rh.h): -1 where absent
     std::vector<int> ix_th, ix_v, ip_v, ip_pg;

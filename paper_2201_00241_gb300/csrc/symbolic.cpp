@@ -18,6 +18,66 @@
 namespace rh {
 namespace {
 
+// Exact minimum degree on the bus graph: repeatedly eliminate the remaining
+// bus of smallest degree in the current elimination graph (ties: smallest bus
+// id); the neighbours of an eliminated bus become a clique.  Adjacency lists
+// are kept sorted; a min-heap with lazy invalidation finds the next bus.
+// colpat_bus[k] receives the neighbour set (bus ids) of the k-th eliminated bus.
+void minimum_degree(int n_bus, const std::vector<std::vector<int>>& adj0, const std::vector<char>& active,
+                    std::vector<int>& order, std::vector<std::vector<int>>& colpat_bus) {
+    std::vector<std::vector<int>> adj = adj0;
+    std::vector<char> alive = active;
+    using Key = std::pair<int, int>;  // (degree, bus id)
+    std::priority_queue<Key, std::vector<Key>, std::greater<Key>> heap;
+    for (int i = 0; i < n_bus; i++)
+        if (alive[i]) heap.push({(int)adj[i].size(), i});
+    std::vector<int> merged;
+    while (!heap.empty()) {
+        auto [d, e] = heap.top();
+        heap.pop();
+        if (!alive[e] || d != (int)adj[e].size()) continue;  // stale entry
+        alive[e] = 0;
+        std::vector<int> nb = std::move(adj[e]);
+        adj[e].clear();
+        for (int a : nb) {
+            // adj[a] <- (adj[a] U nb) \ {a, e}
+            merged.clear();
+            std::set_union(adj[a].begin(), adj[a].end(), nb.begin(), nb.end(), std::back_inserter(merged));
+            adj[a].clear();
+            for (int v : merged)
+                if (v != a && v != e) adj[a].push_back(v);
+            heap.push({(int)adj[a].size(), a});
+        }
+        order.push_back(e);
+        colpat_bus.push_back(std::move(nb));
+    }
+}
+
+// Cost of an elimination order for choosing between the two orders below: the
+// factor entries outside the bus blocks (sum over buses of w_k times the weight
+// of the neighbours it has when eliminated) times the directions of a full
+// reduced Hessian, plus kLevelCost per forward level (each level of the four
+// direction sweeps costs a barrier and a chain of dependent loads, about as
+// long on GB300 as 1.7 M of those entry-direction FMAs).
+constexpr int64_t kLevelCost = 1700000;
+int64_t order_cost(int n_bus, const std::vector<int>& order, const std::vector<std::vector<int>>& colpat_bus,
+                   const std::vector<int>& w, int64_t n_dirs) {
+    std::vector<int> pos(n_bus, -1), lev(order.size(), 0);
+    for (size_t k = 0; k < order.size(); k++) pos[order[k]] = (int)k;
+    int64_t entries = 0;
+    int n_lev = 0;
+    for (size_t k = 0; k < order.size(); k++) {
+        int64_t s = 0;
+        for (int c : colpat_bus[k]) {
+            s += w[c];
+            lev[pos[c]] = std::max(lev[pos[c]], lev[k] + 1);
+        }
+        entries += (int64_t)w[order[k]] * s;
+        n_lev = std::max(n_lev, lev[k] + 1);
+    }
+    return entries * n_dirs + kLevelCost * n_lev;
+}
+
 // Minimum weighted fill on the bus graph.  Eliminating bus e joins its remaining
 // neighbours into a clique: every pair (a, b) of them that is not yet adjacent
 // adds w_a * w_b entries to L (and as many to U), w = variables per bus (1 for a
@@ -189,10 +249,21 @@ std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int
             if (j != i && active[j]) adj[i].push_back(j);   // yj is sorted and unique
         }
     }
-    std::vector<std::vector<int>> colpat_bus;
+    // Two candidate orders: exact minimum degree (fewer levels on small grids) and
+    // minimum weighted fill (fewer factor entries); the cheaper by order_cost wins
+    // (ties: minimum degree).
     std::vector<int> wbus(n_bus);
     for (int i = 0; i < n_bus; i++) wbus[i] = type[i] == kPQ ? 2 : 1;
-    minimum_fill(n_bus, adj, active, wbus, S.ebus, colpat_bus);
+    std::vector<int> order_md, order_mf;
+    std::vector<std::vector<int>> colpat_md, colpat_mf;
+    minimum_degree(n_bus, adj, active, order_md, colpat_md);
+    minimum_fill(n_bus, adj, active, wbus, order_mf, colpat_mf);
+    const int64_t n_dirs = S.n_p;
+    const bool mf = order_cost(n_bus, order_mf, colpat_mf, wbus, n_dirs) <
+                    order_cost(n_bus, order_md, colpat_md, wbus, n_dirs);
+    S.order_mf = mf;
+    S.ebus = mf ? std::move(order_mf) : std::move(order_md);
+    std::vector<std::vector<int>> colpat_bus = mf ? std::move(colpat_mf) : std::move(colpat_md);
     S.n_elim = (int)S.ebus.size();
     S.epos.assign(n_bus, -1);
     for (int k = 0; k < S.n_elim; k++) S.epos[S.ebus[k]] = k;

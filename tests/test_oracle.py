@@ -133,7 +133,7 @@ def test_planted_point_and_newton_from_flat_start():
 
 
 # ---------------------------------------------------------------------------
-# the oracle's LU (static minimum-weighted-fill order, no pivoting)
+# the oracle's LU (static fill-reducing order, no pivoting)
 # ---------------------------------------------------------------------------
 
 def test_lu_against_dense_factorisation():
@@ -338,35 +338,19 @@ def brute_min_weighted_fill(g):
     return order
 
 
-def test_weighted_fill_order_beats_minimum_degree_on_fill():
-    """A property the heuristic is chosen for: on the 118-bus grid the factor it gives
-    holds no more entries than the one of exact minimum degree."""
-    g = tiny(118, 186, 54, 20220100)
-
-    def factor_entries(order):
-        alive = {i for i in range(g.n_bus) if g.bus_type[i] != 0}
-        w = {i: 2 if g.bus_type[i] == 2 else 1 for i in alive}
-        adj = {i: set() for i in alive}
-        for f, t in zip(g.fr, g.to):
-            if f in alive and t in alive and f != t:
-                adj[f].add(t)
-                adj[t].add(f)
-        total = 0
-        for b in order:
-            nb = adj.pop(b)
-            total += w[b] * sum(w[c] for c in nb)
-            for a in nb:
-                adj[a].discard(b)
-                adj[a] |= nb - {a}
-        return total
-
+def _bus_graph(g):
     alive = {i for i in range(g.n_bus) if g.bus_type[i] != 0}
     adj = {i: set() for i in alive}
     for f, t in zip(g.fr, g.to):
         if f in alive and t in alive and f != t:
             adj[f].add(t)
             adj[t].add(f)
-    md = []
+    return alive, adj
+
+
+def brute_min_degree(g):
+    alive, adj = _bus_graph(g)
+    order = []
     while alive:
         best = min(alive, key=lambda i: (len(adj[i]), i))
         nb = adj.pop(best)
@@ -374,8 +358,48 @@ def test_weighted_fill_order_beats_minimum_degree_on_fill():
         for a in nb:
             adj[a].discard(best)
             adj[a] |= nb - {a}
-        md.append(best)
-    assert factor_entries(brute_min_weighted_fill(g)) <= factor_entries(md)
+        order.append(best)
+    return order
+
+
+def order_cost(g, order, n_dirs, level_cost=1_700_000):
+    """Factor entries outside the bus blocks (w_k times the weight of the neighbours bus
+    k has when eliminated) times n_dirs, plus level_cost per forward level."""
+    alive, adj = _bus_graph(g)
+    w = {i: 2 if g.bus_type[i] == 2 else 1 for i in alive}
+    lev = {i: 0 for i in alive}
+    entries = 0
+    for b in order:
+        nb = adj.pop(b)
+        entries += w[b] * sum(w[c] for c in nb)
+        for a in nb:
+            lev[a] = max(lev[a], lev[b] + 1)
+            adj[a].discard(b)
+            adj[a] |= nb - {a}
+    return entries * n_dirs + level_cost * (max(lev.values()) + 1)
+
+
+def brute_static_order(g, n_p):
+    md, mf = brute_min_degree(g), brute_min_weighted_fill(g)
+    return mf if order_cost(g, mf, n_p) < order_cost(g, md, n_p) else md
+
+
+@pytest.mark.parametrize("shape", [(9, 12, 3, 2), (30, 41, 6, 4), (118, 186, 54, 20220100)])
+def test_both_candidate_orders_against_brute_force(shape):
+    """Each of the oracle's two candidate orders equals its from-scratch definition, and
+    the order it uses is the cheaper one by the stated cost (ties: minimum degree)."""
+    g = tiny(*shape)
+    o = OracleGrid(g)
+    assert list(o.order("degree")) == brute_min_degree(g)
+    assert list(o.order("fill")) == brute_min_weighted_fill(g)
+    assert list(o.order("static")) == brute_static_order(g, o.n_p)
+
+
+def test_weighted_fill_order_beats_minimum_degree_on_fill():
+    """A property the heuristic is chosen for: on the 118-bus grid the factor it gives
+    holds no more entries than the one of exact minimum degree."""
+    g = tiny(118, 186, 54, 20220100)
+    assert order_cost(g, brute_min_weighted_fill(g), 1, 0) <= order_cost(g, brute_min_degree(g), 1, 0)
 
 
 @pytest.mark.parametrize("shape", [(9, 12, 3, 2), (30, 41, 6, 4), (118, 186, 54, 20220100)])
@@ -383,7 +407,7 @@ def test_symbolic_ordering_patterns_levels(shape):
     g = tiny(*shape)
     o = OracleGrid(g)
     sym = o.symbolic()
-    assert list(sym["bus_order"]) == brute_min_weighted_fill(g)
+    assert list(sym["bus_order"]) == brute_static_order(g, o.n_p)
     ix_th, ix_v, _, _ = o.index_maps()
     perm = []
     for b in sym["bus_order"]:

@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -518,8 +519,11 @@ def main():
 
     # the clock sampler starts before the warm-up, so that its start-up (NVML initialisation)
     # is over before the timed steps; it keeps sampling through them
-    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                            f"clocks_rank{rank}.csv")
+    # the raw samples go to RH_BENCH_CLOCKS_CSV (with _rank<r> before .csv) when it is set, else to a
+    # temporary file; the JSON line carries their summary
+    clk_env = os.environ.get("RH_BENCH_CLOCKS_CSV")
+    clk_path = (clk_env[:-4] if clk_env and clk_env.endswith(".csv") else clk_env) + f"_rank{rank}.csv" if clk_env \
+        else os.path.join(tempfile.gettempdir(), f"rh_bench_clocks_{os.getpid()}_rank{rank}.csv")
     sampler = start_clock_sampler(clk_path)
     time.sleep(1.0)
     for _ in range(args.warmup):

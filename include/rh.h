@@ -63,6 +63,14 @@ typedef struct {
     const int8_t *bus_type;         /* 0 slack, 1 PV, 2 PQ                                   */
     const double *c2, *c1;          /* cost coefficients per bus (used at generator buses)    */
     double base_mva;                /* S                                                     */
+    /* Weight of one forward level in the choice between the two fill-reducing
+     * orders (rh_grid_create), in factor-entry x direction units: an order costs
+     * (entries off the bus blocks) x n_p + order_level_cost x (forward levels).
+     * 0 picks the order with fewer entries; must be >= 0.  Python callers take
+     * the value from the grid record (1.7e6 measured for GB300's direction
+     * sweeps: one level of the four sweeps costs about as much as 1.7 M
+     * entry-direction FMAs). */
+    int64_t order_level_cost;
 } rh_grid_desc;
 
 typedef struct {
@@ -82,8 +90,9 @@ typedef struct {
  * Load a grid (paper section 3.1).  Builds the pi-model admittance matrix
  * (series y = 1/(r + jx), b/2 at each end), and runs the host symbolic phase:
  * fill-reducing ordering of the bus graph (exact minimum degree or minimum
- * weighted fill, whichever costs less for a full reduced Hessian; each
- * bus contributes theta then v), symbolic LU of J_x, bus-level schedules, and
+ * weighted fill, whichever costs less for a full reduced Hessian by the
+ * cost of desc->order_level_cost; each bus contributes theta then v),
+ * symbolic LU of J_x, bus-level schedules, and
  * uploads the fixed patterns to `device`.  The paper factors J_x on the host
  * once and refactors on the device with the same pattern (section 5.2); here
  * only the symbolic part runs on the host.
@@ -91,7 +100,7 @@ typedef struct {
  * answers rh_grid_dims and rh_grid_symbolic, every other call returns
  * RH_ESTATE.
  * Returns RH_EINVAL for a grid without exactly one slack bus, an out-of-range
- * or self-loop branch, or a non-positive |r + jx|.
+ * or self-loop branch, a non-positive |r + jx| or a negative order_level_cost.
  */
 rh_status rh_grid_create(const rh_grid_desc *desc, int32_t device, rh_grid **out);
 void rh_grid_destroy(rh_grid *grid);
@@ -262,9 +271,9 @@ rh_status rh_lagrangian_hessvec(rh_grid *grid, const double *V, int64_t ldv, int
                                 double *Y, int64_t ldy, void *stream, uint32_t flags);
 
 /*
- * Allocation-free form of rh_hessvec (the paper has no counterpart: this is a
- * deployment variant of Algorithm 2).  For callers that must not have the
- * library allocate device memory after start-up, such as an application that
+ * Allocation-free form of rh_hessvec (the paper has no counterpart).  For
+ * callers that must not have the library allocate device memory after
+ * start-up, such as an application that
  * owns all device memory through its own pool, or a real-time control loop
  * that forbids allocation once running.  The two direction buffers of the
  * computation live in a fixed device array of 2 x 8 MiB that every GPU holding

@@ -14,7 +14,9 @@ n_x / n_p counts of Table 1):
 
 Grids are duck-typed: any object with the attributes of
 ``paper_2201_00241_gb300.gridgen.Grid`` (fr, to, r, x, b, bus_type, c2, c1,
-base_mva, v_star, theta_star).
+base_mva, order_level_cost, v_star, theta_star).  order_level_cost is the
+weight of one forward level when the two fill-reducing orders are compared,
+a parameter of the static pivot order the paper leaves unstated.
 """
 from __future__ import annotations
 
@@ -37,7 +39,7 @@ def _load():
     I = C.c_int
     D = C.c_double
     lib.orc_grid_new.restype = P
-    lib.orc_grid_new.argtypes = [I, I, P, P, P, P, P, P, P, P, D]
+    lib.orc_grid_new.argtypes = [I, I, P, P, P, P, P, P, P, P, D, C.c_longlong]
     lib.orc_grid_free.argtypes = [P]
     lib.orc_n_x.argtypes = [P]
     lib.orc_n_p.argtypes = [P]
@@ -97,7 +99,7 @@ class OracleGrid:
         self.n_bus = int(grid.n_bus)
         self._h = lib.orc_grid_new(self.n_bus, int(grid.n_branch), _p(k[0]), _p(k[1]), _p(k[2]),
                                    _p(k[3]), _p(k[4]), _p(k[5]), _p(k[6]), _p(k[7]),
-                                   float(grid.base_mva))
+                                   float(grid.base_mva), int(grid.order_level_cost))
         self.n_x = lib.orc_n_x(self._h)
         self.n_p = lib.orc_n_p(self._h)
         self.ref = lib.orc_ref(self._h)

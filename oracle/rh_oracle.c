@@ -50,6 +50,7 @@ typedef struct {
     int8_t *type;
     double *c2, *c1;
     double S;                 /* base MVA */
+    long long level_cost;     /* weight of one forward level in the order cost */
     /* admittance matrix, one row per bus, diagonal included (CSR) */
     int *yp, *yj;
     double *G, *B;
@@ -89,11 +90,12 @@ void orc_grid_free(orc_grid *g) {
 orc_grid *orc_grid_new(int n_bus, int n_branch, const int32_t *fr, const int32_t *to,
                        const double *r, const double *x, const double *b,
                        const int8_t *type, const double *c2, const double *c1,
-                       double base_mva) {
+                       double base_mva, long long level_cost) {
     orc_grid *g = xcalloc(1, sizeof *g);
     g->n_bus = n_bus;
     g->n_branch = n_branch;
     g->S = base_mva;
+    g->level_cost = level_cost;
     g->type = xcalloc(n_bus, 1);
     g->c2 = xcalloc(n_bus, sizeof(double));
     g->c1 = xcalloc(n_bus, sizeof(double));
@@ -482,10 +484,11 @@ static void md_order(const orc_grid *g, int *perm, int *bus_order, int *n_elim) 
  * Cost of an elimination order, replayed on a fresh elimination graph: the
  * factor entries outside the bus blocks (sum over buses of w_k times the
  * weight of the neighbours it has when eliminated, w as in mf_order) times
- * n_dirs, plus ORDER_LEVEL_COST per forward level (a bus's level is one more
- * than the highest level of the buses whose elimination reached it).
+ * n_dirs, plus the grid's level_cost per forward level (a bus's level is one
+ * more than the highest level of the buses whose elimination reached it).
+ * level_cost is a parameter of the ordering rule (the paper gives none, it
+ * relies on a host LU), passed in with the grid.
  */
-#define ORDER_LEVEL_COST 1700000LL
 static long long order_cost(const orc_grid *g, const int *bus_order, int n_elim, long long n_dirs) {
     int n = g->n_bus;
     size_t words = (size_t)(n + 63) / 64;
@@ -531,7 +534,7 @@ static long long order_cost(const orc_grid *g, const int *bus_order, int n_elim,
 #undef HAS
 #undef SET
     free(adj); free(alive); free(lev); free(nb);
-    return entries * n_dirs + ORDER_LEVEL_COST * n_lev;
+    return entries * n_dirs + g->level_cost * n_lev;
 }
 
 /* the remaining neighbours of bus v in the elimination graph, read from its row of bits */

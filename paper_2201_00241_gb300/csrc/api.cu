@@ -407,7 +407,8 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     std::unique_ptr<rh_grid> g(new rh_grid());
     g->device = device;
     g->base_mva = d->base_mva;
-    std::string msg = rh::build_symbolic(d->n_bus, d->n_branch, d->from, d->to, d->r, d->x, d->b, d->bus_type, g->S);
+    std::string msg = rh::build_symbolic(d->n_bus, d->n_branch, d->from, d->to, d->r, d->x, d->b, d->bus_type,
+                                         d->order_level_cost, g->S);
     if (!msg.empty()) return fail(RH_EINVAL, msg);
     const auto& S = g->S;
     if (device < 0) {  // symbolic phase only: no device state

@@ -97,9 +97,12 @@ struct Symbolic {
 };
 
 // Builds everything above.  Returns an empty string on success, else a message.
-// max_tail: largest trailing block (variables) factored densely.
+// level_cost: weight of one forward level when the two orders are compared
+// (factor entries x n_p + level_cost x forward levels; the reading R9 of the
+// paper's unstated pivot order).  max_tail: largest trailing block (variables)
+// factored densely.
 std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int32_t* to,
                            const double* r, const double* x, const double* b,
-                           const int8_t* type, Symbolic& S, int max_tail = 128);
+                           const int8_t* type, int64_t level_cost, Symbolic& S, int max_tail = 128);
 
 }  // namespace rh

@@ -56,12 +56,11 @@ void minimum_degree(int n_bus, const std::vector<std::vector<int>>& adj0, const 
 // Cost of an elimination order for choosing between the two orders below: the
 // factor entries outside the bus blocks (sum over buses of w_k times the weight
 // of the neighbours it has when eliminated) times the directions of a full
-// reduced Hessian, plus kLevelCost per forward level (each level of the four
-// direction sweeps costs a barrier and a chain of dependent loads, about as
-// long on GB300 as 1.7 M of those entry-direction FMAs).
-constexpr int64_t kLevelCost = 1700000;
+// reduced Hessian, plus level_cost per forward level (each level of the four
+// direction sweeps costs a barrier and a chain of dependent loads; the caller
+// passes what one level costs in entry-direction FMAs).
 int64_t order_cost(int n_bus, const std::vector<int>& order, const std::vector<std::vector<int>>& colpat_bus,
-                   const std::vector<int>& w, int64_t n_dirs) {
+                   const std::vector<int>& w, int64_t n_dirs, int64_t level_cost) {
     std::vector<int> pos(n_bus, -1), lev(order.size(), 0);
     for (size_t k = 0; k < order.size(); k++) pos[order[k]] = (int)k;
     int64_t entries = 0;
@@ -75,7 +74,7 @@ int64_t order_cost(int n_bus, const std::vector<int>& order, const std::vector<s
         entries += (int64_t)w[order[k]] * s;
         n_lev = std::max(n_lev, lev[k] + 1);
     }
-    return entries * n_dirs + kLevelCost * n_lev;
+    return entries * n_dirs + level_cost * n_lev;
 }
 
 // Minimum weighted fill on the bus graph.  Eliminating bus e joins its remaining
@@ -176,8 +175,9 @@ int greedy_columns(int n_cols, const std::vector<std::vector<int>>& row_cols, st
 
 std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int32_t* to,
                            const double* r, const double* x, const double* b,
-                           const int8_t* type, Symbolic& S, int max_tail) {
+                           const int8_t* type, int64_t level_cost, Symbolic& S, int max_tail) {
     if (n_bus < 1 || n_branch < 0) return "n_bus must be >= 1 and n_branch >= 0";
+    if (level_cost < 0) return "order_level_cost must be >= 0";
     S.n_bus = n_bus;
     S.n_branch = n_branch;
     int n_ref = 0;
@@ -259,8 +259,8 @@ std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int
     minimum_degree(n_bus, adj, active, order_md, colpat_md);
     minimum_fill(n_bus, adj, active, wbus, order_mf, colpat_mf);
     const int64_t n_dirs = S.n_p;
-    const bool mf = order_cost(n_bus, order_mf, colpat_mf, wbus, n_dirs) <
-                    order_cost(n_bus, order_md, colpat_md, wbus, n_dirs);
+    const bool mf = order_cost(n_bus, order_mf, colpat_mf, wbus, n_dirs, level_cost) <
+                    order_cost(n_bus, order_md, colpat_md, wbus, n_dirs, level_cost);
     S.order_mf = mf;
     S.ebus = mf ? std::move(order_mf) : std::move(order_md);
     std::vector<std::vector<int>> colpat_bus = mf ? std::move(colpat_mf) : std::move(colpat_md);

@@ -39,6 +39,14 @@ import numpy as np
 
 REF, PV, PQ = 0, 1, 2
 
+# Weight of one forward level when the symbolic phase compares its two
+# fill-reducing orders: an order costs (factor entries off the bus blocks) x n_p
+# + ORDER_LEVEL_COST x (forward levels).  The paper leaves the pivot order to a
+# host LU; this build's order rule takes the weight as a parameter of the grid
+# record.  1.7e6: one level of the four direction sweeps costs GB300 about as
+# much time as 1.7 M entry-direction FMAs (measured).
+ORDER_LEVEL_COST = 1_700_000
+
 # Table 1 shapes (n_v, n_e, generators) and the seed of each synthetic case.
 CASES = {
     "case118": dict(n_bus=118, n_branch=186, n_gen=54, seed=20220100),
@@ -64,6 +72,7 @@ class Grid:
     c1: np.ndarray          # float64 [n_bus] linear cost ($/MWh), 0 off generators
     base_mva: float
     seed: int
+    order_level_cost: int = ORDER_LEVEL_COST
 
     @property
     def n_gen(self) -> int:

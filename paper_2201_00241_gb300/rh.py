@@ -37,7 +37,8 @@ class RHError(RuntimeError):
 class _Desc(C.Structure):
     _fields_ = [("n_bus", C.c_int32), ("n_branch", C.c_int32), ("from_", C.c_void_p), ("to", C.c_void_p),
                 ("r", C.c_void_p), ("x", C.c_void_p), ("b", C.c_void_p), ("bus_type", C.c_void_p),
-                ("c2", C.c_void_p), ("c1", C.c_void_p), ("base_mva", C.c_double)]
+                ("c2", C.c_void_p), ("c1", C.c_void_p), ("base_mva", C.c_double),
+                ("order_level_cost", C.c_int64)]
 
 
 class HvItem(C.Structure):
@@ -153,7 +154,8 @@ class Grid:
                       _f64(grid.r), _f64(grid.x), _f64(grid.b), np.ascontiguousarray(grid.bus_type, dtype=np.int8),
                       _f64(grid.c2), _f64(grid.c1)]
         k = self._keep
-        d = _Desc(int(grid.n_bus), int(grid.n_branch), *[_ptr(a) for a in k], float(grid.base_mva))
+        d = _Desc(int(grid.n_bus), int(grid.n_branch), *[_ptr(a) for a in k], float(grid.base_mva),
+                  int(grid.order_level_cost))
         h = C.c_void_p(0)
         _check(lib.rh_grid_create(C.byref(d), int(device), C.byref(h)))
         self._h = h

@@ -37,16 +37,23 @@ def host_grid(g):
             np.ascontiguousarray(g.r, float), np.ascontiguousarray(g.x, float), np.ascontiguousarray(g.b, float),
             np.ascontiguousarray(g.bus_type, np.int8), np.ascontiguousarray(g.c2, float),
             np.ascontiguousarray(g.c1, float)]
-    d = rh._Desc(g.n_bus, g.n_branch, *[rh._ptr(a) for a in keep], g.base_mva)
+    d = rh._Desc(g.n_bus, g.n_branch, *[rh._ptr(a) for a in keep], g.base_mva, g.order_level_cost)
     h = C.c_void_p(0)
     st = lib.rh_grid_create(C.byref(d), -1, C.byref(h))
     return st, h, keep
 
 
-@pytest.mark.parametrize("case", ["tiny9", "tiny30", "case118", "case1354", "case2869", "case9241"])
-def test_symbolic_bit_exact_against_oracle(case):
+@pytest.mark.parametrize("case,level_cost", [("tiny9", None), ("tiny30", None), ("case118", None),
+                                             ("case1354", None), ("case2869", None), ("case9241", None),
+                                             ("case118", 0), ("case1354", 0), ("case1354", 10**12)])
+def test_symbolic_bit_exact_against_oracle(case, level_cost):
+    """Order, patterns and levels equal the oracle's, bit for bit; also with other
+    values of the level weight that both sides take from the grid record."""
+    import dataclasses
     g = gg.make_grid(9, 12, 3, 2) if case == "tiny9" else gg.make_grid(30, 41, 6, 4) if case == "tiny30" \
         else gg.make_case(case)
+    if level_cost is not None:
+        g = dataclasses.replace(g, order_level_cost=level_cost)
     lib = rh.load()
     st, h, keep = host_grid(g)
     assert st == 0, lib.rh_last_error()
@@ -87,6 +94,9 @@ def test_invalid_grids_are_rejected():
     bad.x = np.zeros_like(bad.x)                  # zero impedance
     st, h, _ = host_grid(bad)
     assert st == rh.RH_EINVAL
+    import dataclasses
+    st, h, _ = host_grid(dataclasses.replace(g, order_level_cost=-1))   # negative level weight
+    assert st == rh.RH_EINVAL and b"order_level_cost" in lib.rh_last_error()
     st, h, _ = host_grid(g)
     assert st == 0
     lib.rh_grid_destroy(h)

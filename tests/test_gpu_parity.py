@@ -192,17 +192,14 @@ def test_full_hessian_blocks_and_concurrent(case):
     assert rel(Hc, Hc.T) <= 1e-11
 
 
-def test_case9241_full_size_sampled_columns():
+def test_case9241_full_size_all_columns():
     """The benchmark workload: all 2889 columns of H in one concurrent launch (blocks of
-    256); sampled columns against the oracle, symmetry on the whole matrix."""
+    256), every column against the oracle, symmetry on the whole matrix."""
     d = setup_case("case9241")
     lg = d["lg"]
     H = lg.hessian(block_n=256, concurrent=True)
-    cols = np.random.default_rng(9241).choice(lg.n_p, 12, replace=False)
-    E = np.zeros((lg.n_p, len(cols)))
-    E[cols, np.arange(len(cols))] = 1.0
-    Ho = oracle_hv(d, E)
-    assert rel(H[:, cols], Ho) <= TOL_HW
+    Ho = oracle_hv(d, np.eye(lg.n_p))
+    assert rel(H, Ho) <= TOL_HW
     assert rel(H, H.T) <= 1e-10
     # and a random block of N = 256 directions (sampled columns)
     W = gg.random_directions(lg.n_p, 256, 9241)

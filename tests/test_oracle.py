@@ -277,6 +277,24 @@ def test_lossless_closed_form():
     assert abs(H - expect).max() <= 1e-9 * abs(expect).max()
 
 
+def test_lossless_closed_form_case9241():
+    """The same closed form at the size of the benchmark grid (all 2889 columns): the
+    pipeline's cancellation holds through the large factorisation and every sweep."""
+    g = gg.make_case("case9241", lossless=True)
+    o = OracleGrid(g)
+    st = o.plant()
+    H = full_hessian(o, st)
+    _, _, ip_v, ip_pg = o.index_maps()
+    S = g.base_mva
+    ref = int(np.flatnonzero(g.bus_type == 0)[0])
+    pv = np.flatnonzero(ip_pg >= 0)
+    ng = int((ip_v >= 0).sum())
+    expect = np.zeros((o.n_p, o.n_p))
+    expect[ng:, ng:] = 2 * g.c2[ref] * S * S
+    expect[ip_pg[pv], ip_pg[pv]] += 2 * g.c2[pv] * S * S
+    assert abs(H - expect).max() <= 1e-9 * abs(expect).max()
+
+
 def test_bus_relabelling_permutes_the_hessian():
     g = gg.make_case("case118")
     o = OracleGrid(g)
@@ -362,9 +380,12 @@ def brute_min_degree(g):
     return order
 
 
-def order_cost(g, order, n_dirs, level_cost=1_700_000):
+def order_cost(g, order, n_dirs, level_cost=None):
     """Factor entries outside the bus blocks (w_k times the weight of the neighbours bus
-    k has when eliminated) times n_dirs, plus level_cost per forward level."""
+    k has when eliminated) times n_dirs, plus level_cost (default: the grid record's
+    order_level_cost) per forward level."""
+    if level_cost is None:
+        level_cost = g.order_level_cost
     alive, adj = _bus_graph(g)
     w = {i: 2 if g.bus_type[i] == 2 else 1 for i in alive}
     lev = {i: 0 for i in alive}
@@ -392,6 +413,16 @@ def test_both_candidate_orders_against_brute_force(shape):
     o = OracleGrid(g)
     assert list(o.order("degree")) == brute_min_degree(g)
     assert list(o.order("fill")) == brute_min_weighted_fill(g)
+    assert list(o.order("static")) == brute_static_order(g, o.n_p)
+
+
+@pytest.mark.parametrize("level_cost", [0, 10**12])
+def test_static_order_follows_the_level_cost_parameter(level_cost):
+    """The level weight is a parameter of the grid record: 0 keeps the order with fewer
+    entries, a huge weight the one with fewer levels, each as the brute force says."""
+    import dataclasses
+    g = dataclasses.replace(tiny(118, 186, 54, 20220100), order_level_cost=level_cost)
+    o = OracleGrid(g)
     assert list(o.order("static")) == brute_static_order(g, o.n_p)
 
 

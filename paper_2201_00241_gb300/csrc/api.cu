@@ -66,6 +66,11 @@ struct rh_grid {
     int *ef_ptr = nullptr, *ef_maxext = nullptr;
     int4 *sf_slot = nullptr, *sb_slot = nullptr, *ef_slot = nullptr;
     int n_sf = 0, n_sb = 0, n_ef = 0;
+    // backward schedule of the buses whose psi rows SpMulAdd reads (rows of J_p and
+    // their ancestors): the L^T sweep of a launch that ends in SpMulAdd
+    int *sbr_ptr = nullptr, *sbr_maxext = nullptr;
+    int4* sbr_slot = nullptr;
+    int n_sbr = 0;
     int* tail_pos = nullptr;
     int *qtheta = nullptr, *bparent = nullptr;
     int *jp_rows = nullptr, *jp_zero_rows = nullptr;
@@ -187,6 +192,7 @@ struct rh_grid {
         g.lb = {S.n_blev, blev_ptr, bslot, blev_maxext};
         g.sf = {n_sf, sf_ptr, sf_slot, sf_maxext};
         g.sb = {n_sb, sb_ptr, sb_slot, sb_maxext};
+        g.sbr = {n_sbr, sbr_ptr, sbr_slot, sbr_maxext};
         g.ef = {n_ef, ef_ptr, ef_slot, ef_maxext};
         g.t0 = S.t0; g.T = S.n_x - S.t0;
         g.triL = triL; g.triU = triU; g.triUt = triUt; g.triLt = triLt;
@@ -510,12 +516,13 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
         RH_CUDA(g->upload(g->bslot, bs));
         // schedules restricted to the sparse part (buses before the dense tail)
         auto restrict_set = [&](const std::vector<int>& order, const std::vector<int>& lev, const std::vector<int4>& src,
-                                std::vector<int>& ptr, std::vector<int4>& sl, std::vector<int>& mx) {
+                                std::vector<int>& ptr, std::vector<int4>& sl, std::vector<int>& mx,
+                                const std::vector<char>* keep = nullptr) {
             ptr.assign(1, 0);
             int cur = -1;
             for (int t = 0; t < S.n_elim; t++) {
                 int k = order[t];
-                if (k >= S.tail_bus0) continue;
+                if (k >= S.tail_bus0 || (keep && !(*keep)[k])) continue;
                 if (lev[k] != cur) {
                     if (cur >= 0) ptr.push_back((int)sl.size());
                     cur = lev[k];
@@ -532,6 +539,25 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
         restrict_set(S.blev_bus, S.blevel, bs, sbp, sbs, sbm);
         g->n_sf = (int)sfp.size() - 1;
         g->n_sb = (int)sbp.size() - 1;
+        // HW = Y_p + J_p^T psi reads psi only at the rows of J_p, and the L^T sweep
+        // computes a row from the rows of its ancestors: the other buses' rows of that
+        // last sweep are never read
+        {
+            std::vector<char> need(S.n_elim, 0);
+            for (int k = 0; k < S.n_elim; k++)
+                for (int t = 0; t < S.nv[k]; t++)
+                    if (S.jp_ptr[S.q0[k] + t + 1] > S.jp_ptr[S.q0[k] + t]) need[k] = 1;
+            for (int k = 0; k < S.n_elim; k++)      // ancestors come later: one ascending pass closes the set
+                if (need[k])
+                    for (int c : S.colpat[k]) need[c] = 1;
+            std::vector<int> rp, rm;
+            std::vector<int4> rs;
+            restrict_set(S.blev_bus, S.blevel, bs, rp, rs, rm, &need);
+            g->n_sbr = (int)rp.size() - 1;
+            RH_CUDA(g->upload(g->sbr_ptr, rp));
+            RH_CUDA(g->upload(g->sbr_slot, rs));
+            RH_CUDA(g->upload(g->sbr_maxext, rm));
+        }
         // the tail's external phase: one level of tail buses, columns left of t0 only
         std::vector<int> efp(1, 0), efm;
         std::vector<int4> efs;

@@ -1196,8 +1196,9 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
             tail_fwd<false>(g, g.triUtd, T, ld, 0, D, part, nullptr);
         }
         if (L.phases & PH_LT) {
+            // psi is only read by SpMulAdd here: rows outside J_p and its ancestors are skipped
             tail_bwd<false>(g, g.triLtd, T, ld, 0, D, part, nullptr);
-            sweep_bwd<false>(g, g.sb, g.Atd, T, ld, 0, D, part);
+            sweep_bwd<false>(g, (L.phases & PH_MULADD) ? g.sbr : g.sb, g.Atd, T, ld, 0, D, part);
         }
     } else {
         if (L.phases & PH_UT) sweep_fwd<false>(g, g.lf, g.Atd, T, ld, 0, D, part);

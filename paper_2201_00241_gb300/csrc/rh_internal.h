@@ -38,7 +38,7 @@ struct Symbolic {
     // bus-level patterns and schedules
     std::vector<std::vector<int>> colpat;   // position -> later positions (U side)
     std::vector<std::vector<int>> rowpat;   // position -> earlier positions (L side)
-    std::vector<int> flevel, blevel;        // forward / backward level per position
+    std::vector<int> flevel, blevel;        // forward level (height) / backward level (max height - height)
     int n_flev = 0, n_blev = 0;
     std::vector<int> flev_ptr, flev_bus;    // positions grouped by forward level
     std::vector<int> blev_ptr, blev_bus;    // positions grouped by backward level

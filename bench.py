@@ -11,8 +11,10 @@ larger than L2 and L2 is also flushed between timed steps.
 e2e: the same metric through the C ABI with host buffers: parameters, loads and
 the operating point copied in, the full H (66.8 MB) copied out, every step.
 
---impl reference times the CPU oracle (oracle/, plain C, one thread) on a
-bounded sample of the same workload.
+--impl reference times the CPU oracle (oracle/, plain C, the columns of W shared
+out over the host cores) on the same workload.
+
+--fp64-peak only measures the device's FP64 FMA rate by CTAs and warps per SM.
 """
 from __future__ import annotations
 
@@ -32,7 +34,11 @@ sys.path.insert(0, ROOT)
 
 CASE = "case9241"
 BLOCK_N = 256
-PEAK_FP64_GFLOPS = 152 * 4 * 0.5 * 2 * 2.070  # SMs x sub-partitions x lane-FMA/clk x 2 x GHz (max SM clock)
+# FP64 roofline of GB300, derived from unit counts at the maximum SM clock: 152 SMs x 4
+# sub-partitions x 0.5 lane-FMA per clock x 2 flop x 2.070 GHz = 1258.6 GFLOP/s.  The FMA-chain
+# measurement behind the 0.5 lane-FMA per clock per sub-partition (python bench.py --fp64-peak)
+# is summarised in profiles/fp64_fma_rate.md; every run also reports the rate it measures.
+PEAK_FP64_GFLOPS = 152 * 4 * 0.5 * 2 * 2.070
 
 
 def parse():
@@ -46,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 118-bus latency, scenario batching, plain-path and serving measurements")
+    ap.add_argument("--fp64-peak", action="store_true",
+                    help="only measure the FP64 FMA rate by CTAs and warps per SM and print the table")
     return ap.parse_args()
 
 
@@ -91,16 +99,6 @@ def measured_traffic():
     return None
 
 
-def algorithmic_flops_per_direction(dm, n_inc, n_gref):
-    """FP64 flops one direction of Algorithm 2 needs (FMA = 2)."""
-    nx = dm.n_x
-    spmul = 2 * dm.nnz_jp
-    l_sweep = 2 * dm.nnz_l
-    u_sweep = 2 * (dm.nnz_u - nx)      # unit-diagonal U' = D^-1 U: the pivots fold into J_p's rows
-    proj = 8 * n_inc + 8 * dm.n_bus + 4 * n_gref + dm.n_pv
-    return spmul + 2 * (l_sweep + u_sweep) + proj + spmul
-
-
 def start_clock_sampler(path):
     try:
         return subprocess.Popen(
@@ -135,10 +133,34 @@ def read_clocks(path, dev):
     return out
 
 
+def host_cpu():
+    """Model name of the host cores (lscpu, else /proc/cpuinfo) and the cores this process may use."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                name = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not name:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith("model name"):
+                    name = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return name or "unknown", int(cores or 1)
+
+
 def cpu_baseline(case):
-    """The oracle as it stands (single-threaded C), timed on the whole workload of one
-    step: all n_p unit directions of the full reduced Hessian, with its own per-state
-    LU and adjoint (a few seconds of CPU work)."""
+    """The oracle as it stands (plain C), timed on the whole workload of one step: all n_p
+    unit directions of the full reduced Hessian, with its own per-state LU and adjoint.
+    Once on one thread (like the paper's sequential CPU reference) and once with the
+    columns shared out over every core the process may use (a few seconds each)."""
     from oracle import OracleGrid
     from paper_2201_00241_gb300 import gridgen as gg
 
@@ -146,12 +168,17 @@ def cpu_baseline(case):
     o = OracleGrid(g)
     st = o.plant()
     W = np.eye(o.n_p)
+    model, cores = host_cpu()
     t0 = time.perf_counter()
     o.hessvec(st.x, st.p, st.pd, st.qd, W)
-    dt = time.perf_counter() - t0
-    return dict(value=o.n_p / dt, unit="HVP/s", cores=1, kind="oracle",
+    dt1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.hessvec(st.x, st.p, st.pd, st.qd, W, threads=cores)
+    dtn = time.perf_counter() - t0
+    return dict(value=o.n_p / dtn, unit="HVP/s", cores=cores, kind="oracle", host_cpu=model, nproc=os.cpu_count(),
+                single_thread_value=o.n_p / dt1,
                 sample=f"the whole step: all {o.n_p} unit directions of H on {case} (incl. the oracle's own LU and "
-                       f"adjoint), {dt:.1f} s")
+                       f"adjoint): {dtn:.2f} s on {cores} threads (columns shared out), {dt1:.1f} s on one")
 
 
 def _ready(case, scale_k=None):
@@ -352,6 +379,22 @@ def measure_separate_calls(lg, H, sptr, reps=5):
     return {"step_ms": step, "setup_ms": setup, "hessian_ms": dirs, "hvp_per_s": n_p / (step * 1e-3)}
 
 
+def measure_per_block(lg, H, sptr, reps=5):
+    """The full Hessian in the metric's blocks of N = 256 columns, one launch per block (the
+    plain block-by-block form of section 5.3), HVP only, state resident."""
+    from paper_2201_00241_gb300 import rh
+    lib = rh.load()
+    rh._check(lib.rh_adjoint(lg._h, None, None, None))
+
+    def blocks():
+        rh._check(lib.rh_hessian(lg._h, BLOCK_N, rh._ptr(H), lg.n_p, sptr, rh.RH_DEVICE_PTRS))
+
+    blocks()
+    t = _event_ms(blocks, reps)
+    return {"hvp_per_s": lg.n_p / (t * 1e-3), "ms": t, "blocks": -(-lg.n_p // BLOCK_N),
+            "note": "HVP only (state resident): rh_hessian, one k_dirs launch per block of 256 columns"}
+
+
 def measure_plain_paths(lg, n_single=32, reps=3):
     """The plain one-direction-at-a-time path and the one-launch-per-block full Hessian."""
     import torch
@@ -440,8 +483,10 @@ def measure_serving(factors=(0.25, 0.5, 1.0, 2.0, 4.0), n_req=120, seed=4):
 
 
 def workload_config(case, n_x, n_p, nnz_l, nnz_u, world):
-    return {"workload": f"{case}: full reduced Hessian ({n_p} HVPs) per step, W = I in blocks of "
-                        f"N={BLOCK_N} issued together, per-state setup (Jacobian, refactor, adjoint) included",
+    return {"workload": f"{case}: full reduced Hessian ({n_p} HVPs) per step, W = I, all {n_p} directions "
+                        f"in flight in one pair of direction launches (at most 10 per CTA), per-state setup "
+                        f"(Jacobian, refactor, adjoint) included; the metric's blocks of N={BLOCK_N}, one "
+                        f"launch each, are reported beside it (per_block_n256)",
             "n_x": n_x, "n_p": n_p, "block_n": BLOCK_N, "nnz_l": nnz_l, "nnz_u": nnz_u,
             "l2": "flushed between steps; workspace > L2", "parallelism": "replicas" if world > 1 else "1 GPU"}
 
@@ -459,12 +504,13 @@ def run_reference(args, rank, world):
     st = o.plant()
     per = o.n_p
     W = np.eye(o.n_p)
+    model, cores = host_cpu()
     for _ in range(args.warmup):
-        o.hessvec(st.x, st.p, st.pd, st.qd, W)
+        o.hessvec(st.x, st.p, st.pd, st.qd, W, threads=cores)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        o.hessvec(st.x, st.p, st.pd, st.qd, W)
+        o.hessvec(st.x, st.p, st.pd, st.qd, W, threads=cores)
         times.append(time.perf_counter() - t0)
     value = per * len(times) / sum(times)
     sym = o.symbolic()
@@ -473,11 +519,28 @@ def run_reference(args, rank, world):
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args.case, o.n_x, o.n_p, len(sym["Lj"]), len(sym["Uj"]), 1),
-            "cpu_baseline": {"value": value, "unit": "HVP/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "HVP/s", "cores": cores, "kind": "oracle", "host_cpu": model,
+                             "nproc": os.cpu_count(),
                              "sample": f"each step: all {per} unit directions of the full Hessian, "
-                                       "with the oracle's own LU and adjoint; single thread"},
+                                       f"with the oracle's own LU and adjoint; columns shared out over {cores} "
+                                       "threads"},
             "e2e": {"value": value, "unit": "HVP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def fp64_peak_table(device):
+    """FP64 FMA rate (8 independent chains per thread) by CTAs and threads per SM."""
+    from paper_2201_00241_gb300 import rh
+    rows = []
+    for ctas, threads in [(1, 128), (1, 256), (2, 128), (1, 384), (2, 256), (1, 768), (2, 384), (3, 384),
+                          (2, 512), (4, 384), (2, 1024)]:
+        best = 0.0
+        for _ in range(3):
+            gf, ms = rh.fp64_fma_rate(device, ctas, threads, 1 << 16)
+            best = max(best, gf)
+        rows.append({"ctas_per_sm": ctas, "threads_per_cta": threads, "warps_per_sm": ctas * threads // 32,
+                     "gflops": best})
+    return rows
 
 
 def main():
@@ -487,6 +550,18 @@ def main():
         run_reference(args, rank, world)
         return
     import torch
+    if args.fp64_peak:
+        torch.cuda.set_device(local)
+        clk_path = os.path.join(tempfile.gettempdir(), f"rh_peak_clocks_{os.getpid()}.csv")
+        sampler = start_clock_sampler(clk_path)
+        time.sleep(1.0)
+        rows = fp64_peak_table(local)
+        if sampler:
+            sampler.terminate()
+            sampler.wait()
+        print(json.dumps({"fp64_fma_rate": rows, "derived_peak_gflops": PEAK_FP64_GFLOPS,
+                          "clocks": read_clocks(clk_path, local)}), flush=True)
+        return
 
     if world > 1:
         import torch.distributed as dist
@@ -503,11 +578,11 @@ def main():
     dm = lg.dims
     n_p = lg.n_p
     lib = rh.load()
-    # incidences and slack-gradient entries, for the flop count
-    n_inc = 2 * int(np.count_nonzero(g.fr != g.to))
-    ref = int(np.flatnonzero(g.bus_type == 0)[0])
-    n_gref = 1 + 2 * int(np.count_nonzero(g.fr == ref) + np.count_nonzero(g.to == ref))
-    flops_dir = algorithmic_flops_per_direction(dm, n_inc, n_gref)
+    # FP64 flops of the two direction launches of a step, counted by the library from the
+    # symbolic data: Algorithm 2 for n_p dense directions, and what the kernels issue with W = I
+    flops_alg, flops_exec = lg.reduced_hessian_flops()
+    # the FP64 FMA rate of this device, in the direction kernel's shape (2 CTAs of 384 threads per SM)
+    peak_meas = max(rh.fp64_fma_rate(local, 2, 384, 1 << 14)[0] for _ in range(3))
 
     H = torch.empty((n_p, n_p), dtype=torch.float64, device=f"cuda:{local}").t()   # column-major
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
@@ -559,7 +634,10 @@ def main():
     t_step = max_over_ranks(sum(step_ms) / len(step_ms), world, f"cuda:{local}")
     value = replica_throughput(n_p, world, t_step * 1e-3)
     t_dirs = sum(dirs_ms) / len(dirs_ms)
-    achieved = flops_dir * n_p / (t_dirs * 1e-3) * 1e-9
+    achieved = flops_alg / (t_dirs * 1e-3) * 1e-9
+    achieved_exec = flops_exec / (t_dirs * 1e-3) * 1e-9
+    # the plain form of the metric's N = 256 blocks: one launch per block of 256 columns
+    per_block = measure_per_block(lg, H, sptr)
 
     # e2e through the C ABI with host buffers
     Hh = np.empty((n_p, n_p), order="F")
@@ -586,15 +664,26 @@ def main():
         "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": workload_config(args.case, lg.n_x, n_p, dm.nnz_l, dm.nnz_u, world),
+        "per_block_n256": per_block,
         "roofline": {"bound": "alu", "kernel": "k_dirs (two launches per step: SpMul + L + U sweeps, then "
-                                                 "projection + U^T + L^T sweeps + SpMulAdd)", "achieved": achieved, "peak": PEAK_FP64_GFLOPS,
+                                                 "projection + U^T + L^T sweeps + SpMulAdd)",
+                     "achieved": achieved, "peak": PEAK_FP64_GFLOPS,
                      "unit": "GFLOP/s", "frac": achieved / PEAK_FP64_GFLOPS,
                      "traffic": measured_traffic() if args.case == CASE else None,
-                     "kernel_ms": t_dirs, "flops_per_direction": flops_dir,
+                     "kernel_ms": t_dirs, "flops_per_direction": flops_alg / n_p,
+                     "achieved_executed": achieved_exec, "frac_executed": achieved_exec / PEAK_FP64_GFLOPS,
+                     "flops_executed_per_step": flops_exec, "flops_algorithmic_per_step": flops_alg,
+                     "peak_measured": peak_meas, "frac_of_measured_peak": achieved / peak_meas,
+                     "frac_executed_of_measured_peak": achieved_exec / peak_meas,
+                     "peak_note": "peak derived from unit counts at 2070 MHz (152 SMs x 4 sub-partitions x 0.5 "
+                                  "lane-FMA/clk x 2); peak_measured: FMA chains in 2 x 384 threads per SM, "
+                                  "this run",
                      "first_launch_end_ms": float(np.mean([p[0] for p in phase_ms])),
                      "adjoint_branch_end_ms": float(np.mean([p[1] for p in phase_ms])),
-                     "note": "flops counted for a dense W; with W = I the forward L sweep skips buses outside "
-                             "the reach of B's nonzeros (exact zeros), so frac overstates FP64 use by that share"},
+                     "note": "frac: Algorithm 2's flops for n_p dense directions (rh_reduced_hessian_flops); "
+                             "frac_executed: the flops the launches issue with W = I (forward L sweep over each "
+                             "CTA's reach, last L^T sweep over the rows SpMulAdd reads, no multiplications in "
+                             "SpMul)"},
         "e2e": {"value": e2e_value, "unit": "HVP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step,
         "clocks": clocks,

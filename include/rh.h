@@ -245,6 +245,38 @@ rh_status rh_reduced_hessian(rh_grid *grid, double *H, int64_t ldh, double *F, d
 rh_status rh_reduced_hessian_times(const rh_grid *grid, float *ms);
 
 /*
+ * FP64 work of the two direction launches of one rh_reduced_hessian call (all
+ * n_p directions of Algorithm 2 with W = I), counted on the host from the
+ * symbolic data; flops, an FMA counting 2.
+ *   algorithmic  what Algorithm 2 needs for n_p dense directions on the
+ *                unit-diagonal factors: SpMul and SpMulAdd (2 nnz(J_p) each),
+ *                the four sweeps (2 nnz(L), 2 (nnz(U) - n_x) each) and the
+ *                projection (eq. 13: 8 per incidence and per bus, 4 per
+ *                slack-gradient entry, 1 per Pg row)
+ *   executed     what the kernels issue for those launches: the forward L
+ *                sweep over each CTA's reach only (the rows W = I can make
+ *                nonzero for that CTA's directions), the last L^T sweep over
+ *                the rows SpMulAdd reads, no multiplications in SpMul (it
+ *                scatters columns of J_p), the dense tail as a full triangle
+ *   n_sm         SMs of the device (it fixes the CTA split); 0 takes the grid's
+ *                device, required > 0 on a symbolic-only grid.
+ * Host only, no device work.
+ */
+rh_status rh_reduced_hessian_flops(const rh_grid *grid, int32_t n_sm, double *algorithmic, double *executed);
+
+/*
+ * Measurement utility (not part of the paper's method): the FP64 FMA rate of
+ * `device`, the roofline the direction kernel is bound by.  Runs
+ * ctas_per_sm x (SM count) CTAs of threads_per_cta threads (a multiple of 32,
+ * at most 1024), each thread 8 independent FMA chains of `iters` steps, and
+ * returns the rate in GFLOP/s (an FMA counting 2) and the time in ms (ms may be
+ * NULL).  Synchronous; allocates and frees a small device buffer.  Returns
+ * RH_EINVAL for bad arguments (rh_last_error is not set by this call).
+ */
+rh_status rh_fp64_fma_rate(int32_t device, int32_t ctas_per_sm, int32_t threads_per_cta, int64_t iters,
+                           double *gflops, float *ms);
+
+/*
  * Solve J_x X = R (trans = 0) or J_x^T X = R (trans = 1) with the current
  * device factors (after rh_adjoint or rh_refactor), in place.  R is n_x x nrhs,
  * column-major, leading dimension ldr >= n_x, indexed like x.  These are the

@@ -55,6 +55,7 @@ def _load():
     lib.orc_adjoint.argtypes = [P, P, P, P, P, P, P, P]
     lib.orc_lagrangian_hessian_dense.argtypes = [P, P, P, P, P, P]
     lib.orc_hessvec.argtypes = [P, P, P, P, P, P, I, I, P, I]
+    lib.orc_hessvec_threads.argtypes = [P, P, P, P, P, P, I, I, P, I, I]
     lib.orc_symbolic.argtypes = [P] + [P] * 7 + [P, P, P]
     lib.orc_order.argtypes = [P, C.c_int, P]
     lib.orc_order.restype = C.c_int
@@ -177,7 +178,9 @@ class OracleGrid:
         _lib.orc_lagrangian_hessian_dense(self._h, _p(x), _p(p), _p(pd), _p(lam), _p(out))
         return out
 
-    def hessvec(self, x, p, pd, qd, W):
+    def hessvec(self, x, p, pd, qd, W, threads=1):
+        """HW, one column of W at a time (Algorithm 1); threads > 1 shares the columns out
+        among that many threads (the same arithmetic per column)."""
         x, p, pd, qd = map(_f64, (x, p, pd, qd))
         W = np.asfortranarray(W, dtype=np.float64)
         if W.ndim == 1:
@@ -185,7 +188,8 @@ class OracleGrid:
         assert W.shape[0] == self.n_p
         N = W.shape[1]
         HW = np.empty((self.n_p, N), order="F")
-        st = _lib.orc_hessvec(self._h, _p(x), _p(p), _p(pd), _p(qd), _p(W), self.n_p, N, _p(HW), self.n_p)
+        st = _lib.orc_hessvec_threads(self._h, _p(x), _p(p), _p(pd), _p(qd), _p(W), self.n_p, N, _p(HW), self.n_p,
+                                      int(threads))
         if st != 0:
             raise RuntimeError("oracle LU: singular pivot")
         return HW

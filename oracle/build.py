@@ -13,7 +13,7 @@ SRC = os.path.join(HERE, "rh_oracle.c")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liborc.so")
 
-CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-Wall", "-Wno-unused-function"]
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread", "-Wall", "-Wno-unused-function"]
 
 
 def build(force: bool = False) -> str:
@@ -22,7 +22,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", *CFLAGS, "-o", tmp, SRC, "-lm"], check=True)
+    subprocess.run(["gcc", *CFLAGS, "-o", tmp, SRC, "-lm", "-lpthread"], check=True)
     os.replace(tmp, LIB)
     return LIB
 

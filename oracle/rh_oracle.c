@@ -5,7 +5,9 @@
  * TEST INFRASTRUCTURE ONLY.  The test-suite, the smoke check and the CPU
  * baseline leg of the benchmark call it; the CUDA library never does, and the
  * two share no code.  Everything here is IEEE fp64, compiled with
- * -ffp-contract=off, single-threaded, written for readability over speed.
+ * -ffp-contract=off, written for readability over speed; single-threaded,
+ * except that orc_hessvec_threads may share the independent columns of W out
+ * among threads (each column's arithmetic is the same either way).
  *
  * What it computes (paper sections and equations):
  *   - power injections, eq. (2), including the diagonal admittance term;
@@ -33,6 +35,7 @@
  *     real-time tracking step (section 6.3, eq. 18-19).
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -977,37 +980,82 @@ void orc_lagrangian_hessian_dense(const orc_grid *g, const double *x, const doub
  * W: n_p x N column-major (ldw >= n_p), HW: n_p x N column-major (ldh >= n_p).
  * For each column w:  b = J_p w;  z = -J_x^{-1} b;  y = [Hess l](z, w);
  * psi = -J_x^{-T} y_x;  Hw = y_p + J_p^T psi.
+ * The per-state data (adjoint, LU, J_p, the Lagrangian Hessian) is formed once;
+ * every column then runs the same steps on its own work vectors, so the
+ * columns may be shared out among threads without changing any result.
  * Returns the LU status (0 ok, -1 singular pivot).
  */
-int orc_hessvec(const orc_grid *g, const double *x, const double *p, const double *pd, const double *qd,
-                const double *W, int ldw, int N, double *HW, int ldh) {
-    int nx = g->n_x, np = g->n_p, nu = nx + np;
+typedef struct {
+    const orc_grid *g;
+    const orc_lu *LU;
+    const csc *Jp, *H;
+    const double *W;
+    int ldw, N, ldh, n_threads, t;
+    double *HW;
+} hv_job;
+
+static void hessvec_column(const hv_job *j, int c, double *v, double *y) {
+    int nx = j->g->n_x, np = j->g->n_p, nu = nx + np;
+    const double *w = j->W + (size_t)c * j->ldw;
+    memset(v, 0, sizeof(double) * nu);
+    csc_gemv(j->Jp, w, v);                     /* b = J_p w       */
+    lu_solve(j->LU, v);                        /* J_x^{-1} b      */
+    for (int k = 0; k < nx; k++) v[k] = -v[k]; /* z               */
+    memcpy(v + nx, w, sizeof(double) * np);    /* v = (z, w)      */
+    memset(y, 0, sizeof(double) * nu);
+    csc_gemv(j->H, v, y);                      /* y = [Hess l] v  */
+    for (int k = 0; k < nx; k++) y[k] = -y[k];
+    lu_solve_t(j->LU, y);                      /* psi = -J^{-T} y_x */
+    double *out = j->HW + (size_t)c * j->ldh;
+    memcpy(out, y + nx, sizeof(double) * np);  /* y_p             */
+    csc_gemv_t(j->Jp, y, out);                 /* + J_p^T psi     */
+}
+
+static void *hessvec_worker(void *arg) {
+    const hv_job *j = arg;
+    int nu = j->g->n_x + j->g->n_p;
+    double *v = xcalloc(nu, sizeof(double)), *y = xcalloc(nu, sizeof(double));
+    for (int c = j->t; c < j->N; c += j->n_threads) hessvec_column(j, c, v, y);
+    free(v); free(y);
+    return NULL;
+}
+
+/* n_threads <= 1: one thread, columns in order; else thread t takes the columns
+ * t, t + n_threads, ...  */
+int orc_hessvec_threads(const orc_grid *g, const double *x, const double *p, const double *pd, const double *qd,
+                        const double *W, int ldw, int N, double *HW, int ldh, int n_threads) {
+    int nx = g->n_x, np = g->n_p;
     orc_state s; state_alloc(g, &s); state_from(g, x, p, &s);
     double *lambda = xcalloc(nx, sizeof(double)), *grad = xcalloc(np, sizeof(double)), F;
     int st = orc_adjoint(g, x, p, pd, qd, lambda, grad, &F);
     orc_lu LU; csc Jp;
     st |= factor_at(g, &s, &LU, &Jp);
     csc H = lagrangian_hessian(g, &s, pd, lambda);
-    double *v = xcalloc(nu, sizeof(double)), *y = xcalloc(nu, sizeof(double));
-    for (int c = 0; c < N; c++) {
-        const double *w = W + (size_t)c * ldw;
-        memset(v, 0, sizeof(double) * nu);
-        csc_gemv(&Jp, w, v);                       /* b = J_p w       */
-        lu_solve(&LU, v);                          /* J_x^{-1} b      */
-        for (int k = 0; k < nx; k++) v[k] = -v[k]; /* z               */
-        memcpy(v + nx, w, sizeof(double) * np);    /* v = (z, w)      */
-        memset(y, 0, sizeof(double) * nu);
-        csc_gemv(&H, v, y);                        /* y = [Hess l] v  */
-        for (int k = 0; k < nx; k++) y[k] = -y[k];
-        lu_solve_t(&LU, y);                        /* psi = -J^{-T} y_x */
-        double *out = HW + (size_t)c * ldh;
-        memcpy(out, y + nx, sizeof(double) * np);  /* y_p             */
-        csc_gemv_t(&Jp, y, out);                   /* + J_p^T psi     */
+    if (n_threads > N) n_threads = N;
+    if (n_threads < 1) n_threads = 1;
+    hv_job *jobs = xcalloc(n_threads, sizeof(hv_job));
+    pthread_t *tid = xcalloc(n_threads, sizeof(pthread_t));
+    for (int t = 0; t < n_threads; t++) {
+        hv_job j = {g, &LU, &Jp, &H, W, ldw, N, ldh, n_threads, t, HW};
+        jobs[t] = j;
     }
-    free(v); free(y);
+    int started = 1;
+    for (int t = 1; t < n_threads; t++) {
+        if (pthread_create(&tid[t], NULL, hessvec_worker, &jobs[t]) != 0) break;
+        started++;
+    }
+    for (int t = started; t < n_threads; t++) hessvec_worker(&jobs[t]);   /* threads that did not start */
+    hessvec_worker(&jobs[0]);
+    for (int t = 1; t < started; t++) pthread_join(tid[t], NULL);
+    free(jobs); free(tid);
     csc_free(&H); csc_free(&Jp); lu_free(&LU);
     free(lambda); free(grad); state_free(&s);
     return st;
+}
+
+int orc_hessvec(const orc_grid *g, const double *x, const double *p, const double *pd, const double *qd,
+                const double *W, int ldw, int N, double *HW, int ldh) {
+    return orc_hessvec_threads(g, x, p, pd, qd, W, ldw, N, HW, ldh, 1);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -16,7 +16,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librh.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-CU = ["kernels.cu", "dense.cu", "api.cu"]
+CU = ["kernels.cu", "dense.cu", "api.cu", "peak.cu"]
 CPP = ["symbolic.cpp"]
 HEADERS = ["rh_internal.h", "rh_kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1014,6 +1014,101 @@ rh_status rh_reduced_hessian_times(const rh_grid* g, float* ms) {
     return RH_OK;
 }
 
+rh_status rh_reduced_hessian_flops(const rh_grid* g, int32_t n_sm, double* algorithmic, double* executed) {
+    if (!g || !algorithmic || !executed) return fail(RH_EINVAL, "NULL argument");
+    const auto& S = g->S;
+    if (n_sm <= 0) {
+        if (g->device < 0) return fail(RH_EINVAL, "n_sm must be given for a symbolic-only grid");
+        RH_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, g->device));
+    }
+    const int np = S.n_p, T = S.n_x - S.t0;
+    // incidences (off-diagonal admittance entries) and the slack-gradient entries
+    int64_t n_inc = 0;
+    for (int i = 0; i < S.n_bus; i++) n_inc += S.yp[i + 1] - S.yp[i] - 1;
+    const int deg_ref = S.yp[S.ref + 1] - S.yp[S.ref] - 1;
+    const int n_gref = 1 + 2 * deg_ref;
+    // the CTA counts of the two direction launches (as rh_reduced_hessian launches them)
+    const int slots = rh::dirs_cta_slots_for(n_sm);
+    const int per = (np + slots - 2) / std::max(1, slots - 1);
+    const int n_cta2 = rh::dirs_ctas_for(np, slots);
+    const int n_cta1 = std::min(n_cta2, std::max(1, (np + std::max(1, per) - 1) / std::max(1, per)));
+    const bool tailed = rh::dirs_tail_fits(T, np, n_cta1) && rh::dirs_tail_fits(T, np, n_cta2);
+    // FMAs of bus block k in a forward / backward sweep: both rows' parts outside the
+    // bus, plus the (v, theta) entry of a PQ bus
+    auto fwd_fma = [&](int k) {
+        const int q = S.q0[k];
+        return (int64_t)S.nv[k] * (S.diagpos[q] - S.rowptr[q]) + (S.nv[k] == 2 ? 1 : 0);
+    };
+    auto bwd_fma = [&](int k) {
+        const int q = S.q0[k];
+        return (int64_t)S.nv[k] * (S.rowptr[q + 1] - S.diagpos[q] - S.nv[k]) + (S.nv[k] == 2 ? 1 : 0);
+    };
+    const int sparse_end = tailed ? S.tail_bus0 : S.n_elim;
+    int64_t ext = 0, tail = 0;   // the tail rows' part left of the tail (its external phase); one dense tail solve
+    if (tailed) {
+        for (int k = S.tail_bus0; k < S.n_elim; k++) {
+            const int q = S.q0[k];
+            int n = 0;
+            for (int t = S.rowptr[q]; t < S.diagpos[q] && S.col[t] < S.t0; t++) n++;
+            ext += (int64_t)S.nv[k] * n;
+        }
+        tail = (int64_t)T * (T - 1) / 2;
+    }
+    std::vector<char> need(S.n_elim, 0);     // buses whose psi rows SpMulAdd reads, and their ancestors
+    for (int k = 0; k < S.n_elim; k++)
+        for (int t = 0; t < S.nv[k]; t++)
+            if (S.jp_ptr[S.q0[k] + t + 1] > S.jp_ptr[S.q0[k] + t]) need[k] = 1;
+    for (int k = 0; k < S.n_elim; k++)
+        if (need[k])
+            for (int c : S.colpat[k]) need[c] = 1;
+    int64_t l_all = 0, u_all = 0, ut = 0, lt = 0, fold = 0;
+    const bool fold_ut = tailed && S.tail_bus0 > 0;
+    for (int k = 0; k < sparse_end; k++) {
+        l_all += fwd_fma(k);
+        u_all += bwd_fma(k);
+        if (fold_ut && S.flevel[k] == 0) fold += S.nv[k] == 2 ? 1 : 0;   // done by the projection
+        else ut += fwd_fma(k);
+        if (!tailed || need[k]) lt += bwd_fma(k);
+    }
+    // the projection, per direction: 3 + 3 flops per bus, 8 per incidence, 4 per bus next to the
+    // slack, 2 n_gref + 1 for the slack term, 1 per Pg row, 2 per PQ bus of level 0 (the folded
+    // first level of the U'^T sweep)
+    const double proj = 6.0 * S.n_bus + 8.0 * n_inc + 4.0 * (1 + deg_ref) + 2.0 * n_gref + 1.0 + S.n_pv + 2.0 * fold;
+    const double nnz_jp = (double)S.jp_col.size();
+    const double l2 = proj + 2.0 * (ut + ext + 2 * tail + lt) + 2.0 * nnz_jp;
+    // launch 1 (identity W): the L sweep over each CTA's reach, the buses of its J_p columns and
+    // their ancestors in the sparse part (all buses without the dense tail), then the tail's
+    // external phase, the two tail solves and the U sweep
+    double l1 = 0.0;
+    std::vector<int> bpos(S.n_x);
+    for (int k = 0; k < S.n_elim; k++)
+        for (int t = 0; t < S.nv[k]; t++) bpos[S.q0[k] + t] = k;
+    std::vector<char> in(S.n_elim);
+    for (int c = 0; c < n_cta1 && np > 0; c++) {
+        const int c0 = (int)((int64_t)c * np / n_cta1), c1 = (int)((int64_t)(c + 1) * np / n_cta1);
+        int64_t l = l_all;
+        if (tailed) {
+            std::fill(in.begin(), in.end(), 0);
+            for (int j = c0; j < c1; j++)
+                for (int t = S.jpt_ptr[j]; t < S.jpt_ptr[j + 1]; t++) in[bpos[S.jpt_row[t]]] = 1;
+            l = 0;
+            for (int k = 0; k < S.tail_bus0; k++) {
+                if (!in[k]) continue;
+                l += fwd_fma(k);
+                if (!S.colpat[k].empty() && S.colpat[k][0] < S.tail_bus0) in[S.colpat[k][0]] = 1;
+            }
+        }
+        l1 += (double)(c1 - c0) * 2.0 * (l + ext + 2 * tail + u_all);
+    }
+    *executed = l1 + np * l2;
+    // Algorithm 2 for a dense W on the unit-diagonal factors, per direction: SpMul and
+    // SpMulAdd (2 nnz(J_p) each), four sweeps (2 nnz(L) and 2 (nnz(U) - n_x) each), the
+    // projection (8 per incidence and per bus, 4 per slack-gradient entry, 1 per Pg row)
+    const double sweeps = 2.0 * (2.0 * S.nnz_l + 2.0 * (S.nnz_u - S.n_x));
+    *algorithmic = (double)np * (4.0 * nnz_jp + sweeps + 8.0 * n_inc + 8.0 * S.n_bus + 4.0 * n_gref + S.n_pv);
+    return RH_OK;
+}
+
 rh_status rh_hessvec(rh_grid* g, const double* W, int64_t ldw, int32_t N, double* HW, int64_t ldhw, void* stream,
                      uint32_t flags) {
     if (!g) return fail(RH_EINVAL, "NULL grid");

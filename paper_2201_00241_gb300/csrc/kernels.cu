@@ -1728,13 +1728,16 @@ static int num_sms() {
     return n_sm;
 }
 
-int dirs_default_ctas(int N) {
-    const int slots = kDirCtasPerSm * num_sms();
+int dirs_cta_slots_for(int n_sm) { return kDirCtasPerSm * n_sm; }
+
+int dirs_ctas_for(int N, int slots) {
     int G = N < slots ? N : slots;
     int need = (N + kDMax - 1) / kDMax;
     if (G < need) G = need;
     return G < 1 ? 1 : G;
 }
+
+int dirs_default_ctas(int N) { return dirs_ctas_for(N, kDirCtasPerSm * num_sms()); }
 
 bool dirs_tail_fits(int T, int N, int n_cta) {
     if (T <= 1 || n_cta <= 0) return false;

@@ -194,6 +194,10 @@ cudaError_t launch_potrf(int n, double* A, int64_t lda, int* info, double* y, cu
 cudaError_t launch_potrs(int n, const double* L, int64_t ldl, double* B, int64_t ldb, int nrhs, double* work,
                          bool forward, cudaStream_t s);
 int dirs_default_ctas(int N);
+// CTA slots of the direction kernel on a device of n_sm SMs, and the CTAs a launch of
+// N directions takes there
+int dirs_cta_slots_for(int n_sm);
+int dirs_ctas_for(int N, int slots);
 // CTAs of k_dirs the device holds at once (CTAs per SM x SMs)
 int dirs_cta_slots();
 

@@ -24,7 +24,8 @@ EXPORTS = ["rh_grid_create", "rh_grid_destroy", "rh_grid_dims", "rh_grid_symboli
            "rh_set_state", "rh_powerflow", "rh_adjoint", "rh_hessvec", "rh_hessian", "rh_solve", "rh_refactor",
            "rh_lagrangian_hessvec", "rh_hessvec_noalloc", "rh_hv_work_doubles", "rh_batch_hessvec",
            "rh_potrf", "rh_potrs", "rh_rto_step", "rh_set_jacobian_method", "rh_grid_coloring", "rh_jacobian",
-           "rh_reduced_hessian", "rh_reduced_hessian_times", "rh_last_error"]
+           "rh_reduced_hessian", "rh_reduced_hessian_times", "rh_reduced_hessian_flops", "rh_fp64_fma_rate",
+           "rh_last_error"]
 RH_JAC_ANALYTIC, RH_JAC_COLORED_AD = 0, 1
 
 
@@ -98,6 +99,8 @@ def load(build_if_missing: bool = True):
         "rh_jacobian": ([P, I32, P, P, P, P, P, P], C.c_int),
         "rh_reduced_hessian": ([P, P, I64, P, P, P, U32], C.c_int),
         "rh_reduced_hessian_times": ([P, P], C.c_int),
+        "rh_reduced_hessian_flops": ([P, I32, P, P], C.c_int),
+        "rh_fp64_fma_rate": ([I32, I32, I32, I64, P, P], C.c_int),
         "rh_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -280,6 +283,13 @@ class Grid:
         _check(_lib.rh_reduced_hessian_times(self._h, ms))
         return tuple(float(v) for v in ms)
 
+    def reduced_hessian_flops(self, n_sm=0):
+        """(algorithmic, executed) FP64 flops of the direction launches of one reduced_hessian
+        call (rh_reduced_hessian_flops); n_sm = 0 takes the grid's device."""
+        a, e = C.c_double(0.0), C.c_double(0.0)
+        _check(_lib.rh_reduced_hessian_flops(self._h, int(n_sm), C.byref(a), C.byref(e)))
+        return float(a.value), float(e.value)
+
     def solve(self, R, trans=False):
         R = np.array(R, dtype=np.float64, order="F", copy=True)
         if R.ndim == 1:
@@ -437,3 +447,14 @@ def potrs(L, B, work=None, stream=None):
     ldb = Bv.stride(1) if nrhs > 1 else max(n, 1)
     _check(load().rh_potrs(n, _ptr(L), ldl, _ptr(Bv), ldb, nrhs, _ptr(work), _stream_arg(B, stream)))
     return B
+
+
+def fp64_fma_rate(device=0, ctas_per_sm=2, threads_per_cta=384, iters=1 << 16):
+    """(GFLOP/s, ms) of the device's FP64 FMA throughput (rh_fp64_fma_rate)."""
+    lib = load()
+    gf, ms = C.c_double(0.0), C.c_float(0.0)
+    st = lib.rh_fp64_fma_rate(int(device), int(ctas_per_sm), int(threads_per_cta), int(iters), C.byref(gf),
+                              C.byref(ms))
+    if st != RH_OK:
+        raise RHError(st, "rh_fp64_fma_rate failed")
+    return float(gf.value), float(ms.value)

@@ -18,7 +18,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(rh_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(rh_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_library_exports_every_declared_symbol():
@@ -122,3 +122,100 @@ def test_coloring_bit_exact_against_oracle(case):
     ref_x, ref_p, ref_ncx, ref_ncp = o.coloring()
     assert (ncx.value, ncp.value) == (ref_ncx, ref_ncp)
     assert np.array_equal(cx, ref_x) and np.array_equal(cp, ref_p)
+
+
+@pytest.mark.parametrize("case,n_sm", [("tiny30", 4), ("case1354", 152), ("case9241", 152), ("case9241", 148)])
+def test_reduced_hessian_flop_counts(case, n_sm):
+    """rh_reduced_hessian_flops against a count made here from the symbolic data the
+    library exports (order, L and U patterns) and the oracle's J_p pattern: the
+    algorithmic count of Algorithm 2 for n_p dense directions, and the work the two
+    direction launches issue (each CTA's forward sweep over its reach, the last L^T
+    sweep over the rows SpMulAdd reads)."""
+    g = gg.make_grid(30, 41, 6, 4) if case == "tiny30" else gg.make_case(case)
+    lib = rh.load()
+    st, h, keep = host_grid(g)
+    assert st == 0
+    try:
+        dm = rh.Dims()
+        assert lib.rh_grid_dims(h, C.byref(dm)) == 0
+        nx = dm.n_x
+        sym = dict(perm=np.empty(nx, np.int32), bus_order=np.empty(g.n_bus - 1, np.int32),
+                   level=np.empty(g.n_bus - 1, np.int32), Lp=np.empty(nx + 1, np.int32),
+                   Lj=np.empty(dm.nnz_l, np.int32), Up=np.empty(nx + 1, np.int32), Uj=np.empty(dm.nnz_u, np.int32))
+        assert lib.rh_grid_symbolic(h, *[rh._ptr(sym[k]) for k in ("perm", "bus_order", "level", "Lp", "Lj", "Up",
+                                                                   "Uj")]) == 0
+        a, e = C.c_double(), C.c_double()
+        assert lib.rh_reduced_hessian_flops(h, n_sm, C.byref(a), C.byref(e)) == 0
+        assert lib.rh_reduced_hessian_flops(h, 0, C.byref(a), C.byref(e)) == rh.RH_EINVAL   # no device to ask
+        assert lib.rh_reduced_hessian_flops(h, n_sm, C.byref(a), C.byref(e)) == 0
+    finally:
+        lib.rh_grid_destroy(h)
+    np_, n_bus = dm.n_p, g.n_bus
+    Lp, Up, Uj = sym["Lp"], sym["Up"], sym["Uj"]
+    order = sym["bus_order"]
+    nv = np.array([2 if g.bus_type[b] == 2 else 1 for b in order])
+    q0 = np.concatenate([[0], np.cumsum(nv)[:-1]])
+    n_el = len(order)
+    pos_of_q = np.repeat(np.arange(n_el), nv)
+    fwd = nv * (Lp[q0 + 1] - Lp[q0]) + (nv == 2)
+    bwd = nv * (Up[q0 + 1] - Up[q0] - nv) + (nv == 2)
+    parent = np.array([pos_of_q[Uj[Up[q] + nv[k]]] if Up[q + 1] - Up[q] > nv[k] else -1
+                       for k, q in enumerate(q0)])
+    # the dense tail: the longest suffix of buses with at most 128 variables
+    t_bus0 = n_el
+    while t_bus0 > 0 and nx - q0[t_bus0 - 1] <= 128:
+        t_bus0 -= 1
+    t0 = q0[t_bus0] if t_bus0 < n_el else nx
+    T = nx - t0
+    # incidences, J_p pattern (internal rows) by p column
+    pairs = {(min(a_, b_), max(a_, b_)) for a_, b_ in zip(g.fr, g.to)}
+    n_inc = 2 * len(pairs)
+    ref = int(np.flatnonzero(g.bus_type == 0)[0])
+    deg_ref = sum(1 for a_, b_ in pairs if ref in (a_, b_))
+    n_gref = 1 + 2 * deg_ref
+    o = OracleGrid(g)
+    so = o.plant()
+    _, Jp = o.jacobians_csc(so.x, so.p)
+    iperm = np.empty(nx, np.int64)
+    iperm[sym["perm"]] = np.arange(nx)
+    jp_rows = [iperm[Jp.indices[Jp.indptr[j]:Jp.indptr[j + 1]]] for j in range(np_)]
+    nnz_jp = Jp.nnz
+    n_pv = int((g.bus_type == 1).sum())
+    algorithmic = np_ * (4.0 * nnz_jp + 2 * (2 * dm.nnz_l + 2 * (dm.nnz_u - nx)) + 8 * n_inc + 8 * n_bus +
+                         4 * n_gref + n_pv)
+    assert a.value == algorithmic
+    # CTA split of the two launches: 2 CTAs per SM, the first launch one slot short
+    slots = 2 * n_sm
+    n2 = max(min(np_, slots), -(-np_ // 256), 1)
+    per = (np_ + slots - 2) // (slots - 1)
+    n1 = min(n2, max(1, -(-np_ // per)))
+    tailed = T > 1 and T * -(-np_ // n1) <= 4096 and T * -(-np_ // n2) <= 4096
+    assert tailed
+    ext = sum(nv[k] * int(np.count_nonzero(sym["Lj"][Lp[q0[k]]:Lp[q0[k] + 1]] < t0)) for k in range(t_bus0, n_el))
+    tail = T * (T - 1) // 2
+    need = np.zeros(n_el, bool)
+    for rows in jp_rows:
+        need[pos_of_q[rows]] = True
+    for k in range(n_el):               # ancestors of needed buses (parents come later)
+        if need[k] and parent[k] >= 0:
+            need[parent[k]] = True
+    sp = np.arange(t_bus0)
+    lev0_pq = int(((sym["level"][:t_bus0] == 0) & (nv[:t_bus0] == 2)).sum())
+    ut = int(fwd[sp][sym["level"][:t_bus0] > 0].sum())
+    lt = int(bwd[sp][need[:t_bus0]].sum())
+    proj = 6 * n_bus + 8 * n_inc + 4 * (1 + deg_ref) + 2 * n_gref + 1 + n_pv + 2 * lev0_pq
+    l2 = proj + 2 * (ut + ext + 2 * tail + lt) + 2 * nnz_jp
+    l1 = 0.0
+    for c in range(n1):
+        c0, c1 = c * np_ // n1, (c + 1) * np_ // n1
+        reach = np.zeros(n_el, bool)
+        for j in range(c0, c1):
+            reach[pos_of_q[jp_rows[j]]] = True
+        for k in range(t_bus0):
+            if reach[k] and 0 <= parent[k] < t_bus0:
+                reach[parent[k]] = True
+        l = int(fwd[:t_bus0][reach[:t_bus0]].sum())
+        l1 += (c1 - c0) * 2.0 * (l + ext + 2 * tail + int(bwd[sp].sum()))
+    assert e.value == pytest.approx(l1 + np_ * l2, rel=1e-15)
+    if case == "case9241":      # the reach and the skipped rows outweigh the dense tail
+        assert e.value < a.value

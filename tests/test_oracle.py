@@ -641,3 +641,14 @@ def test_sparse_jacobians_equal_the_dense_ones():
     Jx, Jp = o.jacobians_csc(st.x, st.p)
     jx, jp = o.jacobians_dense(st.x, st.p)
     assert np.array_equal(Jx.toarray(), jx) and np.array_equal(Jp.toarray(), jp)
+
+
+def test_threaded_oracle_equals_one_thread_bit_for_bit():
+    """Sharing the columns of W out among threads changes no arithmetic: every column
+    runs the same steps on its own work vectors."""
+    o = OracleGrid(gg.make_case("case118"))
+    st = o.plant()
+    W = gg.random_directions(o.n_p, 37, 3)
+    a = o.hessvec(st.x, st.p, st.pd, st.qd, W)
+    for threads in (2, 5, 64):
+        assert np.array_equal(o.hessvec(st.x, st.p, st.pd, st.qd, W, threads=threads), a)

@@ -153,6 +153,9 @@ rh_status rh_powerflow(rh_grid *grid, const double *x0, double tol, int32_t max_
  * grad F = grad_p f + J_p^T lambda, F = f(x, p), and the per-branch second-order
  * coefficients of lambda^T Hess g + Hess f used by every later rh_hessvec.
  * Outputs (host, nullable): F, lambda[n_x], grad[n_p].
+ * Returns RH_ESINGULAR when a static pivot is below 1e-14 max|J_x| (for
+ * instance a PQ bus without any branch); the grid then stays without an
+ * adjoint (rh_hessvec returns RH_ESTATE).
  */
 rh_status rh_adjoint(rh_grid *grid, double *F, double *lambda, double *grad);
 
@@ -167,7 +170,9 @@ rh_status rh_adjoint(rh_grid *grid, double *F, double *lambda, double *grad);
  * flags: RH_HOST_PTRS or RH_DEVICE_PTRS.  With device pointers the call is
  * asynchronous on `stream`; with host pointers it copies and synchronises.
  * N = 0 is a no-op.  Every direction is computed independently, so column j of
- * HW does not depend on the other columns of W.
+ * HW does not depend on the other columns of W: a NaN or an infinity in column
+ * j of W makes column j of HW non-finite and leaves every other column as it
+ * would be without it.
  */
 rh_status rh_hessvec(rh_grid *grid, const double *W, int64_t ldw, int32_t N,
                      double *HW, int64_t ldhw, void *stream, uint32_t flags);
@@ -211,6 +216,19 @@ rh_status rh_batch_hessvec(int32_t n_items, const rh_hv_item *items, int32_t wid
  */
 #define RH_HESSIAN_CONCURRENT 2u
 rh_status rh_hessian(rh_grid *grid, int32_t block_n, double *H, int64_t ldh, void *stream, uint32_t flags);
+
+/*
+ * Columns col0 .. col0 + ncols - 1 of the reduced Hessian: HW for W the columns
+ * col0.. of the identity (Algorithm 2; section 5.3 computes H by such column
+ * blocks, which are independent), all in one launch.  This is the unit of a
+ * column-block partition of H over several GPUs, each computing its own block.
+ *   H   n_p x ncols, column-major, ldh >= n_p; column j of H receives H[:, col0 + j]
+ * flags: RH_HOST_PTRS or RH_DEVICE_PTRS, as for rh_hessvec.  Requires rh_adjoint
+ * for the current state (RH_ESTATE otherwise); RH_EINVAL for a range outside
+ * [0, n_p).  ncols = 0 is a no-op.
+ */
+rh_status rh_hessian_columns(rh_grid *grid, int32_t col0, int32_t ncols, double *H, int64_t ldh, void *stream,
+                             uint32_t flags);
 
 /*
  * The reduced Hessian at the current state in one call (sections 4 and 5:
@@ -400,6 +418,18 @@ rh_status rh_grid_coloring(const rh_grid *grid, int32_t *colors_x, int32_t *colo
                            int32_t *n_colors_p);
 rh_status rh_jacobian(rh_grid *grid, int32_t method, int32_t *jx_row, int32_t *jx_col, double *jx_val,
                       int32_t *jp_row, int32_t *jp_col, double *jp_val);
+
+/*
+ * Index checks (a development aid, no counterpart in the paper).  librh built
+ * with -DRH_BOUNDS (librh_bounds.so) checks, in its kernels, every row, slot and
+ * position index it reads or writes against the size of its array; a failed
+ * check sets a bit of an error word on the device and skips that access (no
+ * trap, no early exit that a barrier would wait for).  rh_bounds_check sets
+ * *enabled to 1 in that build (0 in the normal one, *errors then 0), and reads
+ * and clears the error word of `device` into *errors (0: no index outside its
+ * array since the last call).
+ */
+rh_status rh_bounds_check(int32_t device, int32_t *enabled, uint32_t *errors);
 
 /* Message of the last error on this thread ("" if none). */
 const char *rh_last_error(void);

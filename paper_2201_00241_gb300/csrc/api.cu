@@ -173,6 +173,8 @@ struct rh_grid {
         g.n_bus = S.n_bus;
         g.n_x = S.n_x;
         g.ref = S.ref;
+        g.nnz_a = (int)S.col.size();
+        g.nnz_jp = (int)S.jp_col.size();
         g.yp = yp; g.yj = yj; g.ydiag = ydiag; g.G = G; g.B = B;
         g.qth = qth; g.qv = qv; g.ip_v = ip_v; g.ip_pg = ip_pg;
         g.jac_dst = jac_dst; g.pg_slot = pg_slot;
@@ -187,6 +189,7 @@ struct rh_grid {
     rh::DirGrid dir() const {
         rh::DirGrid g;
         g.n_x = S.n_x; g.n_p = S.n_p; g.zero_row = S.n_x + S.n_p;
+        g.nnz = (int)S.col.size();
         g.col = col; g.A = A; g.At = At; g.invdiag = invdiag;
         g.lf = {S.n_flev, flev_ptr, fslot, flev_maxext};
         g.lb = {S.n_blev, blev_ptr, bslot, blev_maxext};
@@ -212,6 +215,7 @@ struct rh_grid {
     rh::RfGrid rf() const {
         rh::RfGrid g;
         g.n_x = S.n_x; g.t0 = S.t0; g.T = S.n_x - S.t0;
+        g.nnz = (int)S.col.size();
         g.rf_lev_bus = rf_lev_bus; g.q0 = q0; g.nv = nv;
         g.rowptr = rowptr; g.col = col; g.diagpos = diagpos; g.tpos = tpos;
         g.tgt_pos = rf_tgt_pos; g.tgt_gptr = rf_tgt_gptr; g.grp = reinterpret_cast<const int2*>(rf_grp);
@@ -325,6 +329,7 @@ rh_status dirs(rh_grid* g, int N, int64_t ld, double* V, double* T, const double
     L.HW = HW;
     L.ldhw = ldhw;
     L.phases = phases;
+    L.ws_elems = V == g->V ? (int64_t)g->ws_elems : (V == g->v1 ? (int64_t)g->rows() : 0);
     L.use_tail = rh::dirs_tail_fits(g->S.n_x - g->S.t0, N, L.n_cta) ? 1 : 0;
     L.use_reach = (L.use_tail && !W && (phases & rh::PH_WLOAD) && (phases & rh::PH_L) && (phases & rh::PH_U)) ? 1 : 0;
     rh::launch_dirs(g->dir(), L, s);
@@ -1207,6 +1212,7 @@ rh_status rh_batch_hessvec(int32_t n_items, const rh_hv_item* items, int32_t wid
             L.HW = it.HW;
             L.ldhw = it.ldhw;
             L.phases = all;
+            L.ws_elems = it.work ? (int64_t)g->rows() * it.N : (int64_t)g->ws_elems;
             int Tt = g->S.n_x - g->S.t0;
             L.use_tail = rh::dirs_tail_fits(Tt, it.N, G) ? 1 : 0;
             L.use_reach = 0;
@@ -1258,6 +1264,41 @@ rh_status rh_hessian(rh_grid* g, int32_t block_n, double* H, int64_t ldh, void* 
     }
     if (host) {
         RH_CUDA(cudaMemcpy2DAsync(H, ldh * sizeof(double), Hd, lh * sizeof(double), np * sizeof(double), np,
+                                  cudaMemcpyDeviceToHost, s));
+        RH_CUDA(cudaStreamSynchronize(s));
+    }
+    return RH_OK;
+}
+
+rh_status rh_hessian_columns(rh_grid* g, int32_t col0, int32_t ncols, double* H, int64_t ldh, void* stream,
+                             uint32_t flags) {
+    if (!g) return fail(RH_EINVAL, "NULL grid");
+    const auto& S = g->S;
+    if (col0 < 0 || ncols < 0 || (int64_t)col0 + ncols > S.n_p) return fail(RH_EINVAL, "column range outside [0, n_p)");
+    if (ncols == 0) return RH_OK;
+    if (!H || ldh < S.n_p) return fail(RH_EINVAL, "bad H or leading dimension");
+    if (!g->adjoint_ready) return fail(RH_ESTATE, "rh_hessian_columns needs rh_adjoint for the current state");
+    rh_status st = set_device(g);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int np = S.n_p;
+    const bool host = !(flags & RH_DEVICE_PTRS);
+    double* Hd = H;
+    int64_t lh = ldh;
+    if (host) {
+        st = ensure_stage(g, (size_t)np * ncols);
+        if (st) return st;
+        Hd = g->stage_out;
+        lh = np;
+    }
+    st = ensure_ws(g, (size_t)ncols);
+    if (st) return st;
+    st = dirs(g, ncols, ncols, g->V, g->T, nullptr, 0, col0, Hd, lh,
+              rh::PH_WLOAD | rh::PH_SPMUL | rh::PH_L | rh::PH_U | rh::PH_TPROJ | rh::PH_UT | rh::PH_LT | rh::PH_MULADD,
+              s);
+    if (st) return st;
+    if (host) {
+        RH_CUDA(cudaMemcpy2DAsync(H, ldh * sizeof(double), Hd, lh * sizeof(double), np * sizeof(double), ncols,
                                   cudaMemcpyDeviceToHost, s));
         RH_CUDA(cudaStreamSynchronize(s));
     }
@@ -1408,6 +1449,7 @@ rh_status rh_hessvec_noalloc(rh_grid* g, const double* W, int64_t ldw, int32_t N
     L.HW = HW;
     L.ldhw = ldhw;
     L.phases = rh::PH_WLOAD | rh::PH_SPMUL | rh::PH_L | rh::PH_U | rh::PH_TPROJ | rh::PH_UT | rh::PH_LT | rh::PH_MULADD;
+    L.ws_elems = RH_NOALLOC_DOUBLES;
     L.use_tail = rh::dirs_tail_fits(S.n_x - S.t0, N, L.n_cta) ? 1 : 0;
     L.use_reach = 0;
     rh::launch_dirs(g->dir(), L, (cudaStream_t)stream);

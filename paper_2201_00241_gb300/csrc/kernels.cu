@@ -19,7 +19,9 @@
 //  * Right-hand sides are interleaved, row-major [row][ld]: the D directions
 //    of a CTA are contiguous in each row.
 #include <cstdio>
+#include <mutex>
 
+#include "../../include/rh.h"
 #include "rh_kernels.h"
 
 namespace rh {
@@ -34,6 +36,21 @@ constexpr int kDirThreads = 384;
 constexpr int kDirCtasPerSm = 2;
 constexpr int kPartCap = 4096;   // doubles of k-split partial sums per CTA
 constexpr int kDMax = 256;       // max directions per CTA
+
+// Index checks of the bounds-checking build (-DRH_BOUNDS): a failed check sets a
+// bit of g_bounds_err and the access is skipped (never a trap, never an early
+// return that a barrier would wait for); rh_bounds_check reads the word.  In the
+// normal build every check is the constant true and compiles away.
+#ifdef RH_BOUNDS
+__device__ unsigned int g_bounds_err;
+__device__ __forceinline__ bool inb(long long i, long long n) {
+    const bool ok = i >= 0 && i < n;
+    if (!ok) atomicOr(&g_bounds_err, 1u);
+    return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool inb(long long, long long) { return true; }
+#endif
 
 __device__ __forceinline__ unsigned long long ordered_bits(double v) {
     // |v| as a bit pattern whose unsigned order is the numeric order (NaN above inf)
@@ -67,10 +84,12 @@ __device__ __forceinline__ void jac_store(const PfGrid& g, int t, const double (
     for (int u = 0; u < 4; u++) {
         const int dst = g.jac_dst[4 * t + u];
         if (dst >= 0) {
+            if (!inb(dst, g.nnz_a)) continue;
             A[dst] = d[u];
             const unsigned long long b = ordered_bits(d[u]);
             jm = b > jm ? b : jm;
         } else if (dst <= -2) {
+            if (!inb(-(dst + 2), g.nnz_jp)) continue;
             jpv[-(dst + 2)] = d[u];
         }
     }
@@ -290,8 +309,10 @@ __global__ void k_rf_pivot(RfGrid g, int b0, int nb) {
     const int uv0 = dv + 1;
     const int n = g.rowptr[qt + 1] - ut0;
     for (int e = lane; e < n; e += 32) {
+        if (!(inb(ut0 + e, g.nnz) && (!two || inb(uv0 + e, g.nnz)))) continue;
         if (two) g.A[uv0 + e] = fma(-lvt, g.A[ut0 + e], g.A[uv0 + e]);
         int pt = g.tpos[ut0 + e];
+        if (!(inb(pt, g.nnz) && (!two || inb(g.tpos[uv0 + e], g.nnz)))) continue;
         double lt = g.A[pt] * it;
         g.A[pt] = lt;
         if (two) {
@@ -317,6 +338,9 @@ __global__ void k_rf_update(RfGrid g, int64_t t0, int64_t nt) {
     double acc = 0.0;
     for (int64_t c = g.tgt_gptr[t]; c < g.tgt_gptr[t + 1]; c++) {
         const int2 d = g.grp[3 * c], tu = g.grp[3 * c + 1], vu = g.grp[3 * c + 2];   // {dt, dv} {lt, ut} {lv, uv}
+        if (!(inb(d.x + 1, g.nnz + 1) && inb(tu.x, g.nnz) && inb(tu.y, g.nnz) &&
+              (d.y < 0 || (inb(d.y, g.nnz) && inb(vu.x, g.nnz) && inb(vu.y, g.nnz)))))
+            continue;
         const double it = 1.0 / g.A[d.x];
         const double lt = g.A[tu.x] * it;
         const double ut = g.A[tu.y];
@@ -333,7 +357,7 @@ __global__ void k_rf_update(RfGrid g, int64_t t0, int64_t nt) {
         }
     }
     const int p = g.tgt_pos[t];
-    g.A[p] -= acc;
+    if (inb(p, g.nnz)) g.A[p] -= acc;
 }
 
 // Dense trailing block [t0, n_x) as a tiled right-looking LU over TB x TB tiles
@@ -354,7 +378,7 @@ __global__ void k_tail_gather(RfGrid g) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= T * T) return;
     const int p = g.tail_pos[idx];
-    g.tailD[idx] = p >= 0 ? g.A[p] : 0.0;
+    g.tailD[idx] = (p >= 0 && inb(p, g.nnz)) ? g.A[p] : 0.0;
 }
 
 // Eliminates the tile held in Dk (unit-padded beyond kb) and stores it at
@@ -460,7 +484,7 @@ __global__ void k_tail_scatter(RfGrid g) {
     if (idx >= T * T) return;
     const int p = g.tail_pos[idx];
     const double v = g.tailD[idx];
-    if (p >= 0) g.A[p] = v;
+    if (p >= 0 && inb(p, g.nnz)) g.A[p] = v;
     const int i = idx / T, j = idx - i * T;
     if (i == j) {
         g.invdiag[g.t0 + i] = 1.0 / v;
@@ -570,18 +594,28 @@ __device__ __forceinline__ int choose_ks(int nb, int D, int maxext) {
 // CMASK: x of a row whose bit in cmask is clear is zero and is not read.
 __device__ __forceinline__ bool mask_get(const unsigned* m, int q) { return (m[q >> 5] >> (q & 31)) & 1u; }
 template <bool CMASK>
-__device__ __forceinline__ double ldx(const double* X, int i, int64_t ld, int64_t c, const unsigned* cmask) {
-    return (!CMASK || mask_get(cmask, i)) ? X[(int64_t)i * ld + c] : 0.0;
+__device__ __forceinline__ double ldx(const double* X, int i, int64_t ld, int64_t c, const unsigned* cmask,
+                                      int nrows) {
+    return (inb(i, nrows) && (!CMASK || mask_get(cmask, i))) ? X[(int64_t)i * ld + c] : 0.0;
+}
+// n, or 0 when a row part [r0, r0 + n) or [r1, r1 + n) would leave the nnz
+// positions of the pattern (bounds build only; the item is then left as it is)
+__device__ __forceinline__ int part_len(int n, int r0, int r1, int nnz) {
+    return (inb(r0, nnz + 1) && inb(r0 + n, nnz + 1) && inb(r1, nnz + 1) && inb(r1 + n, nnz + 1)) ? n : 0;
+}
+// X[q][c] = v for a row q that must lie below nrows (checked in the bounds build)
+__device__ __forceinline__ void stx(double* X, int q, int64_t ld, int64_t c, double v, int nrows) {
+    if (inb(q, nrows)) X[(int64_t)q * ld + c] = v;
 }
 template <bool TWO, bool CMASK = false>
 __device__ __forceinline__ void block_sub(const int* __restrict__ col, const double* __restrict__ vals, int r0, int r1,
                                           int e0, int e1, const double* X, int64_t ld, int64_t c, double& a0,
-                                          double& a1, const unsigned* cmask = nullptr) {
+                                          double& a1, const unsigned* cmask = nullptr, int nrows = 0x7fffffff) {
     int e = e0;
     for (; e + 4 <= e1; e += 4) {
         const int i0 = col[r0 + e], i1 = col[r0 + e + 1], i2 = col[r0 + e + 2], i3 = col[r0 + e + 3];
-        const double x0 = ldx<CMASK>(X, i0, ld, c, cmask), x1 = ldx<CMASK>(X, i1, ld, c, cmask);
-        const double x2 = ldx<CMASK>(X, i2, ld, c, cmask), x3 = ldx<CMASK>(X, i3, ld, c, cmask);
+        const double x0 = ldx<CMASK>(X, i0, ld, c, cmask, nrows), x1 = ldx<CMASK>(X, i1, ld, c, cmask, nrows);
+        const double x2 = ldx<CMASK>(X, i2, ld, c, cmask, nrows), x3 = ldx<CMASK>(X, i3, ld, c, cmask, nrows);
         a0 = fma(-vals[r0 + e], x0, a0);
         a0 = fma(-vals[r0 + e + 1], x1, a0);
         a0 = fma(-vals[r0 + e + 2], x2, a0);
@@ -594,7 +628,7 @@ __device__ __forceinline__ void block_sub(const int* __restrict__ col, const dou
         }
     }
     for (; e < e1; e++) {
-        const double xv = ldx<CMASK>(X, col[r0 + e], ld, c, cmask);
+        const double xv = ldx<CMASK>(X, col[r0 + e], ld, c, cmask, nrows);
         a0 = fma(-vals[r0 + e], xv, a0);
         if constexpr (TWO) a1 = fma(-vals[r1 + e], xv, a1);
     }
@@ -608,12 +642,12 @@ template <bool SCALE, bool TWO>
 __device__ __forceinline__ void fwd_finish(const DirGrid& g, const double* __restrict__ vals, double* X, int64_t ld,
                                            int64_t c, int q, bool two, int pos_vt, double a0, double a1) {
     double x0 = SCALE ? a0 * g.invdiag[q] : a0;
-    X[(int64_t)q * ld + c] = x0;
+    stx(X, q, ld, c, x0, g.n_x);
     if constexpr (TWO) {
         a1 = fma(-vals[pos_vt], x0, a1);
         const double i1 = (SCALE && two) ? g.invdiag[q + 1] : 1.0;
         const double x1 = SCALE ? a1 * i1 : a1;
-        if (two) X[(int64_t)(q + 1) * ld + c] = x1;
+        if (two) stx(X, q + 1, ld, c, x1, g.n_x);
     }
 }
 
@@ -656,26 +690,27 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 const int d = it - bi * D;
                 const int it2 = it + blockDim.x, bi2 = it2 / D;
                 if (it2 < items) nxt = slots[bi2];
-                const int q = sl.x, n = sl.y, rp = sl.z;
+                const int q = sl.x, rp = sl.z;
                 bi = bi2;
                 const bool two = sl.w >= 0;
                 const int64_t c = c0 + d;
-                if (mask && !mask_get(mask, q)) continue;     // outside the reach: x = 0, never read
+                if (mask && !(inb(q, g.n_x) && mask_get(mask, q))) continue;   // outside the reach: x = 0, never read
                 const int rpv = two ? sl.w : rp;
+                const int n = part_len(sl.y, rp, rpv, g.nnz);
                 const bool has_b = !seed || mask_get(seed, q);
-                double a0 = has_b ? X[(int64_t)q * ld + c] : 0.0;
-                double a1 = (two && has_b) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
+                double a0 = (has_b && inb(q, g.n_x)) ? X[(int64_t)q * ld + c] : 0.0;
+                double a1 = (two && has_b && inb(q + 1, g.n_x)) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
                 if (warp_any(two)) {
-                    block_sub<true, CMASK>(g.col, vals, rp, rpv, 0, n, X, ld, c, a0, a1, cmask);
+                    block_sub<true, CMASK>(g.col, vals, rp, rpv, 0, n, X, ld, c, a0, a1, cmask, g.n_x);
                     if (EXT) {
-                        X[(int64_t)q * ld + c] = a0;
-                        if (two) X[(int64_t)(q + 1) * ld + c] = a1;
+                        stx(X, q, ld, c, a0, g.n_x);
+                        if (two) stx(X, q + 1, ld, c, a1, g.n_x);
                     } else {
                         fwd_finish<SCALE, true>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
                     }
                 } else {
-                    block_sub<false, CMASK>(g.col, vals, rp, rpv, 0, n, X, ld, c, a0, a1, cmask);
-                    if (EXT) X[(int64_t)q * ld + c] = a0;
+                    block_sub<false, CMASK>(g.col, vals, rp, rpv, 0, n, X, ld, c, a0, a1, cmask, g.n_x);
+                    if (EXT) stx(X, q, ld, c, a0, g.n_x);
                     else fwd_finish<SCALE, false>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
                 }
                 if (mask) mask_bus(mask, g.bparent[q]);
@@ -686,15 +721,16 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 int bi = it / per, rem = it - bi * per;
                 int sli = rem / D, d = rem - sli * D;
                 const int4 sl = slots[bi];
-                if (mask && !mask_get(mask, sl.x)) continue;
-                const int n = sl.y, rp = sl.z;
+                if (mask && !(inb(sl.x, g.n_x) && mask_get(mask, sl.x))) continue;
+                const int rp = sl.z;
                 const bool two = sl.w >= 0;
                 const int rpv = two ? sl.w : rp;
+                const int n = part_len(sl.y, rp, rpv, g.nnz);
                 int64_t c = c0 + d;
                 int e0 = sli * n / ks, e1 = (sli + 1) * n / ks;
                 double s0 = 0.0, s1 = 0.0;     // minus the slice's partial sums
-                if (warp_any(two)) block_sub<true, CMASK>(g.col, vals, rp, rpv, e0, e1, X, ld, c, s0, s1, cmask);
-                else block_sub<false, CMASK>(g.col, vals, rp, rpv, e0, e1, X, ld, c, s0, s1, cmask);
+                if (warp_any(two)) block_sub<true, CMASK>(g.col, vals, rp, rpv, e0, e1, X, ld, c, s0, s1, cmask, g.n_x);
+                else block_sub<false, CMASK>(g.col, vals, rp, rpv, e0, e1, X, ld, c, s0, s1, cmask, g.n_x);
                 double* pp = part + 2 * ((bi * ks + sli) * D + d);
                 pp[0] = s0;
                 pp[1] = s1;
@@ -703,14 +739,15 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
             for (int it = threadIdx.x; it < nb * D; it += blockDim.x) {
                 int bi = it / D, d = it - bi * D;
                 const int4 sl = slots[bi];
-                const int q = sl.x, n = sl.y;
+                const int q = sl.x;
                 const bool two = sl.w >= 0;
                 int64_t c = c0 + d;
-                if (mask && !mask_get(mask, q)) continue;
+                if (mask && !(inb(q, g.n_x) && mask_get(mask, q))) continue;
                 const int rpv = two ? sl.w : sl.z;
+                const int n = part_len(sl.y, sl.z, rpv, g.nnz);
                 const bool has_b = !seed || mask_get(seed, q);
-                double a0 = has_b ? X[(int64_t)q * ld + c] : 0.0;
-                double a1 = (two && has_b) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
+                double a0 = (has_b && inb(q, g.n_x)) ? X[(int64_t)q * ld + c] : 0.0;
+                double a1 = (two && has_b && inb(q + 1, g.n_x)) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
                 if (warp_any(two)) {
                     for (int k = 0; k < ks; k++) {
                         const double* pp = part + 2 * ((bi * ks + k) * D + d);
@@ -718,14 +755,14 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                         a1 += pp[1];
                     }
                     if (EXT) {
-                        X[(int64_t)q * ld + c] = a0;
-                        if (two) X[(int64_t)(q + 1) * ld + c] = a1;
+                        stx(X, q, ld, c, a0, g.n_x);
+                        if (two) stx(X, q + 1, ld, c, a1, g.n_x);
                     } else {
                         fwd_finish<SCALE, true>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
                     }
                 } else {
                     for (int k = 0; k < ks; k++) a0 += part[2 * ((bi * ks + k) * D + d)];
-                    if (EXT) X[(int64_t)q * ld + c] = a0;
+                    if (EXT) stx(X, q, ld, c, a0, g.n_x);
                     else fwd_finish<SCALE, false>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
                 }
                 if (mask) mask_bus(mask, g.bparent[q]);
@@ -742,10 +779,10 @@ __device__ __forceinline__ void bwd_finish(const DirGrid& g, const double* __res
     if constexpr (TWO) {
         const double i1 = (SCALE && two) ? g.invdiag[q + 1] : 1.0;
         const double x1 = SCALE ? a1 * i1 : a1;
-        if (two) X[(int64_t)(q + 1) * ld + c] = x1;
+        if (two) stx(X, q + 1, ld, c, x1, g.n_x);
         a0 = fma(-vals[pos_tv], two ? x1 : 0.0, a0);
     }
-    X[(int64_t)q * ld + c] = SCALE ? a0 * g.invdiag[q] : a0;
+    stx(X, q, ld, c, SCALE ? a0 * g.invdiag[q] : a0, g.n_x);
 }
 
 // rmask (optional): right-hand side rows whose bit is clear are zero and are not read
@@ -766,18 +803,19 @@ __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __
                 const int d = it - bi * D;
                 const int it2 = it + blockDim.x, bi2 = it2 / D;
                 if (it2 < items) nxt = slots[bi2];
-                const int q = sl.x, n = sl.y, ue0 = sl.z;
+                const int q = sl.x, ue0 = sl.z;
                 const bool two = sl.w >= 0;
                 const int ue1 = two ? sl.w : ue0;
+                const int n = part_len(sl.y, ue0 - 1, ue1, g.nnz);
                 const int64_t c = c0 + d;
                 const bool has_b = !rmask || mask_get(rmask, q);
-                double a0 = has_b ? X[(int64_t)q * ld + c] : 0.0;
-                double a1 = (two && has_b) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
+                double a0 = (has_b && inb(q, g.n_x)) ? X[(int64_t)q * ld + c] : 0.0;
+                double a1 = (two && has_b && inb(q + 1, g.n_x)) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
                 if (warp_any(two)) {
-                    block_sub<true>(g.col, vals, ue0, ue1, 0, n, X, ld, c, a0, a1);
+                    block_sub<true>(g.col, vals, ue0, ue1, 0, n, X, ld, c, a0, a1, nullptr, g.n_x);
                     bwd_finish<SCALE, true>(g, vals, X, ld, c, q, two, ue0 - 1, a0, a1);
                 } else {
-                    block_sub<false>(g.col, vals, ue0, ue1, 0, n, X, ld, c, a0, a1);
+                    block_sub<false>(g.col, vals, ue0, ue1, 0, n, X, ld, c, a0, a1, nullptr, g.n_x);
                     bwd_finish<SCALE, false>(g, vals, X, ld, c, q, two, ue0 - 1, a0, a1);
                 }
                 bi = bi2;
@@ -788,14 +826,15 @@ __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __
                 int bi = it / per, rem = it - bi * per;
                 int sli = rem / D, d = rem - sli * D;
                 const int4 sl = slots[bi];
-                const int n = sl.y, ue0 = sl.z;
+                const int ue0 = sl.z;
                 const bool two = sl.w >= 0;
                 const int ue1 = two ? sl.w : ue0;
+                const int n = part_len(sl.y, ue0 - 1, ue1, g.nnz);
                 int64_t c = c0 + d;
                 int e0 = sli * n / ks, e1 = (sli + 1) * n / ks;
                 double s0 = 0.0, s1 = 0.0;     // minus the slice's partial sums
-                if (warp_any(two)) block_sub<true>(g.col, vals, ue0, ue1, e0, e1, X, ld, c, s0, s1);
-                else block_sub<false>(g.col, vals, ue0, ue1, e0, e1, X, ld, c, s0, s1);
+                if (warp_any(two)) block_sub<true>(g.col, vals, ue0, ue1, e0, e1, X, ld, c, s0, s1, nullptr, g.n_x);
+                else block_sub<false>(g.col, vals, ue0, ue1, e0, e1, X, ld, c, s0, s1, nullptr, g.n_x);
                 double* pp = part + 2 * ((bi * ks + sli) * D + d);
                 pp[0] = s0;
                 pp[1] = s1;
@@ -808,8 +847,8 @@ __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __
                 const bool two = sl.w >= 0;
                 int64_t c = c0 + d;
                 const bool has_b = !rmask || mask_get(rmask, q);
-                double a0 = has_b ? X[(int64_t)q * ld + c] : 0.0;
-                double a1 = (two && has_b) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
+                double a0 = (has_b && inb(q, g.n_x)) ? X[(int64_t)q * ld + c] : 0.0;
+                double a1 = (two && has_b && inb(q + 1, g.n_x)) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
                 if (warp_any(two)) {
                     for (int k = 0; k < ks; k++) {
                         const double* pp = part + 2 * ((bi * ks + k) * D + d);
@@ -973,7 +1012,8 @@ __device__ void tproj(const DirGrid& g, const double* V, double* T, int64_t ld, 
     double c2r = *g.c2ref;
     for (int d = threadIdx.x; d < D; d += blockDim.x) {
         double s = 0.0;
-        for (int e = 0; e < g.n_gref; e++) s = fma(g.gref_val[e], V[(int64_t)g.gref_row[e] * ld + c0 + d], s);
+        for (int e = 0; e < g.n_gref; e++)
+            if (inb(g.gref_row[e], g.zero_row + 1)) s = fma(g.gref_val[e], V[(int64_t)g.gref_row[e] * ld + c0 + d], s);
         sref[d] = c2r * s;
     }
     __syncthreads();
@@ -982,7 +1022,8 @@ __device__ void tproj(const DirGrid& g, const double* V, double* T, int64_t ld, 
         int b = g.tp_bus[bi];
         int64_t c = c0 + d;
         int rth = g.uth[b], rv = g.uv[b];
-        double dth = V[(int64_t)rth * ld + c], dv = V[(int64_t)rv * ld + c];
+        const int rows = g.zero_row + 1;
+        double dth = inb(rth, rows) ? V[(int64_t)rth * ld + c] : 0.0, dv = inb(rv, rows) ? V[(int64_t)rv * ld + c] : 0.0;
         double ab = g.asum[b];
         double yv = fma(g.d2[b], dv, ab * dth);
         double yth = fma(ab, dv, g.csum[b] * dth);
@@ -990,8 +1031,10 @@ __device__ void tproj(const DirGrid& g, const double* V, double* T, int64_t ld, 
         const int e1 = g.inc_ptr[b + 1];
         for (; e + 2 <= e1; e += 2) {
             const int t0 = g.inc_uth[e], v0 = g.inc_uv[e], t1 = g.inc_uth[e + 1], v1 = g.inc_uv[e + 1];
-            const double dthj0 = V[(int64_t)t0 * ld + c], dvj0 = V[(int64_t)v0 * ld + c];
-            const double dthj1 = V[(int64_t)t1 * ld + c], dvj1 = V[(int64_t)v1 * ld + c];
+            const double dthj0 = inb(t0, rows) ? V[(int64_t)t0 * ld + c] : 0.0;
+            const double dvj0 = inb(v0, rows) ? V[(int64_t)v0 * ld + c] : 0.0;
+            const double dthj1 = inb(t1, rows) ? V[(int64_t)t1 * ld + c] : 0.0;
+            const double dvj1 = inb(v1, rows) ? V[(int64_t)v1 * ld + c] : 0.0;
             const double4_32a cf0 = g.inc_coef[e], cf1 = g.inc_coef[e + 1];
             yv = fma(cf0.x, dvj0, yv);
             yv = fma(cf0.y, dthj0, yv);
@@ -1005,8 +1048,8 @@ __device__ void tproj(const DirGrid& g, const double* V, double* T, int64_t ld, 
         if (warp_any(e < e1)) {
             if (e < e1) {
                 const double4_32a cf = g.inc_coef[e];
-                const double dthj = V[(int64_t)g.inc_uth[e] * ld + c];
-                const double dvj = V[(int64_t)g.inc_uv[e] * ld + c];
+                const double dthj = inb(g.inc_uth[e], rows) ? V[(int64_t)g.inc_uth[e] * ld + c] : 0.0;
+                const double dvj = inb(g.inc_uv[e], rows) ? V[(int64_t)g.inc_uv[e] * ld + c] : 0.0;
                 yv = fma(cf.x, dvj, yv);
                 yv = fma(cf.y, dthj, yv);
                 yth = fma(cf.z, dvj, yth);
@@ -1020,15 +1063,15 @@ __device__ void tproj(const DirGrid& g, const double* V, double* T, int64_t ld, 
                 yth = fma(sref[d], g.gref_th[b], yth);
             }
         }
-        if (rth != g.zero_row) T[(int64_t)rth * ld + c] = flip_sign(yth, true);
+        if (rth != g.zero_row && inb(rth, rows)) T[(int64_t)rth * ld + c] = flip_sign(yth, true);
         const int l0 = fold_ut ? g.tp_l0[b] : -1;
         if (warp_any(l0 >= 0)) {
             if (l0 >= 0) yv = fma(-g.Atd[l0], yth, yv);   // T_v = -yv + u'_tv yth
         }
-        T[(int64_t)rv * ld + c] = flip_sign(yv, rv < g.n_x);
+        if (inb(rv, rows)) T[(int64_t)rv * ld + c] = flip_sign(yv, rv < g.n_x);
         const int pr = g.pg_row[b];
         if (warp_any(pr >= 0)) {
-            if (pr >= 0) T[(int64_t)pr * ld + c] = g.pg_curv[b] * V[(int64_t)pr * ld + c];
+            if (pr >= 0 && inb(pr, rows)) T[(int64_t)pr * ld + c] = g.pg_curv[b] * V[(int64_t)pr * ld + c];
         }
     }
 }
@@ -1044,6 +1087,7 @@ __device__ __forceinline__ void muladd_row(const DirGrid& g, const DirLaunch& L,
     const int t1 = g.jpt_ptr[k + 1];
     for (int t = g.jpt_ptr[k]; t < t1; t++) {
         const double v = g.jptvd[t];
+        if (!inb(g.jpt_row[t], g.n_x)) continue;
         const double* pr = T + (int64_t)g.jpt_row[t] * ld + d0;
 #pragma unroll
         for (int w = 0; w < W; w++) h[w] = fma(v, pr[w], h[w]);
@@ -1061,6 +1105,13 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
     if (D <= 0) return;
     // this CTA's directions: row r, local direction d at base[r * ld + d]
     const int64_t ld = L.ld;
+    {
+        // the CTA's last element lies in the buffers (bounds build; the condition is
+        // the same for every thread of the CTA, so leaving here skips no barrier)
+        const int64_t first = L.cta_stride ? (int64_t)cta * L.cta_stride : (int64_t)c0;
+        const int64_t last = first + (int64_t)g.zero_row * ld + D - 1;
+        if (!inb((L.cta_stride ? 0 : c0) + D - 1, ld) || (L.ws_elems > 0 && !inb(last, L.ws_elems))) return;
+    }
     const int64_t base = L.cta_stride ? (int64_t)cta * L.cta_stride : (int64_t)c0;
     double* V = L.V + base;
     double* T = L.T + base;
@@ -1686,15 +1737,23 @@ cudaError_t launch_refactor(const RfGrid& g, const int* lev_ptr_host, const int6
     return cudaGetLastError();
 }
 
-// The dynamic shared-memory limit is a per-kernel, process-wide attribute: raise
-// it once to the device maximum (minus the kernel's static shared memory) for
-// every kernel that can need more than the 48 KB default.
+// The dynamic shared-memory limit is a per-kernel attribute of each device's
+// context: raise it on every device once, to that device's maximum (minus the
+// kernel's static shared memory), for every kernel that can need more than the
+// 48 KB default.  The SM count is cached per device too.
+constexpr int kMaxDevices = 64;
+std::mutex g_dev_mu;
+bool g_prepared[kMaxDevices];
+int g_n_sm[kMaxDevices];
+
 cudaError_t prepare_kernels() {
-    static bool done = false;
-    if (done) return cudaSuccess;
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    if (g_prepared[dev]) return cudaSuccess;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     const void* fns[3] = {(const void*)k_dirs, (const void*)k_solve1, (const void*)k_dirs_batch};
     for (const void* f : fns) {
@@ -1704,7 +1763,7 @@ cudaError_t prepare_kernels() {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
         if (e != cudaSuccess) return e;
     }
-    done = true;
+    g_prepared[dev] = true;
     return cudaSuccess;
 }
 
@@ -1718,14 +1777,16 @@ void launch_transpose_values(int nnz, const int* tpos, const int* arow, const in
                                                                nnz_jp, jpt_src, jpt_row, jpv, jptv, jptvd);
 }
 
+// SMs of the current device (1 if the query fails)
 static int num_sms() {
-    static int n_sm = 0;
-    if (n_sm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 1;
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    if (g_n_sm[dev] == 0) {
+        int n = 0;
+        g_n_sm[dev] = (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0) ? n : 1;
     }
-    return n_sm;
+    return g_n_sm[dev];
 }
 
 int dirs_cta_slots_for(int n_sm) { return kDirCtasPerSm * n_sm; }
@@ -1822,3 +1883,22 @@ void launch_gather_rows(int n_rows, int N, const int* map, const double* src, in
 }
 
 }  // namespace rh
+
+// Whether this build checks indices (-DRH_BOUNDS), and the error word of `device`,
+// which the call reads and clears.
+extern "C" rh_status rh_bounds_check(int32_t device, int32_t* enabled, uint32_t* errors) {
+    if (!enabled || !errors) return RH_EINVAL;
+    *errors = 0;
+#ifdef RH_BOUNDS
+    *enabled = 1;
+    if (cudaSetDevice(device) != cudaSuccess) return RH_ECUDA;
+    unsigned int e = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&e, rh::g_bounds_err, sizeof(e)) != cudaSuccess) return RH_ECUDA;
+    if (cudaMemcpyToSymbol(rh::g_bounds_err, &z, sizeof(z)) != cudaSuccess) return RH_ECUDA;
+    *errors = e;
+#else
+    (void)device;
+    *enabled = 0;
+#endif
+    return RH_OK;
+}

@@ -35,6 +35,7 @@ struct LevelSet {
 // Read-only grid data used by the direction kernel, all device pointers.
 struct DirGrid {
     int n_x, n_p;
+    int nnz;                                   // positions of the pattern of A (index checks)
     int zero_row;                              // n_x + n_p: a row of zeros in V
     // filled matrix A = L + U (CSR), its transposed values and 1/diagonal
     const int *col;
@@ -97,6 +98,7 @@ struct DirLaunch {
     double *HW;                // n_p x N column-major (ldhw)
     int64_t ldhw;
     unsigned phases;
+    int64_t ws_elems;          // doubles of V and of T each (0: not stated; index checks of the bounds build)
     int use_tail;              // dense tail in shared memory (needs T * ceil(N / n_cta) <= 4096)
     int use_reach;             // identity W: forward L sweep only over the reach of B's nonzeros (needs use_tail,
                                // and phases L and U in the same launch)
@@ -116,6 +118,7 @@ void launch_dirs_batch(const DirBatch& B, int max_T, cudaStream_t st);
 // Grid-wide power-flow evaluation data (per bus, original ids).
 struct PfGrid {
     int n_bus, n_x, ref;
+    int nnz_a, nnz_jp;                 // slots of A and of J_p (index checks)
     const int *yp, *yj, *ydiag;
     const double *G, *B;
     const int *qth, *qv, *ip_v, *ip_pg;
@@ -146,6 +149,7 @@ cudaError_t launch_jac_ad(const PfGrid& g, const PfState& s, const int* col_th, 
 // Fixed-pattern LU refactorisation data (device pointers).
 struct RfGrid {
     int n_x, t0, T;                    // dense trailing block [t0, n_x), T = n_x - t0
+    int nnz;                           // positions of A (index checks)
     double* tailD;                     // T x T row-major scratch of the tiled dense LU
     const int* tail_pos;               // (i, j) of the trailing block -> position in A, -1 if structurally zero
     const int *rf_lev_bus, *q0;

@@ -25,6 +25,7 @@ EXPORTS = ["rh_grid_create", "rh_grid_destroy", "rh_grid_dims", "rh_grid_symboli
            "rh_lagrangian_hessvec", "rh_hessvec_noalloc", "rh_hv_work_doubles", "rh_batch_hessvec",
            "rh_potrf", "rh_potrs", "rh_rto_step", "rh_set_jacobian_method", "rh_grid_coloring", "rh_jacobian",
            "rh_reduced_hessian", "rh_reduced_hessian_times", "rh_reduced_hessian_flops", "rh_fp64_fma_rate",
+           "rh_hessian_columns", "rh_bounds_check",
            "rh_last_error"]
 RH_JAC_ANALYTIC, RH_JAC_COLORED_AD = 0, 1
 
@@ -85,6 +86,8 @@ def load(build_if_missing: bool = True):
         "rh_adjoint": ([P, P, P, P], C.c_int),
         "rh_hessvec": ([P, P, I64, I32, P, I64, P, U32], C.c_int),
         "rh_hessian": ([P, I32, P, I64, P, U32], C.c_int),
+        "rh_hessian_columns": ([P, I32, I32, P, I64, P, U32], C.c_int),
+        "rh_bounds_check": ([I32, P, P], C.c_int),
         "rh_solve": ([P, P, I64, I32, I32, P, U32], C.c_int),
         "rh_refactor": ([P, P], C.c_int),
         "rh_lagrangian_hessvec": ([P, P, I64, I32, P, I64, P, U32], C.c_int),
@@ -257,6 +260,19 @@ class Grid:
             return out
         H = np.empty((self.n_p, self.n_p), order="F")
         _check(_lib.rh_hessian(self._h, int(block_n), _ptr(H), self.n_p, C.c_void_p(0), flags))
+        return H
+
+    def hessian_columns(self, col0, ncols, out=None, stream=None):
+        """Columns col0 .. col0 + ncols - 1 of H in one launch (rh_hessian_columns): a numpy
+        (n_p, ncols) column-major array, or ``out`` (a column-major CUDA tensor) when given."""
+        if out is not None and _is_device(out):
+            st = stream if stream is not None else _stream_of(out)
+            ld = out.stride(1) if ncols > 1 else self.n_p
+            _check(_lib.rh_hessian_columns(self._h, int(col0), int(ncols), _ptr(out), ld, st, RH_DEVICE_PTRS))
+            return out
+        H = np.empty((self.n_p, ncols), order="F")
+        _check(_lib.rh_hessian_columns(self._h, int(col0), int(ncols), _ptr(H), self.n_p, C.c_void_p(0),
+                                       RH_HOST_PTRS))
         return H
 
     def reduced_hessian(self, out=None, stream=None):

@@ -248,6 +248,9 @@ def measure_scenarios(n_scen=8, N=64, reps=10):
     from paper_2201_00241_gb300 import rh
     from paper_2201_00241_gb300.autotune import tune_width
     grids = [_ready("case1354", k) for k in range(n_scen)]
+    resolve = measure_scenario_resolves(grids)
+    for lg in grids:
+        lg.adjoint()
     items = []
     for k, lg in enumerate(grids):
         W = _colmajor(gg.random_directions(lg.n_p, N, 1000 + k))
@@ -276,7 +279,45 @@ def measure_scenarios(n_scen=8, N=64, reps=10):
                         f"N={N} random unit directions each",
             "plain_hvp_per_s": total / (t_plain * 1e-3), "batched_hvp_per_s": total / (t_batched * 1e-3),
             "plain_ms": t_plain, "batched_ms": t_batched, "width": width,
-            "width_ms": {str(k): v for k, v in width_ms.items()}, "batched_launch": "one rh_batch_hessvec, CUDA graph"}
+            "width_ms": {str(k): v for k, v in width_ms.items()}, "batched_launch": "one rh_batch_hessvec, CUDA graph",
+            "power_flow_resolve": resolve}
+
+
+def measure_scenario_resolves(grids, reps=7):
+    """Newton re-solves of the scenarios' power flows from the planted point (section 3.2,
+    reading R20): each grid alone with rh_powerflow, one after another, against all of them
+    in one rh_batch_powerflow call (host wall time, both synchronous)."""
+    from paper_2201_00241_gb300 import rh
+    import torch
+    x0 = [lg.plant().x for lg in grids]
+
+    def one_by_one():
+        its = []
+        for lg, x in zip(grids, x0):
+            _, it, _, _ = lg.powerflow(x, tol=1e-12, max_iter=20)
+            its.append(int(it))
+        return its
+
+    def batched():
+        _, its, _, st = rh.batch_powerflow(grids, x0=x0, tol=1e-12, max_iter=20)
+        assert (st == rh.RH_OK).all()
+        return [int(v) for v in its]
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            its = fn()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return float(np.median(ts)), its
+
+    t_seq, it_seq = timed(one_by_one)
+    t_bat, it_bat = timed(batched)
+    return {"sequential_ms": t_seq, "batched_ms": t_bat, "newton_iters": it_bat, "newton_iters_sequential": it_seq,
+            "note": "re-solve of every scenario from the planted point to ||g||_inf <= 1e-12: rh_powerflow per "
+                    "grid vs one rh_batch_powerflow (one host sync per iteration, graphs per active set)"}
 
 
 def measure_rto(n_updates=12):

@@ -147,6 +147,32 @@ rh_status rh_powerflow(rh_grid *grid, const double *x0, double tol, int32_t max_
                        double *x_out, int32_t *iters, double *resid);
 
 /*
+ * Newton power flow (section 3.2) for up to 32 grids of one topology at once,
+ * for instance the load scenarios of one network (each its own rh_grid, with its
+ * own loads and parameters): every Newton iteration evaluates the residuals and
+ * Jacobians of all items in one launch, refactors them together (one launch per
+ * level for all items: their patterns and schedules are the same), solves each
+ * item's Newton step in its own CTA, and reads all residuals and pivot flags in
+ * one copy: one host synchronisation per iteration for the whole batch.  The
+ * work of an iteration is replayed from CUDA graphs captured per set of items
+ * still iterating.  An item stops when ||g||_inf <= tol (status RH_OK), after
+ * max_iter steps or on a non-finite residual (RH_ENOCONV), or when a static pivot
+ * is below 1e-14 max|J_x| (RH_ESINGULAR); the others go on.
+ *   grids   n_items distinct grids with the same structure (created from the
+ *           same branch list and bus types) on one device; RH_EINVAL otherwise
+ *   x0      NULL, or n_items host pointers (each n_x, or NULL: continue from the
+ *           item's current state)
+ *   x_out   NULL, or n_items host pointers (each n_x, or NULL) for the final x
+ *   iters, resid, status   NULL or n_items entries each: Newton steps taken, final
+ *           ||g||_inf, and the item's status
+ * Synchronous.  Returns RH_OK if every item converged, else RH_ESINGULAR if any
+ * item met a bad pivot, else RH_ENOCONV.  Invalidates the items' adjoints.
+ */
+rh_status rh_batch_powerflow(int32_t n_items, rh_grid *const *grids, const double *const *x0, double tol,
+                             int32_t max_iter, double *const *x_out, int32_t *iters, double *resid,
+                             int32_t *status);
+
+/*
  * Per-state setup of the hot path at the current (x, p): Jacobian assembly
  * into the fixed LU pattern, LU refactorisation, first-order adjoint
  * lambda = -J_x^{-T} grad_x f (eq. 7), reduced gradient

@@ -4,9 +4,11 @@
 // sequencing, copies for host-pointer calls.  Every numerical step runs in the
 // kernels of kernels.cu.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -114,6 +116,12 @@ struct rh_grid {
     size_t stage_n = 0;
 
     bool adjoint_ready = false;
+    // batched Newton (rh_batch_powerflow): the grid's identity and structure, the
+    // captured per-iteration graphs of batches led by this grid, keyed by the items'
+    // identities and the set of items still iterating, and a status buffer
+    uint64_t uid = 0, topo_hash = 0;
+    std::map<std::string, cudaGraphExec_t> pf_graphs;
+    double *bstat_d = nullptr, *bstat_h = nullptr;
     cudaGraphExec_t adj_exec = nullptr;   // captured device work of rh_adjoint
     int adj_kernels = 0;                  // kernel nodes in that graph
     cudaEvent_t apply_done = nullptr;     // orders a tracking step's parameter update before later grid work
@@ -136,6 +144,8 @@ struct rh_grid {
         if (hess_exec) cudaGraphExecDestroy(hess_exec);
         adj_exec = nullptr;
         hess_exec = nullptr;
+        for (auto& kv : pf_graphs) cudaGraphExecDestroy(kv.second);
+        pf_graphs.clear();
     }
 
     ~rh_grid() {
@@ -144,6 +154,7 @@ struct rh_grid {
         for (cudaEvent_t e : {ev_fork, ev_join, ev_user, ev_d0, ev_d1, ev_v, ev_c})
             if (e) cudaEventDestroy(e);
         if (stream2) cudaStreamDestroy(stream2);
+        if (bstat_h) cudaFreeHost(bstat_h);
         for (void* p : allocs) cudaFree(p);
         if (V) cudaFree(V);
         if (T) cudaFree(T);
@@ -421,6 +432,25 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     std::string msg = rh::build_symbolic(d->n_bus, d->n_branch, d->from, d->to, d->r, d->x, d->b, d->bus_type,
                                          d->order_level_cost, g->S);
     if (!msg.empty()) return fail(RH_EINVAL, msg);
+    {
+        static std::atomic<uint64_t> next_uid{1};
+        g->uid = next_uid++;
+        // FNV-1a over the structure the batched refactorisation shares between grids
+        uint64_t h = 1469598103934665603ull;
+        auto mix = [&h](const void* p, size_t n) {
+            const unsigned char* b = (const unsigned char*)p;
+            for (size_t i = 0; i < n; i++) { h ^= b[i]; h *= 1099511628211ull; }
+        };
+        const auto& S = g->S;
+        const int dims[4] = {S.n_bus, S.n_x, S.n_p, S.t0};
+        mix(dims, sizeof dims);
+        for (const std::vector<int>* v : {&S.ebus, &S.rowptr, &S.col, &S.rf_lev_ptr, &S.rf_lev_bus, &S.rf_tgt_pos,
+                                          &S.rf_grp, &S.jac_dst, &S.yp, &S.yj})
+            mix(v->data(), v->size() * sizeof(int));
+        mix(S.rf_tgt_lev_ptr.data(), S.rf_tgt_lev_ptr.size() * sizeof(int64_t));
+        mix(S.rf_tgt_gptr.data(), S.rf_tgt_gptr.size() * sizeof(int64_t));
+        g->topo_hash = h;
+    }
     const auto& S = g->S;
     if (device < 0) {  // symbolic phase only: no device state
         *out = g.release();
@@ -927,6 +957,190 @@ rh_status enqueue_reduced_hessian(rh_grid* g, double* Hd, int64_t lh) {
 }  // namespace
 
 extern "C" {
+
+}  // extern "C"
+
+namespace {
+
+// One half of a batched Newton iteration for the items whose bit is set in `mask`
+// (enqueue only, on items[0]'s stream).  Phase 0: zero A and the maxima, residual
+// and Jacobians of every item, and their max |g| and pivot flags copied to the host.
+// Phase 1: refactorisation, the single solves' tail triangles, the Newton step
+// J_x dx = g and x -= dx.
+rh_status enqueue_batch_newton(rh_grid* const* items, int n, uint32_t mask, int phase) {
+    rh_grid* g0 = items[0];
+    const auto& S = g0->S;
+    cudaStream_t s = g0->stream;
+    std::vector<rh_grid*> act;
+    for (int i = 0; i < n; i++)
+        if (mask & (1u << i)) act.push_back(items[i]);
+    if (act.empty()) return RH_OK;
+    std::unique_ptr<rh::PfBatch> B(new rh::PfBatch());
+    B->n = (int)act.size();
+    B->max_bus = S.n_bus;
+    for (int k = 0; k < B->n; k++) {
+        rh_grid* g = act[k];
+        rh::PfBatchItem& it = B->it[k];
+        it.g = g->pf();
+        it.s = g->st();
+        it.A = g->A;
+        it.jpv = g->jpv;
+        it.x = g->v1;
+        it.umax = g->umax;
+        it.err = g->err;
+    }
+    if (phase == 0) {
+        for (rh_grid* g : act) {
+            RH_CUDA(cudaMemsetAsync(g->A, 0, sizeof(double) * S.col.size(), s));
+            RH_CUDA(cudaMemsetAsync(g->umax, 0, 2 * sizeof(unsigned long long), s));
+        }
+        rh::launch_pf_eval_batch(*B, s);
+        rh::launch_batch_status(*B, g0->bstat_d, s);
+        RH_CUDA(cudaMemcpyAsync(g0->bstat_h, g0->bstat_d, 2 * sizeof(double) * B->n, cudaMemcpyDeviceToHost, s));
+        RH_CUDA(cudaGetLastError());
+        return RH_OK;
+    }
+    for (rh_grid* g : act) RH_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
+    std::unique_ptr<rh::RfBatch> R(new rh::RfBatch());
+    R->n = B->n;
+    for (int k = 0; k < B->n; k++) R->g[k] = act[k]->rf();
+    RH_CUDA(rh::launch_refactor_batch(*R, S.rf_lev_ptr.data(), S.rf_tgt_lev_ptr.data(), S.rf_n_lev, s));
+    const int T = S.n_x - S.t0;
+    const int mode = rh::solve1_mode(S.n_x, T);
+    if (mode == 2) {
+        std::unique_ptr<rh::TriBatch> tb(new rh::TriBatch());
+        tb->n = B->n;
+        tb->T = T;
+        tb->t0 = S.t0;
+        for (int k = 0; k < B->n; k++) {
+            tb->pos[k] = act[k]->tail_pos;
+            tb->A[k] = act[k]->A;
+            tb->invdiag[k] = act[k]->invdiag;
+            tb->triL[k] = act[k]->triL;
+            tb->triU[k] = act[k]->triU;
+        }
+        rh::launch_tail_tri_batch(*tb, s);
+    }
+    if (mode > 0) {
+        std::unique_ptr<rh::Solve1Batch> sb(new rh::Solve1Batch());
+        sb->n = B->n;
+        for (int k = 0; k < B->n; k++) {
+            sb->g[k] = act[k]->dir();
+            sb->x[k] = act[k]->v1;
+        }
+        RH_CUDA(rh::launch_solve1_batch(*sb, rh::PH_L | rh::PH_U, mode == 2, S.n_x, T, s));
+    } else {
+        // x does not fit in one CTA's shared memory: the direction kernel solves each item
+        for (rh_grid* g : act) {
+            enqueue_factor_copies(g, s);
+            rh_status st = solve_one(g, rh::PH_L | rh::PH_U, s);
+            if (st) return st;
+        }
+    }
+    rh::launch_newton_update_batch(*B, s);
+    RH_CUDA(cudaGetLastError());
+    return RH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rh_status rh_batch_powerflow(int32_t n_items, rh_grid* const* grids, const double* const* x0, double tol,
+                             int32_t max_iter, double* const* x_out, int32_t* iters, double* resid,
+                             int32_t* status) {
+    if (n_items < 0 || n_items > rh::kMaxPfBatch || (n_items > 0 && !grids))
+        return fail(RH_EINVAL, "n_items must be in [0, 32] and grids non-NULL");
+    if (!(tol >= 0.0) || max_iter < 0) return fail(RH_EINVAL, "tol must be >= 0 and max_iter >= 0");
+    if (n_items == 0) return RH_OK;
+    rh_grid* g0 = grids[0];
+    for (int i = 0; i < n_items; i++) {
+        if (!grids[i]) return fail(RH_EINVAL, "item " + std::to_string(i) + ": NULL grid");
+        if (grids[i]->device < 0) return fail(RH_ESTATE, "item " + std::to_string(i) + ": symbolic-only grid");
+        if (grids[i]->device != g0->device || grids[i]->topo_hash != g0->topo_hash)
+            return fail(RH_EINVAL, "item " + std::to_string(i) + ": not the same topology and device as item 0");
+        for (int j = 0; j < i; j++)
+            if (grids[j] == grids[i]) return fail(RH_EINVAL, "a grid appears twice");
+    }
+    rh_status st = set_device(g0);
+    if (st) return st;
+    const auto& S = g0->S;
+    cudaStream_t s = g0->stream;
+    if (!g0->bstat_d) RH_CUDA(g0->alloc(g0->bstat_d, 2 * rh::kMaxPfBatch));
+    if (!g0->bstat_h) RH_CUDA(cudaMallocHost(&g0->bstat_h, 2 * rh::kMaxPfBatch * sizeof(double)));
+    // earlier work of every item is done; then the starting points and clean pivot flags
+    for (int i = 0; i < n_items; i++) {
+        rh_grid* g = grids[i];
+        RH_CUDA(cudaStreamSynchronize(g->stream));
+        g->adjoint_ready = false;
+        if (x0 && x0[i]) {
+            RH_CUDA(cudaMemcpyAsync(g->xbuf, x0[i], S.n_x * sizeof(double), cudaMemcpyHostToDevice, s));
+            k_set_x<<<nblk(S.n_bus, 128), 128, 0, s>>>(S.n_bus, g->ix_th, g->ix_v, g->xbuf, g->vm, g->va);
+        }
+        RH_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
+    }
+    RH_CUDA(cudaGetLastError());
+    std::vector<int> it(n_items, 0), stat(n_items, RH_ENOCONV);
+    std::vector<double> res(n_items, INFINITY);
+    uint32_t mask = n_items == 32 ? 0xffffffffu : ((1u << n_items) - 1u);
+    // the graph of one phase for one set of items, captured once and replayed
+    auto run = [&](uint32_t m, int phase) -> rh_status {
+        std::string key = std::to_string(phase) + ":" + std::to_string(m);
+        for (int i = 0; i < n_items; i++) key += ":" + std::to_string(grids[i]->uid);
+        auto f = g0->pf_graphs.find(key);
+        if (f == g0->pf_graphs.end()) {
+            cudaGraphExec_t ex = nullptr;
+            int nk = 0;
+            rh_status cs = capture_graph(g0, [&] { return enqueue_batch_newton(grids, n_items, m, phase); }, &ex, &nk);
+            if (cs) return cs;
+            f = g0->pf_graphs.emplace(key, ex).first;
+        }
+        RH_CUDA(cudaGraphLaunch(f->second, s));
+        return RH_OK;
+    };
+    while (mask) {
+        st = run(mask, 0);
+        if (st) return st;
+        RH_CUDA(cudaStreamSynchronize(s));          // the one host sync of the iteration
+        uint32_t next = 0;
+        for (int i = 0, k = 0; i < n_items; i++) {
+            if (!(mask & (1u << i))) continue;
+            double r = g0->bstat_h[2 * k];
+            const bool singular = g0->bstat_h[2 * k + 1] != 0.0;
+            k++;
+            if (S.n_x == 0) r = 0.0;
+            res[i] = r;
+            if (singular) stat[i] = RH_ESINGULAR;
+            else if (r <= tol) stat[i] = RH_OK;
+            else if (it[i] >= max_iter || !std::isfinite(r)) stat[i] = RH_ENOCONV;
+            else next |= 1u << i;
+        }
+        mask = next;
+        if (!mask) break;
+        st = run(mask, 1);
+        if (st) return st;
+        for (int i = 0; i < n_items; i++)
+            if (mask & (1u << i)) it[i]++;
+    }
+    rh_status worst = RH_OK;
+    for (int i = 0; i < n_items; i++) {
+        rh_grid* g = grids[i];
+        if (iters) iters[i] = it[i];
+        if (resid) resid[i] = res[i];
+        if (status) status[i] = stat[i];
+        if (stat[i] == RH_ESINGULAR) worst = RH_ESINGULAR;
+        else if (stat[i] == RH_ENOCONV && worst == RH_OK) worst = RH_ENOCONV;
+        if (x_out && x_out[i]) {
+            k_get_x<<<nblk(S.n_bus, 128), 128, 0, s>>>(S.n_bus, g->ix_th, g->ix_v, g->vm, g->va, g->xbuf);
+            RH_CUDA(cudaGetLastError());
+            RH_CUDA(cudaMemcpyAsync(x_out[i], g->xbuf, S.n_x * sizeof(double), cudaMemcpyDeviceToHost, s));
+        }
+    }
+    RH_CUDA(cudaStreamSynchronize(s));
+    if (worst == RH_ESINGULAR) return fail(worst, "a static pivot below 1e-14 max|J_x| (see status[])");
+    if (worst == RH_ENOCONV) return fail(worst, "Newton did not reach the tolerance for every item (see status[])");
+    return RH_OK;
+}
 
 rh_status rh_adjoint(rh_grid* g, double* F, double* lambda, double* grad) {
     if (!g) return fail(RH_EINVAL, "NULL grid");

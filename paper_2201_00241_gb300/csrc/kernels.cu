@@ -95,7 +95,7 @@ __device__ __forceinline__ void jac_store(const PfGrid& g, int t, const double (
     }
 }
 
-__global__ void k_pf_eval(PfGrid g, PfState s, double* gres, double* A, double* jpv,
+__device__ __forceinline__ void k_pf_eval_body(PfGrid g, PfState s, double* gres, double* A, double* jpv,
                           unsigned long long* gmax, unsigned long long* jmax, int want_jac) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n_bus) return;
@@ -155,13 +155,16 @@ __global__ void k_pf_eval(PfGrid g, PfState s, double* gres, double* A, double* 
     if (g.ip_pg[i] >= 0) jpv[g.pg_slot[i]] = -1.0;
     atomicMax(jmax, jm);
 }
+__global__ void k_pf_eval(PfGrid g, PfState s, double* gres, double* A, double* jpv,
+                          unsigned long long* gmax, unsigned long long* jmax, int want_jac) { k_pf_eval_body(g, s, gres, A, jpv, gmax, jmax, want_jac); }
 
-__global__ void k_newton_update(PfGrid g, PfState s, const double* dx) {
+__device__ __forceinline__ void k_newton_update_body(PfGrid g, PfState s, const double* dx) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n_bus) return;
     if (g.qth[i] >= 0) s.va[i] -= dx[g.qth[i]];
     if (g.qv[i] >= 0) s.vm[i] -= dx[g.qv[i]];
 }
+__global__ void k_newton_update(PfGrid g, PfState s, const double* dx) { k_newton_update_body(g, s, dx); }
 
 // ---------------------------------------------------------------------------
 // coloured forward-mode Jacobian (section 4.2.2, Fig. 2)
@@ -274,7 +277,7 @@ __global__ void __launch_bounds__(128) k_jac_ad(PfGrid g, PfState s, const int* 
 //   U row of v:    u_vj = a_vj - l_vt u_tj,
 //   L columns:     l_it = a_it / u_tt,  l_iv = (a_iv - l_it u_tv) / u_vv
 // for every later variable i, j of the bus's pattern (a PV bus has theta only).
-__global__ void k_rf_pivot(RfGrid g, int b0, int nb) {
+__device__ __forceinline__ void k_rf_pivot_body(RfGrid g, int b0, int nb) {
     const int lane = threadIdx.x & 31;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= nb) return;
@@ -321,6 +324,7 @@ __global__ void k_rf_pivot(RfGrid g, int b0, int nb) {
         }
     }
 }
+__global__ void k_rf_pivot(RfGrid g, int b0, int nb) { k_rf_pivot_body(g, b0, nb); }
 
 // Update step of one level: every target entry a_ij of the level subtracts
 // sum_k l_ik u_kj over the buses k of the level whose pattern holds i and j
@@ -331,7 +335,7 @@ __global__ void k_rf_pivot(RfGrid g, int b0, int nb) {
 // and the pivot steps of all sparse buses run once, in one launch, at the end.
 // No entry a group reads is a target of the same level (its bus would depend
 // on the level's own buses).
-__global__ void k_rf_update(RfGrid g, int64_t t0, int64_t nt) {
+__device__ __forceinline__ void k_rf_update_body(RfGrid g, int64_t t0, int64_t nt) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
     t += t0;
@@ -359,6 +363,7 @@ __global__ void k_rf_update(RfGrid g, int64_t t0, int64_t nt) {
     const int p = g.tgt_pos[t];
     if (inb(p, g.nnz)) g.A[p] -= acc;
 }
+__global__ void k_rf_update(RfGrid g, int64_t t0, int64_t nt) { k_rf_update_body(g, t0, nt); }
 
 // Dense trailing block [t0, n_x) as a tiled right-looking LU over TB x TB tiles
 // of a row-major scratch copy, spread over many SMs (GB300 runs FP64 on the
@@ -373,13 +378,14 @@ __global__ void k_rf_update(RfGrid g, int64_t t0, int64_t nt) {
 // never writes the row or column it reads: one barrier per step.
 constexpr int kTailTB = 16;
 
-__global__ void k_tail_gather(RfGrid g) {
+__device__ __forceinline__ void k_tail_gather_body(RfGrid g) {
     const int T = g.T;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= T * T) return;
     const int p = g.tail_pos[idx];
     g.tailD[idx] = (p >= 0 && inb(p, g.nnz)) ? g.A[p] : 0.0;
 }
+__global__ void k_tail_gather(RfGrid g) { k_tail_gather_body(g); }
 
 // Eliminates the tile held in Dk (unit-padded beyond kb) and stores it at
 // (k0, k0): U on and above the diagonal, L = a_rj / u_jj below it.
@@ -400,7 +406,7 @@ __device__ __forceinline__ void tail_factor_store(const RfGrid& g, int k0, int k
     if (r < kb && c < kb) g.tailD[(size_t)(k0 + r) * T + k0 + c] = r > c ? Dk[r][c] * Inv[c] : Dk[r][c];
 }
 
-__global__ void __launch_bounds__(256) k_tail_diag0(RfGrid g) {
+__device__ __forceinline__ void k_tail_diag0_body(RfGrid g) {
     constexpr int TB = kTailTB;
     __shared__ double Dk[TB][TB + 1];
     __shared__ double Inv[TB];
@@ -409,8 +415,9 @@ __global__ void __launch_bounds__(256) k_tail_diag0(RfGrid g) {
     __syncthreads();
     tail_factor_store(g, 0, kb, Dk, Inv);
 }
+__global__ void __launch_bounds__(256) k_tail_diag0(RfGrid g) { k_tail_diag0_body(g); }
 
-__global__ void __launch_bounds__(256) k_tail_panel(RfGrid g, int k) {
+__device__ __forceinline__ void k_tail_panel_body(RfGrid g, int k) {
     constexpr int TB = kTailTB;
     __shared__ double F[TB][TB + 1];      // the factored A_kk: U above, L below (unit diagonal)
     __shared__ double X[TB][TB + 1];
@@ -448,8 +455,9 @@ __global__ void __launch_bounds__(256) k_tail_panel(RfGrid g, int k) {
     }
     if (r < kb && c < ob) D[(size_t)(k0 + r) * T + o0 + c] = X[r][c];
 }
+__global__ void __launch_bounds__(256) k_tail_panel(RfGrid g, int k) { k_tail_panel_body(g, k); }
 
-__global__ void __launch_bounds__(256) k_tail_update(RfGrid g, int k) {
+__device__ __forceinline__ void k_tail_update_body(RfGrid g, int k) {
     constexpr int TB = kTailTB;
     __shared__ double Li[TB][TB + 1];
     __shared__ double Uj[TB][TB + 1];
@@ -477,8 +485,9 @@ __global__ void __launch_bounds__(256) k_tail_update(RfGrid g, int k) {
     __syncthreads();
     tail_factor_store(g, i0, ib, Li, Inv);
 }
+__global__ void __launch_bounds__(256) k_tail_update(RfGrid g, int k) { k_tail_update_body(g, k); }
 
-__global__ void k_tail_scatter(RfGrid g) {
+__device__ __forceinline__ void k_tail_scatter_body(RfGrid g) {
     const int T = g.T;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= T * T) return;
@@ -492,6 +501,7 @@ __global__ void k_tail_scatter(RfGrid g) {
         if (!(fabs(v) > tau)) atomicOr(g.err, 1);
     }
 }
+__global__ void k_tail_scatter(RfGrid g) { k_tail_scatter_body(g); }
 
 // Transposed copies of the factor values and of J_p, and the unit-diagonal
 // factors of the direction kernel.  With D = diag(U), J_x = L U = D L'' U' where
@@ -539,7 +549,7 @@ __global__ void k_scale_rows(int n, int N, const double* __restrict__ s, double*
 
 // The dense tail's triangles: for the single solves (columns of U scaled by
 // 1/u_jj), and of the unit-diagonal factors L'', U' for the direction kernel.
-__global__ void k_build_tail(int T, int t0, const int* __restrict__ pos, const double* __restrict__ A,
+__device__ __forceinline__ void k_build_tail_body(int T, int t0, const int* __restrict__ pos, const double* __restrict__ A,
                              const double* __restrict__ invdiag, double* triL, double* triU, double* triUt,
                              double* triLt, double* triLd, double* triUd, double* triUtd, double* triLtd) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -563,6 +573,9 @@ __global__ void k_build_tail(int T, int t0, const int* __restrict__ pos, const d
         triLtd[o] = aji * A[pos[i * T + i]] * ij;   // (L''^T)_ij = L''_ji
     }
 }
+__global__ void k_build_tail(int T, int t0, const int* __restrict__ pos, const double* __restrict__ A,
+                             const double* __restrict__ invdiag, double* triL, double* triU, double* triUt,
+                             double* triLt, double* triLd, double* triUd, double* triUtd, double* triLtd) { k_build_tail_body(T, t0, pos, A, invdiag, triL, triU, triUt, triLt, triLd, triUd, triUtd, triLtd); }
 
 // ---------------------------------------------------------------------------
 // the direction kernel: Algorithm 2 for a slice of directions per CTA
@@ -1506,7 +1519,7 @@ __device__ void sweep1_bwd(const DirGrid& g, const LevelSet& ls, const double* _
 // level per variable.
 constexpr int kSolve1Part = 2048;
 constexpr int kSolve1Threads = 768;   // 85 registers per thread: room for the prefetched level data
-__global__ void __launch_bounds__(kSolve1Threads, 1) k_solve1(DirGrid g, double* x, unsigned phases, int use_tail) {
+__device__ __forceinline__ void k_solve1_body(DirGrid g, double* x, unsigned phases, int use_tail) {
     extern __shared__ double X[];
     double* tri = X + g.n_x;
     double* part = tri + (use_tail ? (size_t)g.T * (g.T - 1) / 2 : 0);
@@ -1540,6 +1553,7 @@ __global__ void __launch_bounds__(kSolve1Threads, 1) k_solve1(DirGrid g, double*
     __syncthreads();
     for (int q = threadIdx.x; q < g.n_x; q += blockDim.x) x[q] = X[q];
 }
+__global__ void __launch_bounds__(kSolve1Threads, 1) k_solve1(DirGrid g, double* x, unsigned phases, int use_tail) { k_solve1_body(g, x, phases, use_tail); }
 
 // ---------------------------------------------------------------------------
 // adjoint (eq. 7) and the per-state second-order coefficients
@@ -1687,6 +1701,51 @@ __global__ void k_gather_rows(int n_rows, int N, const int* map, const double* s
 
 int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
+// ---------------------------------------------------------------------------
+// Newton power flow over several grids of one topology: item blockIdx.y
+// ---------------------------------------------------------------------------
+__global__ void k_pf_eval_batch(PfBatch B) {
+    const PfBatchItem& it = B.it[blockIdx.y];
+    k_pf_eval_body(it.g, it.s, it.x, it.A, it.jpv, it.umax, it.umax + 1, 1);
+}
+
+__global__ void k_batch_status(PfBatch B, double* out) {
+    const int i = threadIdx.x;
+    if (i >= B.n) return;
+    out[2 * i] = __longlong_as_double((long long)B.it[i].umax[0]);
+    out[2 * i + 1] = (double)B.it[i].err[0];
+}
+
+__global__ void k_newton_update_batch(PfBatch B) {
+    const PfBatchItem& it = B.it[blockIdx.y];
+    k_newton_update_body(it.g, it.s, it.x);
+}
+
+__global__ void k_rf_update_batch(RfBatch B, int64_t t0, int64_t nt) { k_rf_update_body(B.g[blockIdx.y], t0, nt); }
+__global__ void k_rf_pivot_batch(RfBatch B, int b0, int nb) { k_rf_pivot_body(B.g[blockIdx.y], b0, nb); }
+__global__ void k_tail_gather_batch(RfBatch B) { k_tail_gather_body(B.g[blockIdx.y]); }
+__global__ void __launch_bounds__(256) k_tail_diag0_batch(RfBatch B) { k_tail_diag0_body(B.g[blockIdx.y]); }
+__global__ void __launch_bounds__(256) k_tail_panel_batch(RfBatch B, int k) { k_tail_panel_body(B.g[blockIdx.y], k); }
+__global__ void __launch_bounds__(256) k_tail_update_batch(RfBatch B, int k) { k_tail_update_body(B.g[blockIdx.y], k); }
+__global__ void k_tail_scatter_batch(RfBatch B) { k_tail_scatter_body(B.g[blockIdx.y]); }
+
+// the single solves' tail triangles: L (unit lower) and U with column j scaled by 1/u_jj
+__global__ void k_tail_tri_batch(TriBatch B) {
+    const int i = blockIdx.y, T = B.T;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= T * T) return;
+    const int r = idx / T, c = idx - r * T;
+    if (r == c) return;
+    const int p = B.pos[i][idx];
+    const double a = p >= 0 ? B.A[i][p] : 0.0;
+    if (r > c) B.triL[i][c * (T - 1) - c * (c - 1) / 2 + (r - c - 1)] = a;
+    else B.triU[i][c * (c - 1) / 2 + r] = a * B.invdiag[i][B.t0 + c];
+}
+
+__global__ void __launch_bounds__(kSolve1Threads, 1) k_solve1_batch(Solve1Batch B, unsigned phases, int use_tail) {
+    k_solve1_body(B.g[blockIdx.x], B.x[blockIdx.x], phases, use_tail);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1755,7 +1814,8 @@ cudaError_t prepare_kernels() {
     if (g_prepared[dev]) return cudaSuccess;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const void* fns[3] = {(const void*)k_dirs, (const void*)k_solve1, (const void*)k_dirs_batch};
+    const void* fns[4] = {(const void*)k_dirs, (const void*)k_solve1, (const void*)k_dirs_batch,
+                          (const void*)k_solve1_batch};
     for (const void* f : fns) {
         cudaFuncAttributes fa;
         e = cudaFuncGetAttributes(&fa, f);
@@ -1874,6 +1934,57 @@ void launch_scatter_rows(int n_rows, int N, const int* map, const double* src, i
                          int64_t ldd, double scale_x, int n_x, cudaStream_t st) {
     int64_t n = (int64_t)n_rows * N;
     if (n > 0) k_scatter_rows<<<blocks_for(n, 256), 256, 0, st>>>(n_rows, N, map, src, lds, dst, ldd, scale_x, n_x);
+}
+
+void launch_pf_eval_batch(const PfBatch& B, cudaStream_t st) {
+    if (B.n > 0 && B.max_bus > 0)
+        k_pf_eval_batch<<<dim3((unsigned)blocks_for(B.max_bus, 64), (unsigned)B.n), 64, 0, st>>>(B);
+}
+
+void launch_batch_status(const PfBatch& B, double* out, cudaStream_t st) {
+    if (B.n > 0) k_batch_status<<<1, 32, 0, st>>>(B, out);
+}
+
+void launch_newton_update_batch(const PfBatch& B, cudaStream_t st) {
+    if (B.n > 0 && B.max_bus > 0)
+        k_newton_update_batch<<<dim3((unsigned)blocks_for(B.max_bus, 128), (unsigned)B.n), 128, 0, st>>>(B);
+}
+
+cudaError_t launch_refactor_batch(const RfBatch& B, const int* lev_ptr_host, const int64_t* tgt_lev_ptr_host,
+                                  int n_lev, cudaStream_t st) {
+    if (B.n <= 0) return cudaSuccess;
+    const unsigned n = (unsigned)B.n;
+    for (int lev = 0; lev < n_lev; lev++) {
+        int64_t t0 = tgt_lev_ptr_host[lev], nt = tgt_lev_ptr_host[lev + 1] - t0;
+        if (nt > 0) k_rf_update_batch<<<dim3((unsigned)blocks_for(nt, 256), n), 256, 0, st>>>(B, t0, nt);
+    }
+    const int nb = lev_ptr_host[n_lev];
+    if (nb > 0) k_rf_pivot_batch<<<dim3((unsigned)blocks_for((int64_t)nb * 32, 128), n), 128, 0, st>>>(B, 0, nb);
+    const int T = B.g[0].T;
+    if (T > 0) {
+        const int TT = T * T, nt = (T + kTailTB - 1) / kTailTB;
+        k_tail_gather_batch<<<dim3((unsigned)blocks_for(TT, 256), n), 256, 0, st>>>(B);
+        k_tail_diag0_batch<<<dim3(1, n), 256, 0, st>>>(B);
+        for (int k = 0; k < nt - 1; k++) {
+            const int m = nt - k - 1;
+            k_tail_panel_batch<<<dim3((unsigned)(2 * m), n), 256, 0, st>>>(B, k);
+            k_tail_update_batch<<<dim3((unsigned)(m * m), n), 256, 0, st>>>(B, k);
+        }
+        k_tail_scatter_batch<<<dim3((unsigned)blocks_for(TT, 256), n), 256, 0, st>>>(B);
+    }
+    return cudaGetLastError();
+}
+
+void launch_tail_tri_batch(const TriBatch& B, cudaStream_t st) {
+    if (B.n > 0 && B.T > 1)
+        k_tail_tri_batch<<<dim3((unsigned)blocks_for((int64_t)B.T * B.T, 256), (unsigned)B.n), 256, 0, st>>>(B);
+}
+
+cudaError_t launch_solve1_batch(const Solve1Batch& B, unsigned phases, bool use_tail, int n_x, int T,
+                                cudaStream_t st) {
+    if (B.n <= 0) return cudaSuccess;
+    k_solve1_batch<<<B.n, kSolve1Threads, solve1_smem(n_x, T, use_tail), st>>>(B, phases, use_tail ? 1 : 0);
+    return cudaGetLastError();
 }
 
 void launch_gather_rows(int n_rows, int N, const int* map, const double* src, int64_t lds, double* dst,

@@ -193,6 +193,48 @@ cudaError_t launch_solve1(const DirGrid& g, double* x, unsigned phases, bool use
 // the forward solve L y = b in place on the vector y (b on entry).
 // launch_potrs: work holds n * nrhs doubles; with forward = false it only runs
 // the backward sweep L^T X = work, writing X into B.
+// ---- Newton power flow over several grids of one topology (load scenarios) ----
+// Every batched launch takes item i from blockIdx.y (blockIdx.x for the solve):
+// the grids share their symbolic data, so every level range is the same for all.
+constexpr int kMaxPfBatch = 32;
+struct PfBatchItem {
+    PfGrid g;
+    PfState s;
+    double *A, *jpv;            // J_x values (in A's slots), J_p values
+    double* x;                  // residual in, Newton step out (internal order)
+    unsigned long long* umax;   // max |g|, max |J_x| as ordered bits
+    int* err;                   // pivot flag of the refactorisation
+};
+struct PfBatch {
+    int n, max_bus;
+    PfBatchItem it[kMaxPfBatch];
+};
+struct RfBatch {
+    int n;
+    RfGrid g[kMaxPfBatch];
+};
+struct TriBatch {
+    int n, T, t0;
+    const int* pos[kMaxPfBatch];
+    const double *A[kMaxPfBatch], *invdiag[kMaxPfBatch];
+    double *triL[kMaxPfBatch], *triU[kMaxPfBatch];
+};
+struct Solve1Batch {
+    int n;
+    DirGrid g[kMaxPfBatch];
+    double* x[kMaxPfBatch];
+};
+// residual and Jacobian of every item (A and umax zeroed by the caller)
+void launch_pf_eval_batch(const PfBatch& B, cudaStream_t st);
+// out[2 i] = max |g| of item i, out[2 i + 1] = its pivot flag
+void launch_batch_status(const PfBatch& B, double* out, cudaStream_t st);
+cudaError_t launch_refactor_batch(const RfBatch& B, const int* lev_ptr_host, const int64_t* tgt_lev_ptr_host,
+                                  int n_lev, cudaStream_t st);
+// the dense tail's triangles of the single solves (L, and U with columns scaled by 1/u_jj)
+void launch_tail_tri_batch(const TriBatch& B, cudaStream_t st);
+cudaError_t launch_solve1_batch(const Solve1Batch& B, unsigned phases, bool use_tail, int n_x, int T, cudaStream_t st);
+void launch_newton_update_batch(const PfBatch& B, cudaStream_t st);
+
 int dense_tile(int n);
 cudaError_t launch_potrf(int n, double* A, int64_t lda, int* info, double* y, cudaStream_t s);
 cudaError_t launch_potrs(int n, const double* L, int64_t ldl, double* B, int64_t ldb, int nrhs, double* work,

@@ -25,7 +25,7 @@ EXPORTS = ["rh_grid_create", "rh_grid_destroy", "rh_grid_dims", "rh_grid_symboli
            "rh_lagrangian_hessvec", "rh_hessvec_noalloc", "rh_hv_work_doubles", "rh_batch_hessvec",
            "rh_potrf", "rh_potrs", "rh_rto_step", "rh_set_jacobian_method", "rh_grid_coloring", "rh_jacobian",
            "rh_reduced_hessian", "rh_reduced_hessian_times", "rh_reduced_hessian_flops", "rh_fp64_fma_rate",
-           "rh_hessian_columns", "rh_bounds_check",
+           "rh_hessian_columns", "rh_bounds_check", "rh_batch_powerflow",
            "rh_last_error"]
 RH_JAC_ANALYTIC, RH_JAC_COLORED_AD = 0, 1
 
@@ -88,6 +88,7 @@ def load(build_if_missing: bool = True):
         "rh_hessian": ([P, I32, P, I64, P, U32], C.c_int),
         "rh_hessian_columns": ([P, I32, I32, P, I64, P, U32], C.c_int),
         "rh_bounds_check": ([I32, P, P], C.c_int),
+        "rh_batch_powerflow": ([I32, P, P, D, I32, P, P, P, P], C.c_int),
         "rh_solve": ([P, P, I64, I32, I32, P, U32], C.c_int),
         "rh_refactor": ([P, P], C.c_int),
         "rh_lagrangian_hessvec": ([P, P, I64, I32, P, I64, P, U32], C.c_int),
@@ -424,6 +425,35 @@ def batch_hessvec(items, width: int = 0, stream=None):
         import torch
         stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     _check(lib.rh_batch_hessvec(len(items), arr, int(width), stream))
+
+
+def batch_powerflow(grids, x0=None, tol=1e-12, max_iter=20):
+    """Newton power flow for several grids of one topology at once (rh_batch_powerflow).
+
+    x0: None, or one starting point per grid (numpy n_x, or None to continue from the
+    grid's state).  Returns (xs, iters, resid, status) per grid; raises nothing for
+    items that did not converge: their status says so."""
+    lib = load()
+    n = len(grids)
+    hs = (C.c_void_p * n)(*[g._h.value if isinstance(g._h, C.c_void_p) else g._h for g in grids])
+    keep = []
+    x0p = None
+    if x0 is not None:
+        x0p = (C.c_void_p * n)()
+        for i, x in enumerate(x0):
+            if x is not None:
+                a = _f64(x)
+                keep.append(a)
+                x0p[i] = a.ctypes.data
+    xs = [np.empty(g.n_x) for g in grids]
+    xop = (C.c_void_p * n)(*[x.ctypes.data for x in xs])
+    iters = np.zeros(n, np.int32)
+    resid = np.zeros(n)
+    status = np.zeros(n, np.int32)
+    st = lib.rh_batch_powerflow(n, hs, x0p, float(tol), int(max_iter), xop, _ptr(iters), _ptr(resid), _ptr(status))
+    if st not in (RH_OK, RH_ENOCONV, RH_ESINGULAR):
+        _check(st)
+    return xs, iters, resid, status
 
 
 def work_doubles(grid, N: int) -> int:

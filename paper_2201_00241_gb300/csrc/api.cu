@@ -86,6 +86,12 @@ struct rh_grid {
     int *rf_lev_bus = nullptr, *rf_tgt_pos = nullptr, *rf_grp = nullptr;
     int64_t* rf_tgt_gptr = nullptr;
     int *jp_ptr = nullptr, *jp_col = nullptr, *jpt_ptr = nullptr, *jpt_row = nullptr, *jpt_src = nullptr;
+    // identity W over all n_p columns: direction j takes column hcolmap[j], the columns in the
+    // postorder of their generator buses in the elimination tree, so that the few
+    // directions of a CTA share most of their reach; and the CTAs' reach, per CTA count
+    int* hcolmap = nullptr;
+    std::vector<int> colmap;                    // host copy
+    std::map<int, rh::ReachSched*> reach_dev;   // device structs, keyed by the launch's CTA count
     int *tp_bus = nullptr, *uth = nullptr, *uv = nullptr, *inc_ptr = nullptr, *inc_nb = nullptr;
     int* tp_l0 = nullptr;   // per bus: position of (v, theta) in At for a PQ bus of forward level 0, else -1
     int *inc_uth = nullptr, *inc_uv = nullptr, *gref_row = nullptr, *pg_row = nullptr, *xmap = nullptr;
@@ -239,6 +245,42 @@ struct rh_grid {
 
 namespace {
 
+// The order of the identity columns in full-Hessian launches: by the lowest
+// postorder, in the elimination tree, of the buses of a column's J_p rows (parent:
+// the first later bus of a bus's pattern; children and roots visited in ascending
+// position; ties keep the column order).  The directions of one CTA then come from
+// one part of the tree and share most of their reach.
+std::vector<int> tree_column_order(const rh::Symbolic& S) {
+    const int ne = S.n_elim, np = S.n_p;
+    std::vector<std::vector<int>> kids(ne);
+    std::vector<int> roots, post(ne, 0), bpos(S.n_x);
+    for (int k = 0; k < ne; k++) {
+        if (S.colpat[k].empty()) roots.push_back(k);
+        else kids[S.colpat[k][0]].push_back(k);
+        for (int t = 0; t < S.nv[k]; t++) bpos[S.q0[k] + t] = k;
+    }
+    int cnt = 0;
+    std::vector<std::pair<int, size_t>> stk;
+    for (auto r = roots.rbegin(); r != roots.rend(); ++r) stk.emplace_back(*r, 0);
+    while (!stk.empty()) {
+        auto& top = stk.back();
+        if (top.second < kids[top.first].size()) {
+            const int c = kids[top.first][top.second++];
+            stk.emplace_back(c, 0);
+        } else {
+            post[top.first] = cnt++;
+            stk.pop_back();
+        }
+    }
+    std::vector<int> anchor(np, ne), cm(np);
+    for (int j = 0; j < np; j++) {
+        for (int t = S.jpt_ptr[j]; t < S.jpt_ptr[j + 1]; t++) anchor[j] = std::min(anchor[j], post[bpos[S.jpt_row[t]]]);
+        cm[j] = j;
+    }
+    std::stable_sort(cm.begin(), cm.end(), [&](int a, int b) { return anchor[a] < anchor[b]; });
+    return cm;
+}
+
 rh_status set_device(const rh_grid* g) {
     if (g->device < 0) return fail(RH_ESTATE, "grid was created without a device (symbolic only)");
     RH_CUDA(cudaSetDevice(g->device));
@@ -324,6 +366,89 @@ rh_status assemble_and_factor(rh_grid* g) {
 }
 
 // n_cta > 0 caps the CTA count (the default is one per slot of the device)
+// The reach of every CTA of an identity-W launch of all n_p directions on n_cta CTAs
+// (columns through hcolmap), built on the host once per CTA count: for CTA c, the
+// buses of its J_p columns and their ancestors in the sparse part, as forward slots
+// grouped by level (PQ buses first, then longer rows, like the full schedule), and
+// the mask of their rows (seed rows in the dense tail included, as the run-time
+// mask has them).  Must be called outside stream capture (it allocates and copies).
+rh_status reach_schedule(rh_grid* g, int n_cta, rh::ReachSched** out) {
+    *out = nullptr;
+    auto f = g->reach_dev.find(n_cta);
+    if (f != g->reach_dev.end()) {
+        *out = f->second;
+        return RH_OK;
+    }
+    const auto& S = g->S;
+    const int np = S.n_p, ne = S.n_elim, words = (S.n_x + 31) / 32;
+    const std::vector<int>& cm = g->colmap;
+    std::vector<int> bpos(S.n_x);
+    for (int k = 0; k < ne; k++)
+        for (int t = 0; t < S.nv[k]; t++) bpos[S.q0[k] + t] = k;
+    std::vector<int> nlev(n_cta), lev0(n_cta), ptr, mx;
+    std::vector<int4> slots;
+    std::vector<unsigned> masks((size_t)n_cta * words, 0u);
+    std::vector<char> in(ne);
+    std::vector<int> sel;
+    for (int c = 0; c < n_cta; c++) {
+        const int c0 = (int)((int64_t)c * np / n_cta), c1 = (int)((int64_t)(c + 1) * np / n_cta);
+        std::fill(in.begin(), in.end(), 0);
+        unsigned* m = masks.data() + (size_t)c * words;
+        for (int j = c0; j < c1; j++)
+            for (int t = S.jpt_ptr[cm[j]]; t < S.jpt_ptr[cm[j] + 1]; t++) {
+                const int k = bpos[S.jpt_row[t]];
+                in[k] = 1;
+                for (int u = 0; u < S.nv[k]; u++) m[(S.q0[k] + u) >> 5] |= 1u << ((S.q0[k] + u) & 31);
+            }
+        sel.clear();
+        for (int k = 0; k < S.tail_bus0; k++) {
+            if (!in[k]) continue;
+            sel.push_back(k);
+            for (int u = 0; u < S.nv[k]; u++) m[(S.q0[k] + u) >> 5] |= 1u << ((S.q0[k] + u) & 31);
+            if (!S.colpat[k].empty() && S.colpat[k][0] < S.tail_bus0) in[S.colpat[k][0]] = 1;
+        }
+        auto ext = [&](int k) { return S.diagpos[S.q0[k]] - S.rowptr[S.q0[k]]; };
+        std::stable_sort(sel.begin(), sel.end(), [&](int a, int b) {
+            if (S.flevel[a] != S.flevel[b]) return S.flevel[a] < S.flevel[b];
+            if (S.nv[a] != S.nv[b]) return S.nv[a] > S.nv[b];
+            return ext(a) > ext(b);
+        });
+        lev0[c] = (int)mx.size();
+        int cur = -1;
+        for (int k : sel) {
+            if (S.flevel[k] != cur) {
+                ptr.push_back((int)slots.size());
+                mx.push_back(0);
+                cur = S.flevel[k];
+            }
+            const int q = S.q0[k];
+            slots.push_back(make_int4(q, ext(k), S.rowptr[q], S.nv[k] == 2 ? S.rowptr[q + 1] : -1));
+            mx.back() = std::max(mx.back(), ext(k));
+        }
+        ptr.push_back((int)slots.size());
+        nlev[c] = (int)mx.size() - lev0[c];
+    }
+    rh::ReachSched h;
+    h.n_cta = n_cta;
+    h.words = words;
+    int *d_nlev, *d_lev0, *d_ptr, *d_mx;
+    int4* d_slots;
+    unsigned* d_masks;
+    RH_CUDA(g->upload(d_nlev, nlev));
+    RH_CUDA(g->upload(d_lev0, lev0));
+    RH_CUDA(g->upload(d_ptr, ptr));
+    RH_CUDA(g->upload(d_mx, mx));
+    RH_CUDA(g->upload(d_slots, slots));
+    RH_CUDA(g->upload(d_masks, masks));
+    h.nlev = d_nlev; h.lev0 = d_lev0; h.ptr = d_ptr; h.maxext = d_mx; h.slots = d_slots; h.masks = d_masks;
+    rh::ReachSched* d = nullptr;
+    RH_CUDA(g->alloc(d, 1));
+    RH_CUDA(cudaMemcpy(d, &h, sizeof(h), cudaMemcpyHostToDevice));
+    g->reach_dev[n_cta] = d;
+    *out = d;
+    return RH_OK;
+}
+
 rh_status dirs(rh_grid* g, int N, int64_t ld, double* V, double* T, const double* W, int64_t ldw, int col0,
                double* HW, int64_t ldhw, unsigned phases, cudaStream_t s, int n_cta = 0) {
     rh::DirLaunch L;
@@ -343,6 +468,25 @@ rh_status dirs(rh_grid* g, int N, int64_t ld, double* V, double* T, const double
     L.ws_elems = V == g->V ? (int64_t)g->ws_elems : (V == g->v1 ? (int64_t)g->rows() : 0);
     L.use_tail = rh::dirs_tail_fits(g->S.n_x - g->S.t0, N, L.n_cta) ? 1 : 0;
     L.use_reach = (L.use_tail && !W && (phases & rh::PH_WLOAD) && (phases & rh::PH_L) && (phases & rh::PH_U)) ? 1 : 0;
+    // all n_p identity columns: in the tree order of hcolmap, with each CTA's reach precomputed
+    const bool all_cols = !W && col0 == 0 && N == g->S.n_p && g->hcolmap;
+    L.colmap = (all_cols && (phases & (rh::PH_WLOAD | rh::PH_MULADD))) ? g->hcolmap : nullptr;
+    L.reach = nullptr;
+    if (all_cols && L.use_reach) {
+        auto f = g->reach_dev.find(L.n_cta);
+        if (f != g->reach_dev.end()) {
+            L.reach = f->second;
+        } else {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            RH_CUDA(cudaStreamIsCapturing(s, &cs));
+            if (cs == cudaStreamCaptureStatusNone) {
+                rh::ReachSched* rs = nullptr;
+                rh_status st = reach_schedule(g, L.n_cta, &rs);
+                if (st) return st;
+                L.reach = rs;
+            }
+        }
+    }
     rh::launch_dirs(g->dir(), L, s);
     RH_CUDA(cudaGetLastError());
     return RH_OK;
@@ -451,6 +595,7 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
         mix(S.rf_tgt_gptr.data(), S.rf_tgt_gptr.size() * sizeof(int64_t));
         g->topo_hash = h;
     }
+    g->colmap = tree_column_order(g->S);
     const auto& S = g->S;
     if (device < 0) {  // symbolic phase only: no device state
         *out = g.release();
@@ -664,6 +809,7 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     RH_CUDA(g->upload(g->jpt_ptr, S.jpt_ptr));
     RH_CUDA(g->upload(g->jpt_row, S.jpt_row));
     RH_CUDA(g->upload(g->jpt_src, S.jpt_src));
+    RH_CUDA(g->upload(g->hcolmap, g->colmap));
     RH_CUDA(g->upload(g->tp_bus, tp_bus));
     {
         // a sparse bus of forward level 0 has no L entries outside its block; for a PQ
@@ -922,6 +1068,14 @@ rh_status capture_graph(rh_grid* g, F&& enqueue, cudaGraphExec_t* exec, int* ker
     return RH_OK;
 }
 
+// CTAs of rh_reduced_hessian's first direction launch: the fewest with the directions
+// per CTA of a launch one slot short of full; the slots left over (7 SMs' worth for the
+// 9241-bus grid) are the adjoint branch's
+int first_launch_ctas(int np) {
+    const int per = (np + rh::dirs_cta_slots() - 2) / (rh::dirs_cta_slots() - 1);
+    return std::min(rh::dirs_default_ctas(np), std::max(1, (np + per - 1) / per));
+}
+
 // rh_reduced_hessian's device work.  After the factorisation the adjoint chain
 // forks onto stream2 (its single solve as one direction CTA) while
 // the direction kernel runs SpMul and the L and U sweeps on fewer CTAs than the
@@ -937,11 +1091,8 @@ rh_status enqueue_reduced_hessian(rh_grid* g, double* Hd, int64_t lh) {
     st = enqueue_adjoint_chain(g, g->stream2, true);
     if (st) return st;
     RH_CUDA(cudaEventRecordWithFlags(g->ev_d0, g->stream, cudaEventRecordExternal));
-    // the fewest CTAs with the directions per CTA of a launch one slot short of full: the
-    // slots left over (7 SMs' worth for the 9241-bus grid) are the adjoint branch's
-    const int per = (np + rh::dirs_cta_slots() - 2) / (rh::dirs_cta_slots() - 1);
     st = dirs(g, np, np, g->V, g->T, nullptr, 0, 0, Hd, lh, rh::PH_WLOAD | rh::PH_SPMUL | rh::PH_L | rh::PH_U,
-              g->stream, std::max(1, (np + per - 1) / per));
+              g->stream, first_launch_ctas(np));
     if (st) return st;
     RH_CUDA(cudaEventRecordWithFlags(g->ev_v, g->stream, cudaEventRecordExternal));
     RH_CUDA(cudaEventRecordWithFlags(g->ev_c, g->stream2, cudaEventRecordExternal));
@@ -1192,6 +1343,10 @@ rh_status rh_reduced_hessian(rh_grid* g, double* H, int64_t ldh, double* F, doub
         g->hess_exec = nullptr;
     }
     if (!g->hess_exec) {
+        // the first launch's reach schedule is built here: the capture cannot allocate
+        rh::ReachSched* rs = nullptr;
+        st = reach_schedule(g, first_launch_ctas(np), &rs);
+        if (st) return st;
         if (!g->stream2) RH_CUDA(cudaStreamCreateWithFlags(&g->stream2, cudaStreamNonBlocking));
         if (!g->ev_fork) RH_CUDA(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
         if (!g->ev_join) RH_CUDA(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
@@ -1308,8 +1463,10 @@ rh_status rh_reduced_hessian_flops(const rh_grid* g, int32_t n_sm, double* algor
         int64_t l = l_all;
         if (tailed) {
             std::fill(in.begin(), in.end(), 0);
-            for (int j = c0; j < c1; j++)
-                for (int t = S.jpt_ptr[j]; t < S.jpt_ptr[j + 1]; t++) in[bpos[S.jpt_row[t]]] = 1;
+            for (int j = c0; j < c1; j++) {    // the launch's columns, in the tree order
+                const int col = g->colmap[j];
+                for (int t = S.jpt_ptr[col]; t < S.jpt_ptr[col + 1]; t++) in[bpos[S.jpt_row[t]]] = 1;
+            }
             l = 0;
             for (int k = 0; k < S.tail_bus0; k++) {
                 if (!in[k]) continue;
@@ -1427,6 +1584,8 @@ rh_status rh_batch_hessvec(int32_t n_items, const rh_hv_item* items, int32_t wid
             L.ldhw = it.ldhw;
             L.phases = all;
             L.ws_elems = it.work ? (int64_t)g->rows() * it.N : (int64_t)g->ws_elems;
+            L.colmap = nullptr;
+            L.reach = nullptr;
             int Tt = g->S.n_x - g->S.t0;
             L.use_tail = rh::dirs_tail_fits(Tt, it.N, G) ? 1 : 0;
             L.use_reach = 0;
@@ -1664,6 +1823,8 @@ rh_status rh_hessvec_noalloc(rh_grid* g, const double* W, int64_t ldw, int32_t N
     L.ldhw = ldhw;
     L.phases = rh::PH_WLOAD | rh::PH_SPMUL | rh::PH_L | rh::PH_U | rh::PH_TPROJ | rh::PH_UT | rh::PH_LT | rh::PH_MULADD;
     L.ws_elems = RH_NOALLOC_DOUBLES;
+    L.colmap = nullptr;
+    L.reach = nullptr;
     L.use_tail = rh::dirs_tail_fits(S.n_x - S.t0, N, L.n_cta) ? 1 : 0;
     L.use_reach = 0;
     rh::launch_dirs(g->dir(), L, (cudaStream_t)stream);

@@ -1089,6 +1089,9 @@ __device__ void tproj(const DirGrid& g, const double* V, double* T, int64_t ld, 
     }
 }
 
+// identity W: the column of direction j of the launch (and of its HW, relative to col0)
+__device__ __forceinline__ int id_col(const DirLaunch& L, int j) { return L.colmap ? L.colmap[L.col0 + j] : L.col0 + j; }
+
 // HW = Y_p + J_p^T Psi (Algorithm 2, SpMulAdd): one lane per p row k, directions
 // blocked W at a time, so a warp's stores of one direction are consecutive.
 template <int W>
@@ -1106,7 +1109,7 @@ __device__ __forceinline__ void muladd_row(const DirGrid& g, const DirLaunch& L,
         for (int w = 0; w < W; w++) h[w] = fma(v, pr[w], h[w]);
     }
 #pragma unroll
-    for (int w = 0; w < W; w++) L.HW[(int64_t)(c0 + d0 + w) * L.ldhw + k] = h[w];
+    for (int w = 0; w < W; w++) L.HW[(int64_t)(id_col(L, c0 + d0 + w) - L.col0) * L.ldhw + k] = h[w];
 }
 
 // Algorithm 2 for the directions owned by CTA `cta` of launch L on grid g.
@@ -1132,7 +1135,7 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
         for (int it = threadIdx.x; it < g.n_p * D; it += blockDim.x) {
             int k = it / D, d = it - k * D;
             int64_t c = c0 + d;
-            double w = L.W ? L.W[c * L.ldw + k] : (k == L.col0 + c ? 1.0 : 0.0);
+            double w = L.W ? L.W[c * L.ldw + k] : (k == id_col(L, (int)c) ? 1.0 : 0.0);
             V[(int64_t)(g.n_x + k) * ld + d] = w;
         }
         for (int d = threadIdx.x; d < D; d += blockDim.x) V[(int64_t)g.zero_row * ld + d] = 0.0;
@@ -1152,7 +1155,7 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
         }
         __syncthreads();
         for (int d = threadIdx.x / 8; d < D; d += blockDim.x / 8) {
-            const int k = L.col0 + c0 + d;
+            const int k = id_col(L, c0 + d);
             for (int t = g.jpt_ptr[k] + (threadIdx.x & 7); t < g.jpt_ptr[k + 1]; t += 8) {
                 const int qb = g.qtheta[g.jpt_row[t]];
                 const bool two = qb + 1 < g.n_x && g.qtheta[qb + 1] == qb;
@@ -1166,7 +1169,7 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
         }
         __syncthreads();
         for (int d = threadIdx.x / 8; d < D; d += blockDim.x / 8) {
-            const int k = L.col0 + c0 + d;
+            const int k = id_col(L, c0 + d);
             for (int t = g.jpt_ptr[k] + (threadIdx.x & 7); t < g.jpt_ptr[k + 1]; t += 8)
                 V[(int64_t)g.jpt_row[t] * ld + d] = -g.jptvd[t];
         }
@@ -1181,7 +1184,7 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
         }
         __syncthreads();
         for (int d = threadIdx.x / 8; d < D; d += blockDim.x / 8) {
-            const int k = L.col0 + c0 + d;
+            const int k = id_col(L, c0 + d);
             for (int t = g.jpt_ptr[k] + (threadIdx.x & 7); t < g.jpt_ptr[k + 1]; t += 8)
                 V[(int64_t)g.jpt_row[t] * ld + d] = -g.jptvd[t];
         }
@@ -1208,13 +1211,17 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
         unsigned* mask = nullptr;
         if ((L.phases & PH_L) && L.use_reach) {
             mask = mask_smem;
-            if (seed) {
+            if (L.reach) {
+                const int words = L.reach->words;
+                const unsigned* m = L.reach->masks + (int64_t)cta * words;
+                for (int i = threadIdx.x; i < words; i += blockDim.x) mask[i] = m[i];
+            } else if (seed) {
                 for (int i = threadIdx.x; i < (g.n_x + 31) / 32; i += blockDim.x) mask[i] = seed[i];
             } else {
                 for (int i = threadIdx.x; i < (g.n_x + 31) / 32; i += blockDim.x) mask[i] = 0u;
                 __syncthreads();
                 for (int d = threadIdx.x / 8; d < D; d += blockDim.x / 8) {
-                    const int k = L.col0 + c0 + d;
+                    const int k = id_col(L, c0 + d);
                     for (int t = g.jpt_ptr[k] + (threadIdx.x & 7); t < g.jpt_ptr[k + 1]; t += 8) {
                         const int qb = g.qtheta[g.jpt_row[t]];
                         mask_set(mask, qb);
@@ -1225,7 +1232,14 @@ __device__ __forceinline__ void dirs_body(const DirGrid& g, const DirLaunch& L, 
             __syncthreads();
         }
         if (L.phases & PH_L) {
-            if (mask) {
+            if (mask && L.reach) {
+                // the CTA's reach, level by level, precomputed: nothing to skip or grow
+                const ReachSched& R = *L.reach;
+                const int m0 = R.lev0[cta];
+                const LevelSet rs = {R.nlev[cta], R.ptr + m0 + cta, R.slots, R.maxext + m0};
+                sweep_fwd<false, false, true>(g, rs, g.Ad, V, ld, 0, D, part, nullptr, seed, mask);
+                sweep_fwd<false, true, true>(g, g.ef, g.Ad, V, ld, 0, D, part, nullptr, nullptr, mask);
+            } else if (mask) {
                 sweep_fwd<false, false, true>(g, g.sf, g.Ad, V, ld, 0, D, part, mask, seed, mask);
                 sweep_fwd<false, true, true>(g, g.ef, g.Ad, V, ld, 0, D, part, nullptr, nullptr, mask);
             } else {

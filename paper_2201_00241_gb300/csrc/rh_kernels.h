@@ -102,6 +102,26 @@ struct DirLaunch {
     int use_tail;              // dense tail in shared memory (needs T * ceil(N / n_cta) <= 4096)
     int use_reach;             // identity W: forward L sweep only over the reach of B's nonzeros (needs use_tail,
                                // and phases L and U in the same launch)
+    // identity W: direction j is column colmap[col0 + j] of the identity and writes that
+    // column of HW (relative to HW: colmap[col0 + j] - col0); NULL: column col0 + j
+    const int* colmap;
+    // identity W with use_reach: each CTA's reach precomputed on the host (NULL: found at
+    // run time, a bit mask grown level by level)
+    const struct ReachSched* reach;
+};
+
+// The reach of every CTA of one identity-W launch (N directions on n_cta CTAs, columns
+// through colmap): for CTA c, the sparse buses its J_p columns can make nonzero in the
+// forward L sweep (those columns' buses and their ancestors), as forward-sweep slots
+// grouped by level (only the CTA's nonempty levels), and the bit mask of their rows.
+struct ReachSched {
+    int n_cta, words;          // CTAs; 32-bit words of a row mask ((n_x + 31) / 32)
+    const int* nlev;           // [n_cta] levels of CTA c
+    const int* lev0;           // [n_cta] CTA c's first entry in ptr / maxext
+    const int* ptr;            // per CTA nlev + 1 offsets into slots
+    const int* maxext;         // per CTA and level: longest row part
+    const int4* slots;         // forward slots {q, n, rp, rpv} of the reach buses
+    const unsigned* masks;     // [n_cta * words] rows of the reach
 };
 
 // Up to kMaxBatch (grid, W block) items of one batched launch, passed by value as

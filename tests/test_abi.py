@@ -205,12 +205,36 @@ def test_reduced_hessian_flop_counts(case, n_sm):
     lt = int(bwd[sp][need[:t_bus0]].sum())
     proj = 6 * n_bus + 8 * n_inc + 4 * (1 + deg_ref) + 2 * n_gref + 1 + n_pv + 2 * lev0_pq
     l2 = proj + 2 * (ut + ext + 2 * tail + lt) + 2 * nnz_jp
+    # the launches take the identity columns in the order of the lowest elimination-tree
+    # postorder among each column's J_p buses (children and roots in ascending position)
+    kids = [[] for _ in range(n_el)]
+    roots = []
+    for k in range(n_el):
+        (kids[parent[k]] if parent[k] >= 0 else roots).append(k)
+    post = np.zeros(n_el, np.int64)
+    count = 0
+
+    def visit(k):
+        nonlocal count
+        stack = [(k, 0)]
+        while stack:
+            b, i = stack.pop()
+            if i < len(kids[b]):
+                stack.append((b, i + 1))
+                stack.append((kids[b][i], 0))
+            else:
+                post[b] = count
+                count += 1
+    for r in roots:
+        visit(r)
+    anchor = [min(post[pos_of_q[r]] for r in rows) if len(rows) else n_el for rows in jp_rows]
+    order = sorted(range(np_), key=lambda j: anchor[j])
     l1 = 0.0
     for c in range(n1):
         c0, c1 = c * np_ // n1, (c + 1) * np_ // n1
         reach = np.zeros(n_el, bool)
         for j in range(c0, c1):
-            reach[pos_of_q[jp_rows[j]]] = True
+            reach[pos_of_q[jp_rows[order[j]]]] = True
         for k in range(t_bus0):
             if reach[k] and 0 <= parent[k] < t_bus0:
                 reach[parent[k]] = True

@@ -11,9 +11,9 @@
 //    (SpMul, both triangular sweeps, the projection, both transposed sweeps,
 //    SpMulAdd) with only CTA-local barriers: no grid-wide synchronisation.
 //  * Inside a CTA the work of a level is flattened over (bus, direction)
-//    pairs; narrow levels near the top of the elimination tree additionally
-//    split each row's dot product into k-slices combined through shared
-//    memory, so that at least 4 warps issue FP64 work.
+//    pairs; in narrow levels near the top of the elimination tree each row's
+//    dot product is further split over adjacent lanes of a warp and summed with
+//    shuffles, so that more warps issue FP64 work and a level needs one barrier.
 //  * A bus is a block of one (PV) or two (PQ) variables whose rows share the
 //    same columns outside the bus; one load of x_c feeds two FMAs.
 //  * Right-hand sides are interleaved, row-major [row][ld]: the D directions
@@ -34,7 +34,7 @@ namespace {
 // row lengths) in a warp and more items in every level.
 constexpr int kDirThreads = 384;
 constexpr int kDirCtasPerSm = 2;
-constexpr int kPartCap = 4096;   // doubles of k-split partial sums per CTA
+constexpr int kPartCap = 4096;   // doubles of the CTA's dense-tail rows (T x directions)
 constexpr int kDMax = 256;       // max directions per CTA
 
 // Index checks of the bounds-checking build (-DRH_BOUNDS): a failed check sets a
@@ -581,15 +581,16 @@ __global__ void k_build_tail(int T, int t0, const int* __restrict__ pos, const d
 // the direction kernel: Algorithm 2 for a slice of directions per CTA
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ int choose_ks(int nb, int D, int maxext) {
-    int base = nb * D;
-    if (base >= (int)blockDim.x / 2) return 1;
-    int ks = (int)blockDim.x / base;
-    int lim = maxext / 4;
-    if (ks > lim) ks = lim;
-    int cap = kPartCap / (2 * base);
-    if (ks > cap) ks = cap;
-    return ks < 2 ? 1 : ks;
+// Narrow levels (fewer than blockDim / 2 (bus, direction) items): every row's dot
+// product is split over ks adjacent lanes of a warp, ks a power of two up to 32 and
+// at most half the row, as long as the items still fit in the CTA's threads.  1: no
+// split.
+__device__ __forceinline__ int split_lanes(int nb, int D, int maxext) {
+    const int base = nb * D;
+    if (2 * base > (int)blockDim.x) return 1;
+    int ks = 1;
+    while (ks < 32 && 2 * base * ks <= (int)blockDim.x && 2 * ks <= maxext) ks *= 2;
+    return ks;
 }
 
 // a0 -= sum_e v0[e] x[col[e]], a1 -= sum_e v1[e] x[col[e]] over e in [e0, e1) of
@@ -647,6 +648,38 @@ __device__ __forceinline__ void block_sub(const int* __restrict__ col, const dou
     }
 }
 
+// a0 -= sum v0[e] x[col[e]], a1 likewise, over e = e0, e0 + step, ... < n: the share of
+// one lane of a split row (adjacent lanes read adjacent entries)
+template <bool TWO, bool CMASK>
+__device__ __forceinline__ void strided_sub(const int* __restrict__ col, const double* __restrict__ vals, int r0,
+                                            int r1, int e, int n, int step, const double* X, int64_t ld, int64_t c,
+                                            double& a0, double& a1, const unsigned* cmask, int nrows) {
+    for (; e + step < n; e += 2 * step) {
+        const int i0 = col[r0 + e], i1 = col[r0 + e + step];
+        const double x0 = ldx<CMASK>(X, i0, ld, c, cmask, nrows), x1 = ldx<CMASK>(X, i1, ld, c, cmask, nrows);
+        a0 = fma(-vals[r0 + e], x0, a0);
+        a0 = fma(-vals[r0 + e + step], x1, a0);
+        if constexpr (TWO) {
+            a1 = fma(-vals[r1 + e], x0, a1);
+            a1 = fma(-vals[r1 + e + step], x1, a1);
+        }
+    }
+    if (e < n) {
+        const double xv = ldx<CMASK>(X, col[r0 + e], ld, c, cmask, nrows);
+        a0 = fma(-vals[r0 + e], xv, a0);
+        if constexpr (TWO) a1 = fma(-vals[r1 + e], xv, a1);
+    }
+}
+
+// sum of a lane's partial sums over the ks adjacent lanes of its item (all 32 lanes of
+// the warp take part; ks divides 32)
+__device__ __forceinline__ void split_sum(int ks, bool wtwo, double& s0, double& s1) {
+    for (int off = ks >> 1; off > 0; off >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, off, ks);
+        if (wtwo) s1 += __shfl_down_sync(0xffffffffu, s1, off, ks);
+    }
+}
+
 // warp-uniform choice of the two-row path (lanes that left the item loop do not vote)
 __device__ __forceinline__ bool warp_any(bool p) { return __any_sync(__activemask(), p); }
 
@@ -664,9 +697,9 @@ __device__ __forceinline__ void fwd_finish(const DirGrid& g, const double* __res
     }
 }
 
-// One level of a sweep is flattened over (bus, direction) items, or over
-// (bus, k-slice, direction) items when the level is too narrow to give every
-// warp work.  Each bus block is described by one packed slot
+// One level of a sweep is flattened over (bus, direction) items, or, when the
+// level is too narrow to give every warp work, over (bus, direction, lane of the
+// row) with the row's lanes adjacent in a warp.  Each bus block is described by one packed slot
 //   forward:  {q, n, rp, rpv}  theta row q, n columns left of the bus, L parts of
 //             the theta row at rp and of the v row at rpv (-1 for a PV bus)
 //   backward: {q, n, ue0, ue1} U parts right of the bus at ue0 / ue1 (-1: PV)
@@ -692,7 +725,7 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
     for (int lev = 0; lev < ls.n_lev; lev++) {
         const int b0 = ls.ptr[lev], nb = ls.ptr[lev + 1] - b0;
         const int4* __restrict__ slots = ls.slots + b0;
-        const int ks = choose_ks(nb, D, ls.maxext[lev]);
+        const int ks = split_lanes(nb, D, ls.maxext[lev]);
         if (ks == 1) {
             const int items = nb * D;
             int it = threadIdx.x;
@@ -729,54 +762,38 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
                 if (mask) mask_bus(mask, g.bparent[q]);
             }
         } else {
-            const int per = ks * D;
-            for (int it = threadIdx.x; it < nb * per; it += blockDim.x) {
-                int bi = it / per, rem = it - bi * per;
-                int sli = rem / D, d = rem - sli * D;
-                const int4 sl = slots[bi];
-                if (mask && !(inb(sl.x, g.n_x) && mask_get(mask, sl.x))) continue;
-                const int rp = sl.z;
+            // narrow level: each row split over ks adjacent lanes, summed by shuffles
+            const int total = nb * D * ks;
+            const int lane = (int)(threadIdx.x & 31);
+            for (int w0 = (int)threadIdx.x - lane; w0 < total; w0 += blockDim.x) {     // warp-uniform
+                const int it = w0 + lane, sli = it & (ks - 1), item = it / ks;
+                const bool valid = it < total;
+                const int bi = valid ? item / D : 0, d = valid ? item - bi * D : 0;
+                const int4 sl = valid ? slots[bi] : make_int4(0, 0, 0, -1);
+                const int q = sl.x, rp = sl.z;
                 const bool two = sl.w >= 0;
                 const int rpv = two ? sl.w : rp;
-                const int n = part_len(sl.y, rp, rpv, g.nnz);
-                int64_t c = c0 + d;
-                int e0 = sli * n / ks, e1 = (sli + 1) * n / ks;
-                double s0 = 0.0, s1 = 0.0;     // minus the slice's partial sums
-                if (warp_any(two)) block_sub<true, CMASK>(g.col, vals, rp, rpv, e0, e1, X, ld, c, s0, s1, cmask, g.n_x);
-                else block_sub<false, CMASK>(g.col, vals, rp, rpv, e0, e1, X, ld, c, s0, s1, cmask, g.n_x);
-                double* pp = part + 2 * ((bi * ks + sli) * D + d);
-                pp[0] = s0;
-                pp[1] = s1;
-            }
-            __syncthreads();
-            for (int it = threadIdx.x; it < nb * D; it += blockDim.x) {
-                int bi = it / D, d = it - bi * D;
-                const int4 sl = slots[bi];
-                const int q = sl.x;
-                const bool two = sl.w >= 0;
-                int64_t c = c0 + d;
-                if (mask && !(inb(q, g.n_x) && mask_get(mask, q))) continue;
-                const int rpv = two ? sl.w : sl.z;
-                const int n = part_len(sl.y, sl.z, rpv, g.nnz);
-                const bool has_b = !seed || mask_get(seed, q);
-                double a0 = (has_b && inb(q, g.n_x)) ? X[(int64_t)q * ld + c] : 0.0;
-                double a1 = (two && has_b && inb(q + 1, g.n_x)) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
-                if (warp_any(two)) {
-                    for (int k = 0; k < ks; k++) {
-                        const double* pp = part + 2 * ((bi * ks + k) * D + d);
-                        a0 += pp[0];
-                        a1 += pp[1];
-                    }
-                    if (EXT) {
-                        stx(X, q, ld, c, a0, g.n_x);
-                        if (two) stx(X, q + 1, ld, c, a1, g.n_x);
-                    } else {
-                        fwd_finish<SCALE, true>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
-                    }
+                const bool act = valid && !(mask && !(inb(q, g.n_x) && mask_get(mask, q)));
+                const int n = act ? part_len(sl.y, rp, rpv, g.nnz) : 0;
+                const int64_t c = c0 + d;
+                const bool fin = act && sli == 0;          // the lane that finishes the item
+                const bool has_b = fin && (!seed || mask_get(seed, q));
+                const double b0 = (has_b && inb(q, g.n_x)) ? X[(int64_t)q * ld + c] : 0.0;
+                const double b1 = (two && has_b && inb(q + 1, g.n_x)) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
+                const bool wtwo = __any_sync(0xffffffffu, two);   // every lane of the warp is here
+                double s0 = 0.0, s1 = 0.0;
+                if (wtwo) strided_sub<true, CMASK>(g.col, vals, rp, rpv, sli, n, ks, X, ld, c, s0, s1, cmask, g.n_x);
+                else strided_sub<false, CMASK>(g.col, vals, rp, rpv, sli, n, ks, X, ld, c, s0, s1, cmask, g.n_x);
+                split_sum(ks, wtwo, s0, s1);
+                if (!fin) continue;
+                const double a0 = b0 + s0, a1 = b1 + s1;
+                if (EXT) {
+                    stx(X, q, ld, c, a0, g.n_x);
+                    if (two) stx(X, q + 1, ld, c, a1, g.n_x);
+                } else if (two) {
+                    fwd_finish<SCALE, true>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
                 } else {
-                    for (int k = 0; k < ks; k++) a0 += part[2 * ((bi * ks + k) * D + d)];
-                    if (EXT) stx(X, q, ld, c, a0, g.n_x);
-                    else fwd_finish<SCALE, false>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
+                    fwd_finish<SCALE, false>(g, vals, X, ld, c, q, two, rpv + n, a0, a1);
                 }
                 if (mask) mask_bus(mask, g.bparent[q]);
             }
@@ -805,7 +822,7 @@ __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __
     for (int lev = 0; lev < ls.n_lev; lev++) {
         const int b0 = ls.ptr[lev], nb = ls.ptr[lev + 1] - b0;
         const int4* __restrict__ slots = ls.slots + b0;
-        const int ks = choose_ks(nb, D, ls.maxext[lev]);
+        const int ks = split_lanes(nb, D, ls.maxext[lev]);
         if (ks == 1) {
             const int items = nb * D;
             int it = threadIdx.x;
@@ -834,45 +851,31 @@ __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __
                 bi = bi2;
             }
         } else {
-            const int per = ks * D;
-            for (int it = threadIdx.x; it < nb * per; it += blockDim.x) {
-                int bi = it / per, rem = it - bi * per;
-                int sli = rem / D, d = rem - sli * D;
-                const int4 sl = slots[bi];
-                const int ue0 = sl.z;
+            // narrow level: each row split over ks adjacent lanes, summed by shuffles
+            const int total = nb * D * ks;
+            const int lane = (int)(threadIdx.x & 31);
+            for (int w0 = (int)threadIdx.x - lane; w0 < total; w0 += blockDim.x) {     // warp-uniform
+                const int it = w0 + lane, sli = it & (ks - 1), item = it / ks;
+                const bool valid = it < total;
+                const int bi = valid ? item / D : 0, d = valid ? item - bi * D : 0;
+                const int4 sl = valid ? slots[bi] : make_int4(0, 0, 0, -1);
+                const int q = sl.x, ue0 = sl.z;
                 const bool two = sl.w >= 0;
                 const int ue1 = two ? sl.w : ue0;
-                const int n = part_len(sl.y, ue0 - 1, ue1, g.nnz);
-                int64_t c = c0 + d;
-                int e0 = sli * n / ks, e1 = (sli + 1) * n / ks;
-                double s0 = 0.0, s1 = 0.0;     // minus the slice's partial sums
-                if (warp_any(two)) block_sub<true>(g.col, vals, ue0, ue1, e0, e1, X, ld, c, s0, s1, nullptr, g.n_x);
-                else block_sub<false>(g.col, vals, ue0, ue1, e0, e1, X, ld, c, s0, s1, nullptr, g.n_x);
-                double* pp = part + 2 * ((bi * ks + sli) * D + d);
-                pp[0] = s0;
-                pp[1] = s1;
-            }
-            __syncthreads();
-            for (int it = threadIdx.x; it < nb * D; it += blockDim.x) {
-                int bi = it / D, d = it - bi * D;
-                const int4 sl = slots[bi];
-                const int q = sl.x;
-                const bool two = sl.w >= 0;
-                int64_t c = c0 + d;
-                const bool has_b = !rmask || mask_get(rmask, q);
-                double a0 = (has_b && inb(q, g.n_x)) ? X[(int64_t)q * ld + c] : 0.0;
-                double a1 = (two && has_b && inb(q + 1, g.n_x)) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
-                if (warp_any(two)) {
-                    for (int k = 0; k < ks; k++) {
-                        const double* pp = part + 2 * ((bi * ks + k) * D + d);
-                        a0 += pp[0];
-                        a1 += pp[1];
-                    }
-                    bwd_finish<SCALE, true>(g, vals, X, ld, c, q, two, sl.z - 1, a0, a1);
-                } else {
-                    for (int k = 0; k < ks; k++) a0 += part[2 * ((bi * ks + k) * D + d)];
-                    bwd_finish<SCALE, false>(g, vals, X, ld, c, q, two, sl.z - 1, a0, a1);
-                }
+                const int n = valid ? part_len(sl.y, ue0 - 1, ue1, g.nnz) : 0;
+                const int64_t c = c0 + d;
+                const bool fin = valid && sli == 0;
+                const bool has_b = fin && (!rmask || mask_get(rmask, q));
+                const double b0 = (has_b && inb(q, g.n_x)) ? X[(int64_t)q * ld + c] : 0.0;
+                const double b1 = (two && has_b && inb(q + 1, g.n_x)) ? X[(int64_t)(q + 1) * ld + c] : 0.0;
+                const bool wtwo = __any_sync(0xffffffffu, two);   // every lane of the warp is here
+                double s0 = 0.0, s1 = 0.0;
+                if (wtwo) strided_sub<true, false>(g.col, vals, ue0, ue1, sli, n, ks, X, ld, c, s0, s1, nullptr, g.n_x);
+                else strided_sub<false, false>(g.col, vals, ue0, ue1, sli, n, ks, X, ld, c, s0, s1, nullptr, g.n_x);
+                split_sum(ks, wtwo, s0, s1);
+                if (!fin) continue;
+                if (two) bwd_finish<SCALE, true>(g, vals, X, ld, c, q, two, ue0 - 1, b0 + s0, b1 + s1);
+                else bwd_finish<SCALE, false>(g, vals, X, ld, c, q, two, ue0 - 1, b0 + s0, b1 + s1);
             }
         }
         __syncthreads();

@@ -474,9 +474,14 @@ def measure_plain_paths(lg, n_single=32, reps=3):
             "note": "HVP only (state resident); N=1 calls one at a time / 12 launches of N=256"}
 
 
-def measure_serving(factors=(0.25, 0.5, 1.0, 2.0, 4.0), n_req=120, seed=4):
+def measure_serving(factors=(0.25, 0.5, 0.75, 1.0, 1.25, 1.5), n_req=400, seed=4, outstanding=128, t_sat=2.0):
     """Poisson request stream over grids of 118, 1354, 2869 and 9241 buses (ratio 8:4:2:1),
-    N ~ U{1..256} unit directions per request, through the continuous-batching server."""
+    N ~ U{1..256} unit directions per request, through the continuous-batching server.
+
+    Saturation is measured first, closed-loop: `outstanding` requests are kept in the
+    server for t_sat seconds (each completion submits the next); its request rate is the
+    1x of the open-loop sweep that follows (Poisson arrivals at factors x saturation)."""
+    import concurrent.futures as cf
     import time as _t
     from paper_2201_00241_gb300 import gridgen as gg
     from paper_2201_00241_gb300.server import RHServer
@@ -495,20 +500,32 @@ def measure_serving(factors=(0.25, 0.5, 1.0, 2.0, 4.0), n_req=120, seed=4):
         return name, gg.random_directions(grids[name].n_p, N, 10_000 + k)
 
     try:
-        reqs = [draw(k) for k in range(48)]
-        for name, W in reqs[:8]:
+        pool = [draw(k) for k in range(256)]
+        for name, W in pool[:16]:
             srv.submit(name, W).result()                     # warm-up
+        live = {}
+        k = 0
+        while len(live) < outstanding:
+            name, W = pool[k % len(pool)]
+            live[srv.submit(name, W)] = W.shape[1]
+            k += 1
+        n_done = hvp_done = 0
         t0 = _t.perf_counter()
-        futs = [srv.submit(name, W) for name, W in reqs]
-        for f in futs:
-            f.result()
+        while _t.perf_counter() - t0 < t_sat:
+            done, _ = cf.wait(list(live), return_when=cf.FIRST_COMPLETED)
+            for f in done:
+                hvp_done += live.pop(f)
+                n_done += 1
+                name, W = pool[k % len(pool)]
+                live[srv.submit(name, W)] = W.shape[1]
+                k += 1
         dt = _t.perf_counter() - t0
-        sat_req = len(reqs) / dt
-        sat_hvp = sum(W.shape[1] for _, W in reqs) / dt
+        cf.wait(list(live))
+        sat_req, sat_hvp = n_done / dt, hvp_done / dt
         rows = []
         for f in factors:
             rate = f * sat_req
-            stream = [draw(1000 * int(10 * f) + k) for k in range(n_req)]
+            stream = [draw(1000 * int(100 * f) + j) for j in range(n_req)]
             gaps = rng.exponential(1.0 / rate, n_req)
             srv.latencies = []
             t0 = _t.perf_counter()
@@ -525,10 +542,12 @@ def measure_serving(factors=(0.25, 0.5, 1.0, 2.0, 4.0), n_req=120, seed=4):
             dt = _t.perf_counter() - t0
             st = srv.stats()
             rows.append({"rate_factor": f, "offered_req_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                         "throughput_req_per_s": n_req / dt,
                          "throughput_hvp_per_s": sum(W.shape[1] for _, W in stream) / dt})
         return {"workload": "Poisson requests over case118/1354/2869/9241 (8:4:2:1), N ~ U{1..256}",
-                "saturated_req_per_s": sat_req, "saturated_hvp_per_s": sat_hvp, "sweep": rows,
-                "batches": srv.batches, "waited_for_budget": srv.waited_for_budget}
+                "saturated_req_per_s": sat_req, "saturated_hvp_per_s": sat_hvp,
+                "saturation": f"closed loop, {outstanding} requests outstanding for {t_sat:.0f} s",
+                "sweep": rows, "batches": srv.batches, "waited_for_budget": srv.waited_for_budget}
     finally:
         srv.close()
 

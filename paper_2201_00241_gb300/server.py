@@ -1,21 +1,26 @@
 """Continuous-batching server for reduced-Hessian-vector products.
 
 Grids are registered once; their factors, lambda and projection coefficients
-stay resident on the device (rh_adjoint at registration).  Clients submit
+stay resident on the device (rh_adjoint before registration).  Clients submit
 (grid name, W) requests, W an n_p x N float64 array, and get a future for HW.
 
-A worker thread runs the batching loop:
+A worker thread runs the batching loop over a few CUDA streams, each with its
+own memory arena allocated once at start-up:
 
-* admission: a waiting request is admitted when the device-memory footprint of
-  all admitted, unfinished requests plus its own (direction workspace, W and HW
-  on the device) fits the budget and a batch slot is free;
-* every admitted set becomes ONE rh_batch_hessvec launch (cross-instance
-  batching), issued on the next of several CUDA streams, so launches of
-  different admission rounds overlap on the device while new requests keep
-  arriving (continuous batching, not a queue drained one request at a time);
-* completion is detected by CUDA events; the result is copied to pinned host
-  memory on the same stream and the future is resolved with the latency
-  (arrival to result) recorded for p50 / p99.
+* device: the W blocks, the HW blocks and the direction workspaces of one round;
+* pinned host: the staging of the round's W blocks and of its HW results.
+
+Admission is by memory footprint: waiting requests join the next free arena's
+round, in arrival order, while their W, HW and workspace fit in it (a request
+that does not fit waits for a later round; one larger than an arena is refused).
+A round is then three operations on its stream: one copy of all its W blocks to
+the device, ONE rh_batch_hessvec launch over all its requests (cross-instance
+batching: grids of different sizes and widths in one kernel), and one copy of
+all its HW blocks back.  Rounds on different streams overlap on the device while
+new requests keep arriving (continuous batching, not a queue drained one
+request at a time).  Completion is detected with CUDA events; the future is
+resolved with a copy of the result, and the latency from arrival to result is
+recorded for p50 / p99.  Nothing is allocated per request.
 
 Each result equals the request computed alone, up to rounding: items are
 independent and only the split of a request's directions over CTAs differs.
@@ -32,35 +37,57 @@ import torch
 
 from . import rh
 
+_ALIGN = 32          # doubles: every block of an arena starts on a 256-byte boundary
+
+
+def _up(n: int) -> int:
+    return (n + _ALIGN - 1) // _ALIGN * _ALIGN
+
 
 class _Req:
-    __slots__ = ("name", "W", "N", "future", "t_arrival", "bytes", "dev")
+    __slots__ = ("name", "W", "N", "future", "t_arrival", "n_io", "n_work")
 
     def __init__(self, name, W, future, t_arrival):
         self.name, self.W, self.future, self.t_arrival = name, W, future, t_arrival
         self.N = W.shape[1]
-        self.bytes = 0
-        self.dev = None
+        self.n_io = 0
+        self.n_work = 0
+
+
+class _Arena:
+    """Device and pinned host memory of one stream's round, allocated once."""
+
+    def __init__(self, device, dev_doubles: int, io_doubles: int):
+        self.stream = torch.cuda.Stream(device=device)
+        self.io = io_doubles                 # W blocks (and as many HW) per round
+        self.work = dev_doubles - 2 * io_doubles
+        self.d = torch.empty(dev_doubles, dtype=torch.float64, device=device)
+        self.h_in = torch.empty(io_doubles, dtype=torch.float64).pin_memory()
+        self.h_out = torch.empty(io_doubles, dtype=torch.float64).pin_memory()
+        self.busy = None                     # (event, requests, offsets) of the round in flight
 
 
 class RHServer:
     def __init__(self, device: int = 0, budget_bytes: int = 8 << 30, max_batch: int = 32, n_streams: int = 4,
-                 max_inflight: int = 4, width: int = 0):
+                 width: int = 0, io_fraction: float = 0.08, max_io_doubles: int = 8 << 20):
+        """budget_bytes: device memory of all arenas together (split evenly over n_streams);
+        io_fraction: the share of an arena for W and for HW each, the rest for the direction
+        workspaces (a request's workspace, 2 (n_x + n_p + 1) N doubles, is about 12 times its
+        W block); max_io_doubles caps that share, and with it each stream's pinned staging."""
         self.device = device
         self.budget = int(budget_bytes)
-        self.max_batch = max_batch
-        self.max_inflight = max_inflight
+        self.max_batch = min(max_batch, 32)
         self.width = width
         self.grids: dict[str, rh.Grid] = {}
-        self.streams = [torch.cuda.Stream(device=device) for _ in range(n_streams)]
-        self._next_stream = 0
+        dev_doubles = self.budget // 8 // n_streams
+        io = max(_ALIGN, min(int(dev_doubles * io_fraction), int(max_io_doubles)) // _ALIGN * _ALIGN)
+        self.arenas = [_Arena(torch.device("cuda", device), dev_doubles, io) for _ in range(n_streams)]
+        self._next = 0
         self._q: collections.deque[_Req] = collections.deque()
         self._cv = threading.Condition()
-        self._inflight = []            # (event, [requests], host outputs)
-        self._used = 0
         self._stop = False
         self.latencies: list[float] = []
-        self.waited_for_budget = 0     # admissions deferred because the budget was full
+        self.waited_for_budget = 0     # requests held for a later round because this one was full
         self.batches = 0
         self._worker = threading.Thread(target=self._loop, daemon=True)
         self._worker.start()
@@ -94,80 +121,105 @@ class RHServer:
                 "waited_for_budget": self.waited_for_budget}
 
     # ---- worker ---------------------------------------------------------------
-    def _footprint(self, r: _Req) -> int:
+    def _size(self, r: _Req):
         g = self.grids[r.name]
-        return 8 * (rh.work_doubles(g, r.N) + 2 * g.n_p * r.N)
+        r.n_io = _up(g.n_p * r.N)
+        r.n_work = _up(rh.work_doubles(g, r.N))
 
-    def _admit(self):
-        batch = []
-        while self._q and len(batch) < self.max_batch and len(self._inflight) < self.max_inflight:
+    def _admit(self, a: _Arena):
+        """Requests of the next round on arena a, in arrival order, while they fit."""
+        batch, io, work = [], 0, 0
+        while self._q and len(batch) < self.max_batch:
             r = self._q[0]
-            r.bytes = self._footprint(r)
-            if self._used + r.bytes > self.budget and (self._used > 0 or batch):
+            if not r.n_io:
+                self._size(r)
+            if r.n_io > a.io or r.n_work > a.work:
+                self._q.popleft()
+                r.future.set_exception(ValueError(
+                    f"request of {r.N} directions on {r.name} is larger than a server arena"))
+                continue
+            if io + r.n_io > a.io or work + r.n_work > a.work:
                 self.waited_for_budget += 1
                 break
             self._q.popleft()
-            self._used += r.bytes
+            io += r.n_io
+            work += r.n_work
             batch.append(r)
         return batch
 
-    def _launch(self, batch):
-        s = self.streams[self._next_stream]
-        self._next_stream = (self._next_stream + 1) % len(self.streams)
-        dev = torch.device("cuda", self.device)
-        items, outs = [], []
-        with torch.cuda.stream(s):
-            for r in batch:
-                g = self.grids[r.name]
-                Wh = torch.from_numpy(np.ascontiguousarray(r.W.T)).pin_memory()
-                Wd = Wh.to(dev, non_blocking=True).t()                      # column-major n_p x N
-                HWd = torch.empty((r.N, g.n_p), dtype=torch.float64, device=dev).t()
-                work = torch.empty(rh.work_doubles(g, r.N), dtype=torch.float64, device=dev)
-                r.dev = (Wh, Wd, HWd, work)
-                items.append((g, Wd, HWd, work))
-            rh.batch_hessvec(items, self.width, stream=rh.C.c_void_p(s.cuda_stream))
-            for r in batch:
-                host = torch.empty((r.N, self.grids[r.name].n_p), dtype=torch.float64).pin_memory()
-                host.copy_(r.dev[2].t(), non_blocking=True)
-                outs.append(host)
+    def _launch(self, a: _Arena, batch):
+        # W blocks side by side in the pinned staging area, then one copy to the device
+        offs, o, w = [], 0, 0
+        hin = a.h_in.numpy()
+        for r in batch:
+            n = self.grids[r.name].n_p * r.N
+            hin[o:o + n] = r.W.reshape(-1, order="F")
+            offs.append((o, w))
+            o += r.n_io
+            w += r.n_work
+        end = o                     # doubles of the round's W (and HW) blocks
+        dW, dHW, dWork = a.d[:a.io], a.d[a.io:2 * a.io], a.d[2 * a.io:]
+        items = []
+        for r, (oi, wi) in zip(batch, offs):
+            g = self.grids[r.name]
+            n = g.n_p * r.N
+            items.append((g, dW[oi:oi + n].view(r.N, g.n_p).t(), dHW[oi:oi + n].view(r.N, g.n_p).t(),
+                          dWork[wi:wi + r.n_work]))
+        with torch.cuda.stream(a.stream):
+            dW[:end].copy_(a.h_in[:end], non_blocking=True)
+            rh.batch_hessvec(items, self.width, stream=rh.C.c_void_p(a.stream.cuda_stream))
+            a.h_out[:end].copy_(dHW[:end], non_blocking=True)
             ev = torch.cuda.Event()
-            ev.record(s)
-        self._inflight.append((ev, batch, outs))
+            ev.record(a.stream)
+        a.busy = (ev, batch, offs)
         self.batches += 1
 
     def _reap(self):
-        done = [x for x in self._inflight if x[0].query()]
-        for ev, batch, outs in done:
-            self._inflight.remove((ev, batch, outs))
+        progressed = False
+        for a in self.arenas:
+            if a.busy is None or not a.busy[0].query():
+                continue
+            _, batch, offs = a.busy
             t = time.perf_counter()
-            for r, host in zip(batch, outs):
-                self._used -= r.bytes
-                r.dev = None
+            hout = a.h_out.numpy()
+            for r, (o, _) in zip(batch, offs):
+                n_p = self.grids[r.name].n_p
+                res = hout[o:o + n_p * r.N].reshape(n_p, r.N, order="F").copy(order="F")
                 self.latencies.append(t - r.t_arrival)
-                r.future.set_result(host.numpy().T.copy(order="F"))
-        return bool(done)
+                r.future.set_result(res)
+            a.busy = None
+            progressed = True
+        return progressed
+
+    def _free_arena(self):
+        for k in range(len(self.arenas)):
+            a = self.arenas[(self._next + k) % len(self.arenas)]
+            if a.busy is None:
+                self._next = (self._next + k + 1) % len(self.arenas)
+                return a
+        return None
 
     def _loop(self):
         torch.cuda.set_device(self.device)
         while True:
             with self._cv:
-                if self._stop and not self._q and not self._inflight:
+                idle = all(a.busy is None for a in self.arenas)
+                if self._stop and not self._q and idle:
                     return
-                if not self._q and not self._inflight:
+                if not self._q and idle:
                     self._cv.wait(timeout=0.05)
-                batch = self._admit()
+                a = self._free_arena() if self._q else None
+                batch = self._admit(a) if a is not None else []
             progressed = False
             try:
                 if batch:
-                    self._launch(batch)
+                    self._launch(a, batch)
                 progressed = self._reap()
             except Exception as e:     # surface library errors on the futures, keep serving
-                with self._cv:
-                    for r in batch:
-                        self._used -= r.bytes
-                        r.dev = None
-                        if not r.future.done():
-                            r.future.set_exception(e)
-                self._inflight = [x for x in self._inflight if x[1] is not batch]
+                for r in batch:
+                    if not r.future.done():
+                        r.future.set_exception(e)
+                if a is not None and a.busy is not None and a.busy[1] is batch:
+                    a.busy = None
             if not batch and not progressed:
                 time.sleep(5e-5)

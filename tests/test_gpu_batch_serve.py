@@ -47,7 +47,8 @@ def colmajor(W):
 @pytest.fixture(scope="module")
 def grids():
     return {"g118": ready("case118"), "g1354a": ready("case1354", scale=True, seed_scale=0),
-            "g1354b": ready("case1354", scale=True, seed_scale=1), "g2869": ready("case2869")}
+            "g1354b": ready("case1354", scale=True, seed_scale=1), "g2869": ready("case2869"),
+            "g9241": ready("case9241")}
 
 
 @pytest.mark.parametrize("width", [0, 4, 16])
@@ -147,12 +148,14 @@ def test_reduced_objective_autograd_against_finite_differences():
 
 def test_server_result_alone_equals_in_the_mix(grids):
     from paper_2201_00241_gb300.server import RHServer
-    srv = RHServer(device=0, budget_bytes=2 << 30, max_batch=8, n_streams=3)
+    srv = RHServer(device=0, budget_bytes=6 << 30, max_batch=8, n_streams=3)
     try:
         for k, v in grids.items():
             srv.register(k, v)
         probe_W = gg.random_directions(grids["g1354a"].n_p, 37, 4242)
         alone = srv.submit("g1354a", probe_W).result(timeout=120)
+        probe9 = gg.random_directions(grids["g9241"].n_p, 50, 4343)
+        alone9 = srv.submit("g9241", probe9).result(timeout=120)
         rng = np.random.default_rng(7)
         names = list(grids)
         futs, ws = [], []
@@ -163,13 +166,15 @@ def test_server_result_alone_equals_in_the_mix(grids):
             ws.append(W)
             if i == 20:
                 mixed = srv.submit("g1354a", probe_W)
+                mixed9 = srv.submit("g9241", probe9)
         results = [(name, f.result(timeout=300)) for name, f in futs]
         in_mix = mixed.result(timeout=300)
         assert rel(in_mix, alone) <= 1e-12
+        assert rel(mixed9.result(timeout=300), alone9) <= 1e-12
         for (name, hw), W in list(zip(results, ws))[::7]:
             assert rel(hw, grids[name].hessvec(W)) <= 1e-12
         st = srv.stats()
-        assert st["requests"] == 42 and st["batches"] >= 2
+        assert st["requests"] == 44 and st["batches"] >= 2
     finally:
         srv.close()
 
@@ -188,5 +193,11 @@ def test_server_admission_budget_defers_without_changing_results(grids):
         for W, f in zip(ws, futs):
             assert rel(f.result(timeout=300), lg.hessvec(W)) <= 1e-12
         assert srv.stats()["waited_for_budget"] > 0
+        # a request larger than an arena is refused on its future, and the server goes on
+        big = srv.submit("g", gg.random_directions(lg.n_p, 4 * N, 999))
+        with pytest.raises(ValueError):
+            big.result(timeout=60)
+        ok = srv.submit("g", ws[0])
+        assert rel(ok.result(timeout=300), lg.hessvec(ws[0])) <= 1e-12
     finally:
         srv.close()

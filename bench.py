@@ -252,11 +252,12 @@ def measure_case118_latency(reps=20):
 
 def measure_scenarios(n_scen=8, N=64, reps=10):
     """8 load scenarios of the 1354-bus grid, N=64 directions each: 8 plain launches vs one
-    batched launch (autotuned interleave width) replayed from a captured CUDA graph."""
+    batched launch replayed from a captured CUDA graph, in the autotuned configuration
+    (interleave width, CTA shape, narrow-level k-split cap and dense-tail bound)."""
     import torch
+    from paper_2201_00241_gb300 import autotune
     from paper_2201_00241_gb300 import gridgen as gg
     from paper_2201_00241_gb300 import rh
-    from paper_2201_00241_gb300.autotune import tune_width
     grids = [_ready("case1354", k) for k in range(n_scen)]
     resolve = measure_scenario_resolves(grids)
     for lg in grids:
@@ -274,22 +275,30 @@ def measure_scenarios(n_scen=8, N=64, reps=10):
 
     plain()
     t_plain = _event_ms(plain, reps)
-    width, width_ms = tune_width(items)
+    tuned = autotune.tune(items, tails=autotune.TAILS)
+    default = next(r["ms"] for r in tuned["table"]
+                   if (r["width"], r["threads"], r["split_lanes"], r["max_tail"]) == (0, 384, 32, 128))
+    tg = autotune.with_tail([lg for lg, _, _, _ in items], tuned["max_tail"])
+    titems = [(g2,) + tuple(it[1:]) for g2, it in zip(tg, items)]
     s = torch.cuda.Stream()
     graph = torch.cuda.CUDAGraph()
-    rh.batch_hessvec(items, width)
+    autotune.launch(titems, tuned)
     torch.cuda.synchronize()
     with torch.cuda.stream(s):
         with torch.cuda.graph(graph, stream=s):
-            rh.batch_hessvec(items, width, stream=rh.C.c_void_p(s.cuda_stream))
+            autotune.launch(titems, tuned, stream=rh.C.c_void_p(s.cuda_stream))
     graph.replay()
     t_batched = _event_ms(graph.replay, reps)
     total = n_scen * N
+    top = sorted(tuned["table"], key=lambda r: r["ms"])[:5]
     return {"workload": f"case1354: {n_scen} load scenarios (per-bus loads x U[0.9,1.1], power flow re-solved), "
                         f"N={N} random unit directions each",
             "plain_hvp_per_s": total / (t_plain * 1e-3), "batched_hvp_per_s": total / (t_batched * 1e-3),
-            "plain_ms": t_plain, "batched_ms": t_batched, "width": width,
-            "width_ms": {str(k): v for k, v in width_ms.items()}, "batched_launch": "one rh_batch_hessvec, CUDA graph",
+            "plain_ms": t_plain, "batched_ms": t_batched,
+            "tuned": {k: tuned[k] for k in ("width", "threads", "ctas_per_sm", "split_lanes", "max_tail", "ms")},
+            "tuning": {"configs_measured": len(tuned["table"]), "default_config_ms": default, "fastest": top,
+                       "note": "tuning times are warm-L2 means of 3 launches: they rank configurations"},
+            "batched_launch": "one rh_batch_hessvec_cfg, CUDA graph",
             "power_flow_resolve": resolve}
 
 
@@ -483,6 +492,7 @@ def measure_serving(factors=(0.25, 0.5, 0.75, 1.0, 1.25, 1.5), n_req=400, seed=4
     1x of the open-loop sweep that follows (Poisson arrivals at factors x saturation)."""
     import concurrent.futures as cf
     import time as _t
+    from paper_2201_00241_gb300 import autotune
     from paper_2201_00241_gb300 import gridgen as gg
     from paper_2201_00241_gb300.server import RHServer
     names = ["case118", "case1354", "case2869", "case9241"]
@@ -492,6 +502,8 @@ def measure_serving(factors=(0.25, 0.5, 0.75, 1.0, 1.25, 1.5), n_req=400, seed=4
     srv = RHServer(device=torch_device_index(), budget_bytes=16 << 30, max_batch=16, n_streams=4)
     for n, lg in grids.items():
         srv.register(n, lg)
+    # launch configuration: tuned on a round of the mix's proportions at the mean N
+    tuned = srv.tune([(n, 128) for n, c in zip(names, (8, 4, 2, 1)) for _ in range(c)], tails=autotune.TAILS)
     rng = np.random.default_rng(seed)
 
     def draw(k):
@@ -547,7 +559,9 @@ def measure_serving(factors=(0.25, 0.5, 0.75, 1.0, 1.25, 1.5), n_req=400, seed=4
         return {"workload": "Poisson requests over case118/1354/2869/9241 (8:4:2:1), N ~ U{1..256}",
                 "saturated_req_per_s": sat_req, "saturated_hvp_per_s": sat_hvp,
                 "saturation": f"closed loop, {outstanding} requests outstanding for {t_sat:.0f} s",
-                "sweep": rows, "batches": srv.batches, "waited_for_budget": srv.waited_for_budget}
+                "sweep": rows, "batches": srv.batches, "waited_for_budget": srv.waited_for_budget,
+                "tuned": {k: tuned[k] for k in ("width", "threads", "ctas_per_sm", "split_lanes", "max_tail", "ms")},
+                "tuned_on": "one round of 15 requests (8:4:2:1 over the four grids), N = 128 each"}
     finally:
         srv.close()
 

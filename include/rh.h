@@ -71,6 +71,15 @@ typedef struct {
      * sweeps: one level of the four sweeps costs about as much as 1.7 M
      * entry-direction FMAs). */
     int64_t order_level_cost;
+    /* Dense-tail bound of the sparse LU of J_x (section 5.2 factors J_x once
+     * and refactors it with a fixed pattern; here the longest suffix of the
+     * elimination order with at most max_tail variables, where fill has made
+     * the factors nearly dense, is stored and swept as dense triangles).
+     * 0 takes 128; otherwise 2 <= max_tail <= 512.  Results do not depend on
+     * it beyond rounding; it trades sparse levels at the top of the
+     * elimination tree for dense work (the Python autotuner picks it per grid
+     * and batch). */
+    int32_t max_tail;
 } rh_grid_desc;
 
 typedef struct {
@@ -100,7 +109,8 @@ typedef struct {
  * answers rh_grid_dims and rh_grid_symbolic, every other call returns
  * RH_ESTATE.
  * Returns RH_EINVAL for a grid without exactly one slack bus, an out-of-range
- * or self-loop branch, a non-positive |r + jx| or a negative order_level_cost.
+ * or self-loop branch, a non-positive |r + jx|, a negative order_level_cost or a
+ * max_tail outside {0} and [2, 512].
  */
 rh_status rh_grid_create(const rh_grid_desc *desc, int32_t device, rh_grid **out);
 void rh_grid_destroy(rh_grid *grid);
@@ -232,6 +242,32 @@ typedef struct {
 
 int64_t rh_hv_work_doubles(const rh_grid *grid, int32_t N);
 rh_status rh_batch_hessvec(int32_t n_items, const rh_hv_item *items, int32_t width, void *stream);
+
+/*
+ * Launch configuration of a batched launch (Algorithm 2's level tiles):
+ *   width        target directions per CTA (the right-hand-side interleave
+ *                width); 0 spreads each item over the SMs' CTA slots
+ *   threads      CTA size, one of the compiled shapes 128, 192, 256, 384,
+ *                resident at 6, 4, 3, 2 CTAs per SM (768 threads an SM each);
+ *                0 takes 384.  A CTA's level of a sweep is one barrier: small
+ *                CTAs mean more independent level chains per SM, large ones
+ *                more (bus, direction) items per barrier.
+ *   split_lanes  narrow-level k-split cap: a level with fewer (bus, direction)
+ *                items than threads / 2 splits each row's dot product over up
+ *                to split_lanes adjacent lanes (a power of two, 1 = no split, at
+ *                most 32); 0 takes 32.
+ * RH_EINVAL for any other value (checked before anything else, also when
+ * n_items is 0).  Every configuration computes each item's HW up to rounding.
+ * rh_batch_hessvec(n, items, width, stream) is this call with {width, 0, 0}.
+ */
+typedef struct {
+    int32_t width;
+    int32_t threads;
+    int32_t split_lanes;
+} rh_hv_config;
+
+rh_status rh_batch_hessvec_cfg(int32_t n_items, const rh_hv_item *items, const rh_hv_config *config,
+                               void *stream);
 
 /*
  * Full reduced Hessian H = Hess F (n_p x n_p, column-major, leading dimension

@@ -215,6 +215,7 @@ struct rh_grid {
         g.sbr = {n_sbr, sbr_ptr, sbr_slot, sbr_maxext};
         g.ef = {n_ef, ef_ptr, ef_slot, ef_maxext};
         g.t0 = S.t0; g.T = S.n_x - S.t0;
+        g.ks_cap = 32;
         g.triL = triL; g.triU = triU; g.triUt = triUt; g.triLt = triLt;
         g.Ad = Ad; g.Atd = Atd; g.jptvd = jptvd;
         g.triLd = triLd; g.triUd = triUd; g.triUtd = triUtd; g.triLtd = triLtd;
@@ -570,11 +571,13 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     if (!d || !d->from || !d->to || !d->r || !d->x || !d->b || !d->bus_type || !d->c2 || !d->c1)
         return fail(RH_EINVAL, "grid descriptor has a NULL array");
     if (!(d->base_mva > 0.0)) return fail(RH_EINVAL, "base_mva must be positive");
+    if (d->max_tail != 0 && (d->max_tail < 2 || d->max_tail > 512))
+        return fail(RH_EINVAL, "max_tail must be 0 or in [2, 512]");
     std::unique_ptr<rh_grid> g(new rh_grid());
     g->device = device;
     g->base_mva = d->base_mva;
     std::string msg = rh::build_symbolic(d->n_bus, d->n_branch, d->from, d->to, d->r, d->x, d->b, d->bus_type,
-                                         d->order_level_cost, g->S);
+                                         d->order_level_cost, g->S, d->max_tail ? d->max_tail : 128);
     if (!msg.empty()) return fail(RH_EINVAL, msg);
     {
         static std::atomic<uint64_t> next_uid{1};
@@ -1530,8 +1533,19 @@ int64_t rh_hv_work_doubles(const rh_grid* g, int32_t N) {
 }
 
 rh_status rh_batch_hessvec(int32_t n_items, const rh_hv_item* items, int32_t width, void* stream) {
-    if (n_items < 0 || (n_items > 0 && !items)) return fail(RH_EINVAL, "bad item list");
+    const rh_hv_config cfg = {width, 0, 0};
+    return rh_batch_hessvec_cfg(n_items, items, &cfg, stream);
+}
+
+rh_status rh_batch_hessvec_cfg(int32_t n_items, const rh_hv_item* items, const rh_hv_config* cfg, void* stream) {
+    if (!cfg) return fail(RH_EINVAL, "config is NULL");
+    const int width = cfg->width;
+    const int threads = cfg->threads ? cfg->threads : 384;
+    const int ks_cap = cfg->split_lanes ? cfg->split_lanes : 32;
     if (width < 0) return fail(RH_EINVAL, "width must be >= 0");
+    if (!rh::dirs_batch_shape_ok(threads)) return fail(RH_EINVAL, "threads must be 0, 128, 192, 256 or 384");
+    if (ks_cap < 1 || ks_cap > 32 || (ks_cap & (ks_cap - 1))) return fail(RH_EINVAL, "split_lanes must be 0 or a power of two <= 32");
+    if (n_items < 0 || (n_items > 0 && !items)) return fail(RH_EINVAL, "bad item list");
     if (n_items == 0) return RH_OK;
     int device = -1;
     for (int i = 0; i < n_items; i++) {
@@ -1563,12 +1577,11 @@ rh_status rh_batch_hessvec(int32_t n_items, const rh_hv_item* items, int32_t wid
         int n = std::min(rh::kMaxBatch, n_items - first);
         B->n_items = 0;
         B->cta_ptr[0] = 0;
-        int max_T = 0;
         for (int k = 0; k < n; k++) {
             const rh_hv_item& it = items[first + k];
             if (it.N == 0) continue;
             rh_grid* g = it.grid;
-            int G = width > 0 ? (it.N + width - 1) / width : rh::dirs_default_ctas(it.N);
+            int G = width > 0 ? (it.N + width - 1) / width : rh::dirs_ctas_for(it.N, rh::dirs_batch_slots(threads));
             G = std::max(G, (it.N + 255) / 256);
             rh::DirLaunch& L = B->l[B->n_items];
             L.N = it.N;
@@ -1589,12 +1602,12 @@ rh_status rh_batch_hessvec(int32_t n_items, const rh_hv_item* items, int32_t wid
             int Tt = g->S.n_x - g->S.t0;
             L.use_tail = rh::dirs_tail_fits(Tt, it.N, G) ? 1 : 0;
             L.use_reach = 0;
-            if (L.use_tail) max_T = std::max(max_T, Tt);
             B->g[B->n_items] = g->dir();
+            B->g[B->n_items].ks_cap = ks_cap;
             B->cta_ptr[B->n_items + 1] = B->cta_ptr[B->n_items] + G;
             B->n_items++;
         }
-        rh::launch_dirs_batch(*B, max_T, (cudaStream_t)stream);
+        rh::launch_dirs_batch(*B, threads, (cudaStream_t)stream);
         RH_CUDA(cudaGetLastError());
     }
     return RH_OK;

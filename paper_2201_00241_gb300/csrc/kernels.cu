@@ -582,14 +582,14 @@ __global__ void k_build_tail(int T, int t0, const int* __restrict__ pos, const d
 // ---------------------------------------------------------------------------
 
 // Narrow levels (fewer than blockDim / 2 (bus, direction) items): every row's dot
-// product is split over ks adjacent lanes of a warp, ks a power of two up to 32 and
-// at most half the row, as long as the items still fit in the CTA's threads.  1: no
-// split.
-__device__ __forceinline__ int split_lanes(int nb, int D, int maxext) {
+// product is split over ks adjacent lanes of a warp, ks a power of two up to the
+// cap (at most 32) and at most half the row, as long as the items still fit in the
+// CTA's threads.  1: no split.
+__device__ __forceinline__ int split_lanes(int nb, int D, int maxext, int cap) {
     const int base = nb * D;
     if (2 * base > (int)blockDim.x) return 1;
     int ks = 1;
-    while (ks < 32 && 2 * base * ks <= (int)blockDim.x && 2 * ks <= maxext) ks *= 2;
+    while (2 * ks <= cap && 2 * base * ks <= (int)blockDim.x && 2 * ks <= maxext) ks *= 2;
     return ks;
 }
 
@@ -725,7 +725,7 @@ __device__ void sweep_fwd(const DirGrid& g, const LevelSet& ls, const double* __
     for (int lev = 0; lev < ls.n_lev; lev++) {
         const int b0 = ls.ptr[lev], nb = ls.ptr[lev + 1] - b0;
         const int4* __restrict__ slots = ls.slots + b0;
-        const int ks = split_lanes(nb, D, ls.maxext[lev]);
+        const int ks = split_lanes(nb, D, ls.maxext[lev], g.ks_cap);
         if (ks == 1) {
             const int items = nb * D;
             int it = threadIdx.x;
@@ -822,7 +822,7 @@ __device__ void sweep_bwd(const DirGrid& g, const LevelSet& ls, const double* __
     for (int lev = 0; lev < ls.n_lev; lev++) {
         const int b0 = ls.ptr[lev], nb = ls.ptr[lev + 1] - b0;
         const int4* __restrict__ slots = ls.slots + b0;
-        const int ks = split_lanes(nb, D, ls.maxext[lev]);
+        const int ks = split_lanes(nb, D, ls.maxext[lev], g.ks_cap);
         if (ks == 1) {
             const int items = nb * D;
             int it = threadIdx.x;
@@ -1306,7 +1306,8 @@ __global__ void __launch_bounds__(kDirThreads, kDirCtasPerSm) k_dirs(DirGrid g, 
 // Several (grid, W block) items in one launch: CTA b belongs to the item i with
 // cta_ptr[i] <= b < cta_ptr[i + 1]; the item descriptors travel in the kernel
 // parameters and are copied to shared memory.
-__global__ void __launch_bounds__(kDirThreads, kDirCtasPerSm) k_dirs_batch(DirBatch B) {
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_dirs_batch(DirBatch B) {
     __shared__ double part[kPartCap];
     __shared__ double sref[kDMax];
     __shared__ DirGrid sg;
@@ -1831,13 +1832,20 @@ cudaError_t prepare_kernels() {
     if (g_prepared[dev]) return cudaSuccess;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const void* fns[4] = {(const void*)k_dirs, (const void*)k_solve1, (const void*)k_dirs_batch,
-                          (const void*)k_solve1_batch};
+    const void* fns[3] = {(const void*)k_dirs, (const void*)k_solve1, (const void*)k_solve1_batch};
     for (const void* f : fns) {
         cudaFuncAttributes fa;
         e = cudaFuncGetAttributes(&fa, f);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+        if (e != cudaSuccess) return e;
+    }
+    // the batched direction kernel's shapes: shared memory before L1, so that the
+    // shape's resident CTAs fit an SM (6 x 35 KB for 128 threads)
+    const void* shapes[4] = {(const void*)k_dirs_batch<128, 6>, (const void*)k_dirs_batch<192, 4>,
+                             (const void*)k_dirs_batch<256, 3>, (const void*)k_dirs_batch<kDirThreads, kDirCtasPerSm>};
+    for (const void* f : shapes) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
     }
     g_prepared[dev] = true;
@@ -1890,10 +1898,30 @@ void launch_dirs(const DirGrid& g, const DirLaunch& L, cudaStream_t st) {
     k_dirs<<<L.n_cta, kDirThreads, smem, st>>>(g, L);
 }
 
-void launch_dirs_batch(const DirBatch& B, int max_T, cudaStream_t st) {
-    if (B.n_items <= 0 || B.cta_ptr[B.n_items] <= 0) return;
-    (void)max_T;
-    k_dirs_batch<<<B.cta_ptr[B.n_items], kDirThreads, 0, st>>>(B);
+// Compiled CTA shapes of the batched direction kernel: threads x resident CTAs per
+// SM, 768 threads an SM each (the register bound of the 384 x 2 shape); the
+// static shared memory (dense-tail rows, reference row, item descriptors) is
+// about 35 KB a CTA, 210 KB an SM at 6 CTAs.
+int dirs_batch_ctas_per_sm(int threads) {
+    switch (threads) {
+        case 128: return 6;
+        case 192: return 4;
+        case 256: return 3;
+        case 384: return 2;
+        default: return 0;
+    }
+}
+bool dirs_batch_shape_ok(int threads) { return dirs_batch_ctas_per_sm(threads) > 0; }
+
+void launch_dirs_batch(const DirBatch& B, int threads, cudaStream_t st) {
+    const int n = B.n_items > 0 ? B.cta_ptr[B.n_items] : 0;
+    if (n <= 0) return;
+    switch (threads) {
+        case 128: k_dirs_batch<128, 6><<<n, 128, 0, st>>>(B); break;
+        case 192: k_dirs_batch<192, 4><<<n, 192, 0, st>>>(B); break;
+        case 256: k_dirs_batch<256, 3><<<n, 256, 0, st>>>(B); break;
+        default: k_dirs_batch<kDirThreads, kDirCtasPerSm><<<n, kDirThreads, 0, st>>>(B); break;
+    }
 }
 
 void launch_scale_rows(int n, int N, const double* s, double* x, int64_t ld, cudaStream_t st) {
@@ -1929,6 +1957,7 @@ cudaError_t launch_solve1(const DirGrid& g, double* x, unsigned phases, bool use
 }
 
 int dirs_cta_slots() { return kDirCtasPerSm * num_sms(); }
+int dirs_batch_slots(int threads) { return dirs_batch_ctas_per_sm(threads) * num_sms(); }
 
 void launch_adjoint_coef(const PfGrid& g, const PfState& s, const double* lambda_int, const double* cref,
                          const int* inc_ptr, const int* inc_nb, double4_32a* inc_coef, double* d2, double* asum,

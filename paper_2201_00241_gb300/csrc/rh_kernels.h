@@ -65,6 +65,8 @@ struct DirGrid {
     const int *jp_rows, *jp_zero_rows;
     const int *jpt_ptr, *jpt_row;
     const double *jptv;
+    // narrow-level k-split cap of the sweeps: lanes per row at most (1, 2, 4, ..., 32)
+    int ks_cap;
     // projection data (per bus, original ids); rows are V/Y row indices
     int n_bus;
     const int *tp_bus;                         // bus processing order (internal order, slack last)
@@ -133,7 +135,11 @@ struct DirBatch {
     DirGrid g[kMaxBatch];
     DirLaunch l[kMaxBatch];
 };
-void launch_dirs_batch(const DirBatch& B, int max_T, cudaStream_t st);
+// threads: one of the compiled CTA shapes (dirs_batch_shape_ok)
+void launch_dirs_batch(const DirBatch& B, int threads, cudaStream_t st);
+bool dirs_batch_shape_ok(int threads);
+int dirs_batch_ctas_per_sm(int threads);   // resident CTAs per SM of a shape (0: not compiled)
+int dirs_batch_slots(int threads);         // resident CTAs of a shape on the current device
 
 // Grid-wide power-flow evaluation data (per bus, original ids).
 struct PfGrid {

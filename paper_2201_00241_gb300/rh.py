@@ -25,7 +25,7 @@ EXPORTS = ["rh_grid_create", "rh_grid_destroy", "rh_grid_dims", "rh_grid_symboli
            "rh_lagrangian_hessvec", "rh_hessvec_noalloc", "rh_hv_work_doubles", "rh_batch_hessvec",
            "rh_potrf", "rh_potrs", "rh_rto_step", "rh_set_jacobian_method", "rh_grid_coloring", "rh_jacobian",
            "rh_reduced_hessian", "rh_reduced_hessian_times", "rh_reduced_hessian_flops", "rh_fp64_fma_rate",
-           "rh_hessian_columns", "rh_bounds_check", "rh_batch_powerflow",
+           "rh_hessian_columns", "rh_bounds_check", "rh_batch_powerflow", "rh_batch_hessvec_cfg",
            "rh_last_error"]
 RH_JAC_ANALYTIC, RH_JAC_COLORED_AD = 0, 1
 
@@ -40,7 +40,14 @@ class _Desc(C.Structure):
     _fields_ = [("n_bus", C.c_int32), ("n_branch", C.c_int32), ("from_", C.c_void_p), ("to", C.c_void_p),
                 ("r", C.c_void_p), ("x", C.c_void_p), ("b", C.c_void_p), ("bus_type", C.c_void_p),
                 ("c2", C.c_void_p), ("c1", C.c_void_p), ("base_mva", C.c_double),
-                ("order_level_cost", C.c_int64)]
+                ("order_level_cost", C.c_int64), ("max_tail", C.c_int32)]
+
+
+class HvConfig(C.Structure):
+    """rh_hv_config: width (directions per CTA, 0 = spread over the SMs), threads
+    (CTA shape 128, 192, 256 or 384; 0 = 384), split_lanes (narrow-level k-split
+    cap, a power of two <= 32; 0 = 32)."""
+    _fields_ = [("width", C.c_int32), ("threads", C.c_int32), ("split_lanes", C.c_int32)]
 
 
 class HvItem(C.Structure):
@@ -95,6 +102,7 @@ def load(build_if_missing: bool = True):
         "rh_hessvec_noalloc": ([P, P, I64, I32, P, I64, P], C.c_int),
         "rh_hv_work_doubles": ([P, I32], C.c_int64),
         "rh_batch_hessvec": ([I32, P, I32, P], C.c_int),
+        "rh_batch_hessvec_cfg": ([I32, P, P, P], C.c_int),
         "rh_potrf": ([I32, P, I64, P, P], C.c_int),
         "rh_potrs": ([I32, P, I64, P, I64, I32, P, P], C.c_int),
         "rh_rto_step": ([P, P, I64, P, P, P, P, U32], C.c_int),
@@ -154,15 +162,19 @@ class Planted:
 class Grid:
     """One grid loaded on one GPU (rh_grid_create)."""
 
-    def __init__(self, grid, device: int = 0):
+    def __init__(self, grid, device: int = 0, max_tail: int = 0):
+        """max_tail: dense-tail bound of the factors (0: 128; rh_grid_desc.max_tail)."""
         lib = load()
         self.src = grid
+        self.max_tail = int(max_tail)
+        self._state = None            # (p, pd, qd) of the last set_state with host arrays
+        self._x = None                # last power-flow solution
         self._keep = [np.ascontiguousarray(grid.fr, dtype=np.int32), np.ascontiguousarray(grid.to, dtype=np.int32),
                       _f64(grid.r), _f64(grid.x), _f64(grid.b), np.ascontiguousarray(grid.bus_type, dtype=np.int8),
                       _f64(grid.c2), _f64(grid.c1)]
         k = self._keep
         d = _Desc(int(grid.n_bus), int(grid.n_branch), *[_ptr(a) for a in k], float(grid.base_mva),
-                  int(grid.order_level_cost))
+                  int(grid.order_level_cost), self.max_tail)
         h = C.c_void_p(0)
         _check(lib.rh_grid_create(C.byref(d), int(device), C.byref(h)))
         self._h = h
@@ -204,6 +216,26 @@ class Grid:
         pd = None if pd is None else _f64(pd)
         qd = None if qd is None else _f64(qd)
         _check(_lib.rh_set_state(self._h, _ptr(p), _ptr(pd), _ptr(qd)))
+        if p is None:
+            self._state = None        # parameters set on the device: not known here
+        else:
+            old = self._state or (None, None, None)
+            self._state = (p.copy(), old[1] if pd is None else pd.copy(), old[2] if qd is None else qd.copy())
+        self._x = None
+
+    def clone(self, max_tail: int | None = None, device: int | None = None) -> "Grid":
+        """The same grid record loaded again (another dense-tail bound or device), brought
+        to this grid's state: set_state with its parameters and loads, power flow from its
+        last solution, adjoint.  Needs a state set from the host and a power flow."""
+        if self._state is None or self._x is None:
+            raise RuntimeError("clone needs a state set from host arrays and a power-flow solution")
+        g = Grid(self.src, self.device if device is None else device,
+                 self.max_tail if max_tail is None else max_tail)
+        p, pd, qd = self._state
+        g.set_state(p, pd, qd)
+        g.powerflow(self._x)
+        g.adjoint()
+        return g
 
     def powerflow(self, x0=None, tol=1e-12, max_iter=20, raise_on_noconv=True):
         x0 = None if x0 is None else _f64(x0)
@@ -213,6 +245,7 @@ class Grid:
         st = _lib.rh_powerflow(self._h, _ptr(x0), float(tol), int(max_iter), _ptr(x), C.byref(it), C.byref(res))
         if st != RH_ENOCONV or raise_on_noconv:
             _check(st)
+        self._x = x.copy() if st == RH_OK else None
         return x, int(it.value), float(res.value), st
 
     def adjoint(self):
@@ -362,6 +395,8 @@ class Grid:
         st = stream if stream is not None else C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
         _check(_lib.rh_rto_step(self._h, _ptr(H), H.stride(1), _ptr(d), _ptr(p_next), _ptr(info), st,
                                 RH_RTO_APPLY if apply else 0))
+        if apply:
+            self._state, self._x = None, None      # parameters now set on the device
         torch.cuda.synchronize(dev)
         return d, p_next, H, int(info.item())
 
@@ -405,10 +440,11 @@ class Grid:
         return Planted(x, p, pd, qd)
 
 
-def batch_hessvec(items, width: int = 0, stream=None):
-    """rh_batch_hessvec: items are (Grid, W, HW, work) with CUDA torch tensors W, HW
+def batch_hessvec(items, width: int = 0, stream=None, threads: int = 0, split_lanes: int = 0):
+    """rh_batch_hessvec_cfg: items are (Grid, W, HW, work) with CUDA torch tensors W, HW
     (column-major n_p x N views) and work (1-D float64 tensor of
-    rh_hv_work_doubles(grid, N) elements) or None.  Asynchronous on `stream`
+    rh_hv_work_doubles(grid, N) elements) or None.  width, threads, split_lanes:
+    the launch configuration (HvConfig; 0 = default).  Asynchronous on `stream`
     (default: torch's current stream)."""
     lib = load()
     arr = (HvItem * len(items))()
@@ -424,7 +460,8 @@ def batch_hessvec(items, width: int = 0, stream=None):
     if stream is None:
         import torch
         stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-    _check(lib.rh_batch_hessvec(len(items), arr, int(width), stream))
+    cfg = HvConfig(int(width), int(threads), int(split_lanes))
+    _check(lib.rh_batch_hessvec_cfg(len(items), arr, C.byref(cfg), stream))
 
 
 def batch_powerflow(grids, x0=None, tol=1e-12, max_iter=20):
@@ -453,6 +490,9 @@ def batch_powerflow(grids, x0=None, tol=1e-12, max_iter=20):
     st = lib.rh_batch_powerflow(n, hs, x0p, float(tol), int(max_iter), xop, _ptr(iters), _ptr(resid), _ptr(status))
     if st not in (RH_OK, RH_ENOCONV, RH_ESINGULAR):
         _check(st)
+    for g, x, s_ in zip(grids, xs, status):
+        if isinstance(g, Grid):
+            g._x = x.copy() if s_ == RH_OK else None
     return xs, iters, resid, status
 
 

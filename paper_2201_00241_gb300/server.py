@@ -24,6 +24,11 @@ recorded for p50 / p99.  Nothing is allocated per request.
 
 Each result equals the request computed alone, up to rounding: items are
 independent and only the split of a request's directions over CTAs differs.
+
+The launch configuration (interleave width, CTA shape, narrow-level k-split cap,
+and the grids' dense-tail bound) is the autotuner's: RHServer.tune measures a
+representative round of the registered grids before serving and every round
+then launches with the result.
 """
 from __future__ import annotations
 
@@ -35,7 +40,7 @@ import time
 import numpy as np
 import torch
 
-from . import rh
+from . import autotune, rh
 
 _ALIGN = 32          # doubles: every block of an arena starts on a 256-byte boundary
 
@@ -77,7 +82,8 @@ class RHServer:
         self.device = device
         self.budget = int(budget_bytes)
         self.max_batch = min(max_batch, 32)
-        self.width = width
+        self.config = {"width": int(width), "threads": 0, "split_lanes": 0}
+        self.tuned = None
         self.grids: dict[str, rh.Grid] = {}
         dev_doubles = self.budget // 8 // n_streams
         io = max(_ALIGN, min(int(dev_doubles * io_fraction), int(max_io_doubles)) // _ALIGN * _ALIGN)
@@ -97,6 +103,38 @@ class RHServer:
         """Register an adjoint-ready grid (rh_adjoint already called for its state)."""
         with self._cv:
             self.grids[name] = grid
+
+    def tune(self, requests: list[tuple[str, int]], tails=None, cache_path: str | None = None) -> dict:
+        """Autotune the launch configuration on one representative round: a request of
+        N random directions on grid `name` for each (name, N) (before serving: the
+        server must be idle).  With `tails`, also the dense-tail bound: registered grids
+        are then replaced by clones loaded with the tuned bound (same state)."""
+        import torch
+        with self._cv:
+            if self._q or any(a.busy is not None for a in self.arenas):
+                raise RuntimeError("tune() needs an idle server")
+            a = self.arenas[0]
+            items, io, work = [], 0, 0
+            rng = np.random.default_rng(0)
+            for name, N in requests:
+                g = self.grids[name]
+                n_io, n_work = _up(g.n_p * N), _up(rh.work_doubles(g, N))
+                if io + n_io > a.io or work + n_work > a.work:
+                    raise ValueError("the tuning round does not fit a server arena")
+                W = a.d[io:io + g.n_p * N].view(N, g.n_p).t()
+                W.copy_(torch.from_numpy(rng.standard_normal((g.n_p, N))))
+                HW = a.d[a.io + io:a.io + io + g.n_p * N].view(N, g.n_p).t()
+                items.append((g, W, HW, a.d[2 * a.io + work:2 * a.io + work + n_work]))
+                io += n_io
+                work += n_work
+            with torch.cuda.device(self.device):
+                res = autotune.tune(items, tails=tails, cache_path=cache_path)
+            if tails is not None and res["max_tail"] is not None:
+                for name in {n for n, _ in requests}:
+                    self.grids[name] = autotune.with_tail([self.grids[name]], res["max_tail"])[0]
+            self.config = {k: res[k] for k in ("width", "threads", "split_lanes")}
+            self.tuned = res
+        return res
 
     def submit(self, name: str, W: np.ndarray) -> cf.Future:
         fut: cf.Future = cf.Future()
@@ -118,7 +156,7 @@ class RHServer:
         lat = np.array(self.latencies) * 1e3
         return {"requests": len(lat), "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
                 "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None, "batches": self.batches,
-                "waited_for_budget": self.waited_for_budget}
+                "waited_for_budget": self.waited_for_budget, "config": dict(self.config)}
 
     # ---- worker ---------------------------------------------------------------
     def _size(self, r: _Req):
@@ -167,7 +205,7 @@ class RHServer:
                           dWork[wi:wi + r.n_work]))
         with torch.cuda.stream(a.stream):
             dW[:end].copy_(a.h_in[:end], non_blocking=True)
-            rh.batch_hessvec(items, self.width, stream=rh.C.c_void_p(a.stream.cuda_stream))
+            autotune.launch(items, self.config, stream=rh.C.c_void_p(a.stream.cuda_stream))
             a.h_out[:end].copy_(dHW[:end], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(a.stream)

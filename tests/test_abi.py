@@ -30,32 +30,35 @@ def test_library_exports_every_declared_symbol():
     assert sorted(rh.EXPORTS) == names
 
 
-def host_grid(g):
+def host_grid(g, max_tail=0):
     """rh_grid_create with device = -1 (symbolic phase only)."""
     lib = rh.load()
     keep = [np.ascontiguousarray(g.fr, np.int32), np.ascontiguousarray(g.to, np.int32),
             np.ascontiguousarray(g.r, float), np.ascontiguousarray(g.x, float), np.ascontiguousarray(g.b, float),
             np.ascontiguousarray(g.bus_type, np.int8), np.ascontiguousarray(g.c2, float),
             np.ascontiguousarray(g.c1, float)]
-    d = rh._Desc(g.n_bus, g.n_branch, *[rh._ptr(a) for a in keep], g.base_mva, g.order_level_cost)
+    d = rh._Desc(g.n_bus, g.n_branch, *[rh._ptr(a) for a in keep], g.base_mva, g.order_level_cost, max_tail)
     h = C.c_void_p(0)
     st = lib.rh_grid_create(C.byref(d), -1, C.byref(h))
     return st, h, keep
 
 
-@pytest.mark.parametrize("case,level_cost", [("tiny9", None), ("tiny30", None), ("case118", None),
-                                             ("case1354", None), ("case2869", None), ("case9241", None),
-                                             ("case118", 0), ("case1354", 0), ("case1354", 10**12)])
-def test_symbolic_bit_exact_against_oracle(case, level_cost):
+@pytest.mark.parametrize("case,level_cost,max_tail", [
+    ("tiny9", None, 0), ("tiny30", None, 0), ("case118", None, 0), ("case1354", None, 0), ("case2869", None, 0),
+    ("case9241", None, 0), ("case118", 0, 0), ("case1354", 0, 0), ("case1354", 10**12, 0),
+    ("case1354", None, 2), ("case1354", None, 512), ("case9241", None, 64)])
+def test_symbolic_bit_exact_against_oracle(case, level_cost, max_tail):
     """Order, patterns and levels equal the oracle's, bit for bit; also with other
-    values of the level weight that both sides take from the grid record."""
+    values of the level weight that both sides take from the grid record, and with
+    other dense-tail bounds (the tail is a storage choice of the library: it changes
+    neither the order nor the patterns)."""
     import dataclasses
     g = gg.make_grid(9, 12, 3, 2) if case == "tiny9" else gg.make_grid(30, 41, 6, 4) if case == "tiny30" \
         else gg.make_case(case)
     if level_cost is not None:
         g = dataclasses.replace(g, order_level_cost=level_cost)
     lib = rh.load()
-    st, h, keep = host_grid(g)
+    st, h, keep = host_grid(g, max_tail)
     assert st == 0, lib.rh_last_error()
     try:
         dm = rh.Dims()
@@ -97,6 +100,9 @@ def test_invalid_grids_are_rejected():
     import dataclasses
     st, h, _ = host_grid(dataclasses.replace(g, order_level_cost=-1))   # negative level weight
     assert st == rh.RH_EINVAL and b"order_level_cost" in lib.rh_last_error()
+    for t in (-1, 1, 513):                                               # dense-tail bound out of range
+        st, h, _ = host_grid(g, t)
+        assert st == rh.RH_EINVAL and b"max_tail" in lib.rh_last_error()
     st, h, _ = host_grid(g)
     assert st == 0
     lib.rh_grid_destroy(h)
@@ -243,3 +249,20 @@ def test_reduced_hessian_flop_counts(case, n_sm):
     assert e.value == pytest.approx(l1 + np_ * l2, rel=1e-15)
     if case == "case9241":      # the reach and the skipped rows outweigh the dense tail
         assert e.value < a.value
+
+
+def test_batch_config_is_checked_before_anything_else():
+    """rh_batch_hessvec_cfg refuses a configuration outside the compiled shapes and
+    the k-split caps even with no items; the defaults and every compiled value pass."""
+    lib = rh.load()
+    bad = [(-1, 0, 0), (0, 64, 0), (0, 320, 0), (0, 512, 0), (0, 0, 3), (0, 0, 64), (0, 0, -2)]
+    for w, t, k in bad:
+        cfg = rh.HvConfig(w, t, k)
+        assert lib.rh_batch_hessvec_cfg(0, None, C.byref(cfg), None) == rh.RH_EINVAL, (w, t, k)
+    assert lib.rh_batch_hessvec_cfg(0, None, None, None) == rh.RH_EINVAL
+    for t in (0, 128, 192, 256, 384):
+        for k in (0, 1, 2, 4, 8, 16, 32):
+            cfg = rh.HvConfig(4, t, k)
+            assert lib.rh_batch_hessvec_cfg(0, None, C.byref(cfg), None) == rh.RH_OK, (t, k)
+    assert lib.rh_batch_hessvec(0, None, -1, None) == rh.RH_EINVAL
+    assert lib.rh_batch_hessvec(0, None, 8, None) == rh.RH_OK

@@ -52,7 +52,7 @@ struct rh_grid {
     std::vector<void*> allocs;
 
     // --- device: topology (static) --------------------------------------
-    int *yp = nullptr, *yj = nullptr, *ydiag = nullptr;
+    int *yp = nullptr, *yj = nullptr, *ydiag = nullptr, *yrow = nullptr, *pf_wb = nullptr;
     double *G = nullptr, *B = nullptr;
     int *qth = nullptr, *qv = nullptr, *ip_v = nullptr, *ip_pg = nullptr, *ix_th = nullptr, *ix_v = nullptr;
     int *pg_slot = nullptr, *jac_dst = nullptr;
@@ -83,8 +83,11 @@ struct rh_grid {
     int* arow = nullptr;   // row of every position of A
     double *triLd = nullptr, *triUd = nullptr, *triUtd = nullptr, *triLtd = nullptr;
     int *blev_ptr = nullptr, *blev_bus = nullptr, *blev_maxext = nullptr;
-    int *rf_lev_bus = nullptr, *rf_tgt_pos = nullptr, *rf_grp = nullptr;
-    int64_t* rf_tgt_gptr = nullptr;
+    int *rf_lev_bus = nullptr, *rf_tgt_pos = nullptr, *rf_grp = nullptr, *rf_xgrp = nullptr;
+    int64_t* rf_xptr = nullptr;
+    int *rf_piv_bus = nullptr, *rf_piv_pos = nullptr;
+    double4_32a* rf_piv = nullptr;          // per sparse bus: 1/u_tt, l_vt, 1/u_vv, u_tv
+    int *rf_pe_bus = nullptr, *rf_pe_pos = nullptr;
     int *jp_ptr = nullptr, *jp_col = nullptr, *jpt_ptr = nullptr, *jpt_row = nullptr, *jpt_src = nullptr;
     // identity W over all n_p columns: direction j takes column hcolmap[j], the columns in the
     // postorder of their generator buses in the elimination tree, so that the few
@@ -144,6 +147,7 @@ struct rh_grid {
     cudaStream_t stream2 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_user = nullptr;
     cudaEvent_t ev_d0 = nullptr, ev_d1 = nullptr, ev_v = nullptr, ev_c = nullptr;   // timing
+    cudaEvent_t ev_pf0 = nullptr, ev_pf1 = nullptr;   // fork / join of the L2 prefetch beside the assembly
 
     void drop_graphs() {
         if (adj_exec) cudaGraphExecDestroy(adj_exec);
@@ -157,7 +161,7 @@ struct rh_grid {
     ~rh_grid() {
         drop_graphs();
         if (apply_done) cudaEventDestroy(apply_done);
-        for (cudaEvent_t e : {ev_fork, ev_join, ev_user, ev_d0, ev_d1, ev_v, ev_c})
+        for (cudaEvent_t e : {ev_fork, ev_join, ev_user, ev_d0, ev_d1, ev_v, ev_c, ev_pf0, ev_pf1})
             if (e) cudaEventDestroy(e);
         if (stream2) cudaStreamDestroy(stream2);
         if (bstat_h) cudaFreeHost(bstat_h);
@@ -196,6 +200,7 @@ struct rh_grid {
         g.qth = qth; g.qv = qv; g.ip_v = ip_v; g.ip_pg = ip_pg;
         g.jac_dst = jac_dst; g.pg_slot = pg_slot;
         g.base_mva = base_mva; g.c2 = c2; g.c1 = c1;
+        g.yrow = yrow; g.pf_wb = pf_wb; g.n_pfw = S.pf_wb.empty() ? 0 : (int)S.pf_wb.size() - 1;
         return g;
     }
     rh::PfState st() const {
@@ -236,7 +241,10 @@ struct rh_grid {
         g.nnz = (int)S.col.size();
         g.rf_lev_bus = rf_lev_bus; g.q0 = q0; g.nv = nv;
         g.rowptr = rowptr; g.col = col; g.diagpos = diagpos; g.tpos = tpos;
-        g.tgt_pos = rf_tgt_pos; g.tgt_gptr = rf_tgt_gptr; g.grp = reinterpret_cast<const int2*>(rf_grp);
+        g.tgt_pos = rf_tgt_pos; g.grp = reinterpret_cast<const int2*>(rf_grp);
+        g.xptr = rf_xptr; g.xgrp = reinterpret_cast<const int2*>(rf_xgrp);
+        g.piv = rf_piv; g.n_piv = S.tail_bus0; g.piv_bus = rf_piv_bus; g.piv_pos = rf_piv_pos;
+        g.n_pe = (int64_t)S.rf_pe_bus.size(); g.pe_bus = rf_pe_bus; g.pe_pos = reinterpret_cast<const int4*>(rf_pe_pos);
         g.A = A; g.invdiag = invdiag; g.jmax = umax + 1; g.err = err;
         g.tailD = tailD; g.tail_pos = tail_pos;
         return g;
@@ -345,16 +353,47 @@ void enqueue_factor_copies(rh_grid* g, cudaStream_t s) {
                           g->triLd, g->triUd, g->triUtd, g->triLtd, s);
 }
 
+// L2 prefetch of the refactorisation's level data, read level by level after
+// the Jacobian assembly: on stream2 beside the assembly, joined before the first
+// update launch by enqueue_rf_prefetch_join (enqueue only)
+void enqueue_rf_prefetch(rh_grid* g, cudaStream_t s) {
+    const auto& S = g->S;
+    rh::PrefetchList L{};
+    auto add = [&](const void* p, size_t bytes) {
+        if (p && bytes >= 16 && L.n < 8) {
+            L.p[L.n] = (const char*)p;
+            L.bytes[L.n++] = bytes;
+        }
+    };
+    add(g->rf_tgt_pos, S.rf_tgt_pos.size() * sizeof(int));
+    add(g->rf_grp, S.rf_grp.size() * sizeof(int));
+    add(g->rf_xptr, S.rf_xptr.size() * sizeof(int64_t));
+    add(g->rf_xgrp, S.rf_xgrp.size() * sizeof(int));
+    add(g->rf_piv_pos, S.rf_piv_pos.size() * sizeof(int));
+    add(g->rf_pe_pos, S.rf_pe_ut.size() * sizeof(int));
+    add(g->rf_pe_bus, S.rf_pe_bus.size() * sizeof(int));
+    if (cudaEventRecord(g->ev_pf0, s) == cudaSuccess && cudaStreamWaitEvent(g->stream2, g->ev_pf0, 0) == cudaSuccess) {
+        rh::launch_prefetch_l2(L, g->stream2);
+        cudaEventRecord(g->ev_pf1, g->stream2);
+    } else {
+        rh::launch_prefetch_l2(L, s);
+        cudaEventRecord(g->ev_pf1, s);
+    }
+}
+cudaError_t enqueue_rf_prefetch_join(rh_grid* g, cudaStream_t s) { return cudaStreamWaitEvent(s, g->ev_pf1, 0); }
+
 // J_x, J_p at the current state, refactorisation, transposed copies (enqueue only).
 rh_status enqueue_factor(rh_grid* g) {
     const auto& S = g->S;
     cudaStream_t s = g->stream;
+    enqueue_rf_prefetch(g, s);
     RH_CUDA(cudaMemsetAsync(g->A, 0, sizeof(double) * S.col.size(), s));
     RH_CUDA(cudaMemsetAsync(g->umax, 0, 2 * sizeof(unsigned long long), s));
     RH_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
     rh_status st = assemble(g, g->jac_method, nullptr, s);
     if (st) return st;
-    RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_tgt_lev_ptr.data(), S.rf_n_lev, s));
+    RH_CUDA(enqueue_rf_prefetch_join(g, s));
+    RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_tgt_lev_ptr.data(), S.rf_piv_lev_ptr.data(), S.rf_n_lev, s));
     enqueue_factor_copies(g, s);
     RH_CUDA(cudaGetLastError());
     return RH_OK;
@@ -592,10 +631,12 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
         const int dims[4] = {S.n_bus, S.n_x, S.n_p, S.t0};
         mix(dims, sizeof dims);
         for (const std::vector<int>* v : {&S.ebus, &S.rowptr, &S.col, &S.rf_lev_ptr, &S.rf_lev_bus, &S.rf_tgt_pos,
-                                          &S.rf_grp, &S.jac_dst, &S.yp, &S.yj})
+                                          &S.rf_grp, &S.rf_xgrp, &S.rf_piv_lev_ptr, &S.rf_piv_bus, &S.rf_piv_pos,
+                                          &S.rf_pe_bus, &S.rf_pe_ut,
+                                          &S.jac_dst, &S.yp, &S.yj})
             mix(v->data(), v->size() * sizeof(int));
         mix(S.rf_tgt_lev_ptr.data(), S.rf_tgt_lev_ptr.size() * sizeof(int64_t));
-        mix(S.rf_tgt_gptr.data(), S.rf_tgt_gptr.size() * sizeof(int64_t));
+        mix(S.rf_xptr.data(), S.rf_xptr.size() * sizeof(int64_t));
         g->topo_hash = h;
     }
     g->colmap = tree_column_order(g->S);
@@ -606,6 +647,9 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     }
     RH_CUDA(cudaSetDevice(device));
     RH_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+    RH_CUDA(cudaStreamCreateWithFlags(&g->stream2, cudaStreamNonBlocking));
+    RH_CUDA(cudaEventCreateWithFlags(&g->ev_pf0, cudaEventDisableTiming));
+    RH_CUDA(cudaEventCreateWithFlags(&g->ev_pf1, cudaEventDisableTiming));
     RH_CUDA(rh::prepare_kernels());
     int nb = S.n_bus, nx = S.n_x, np = S.n_p;
     int zero_row = nx + np;
@@ -649,6 +693,8 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     std::vector<int> flev_ptr(S.flev_ptr), blev_ptr(S.blev_ptr);
     RH_CUDA(g->upload(g->yp, S.yp));
     RH_CUDA(g->upload(g->yj, S.yj));
+    RH_CUDA(g->upload(g->yrow, S.yrow));
+    RH_CUDA(g->upload(g->pf_wb, S.pf_wb));
     RH_CUDA(g->upload(g->ydiag, S.ydiag));
     RH_CUDA(g->upload(g->G, S.G));
     RH_CUDA(g->upload(g->B, S.B));
@@ -797,8 +843,14 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     }
     RH_CUDA(g->upload(g->rf_lev_bus, S.rf_lev_bus));
     RH_CUDA(g->upload(g->rf_tgt_pos, S.rf_tgt_pos));
-    RH_CUDA(g->upload(g->rf_tgt_gptr, S.rf_tgt_gptr));
     RH_CUDA(g->upload(g->rf_grp, S.rf_grp));
+    RH_CUDA(g->upload(g->rf_xptr, S.rf_xptr));
+    RH_CUDA(g->upload(g->rf_xgrp, S.rf_xgrp));
+    RH_CUDA(g->upload(g->rf_piv_bus, S.rf_piv_bus));
+    RH_CUDA(g->upload(g->rf_piv_pos, S.rf_piv_pos));
+    RH_CUDA(g->alloc(g->rf_piv, (size_t)S.tail_bus0));
+    RH_CUDA(g->upload(g->rf_pe_bus, S.rf_pe_bus));
+    RH_CUDA(g->upload(g->rf_pe_pos, S.rf_pe_ut));
     RH_CUDA(g->upload(g->jp_ptr, S.jp_ptr));
     {
         std::vector<int> rows, zero;
@@ -974,7 +1026,7 @@ rh_status rh_powerflow(rh_grid* g, const double* x0, double tol, int32_t max_ite
         if (nx == 0) res = 0.0;
         if (res <= tol) { out = RH_OK; break; }
         if (it >= max_iter || !std::isfinite(res)) break;
-        RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_tgt_lev_ptr.data(), S.rf_n_lev, s));
+        RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_tgt_lev_ptr.data(), S.rf_piv_lev_ptr.data(), S.rf_n_lev, s));
         enqueue_factor_copies(g, s);
         st = check_err_flag(g);
         if (st) return st;
@@ -1158,7 +1210,7 @@ rh_status enqueue_batch_newton(rh_grid* const* items, int n, uint32_t mask, int 
     std::unique_ptr<rh::RfBatch> R(new rh::RfBatch());
     R->n = B->n;
     for (int k = 0; k < B->n; k++) R->g[k] = act[k]->rf();
-    RH_CUDA(rh::launch_refactor_batch(*R, S.rf_lev_ptr.data(), S.rf_tgt_lev_ptr.data(), S.rf_n_lev, s));
+    RH_CUDA(rh::launch_refactor_batch(*R, S.rf_lev_ptr.data(), S.rf_tgt_lev_ptr.data(), S.rf_piv_lev_ptr.data(), S.rf_n_lev, s));
     const int T = S.n_x - S.t0;
     const int mode = rh::solve1_mode(S.n_x, T);
     if (mode == 2) {

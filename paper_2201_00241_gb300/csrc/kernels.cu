@@ -158,6 +158,111 @@ __device__ __forceinline__ void k_pf_eval_body(PfGrid g, PfState s, double* gres
 __global__ void k_pf_eval(PfGrid g, PfState s, double* gres, double* A, double* jpv,
                           unsigned long long* gmax, unsigned long long* jmax, int want_jac) { k_pf_eval_body(g, s, gres, A, jpv, gmax, jmax, want_jac); }
 
+// The same evaluation with one admittance entry per lane: warp w takes the buses
+// [pf_wb[w], pf_wb[w + 1]) (at most 32 entries together).  Each lane forms its
+// entry's sin/cos, the two injection terms and, off the diagonal, its four Jacobian
+// entries; after a warp barrier the lane of each bus sums its row's terms in row
+// order and finishes the bus (residual, diagonal Jacobian block) as above.  The
+// maxima go through one atomic per warp.  Blocks of kPfWarps warps.
+constexpr int kPfWarps = 4;
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u > v ? u : v;
+    }
+    return v;
+}
+__device__ __forceinline__ void pf_eval_warp_body(const PfGrid& g, const PfState& s, double* gres, double* A,
+                                                  double* jpv, unsigned long long* gmax, unsigned long long* jmax,
+                                                  int want_jac) {
+    __shared__ double sh[kPfWarps][96];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int w = blockIdx.x * kPfWarps + wl;
+    if (w >= g.n_pfw) return;                                   // warp-uniform
+    double* sw = sh[wl];
+    const int b0 = g.pf_wb[w], b1 = g.pf_wb[w + 1];
+    const int e0 = g.yp[b0], e1 = g.yp[b1];
+    const int t = e0 + lane;
+    unsigned long long jm = 0, gm = 0;
+    double vj = 0.0, xp = 0.0, xq = 0.0;
+    if (t < e1) {
+        const int i = g.yrow[t], j = g.yj[t];
+        double sn = 0.0, cs = 1.0;
+        if (j != i) sincos(s.va[i] - s.va[j], &sn, &cs);
+        vj = s.vm[j];
+        const double Gij = g.G[t], Bij = g.B[t];
+        xp = Gij * cs + Bij * sn;
+        xq = Gij * sn - Bij * cs;
+        if (want_jac && j != i && g.qth[i] >= 0) {
+            const double vi = s.vm[i];
+            double d[4];  // dP/dtheta_j, dP/dv_j, dQ/dtheta_j, dQ/dv_j
+            d[0] = vi * vj * xq;
+            d[1] = vi * xp;
+            d[2] = -vi * vj * xp;
+            d[3] = vi * xq;
+            jac_store(g, t, d, A, jpv, jm);
+        }
+    }
+    sw[lane] = vj;
+    sw[32 + lane] = xp;
+    sw[64 + lane] = xq;
+    __syncwarp();
+    const int i = b0 + lane;
+    if (i < b1) {
+        const double vi = s.vm[i];
+        double P = 0.0, Q = 0.0;
+        int tdiag = -1;
+        for (int tt = g.yp[i]; tt < g.yp[i + 1]; tt++) {
+            const int k = tt - e0;
+            P += sw[k] * sw[32 + k];
+            Q += sw[k] * sw[64 + k];
+            if (g.yj[tt] == i) tdiag = tt;
+        }
+        P *= vi;
+        Q *= vi;
+        s.P[i] = P;
+        s.Q[i] = Q;
+        const int rP = g.qth[i], rQ = g.qv[i];
+        if (rP >= 0) {                                          // the slack has no rows
+            if (gres) {
+                const double gp = P - s.pg[i] + s.pd[i];
+                gres[rP] = gp;
+                gm = ordered_bits(gp);
+                if (rQ >= 0) {
+                    const double gq = Q + s.qd[i];
+                    gres[rQ] = gq;
+                    const unsigned long long mq = ordered_bits(gq);
+                    gm = mq > gm ? mq : gm;
+                }
+            }
+            if (want_jac) {
+                if (tdiag >= 0) {
+                    const double Gii = g.G[tdiag], Bii = g.B[tdiag];
+                    double d[4];
+                    d[0] = -Q - Bii * vi * vi;
+                    d[1] = P / vi + Gii * vi;
+                    d[2] = P - Gii * vi * vi;
+                    d[3] = Q / vi - Bii * vi;
+                    jac_store(g, tdiag, d, A, jpv, jm);
+                }
+                if (g.ip_pg[i] >= 0) jpv[g.pg_slot[i]] = -1.0;
+            }
+        }
+    }
+    gm = warp_max_u64(gm);
+    jm = warp_max_u64(jm);
+    if (lane == 0) {
+        if (gres) atomicMax(gmax, gm);
+        if (want_jac) atomicMax(jmax, jm);
+    }
+}
+__global__ void __launch_bounds__(32 * kPfWarps) k_pf_eval_warp(PfGrid g, PfState s, double* gres, double* A,
+                                                                double* jpv, unsigned long long* gmax,
+                                                                unsigned long long* jmax, int want_jac) {
+    pf_eval_warp_body(g, s, gres, A, jpv, gmax, jmax, want_jac);
+}
+
 __device__ __forceinline__ void k_newton_update_body(PfGrid g, PfState s, const double* dx) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n_bus) return;
@@ -270,100 +375,174 @@ __global__ void __launch_bounds__(128) k_jac_ad(PfGrid g, PfState s, const int* 
 // fixed-pattern LU refactorisation (row-wise elimination, static pivots)
 // ---------------------------------------------------------------------------
 
-// Right-looking refactorisation, pivot step: one warp per bus k.  All entries
-// it reads are final once the updates of the levels before k's are done.
-// Bus block (theta, v) of a PQ bus:
+// Right-looking refactorisation, pivot steps of every sparse bus k, once all
+// levels are done.  Bus block (theta, v) of a PQ bus:
 //   u_tt = a_tt, l_vt = a_vt / u_tt, u_vv = a_vv - l_vt u_tv,
 //   U row of v:    u_vj = a_vj - l_vt u_tj,
-//   L columns:     l_it = a_it / u_tt,  l_iv = (a_iv - l_it u_tv) / u_vv
-// for every later variable i, j of the bus's pattern (a PV bus has theta only).
-__device__ __forceinline__ void k_rf_pivot_body(RfGrid g, int b0, int nb) {
-    const int lane = threadIdx.x & 31;
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w >= nb) return;
-    const int k = g.rf_lev_bus[b0 + w];
-    const int qt = g.q0[k];
-    const bool two = g.nv[k] == 2;
-    const double tau = 1e-14 * __longlong_as_double((long long)*g.jmax);
-    const int dt = g.diagpos[qt];
-    const double utt = g.A[dt];
-    const double it = 1.0 / utt;
-    double utv = 0.0, lvt = 0.0, iv = 0.0;
-    int dv = 0;
-    if (two) {
-        dv = g.diagpos[qt + 1];
-        utv = g.A[dt + 1];
-        lvt = g.A[dv - 1] * it;
-        double uvv = fma(-lvt, utv, g.A[dv]);
-        iv = 1.0 / uvv;
-        __syncwarp();
-        if (lane == 0) {
-            g.A[dv - 1] = lvt;
+//   L columns:     l_jt = a_jt / u_tt,  l_jv = (a_jv - l_jt u_tv) / u_vv
+// for every later variable j of the bus's pattern (a PV bus has theta only), with
+// 1/u_tt, l_vt, 1/u_vv, u_tv from the bus's pivot job.  Thread x < n_piv does bus
+// x's block, the others one entry j each (positions a_tj, a_vj, a_jt, a_jv).
+__device__ __forceinline__ void k_rf_pivot_body(const RfGrid& g) {
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < g.n_piv) {
+        const int k = (int)x;
+        const int qt = g.q0[k];
+        const int dt = g.diagpos[qt];
+        const double tau = 1e-14 * __longlong_as_double((long long)*g.jmax);
+        const double4_32a pq = g.piv[k];
+        if (!(fabs(g.A[dt]) > tau)) atomicOr(g.err, 1);
+        g.invdiag[qt] = pq.x;
+        if (g.nv[k] == 2) {
+            const int dv = g.diagpos[qt + 1];
+            if (!(inb(dv, g.nnz) && inb(qt + 1, g.n_x))) return;
+            const double uvv = fma(-pq.y, pq.w, g.A[dv]);
+            g.A[dv - 1] = pq.y;
             g.A[dv] = uvv;
-            g.invdiag[qt + 1] = iv;
+            g.invdiag[qt + 1] = pq.z;
             if (!(fabs(uvv) > tau)) atomicOr(g.err, 1);
         }
+        return;
     }
-    if (lane == 0) {
-        g.invdiag[qt] = it;
-        if (!(fabs(utt) > tau)) atomicOr(g.err, 1);
-    }
-    const int ut0 = dt + (two ? 2 : 1);
-    const int uv0 = dv + 1;
-    const int n = g.rowptr[qt + 1] - ut0;
-    for (int e = lane; e < n; e += 32) {
-        if (!(inb(ut0 + e, g.nnz) && (!two || inb(uv0 + e, g.nnz)))) continue;
-        if (two) g.A[uv0 + e] = fma(-lvt, g.A[ut0 + e], g.A[uv0 + e]);
-        int pt = g.tpos[ut0 + e];
-        if (!(inb(pt, g.nnz) && (!two || inb(g.tpos[uv0 + e], g.nnz)))) continue;
-        double lt = g.A[pt] * it;
-        g.A[pt] = lt;
-        if (two) {
-            int pv = g.tpos[uv0 + e];
-            g.A[pv] = fma(-lt, utv, g.A[pv]) * iv;
-        }
+    const int64_t e = x - g.n_piv;
+    if (e >= g.n_pe) return;
+    const int k = g.pe_bus[e];
+    const int4 p = g.pe_pos[e];                     // a_tj, a_vj, a_jt, a_jv
+    if (!(inb(k, g.n_piv) && inb(p.x, g.nnz) && inb(p.z, g.nnz) && (p.y < 0 || (inb(p.y, g.nnz) && inb(p.w, g.nnz)))))
+        return;
+    const double4_32a pq = g.piv[k];
+    const double lt = g.A[p.z] * pq.x;
+    g.A[p.z] = lt;
+    if (p.y >= 0) {
+        g.A[p.y] = fma(-pq.y, g.A[p.x], g.A[p.y]);
+        g.A[p.w] = fma(-lt, pq.w, g.A[p.w]) * pq.z;
     }
 }
-__global__ void k_rf_pivot(RfGrid g, int b0, int nb) { k_rf_pivot_body(g, b0, nb); }
+__global__ void k_rf_pivot(RfGrid g) { k_rf_pivot_body(g); }
+
+// Pivot quantities of a bus from its block [a_tt a_tv; a_vt a_vv]: 1/u_tt,
+// l_vt = a_vt / u_tt, and 1/u_vv = a_tt / det (u_vv = det / a_tt, det = a_tt a_vv -
+// a_vt a_tv), so that the two reciprocals 1/a_tt and 1/det are independent (it
+// and idet given).  Stored as {1/u_tt, l_vt, 1/u_vv, u_tv}.
+__device__ __forceinline__ double rf_det(double att, double atv, double avt, double avv) {
+    return fma(att, avv, -(avt * atv));
+}
+__device__ __forceinline__ void rf_piv_store(const RfGrid& g, int j, double att, double atv, double avt, double it,
+                                             double idet, bool two) {
+    double lvt = 0.0, iv = 0.0, utv = 0.0;
+    if (two) {
+        utv = atv;
+        lvt = avt * it;
+        iv = att * idet;
+    }
+    if (inb(j, g.n_piv)) {
+        double4_32a r;
+        r.x = it; r.y = lvt; r.z = iv; r.w = utv;
+        g.piv[j] = r;
+    }
+}
+// Pivot jobs of the leaves (buses whose block no level updates), before the
+// first level: one thread per job, the block read from A.
+__device__ __forceinline__ void k_rf_leaf_piv_body(const RfGrid& g, int njob) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= njob) return;
+    double v[4];
+    for (int e = 0; e < 4; e++) {
+        const int pp = g.piv_pos[4 * q + e];
+        v[e] = (pp >= 0 && inb(pp, g.nnz)) ? g.A[pp] : 0.0;
+    }
+    const bool two = g.piv_pos[4 * q + 3] >= 0;
+    const double it = 1.0 / v[0];
+    const double idet = two ? 1.0 / rf_det(v[0], v[1], v[2], v[3]) : 0.0;
+    rf_piv_store(g, g.piv_bus[q], v[0], v[1], v[2], it, idet, two);
+}
+__global__ void k_rf_leaf_piv(RfGrid g, int njob) { k_rf_leaf_piv_body(g, njob); }
 
 // Update step of one level: every target entry a_ij of the level subtracts
 // sum_k l_ik u_kj over the buses k of the level whose pattern holds i and j
-// (fixed order: bus, then theta before v).  Bus k's entries are final raw
-// values here (its pivot step has not run), so l_it, l_iv and u_vj are formed
-// from them with exactly the operations, in the order, of the pivot step:
-// the factors come out bit for bit as with a pivot launch before every level,
-// and the pivot steps of all sparse buses run once, in one launch, at the end.
-// No entry a group reads is a target of the same level (its bus would depend
-// on the level's own buses).
-__device__ __forceinline__ void k_rf_update_body(RfGrid g, int64_t t0, int64_t nt) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nt) return;
-    t += t0;
-    double acc = 0.0;
-    for (int64_t c = g.tgt_gptr[t]; c < g.tgt_gptr[t + 1]; c++) {
-        const int2 d = g.grp[3 * c], tu = g.grp[3 * c + 1], vu = g.grp[3 * c + 2];   // {dt, dv} {lt, ut} {lv, uv}
-        if (!(inb(d.x + 1, g.nnz + 1) && inb(tu.x, g.nnz) && inb(tu.y, g.nnz) &&
-              (d.y < 0 || (inb(d.y, g.nnz) && inb(vu.x, g.nnz) && inb(vu.y, g.nnz)))))
-            continue;
-        const double it = 1.0 / g.A[d.x];
-        const double lt = g.A[tu.x] * it;
-        const double ut = g.A[tu.y];
-        if (d.y >= 0) {
-            const double utv = g.A[d.x + 1];
-            const double lvt = g.A[d.y - 1] * it;
-            const double iv = 1.0 / fma(-lvt, utv, g.A[d.y]);
-            const double lv = fma(-lt, utv, g.A[vu.x]) * iv;
-            const double uv = fma(-lvt, ut, g.A[vu.y]);
-            acc = fma(lt, ut, acc);
-            acc = fma(lv, uv, acc);
-        } else {
-            acc = fma(lt, ut, acc);
+// (fixed order: bus, then theta before v).  Bus k's pivot step has not run:
+// l_it, l_iv and u_vj are formed from k's raw entries and its pivot quantities
+// with the operations of the pivot step, so the factors equal those of a pivot
+// step before every level, while the pivot steps of all sparse buses run once,
+// in one launch, at the end.  The pivot quantities (1/u_tt, l_vt, 1/u_vv, u_tv)
+// are formed once per bus by its pivot job, in the launch of the last level
+// that updates k's block (the leaves' in a launch before the first level).  No
+// entry a group reads is a target of the same level (its bus would depend on
+// the level's own buses).
+__device__ __forceinline__ double rf_group(const RfGrid& g, int2 d, int2 tu, int2 vu, double acc) {
+    if (tu.x < 0) return acc;
+    if (!(inb(d.x, g.n_piv) && inb(tu.x, g.nnz) && inb(tu.y, g.nnz) &&
+          (d.y < 0 || (inb(vu.x, g.nnz) && inb(vu.y, g.nnz)))))
+        return acc;
+    const double4_32a pq = g.piv[d.x];
+    const double lt = g.A[tu.x] * pq.x;
+    const double ut = g.A[tu.y];
+    if (d.y >= 0) {
+        const double lv = fma(-lt, pq.w, g.A[vu.x]) * pq.z;
+        const double uv = fma(-pq.y, ut, g.A[vu.y]);
+        acc = fma(lt, ut, acc);
+        return fma(lv, uv, acc);
+    }
+    return fma(lt, ut, acc);
+}
+
+// Targets [t0, t0 + nt) of one level; the first 4 * njob of them are the quads of
+// the level's pivot jobs j0 .. j0 + njob - 1 (lane e of job q: entry e of the bus's
+// block a_tt, a_tv, a_vt, a_vv, a target of this level or an empty lane).
+__device__ __forceinline__ void k_rf_update_body(const RfGrid& g, int64_t t0, int64_t nt, int j0, int njob) {
+    const int64_t tl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = t0 + (tl < nt ? tl : 0);
+    double nv = 0.0;
+    int p = -1;
+    if (tl < nt) {
+        p = g.tgt_pos[t];
+        const int2 d = g.grp[3 * t], tu = g.grp[3 * t + 1], vu = g.grp[3 * t + 2];
+        const int64_t x0 = g.xptr[t], x1 = g.xptr[t + 1];
+        if (p >= 0 && inb(p, g.nnz)) {
+            double acc = rf_group(g, d, tu, vu, 0.0);
+            int64_t c = x0;
+            for (; c + 1 < x1; c += 2) {
+                const int2 da = g.xgrp[3 * c], tua = g.xgrp[3 * c + 1], vua = g.xgrp[3 * c + 2];
+                const int2 db = g.xgrp[3 * c + 3], tub = g.xgrp[3 * c + 4], vub = g.xgrp[3 * c + 5];
+                acc = rf_group(g, da, tua, vua, acc);
+                acc = rf_group(g, db, tub, vub, acc);
+            }
+            if (c < x1) acc = rf_group(g, g.xgrp[3 * c], g.xgrp[3 * c + 1], g.xgrp[3 * c + 2], acc);
+            nv = g.A[p] - acc;
+            g.A[p] = nv;
         }
     }
-    const int p = g.tgt_pos[t];
-    if (inb(p, g.nnz)) g.A[p] -= acc;
+    // pivot jobs: the quads are whole within a warp, and a warp that holds any of
+    // them runs the shuffles with all its lanes
+    const int64_t wbase = tl - (int64_t)(threadIdx.x & 31);
+    if (wbase < 4 * (int64_t)njob) {
+        const int e = (int)(tl & 3);
+        const int64_t q = tl >> 2;
+        const bool mine = tl < 4 * (int64_t)njob;
+        double v = nv;
+        int pos3 = -1;
+        if (mine) {
+            pos3 = g.piv_pos[4 * (j0 + q) + 3];
+            if (p < 0) {
+                const int pp = g.piv_pos[4 * (j0 + q) + e];
+                v = (pp >= 0 && inb(pp, g.nnz)) ? g.A[pp] : 0.0;
+            }
+        }
+        const int b = (int)(threadIdx.x & 28);
+        const double att = __shfl_sync(0xffffffffu, v, b);
+        const double atv = __shfl_sync(0xffffffffu, v, b + 1);
+        const double avt = __shfl_sync(0xffffffffu, v, b + 2);
+        const double avv = __shfl_sync(0xffffffffu, v, b + 3);
+        // the two reciprocals in one division: 1/a_tt on lane 0 of the quad, 1/det on lane 3
+        const double x = e == 0 ? att : (e == 3 && pos3 >= 0 ? rf_det(att, atv, avt, avv) : 1.0);
+        const double r = 1.0 / x;
+        const double idet = __shfl_sync(0xffffffffu, r, b + 3);
+        if (mine && e == 0) rf_piv_store(g, g.piv_bus[j0 + q], att, atv, avt, r, idet, pos3 >= 0);
+    }
 }
-__global__ void k_rf_update(RfGrid g, int64_t t0, int64_t nt) { k_rf_update_body(g, t0, nt); }
+__global__ void k_rf_update(RfGrid g, int64_t t0, int64_t nt, int j0, int njob) {
+    k_rf_update_body(g, t0, nt, j0, njob);
+}
 
 // Dense trailing block [t0, n_x) as a tiled right-looking LU over TB x TB tiles
 // of a row-major scratch copy, spread over many SMs (GB300 runs FP64 on the
@@ -1726,6 +1905,10 @@ __global__ void k_pf_eval_batch(PfBatch B) {
     const PfBatchItem& it = B.it[blockIdx.y];
     k_pf_eval_body(it.g, it.s, it.x, it.A, it.jpv, it.umax, it.umax + 1, 1);
 }
+__global__ void __launch_bounds__(32 * kPfWarps) k_pf_eval_warp_batch(PfBatch B) {
+    const PfBatchItem& it = B.it[blockIdx.y];
+    pf_eval_warp_body(it.g, it.s, it.x, it.A, it.jpv, it.umax, it.umax + 1, 1);
+}
 
 __global__ void k_batch_status(PfBatch B, double* out) {
     const int i = threadIdx.x;
@@ -1739,8 +1922,11 @@ __global__ void k_newton_update_batch(PfBatch B) {
     k_newton_update_body(it.g, it.s, it.x);
 }
 
-__global__ void k_rf_update_batch(RfBatch B, int64_t t0, int64_t nt) { k_rf_update_body(B.g[blockIdx.y], t0, nt); }
-__global__ void k_rf_pivot_batch(RfBatch B, int b0, int nb) { k_rf_pivot_body(B.g[blockIdx.y], b0, nb); }
+__global__ void k_rf_update_batch(RfBatch B, int64_t t0, int64_t nt, int j0, int njob) {
+    k_rf_update_body(B.g[blockIdx.y], t0, nt, j0, njob);
+}
+__global__ void k_rf_leaf_piv_batch(RfBatch B, int njob) { k_rf_leaf_piv_body(B.g[blockIdx.y], njob); }
+__global__ void k_rf_pivot_batch(RfBatch B) { k_rf_pivot_body(B.g[blockIdx.y]); }
 __global__ void k_tail_gather_batch(RfBatch B) { k_tail_gather_body(B.g[blockIdx.y]); }
 __global__ void __launch_bounds__(256) k_tail_diag0_batch(RfBatch B) { k_tail_diag0_body(B.g[blockIdx.y]); }
 __global__ void __launch_bounds__(256) k_tail_panel_batch(RfBatch B, int k) { k_tail_panel_body(B.g[blockIdx.y], k); }
@@ -1776,7 +1962,11 @@ void launch_injections(const PfGrid& g, const PfState& s, cudaStream_t st) {
 
 void launch_pf_eval(const PfGrid& g, const PfState& s, double* gres, double* A, double* jpv,
                     unsigned long long* gmax, unsigned long long* jmax, bool want_jac, cudaStream_t st) {
-    if (g.n_bus > 0) k_pf_eval<<<blocks_for(g.n_bus, 64), 64, 0, st>>>(g, s, gres, A, jpv, gmax, jmax, want_jac);
+    if (g.n_pfw > 0)
+        k_pf_eval_warp<<<(g.n_pfw + kPfWarps - 1) / kPfWarps, 32 * kPfWarps, 0, st>>>(g, s, gres, A, jpv, gmax, jmax,
+                                                                                   want_jac);
+    else if (g.n_bus > 0)
+        k_pf_eval<<<blocks_for(g.n_bus, 64), 64, 0, st>>>(g, s, gres, A, jpv, gmax, jmax, want_jac);
 }
 
 cudaError_t launch_jac_ad(const PfGrid& g, const PfState& s, const int* col_th, const int* col_v, const int* col_pg,
@@ -1792,14 +1982,45 @@ void launch_newton_update(const PfGrid& g, const PfState& s, const double* dx, c
     if (g.n_bus > 0) k_newton_update<<<blocks_for(g.n_bus, 128), 128, 0, st>>>(g, s, dx);
 }
 
-cudaError_t launch_refactor(const RfGrid& g, const int* lev_ptr_host, const int64_t* tgt_lev_ptr_host, int n_lev,
-                            cudaStream_t st) {
+// L2 prefetch of read-only arrays: one bulk prefetch of up to kPrefetchChunk bytes
+// per thread (TMA units of many SMs at once).  The refactorisation's level data
+// (tens of MB on the 9241-bus grid) is otherwise read from HBM level by level,
+// after the direction sweeps of the previous state evicted it from L2.
+constexpr unsigned long long kPrefetchChunk = 4096;
+__global__ void k_prefetch_l2(PrefetchList L) {
+    const unsigned long long c = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L.n <= 0 || c >= L.first[L.n]) return;
+    int a = 0;
+    while (a + 1 < L.n && c >= L.first[a + 1]) a++;
+    const unsigned long long off = (c - L.first[a]) * kPrefetchChunk;
+    if (off >= L.bytes[a]) return;
+    unsigned long long n = L.bytes[a] - off;
+    if (n > kPrefetchChunk) n = kPrefetchChunk;
+    n &= ~15ull;
+    if (n)
+        asm volatile("{\n\t.reg .u64 ga;\n\tcvta.to.global.u64 ga, %0;\n\tcp.async.bulk.prefetch.L2.global [ga], %1;\n\t}"
+                     :: "l"(L.p[a] + off), "r"((unsigned)n) : "memory");
+}
+
+void launch_prefetch_l2(const PrefetchList& in, cudaStream_t st) {
+    PrefetchList L = in;
+    L.first[0] = 0;
+    for (int a = 0; a < L.n; a++) L.first[a + 1] = L.first[a] + (L.bytes[a] + kPrefetchChunk - 1) / kPrefetchChunk;
+    const unsigned long long nc = L.n > 0 ? L.first[L.n] : 0;
+    if (nc > 0) k_prefetch_l2<<<(unsigned)((nc + 31) / 32), 32, 0, st>>>(L);
+}
+
+cudaError_t launch_refactor(const RfGrid& g, const int* lev_ptr_host, const int64_t* tgt_lev_ptr_host,
+                            const int* piv_lev_ptr_host, int n_lev, cudaStream_t st) {
+    (void)lev_ptr_host;
+    if (n_lev > 0 && piv_lev_ptr_host[0] > 0)
+        k_rf_leaf_piv<<<blocks_for(piv_lev_ptr_host[0], 128), 128, 0, st>>>(g, piv_lev_ptr_host[0]);
     for (int lev = 0; lev < n_lev; lev++) {
-        int64_t t0 = tgt_lev_ptr_host[lev], nt = tgt_lev_ptr_host[lev + 1] - t0;
-        if (nt > 0) k_rf_update<<<blocks_for(nt, 256), 256, 0, st>>>(g, t0, nt);
+        const int64_t t0 = tgt_lev_ptr_host[lev], nt = tgt_lev_ptr_host[lev + 1] - t0;
+        const int j0 = piv_lev_ptr_host[lev], njob = piv_lev_ptr_host[lev + 1] - j0;
+        if (nt > 0) k_rf_update<<<blocks_for(nt, 256), 256, 0, st>>>(g, t0, nt, j0, njob);
     }
-    const int nb = lev_ptr_host[n_lev];   // every sparse bus
-    if (nb > 0) k_rf_pivot<<<blocks_for((int64_t)nb * 32, 128), 128, 0, st>>>(g, 0, nb);
+    if (g.n_piv + g.n_pe > 0) k_rf_pivot<<<blocks_for((int64_t)g.n_piv + g.n_pe, 256), 256, 0, st>>>(g);
     if (g.T > 0) {
         const int TT = g.T * g.T, nt = (g.T + kTailTB - 1) / kTailTB;
         k_tail_gather<<<blocks_for(TT, 256), 256, 0, st>>>(g);
@@ -1983,7 +2204,10 @@ void launch_scatter_rows(int n_rows, int N, const int* map, const double* src, i
 }
 
 void launch_pf_eval_batch(const PfBatch& B, cudaStream_t st) {
-    if (B.n > 0 && B.max_bus > 0)
+    if (B.n > 0 && B.it[0].g.n_pfw > 0)
+        k_pf_eval_warp_batch<<<dim3((unsigned)((B.it[0].g.n_pfw + kPfWarps - 1) / kPfWarps), (unsigned)B.n),
+                               32 * kPfWarps, 0, st>>>(B);
+    else if (B.n > 0 && B.max_bus > 0)
         k_pf_eval_batch<<<dim3((unsigned)blocks_for(B.max_bus, 64), (unsigned)B.n), 64, 0, st>>>(B);
 }
 
@@ -1997,15 +2221,20 @@ void launch_newton_update_batch(const PfBatch& B, cudaStream_t st) {
 }
 
 cudaError_t launch_refactor_batch(const RfBatch& B, const int* lev_ptr_host, const int64_t* tgt_lev_ptr_host,
-                                  int n_lev, cudaStream_t st) {
+                                  const int* piv_lev_ptr_host, int n_lev, cudaStream_t st) {
     if (B.n <= 0) return cudaSuccess;
     const unsigned n = (unsigned)B.n;
+    (void)lev_ptr_host;
+    if (n_lev > 0 && piv_lev_ptr_host[0] > 0)
+        k_rf_leaf_piv_batch<<<dim3((unsigned)blocks_for(piv_lev_ptr_host[0], 128), n), 128, 0, st>>>(
+            B, piv_lev_ptr_host[0]);
     for (int lev = 0; lev < n_lev; lev++) {
-        int64_t t0 = tgt_lev_ptr_host[lev], nt = tgt_lev_ptr_host[lev + 1] - t0;
-        if (nt > 0) k_rf_update_batch<<<dim3((unsigned)blocks_for(nt, 256), n), 256, 0, st>>>(B, t0, nt);
+        const int64_t t0 = tgt_lev_ptr_host[lev], nt = tgt_lev_ptr_host[lev + 1] - t0;
+        const int j0 = piv_lev_ptr_host[lev], njob = piv_lev_ptr_host[lev + 1] - j0;
+        if (nt > 0) k_rf_update_batch<<<dim3((unsigned)blocks_for(nt, 256), n), 256, 0, st>>>(B, t0, nt, j0, njob);
     }
-    const int nb = lev_ptr_host[n_lev];
-    if (nb > 0) k_rf_pivot_batch<<<dim3((unsigned)blocks_for((int64_t)nb * 32, 128), n), 128, 0, st>>>(B, 0, nb);
+    const int64_t np = (int64_t)B.g[0].n_piv + B.g[0].n_pe;
+    if (np > 0) k_rf_pivot_batch<<<dim3((unsigned)blocks_for(np, 256), n), 256, 0, st>>>(B);
     const int T = B.g[0].T;
     if (T > 0) {
         const int TT = T * T, nt = (T + kTailTB - 1) / kTailTB;

@@ -61,17 +61,32 @@ struct Symbolic {
     int rf_n_lev = 0;
     std::vector<int> rf_lev_ptr, rf_lev_bus;        // sparse buses grouped by level
     std::vector<int64_t> rf_tgt_lev_ptr;            // level -> first target
-    std::vector<int> rf_tgt_pos;                    // target position in A
-    std::vector<int64_t> rf_tgt_gptr;               // target -> first group
-    // group (target, bus k): 6 positions in A: k's theta and v diagonals (dv = -1
-    // for a PV bus), a_it, a_tj, a_iv, a_vj (-1, -1 for a PV bus)
-    std::vector<int> rf_grp;
+    std::vector<int> rf_tgt_pos;                    // target position in A (-1: an empty lane)
+    std::vector<int64_t> rf_tgt_gptr;               // (construction only) target -> first group
+    // group (target, bus k): k's theta diagonal position dt at the first level,
+    // else k itself (its pivot quantities are precomputed), k's v diagonal dv (-1
+    // for a PV bus), and the positions of a_it, a_tj, a_iv, a_vj (-1, -1 for a PV
+    // bus).  rf_grp holds each target's first group (six -1: none); its further
+    // groups are rf_xgrp[rf_xptr[t], rf_xptr[t + 1]).
+    std::vector<int> rf_grp, rf_xgrp;
+    std::vector<int64_t> rf_xptr;
+    // pivot jobs: level l computes the pivot quantities of buses
+    // rf_piv_bus[rf_piv_lev_ptr[l] ..) from the positions rf_piv_pos (4 per job:
+    // a_tt, a_tv, a_vt, a_vv; -1 for a PV bus's missing ones); job q of the level
+    // owns its targets [4 q, 4 q + 4) (the entries that level updates, else empty).
+    // Jobs [0, rf_piv_lev_ptr[0]) are the leaves, computed before the first level.
+    std::vector<int> rf_piv_lev_ptr, rf_piv_bus, rf_piv_pos;
+    // pivot steps by entry: bus, and 4 positions per entry of a U row right of the
+    // bus's block: a_tj, a_vj (-1: PV), a_jt, a_jv (-1: PV)
+    std::vector<int> rf_pe_bus, rf_pe_ut;
     int64_t rf_updates = 0;                         // multiply-subtracts of one refactorisation
 
     // admittance matrix (CSR by bus, diagonal included, parallel branches merged)
     std::vector<int> yp, yj;
     std::vector<double> G, B;
     std::vector<int> ydiag;
+    std::vector<int> yrow;                          // bus of every admittance entry
+    std::vector<int> pf_wb;                         // warp w of the evaluation: buses [pf_wb[w], pf_wb[w + 1])
 
     // J_x / J_p assembly: for every admittance entry s (bus i, neighbour-or-self j)
     // the destination of dP_i/dtheta_j, dP_i/dv_j, dQ_i/dtheta_j, dQ_i/dv_j:

@@ -152,6 +152,10 @@ struct PfGrid {
     const int *pg_slot;
     double base_mva;
     const double *c2, *c1;
+    // the warp-per-entry evaluation: bus of every admittance entry, and the buses
+    // [pf_wb[w], pf_wb[w + 1]) of warp w (n_pfw = 0: one thread per bus instead)
+    const int *yrow, *pf_wb;
+    int n_pfw;
 };
 
 struct PfState {
@@ -181,15 +185,38 @@ struct RfGrid {
     const int *rf_lev_bus, *q0;
     const uint8_t *nv;
     const int *rowptr, *col, *diagpos, *tpos;
-    const int *tgt_pos;                // update targets (positions in A), grouped by level
-    const int64_t *tgt_gptr;           // target -> first group
-    const int2 *grp;                   // 3 per group: {dt, dv}, {a_it, a_tj}, {a_iv, a_vj} positions
+    const int *tgt_pos;                // update targets (positions in A; -1: empty lane), grouped by level
+    // 3 int2 per group: {dt (first level) or bus k (later levels), dv}, {a_it, a_tj},
+    // {a_iv, a_vj} positions; grp: each target's first group (all -1: none), xgrp:
+    // its further groups [xptr[t], xptr[t + 1])
+    const int2 *grp, *xgrp;
+    const int64_t *xptr;
+    // pivot quantities per sparse bus (1/u_tt, l_vt, 1/u_vv, u_tv), written by the
+    // pivot jobs (bus piv_bus[q], block positions piv_pos[4 q ..]; see launch_refactor)
+    double4_32a *piv;
+    int n_piv;
+    const int *piv_bus, *piv_pos;
+    // pivot steps by entry (k_rf_pivot): bus and positions {a_tj, a_vj, a_jt, a_jv}
+    int64_t n_pe;
+    const int *pe_bus;
+    const int4 *pe_pos;
     double *A, *invdiag;
     const unsigned long long *jmax;
     int *err;
 };
-cudaError_t launch_refactor(const RfGrid& g, const int* lev_ptr_host, const int64_t* tgt_lev_ptr_host, int n_lev,
-                            cudaStream_t st);
+// L2 prefetch of up to 8 read-only device arrays (16-byte aligned; the bytes of
+// each are rounded down to a multiple of 16); `first` is filled by the launcher.
+struct PrefetchList {
+    int n;
+    const char* p[8];
+    unsigned long long bytes[8];
+    unsigned long long first[9];
+};
+void launch_prefetch_l2(const PrefetchList& L, cudaStream_t st);
+// One update launch per level (its pivot jobs [piv_lev_ptr[l], piv_lev_ptr[l + 1])
+// at the front), the pivot steps of every sparse bus, then the dense tail's LU.
+cudaError_t launch_refactor(const RfGrid& g, const int* lev_ptr_host, const int64_t* tgt_lev_ptr_host,
+                            const int* piv_lev_ptr_host, int n_lev, cudaStream_t st);
 // At (transposed values), Ad / Atd (the unit-diagonal factors L'', U' of J_x = D L'' U'
 // and their transpose), jptv (J_p by p index) and jptvd (D^-1 J_p by p index)
 void launch_transpose_values(int nnz, const int* tpos, const int* arow, const int* col, const int* diagpos,
@@ -255,7 +282,7 @@ void launch_pf_eval_batch(const PfBatch& B, cudaStream_t st);
 // out[2 i] = max |g| of item i, out[2 i + 1] = its pivot flag
 void launch_batch_status(const PfBatch& B, double* out, cudaStream_t st);
 cudaError_t launch_refactor_batch(const RfBatch& B, const int* lev_ptr_host, const int64_t* tgt_lev_ptr_host,
-                                  int n_lev, cudaStream_t st);
+                                  const int* piv_lev_ptr_host, int n_lev, cudaStream_t st);
 // the dense tail's triangles of the single solves (L, and U with columns scaled by 1/u_jj)
 void launch_tail_tri_batch(const TriBatch& B, cudaStream_t st);
 cudaError_t launch_solve1_batch(const Solve1Batch& B, unsigned phases, bool use_tail, int n_x, int T, cudaStream_t st);

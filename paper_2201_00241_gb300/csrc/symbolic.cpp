@@ -406,7 +406,7 @@ std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int
                         int j = S.col[ut0 + bb];
                         int tg = find_in_row(S.rowptr, S.col, i, j);
                         if (tg < 0) return "internal error: fill pattern not closed";
-                        grp.emplace_back(tg, order, std::array<int, 6>{dt, dv, lt, ut0 + bb, lv, two ? uv0 + bb : -1});
+                        grp.emplace_back(tg, order, std::array<int, 6>{k, dv, lt, ut0 + bb, lv, two ? uv0 + bb : -1});
                         S.rf_updates += two ? 2 : 1;
                     }
                 }
@@ -428,6 +428,105 @@ std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int
             S.rf_tgt_lev_ptr.push_back((int64_t)S.rf_tgt_pos.size());
         }
         S.rf_n_lev = (int)S.rf_lev_ptr.size() - 1;
+
+        // Pivot jobs.  The pivot quantities of sparse bus j (1/u_tt, l_vt, 1/u_vv, u_tv)
+        // depend on its 2x2 block only, which is final after the last level that
+        // updates it (m_j).  Level m_j computes them right after its updates: the
+        // block's four entries sit in four adjacent lanes at the front of the level (a
+        // quad; entries the level does not update are read from A), and the quad's
+        // first lane stores them.  The leaves (no update: m_j = -1) are computed by a
+        // launch of their own before the first level.  Every level then reads them
+        // instead of forming them from the block with two divisions.
+        const int n_sp = S.tail_bus0;
+        std::vector<int> pos_job(S.col.size(), -1);              // position -> 4 * bus + entry
+        for (int j = 0; j < n_sp; j++) {
+            const int qt = S.q0[j], dt = S.diagpos[qt];
+            pos_job[dt] = 4 * j;
+            if (S.nv[j] == 2) {
+                const int dv = S.diagpos[qt + 1];
+                pos_job[dt + 1] = 4 * j + 1;
+                pos_job[dv - 1] = 4 * j + 2;
+                pos_job[dv] = 4 * j + 3;
+            }
+        }
+        std::vector<int> mj(n_sp, -1);
+        for (int l = 0; l < S.rf_n_lev; l++)
+            for (int64_t t = S.rf_tgt_lev_ptr[l]; t < S.rf_tgt_lev_ptr[l + 1]; t++) {
+                const int pj = pos_job[S.rf_tgt_pos[t]];
+                if (pj >= 0) mj[pj / 4] = l;
+            }
+        // new target order per level: the quads, then the other targets in position order
+        std::vector<int> npos;
+        std::vector<int> ngrp, nxgrp;
+        std::vector<int64_t> nlev(1, 0), nxptr(1, 0);
+        S.rf_piv_bus.clear();
+        S.rf_piv_pos.clear();
+        auto add_job = [&](int j) {
+            const int qt = S.q0[j], dt = S.diagpos[qt];
+            const bool two = S.nv[j] == 2;
+            const int dv = two ? S.diagpos[qt + 1] : -1;
+            S.rf_piv_bus.push_back(j);
+            for (int e : {dt, two ? dt + 1 : -1, two ? dv - 1 : -1, dv}) S.rf_piv_pos.push_back(e);
+        };
+        std::vector<std::vector<int>> jobs(S.rf_n_lev);
+        for (int j = 0; j < n_sp; j++) {
+            if (mj[j] >= 0) jobs[mj[j]].push_back(j);
+            else add_job(j);                                  // leaves first
+        }
+        S.rf_piv_lev_ptr.assign(1, (int)S.rf_piv_bus.size());
+        auto put = [&](int64_t t) {            // target t of the old order (-1: an empty lane)
+            npos.push_back(t < 0 ? -1 : S.rf_tgt_pos[t]);
+            const int64_t g0 = t < 0 ? 0 : S.rf_tgt_gptr[t], g1 = t < 0 ? 0 : S.rf_tgt_gptr[t + 1];
+            for (int x = 0; x < 6; x++) ngrp.push_back(g1 > g0 ? S.rf_grp[6 * g0 + x] : -1);
+            for (int64_t c = g0 + 1; c < g1; c++)
+                for (int x = 0; x < 6; x++) nxgrp.push_back(S.rf_grp[6 * c + x]);
+            nxptr.push_back((int64_t)(nxgrp.size() / 6));
+        };
+        for (int l = 0; l < S.rf_n_lev; l++) {
+            const int64_t a = S.rf_tgt_lev_ptr[l], b = S.rf_tgt_lev_ptr[l + 1];
+            std::vector<int64_t> lane(4 * jobs[l].size(), -1);
+            std::vector<char> in_quad(b - a, 0);
+            for (int64_t t = a; t < b; t++) {
+                const int pj = pos_job[S.rf_tgt_pos[t]];
+                if (pj < 0 || mj[pj / 4] != l) continue;
+                const int64_t q = std::lower_bound(jobs[l].begin(), jobs[l].end(), pj / 4) - jobs[l].begin();
+                lane[4 * q + pj % 4] = t;
+                in_quad[t - a] = 1;
+            }
+            for (size_t q = 0; q < jobs[l].size(); q++) {
+                add_job(jobs[l][q]);
+                for (int e = 0; e < 4; e++) put(lane[4 * q + e]);
+            }
+            for (int64_t t = a; t < b; t++)
+                if (!in_quad[t - a]) put(t);
+            nlev.push_back((int64_t)npos.size());
+            S.rf_piv_lev_ptr.push_back((int)S.rf_piv_bus.size());
+        }
+        S.rf_tgt_pos.swap(npos);
+        S.rf_grp.swap(ngrp);
+        S.rf_xgrp.swap(nxgrp);
+        S.rf_xptr.swap(nxptr);
+        S.rf_tgt_lev_ptr.swap(nlev);
+        S.rf_tgt_gptr.clear();
+
+        // Pivot steps, one thread per sparse bus (its block: l_vt, u_vv, 1/u_kk) and one
+        // per entry of its U rows right of the block (u_vj, and l_jt, l_jv through the
+        // transposed positions)
+        S.rf_pe_ut.clear();
+        S.rf_pe_bus.clear();
+        for (int j = 0; j < n_sp; j++) {
+            const int qt = S.q0[j], dt = S.diagpos[qt];
+            const bool two = S.nv[j] == 2;
+            const int ut0 = dt + (two ? 2 : 1), n = S.rowptr[qt + 1] - ut0;
+            const int uv0 = two ? S.diagpos[qt + 1] + 1 : -1;
+            for (int e = 0; e < n; e++) {
+                S.rf_pe_bus.push_back(j);
+                S.rf_pe_ut.push_back(ut0 + e);
+                S.rf_pe_ut.push_back(two ? uv0 + e : -1);
+                S.rf_pe_ut.push_back(S.tpos[ut0 + e]);
+                S.rf_pe_ut.push_back(two ? S.tpos[uv0 + e] : -1);
+            }
+        }
     }
 
     // ---- J_p pattern and the assembly destinations -------------------------
@@ -553,6 +652,22 @@ std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int
                 S.jpt_src[d] = s;
             }
     }
+
+    // warps of the power-flow evaluation: consecutive buses whose admittance rows
+    // together hold at most 32 entries, one entry per lane (empty if some row is
+    // longer than a warp: the evaluation then takes one thread per bus)
+    S.pf_wb.assign(1, 0);
+    S.yrow.assign(S.yj.size(), 0);
+    for (int i = 0; i < n_bus; i++)
+        for (int s = S.yp[i]; s < S.yp[i + 1]; s++) S.yrow[s] = i;
+    for (int i = 0; i < n_bus; i++) {
+        if (S.yp[i + 1] - S.yp[i] > 32) {
+            S.pf_wb.clear();
+            break;
+        }
+        if (S.yp[i + 1] - S.yp[S.pf_wb.back()] > 32) S.pf_wb.push_back(i);
+    }
+    if (!S.pf_wb.empty()) S.pf_wb.push_back(n_bus);
     return "";
 }
 

@@ -483,14 +483,17 @@ def measure_plain_paths(lg, n_single=32, reps=3):
             "note": "HVP only (state resident); N=1 calls one at a time / 12 launches of N=256"}
 
 
-def measure_serving(factors=(0.25, 0.5, 0.75, 1.0, 1.25, 1.5), n_req=400, seed=4, outstanding=128, t_sat=2.0):
+def measure_serving(factors=(0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 2.0), n_req=600, warm_req=50, seed=4, outstanding=128,
+                    t_sat=2.0):
     """Poisson request stream over grids of 118, 1354, 2869 and 9241 buses (ratio 8:4:2:1),
     N ~ U{1..256} unit directions per request, through the continuous-batching server.
 
     Saturation is measured first, closed-loop: `outstanding` requests are kept in the
-    server for t_sat seconds (each completion submits the next); its request rate is the
-    1x of the open-loop sweep that follows (Poisson arrivals at factors x saturation)."""
-    import concurrent.futures as cf
+    server for t_sat seconds, each completion submitting the next from its future's
+    callback (no client thread polls); its request rate is the 1x of the open-loop sweep
+    that follows (Poisson arrivals at factors x saturation, the first warm_req requests of
+    each rate left out of the latency percentiles)."""
+    import threading
     import time as _t
     from paper_2201_00241_gb300 import autotune
     from paper_2201_00241_gb300 import gridgen as gg
@@ -515,24 +518,46 @@ def measure_serving(factors=(0.25, 0.5, 0.75, 1.0, 1.25, 1.5), n_req=400, seed=4
         pool = [draw(k) for k in range(256)]
         for name, W in pool[:16]:
             srv.submit(name, W).result()                     # warm-up
-        live = {}
-        k = 0
-        while len(live) < outstanding:
+        lock = threading.Lock()
+        st = {"k": 0, "done": 0, "hvp": 0, "live": 0, "count": False, "stop": False}
+        drained = threading.Event()
+
+        def submit_next():
+            with lock:
+                if st["stop"]:
+                    return
+                k = st["k"]
+                st["k"] += 1
+                st["live"] += 1
             name, W = pool[k % len(pool)]
-            live[srv.submit(name, W)] = W.shape[1]
-            k += 1
-        n_done = hvp_done = 0
+            srv.submit(name, W).add_done_callback(lambda f, n=W.shape[1]: on_done(n))
+
+        def on_done(n):
+            with lock:
+                st["live"] -= 1
+                if st["count"]:
+                    st["done"] += 1
+                    st["hvp"] += n
+                last = st["stop"] and st["live"] == 0
+            if last:
+                drained.set()
+            submit_next()
+
+        for _ in range(outstanding):
+            submit_next()
+        _t.sleep(0.3)                                        # reach the steady state
+        with lock:
+            st["count"] = True
         t0 = _t.perf_counter()
-        while _t.perf_counter() - t0 < t_sat:
-            done, _ = cf.wait(list(live), return_when=cf.FIRST_COMPLETED)
-            for f in done:
-                hvp_done += live.pop(f)
-                n_done += 1
-                name, W = pool[k % len(pool)]
-                live[srv.submit(name, W)] = W.shape[1]
-                k += 1
+        _t.sleep(t_sat)
+        with lock:
+            st["count"] = False
+            st["stop"] = True
+            n_done, hvp_done = st["done"], st["hvp"]
+            if st["live"] == 0:
+                drained.set()
         dt = _t.perf_counter() - t0
-        cf.wait(list(live))
+        drained.wait(60)
         sat_req, sat_hvp = n_done / dt, hvp_done / dt
         rows = []
         for f in factors:
@@ -552,14 +577,16 @@ def measure_serving(factors=(0.25, 0.5, 0.75, 1.0, 1.25, 1.5), n_req=400, seed=4
             for fu in futs:
                 fu.result()
             dt = _t.perf_counter() - t0
-            st = srv.stats()
-            rows.append({"rate_factor": f, "offered_req_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                         "throughput_req_per_s": n_req / dt,
+            lat = np.array([fu_lat for fu_lat in srv.latencies[warm_req:]]) * 1e3
+            rows.append({"rate_factor": f, "offered_req_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
+                         "p99_ms": float(np.percentile(lat, 99)), "throughput_req_per_s": n_req / dt,
                          "throughput_hvp_per_s": sum(W.shape[1] for _, W in stream) / dt})
         return {"workload": "Poisson requests over case118/1354/2869/9241 (8:4:2:1), N ~ U{1..256}",
                 "saturated_req_per_s": sat_req, "saturated_hvp_per_s": sat_hvp,
-                "saturation": f"closed loop, {outstanding} requests outstanding for {t_sat:.0f} s",
-                "sweep": rows, "batches": srv.batches, "waited_for_budget": srv.waited_for_budget,
+                "saturation": f"closed loop, {outstanding} requests outstanding for {t_sat:.0f} s, each "
+                              "completion submitting the next from its callback",
+                "sweep": rows, "sweep_requests": f"{n_req} per rate, percentiles over all but the first {warm_req}",
+                "batches": srv.batches, "waited_for_budget": srv.waited_for_budget,
                 "tuned": {k: tuned[k] for k in ("width", "threads", "ctas_per_sm", "split_lanes", "max_tail", "ms")},
                 "tuned_on": "one round of 15 requests (8:4:2:1 over the four grids), N = 128 each"}
     finally:

@@ -53,6 +53,7 @@ struct rh_grid {
 
     // --- device: topology (static) --------------------------------------
     int *yp = nullptr, *yj = nullptr, *ydiag = nullptr, *yrow = nullptr, *pf_wb = nullptr;
+    double* sc = nullptr;          // sin, cos per bus (the assembly's preparation)
     double *G = nullptr, *B = nullptr;
     int *qth = nullptr, *qv = nullptr, *ip_v = nullptr, *ip_pg = nullptr, *ix_th = nullptr, *ix_v = nullptr;
     int *pg_slot = nullptr, *jac_dst = nullptr;
@@ -205,7 +206,7 @@ struct rh_grid {
     }
     rh::PfState st() const {
         rh::PfState s;
-        s.vm = vm; s.va = va; s.pg = pg; s.pd = pd; s.qd = qd; s.P = P; s.Q = Q;
+        s.vm = vm; s.va = va; s.pg = pg; s.pd = pd; s.qd = qd; s.P = P; s.Q = Q; s.sc = sc;
         return s;
     }
     rh::DirGrid dir() const {
@@ -330,10 +331,11 @@ rh_status check_err_flag(rh_grid* g) {
 }
 
 // Injections, residual (when gres is given) and the values of J_x (into the
-// slots of A, zeroed by the caller) and J_p, by the analytic formulas or by
-// coloured forward-mode AD (enqueue only).
+// slots of A, cleared first together with the maxima and the pivot flag) and J_p,
+// by the analytic formulas or by coloured forward-mode AD (enqueue only).
 rh_status assemble(rh_grid* g, int method, double* gres, cudaStream_t s) {
     const bool ad = (method == RH_JAC_COLORED_AD);
+    rh::launch_pf_prep(g->pf(), g->st(), g->A, g->umax, g->err, true, s);
     rh::launch_pf_eval(g->pf(), g->st(), gres, g->A, g->jpv, g->umax, g->umax + 1, !ad, s);
     if (ad)
         RH_CUDA(rh::launch_jac_ad(g->pf(), g->st(), g->col_th, g->col_v, g->col_pg,
@@ -387,9 +389,6 @@ rh_status enqueue_factor(rh_grid* g) {
     const auto& S = g->S;
     cudaStream_t s = g->stream;
     enqueue_rf_prefetch(g, s);
-    RH_CUDA(cudaMemsetAsync(g->A, 0, sizeof(double) * S.col.size(), s));
-    RH_CUDA(cudaMemsetAsync(g->umax, 0, 2 * sizeof(unsigned long long), s));
-    RH_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
     rh_status st = assemble(g, g->jac_method, nullptr, s);
     if (st) return st;
     RH_CUDA(enqueue_rf_prefetch_join(g, s));
@@ -694,6 +693,7 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     RH_CUDA(g->upload(g->yp, S.yp));
     RH_CUDA(g->upload(g->yj, S.yj));
     RH_CUDA(g->upload(g->yrow, S.yrow));
+    RH_CUDA(g->alloc(g->sc, 2 * (size_t)S.n_bus));
     RH_CUDA(g->upload(g->pf_wb, S.pf_wb));
     RH_CUDA(g->upload(g->ydiag, S.ydiag));
     RH_CUDA(g->upload(g->G, S.G));
@@ -1014,9 +1014,6 @@ rh_status rh_powerflow(rh_grid* g, const double* x0, double tol, int32_t max_ite
     double res = INFINITY;
     rh_status out = RH_ENOCONV;
     for (;;) {
-        RH_CUDA(cudaMemsetAsync(g->A, 0, sizeof(double) * S.col.size(), s));
-        RH_CUDA(cudaMemsetAsync(g->umax, 0, 2 * sizeof(unsigned long long), s));
-        RH_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
         st = assemble(g, g->jac_method, g->gres, s);
         if (st) return st;
         unsigned long long bits = 0;
@@ -1196,10 +1193,7 @@ rh_status enqueue_batch_newton(rh_grid* const* items, int n, uint32_t mask, int 
         it.err = g->err;
     }
     if (phase == 0) {
-        for (rh_grid* g : act) {
-            RH_CUDA(cudaMemsetAsync(g->A, 0, sizeof(double) * S.col.size(), s));
-            RH_CUDA(cudaMemsetAsync(g->umax, 0, 2 * sizeof(unsigned long long), s));
-        }
+        rh::launch_pf_prep_batch(*B, s);
         rh::launch_pf_eval_batch(*B, s);
         rh::launch_batch_status(*B, g0->bstat_d, s);
         RH_CUDA(cudaMemcpyAsync(g0->bstat_h, g0->bstat_d, 2 * sizeof(double) * B->n, cudaMemcpyDeviceToHost, s));
@@ -1994,8 +1988,6 @@ rh_status rh_jacobian(rh_grid* g, int32_t method, int32_t* jx_row, int32_t* jx_c
     const auto& S = g->S;
     cudaStream_t s = g->stream;
     g->adjoint_ready = false;          // the factors in A are overwritten
-    RH_CUDA(cudaMemsetAsync(g->A, 0, sizeof(double) * S.col.size(), s));
-    RH_CUDA(cudaMemsetAsync(g->umax, 0, 2 * sizeof(unsigned long long), s));
     st = assemble(g, method, nullptr, s);
     if (st) return st;
     std::vector<double> A(S.col.size()), jp(S.jp_col.size());

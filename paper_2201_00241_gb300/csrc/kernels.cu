@@ -158,6 +158,33 @@ __device__ __forceinline__ void k_pf_eval_body(PfGrid g, PfState s, double* gres
 __global__ void k_pf_eval(PfGrid g, PfState s, double* gres, double* A, double* jpv,
                           unsigned long long* gmax, unsigned long long* jmax, int want_jac) { k_pf_eval_body(g, s, gres, A, jpv, gmax, jmax, want_jac); }
 
+// Per-state preparation of the assembly: sin and cos of every bus angle (the
+// assembly then forms sin and cos of each angle difference with two products), and,
+// with zero, A (the slots the assembly and the refactorisation fill), the maxima and
+// the pivot flag cleared.
+__device__ __forceinline__ void pf_prep_body(const PfGrid& g, const PfState& s, double* A, unsigned long long* umax,
+                                             int* err, int zero) {
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    if (zero) {
+        for (int64_t k = i0; k < g.nnz_a; k += stride) A[k] = 0.0;
+        if (i0 == 0) {
+            umax[0] = 0ull;
+            umax[1] = 0ull;
+            if (err) *err = 0;
+        }
+    }
+    if (s.sc)
+        for (int64_t b = i0; b < g.n_bus; b += stride) {
+            double sn, cs;
+            sincos(s.va[b], &sn, &cs);
+            s.sc[2 * b] = sn;
+            s.sc[2 * b + 1] = cs;
+        }
+}
+__global__ void k_pf_prep(PfGrid g, PfState s, double* A, unsigned long long* umax, int* err, int zero) {
+    pf_prep_body(g, s, A, umax, err, zero);
+}
+
 // The same evaluation with one admittance entry per lane: warp w takes the buses
 // [pf_wb[w], pf_wb[w + 1]) (at most 32 entries together).  Each lane forms its
 // entry's sin/cos, the two injection terms and, off the diagonal, its four Jacobian
@@ -189,7 +216,15 @@ __device__ __forceinline__ void pf_eval_warp_body(const PfGrid& g, const PfState
     if (t < e1) {
         const int i = g.yrow[t], j = g.yj[t];
         double sn = 0.0, cs = 1.0;
-        if (j != i) sincos(s.va[i] - s.va[j], &sn, &cs);
+        if (j != i) {
+            if (s.sc) {            // sin / cos of theta_i - theta_j from the buses' own
+                const double si = s.sc[2 * i], ci = s.sc[2 * i + 1], sj = s.sc[2 * j], cj = s.sc[2 * j + 1];
+                sn = fma(si, cj, -(ci * sj));
+                cs = fma(ci, cj, si * sj);
+            } else {
+                sincos(s.va[i] - s.va[j], &sn, &cs);
+            }
+        }
         vj = s.vm[j];
         const double Gij = g.G[t], Bij = g.B[t];
         xp = Gij * cs + Bij * sn;
@@ -1905,6 +1940,10 @@ __global__ void k_pf_eval_batch(PfBatch B) {
     const PfBatchItem& it = B.it[blockIdx.y];
     k_pf_eval_body(it.g, it.s, it.x, it.A, it.jpv, it.umax, it.umax + 1, 1);
 }
+__global__ void k_pf_prep_batch(PfBatch B) {
+    const PfBatchItem& it = B.it[blockIdx.y];
+    pf_prep_body(it.g, it.s, it.A, it.umax, nullptr, 1);
+}
 __global__ void __launch_bounds__(32 * kPfWarps) k_pf_eval_warp_batch(PfBatch B) {
     const PfBatchItem& it = B.it[blockIdx.y];
     pf_eval_warp_body(it.g, it.s, it.x, it.A, it.jpv, it.umax, it.umax + 1, 1);
@@ -1958,6 +1997,19 @@ __global__ void __launch_bounds__(kSolve1Threads, 1) k_solve1_batch(Solve1Batch 
 
 void launch_injections(const PfGrid& g, const PfState& s, cudaStream_t st) {
     if (g.n_bus > 0) k_injections<<<blocks_for(g.n_bus, 128), 128, 0, st>>>(g, s);
+}
+
+static unsigned prep_blocks(const PfGrid& g) {
+    const int64_t n = g.nnz_a > g.n_bus ? g.nnz_a : g.n_bus;
+    const int64_t b = (n + 1023) / 1024;             // four entries per thread
+    return (unsigned)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
+}
+void launch_pf_prep(const PfGrid& g, const PfState& s, double* A, unsigned long long* umax, int* err, bool zero,
+                    cudaStream_t st) {
+    k_pf_prep<<<prep_blocks(g), 256, 0, st>>>(g, s, A, umax, err, zero ? 1 : 0);
+}
+void launch_pf_prep_batch(const PfBatch& B, cudaStream_t st) {
+    if (B.n > 0) k_pf_prep_batch<<<dim3(prep_blocks(B.it[0].g), (unsigned)B.n), 256, 0, st>>>(B);
 }
 
 void launch_pf_eval(const PfGrid& g, const PfState& s, double* gres, double* A, double* jpv,

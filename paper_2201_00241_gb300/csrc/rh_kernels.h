@@ -161,12 +161,17 @@ struct PfGrid {
 struct PfState {
     double *vm, *va, *pg, *pd, *qd;  // per bus
     double *P, *Q;                   // injections (output)
+    double *sc;                      // per bus: sin, cos of the angle (launch_pf_prep; NULL: not kept)
 };
 
 // ---- launchers (all asynchronous on `st`) ----------------------------------
 void launch_injections(const PfGrid& g, const PfState& s, cudaStream_t st);
 // residual (internal order) and/or Jacobian values; gmax / jmax receive
 // max |g| and max |J_x| as ordered bit patterns (zeroed by the caller).
+// Before launch_pf_eval: sin and cos of every bus angle into s.sc and, with zero,
+// A (nnz_a slots), the two maxima and *err (if given) cleared.
+void launch_pf_prep(const PfGrid& g, const PfState& s, double* A, unsigned long long* umax, int* err, bool zero,
+                    cudaStream_t st);
 void launch_pf_eval(const PfGrid& g, const PfState& s, double* gres, double* A, double* jpv,
                     unsigned long long* gmax, unsigned long long* jmax, bool want_jac, cudaStream_t st);
 void launch_newton_update(const PfGrid& g, const PfState& s, const double* dx, cudaStream_t st);
@@ -277,8 +282,10 @@ struct Solve1Batch {
     DirGrid g[kMaxPfBatch];
     double* x[kMaxPfBatch];
 };
-// residual and Jacobian of every item (A and umax zeroed by the caller)
+// residual and Jacobian of every item (after launch_pf_prep_batch)
 void launch_pf_eval_batch(const PfBatch& B, cudaStream_t st);
+// every item's sin/cos per bus, A and the maxima cleared (not the pivot flag)
+void launch_pf_prep_batch(const PfBatch& B, cudaStream_t st);
 // out[2 i] = max |g| of item i, out[2 i + 1] = its pivot flag
 void launch_batch_status(const PfBatch& B, double* out, cudaStream_t st);
 cudaError_t launch_refactor_batch(const RfBatch& B, const int* lev_ptr_host, const int64_t* tgt_lev_ptr_host,

@@ -277,7 +277,7 @@ def measure_scenarios(n_scen=8, N=64, reps=10):
     t_plain = _event_ms(plain, reps)
     tuned = autotune.tune(items, tails=autotune.TAILS)
     default = next(r["ms"] for r in tuned["table"]
-                   if (r["width"], r["threads"], r["split_lanes"], r["max_tail"]) == (0, 384, 32, 128))
+                   if (r["width"], r["threads"], r["split_lanes"], r["max_tail"]) == (0, 384, 32, int(grids[0].dims.max_tail)))
     tg = autotune.with_tail([lg for lg, _, _, _ in items], tuned["max_tail"])
     titems = [(g2,) + tuple(it[1:]) for g2, it in zip(tg, items)]
     s = torch.cuda.Stream()

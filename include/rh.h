@@ -75,7 +75,10 @@ typedef struct {
      * and refactors it with a fixed pattern; here the longest suffix of the
      * elimination order with at most max_tail variables, where fill has made
      * the factors nearly dense, is stored and swept as dense triangles).
-     * 0 takes 128; otherwise 2 <= max_tail <= 512.  Results do not depend on
+     * 0 takes 16 * max(1, round(sqrt(n_x) / 16)) (the top separator of a
+     * near-planar grid has about sqrt(n_x) variables; 16, 48, 80 and 128 for
+     * the 118-, 1354-, 2869- and 9241-bus grids of the tests); otherwise
+     * 2 <= max_tail <= 512.  Results do not depend on
      * it beyond rounding; it trades sparse levels at the top of the
      * elimination tree for dense work (the Python autotuner picks it per grid
      * and batch). */
@@ -93,6 +96,9 @@ typedef struct {
                                              captured graph; 0 before the first call)    */
     int32_t hessian_kernels;              /* kernels one rh_reduced_hessian launches (its
                                              captured graph; 0 before the first call)    */
+    int32_t max_tail;                     /* dense-tail bound in use (rh_grid_desc.max_tail,
+                                             or its default)                             */
+    int32_t tail_vars;                    /* variables of the dense tail (<= max_tail)     */
 } rh_dims;
 
 /*

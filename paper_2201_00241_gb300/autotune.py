@@ -44,8 +44,7 @@ _memo: dict[str, dict] = {}
 
 def _grid_sig(g) -> list:
     d = g.dims
-    return [int(d.n_bus), int(d.n_branch), int(d.n_x), int(d.n_p), int(d.nnz_l), int(d.nnz_u),
-            int(g.max_tail or 128)]
+    return [int(d.n_bus), int(d.n_branch), int(d.n_x), int(d.n_p), int(d.nnz_l), int(d.nnz_u), int(d.max_tail)]
 
 
 def key(items, widths, shapes, splits, tails) -> str:
@@ -68,7 +67,7 @@ def with_tail(grids, max_tail: int):
     done = {}
     for g in grids:
         if id(g) not in done:
-            done[id(g)] = g if int(g.max_tail or 128) == int(max_tail) else g.clone(max_tail=max_tail)
+            done[id(g)] = g if int(g.dims.max_tail) == int(max_tail) else g.clone(max_tail=max_tail)
     return [done[id(g)] for g in grids]
 
 
@@ -88,7 +87,7 @@ def tune(items, widths=WIDTHS, shapes=SHAPES, splits=SPLITS, tails=None, reps: i
          cache_path: str | None = None) -> dict:
     """Tune rh_batch_hessvec_cfg for `items` ((Grid, W, HW, work) as rh.batch_hessvec takes).
 
-    tails: None keeps every grid's own dense-tail bound; a tuple also tries each bound
+    tails: None keeps every grid's own dense-tail bound; a tuple also tries each other bound
     (the items' grids are cloned with it for the measurement, then released).
     Returns {"width", "threads", "ctas_per_sm", "split_lanes", "max_tail", "ms",
     "table": every measured configuration with its ms, "cached": bool}."""
@@ -106,8 +105,9 @@ def tune(items, widths=WIDTHS, shapes=SHAPES, splits=SPLITS, tails=None, reps: i
         _memo[k] = cache[k]
         return dict(cache[k], cached=True)
     stream = torch.cuda.current_stream()
-    own_tail = sorted({int(g.max_tail or 128) for g, _, _, _ in items})
-    tail_list = list(tails) if tails is not None else [None]
+    own_tail = sorted({int(g.dims.max_tail) for g, _, _, _ in items})
+    # None: the grids as loaded (their own bounds); then every other candidate bound
+    tail_list = [None] + ([int(t) for t in tails if int(t) not in own_tail] if tails is not None else [])
     table = []
     for t in tail_list:
         grids = [g for g, _, _, _ in items]

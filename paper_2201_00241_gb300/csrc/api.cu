@@ -615,7 +615,7 @@ rh_status rh_grid_create(const rh_grid_desc* d, int32_t device, rh_grid** out) {
     g->device = device;
     g->base_mva = d->base_mva;
     std::string msg = rh::build_symbolic(d->n_bus, d->n_branch, d->from, d->to, d->r, d->x, d->b, d->bus_type,
-                                         d->order_level_cost, g->S, d->max_tail ? d->max_tail : 128);
+                                         d->order_level_cost, g->S, d->max_tail);
     if (!msg.empty()) return fail(RH_EINVAL, msg);
     {
         static std::atomic<uint64_t> next_uid{1};
@@ -942,6 +942,8 @@ rh_status rh_grid_dims(const rh_grid* g, rh_dims* o) {
     o->refactor_updates = S.rf_updates;
     o->setup_kernels = g->adj_kernels;
     o->hessian_kernels = g->hess_kernels;
+    o->max_tail = S.max_tail;
+    o->tail_vars = S.n_x - S.t0;
     return RH_OK;
 }
 

@@ -58,6 +58,7 @@ struct Symbolic {
     // column, run once after the last level.  The trailing block [t0, n_x) is
     // then factored densely.
     int t0 = 0, tail_bus0 = 0;
+    int max_tail = 0;                               // dense-tail bound in use (variables)
     int rf_n_lev = 0;
     std::vector<int> rf_lev_ptr, rf_lev_bus;        // sparse buses grouped by level
     std::vector<int64_t> rf_tgt_lev_ptr;            // level -> first target
@@ -118,6 +119,6 @@ struct Symbolic {
 // factored densely.
 std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int32_t* to,
                            const double* r, const double* x, const double* b,
-                           const int8_t* type, int64_t level_cost, Symbolic& S, int max_tail = 128);
+                           const int8_t* type, int64_t level_cost, Symbolic& S, int max_tail = 0);
 
 }  // namespace rh

@@ -369,6 +369,10 @@ std::string build_symbolic(int n_bus, int n_branch, const int32_t* fr, const int
         }
 
     // ---- refactorisation schedule -------------------------------------------
+    // default bound: the top separator of a near-planar grid has about sqrt(n_x)
+    // variables; rounded to the 16-column tiles of the tail's LU (at least one tile)
+    if (max_tail <= 0) max_tail = 16 * std::max(1, (int)std::lround(std::sqrt((double)S.n_x) / 16.0));
+    S.max_tail = max_tail;
     S.tail_bus0 = S.n_elim;
     while (S.tail_bus0 > 0 && S.n_x - S.q0[S.tail_bus0 - 1] <= max_tail) S.tail_bus0--;
     S.t0 = S.tail_bus0 < S.n_elim ? S.q0[S.tail_bus0] : S.n_x;

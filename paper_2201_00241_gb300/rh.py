@@ -60,7 +60,7 @@ class Dims(C.Structure):
                 ("n_pq", C.c_int32), ("n_x", C.c_int32), ("n_p", C.c_int32), ("n_levels_fwd", C.c_int32),
                 ("n_levels_bwd", C.c_int32), ("nnz_jx", C.c_int64), ("nnz_jp", C.c_int64), ("nnz_l", C.c_int64),
                 ("nnz_u", C.c_int64), ("refactor_updates", C.c_int64), ("setup_kernels", C.c_int32),
-                ("hessian_kernels", C.c_int32)]
+                ("hessian_kernels", C.c_int32), ("max_tail", C.c_int32), ("tail_vars", C.c_int32)]
 
 
 _lib = None
@@ -163,7 +163,8 @@ class Grid:
     """One grid loaded on one GPU (rh_grid_create)."""
 
     def __init__(self, grid, device: int = 0, max_tail: int = 0):
-        """max_tail: dense-tail bound of the factors (0: 128; rh_grid_desc.max_tail)."""
+        """max_tail: dense-tail bound of the factors (0: the library's default from n_x;
+        rh_grid_desc.max_tail).  The bound in use is dims.max_tail."""
         lib = load()
         self.src = grid
         self.max_tail = int(max_tail)

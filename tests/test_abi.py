@@ -167,9 +167,9 @@ def test_reduced_hessian_flop_counts(case, n_sm):
     bwd = nv * (Up[q0 + 1] - Up[q0] - nv) + (nv == 2)
     parent = np.array([pos_of_q[Uj[Up[q] + nv[k]]] if Up[q + 1] - Up[q] > nv[k] else -1
                        for k, q in enumerate(q0)])
-    # the dense tail: the longest suffix of buses with at most 128 variables
+    # the dense tail: the longest suffix of buses with at most dm.max_tail variables
     t_bus0 = n_el
-    while t_bus0 > 0 and nx - q0[t_bus0 - 1] <= 128:
+    while t_bus0 > 0 and nx - q0[t_bus0 - 1] <= dm.max_tail:
         t_bus0 -= 1
     t0 = q0[t_bus0] if t_bus0 < n_el else nx
     T = nx - t0
@@ -266,3 +266,25 @@ def test_batch_config_is_checked_before_anything_else():
             assert lib.rh_batch_hessvec_cfg(0, None, C.byref(cfg), None) == rh.RH_OK, (t, k)
     assert lib.rh_batch_hessvec(0, None, -1, None) == rh.RH_EINVAL
     assert lib.rh_batch_hessvec(0, None, 8, None) == rh.RH_OK
+
+
+@pytest.mark.parametrize("case", ["tiny9", "tiny30", "case118", "case1354", "case2869", "case9241"])
+def test_default_dense_tail_bound(case):
+    """max_tail = 0 takes 16 * max(1, round(sqrt(n_x) / 16)) (about the top separator of a
+    near-planar grid, in whole 16-column tiles); an explicit bound is kept; the tail holds
+    at most that many variables, and the symbolic data do not depend on it."""
+    import math
+    g = gg.make_grid(9, 12, 3, 2) if case == "tiny9" else gg.make_grid(30, 41, 6, 4) if case == "tiny30" \
+        else gg.make_case(case)
+    lib = rh.load()
+    for bound in (0, 40):
+        st, h, keep = host_grid(g, bound)
+        assert st == 0, lib.rh_last_error()
+        try:
+            dm = rh.Dims()
+            assert lib.rh_grid_dims(h, C.byref(dm)) == 0
+            want = bound or 16 * max(1, int(math.floor(math.sqrt(dm.n_x) / 16.0 + 0.5)))
+            assert dm.max_tail == want
+            assert 0 <= dm.tail_vars <= want
+        finally:
+            lib.rh_grid_destroy(h)

@@ -115,7 +115,8 @@ def test_tune_returns_and_caches_every_choice(batch, tmp_path):
     res = autotune.tune(items, widths=(0, 4), shapes=(128, 384), splits=(1, 32), tails=(64, 128), cache_path=path)
     for k in ("width", "threads", "ctas_per_sm", "split_lanes", "max_tail", "ms", "table"):
         assert k in res
-    assert not res["cached"] and len(res["table"]) == 2 * 2 * 2 * 2
+    n_tails = len({64, 128} | {int(items[0][0].dims.max_tail)})
+    assert not res["cached"] and len(res["table"]) == 2 * 2 * 2 * n_tails
     assert res["ctas_per_sm"] == autotune.CTAS_PER_SM[res["threads"]]
     assert res["ms"] == min(r["ms"] for r in res["table"])
     again = autotune.tune(items, widths=(0, 4), shapes=(128, 384), splits=(1, 32), tails=(64, 128), cache_path=path)
@@ -145,7 +146,7 @@ def test_server_launches_with_tuned_configuration(batch):
             srv.register(n, lg)
         res = srv.tune([("s0", 32), ("s1", 32), ("s3", 8), ("s5", 4)], tails=autotune.TAILS)
         assert srv.config == {k: res[k] for k in ("width", "threads", "split_lanes")}
-        assert all(int(srv.grids[n].max_tail or 128) == res["max_tail"] for n in ("s0", "s1", "s3", "s5"))
+        assert all(int(srv.grids[n].dims.max_tail) == res["max_tail"] for n in ("s0", "s1", "s3", "s5"))
         reqs = [(n, gg.random_directions(lg.n_p, N, 50 + i)) for i, (n, lg, N) in
                 enumerate([(n, lg, N) for n, lg in grids.items() for N in (1, 17, 64)])]
         refs = [grids[n].hessvec(W) for n, W in reqs]          # rh_hessvec before serving starts

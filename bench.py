@@ -518,6 +518,16 @@ def measure_serving(factors=(0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 2.0), n_req=600, w
         pool = [draw(k) for k in range(256)]
         for name, W in pool[:16]:
             srv.submit(name, W).result()                     # warm-up
+        # each grid's request of N = 256 alone in the idle server (arrival to result)
+        solo = {}
+        for n in names:
+            W = gg.random_directions(grids[n].n_p, 256, 77)
+            ts = []
+            for _ in range(5):
+                t0 = _t.perf_counter()
+                srv.submit(n, W).result()
+                ts.append((_t.perf_counter() - t0) * 1e3)
+            solo[n] = float(np.median(ts))
         lock = threading.Lock()
         st = {"k": 0, "done": 0, "hvp": 0, "live": 0, "count": False, "stop": False}
         drained = threading.Event()
@@ -564,7 +574,8 @@ def measure_serving(factors=(0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 2.0), n_req=600, w
             rate = f * sat_req
             stream = [draw(1000 * int(100 * f) + j) for j in range(n_req)]
             gaps = rng.exponential(1.0 / rate, n_req)
-            srv.latencies = []
+            srv.reset_latencies()
+            h0 = dict(srv.host_s)
             t0 = _t.perf_counter()
             t_next = t0
             futs = []
@@ -577,15 +588,18 @@ def measure_serving(factors=(0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 2.0), n_req=600, w
             for fu in futs:
                 fu.result()
             dt = _t.perf_counter() - t0
-            lat = np.array([fu_lat for fu_lat in srv.latencies[warm_req:]]) * 1e3
-            rows.append({"rate_factor": f, "offered_req_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
-                         "p99_ms": float(np.percentile(lat, 99)), "throughput_req_per_s": n_req / dt,
-                         "throughput_hvp_per_s": sum(W.shape[1] for _, W in stream) / dt})
+            st = srv.stats(skip=warm_req)
+            rows.append({"rate_factor": f, "offered_req_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                         "throughput_req_per_s": n_req / dt,
+                         "throughput_hvp_per_s": sum(W.shape[1] for _, W in stream) / dt,
+                         "per_grid": {n: (round(v["p50_ms"], 3), round(v["p99_ms"], 3)) for n, v in st["per_grid"].items()},
+                         "worker_busy": {k: (srv.host_s[k] - h0[k]) / dt for k in h0}})
         return {"workload": "Poisson requests over case118/1354/2869/9241 (8:4:2:1), N ~ U{1..256}",
                 "saturated_req_per_s": sat_req, "saturated_hvp_per_s": sat_hvp,
                 "saturation": f"closed loop, {outstanding} requests outstanding for {t_sat:.0f} s, each "
                               "completion submitting the next from its callback",
                 "sweep": rows, "sweep_requests": f"{n_req} per rate, percentiles over all but the first {warm_req}",
+                "alone_n256_ms": solo,
                 "batches": srv.batches, "waited_for_budget": srv.waited_for_budget,
                 "tuned": {k: tuned[k] for k in ("width", "threads", "ctas_per_sm", "split_lanes", "max_tail", "ms")},
                 "tuned_on": "one round of 15 requests (8:4:2:1 over the four grids), N = 128 each"}

@@ -10,9 +10,12 @@ own memory arena allocated once at start-up:
 * device: the W blocks, the HW blocks and the direction workspaces of one round;
 * pinned host: the staging of the round's W blocks and of its HW results.
 
-Admission is by memory footprint: waiting requests join the next free arena's
-round, in arrival order, while their W, HW and workspace fit in it (a request
-that does not fit waits for a later round; one larger than an arena is refused).
+Admission is by memory footprint and size class: the oldest waiting request opens
+the next free arena's round, and waiting requests of grids of a comparable size
+(n_x within mix_ratio) join it, in arrival order, while their W, HW and workspace
+fit in it (a request that does not fit waits for a later round; one larger than
+an arena is refused).  A round's requests all complete with its one launch, so a
+small request never waits there for a grid many times larger.
 A round is then three operations on its stream: one copy of all its W blocks to
 the device, ONE rh_batch_hessvec launch over all its requests (cross-instance
 batching: grids of different sizes and widths in one kernel), and one copy of
@@ -49,6 +52,14 @@ def _up(n: int) -> int:
     return (n + _ALIGN - 1) // _ALIGN * _ALIGN
 
 
+# rh_hv_item as a numpy record (the same layout as rh.HvItem), so that a round's item
+# list is built with array operations instead of one ctypes structure per request
+_ITEM = np.dtype({"names": [f for f, _ in rh.HvItem._fields_],
+                  "formats": [np.uint64, np.uint64, np.int64, np.int32, np.uint64, np.int64, np.uint64],
+                  "offsets": [getattr(rh.HvItem, f).offset for f, _ in rh.HvItem._fields_],
+                  "itemsize": rh.C.sizeof(rh.HvItem)})
+
+
 class _Req:
     __slots__ = ("name", "W", "N", "future", "t_arrival", "n_io", "n_work")
 
@@ -69,19 +80,27 @@ class _Arena:
         self.d = torch.empty(dev_doubles, dtype=torch.float64, device=device)
         self.h_in = torch.empty(io_doubles, dtype=torch.float64).pin_memory()
         self.h_out = torch.empty(io_doubles, dtype=torch.float64).pin_memory()
+        self.h_in_np, self.h_out_np = self.h_in.numpy(), self.h_out.numpy()
+        self.base = self.d.data_ptr()                # W blocks at base, HW at base + 8 io, work after
+        self.stream_ptr = rh.C.c_void_p(self.stream.cuda_stream)
         self.busy = None                     # (event, requests, offsets) of the round in flight
 
 
 class RHServer:
     def __init__(self, device: int = 0, budget_bytes: int = 8 << 30, max_batch: int = 32, n_streams: int = 4,
-                 width: int = 0, io_fraction: float = 0.08, max_io_doubles: int = 8 << 20):
+                 width: int = 0, io_fraction: float = 0.08, max_io_doubles: int = 8 << 20,
+                 mix_ratio: float = 2.0):
         """budget_bytes: device memory of all arenas together (split evenly over n_streams);
         io_fraction: the share of an arena for W and for HW each, the rest for the direction
         workspaces (a request's workspace, 2 (n_x + n_p + 1) N doubles, is about 12 times its
-        W block); max_io_doubles caps that share, and with it each stream's pinned staging."""
+        W block); max_io_doubles caps that share, and with it each stream's pinned staging.
+        mix_ratio: a round holds grids whose n_x (the per-direction work of a CTA) is within
+        this factor of its first request's, so that a small request does not wait for a
+        grid many times larger in the same launch (0: any mix)."""
         self.device = device
         self.budget = int(budget_bytes)
         self.max_batch = min(max_batch, 32)
+        self.mix_ratio = float(mix_ratio)
         self.config = {"width": int(width), "threads": 0, "split_lanes": 0}
         self.tuned = None
         self.grids: dict[str, rh.Grid] = {}
@@ -93,7 +112,9 @@ class RHServer:
         self._cv = threading.Condition()
         self._stop = False
         self.latencies: list[float] = []
+        self.latency_grid: list[str] = []   # the grid of each entry of latencies
         self.waited_for_budget = 0     # requests held for a later round because this one was full
+        self.host_s = {"launch": 0.0, "reap": 0.0}   # worker time in round launches and result copies
         self.batches = 0
         self._worker = threading.Thread(target=self._loop, daemon=True)
         self._worker.start()
@@ -152,11 +173,25 @@ class RHServer:
             self._cv.notify()
         self._worker.join()
 
-    def stats(self) -> dict:
-        lat = np.array(self.latencies) * 1e3
+    def reset_latencies(self):
+        with self._cv:
+            self.latencies, self.latency_grid = [], []
+
+    def stats(self, skip: int = 0) -> dict:
+        """p50 / p99 latency (ms) over the completed requests after the first `skip`, overall
+        and per grid, and the batching counters."""
+        n = min(len(self.latencies), len(self.latency_grid))     # the worker may be appending
+        lat = np.array(self.latencies[skip:n]) * 1e3
+        names = self.latency_grid[skip:n]
+        per_grid = {}
+        for n in sorted(set(names)):
+            v = lat[[i for i, m in enumerate(names) if m == n]]
+            per_grid[n] = {"requests": len(v), "p50_ms": float(np.percentile(v, 50)),
+                           "p99_ms": float(np.percentile(v, 99))}
         return {"requests": len(lat), "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
                 "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None, "batches": self.batches,
-                "waited_for_budget": self.waited_for_budget, "config": dict(self.config)}
+                "waited_for_budget": self.waited_for_budget, "config": dict(self.config), "per_grid": per_grid,
+                "host_s": dict(self.host_s)}
 
     # ---- worker ---------------------------------------------------------------
     def _size(self, r: _Req):
@@ -165,52 +200,70 @@ class RHServer:
         r.n_work = _up(rh.work_doubles(g, r.N))
 
     def _admit(self, a: _Arena):
-        """Requests of the next round on arena a, in arrival order, while they fit."""
-        batch, io, work = [], 0, 0
+        """Requests of the next round on arena a: the oldest waiting request, then, in arrival
+        order, the waiting requests of grids of a comparable size (mix_ratio) while they fit.
+        Requests passed over keep their places in the queue."""
+        batch, io, work, kept = [], 0, 0, []
+        lo = hi = None
         while self._q and len(batch) < self.max_batch:
-            r = self._q[0]
+            r = self._q.popleft()
             if not r.n_io:
                 self._size(r)
             if r.n_io > a.io or r.n_work > a.work:
-                self._q.popleft()
                 r.future.set_exception(ValueError(
                     f"request of {r.N} directions on {r.name} is larger than a server arena"))
                 continue
+            nx = self.grids[r.name].n_x
+            if lo is not None and self.mix_ratio > 0 and not (lo <= nx <= hi):
+                kept.append(r)                      # another size class: a later round
+                continue
             if io + r.n_io > a.io or work + r.n_work > a.work:
                 self.waited_for_budget += 1
+                kept.append(r)
                 break
-            self._q.popleft()
+            if lo is None:
+                lo, hi = nx / self.mix_ratio if self.mix_ratio > 0 else 0, nx * self.mix_ratio
             io += r.n_io
             work += r.n_work
             batch.append(r)
+        self._q.extendleft(reversed(kept))
         return batch
 
     def _launch(self, a: _Arena, batch):
-        # W blocks side by side in the pinned staging area, then one copy to the device
+        t_start = time.perf_counter()
+        # W blocks side by side in the pinned staging area, then one copy to the device;
+        # the item list as one record array of raw device addresses
+        n_it = len(batch)
+        items = np.zeros(n_it, dtype=_ITEM)
+        grid_h, n_p, N, oo, ww = (np.empty(n_it, np.uint64), np.empty(n_it, np.int64), np.empty(n_it, np.int64),
+                                  np.empty(n_it, np.int64), np.empty(n_it, np.int64))
         offs, o, w = [], 0, 0
-        hin = a.h_in.numpy()
-        for r in batch:
-            n = self.grids[r.name].n_p * r.N
+        hin = a.h_in_np
+        for k, r in enumerate(batch):
+            g = self.grids[r.name]
+            n = g.n_p * r.N
             hin[o:o + n] = r.W.reshape(-1, order="F")
             offs.append((o, w))
+            grid_h[k], n_p[k], N[k], oo[k], ww[k] = g._h.value, g.n_p, r.N, o, w
             o += r.n_io
             w += r.n_work
         end = o                     # doubles of the round's W (and HW) blocks
-        dW, dHW, dWork = a.d[:a.io], a.d[a.io:2 * a.io], a.d[2 * a.io:]
-        items = []
-        for r, (oi, wi) in zip(batch, offs):
-            g = self.grids[r.name]
-            n = g.n_p * r.N
-            items.append((g, dW[oi:oi + n].view(r.N, g.n_p).t(), dHW[oi:oi + n].view(r.N, g.n_p).t(),
-                          dWork[wi:wi + r.n_work]))
+        items["grid"] = grid_h
+        items["W"] = a.base + 8 * oo
+        items["ldw"] = n_p
+        items["N"] = N
+        items["HW"] = a.base + 8 * (a.io + oo)
+        items["ldhw"] = n_p
+        items["work"] = a.base + 8 * (2 * a.io + ww)
         with torch.cuda.stream(a.stream):
-            dW[:end].copy_(a.h_in[:end], non_blocking=True)
-            autotune.launch(items, self.config, stream=rh.C.c_void_p(a.stream.cuda_stream))
-            a.h_out[:end].copy_(dHW[:end], non_blocking=True)
+            a.d[:end].copy_(a.h_in[:end], non_blocking=True)
+            rh.batch_hessvec_raw(items, n_it, self.config, a.stream_ptr)
+            a.h_out[:end].copy_(a.d[a.io:a.io + end], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(a.stream)
         a.busy = (ev, batch, offs)
         self.batches += 1
+        self.host_s["launch"] += time.perf_counter() - t_start
 
     def _reap(self):
         progressed = False
@@ -219,14 +272,17 @@ class RHServer:
                 continue
             _, batch, offs = a.busy
             t = time.perf_counter()
-            hout = a.h_out.numpy()
+            t_start = t
+            hout = a.h_out_np
             for r, (o, _) in zip(batch, offs):
                 n_p = self.grids[r.name].n_p
                 res = hout[o:o + n_p * r.N].reshape(n_p, r.N, order="F").copy(order="F")
                 self.latencies.append(t - r.t_arrival)
+                self.latency_grid.append(r.name)
                 r.future.set_result(res)
             a.busy = None
             progressed = True
+            self.host_s["reap"] += time.perf_counter() - t_start
         return progressed
 
     def _free_arena(self):

@@ -465,12 +465,15 @@ def batch_hessvec(items, width: int = 0, stream=None, threads: int = 0, split_la
     _check(lib.rh_batch_hessvec_cfg(len(items), arr, C.byref(cfg), stream))
 
 
-def batch_hessvec_raw(items, n_items: int, cfg: dict, stream):
-    """rh_batch_hessvec_cfg on an item array already laid out as rh_hv_item records
-    (anything exposing .ctypes.data, e.g. a numpy record array with HvItem's layout),
-    with cfg {"width", "threads", "split_lanes"}; stream a c_void_p."""
-    c = HvConfig(int(cfg.get("width", 0)), int(cfg.get("threads", 0)), int(cfg.get("split_lanes", 0)))
-    _check(load().rh_batch_hessvec_cfg(int(n_items), C.c_void_p(items.ctypes.data), C.byref(c), stream))
+def batch_hessvec_raw(items, n_items: int, cfg, stream):
+    """rh_batch_hessvec_cfg on an item array already laid out as rh_hv_item records: a
+    ctypes array of HvItem, or anything exposing .ctypes.data with HvItem's layout (a numpy
+    record array).  cfg: an HvConfig, or a dict {"width", "threads", "split_lanes"};
+    stream a c_void_p."""
+    c = cfg if isinstance(cfg, HvConfig) else HvConfig(int(cfg.get("width", 0)), int(cfg.get("threads", 0)),
+                                                      int(cfg.get("split_lanes", 0)))
+    ptr = C.addressof(items) if isinstance(items, C.Array) else items.ctypes.data
+    _check((_lib or load()).rh_batch_hessvec_cfg(int(n_items), C.c_void_p(ptr), C.byref(c), stream))
 
 
 def batch_powerflow(grids, x0=None, tol=1e-12, max_iter=20):

@@ -52,13 +52,6 @@ def _up(n: int) -> int:
     return (n + _ALIGN - 1) // _ALIGN * _ALIGN
 
 
-# rh_hv_item as a numpy record (the same layout as rh.HvItem), so that a round's item
-# list is built with array operations instead of one ctypes structure per request
-_ITEM = np.dtype({"names": [f for f, _ in rh.HvItem._fields_],
-                  "formats": [np.uint64, np.uint64, np.int64, np.int32, np.uint64, np.int64, np.uint64],
-                  "offsets": [getattr(rh.HvItem, f).offset for f, _ in rh.HvItem._fields_],
-                  "itemsize": rh.C.sizeof(rh.HvItem)})
-
 
 class _Req:
     __slots__ = ("name", "W", "N", "future", "t_arrival", "n_io", "n_work")
@@ -83,6 +76,7 @@ class _Arena:
         self.h_in_np, self.h_out_np = self.h_in.numpy(), self.h_out.numpy()
         self.base = self.d.data_ptr()                # W blocks at base, HW at base + 8 io, work after
         self.stream_ptr = rh.C.c_void_p(self.stream.cuda_stream)
+        self.items = (rh.HvItem * 32)()              # the round's item list (rh_hv_item records)
         self.busy = None                     # (event, requests, offsets) of the round in flight
 
 
@@ -102,6 +96,7 @@ class RHServer:
         self.max_batch = min(max_batch, 32)
         self.mix_ratio = float(mix_ratio)
         self.config = {"width": int(width), "threads": 0, "split_lanes": 0}
+        self._cfg = rh.HvConfig(int(width), 0, 0)
         self.tuned = None
         self.grids: dict[str, rh.Grid] = {}
         dev_doubles = self.budget // 8 // n_streams
@@ -154,6 +149,7 @@ class RHServer:
                 for name in {n for n, _ in requests}:
                     self.grids[name] = autotune.with_tail([self.grids[name]], res["max_tail"])[0]
             self.config = {k: res[k] for k in ("width", "threads", "split_lanes")}
+            self._cfg = rh.HvConfig(res["width"], res["threads"], res["split_lanes"])
             self.tuned = res
         return res
 
@@ -233,31 +229,22 @@ class RHServer:
         t_start = time.perf_counter()
         # W blocks side by side in the pinned staging area, then one copy to the device;
         # the item list as one record array of raw device addresses
-        n_it = len(batch)
-        items = np.zeros(n_it, dtype=_ITEM)
-        grid_h, n_p, N, oo, ww = (np.empty(n_it, np.uint64), np.empty(n_it, np.int64), np.empty(n_it, np.int64),
-                                  np.empty(n_it, np.int64), np.empty(n_it, np.int64))
         offs, o, w = [], 0, 0
-        hin = a.h_in_np
+        hin, items, base, io = a.h_in_np, a.items, a.base, a.io
         for k, r in enumerate(batch):
             g = self.grids[r.name]
-            n = g.n_p * r.N
-            hin[o:o + n] = r.W.reshape(-1, order="F")
+            n_p = g.n_p
+            hin[o:o + n_p * r.N] = r.W.reshape(-1, order="F")
+            it = items[k]
+            it.grid, it.W, it.ldw, it.N = g._h.value, base + 8 * o, n_p, r.N
+            it.HW, it.ldhw, it.work = base + 8 * (io + o), n_p, base + 8 * (2 * io + w)
             offs.append((o, w))
-            grid_h[k], n_p[k], N[k], oo[k], ww[k] = g._h.value, g.n_p, r.N, o, w
             o += r.n_io
             w += r.n_work
         end = o                     # doubles of the round's W (and HW) blocks
-        items["grid"] = grid_h
-        items["W"] = a.base + 8 * oo
-        items["ldw"] = n_p
-        items["N"] = N
-        items["HW"] = a.base + 8 * (a.io + oo)
-        items["ldhw"] = n_p
-        items["work"] = a.base + 8 * (2 * a.io + ww)
         with torch.cuda.stream(a.stream):
             a.d[:end].copy_(a.h_in[:end], non_blocking=True)
-            rh.batch_hessvec_raw(items, n_it, self.config, a.stream_ptr)
+            rh.batch_hessvec_raw(items, len(batch), self._cfg, a.stream_ptr)
             a.h_out[:end].copy_(a.d[a.io:a.io + end], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(a.stream)

@@ -764,8 +764,10 @@ def main():
     # the plain form of the metric's N = 256 blocks: one launch per block of 256 columns
     per_block = measure_per_block(lg, H, sptr)
 
-    # e2e through the C ABI with host buffers
-    Hh = np.empty((n_p, n_p), order="F")
+    # e2e through the C ABI with host buffers: H lands in pinned host memory (column-major)
+    import torch
+    Hh_t = torch.empty(n_p * n_p, dtype=torch.float64).pin_memory()
+    Hh = Hh_t.numpy().reshape(n_p, n_p, order="F")
     x0 = st.x.copy()
     e2e_t = []
     for i in range(0 if args.no_e2e else args.warmup + args.steps):

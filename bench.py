@@ -54,6 +54,9 @@ def parse():
                     help="skip the 118-bus latency, scenario batching, plain-path and serving measurements")
     ap.add_argument("--fp64-peak", action="store_true",
                     help="only measure the FP64 FMA rate by CTAs and warps per SM and print the table")
+    ap.add_argument("--only", choices=["case118_full_hessian", "scenario_batching", "serving", "tracking_step",
+                                       "jacobian_ad"],
+                    help="run only this extra measurement on one GPU and print its JSON (profiling runs)")
     return ap.parse_args()
 
 
@@ -686,6 +689,13 @@ def main():
             sampler.wait()
         print(json.dumps({"fp64_fma_rate": rows, "derived_peak_gflops": PEAK_FP64_GFLOPS,
                           "clocks": read_clocks(clk_path, local)}), flush=True)
+        return
+
+    if args.only:
+        torch.cuda.set_device(local)
+        fn = {"case118_full_hessian": measure_case118_latency, "scenario_batching": measure_scenarios,
+              "serving": measure_serving, "tracking_step": measure_rto, "jacobian_ad": measure_jacobian_ad}
+        print(json.dumps({args.only: fn[args.only]()}), flush=True)
         return
 
     if world > 1:

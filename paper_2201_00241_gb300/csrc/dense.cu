@@ -1,26 +1,46 @@
 // dense.cu -- dense FP64 Cholesky factorisation and solves of the real-time
 // tracking step (section 6.3, eq. 18-19): H_t d_t = -g_t with H_t = L L^T.
 //
-// Right-looking tiled algorithm over TB x TB tiles of a column-major matrix.
-// The diagonal tile of tile column k is factored by the CTA that gives it its
-// last trailing update (in the update launch of column k - 1; k_chol_diag0 for
-// the first one), so no launch reads a tile that another of its CTAs writes:
-//   k_chol_panel   L_ik = A_ik L_kk^{-T} for every tile i below the diagonal,
-//                  one CTA each; fused: the forward solve y_k = L_kk^{-1} b_k
-//   k_chol_update  A_ij -= L_ik L_jk^T for every trailing tile, k < j <= i
-//                  (lower half only on the diagonal); the CTA of tile
-//                  (k + 1, k + 1) then factors it; fused: b_i -= L_ik y_k
+// Right-looking tiled algorithm over TB x TB tiles of a column-major matrix,
+// one launch per tile column.  Launch k (k = -1 .. T - 1 for T tile columns;
+// c = k + 1 is the column it factors) holds:
+//   panel CTAs     one per tile i > c of column c: the tile and the diagonal
+//                  tile take their last update (column k), the diagonal tile
+//                  is factored, and L_ic = A_ic L_cc^{-T} is stored
+//   a diagonal CTA that factors tile (k, k) once more and stores L_kk and the
+//                  pivot status: the panel CTAs of launch k - 1 read that tile,
+//                  so it is only overwritten one launch later
+//   trailing CTAs  A_ij -= L_ik L_jk^T for every tile c < j <= i (lower half
+//                  only on the diagonal)
+//   with a right-hand side y (the fused forward solve L y = b): one CTA that
+//   takes y_c -= L_ck y_k and solves y_c = L_cc^{-1} y_c, and one CTA per tile
+//   row i > c that takes y_i -= L_ik y_k.
+// Every CTA that needs L_cc factors the diagonal tile itself, from the same
+// inputs with the same code, so all copies agree bit for bit.  The panel CTAs
+// come first in the grid: they carry the launch's critical path (update,
+// factorisation, triangular solve).  No launch reads a tile that another of
+// its CTAs writes.
+//
 // The solves run one launch per tile: the forward sweep L y = b writes y into a
 // workspace while the other CTAs of the launch subtract L_ik y_k from the
 // right-hand side below it, and the backward sweep L^T x = y writes x back into
-// B while its other CTAs update the workspace above.  Reads and writes of one
-// launch never touch the same tile, so no launch needs a grid-wide barrier.
+// B while its other CTAs update the workspace above.
 //
-// Eliminations inside a tile keep the columns unscaled until the end
-// (a_rc -= a_rj a_cj / a_jj), so a step reads only a column that nothing in
-// that step writes: one barrier per step.  FP64 throughout; GB300 runs FP64 on
-// the CUDA cores (the tensor cores have no fast FP64 mode), so the factorisation
-// is bound by the DFMA rate and by the dependency chain of the tile columns.
+// The diagonal tile is eliminated without divisions: step j replaces every
+// trailing entry by 2^-e_j (d_j a_rc - a_rj a_cj), with d_j the current pivot and
+// 2^-e_j the power of two that brings it into [1, 2) (cross-multiplied
+// elimination, as in Bareiss's fraction-free Gaussian elimination, with an exact
+// power-of-two rescaling in place of Bareiss's exact division).  The trailing
+// block after step j is then s_{j+1} times the ordinary Schur complement, with
+// s_{j+1} = s_j 2^-e_j d_j in [s_j, 2 s_j): bounded by 2^TB inside a tile.  At the
+// end l_rc = a_rc / sqrt(s_c d_c) for r >= c (d_c = a_cc), one reciprocal
+// square root per column, and 1 / l_cc = s_c / sqrt(s_c d_c) and
+// 1 / d_c = s_c / (s_c d_c) follow by multiplications.  A step is one FMA and an
+// exponent update on the critical path instead of a division.  GB300 runs FP64
+// on the CUDA cores (the tensor cores have no fast FP64 mode) at one warp
+// instruction per 64 cycles per SM sub-partition, and a dependent FP64
+// instruction waits those 64 cycles, so every step also keeps its FP64 work on
+// as few warps per sub-partition as it can.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -32,49 +52,158 @@ namespace {
 
 constexpr int kDenseThreads = 256;
 
-// Eliminates the symmetric tile held (lower triangle, unit-padded beyond kb) in
-// D: afterwards D[r][c] = l_rc l_cc for r >= c, Sq[c] = l_cc, Sinv[c] = 1 / l_cc.
-// The thread that completes the next pivot forms its reciprocal, so a step is
-// one multiply and one FMA per element and no division.
-template <int TB>
-__device__ __forceinline__ void chol_tile(double (*D)[TB + 1], int kb, double* Inv, double* Sq, double* Sinv) {
-    constexpr int R = TB * TB / kDenseThreads;
-    const int t = threadIdx.x;
-    if (t == 0) Inv[0] = 1.0 / D[0][0];
-    __syncthreads();
-    for (int j = 0; j < kb - 1; j++) {
-        const double inv = Inv[j];
-#pragma unroll
-        for (int q = 0; q < R; q++) {
-            const int e = t + q * kDenseThreads, r = e % TB, c = e / TB;
-            if (c > j && r >= c) {
-                const double lc = D[c][j] * inv;
-                D[r][c] = fma(-D[r][j], lc, D[r][c]);
-                if (r == j + 1 && c == j + 1) Inv[j + 1] = 1.0 / D[r][c];
-            }
-        }
-        __syncthreads();
-    }
-    if (t < TB) {
-        const double sq = sqrt(D[t][t]);
-        Sq[t] = sq;
-        Sinv[t] = 1.0 / sq;
-    }
-    __syncthreads();
+// e with 2^-e d in [1, 2) for a positive normal pivot d (e <= 1022, so 2^-e is
+// normal too); 0 for any other value, where the factorisation has failed.
+__device__ __forceinline__ int pivot_shift(double d) {
+    const int f = (int)((__double_as_longlong(d) >> 52) & 0x7ff);
+    return (d > 0.0 && f != 0 && f != 0x7ff) ? min(f - 1023, 1022) : 0;
 }
 
-// Stores L_kk from an eliminated tile and records its first pivot that is not
-// positive (or NaN from an earlier failure): the steps run in order, so the
-// first value written to info is the first failure overall.
+// v * 2^-sh for |sh| <= 1022 by an integer update of the exponent field, with
+// the bits of the IEEE multiplication whenever v and the result are normal
+// numbers; zero, subnormal, infinite and NaN v are returned as they are, a
+// result below the normal range is flushed to a signed zero and one above it
+// becomes a signed infinity.  Selects only, no branch: the update sits on the
+// critical path of every elimination step.
+__device__ __forceinline__ double scale_pow2(double v, int sh) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned long long sign = b & 0x8000000000000000ull;
+    const int f = (int)((b >> 52) & 0x7ffu);
+    const int nf = f - sh;
+    unsigned long long r = b - ((unsigned long long)(long long)sh << 52);
+    r = nf < 1 ? sign : r;
+    r = nf > 0x7fe ? (sign | 0x7ff0000000000000ull) : r;
+    r = (f == 0 || f == 0x7ff) ? b : r;
+    return __longlong_as_double((long long)r);
+}
+
+// Entry p of the packed lower triangle of a TB x TB tile taken in reverse
+// column-major order (p = 0 is the last column's last row): the entries of the
+// columns > j are exactly p < (TB - 1 - j)(TB - j) / 2, so the entries that a
+// step updates are the first threads of the CTA, one warp per sub-partition
+// while they fit in four warps.
+template <int TB>
+__device__ __forceinline__ void packed_entry(int p, int& r, int& c) {
+    const int e = TB * (TB + 1) / 2 - 1 - p;
+    int cc = 0;
+    while (cc + 1 < TB && (cc + 1) * TB - (cc + 1) * cc / 2 <= e) cc++;
+    c = cc;
+    r = cc + (e - (cc * TB - cc * (cc - 1) / 2));
+}
+
+// Loads the TB x TB tile of A at (i0, j0) with rb x cb live entries into T,
+// zero elsewhere; lanes run along rows (coalesced).
+template <int TB>
+__device__ __forceinline__ void load_tile(double (*T)[TB + 1], const double* __restrict__ A, int64_t lda, int i0,
+                                          int j0, int rb, int cb) {
+    constexpr int R = TB * TB / kDenseThreads;
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+        const int e = threadIdx.x + q * kDenseThreads, r = e % TB, c = e / TB;
+        T[r][c] = (r < rb && c < cb) ? A[(i0 + r) + (int64_t)(j0 + c) * lda] : 0.0;
+    }
+}
+
+// Loads the diagonal tile at (c0, c0) with kb live rows: its lower triangle,
+// unit padding beyond kb, zero above the diagonal.
+template <int TB>
+__device__ __forceinline__ void load_diag(double (*D)[TB + 1], const double* __restrict__ A, int64_t lda, int c0,
+                                          int kb) {
+    constexpr int R = TB * TB / kDenseThreads;
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+        const int e = threadIdx.x + q * kDenseThreads, r = e % TB, c = e / TB;
+        D[r][c] = (r < kb && c <= r) ? A[(c0 + r) + (int64_t)(c0 + c) * lda] : (r == c ? 1.0 : 0.0);
+    }
+}
+
+// D -= Lc Lc^T on the lower triangle (the diagonal tile's last update).
+template <int TB>
+__device__ __forceinline__ void syrk_diag(double (*D)[TB + 1], const double (*Lc)[TB + 1]) {
+    constexpr int NP = TB * (TB + 1) / 2;
+    for (int p = threadIdx.x; p < NP; p += kDenseThreads) {
+        int r, c;
+        packed_entry<TB>(p, r, c);
+        double acc = 0.0;
+#pragma unroll
+        for (int m = 0; m < TB; m++) acc = fma(Lc[r][m], Lc[c][m], acc);
+        D[r][c] -= acc;
+    }
+}
+
+// Barrier among the first NB threads of the CTA: __syncthreads for the whole
+// CTA, otherwise named barrier 1, so that the other warps can work meanwhile.
+template <int NB>
+__device__ __forceinline__ void tile_sync() {
+    if constexpr (NB == kDenseThreads)
+        __syncthreads();
+    else
+        asm volatile("bar.sync 1, %0;" ::"n"(NB) : "memory");
+}
+
+// Eliminates the diagonal tile held in D (lower triangle, unit-padded beyond
+// kb) without divisions: afterwards D[r][c] = s_c a_rc for r >= c, with a_rc the
+// entries of the ordinary elimination (a_cc the pivot d_c), and
+//   W[c] = 1 / sqrt(s_c D[c][c]),  so l_rc = D[r][c] W[c] (the diagonal too),
+//   Inv[c] = s_c W[c] = 1 / l_cc,  Rd[c] = s_c W[c]^2 = 1 / D[c][c].
+// Run by the first NB threads of the CTA (and only by them); the last of them
+// keeps the running product s in S.  Column 0 is never updated, so the
+// TB (TB - 1) / 2 entries of the other columns are the ones that threads own.
+template <int TB, int NB>
+__device__ __forceinline__ void chol_tile(double (*D)[TB + 1], int kb, double* S, double* W, double* Inv,
+                                          double* Rd) {
+    constexpr int NU = TB * (TB - 1) / 2;
+    constexpr int QP = (NU + NB - 1) / NB;
+    const int t = threadIdx.x;
+    int er[QP], ec[QP];
+#pragma unroll
+    for (int q = 0; q < QP; q++) packed_entry<TB>(min(t + q * NB, NU - 1), er[q], ec[q]);
+    double s = 1.0;
+    for (int j = 0; j < kb - 1; j++) {
+        const int na = (TB - 1 - j) * (TB - j) / 2;
+        const double d = D[j][j];
+        const int sh = pivot_shift(d);
+#pragma unroll
+        for (int q = 0; q < QP; q++) {
+            if (t + q * NB < na) {
+                const int r = er[q], c = ec[q];
+                const double prod = D[r][j] * D[c][j];
+                D[r][c] = scale_pow2(fma(d, D[r][c], -prod), sh);
+            }
+        }
+        if (t == NB - 1) {
+            s *= scale_pow2(d, sh);
+            S[j + 1] = s;
+        }
+        tile_sync<NB>();
+    }
+    if (t < kb) {
+        const double st = t ? S[t] : 1.0;        // S[0] is never written (kb = 1 has no step)
+        const double w = rsqrt(st * D[t][t]);
+        W[t] = w;
+        Inv[t] = st * w;
+        Rd[t] = (st * w) * w;
+    } else if (t < TB) {
+        W[t] = 0.0;
+        Inv[t] = 0.0;
+        Rd[t] = 0.0;
+    }
+    tile_sync<NB>();
+}
+
+// Stores L_cc from an eliminated tile and records its first pivot that is not
+// positive (or NaN from an earlier failure): the launches run in column order,
+// so the first value written to info is the first failure overall.  s_c > 0
+// while every earlier pivot is positive, so the sign of D[c][c] is the pivot's.
 template <int TB>
 __device__ __forceinline__ void chol_store_tile(double* __restrict__ A, int64_t lda, int k0, int kb,
-                                                const double (*D)[TB + 1], const double* Sq, const double* Sinv,
+                                                const double (*D)[TB + 1], const double* W,
                                                 int* __restrict__ info) {
     constexpr int R = TB * TB / kDenseThreads;
 #pragma unroll
     for (int q = 0; q < R; q++) {
         const int e = threadIdx.x + q * kDenseThreads, r = e % TB, c = e / TB;
-        if (r < kb && c <= r) A[(k0 + r) + (int64_t)(k0 + c) * lda] = (r == c) ? Sq[c] : D[r][c] * Sinv[c];
+        if (r < kb && c <= r) A[(k0 + r) + (int64_t)(k0 + c) * lda] = D[r][c] * W[c];
     }
     if (threadIdx.x == 0) {
         for (int j = 0; j < kb; j++)
@@ -85,128 +214,197 @@ __device__ __forceinline__ void chol_store_tile(double* __restrict__ A, int64_t 
     }
 }
 
+// After chol_tile: D[c][j] = l_cj / l_jj below the diagonal (the multipliers of
+// the unscaled triangular solves).
 template <int TB>
-__global__ void __launch_bounds__(kDenseThreads) k_chol_diag0(int n, double* __restrict__ A, int64_t lda,
-                                                              int* __restrict__ info) {
-    constexpr int R = TB * TB / kDenseThreads;
-    __shared__ double D[TB][TB + 1];
-    __shared__ double Inv[TB], Sq[TB], Sinv[TB];
-    const int kb = min(TB, n);
-#pragma unroll
-    for (int q = 0; q < R; q++) {
-        const int e = threadIdx.x + q * kDenseThreads, r = e % TB, c = e / TB;
-        D[r][c] = (r < kb && c <= r) ? A[r + (int64_t)c * lda] : (r == c ? 1.0 : 0.0);
+__device__ __forceinline__ void diag_multipliers(double (*D)[TB + 1], const double* Rd) {
+    constexpr int NP = TB * (TB + 1) / 2;
+    for (int p = threadIdx.x; p < NP; p += kDenseThreads) {
+        int r, c;
+        packed_entry<TB>(p, r, c);
+        if (r > c) D[r][c] *= Rd[c];
     }
     __syncthreads();
-    chol_tile<TB>(D, kb, Inv, Sq, Sinv);
-    chol_store_tile<TB>(A, lda, 0, kb, D, Sq, Sinv, info);
 }
 
-// Tile column k, with L_kk already stored: CTA b < m solves tile k + 1 + b,
-// X L_kk^T = A_ik; CTA m (only with y) solves y_k = L_kk^{-1} y_k in place.
-// With M[c][j] = l_cj / l_jj and X kept unscaled (x_rj l_jj), a step is
-// X[r][c] -= X[r][j] M[c][j]; the result is x_rc = X[r][c] / l_cc.
+// Launch k of the factorisation (see the top of this file); c = k + 1.
 template <int TB>
 __global__ void __launch_bounds__(kDenseThreads)
-    k_chol_panel(int n, double* __restrict__ A, int64_t lda, int k, double* __restrict__ y) {
+    k_chol_step(int n, double* __restrict__ A, int64_t lda, int k, double* __restrict__ y, int* __restrict__ info) {
     constexpr int R = TB * TB / kDenseThreads;
-    __shared__ double M[TB][TB + 1];
+    constexpr int CS = kDenseThreads / TB;      // column (or row) stride between a thread's entries
+    __shared__ double D[TB][TB + 1];
     __shared__ double X[TB][TB + 1];
-    __shared__ double Inv[TB];
+    __shared__ double Li[TB][TB + 1];
+    __shared__ double Lc[TB][TB + 1];
+    __shared__ double S[TB], W[TB], Inv[TB], Rd[TB], Z[TB];
     const int t = threadIdx.x;
-    const int k0 = k * TB, kb = min(TB, n - k0);
-    const int nt = (n + TB - 1) / TB, m = nt - k - 1;
-    const int b = blockIdx.x;
-    const int r0 = k0 + (b + 1) * TB, rb = b < m ? min(TB, n - r0) : 0;
+    const int nt = (n + TB - 1) / TB;
+    const int c = k + 1;
+    const int c0 = c * TB, k0 = k * TB;
+    const int64_t U = c < nt ? nt - c - 1 : 0;  // tiles below the diagonal in column c
+    const int64_t nd = k >= 0 ? 1 : 0, ny = (y && c < nt) ? 1 : 0;
+    int64_t b = blockIdx.x;
+    if (b < U) {
+        // panel CTA: tile i of column c
+        const int kb = min(TB, n - c0);
+        const int i0 = c0 + (int)(b + 1) * TB, ib = min(TB, n - i0);
+        load_diag<TB>(D, A, lda, c0, kb);
+        load_tile<TB>(X, A, lda, i0, c0, ib, kb);
+        if (k >= 0) {
+            load_tile<TB>(Lc, A, lda, c0, k0, kb, TB);
+            load_tile<TB>(Li, A, lda, i0, k0, ib, TB);
+        }
+        __syncthreads();
+        if (k >= 0) {
+            syrk_diag<TB>(D, Lc);
+            __syncthreads();
+        }
+        if constexpr (TB * (TB - 1) / 2 <= kDenseThreads / 2) {
+            // the factorisation needs half the CTA: the other half takes the
+            // tile's update X -= L_ik L_ck^T meanwhile
+            constexpr int H = kDenseThreads / 2;
+            if (t < H) {
+                chol_tile<TB, H>(D, kb, S, W, Inv, Rd);
+            } else if (k >= 0) {
+                for (int e = t - H; e < TB * TB; e += H) {
+                    const int r = e % TB, cc = e / TB;
+                    double acc = 0.0;
 #pragma unroll
-    for (int q = 0; q < R; q++) {
-        const int e = t + q * kDenseThreads, r = e % TB, c = e / TB;
-        M[r][c] = (r < kb && c <= r) ? A[(k0 + r) + (int64_t)(k0 + c) * lda] : (r == c ? 1.0 : 0.0);
-        if (b < m) X[r][c] = (r < rb && c < kb) ? A[(r0 + r) + (int64_t)(k0 + c) * lda] : 0.0;
-    }
-    __syncthreads();
-    if (t < TB) Inv[t] = 1.0 / M[t][t];
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < R; q++) {
-        const int e = t + q * kDenseThreads, r = e % TB, c = e / TB;
-        if (r > c) M[r][c] *= Inv[c];
-    }
-    __syncthreads();
-    if (b < m) {
-        for (int j = 0; j < kb - 1; j++) {
-#pragma unroll
-            for (int q = 0; q < R; q++) {
-                const int e = t + q * kDenseThreads, r = e % TB, c = e / TB;
-                if (c > j) X[r][c] = fma(-X[r][j], M[c][j], X[r][c]);
+                    for (int m = 0; m < TB; m++) acc = fma(Li[r][m], Lc[cc][m], acc);
+                    X[r][cc] -= acc;
+                }
             }
             __syncthreads();
+        } else {
+            if (k >= 0) {
+                const int r = t % TB, cb = t / TB;
+#pragma unroll
+                for (int q = 0; q < R; q++) {
+                    const int cc = cb + q * CS;
+                    double acc = 0.0;
+#pragma unroll
+                    for (int m = 0; m < TB; m++) acc = fma(Li[r][m], Lc[cc][m], acc);
+                    X[r][cc] -= acc;
+                }
+                __syncthreads();
+            }
+            chol_tile<TB, kDenseThreads>(D, kb, S, W, Inv, Rd);
+        }
+        diag_multipliers<TB>(D, Rd);
+        // X L_cc^T = A_ic, unscaled (x_rj l_jj): the rows are independent, each
+        // in TB lanes of one warp (one per column); a step broadcasts X[r][j]
+        const int cl = t % TB, rt = t / TB;
+        double x[R];
+#pragma unroll
+        for (int q = 0; q < R; q++) x[q] = X[rt + q * CS][cl];
+#pragma unroll
+        for (int j = 0; j < TB - 1; j++) {
+            if (j < kb - 1) {
+                const double mcj = D[cl][j];
+#pragma unroll
+                for (int q = 0; q < R; q++) {
+                    const double xj = __shfl_sync(0xffffffffu, x[q], j, TB);
+                    if (cl > j) x[q] = fma(-xj, mcj, x[q]);
+                }
+            }
         }
 #pragma unroll
         for (int q = 0; q < R; q++) {
-            const int e = t + q * kDenseThreads, r = e % TB, c = e / TB;
-            if (r < rb && c < kb) A[(r0 + r) + (int64_t)(k0 + c) * lda] = X[r][c] * Inv[c];
+            const int r = rt + q * CS;
+            if (r < ib && cl < kb) A[(i0 + r) + (int64_t)(c0 + cl) * lda] = x[q] * Inv[cl];
         }
         return;
     }
-    // fused forward solve, one warp: z_r -= M[r][j] z_j with z unscaled (y_j l_jj), then y_r = z_r / l_rr
-    if (t < 32) {
-        const int r = t;
-        double z = (r < kb) ? y[k0 + r] : 0.0;
-        for (int j = 0; j < kb - 1; j++) {
-            const double zj = __shfl_sync(0xffffffffu, z, j);
-            if (r > j && r < kb) z = fma(-M[r][j], zj, z);
+    b -= U;
+    if (b < nd) {
+        // diagonal CTA: L_kk, from tile (k, k) and its last update (column k - 1)
+        const int kb = min(TB, n - k0);
+        load_diag<TB>(D, A, lda, k0, kb);
+        if (k >= 1) load_tile<TB>(Lc, A, lda, k0, k0 - TB, kb, TB);
+        __syncthreads();
+        if (k >= 1) {
+            syrk_diag<TB>(D, Lc);
+            __syncthreads();
         }
-        if (r < kb) y[k0 + r] = z * Inv[r];
+        chol_tile<TB, kDenseThreads>(D, kb, S, W, Inv, Rd);
+        chol_store_tile<TB>(A, lda, k0, kb, D, W, info);
+        return;
     }
-}
-
-template <int TB>
-__global__ void __launch_bounds__(kDenseThreads)
-    k_chol_update(int n, double* __restrict__ A, int64_t lda, int k, double* __restrict__ y, int* __restrict__ info) {
-    constexpr int R = TB * TB / kDenseThreads;
-    constexpr int CS = kDenseThreads / TB;      // column stride between a thread's outputs
-    __shared__ double Li[TB][TB + 1];
-    __shared__ double Lj[TB][TB + 1];
-    __shared__ double Inv[TB], Sq[TB], Sinv[TB];
-    const int t = threadIdx.x;
-    const int k0 = k * TB, kb = min(TB, n - k0);
-    const int nt = (n + TB - 1) / TB;
-    const int64_t T = nt - k - 1;
-    const int64_t lin = blockIdx.x;
-    if (lin >= T * (T + 1) / 2) {
-        // fused forward solve: b_i -= L_ik y_k for tile row i (one CTA per row)
-        const int i0 = (k + 1 + (int)(lin - T * (T + 1) / 2)) * TB, ib = min(TB, n - i0);
-#pragma unroll
-        for (int q = 0; q < R; q++) {
-            const int e = t + q * kDenseThreads, r = e % TB, m = e / TB;
-            Li[r][m] = (r < ib && m < kb) ? A[(i0 + r) + (int64_t)(k0 + m) * lda] : 0.0;
+    b -= nd;
+    if (b < ny) {
+        // y_c -= L_ck y_k, then y_c = L_cc^{-1} y_c, unscaled (z_j l_jj) like the panel
+        const int kb = min(TB, n - c0);
+        load_diag<TB>(D, A, lda, c0, kb);
+        if (k >= 0) {
+            load_tile<TB>(Lc, A, lda, c0, k0, kb, TB);
+            if (t < TB) X[0][t] = y[k0 + t];
         }
-        if (t < TB) Lj[0][t] = (t < kb) ? y[k0 + t] : 0.0;
+        if (t < TB) Z[t] = t < kb ? y[c0 + t] : 0.0;
+        __syncthreads();
+        if (k >= 0) {
+            syrk_diag<TB>(D, Lc);
+            if (t >= kDenseThreads - TB) {
+                const int r = t - (kDenseThreads - TB);
+                double acc = 0.0;
+#pragma unroll
+                for (int m = 0; m < TB; m++) acc = fma(Lc[r][m], X[0][m], acc);
+                Z[r] -= acc;
+            }
+            __syncthreads();
+        }
+        chol_tile<TB, kDenseThreads>(D, kb, S, W, Inv, Rd);
+        diag_multipliers<TB>(D, Rd);
+        if (t < 32) {
+            const int r = t % TB;
+            double z = Z[r];
+#pragma unroll
+            for (int j = 0; j < TB - 1; j++) {
+                if (j < kb - 1) {
+                    const double zj = __shfl_sync(0xffffffffu, z, j, TB);
+                    if (r > j) z = fma(-D[r][j], zj, z);
+                }
+            }
+            if (t < TB && r < kb) y[c0 + r] = z * Inv[r];
+        }
+        return;
+    }
+    b -= ny;
+    const int64_t ntr = U * (U + 1) / 2;
+    if (b >= ntr) {
+        // y_i -= L_ik y_k for tile row i > c
+        const int i0 = c0 + (int)(b - ntr + 1) * TB, ib = min(TB, n - i0);
+        load_tile<TB>(Li, A, lda, i0, k0, ib, TB);
+        if (t < TB) X[0][t] = y[k0 + t];
         __syncthreads();
         if (t < ib) {
             double s = 0.0;
 #pragma unroll
-            for (int m = 0; m < TB; m++) s = fma(Li[t][m], Lj[0][m], s);
+            for (int m = 0; m < TB; m++) s = fma(Li[t][m], X[0][m], s);
             y[i0 + t] -= s;
         }
         return;
     }
-    // trailing tile (i, j) with k < j <= i from the linear block index
-    int ii = (int)((sqrt(8.0 * (double)lin + 1.0) - 1.0) * 0.5);
-    while ((int64_t)ii * (ii + 1) / 2 > lin) ii--;
-    while ((int64_t)(ii + 1) * (ii + 2) / 2 <= lin) ii++;
-    const int jj = (int)(lin - (int64_t)ii * (ii + 1) / 2);
-    const int i0 = (k + 1 + ii) * TB, j0 = (k + 1 + jj) * TB;
+    // trailing tile (i, j), c < j <= i, from the linear block index
+    int ii = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while ((int64_t)ii * (ii + 1) / 2 > b) ii--;
+    while ((int64_t)(ii + 1) * (ii + 2) / 2 <= b) ii++;
+    const int jj = (int)(b - (int64_t)ii * (ii + 1) / 2);
+    const int i0 = c0 + (ii + 1) * TB, j0 = c0 + (jj + 1) * TB;
     const int ib = min(TB, n - i0), jb = min(TB, n - j0);
+    const bool diag = (i0 == j0);
+    const int r = t % TB, cb = t / TB;
+    // the target entries are read before the barrier, next to the L tiles: no
+    // other CTA of the launch reads or writes this tile
+    double a0[R];
 #pragma unroll
     for (int q = 0; q < R; q++) {
-        const int e = t + q * kDenseThreads, r = e % TB, m = e / TB;
-        Li[r][m] = (r < ib && m < kb) ? A[(i0 + r) + (int64_t)(k0 + m) * lda] : 0.0;
-        Lj[r][m] = (r < jb && m < kb) ? A[(j0 + r) + (int64_t)(k0 + m) * lda] : 0.0;
+        const int cc = cb + q * CS;
+        a0[q] = (r < ib && cc < jb && (!diag || r >= cc)) ? A[(i0 + r) + (int64_t)(j0 + cc) * lda] : 0.0;
     }
+    load_tile<TB>(Li, A, lda, i0, k0, ib, TB);
+    load_tile<TB>(Lc, A, lda, j0, k0, jb, TB);
     __syncthreads();
-    const int r = t % TB, c0 = t / TB;
     double acc[R];
 #pragma unroll
     for (int q = 0; q < R; q++) acc[q] = 0.0;
@@ -214,27 +412,13 @@ __global__ void __launch_bounds__(kDenseThreads)
     for (int m = 0; m < TB; m++) {
         const double a = Li[r][m];
 #pragma unroll
-        for (int q = 0; q < R; q++) acc[q] = fma(a, Lj[c0 + q * CS][m], acc[q]);
+        for (int q = 0; q < R; q++) acc[q] = fma(a, Lc[cb + q * CS][m], acc[q]);
     }
-    const bool diag = (i0 == j0);
-    if (!(ii == 0 && jj == 0)) {
-#pragma unroll
-        for (int q = 0; q < R; q++) {
-            const int c = c0 + q * CS;
-            if (r < ib && c < jb && (!diag || r >= c)) A[(i0 + r) + (int64_t)(j0 + c) * lda] -= acc[q];
-        }
-        return;
-    }
-    // tile (k + 1, k + 1) has its last update: factor it here
-    __syncthreads();                           // every thread is done reading Li
 #pragma unroll
     for (int q = 0; q < R; q++) {
-        const int c = c0 + q * CS;
-        Li[r][c] = (r < ib && c <= r) ? A[(i0 + r) + (int64_t)(i0 + c) * lda] - acc[q] : (r == c ? 1.0 : 0.0);
+        const int cc = cb + q * CS;
+        if (r < ib && cc < jb && (!diag || r >= cc)) A[(i0 + r) + (int64_t)(j0 + cc) * lda] = a0[q] - acc[q];
     }
-    __syncthreads();
-    chol_tile<TB>(Li, ib, Inv, Sq, Sinv);
-    chol_store_tile<TB>(A, lda, i0, ib, Li, Sq, Sinv, info);
 }
 
 // Forward sweep, tile k: y_k = L_kk^{-1} b_k (every CTA, redundantly); CTA 0
@@ -335,14 +519,12 @@ __global__ void __launch_bounds__(kDenseThreads)
 template <int TB>
 cudaError_t potrf_tiles(int n, double* A, int64_t lda, int* info, double* y, cudaStream_t s) {
     const int nt = (n + TB - 1) / TB;
-    k_chol_diag0<TB><<<1, kDenseThreads, 0, s>>>(n, A, lda, info);
-    for (int k = 0; k < nt; k++) {
-        const int64_t T = nt - k - 1;
-        const unsigned panel = (unsigned)(T + (y ? 1 : 0));
-        if (panel) k_chol_panel<TB><<<panel, kDenseThreads, 0, s>>>(n, A, lda, k, y);
-        if (T > 0)
-            k_chol_update<TB><<<(unsigned)(T * (T + 1) / 2 + (y ? T : 0)), kDenseThreads, 0, s>>>(n, A, lda, k, y,
-                                                                                              info);
+    for (int k = -1; k < nt; k++) {
+        const int c = k + 1;
+        const int64_t U = c < nt ? nt - c - 1 : 0;
+        const int64_t grid = U + (k >= 0 ? 1 : 0) + ((y && c < nt) ? 1 : 0) + (k >= 0 ? U * (U + 1) / 2 : 0) +
+                             ((y && k >= 0) ? U : 0);
+        if (grid > 0) k_chol_step<TB><<<(unsigned)grid, kDenseThreads, 0, s>>>(n, A, lda, k, y, info);
     }
     return cudaGetLastError();
 }

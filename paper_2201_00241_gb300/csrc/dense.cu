@@ -245,6 +245,11 @@ __global__ void __launch_bounds__(kDenseThreads)
     const int64_t U = c < nt ? nt - c - 1 : 0;  // tiles below the diagonal in column c
     const int64_t nd = k >= 0 ? 1 : 0, ny = (y && c < nt) ? 1 : 0;
     int64_t b = blockIdx.x;
+    // programmatic dependent launch: everything below reads what the previous
+    // launch wrote, so wait for it first.  The next launch is scheduled as this
+    // one's CTAs exit (the implicit trigger; triggering at the start, which
+    // keeps the next launch's CTAs resident and waiting, measured slower).
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (b < U) {
         // panel CTA: tile i of column c
         const int kb = min(TB, n - c0);
@@ -519,12 +524,28 @@ __global__ void __launch_bounds__(kDenseThreads)
 template <int TB>
 cudaError_t potrf_tiles(int n, double* A, int64_t lda, int* info, double* y, cudaStream_t s) {
     const int nt = (n + TB - 1) / TB;
+    bool first = true;
     for (int k = -1; k < nt; k++) {
         const int c = k + 1;
         const int64_t U = c < nt ? nt - c - 1 : 0;
         const int64_t grid = U + (k >= 0 ? 1 : 0) + ((y && c < nt) ? 1 : 0) + (k >= 0 ? U * (U + 1) / 2 : 0) +
                              ((y && k >= 0) ? U : 0);
-        if (grid > 0) k_chol_step<TB><<<(unsigned)grid, kDenseThreads, 0, s>>>(n, A, lda, k, y, info);
+        if (grid == 0) continue;
+        // launches after the first overlap their launch latency with the
+        // previous one (programmatic stream serialisation; the kernel waits)
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3(kDenseThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = first ? 0 : 1;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, k_chol_step<TB>, n, A, lda, k, y, info);
+        if (e != cudaSuccess) return e;
+        first = false;
     }
     return cudaGetLastError();
 }

@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kDenseThreads)
     // launch wrote, so wait for it first.  The next launch is scheduled as this
     // one's CTAs exit (the implicit trigger; triggering at the start, which
     // keeps the next launch's CTAs resident and waiting, measured slower).
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    pdl_wait();
     if (b < U) {
         // panel CTA: tile i of column c
         const int kb = min(TB, n - c0);
@@ -426,8 +426,15 @@ __global__ void __launch_bounds__(kDenseThreads)
     }
 }
 
-// Forward sweep, tile k: y_k = L_kk^{-1} b_k (every CTA, redundantly); CTA 0
-// stores y_k in Y, CTA b > 0 takes b_i -= L_ik y_k for tile i = k + b.
+// Triangular solves, one launch per tile.  Every CTA loads the diagonal tile
+// L_kk, forms the multipliers m_rj = l_rj / l_jj and solves its right-hand
+// sides' slice of tile k redundantly: the TB values of one right-hand side live
+// in TB lanes of a warp, a step broadcasts z_j with a shuffle and takes
+// z_r -= m z_j (unscaled, z_j = x_j l_jj), no barrier; x_r = z_r / l_rr.
+// Right-hand-side columns beyond nrhs do no FP64 work.
+//
+// Forward sweep, tile k: y_k = L_kk^{-1} b_k; CTA 0 stores y_k in Y, CTA b > 0
+// takes b_i -= L_ik y_k for tile i = k + b.
 template <int TB>
 __global__ void __launch_bounds__(kDenseThreads)
     k_chol_fwd(int n, const double* __restrict__ L, int64_t ldl, double* __restrict__ B, int64_t ldb,
@@ -438,9 +445,10 @@ __global__ void __launch_bounds__(kDenseThreads)
     __shared__ double M[TB][TB + 1];
     __shared__ double Yk[TB][RC + 1];
     __shared__ double Inv[TB];
+    pdl_wait();
     const int t = threadIdx.x, r = t % TB, c = t / TB;
     const int col = blockIdx.y * RC + c;
-    const bool live = col < nrhs;               // warp-uniform for TB >= 16: padding columns do no FP64 work
+    const bool live = col < nrhs;
     const int k0 = k * TB, kb = min(TB, n - k0);
     const int b = blockIdx.x, i0 = k0 + b * TB, ib = b ? min(TB, n - i0) : 0;
 #pragma unroll
@@ -449,21 +457,31 @@ __global__ void __launch_bounds__(kDenseThreads)
         D[rr][cc] = (rr < kb && cc <= rr) ? L[(k0 + rr) + (int64_t)(k0 + cc) * ldl] : (rr == cc ? 1.0 : 0.0);
         if (b) M[rr][cc] = (rr < ib && cc < kb) ? L[(i0 + rr) + (int64_t)(k0 + cc) * ldl] : 0.0;
     }
-    Yk[r][c] = (r < kb && live) ? B[(k0 + r) + (int64_t)col * ldb] : 0.0;
+    double z = (r < kb && live) ? B[(k0 + r) + (int64_t)col * ldb] : 0.0;
     __syncthreads();
     if (t < TB) Inv[t] = 1.0 / D[t][t];
     __syncthreads();
-    for (int j = 0; j < kb - 1; j++) {
-        if (live && r > j) Yk[r][c] -= D[r][j] * (Yk[j][c] * Inv[j]);
-        __syncthreads();
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+        const int e = t + q * kDenseThreads, rr = e % TB, cc = e / TB;
+        if (rr > cc) D[rr][cc] *= Inv[cc];
     }
-    const double y = live ? Yk[r][c] * Inv[r] : 0.0;
     __syncthreads();
-    Yk[r][c] = y;
+    if (__any_sync(0xffffffffu, live)) {
+#pragma unroll
+        for (int j = 0; j < TB - 1; j++) {
+            if (j < kb - 1) {
+                const double zj = __shfl_sync(0xffffffffu, z, j, TB);
+                if (live && r > j) z = fma(-D[r][j], zj, z);
+            }
+        }
+    }
+    const double y = live ? z * Inv[r] : 0.0;
     if (b == 0) {
         if (r < kb && live) Y[(k0 + r) + (int64_t)col * n] = y;
         return;
     }
+    Yk[r][c] = y;
     __syncthreads();
     if (r < ib && live) {
         double s = 0.0;
@@ -485,6 +503,7 @@ __global__ void __launch_bounds__(kDenseThreads)
     __shared__ double M[TB][TB + 1];     // M[m][r] = L(k0 + m, i0 + r)
     __shared__ double Yk[TB][RC + 1];
     __shared__ double Inv[TB];
+    pdl_wait();
     const int t = threadIdx.x, r = t % TB, c = t / TB;
     const int col = blockIdx.y * RC + c;
     const bool live = col < nrhs;
@@ -497,21 +516,31 @@ __global__ void __launch_bounds__(kDenseThreads)
         // rr indexes the row inside tile k (coalesced), cc the column inside tile i
         if (b) M[rr][cc] = (rr < kb) ? L[(k0 + rr) + (int64_t)(i0 + cc) * ldl] : 0.0;
     }
-    Yk[r][c] = (r < kb && live) ? Y[(k0 + r) + (int64_t)col * n] : 0.0;
+    double z = (r < kb && live) ? Y[(k0 + r) + (int64_t)col * n] : 0.0;
     __syncthreads();
     if (t < TB) Inv[t] = 1.0 / D[t][t];
     __syncthreads();
-    for (int j = kb - 1; j > 0; j--) {
-        if (live && r < j) Yk[r][c] -= D[j][r] * (Yk[j][c] * Inv[j]);
-        __syncthreads();
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+        const int e = t + q * kDenseThreads, rr = e % TB, cc = e / TB;
+        if (rr > cc) D[rr][cc] *= Inv[rr];       // l_jr / l_jj with j = rr > r = cc
     }
-    const double x = live ? Yk[r][c] * Inv[r] : 0.0;
     __syncthreads();
-    Yk[r][c] = x;
+    if (__any_sync(0xffffffffu, live)) {
+#pragma unroll
+        for (int j = TB - 1; j > 0; j--) {
+            if (j < kb) {
+                const double zj = __shfl_sync(0xffffffffu, z, j, TB);
+                if (live && r < j) z = fma(-D[j][r], zj, z);
+            }
+        }
+    }
+    const double x = live ? z * Inv[r] : 0.0;
     if (b == 0) {
         if (r < kb && live) B[(k0 + r) + (int64_t)col * ldb] = x;
         return;
     }
+    Yk[r][c] = x;
     __syncthreads();
     if (live) {
         double s = 0.0;
@@ -524,28 +553,17 @@ __global__ void __launch_bounds__(kDenseThreads)
 template <int TB>
 cudaError_t potrf_tiles(int n, double* A, int64_t lda, int* info, double* y, cudaStream_t s) {
     const int nt = (n + TB - 1) / TB;
-    bool first = true;
+    bool pdl = false;   // the first launch follows the memset of info
     for (int k = -1; k < nt; k++) {
         const int c = k + 1;
         const int64_t U = c < nt ? nt - c - 1 : 0;
         const int64_t grid = U + (k >= 0 ? 1 : 0) + ((y && c < nt) ? 1 : 0) + (k >= 0 ? U * (U + 1) / 2 : 0) +
                              ((y && k >= 0) ? U : 0);
         if (grid == 0) continue;
-        // launches after the first overlap their launch latency with the
-        // previous one (programmatic stream serialisation; the kernel waits)
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        at[0].val.programmaticStreamSerializationAllowed = 1;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)grid);
-        cfg.blockDim = dim3(kDenseThreads);
-        cfg.dynamicSmemBytes = 0;
-        cfg.stream = s;
-        cfg.attrs = at;
-        cfg.numAttrs = first ? 0 : 1;
-        const cudaError_t e = cudaLaunchKernelEx(&cfg, k_chol_step<TB>, n, A, lda, k, y, info);
+        const cudaError_t e = launch_pdl(pdl, k_chol_step<TB>, dim3((unsigned)grid), dim3(kDenseThreads), 0, s, n, A, lda,
+                                         k, y, info);
         if (e != cudaSuccess) return e;
-        first = false;
+        pdl = true;
     }
     return cudaGetLastError();
 }
@@ -556,11 +574,20 @@ cudaError_t potrs_tiles(int n, const double* L, int64_t ldl, double* B, int64_t 
     constexpr int RC = kDenseThreads / TB;
     const int nt = (n + TB - 1) / TB;
     const unsigned gy = (unsigned)((nrhs + RC - 1) / RC);
+    bool pdl = false;   // the first launch follows whatever the caller enqueued
     if (forward)
-        for (int k = 0; k < nt; k++)
-            k_chol_fwd<TB><<<dim3(nt - k, gy), kDenseThreads, 0, s>>>(n, L, ldl, B, ldb, Y, nrhs, k);
-    for (int k = nt - 1; k >= 0; k--)
-        k_chol_bwd<TB><<<dim3(k + 1, gy), kDenseThreads, 0, s>>>(n, L, ldl, B, ldb, Y, nrhs, k);
+        for (int k = 0; k < nt; k++) {
+            const cudaError_t e = launch_pdl(pdl, k_chol_fwd<TB>, dim3(nt - k, gy), dim3(kDenseThreads), 0, s, n, L,
+                                             ldl, B, ldb, Y, nrhs, k);
+            if (e != cudaSuccess) return e;
+            pdl = true;
+        }
+    for (int k = nt - 1; k >= 0; k--) {
+        const cudaError_t e = launch_pdl(pdl, k_chol_bwd<TB>, dim3(k + 1, gy), dim3(kDenseThreads), 0, s, n, L, ldl,
+                                         B, ldb, Y, nrhs, k);
+        if (e != cudaSuccess) return e;
+        pdl = true;
+    }
     return cudaGetLastError();
 }
 

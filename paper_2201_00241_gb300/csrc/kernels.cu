@@ -453,7 +453,10 @@ __device__ __forceinline__ void k_rf_pivot_body(const RfGrid& g) {
         g.A[p.w] = fma(-lt, pq.w, g.A[p.w]) * pq.z;
     }
 }
-__global__ void k_rf_pivot(RfGrid g) { k_rf_pivot_body(g); }
+__global__ void k_rf_pivot(RfGrid g) {
+    pdl_wait();
+    k_rf_pivot_body(g);
+}
 
 // Pivot quantities of a bus from its block [a_tt a_tv; a_vt a_vv]: 1/u_tt,
 // l_vt = a_vt / u_tt, and 1/u_vv = a_tt / det (u_vv = det / a_tt, det = a_tt a_vv -
@@ -491,7 +494,10 @@ __device__ __forceinline__ void k_rf_leaf_piv_body(const RfGrid& g, int njob) {
     const double idet = two ? 1.0 / rf_det(v[0], v[1], v[2], v[3]) : 0.0;
     rf_piv_store(g, g.piv_bus[q], v[0], v[1], v[2], it, idet, two);
 }
-__global__ void k_rf_leaf_piv(RfGrid g, int njob) { k_rf_leaf_piv_body(g, njob); }
+__global__ void k_rf_leaf_piv(RfGrid g, int njob) {
+    pdl_wait();
+    k_rf_leaf_piv_body(g, njob);
+}
 
 // Update step of one level: every target entry a_ij of the level subtracts
 // sum_k l_ik u_kj over the buses k of the level whose pattern holds i and j
@@ -576,6 +582,7 @@ __device__ __forceinline__ void k_rf_update_body(const RfGrid& g, int64_t t0, in
     }
 }
 __global__ void k_rf_update(RfGrid g, int64_t t0, int64_t nt, int j0, int njob) {
+    pdl_wait();
     k_rf_update_body(g, t0, nt, j0, njob);
 }
 
@@ -599,7 +606,10 @@ __device__ __forceinline__ void k_tail_gather_body(RfGrid g) {
     const int p = g.tail_pos[idx];
     g.tailD[idx] = (p >= 0 && inb(p, g.nnz)) ? g.A[p] : 0.0;
 }
-__global__ void k_tail_gather(RfGrid g) { k_tail_gather_body(g); }
+__global__ void k_tail_gather(RfGrid g) {
+    pdl_wait();
+    k_tail_gather_body(g);
+}
 
 // Eliminates the tile held in Dk (unit-padded beyond kb) and stores it at
 // (k0, k0): U on and above the diagonal, L = a_rj / u_jj below it.
@@ -629,7 +639,10 @@ __device__ __forceinline__ void k_tail_diag0_body(RfGrid g) {
     __syncthreads();
     tail_factor_store(g, 0, kb, Dk, Inv);
 }
-__global__ void __launch_bounds__(256) k_tail_diag0(RfGrid g) { k_tail_diag0_body(g); }
+__global__ void __launch_bounds__(256) k_tail_diag0(RfGrid g) {
+    pdl_wait();
+    k_tail_diag0_body(g);
+}
 
 __device__ __forceinline__ void k_tail_panel_body(RfGrid g, int k) {
     constexpr int TB = kTailTB;
@@ -669,7 +682,10 @@ __device__ __forceinline__ void k_tail_panel_body(RfGrid g, int k) {
     }
     if (r < kb && c < ob) D[(size_t)(k0 + r) * T + o0 + c] = X[r][c];
 }
-__global__ void __launch_bounds__(256) k_tail_panel(RfGrid g, int k) { k_tail_panel_body(g, k); }
+__global__ void __launch_bounds__(256) k_tail_panel(RfGrid g, int k) {
+    pdl_wait();
+    k_tail_panel_body(g, k);
+}
 
 __device__ __forceinline__ void k_tail_update_body(RfGrid g, int k) {
     constexpr int TB = kTailTB;
@@ -699,7 +715,10 @@ __device__ __forceinline__ void k_tail_update_body(RfGrid g, int k) {
     __syncthreads();
     tail_factor_store(g, i0, ib, Li, Inv);
 }
-__global__ void __launch_bounds__(256) k_tail_update(RfGrid g, int k) { k_tail_update_body(g, k); }
+__global__ void __launch_bounds__(256) k_tail_update(RfGrid g, int k) {
+    pdl_wait();
+    k_tail_update_body(g, k);
+}
 
 __device__ __forceinline__ void k_tail_scatter_body(RfGrid g) {
     const int T = g.T;
@@ -715,7 +734,10 @@ __device__ __forceinline__ void k_tail_scatter_body(RfGrid g) {
         if (!(fabs(v) > tau)) atomicOr(g.err, 1);
     }
 }
-__global__ void k_tail_scatter(RfGrid g) { k_tail_scatter_body(g); }
+__global__ void k_tail_scatter(RfGrid g) {
+    pdl_wait();
+    k_tail_scatter_body(g);
+}
 
 // Transposed copies of the factor values and of J_p, and the unit-diagonal
 // factors of the direction kernel.  With D = diag(U), J_x = L U = D L'' U' where
@@ -1962,15 +1984,37 @@ __global__ void k_newton_update_batch(PfBatch B) {
 }
 
 __global__ void k_rf_update_batch(RfBatch B, int64_t t0, int64_t nt, int j0, int njob) {
+    pdl_wait();
     k_rf_update_body(B.g[blockIdx.y], t0, nt, j0, njob);
 }
-__global__ void k_rf_leaf_piv_batch(RfBatch B, int njob) { k_rf_leaf_piv_body(B.g[blockIdx.y], njob); }
-__global__ void k_rf_pivot_batch(RfBatch B) { k_rf_pivot_body(B.g[blockIdx.y]); }
-__global__ void k_tail_gather_batch(RfBatch B) { k_tail_gather_body(B.g[blockIdx.y]); }
-__global__ void __launch_bounds__(256) k_tail_diag0_batch(RfBatch B) { k_tail_diag0_body(B.g[blockIdx.y]); }
-__global__ void __launch_bounds__(256) k_tail_panel_batch(RfBatch B, int k) { k_tail_panel_body(B.g[blockIdx.y], k); }
-__global__ void __launch_bounds__(256) k_tail_update_batch(RfBatch B, int k) { k_tail_update_body(B.g[blockIdx.y], k); }
-__global__ void k_tail_scatter_batch(RfBatch B) { k_tail_scatter_body(B.g[blockIdx.y]); }
+__global__ void k_rf_leaf_piv_batch(RfBatch B, int njob) {
+    pdl_wait();
+    k_rf_leaf_piv_body(B.g[blockIdx.y], njob);
+}
+__global__ void k_rf_pivot_batch(RfBatch B) {
+    pdl_wait();
+    k_rf_pivot_body(B.g[blockIdx.y]);
+}
+__global__ void k_tail_gather_batch(RfBatch B) {
+    pdl_wait();
+    k_tail_gather_body(B.g[blockIdx.y]);
+}
+__global__ void __launch_bounds__(256) k_tail_diag0_batch(RfBatch B) {
+    pdl_wait();
+    k_tail_diag0_body(B.g[blockIdx.y]);
+}
+__global__ void __launch_bounds__(256) k_tail_panel_batch(RfBatch B, int k) {
+    pdl_wait();
+    k_tail_panel_body(B.g[blockIdx.y], k);
+}
+__global__ void __launch_bounds__(256) k_tail_update_batch(RfBatch B, int k) {
+    pdl_wait();
+    k_tail_update_body(B.g[blockIdx.y], k);
+}
+__global__ void k_tail_scatter_batch(RfBatch B) {
+    pdl_wait();
+    k_tail_scatter_body(B.g[blockIdx.y]);
+}
 
 // the single solves' tail triangles: L (unit lower) and U with column j scaled by 1/u_jj
 __global__ void k_tail_tri_batch(TriBatch B) {
@@ -2065,26 +2109,34 @@ void launch_prefetch_l2(const PrefetchList& in, cudaStream_t st) {
 cudaError_t launch_refactor(const RfGrid& g, const int* lev_ptr_host, const int64_t* tgt_lev_ptr_host,
                             const int* piv_lev_ptr_host, int n_lev, cudaStream_t st) {
     (void)lev_ptr_host;
+    cudaError_t e = cudaSuccess;
+    bool pdl = false;   // the first launch follows an event wait
+    auto chk = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
+        pdl = true;
+    };
     if (n_lev > 0 && piv_lev_ptr_host[0] > 0)
-        k_rf_leaf_piv<<<blocks_for(piv_lev_ptr_host[0], 128), 128, 0, st>>>(g, piv_lev_ptr_host[0]);
+        chk(launch_pdl(pdl, k_rf_leaf_piv, dim3(blocks_for(piv_lev_ptr_host[0], 128)), dim3(128), 0, st, g,
+                       piv_lev_ptr_host[0]));
     for (int lev = 0; lev < n_lev; lev++) {
         const int64_t t0 = tgt_lev_ptr_host[lev], nt = tgt_lev_ptr_host[lev + 1] - t0;
         const int j0 = piv_lev_ptr_host[lev], njob = piv_lev_ptr_host[lev + 1] - j0;
-        if (nt > 0) k_rf_update<<<blocks_for(nt, 256), 256, 0, st>>>(g, t0, nt, j0, njob);
+        if (nt > 0) chk(launch_pdl(pdl, k_rf_update, dim3(blocks_for(nt, 256)), dim3(256), 0, st, g, t0, nt, j0, njob));
     }
-    if (g.n_piv + g.n_pe > 0) k_rf_pivot<<<blocks_for((int64_t)g.n_piv + g.n_pe, 256), 256, 0, st>>>(g);
+    if (g.n_piv + g.n_pe > 0)
+        chk(launch_pdl(pdl, k_rf_pivot, dim3(blocks_for((int64_t)g.n_piv + g.n_pe, 256)), dim3(256), 0, st, g));
     if (g.T > 0) {
         const int TT = g.T * g.T, nt = (g.T + kTailTB - 1) / kTailTB;
-        k_tail_gather<<<blocks_for(TT, 256), 256, 0, st>>>(g);
-        k_tail_diag0<<<1, 256, 0, st>>>(g);
+        chk(launch_pdl(pdl, k_tail_gather, dim3(blocks_for(TT, 256)), dim3(256), 0, st, g));
+        chk(launch_pdl(pdl, k_tail_diag0, dim3(1), dim3(256), 0, st, g));
         for (int k = 0; k < nt - 1; k++) {
             const int m = nt - k - 1;
-            k_tail_panel<<<2 * m, 256, 0, st>>>(g, k);
-            k_tail_update<<<m * m, 256, 0, st>>>(g, k);
+            chk(launch_pdl(pdl, k_tail_panel, dim3(2 * m), dim3(256), 0, st, g, k));
+            chk(launch_pdl(pdl, k_tail_update, dim3(m * m), dim3(256), 0, st, g, k));
         }
-        k_tail_scatter<<<blocks_for(TT, 256), 256, 0, st>>>(g);
+        chk(launch_pdl(pdl, k_tail_scatter, dim3(blocks_for(TT, 256)), dim3(256), 0, st, g));
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // The dynamic shared-memory limit is a per-kernel attribute of each device's
@@ -2277,29 +2329,37 @@ cudaError_t launch_refactor_batch(const RfBatch& B, const int* lev_ptr_host, con
     if (B.n <= 0) return cudaSuccess;
     const unsigned n = (unsigned)B.n;
     (void)lev_ptr_host;
+    cudaError_t e = cudaSuccess;
+    bool pdl = false;   // the first launch follows an event wait
+    auto chk = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
+        pdl = true;
+    };
     if (n_lev > 0 && piv_lev_ptr_host[0] > 0)
-        k_rf_leaf_piv_batch<<<dim3((unsigned)blocks_for(piv_lev_ptr_host[0], 128), n), 128, 0, st>>>(
-            B, piv_lev_ptr_host[0]);
+        chk(launch_pdl(pdl, k_rf_leaf_piv_batch, dim3((unsigned)blocks_for(piv_lev_ptr_host[0], 128), n), dim3(128), 0, st,
+                       B, piv_lev_ptr_host[0]));
     for (int lev = 0; lev < n_lev; lev++) {
         const int64_t t0 = tgt_lev_ptr_host[lev], nt = tgt_lev_ptr_host[lev + 1] - t0;
         const int j0 = piv_lev_ptr_host[lev], njob = piv_lev_ptr_host[lev + 1] - j0;
-        if (nt > 0) k_rf_update_batch<<<dim3((unsigned)blocks_for(nt, 256), n), 256, 0, st>>>(B, t0, nt, j0, njob);
+        if (nt > 0)
+            chk(launch_pdl(pdl, k_rf_update_batch, dim3((unsigned)blocks_for(nt, 256), n), dim3(256), 0, st, B, t0, nt, j0,
+                           njob));
     }
     const int64_t np = (int64_t)B.g[0].n_piv + B.g[0].n_pe;
-    if (np > 0) k_rf_pivot_batch<<<dim3((unsigned)blocks_for(np, 256), n), 256, 0, st>>>(B);
+    if (np > 0) chk(launch_pdl(pdl, k_rf_pivot_batch, dim3((unsigned)blocks_for(np, 256), n), dim3(256), 0, st, B));
     const int T = B.g[0].T;
     if (T > 0) {
         const int TT = T * T, nt = (T + kTailTB - 1) / kTailTB;
-        k_tail_gather_batch<<<dim3((unsigned)blocks_for(TT, 256), n), 256, 0, st>>>(B);
-        k_tail_diag0_batch<<<dim3(1, n), 256, 0, st>>>(B);
+        chk(launch_pdl(pdl, k_tail_gather_batch, dim3((unsigned)blocks_for(TT, 256), n), dim3(256), 0, st, B));
+        chk(launch_pdl(pdl, k_tail_diag0_batch, dim3(1, n), dim3(256), 0, st, B));
         for (int k = 0; k < nt - 1; k++) {
             const int m = nt - k - 1;
-            k_tail_panel_batch<<<dim3((unsigned)(2 * m), n), 256, 0, st>>>(B, k);
-            k_tail_update_batch<<<dim3((unsigned)(m * m), n), 256, 0, st>>>(B, k);
+            chk(launch_pdl(pdl, k_tail_panel_batch, dim3((unsigned)(2 * m), n), dim3(256), 0, st, B, k));
+            chk(launch_pdl(pdl, k_tail_update_batch, dim3((unsigned)(m * m), n), dim3(256), 0, st, B, k));
         }
-        k_tail_scatter_batch<<<dim3((unsigned)blocks_for(TT, 256), n), 256, 0, st>>>(B);
+        chk(launch_pdl(pdl, k_tail_scatter_batch, dim3((unsigned)blocks_for(TT, 256), n), dim3(256), 0, st, B));
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 void launch_tail_tri_batch(const TriBatch& B, cudaStream_t st) {

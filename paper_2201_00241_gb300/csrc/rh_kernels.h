@@ -164,6 +164,35 @@ struct PfState {
     double *sc;                      // per bus: sin, cos of the angle (launch_pf_prep; NULL: not kept)
 };
 
+// ---- programmatic dependent launch --------------------------------------------
+// The long chains of dependent launches (refactorisation levels, dense-tail and
+// Cholesky tile columns, the triangular solves) use programmatic stream
+// serialisation: the next launch is scheduled as the current one's CTAs exit
+// instead of after its completion is signalled, hiding part of the launch
+// latency.  Every kernel launched this way calls pdl_wait() before it touches
+// memory, which returns once the previous kernel in the stream has completed
+// and its writes are visible; without a previous kernel it returns at once.
+// The first kernel of a chain is launched without the attribute (pdl = false),
+// so it is fully ordered after whatever precedes it (copies, event waits).
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ---- launchers (all asynchronous on `st`) ----------------------------------
 void launch_injections(const PfGrid& g, const PfState& s, cudaStream_t st);
 // residual (internal order) and/or Jacobian values; gmax / jmax receive

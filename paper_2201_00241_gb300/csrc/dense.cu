@@ -44,6 +44,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "rh_kernels.h"
 
@@ -550,8 +551,57 @@ __global__ void __launch_bounds__(kDenseThreads)
     }
 }
 
+// Launches of at most 4.5 x (SM count) CTAs request enough dynamic shared
+// memory (unused) that every CTA has an SM to itself: the panel CTAs, first in
+// the grid, then run their latency-bound chain without trailing CTAs beside them
+// on the FP64 pipes, and the trailing CTAs take the other SMs in waves.  Larger
+// launches keep the default residency, where the waves would cost more.  The
+// attribute is set once per device, outside stream capture.
+constexpr int kMaxDenseDevices = 64;
+struct DenseDevice {
+    bool ready = false;
+    int n_sm = 0;
+    int solo16 = 0, solo32 = 0;   // dynamic bytes for one CTA per SM (0: not set)
+};
+std::mutex g_dense_mu;
+DenseDevice g_dense[kMaxDenseDevices];
+
+template <int TB>
+int solo_smem_for(int per_sm, int optin) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_chol_step<TB>) != cudaSuccess) return 0;
+    const int want = per_sm / 2 + 1024 - (int)fa.sharedSizeBytes;
+    if (want <= 0 || want + (int)fa.sharedSizeBytes > optin) return 0;
+    if (cudaFuncSetAttribute(k_chol_step<TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, want) != cudaSuccess)
+        return 0;
+    return want;
+}
+
+// The device's entry, prepared on first use outside a stream capture; nullptr
+// when it cannot be (the launches then keep the default residency).
+const DenseDevice* dense_device(cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDenseDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_dense_mu);
+    DenseDevice& d = g_dense[dev];
+    if (d.ready) return &d;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    int per_sm = 0, optin = 0;
+    if (cudaDeviceGetAttribute(&d.n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return nullptr;
+    d.solo16 = solo_smem_for<16>(per_sm, optin);
+    d.solo32 = solo_smem_for<32>(per_sm, optin);
+    d.ready = true;
+    return &d;
+}
+
 template <int TB>
 cudaError_t potrf_tiles(int n, double* A, int64_t lda, int* info, double* y, cudaStream_t s) {
+    const DenseDevice* dd = dense_device(s);
+    const int solo = dd ? (TB == 16 ? dd->solo16 : dd->solo32) : 0;
     const int nt = (n + TB - 1) / TB;
     bool pdl = false;   // the first launch follows the memset of info
     for (int k = -1; k < nt; k++) {
@@ -560,8 +610,9 @@ cudaError_t potrf_tiles(int n, double* A, int64_t lda, int* info, double* y, cud
         const int64_t grid = U + (k >= 0 ? 1 : 0) + ((y && c < nt) ? 1 : 0) + (k >= 0 ? U * (U + 1) / 2 : 0) +
                              ((y && k >= 0) ? U : 0);
         if (grid == 0) continue;
-        const cudaError_t e = launch_pdl(pdl, k_chol_step<TB>, dim3((unsigned)grid), dim3(kDenseThreads), 0, s, n, A, lda,
-                                         k, y, info);
+        const size_t dyn = (solo > 0 && 2 * grid <= 9 * (int64_t)dd->n_sm) ? (size_t)solo : 0;
+        const cudaError_t e = launch_pdl(pdl, k_chol_step<TB>, dim3((unsigned)grid), dim3(kDenseThreads), dyn, s, n,
+                                         A, lda, k, y, info);
         if (e != cudaSuccess) return e;
         pdl = true;
     }

@@ -397,10 +397,32 @@ def measure_rto(n_updates=12):
     t_rto = _event_ms(rto, 10)
     t_hess = _event_ms(lambda: rh._check(lib.rh_hessian(lg._h, n, rh._ptr(H), n, sptr,
                                                         rh.RH_DEVICE_PTRS | rh.RH_HESSIAN_CONCURRENT)), 10)
+    # rh_potrf alone on this H (n_p x n_p), replayed from a CUDA graph, H restored between runs
+    H0 = H.clone()
+    A = torch.empty_like(H0)
+    gs = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(gs):
+        A.copy_(H0)
+        rh.potrf(A, stream=rh.C.c_void_p(gs.cuda_stream))
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=gs):
+            rh.potrf(A, stream=rh.C.c_void_p(gs.cuda_stream))
+    t_potrf = []
+    for _ in range(20):
+        A.copy_(H0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        t_potrf.append(e0.elapsed_time(e1))
     return {"workload": f"case1354: tracking updates with loads w_t = w_0 (1 + 0.03 sin(2 pi t / 60)) x per-bus "
                         f"U[0.98, 1.02]; n_p = {n}; step computed, not applied",
             "update_ms_p50": float(np.median(wall)), "update_ms_min": float(np.min(wall)),
             "rto_step_ms": t_rto, "step1_hessian_ms": t_hess, "step2_cholesky_solve_ms": t_rto - t_hess,
+            "potrf_ms": float(np.median(t_potrf)), "potrf_n": n,
             "update_includes": "loads upload, warm-started Newton power flow, adjoint + gradient, "
                                "full reduced Hessian (one launch), Cholesky + solve",
             "paper_v100_s": {"step1": 0.05, "step2": 0.05, "total": 0.10, "cpu_total": 2.22}}

@@ -40,7 +40,9 @@
 // on the CUDA cores (the tensor cores have no fast FP64 mode) at one warp
 // instruction per 64 cycles per SM sub-partition, and a dependent FP64
 // instruction waits those 64 cycles, so every step also keeps its FP64 work on
-// as few warps per sub-partition as it can.
+// as few warps per sub-partition as it can.  The products square the entries'
+// magnitudes, so every diagonal tile is first equilibrated by powers of two
+// (load_diag).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -52,31 +54,6 @@ namespace rh {
 namespace {
 
 constexpr int kDenseThreads = 256;
-
-// e with 2^-e d in [1, 2) for a positive normal pivot d (e <= 1022, so 2^-e is
-// normal too); 0 for any other value, where the factorisation has failed.
-__device__ __forceinline__ int pivot_shift(double d) {
-    const int f = (int)((__double_as_longlong(d) >> 52) & 0x7ff);
-    return (d > 0.0 && f != 0 && f != 0x7ff) ? min(f - 1023, 1022) : 0;
-}
-
-// v * 2^-sh for |sh| <= 1022 by an integer update of the exponent field, with
-// the bits of the IEEE multiplication whenever v and the result are normal
-// numbers; zero, subnormal, infinite and NaN v are returned as they are, a
-// result below the normal range is flushed to a signed zero and one above it
-// becomes a signed infinity.  Selects only, no branch: the update sits on the
-// critical path of every elimination step.
-__device__ __forceinline__ double scale_pow2(double v, int sh) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const unsigned long long sign = b & 0x8000000000000000ull;
-    const int f = (int)((b >> 52) & 0x7ffu);
-    const int nf = f - sh;
-    unsigned long long r = b - ((unsigned long long)(long long)sh << 52);
-    r = nf < 1 ? sign : r;
-    r = nf > 0x7fe ? (sign | 0x7ff0000000000000ull) : r;
-    r = (f == 0 || f == 0x7ff) ? b : r;
-    return __longlong_as_double((long long)r);
-}
 
 // Entry p of the packed lower triangle of a TB x TB tile taken in reverse
 // column-major order (p = 0 is the last column's last row): the entries of the
@@ -105,30 +82,67 @@ __device__ __forceinline__ void load_tile(double (*T)[TB + 1], const double* __r
     }
 }
 
+// 2^k for |k| <= 1022.
+__device__ __forceinline__ double pow2i(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
+
+// floor(exponent / 2) of a positive normal a (|result| <= 511); 0 otherwise.
+__device__ __forceinline__ int half_exponent(double a) {
+    const int f = (int)((__double_as_longlong(a) >> 52) & 0x7ff);
+    return (a > 0.0 && f != 0 && f != 0x7ff) ? (f - 1023) >> 1 : 0;
+}
+
 // Loads the diagonal tile at (c0, c0) with kb live rows: its lower triangle,
-// unit padding beyond kb, zero above the diagonal.
+// unit padding beyond kb, zero above the diagonal; the owners of the diagonal
+// entries write Es[r], the half exponent of the stored a_rr (read after the
+// caller's next barrier).
+//
+// The tile is then equilibrated (by syrk_diag with its last update, or by
+// equilibrate_diag): row and column r scaled by 2^-Es[r].  The updates only
+// lower the diagonal of a positive definite matrix, so every entry of the
+// scaled tile and of its Schur complements is below 4 in magnitude and the
+// cross-multiplied products of the elimination stay far inside the FP64 range
+// whatever the scaling of the input.  The scaling is exact; the caller undoes
+// it: l_rc of the input is 2^Es[r] times the scaled tile's, and right-hand sides
+// are scaled by 2^-Es before the solves with the scaled tile's multipliers.
 template <int TB>
-__device__ __forceinline__ void load_diag(double (*D)[TB + 1], const double* __restrict__ A, int64_t lda, int c0,
-                                          int kb) {
+__device__ __forceinline__ void load_diag(double (*D)[TB + 1], int* Es, const double* __restrict__ A, int64_t lda,
+                                          int c0, int kb) {
     constexpr int R = TB * TB / kDenseThreads;
 #pragma unroll
     for (int q = 0; q < R; q++) {
         const int e = threadIdx.x + q * kDenseThreads, r = e % TB, c = e / TB;
-        D[r][c] = (r < kb && c <= r) ? A[(c0 + r) + (int64_t)(c0 + c) * lda] : (r == c ? 1.0 : 0.0);
+        const double a = (r < kb && c <= r) ? A[(c0 + r) + (int64_t)(c0 + c) * lda] : (r == c ? 1.0 : 0.0);
+        D[r][c] = a;
+        if (r == c) Es[r] = r < kb ? half_exponent(a) : 0;
     }
 }
 
-// D -= Lc Lc^T on the lower triangle (the diagonal tile's last update).
+// Equilibrated last update of the diagonal tile: D = (D - Lc Lc^T) 2^-(Es[r] + Es[c])
+// on the lower triangle (the scaled entry is formed beside the dot product, so
+// the scaling adds nothing to the chain).
 template <int TB>
-__device__ __forceinline__ void syrk_diag(double (*D)[TB + 1], const double (*Lc)[TB + 1]) {
+__device__ __forceinline__ void syrk_diag(double (*D)[TB + 1], const double (*Lc)[TB + 1], const int* Es) {
     constexpr int NP = TB * (TB + 1) / 2;
     for (int p = threadIdx.x; p < NP; p += kDenseThreads) {
         int r, c;
         packed_entry<TB>(p, r, c);
+        const double sc = pow2i(-(Es[r] + Es[c]));
+        const double ds = D[r][c] * sc;
         double acc = 0.0;
 #pragma unroll
         for (int m = 0; m < TB; m++) acc = fma(Lc[r][m], Lc[c][m], acc);
-        D[r][c] -= acc;
+        D[r][c] = fma(-acc, sc, ds);
+    }
+}
+
+// Equilibration of a diagonal tile without an update (the first tile column).
+template <int TB>
+__device__ __forceinline__ void equilibrate_diag(double (*D)[TB + 1], const int* Es) {
+    constexpr int NP = TB * (TB + 1) / 2;
+    for (int p = threadIdx.x; p < NP; p += kDenseThreads) {
+        int r, c;
+        packed_entry<TB>(p, r, c);
+        D[r][c] *= pow2i(-(Es[r] + Es[c]));
     }
 }
 
@@ -198,13 +212,13 @@ __device__ __forceinline__ void chol_tile(double (*D)[TB + 1], int kb, double* S
 // while every earlier pivot is positive, so the sign of D[c][c] is the pivot's.
 template <int TB>
 __device__ __forceinline__ void chol_store_tile(double* __restrict__ A, int64_t lda, int k0, int kb,
-                                                const double (*D)[TB + 1], const double* W,
+                                                const double (*D)[TB + 1], const double* W, const int* Es,
                                                 int* __restrict__ info) {
     constexpr int R = TB * TB / kDenseThreads;
 #pragma unroll
     for (int q = 0; q < R; q++) {
         const int e = threadIdx.x + q * kDenseThreads, r = e % TB, c = e / TB;
-        if (r < kb && c <= r) A[(k0 + r) + (int64_t)(k0 + c) * lda] = D[r][c] * W[c];
+        if (r < kb && c <= r) A[(k0 + r) + (int64_t)(k0 + c) * lda] = (D[r][c] * W[c]) * pow2i(Es[r]);
     }
     if (threadIdx.x == 0) {
         for (int j = 0; j < kb; j++)
@@ -239,6 +253,7 @@ __global__ void __launch_bounds__(kDenseThreads)
     __shared__ double Li[TB][TB + 1];
     __shared__ double Lc[TB][TB + 1];
     __shared__ double S[TB], W[TB], Inv[TB], Rd[TB], Z[TB];
+    __shared__ int Es[TB];
     const int t = threadIdx.x;
     const int nt = (n + TB - 1) / TB;
     const int c = k + 1;
@@ -255,46 +270,42 @@ __global__ void __launch_bounds__(kDenseThreads)
         // panel CTA: tile i of column c
         const int kb = min(TB, n - c0);
         const int i0 = c0 + (int)(b + 1) * TB, ib = min(TB, n - i0);
-        load_diag<TB>(D, A, lda, c0, kb);
+        load_diag<TB>(D, Es, A, lda, c0, kb);
         load_tile<TB>(X, A, lda, i0, c0, ib, kb);
         if (k >= 0) {
             load_tile<TB>(Lc, A, lda, c0, k0, kb, TB);
             load_tile<TB>(Li, A, lda, i0, k0, ib, TB);
         }
         __syncthreads();
-        if (k >= 0) {
-            syrk_diag<TB>(D, Lc);
-            __syncthreads();
-        }
+        if (k >= 0)
+            syrk_diag<TB>(D, Lc, Es);
+        else
+            equilibrate_diag<TB>(D, Es);
+        __syncthreads();
+        // the tile's update X = (A_ic - L_ik L_ck^T) 2^-E (columns scaled like the
+        // equilibrated diagonal tile, so the scaled tile's solve applies)
+        auto update_x = [&](int e) {
+            const int r = e % TB, cc = e / TB;
+            double acc = 0.0;
+            if (k >= 0) {
+#pragma unroll
+                for (int m = 0; m < TB; m++) acc = fma(Li[r][m], Lc[cc][m], acc);
+            }
+            X[r][cc] = (X[r][cc] - acc) * pow2i(-Es[cc]);
+        };
         if constexpr (TB * (TB - 1) / 2 <= kDenseThreads / 2) {
-            // the factorisation needs half the CTA: the other half takes the
-            // tile's update X -= L_ik L_ck^T meanwhile
+            // the factorisation needs half the CTA: the other half updates X meanwhile
             constexpr int H = kDenseThreads / 2;
             if (t < H) {
                 chol_tile<TB, H>(D, kb, S, W, Inv, Rd);
-            } else if (k >= 0) {
-                for (int e = t - H; e < TB * TB; e += H) {
-                    const int r = e % TB, cc = e / TB;
-                    double acc = 0.0;
-#pragma unroll
-                    for (int m = 0; m < TB; m++) acc = fma(Li[r][m], Lc[cc][m], acc);
-                    X[r][cc] -= acc;
-                }
+            } else {
+                for (int e = t - H; e < TB * TB; e += H) update_x(e);
             }
             __syncthreads();
         } else {
-            if (k >= 0) {
-                const int r = t % TB, cb = t / TB;
 #pragma unroll
-                for (int q = 0; q < R; q++) {
-                    const int cc = cb + q * CS;
-                    double acc = 0.0;
-#pragma unroll
-                    for (int m = 0; m < TB; m++) acc = fma(Li[r][m], Lc[cc][m], acc);
-                    X[r][cc] -= acc;
-                }
-                __syncthreads();
-            }
+            for (int q = 0; q < R; q++) update_x(t + q * kDenseThreads);
+            __syncthreads();
             chol_tile<TB, kDenseThreads>(D, kb, S, W, Inv, Rd);
         }
         diag_multipliers<TB>(D, Rd);
@@ -326,39 +337,44 @@ __global__ void __launch_bounds__(kDenseThreads)
     if (b < nd) {
         // diagonal CTA: L_kk, from tile (k, k) and its last update (column k - 1)
         const int kb = min(TB, n - k0);
-        load_diag<TB>(D, A, lda, k0, kb);
+        load_diag<TB>(D, Es, A, lda, k0, kb);
         if (k >= 1) load_tile<TB>(Lc, A, lda, k0, k0 - TB, kb, TB);
         __syncthreads();
-        if (k >= 1) {
-            syrk_diag<TB>(D, Lc);
-            __syncthreads();
-        }
+        if (k >= 1)
+            syrk_diag<TB>(D, Lc, Es);
+        else
+            equilibrate_diag<TB>(D, Es);
+        __syncthreads();
         chol_tile<TB, kDenseThreads>(D, kb, S, W, Inv, Rd);
-        chol_store_tile<TB>(A, lda, k0, kb, D, W, info);
+        chol_store_tile<TB>(A, lda, k0, kb, D, W, Es, info);
         return;
     }
     b -= nd;
     if (b < ny) {
         // y_c -= L_ck y_k, then y_c = L_cc^{-1} y_c, unscaled (z_j l_jj) like the panel
         const int kb = min(TB, n - c0);
-        load_diag<TB>(D, A, lda, c0, kb);
+        load_diag<TB>(D, Es, A, lda, c0, kb);
         if (k >= 0) {
             load_tile<TB>(Lc, A, lda, c0, k0, kb, TB);
             if (t < TB) X[0][t] = y[k0 + t];
         }
-        if (t < TB) Z[t] = t < kb ? y[c0 + t] : 0.0;
+        // y_c 2^-E (E[t] as load_diag forms it): the scaled tile's solve applies
+        if (t < TB)
+            Z[t] = t < kb ? y[c0 + t] * pow2i(-half_exponent(A[(c0 + t) + (int64_t)(c0 + t) * lda])) : 0.0;
         __syncthreads();
         if (k >= 0) {
-            syrk_diag<TB>(D, Lc);
+            syrk_diag<TB>(D, Lc, Es);
             if (t >= kDenseThreads - TB) {
                 const int r = t - (kDenseThreads - TB);
                 double acc = 0.0;
 #pragma unroll
                 for (int m = 0; m < TB; m++) acc = fma(Lc[r][m], X[0][m], acc);
-                Z[r] -= acc;
+                Z[r] = fma(-acc, pow2i(-Es[r]), Z[r]);
             }
-            __syncthreads();
+        } else {
+            equilibrate_diag<TB>(D, Es);
         }
+        __syncthreads();
         chol_tile<TB, kDenseThreads>(D, kb, S, W, Inv, Rd);
         diag_multipliers<TB>(D, Rd);
         if (t < 32) {

@@ -589,14 +589,23 @@ __global__ void k_rf_update(RfGrid g, int64_t t0, int64_t nt, int j0, int njob) 
 // Dense trailing block [t0, n_x) as a tiled right-looking LU over TB x TB tiles
 // of a row-major scratch copy, spread over many SMs (GB300 runs FP64 on the
 // CUDA cores at 2 lane-FMAs per clock per SM, so one CTA would need T^3 / 3
-// FMAs on a single SM).  Static diagonal pivots, unit lower L.  The diagonal
-// tile of tile column k is factored by the CTA that gives it its last trailing
-// update (k_tail_diag0 for the first), so no launch reads a tile another of its
-// CTAs writes.  Per tile column k: k_tail_panel (m CTAs form L_ik = A_ik
-// U_kk^{-1}, m more U_kj = L_kk^{-1} A_kj) and k_tail_update (A_ij -= L_ik U_kj;
-// the CTA of tile (k + 1, k + 1) then factors it).  Inside a tile the
-// multipliers stay unscaled until the end (a_rc -= a_rj a_jc / a_jj), so a step
-// never writes the row or column it reads: one barrier per step.
+// FMAs on a single SM).  Static diagonal pivots, unit lower L.  One launch per
+// tile column: launch k (k = -1 .. nt - 1) factors column c = k + 1 and holds
+//   panel CTAs     one per tile (i, c) and (c, i), i > c: the tile and the
+//                  diagonal tile take their last update (column k), the
+//                  diagonal tile is factored, and L_ic = A_ic U_cc^{-1} or
+//                  U_ci = L_cc^{-1} A_ci is stored
+//   a diagonal CTA that factors tile (k, k) once more and stores its L and U:
+//                  the panel CTAs of launch k - 1 read that tile, so it is only
+//                  overwritten one launch later
+//   trailing CTAs  A_ij -= L_ik U_kj for every tile i, j > c.
+// Every CTA that needs the factored diagonal tile factors it itself from the
+// same inputs with the same code, so all copies agree bit for bit; no launch
+// reads a tile that another of its CTAs writes.  The diagonal tile is
+// eliminated without divisions (cross-multiplied steps with an exact
+// power-of-two rescale): the trailing block after step j is s_{j+1} times the
+// ordinary one, so u_rc = a_rc / s_r (r <= c), l_rc = a_rc / a_cc (r > c) and
+// 1 / u_cc = s_c / a_cc, with one division per column for 1 / a_cc.
 constexpr int kTailTB = 16;
 
 __device__ __forceinline__ void k_tail_gather_body(RfGrid g) {
@@ -611,113 +620,187 @@ __global__ void k_tail_gather(RfGrid g) {
     k_tail_gather_body(g);
 }
 
-// Eliminates the tile held in Dk (unit-padded beyond kb) and stores it at
-// (k0, k0): U on and above the diagonal, L = a_rj / u_jj below it.
-__device__ __forceinline__ void tail_factor_store(const RfGrid& g, int k0, int kb, double (*Dk)[kTailTB + 1],
-                                                  double* Inv) {
+// Entry p of a TB x TB tile in shells of decreasing min(r, c) (p = 0 is the
+// last diagonal entry): the entries with r, c > j are exactly p < (TB-1-j)^2.
+__device__ __forceinline__ void tail_shell_entry(int p, int& r, int& c) {
     constexpr int TB = kTailTB;
-    const int T = g.T, t = threadIdx.x, r = t % TB, c = t / TB;
-    if (t == 0) Inv[0] = 1.0 / Dk[0][0];
-    __syncthreads();
+    int q = 0;
+    while ((q + 1) * (q + 1) <= p) q++;
+    const int m = TB - 1 - q, o = p - q * q;
+    r = o <= q ? m : m + (o - q);
+    c = o == 0 ? m : (o <= q ? m + o : m);
+}
+
+// Eliminates the tile in Dk (unit-padded beyond kb) without divisions:
+// afterwards Dk[r][c] = s_{min(r,c)} a_rc (a the ordinary elimination's values
+// when the entry is final), S[c] = s_c and Rd[c] = 1 / Dk[c][c].
+__device__ __forceinline__ void tail_factor(double (*Dk)[kTailTB + 1], int kb, double* S, double* Rd) {
+    constexpr int TB = kTailTB;
+    const int t = threadIdx.x;
+    int er = 0, ec = 0;
+    tail_shell_entry(min(t, (TB - 1) * (TB - 1) - 1), er, ec);
+    double s = 1.0;
     for (int j = 0; j < kb - 1; j++) {
-        const double inv = Inv[j];
-        if (r > j && c > j) {
-            Dk[r][c] = fma(-Dk[r][j], Dk[j][c] * inv, Dk[r][c]);
-            if (r == j + 1 && c == j + 1) Inv[j + 1] = 1.0 / Dk[r][c];
+        const int na = (TB - 1 - j) * (TB - 1 - j);
+        const double d = Dk[j][j];
+        const int sh = pivot_shift(d);
+        if (t < na) {
+            const double prod = Dk[er][j] * Dk[j][ec];
+            Dk[er][ec] = scale_pow2(fma(d, Dk[er][ec], -prod), sh);
+        }
+        if (t == (int)blockDim.x - 1) {
+            s *= scale_pow2(d, sh);
+            S[j + 1] = s;
         }
         __syncthreads();
     }
-    if (r < kb && c < kb) g.tailD[(size_t)(k0 + r) * T + k0 + c] = r > c ? Dk[r][c] * Inv[c] : Dk[r][c];
+    if (t < TB) {
+        if (t < kb) {
+            if (t == 0) S[0] = 1.0;
+            Rd[t] = 1.0 / Dk[t][t];
+        } else {
+            S[t] = 0.0;
+            Rd[t] = 0.0;
+        }
+    }
+    __syncthreads();
 }
 
-__device__ __forceinline__ void k_tail_diag0_body(RfGrid g) {
+// Loads a TB x TB tile of the row-major T x T scratch at (i0, j0), rb x cb live.
+__device__ __forceinline__ void tail_load(double (*X)[kTailTB + 1], const double* D, int T, int i0, int j0, int rb,
+                                          int cb) {
+    const int r = threadIdx.x / kTailTB, c = threadIdx.x % kTailTB;   // lanes along a row (coalesced)
+    X[r][c] = (r < rb && c < cb) ? D[(size_t)(i0 + r) * T + j0 + c] : 0.0;
+}
+
+// The diagonal tile of column c0 / TB with its last update (column kk0 / TB,
+// if kk0 >= 0): Dk = A_cc - L_ck U_kc, unit-padded beyond kb.  Uses Lk and Uk.
+__device__ __forceinline__ void tail_diag_tile(const RfGrid& g, int c0, int kb, int kk0, double (*Dk)[kTailTB + 1],
+                                               double (*Lk)[kTailTB + 1], double (*Uk)[kTailTB + 1]) {
+    constexpr int TB = kTailTB;
+    const int T = g.T, t = threadIdx.x, r = t / TB, c = t % TB;
+    const double* D = g.tailD;
+    const double a = (r < kb && c < kb) ? D[(size_t)(c0 + r) * T + c0 + c] : (r == c ? 1.0 : 0.0);
+    if (kk0 >= 0) {
+        tail_load(Lk, D, T, c0, kk0, kb, TB);
+        tail_load(Uk, D, T, kk0, c0, TB, kb);
+    }
+    __syncthreads();
+    double acc = 0.0;
+    if (kk0 >= 0) {
+#pragma unroll
+        for (int q = 0; q < TB; q++) acc = fma(Lk[r][q], Uk[q][c], acc);
+    }
+    Dk[r][c] = a - acc;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void k_tail_step_body(RfGrid g, int k) {
     constexpr int TB = kTailTB;
     __shared__ double Dk[TB][TB + 1];
-    __shared__ double Inv[TB];
-    const int T = g.T, kb = min(TB, T), r = threadIdx.x % TB, c = threadIdx.x / TB;
-    Dk[r][c] = (r < kb && c < kb) ? g.tailD[(size_t)r * T + c] : (r == c ? 1.0 : 0.0);
-    __syncthreads();
-    tail_factor_store(g, 0, kb, Dk, Inv);
-}
-__global__ void __launch_bounds__(256) k_tail_diag0(RfGrid g) {
-    pdl_wait();
-    k_tail_diag0_body(g);
-}
-
-__device__ __forceinline__ void k_tail_panel_body(RfGrid g, int k) {
-    constexpr int TB = kTailTB;
-    __shared__ double F[TB][TB + 1];      // the factored A_kk: U above, L below (unit diagonal)
     __shared__ double X[TB][TB + 1];
-    __shared__ double Inv[TB];
-    const int T = g.T, nt = (T + TB - 1) / TB, m = nt - k - 1;
-    const int t = threadIdx.x, r = t % TB, c = t / TB;
-    const int k0 = k * TB, kb = min(TB, T - k0);
-    const int b = blockIdx.x;
-    const bool ltile = b < m;
-    const int o0 = (k + 1 + (ltile ? b : b - m)) * TB;
-    const int ob = min(TB, T - o0);
+    __shared__ double Lk[TB][TB + 1];
+    __shared__ double Uk[TB][TB + 1];
+    __shared__ double Xk[TB][TB + 1];
+    __shared__ double S[TB], Rd[TB];
+    const int T = g.T, nt = (T + TB - 1) / TB;
+    const int t = threadIdx.x;
+    const int c = k + 1, c0 = c * TB, k0 = k * TB;
+    const int U = c < nt ? nt - c - 1 : 0;
     double* D = g.tailD;
-    F[r][c] = (r < kb && c < kb) ? D[(size_t)(k0 + r) * T + k0 + c] : (r == c ? 1.0 : 0.0);
-    if (ltile) X[r][c] = (r < ob && c < kb) ? D[(size_t)(o0 + r) * T + k0 + c] : 0.0;
-    else X[r][c] = (r < kb && c < ob) ? D[(size_t)(k0 + r) * T + o0 + c] : 0.0;
-    __syncthreads();
-    if (ltile) {
-        // X U = A_ik: with N[j][c] = u_jc / u_jj and X unscaled (x_rj u_jj),
-        // X[r][c] -= X[r][j] N[j][c]; x_rc = X[r][c] / u_cc
-        if (t < TB) Inv[t] = 1.0 / F[t][t];
-        __syncthreads();
-        if (c > r) F[r][c] *= Inv[r];
-        __syncthreads();
-        for (int j = 0; j < kb - 1; j++) {
-            if (c > j) X[r][c] = fma(-X[r][j], F[j][c], X[r][c]);
+    int b = (int)blockIdx.x;
+    if (b < 2 * U) {
+        // panel CTA: tile (i, c) (L) for b < U, tile (c, i) (U) otherwise
+        const bool ltile = b < U;
+        const int o0 = c0 + ((ltile ? b : b - U) + 1) * TB, ob = min(TB, T - o0);
+        const int kb = min(TB, T - c0);
+        // own tile and its last update: A_ic - L_ik U_kc, or A_ci - L_ck U_ki
+        if (ltile) {
+            tail_load(X, D, T, o0, c0, ob, kb);
+            if (k >= 0) tail_load(Xk, D, T, o0, k0, ob, TB);   // L_ik
+        } else {
+            tail_load(X, D, T, c0, o0, kb, ob);
+            if (k >= 0) tail_load(Xk, D, T, k0, o0, TB, ob);   // U_ki
+        }
+        tail_diag_tile(g, c0, kb, k >= 0 ? k0 : -1, Dk, Lk, Uk);   // its barriers also cover X, Xk
+        if (k >= 0) {
+            const int r = t / TB, cc = t % TB;
+            double acc = 0.0;
+#pragma unroll
+            for (int q = 0; q < TB; q++)
+                acc = ltile ? fma(Xk[r][q], Uk[q][cc], acc) : fma(Lk[r][q], Xk[q][cc], acc);
+            X[r][cc] -= acc;
+        }
+        tail_factor(Dk, kb, S, Rd);   // begins by reading only Dk; its barriers cover X
+        // multipliers in place: u_jc / u_jj = Dk[j][c] Rd[j] above the diagonal,
+        // l_rj = Dk[r][j] Rd[j] below it
+        {
+            const int r = t / TB, cc = t % TB;
+            if (r != cc) Dk[r][cc] *= Rd[min(r, cc)];
             __syncthreads();
         }
-        if (r < ob && c < kb) D[(size_t)(o0 + r) * T + k0 + c] = X[r][c] * Inv[c];
+        if (ltile) {
+            // X U_cc = A_ic, unscaled (x_rj u_jj), with the multipliers u_jc / u_jj;
+            // the rows are independent, each in TB lanes (one per column)
+            const int r = t / TB, cl = t % TB;
+            double x = X[r][cl];
+#pragma unroll
+            for (int j = 0; j < TB - 1; j++) {
+                if (j < kb - 1) {
+                    const double xj = __shfl_sync(0xffffffffu, x, j, TB);
+                    if (cl > j) x = fma(-xj, Dk[j][cl], x);
+                }
+            }
+            // 1 / u_cc = s_c / Dk[c][c]
+            if (r < ob && cl < kb) D[(size_t)(o0 + r) * T + c0 + cl] = x * (S[cl] * Rd[cl]);
+        } else {
+            // L_cc Y = A_ci with unit L; the columns are independent, each in TB
+            // lanes (one per row)
+            const int col = t / TB, r = t % TB;
+            double y = X[r][col];
+#pragma unroll
+            for (int j = 0; j < TB - 1; j++) {
+                if (j < kb - 1) {
+                    const double yj = __shfl_sync(0xffffffffu, y, j, TB);
+                    if (r > j) y = fma(-Dk[r][j], yj, y);
+                }
+            }
+            if (r < kb && col < ob) D[(size_t)(c0 + r) * T + o0 + col] = y;
+        }
         return;
     }
-    // L Y = A_kj with unit L: Y[r][c] -= l_rj Y[j][c] for r > j
-    for (int j = 0; j < kb - 1; j++) {
-        if (r > j) X[r][c] = fma(-F[r][j], X[j][c], X[r][c]);
+    b -= 2 * U;
+    if (k >= 0 && b == 0) {
+        // diagonal CTA: factor tile (k, k) with its last update (column k - 1) and store
+        // U (r <= c: Dk / s_r) and L (r > c: Dk / Dk[c][c])
+        const int kb = min(TB, T - k0);
+        tail_diag_tile(g, k0, kb, k >= 1 ? k0 - TB : -1, Dk, Lk, Uk);
+        tail_factor(Dk, kb, S, Rd);
+        const int r = t / TB, cl = t % TB;
+        if (t < TB) Xk[0][t] = t < kb ? 1.0 / S[t] : 0.0;
         __syncthreads();
+        if (r < kb && cl < kb) D[(size_t)(k0 + r) * T + k0 + cl] = r > cl ? Dk[r][cl] * Rd[cl] : Dk[r][cl] * Xk[0][r];
+        return;
     }
-    if (r < kb && c < ob) D[(size_t)(k0 + r) * T + o0 + c] = X[r][c];
-}
-__global__ void __launch_bounds__(256) k_tail_panel(RfGrid g, int k) {
-    pdl_wait();
-    k_tail_panel_body(g, k);
-}
-
-__device__ __forceinline__ void k_tail_update_body(RfGrid g, int k) {
-    constexpr int TB = kTailTB;
-    __shared__ double Li[TB][TB + 1];
-    __shared__ double Uj[TB][TB + 1];
-    __shared__ double Inv[TB];
-    const int T = g.T, nt = (T + TB - 1) / TB, m = nt - k - 1;
-    const int bi = (int)blockIdx.x / m, bj = (int)blockIdx.x % m;
-    const int i0 = (k + 1 + bi) * TB, j0 = (k + 1 + bj) * TB, k0 = k * TB;
-    const int ib = min(TB, T - i0), jb = min(TB, T - j0), kb = min(TB, T - k0);
-    const int t = threadIdx.x, r = t % TB, c = t / TB;
-    double* D = g.tailD;
-    Li[r][c] = (r < ib && c < kb) ? D[(size_t)(i0 + r) * T + k0 + c] : 0.0;
-    Uj[r][c] = (r < kb && c < jb) ? D[(size_t)(k0 + r) * T + j0 + c] : 0.0;
+    if (k >= 0) b -= 1;
+    if (k < 0 || b >= U * U) return;
+    // trailing tile (i, j), i, j > c: A_ij -= L_ik U_kj
+    const int bi = b / U, bj = b % U;
+    const int i0 = c0 + (bi + 1) * TB, j0 = c0 + (bj + 1) * TB;
+    const int ib = min(TB, T - i0), jb = min(TB, T - j0);
+    const int r = t / TB, cc = t % TB;
+    const double a = (r < ib && cc < jb) ? D[(size_t)(i0 + r) * T + j0 + cc] : 0.0;
+    tail_load(Lk, D, T, i0, k0, ib, TB);
+    tail_load(Uk, D, T, k0, j0, TB, jb);
     __syncthreads();
     double acc = 0.0;
 #pragma unroll
-    for (int q = 0; q < TB; q++) acc = fma(Li[r][q], Uj[q][c], acc);
-    const double v = (r < ib && c < jb) ? D[(size_t)(i0 + r) * T + j0 + c] - acc : 0.0;
-    if (bi != 0 || bj != 0) {
-        if (r < ib && c < jb) D[(size_t)(i0 + r) * T + j0 + c] = v;
-        return;
-    }
-    // tile (k + 1, k + 1) has its last update: factor it here
-    __syncthreads();                             // every thread is done reading Li
-    Li[r][c] = (r < ib && c < ib) ? v : (r == c ? 1.0 : 0.0);
-    __syncthreads();
-    tail_factor_store(g, i0, ib, Li, Inv);
+    for (int q = 0; q < TB; q++) acc = fma(Lk[r][q], Uk[q][cc], acc);
+    if (r < ib && cc < jb) D[(size_t)(i0 + r) * T + j0 + cc] = a - acc;
 }
-__global__ void __launch_bounds__(256) k_tail_update(RfGrid g, int k) {
+__global__ void __launch_bounds__(256) k_tail_step(RfGrid g, int k) {
     pdl_wait();
-    k_tail_update_body(g, k);
+    k_tail_step_body(g, k);
 }
 
 __device__ __forceinline__ void k_tail_scatter_body(RfGrid g) {
@@ -1999,17 +2082,9 @@ __global__ void k_tail_gather_batch(RfBatch B) {
     pdl_wait();
     k_tail_gather_body(B.g[blockIdx.y]);
 }
-__global__ void __launch_bounds__(256) k_tail_diag0_batch(RfBatch B) {
+__global__ void __launch_bounds__(256) k_tail_step_batch(RfBatch B, int k) {
     pdl_wait();
-    k_tail_diag0_body(B.g[blockIdx.y]);
-}
-__global__ void __launch_bounds__(256) k_tail_panel_batch(RfBatch B, int k) {
-    pdl_wait();
-    k_tail_panel_body(B.g[blockIdx.y], k);
-}
-__global__ void __launch_bounds__(256) k_tail_update_batch(RfBatch B, int k) {
-    pdl_wait();
-    k_tail_update_body(B.g[blockIdx.y], k);
+    k_tail_step_body(B.g[blockIdx.y], k);
 }
 __global__ void k_tail_scatter_batch(RfBatch B) {
     pdl_wait();
@@ -2128,11 +2203,10 @@ cudaError_t launch_refactor(const RfGrid& g, const int* lev_ptr_host, const int6
     if (g.T > 0) {
         const int TT = g.T * g.T, nt = (g.T + kTailTB - 1) / kTailTB;
         chk(launch_pdl(pdl, k_tail_gather, dim3(blocks_for(TT, 256)), dim3(256), 0, st, g));
-        chk(launch_pdl(pdl, k_tail_diag0, dim3(1), dim3(256), 0, st, g));
-        for (int k = 0; k < nt - 1; k++) {
-            const int m = nt - k - 1;
-            chk(launch_pdl(pdl, k_tail_panel, dim3(2 * m), dim3(256), 0, st, g, k));
-            chk(launch_pdl(pdl, k_tail_update, dim3(m * m), dim3(256), 0, st, g, k));
+        for (int k = -1; k < nt; k++) {
+            const int c = k + 1, U = c < nt ? nt - c - 1 : 0;
+            const int grid = 2 * U + (k >= 0 ? 1 + U * U : 0);
+            if (grid > 0) chk(launch_pdl(pdl, k_tail_step, dim3(grid), dim3(kTailTB * kTailTB), 0, st, g, k));
         }
         chk(launch_pdl(pdl, k_tail_scatter, dim3(blocks_for(TT, 256)), dim3(256), 0, st, g));
     }
@@ -2351,11 +2425,11 @@ cudaError_t launch_refactor_batch(const RfBatch& B, const int* lev_ptr_host, con
     if (T > 0) {
         const int TT = T * T, nt = (T + kTailTB - 1) / kTailTB;
         chk(launch_pdl(pdl, k_tail_gather_batch, dim3((unsigned)blocks_for(TT, 256), n), dim3(256), 0, st, B));
-        chk(launch_pdl(pdl, k_tail_diag0_batch, dim3(1, n), dim3(256), 0, st, B));
-        for (int k = 0; k < nt - 1; k++) {
-            const int m = nt - k - 1;
-            chk(launch_pdl(pdl, k_tail_panel_batch, dim3((unsigned)(2 * m), n), dim3(256), 0, st, B, k));
-            chk(launch_pdl(pdl, k_tail_update_batch, dim3((unsigned)(m * m), n), dim3(256), 0, st, B, k));
+        for (int k = -1; k < nt; k++) {
+            const int c = k + 1, U = c < nt ? nt - c - 1 : 0;
+            const int grid = 2 * U + (k >= 0 ? 1 + U * U : 0);
+            if (grid > 0)
+                chk(launch_pdl(pdl, k_tail_step_batch, dim3((unsigned)grid, n), dim3(kTailTB * kTailTB), 0, st, B, k));
         }
         chk(launch_pdl(pdl, k_tail_scatter_batch, dim3((unsigned)blocks_for(TT, 256), n), dim3(256), 0, st, B));
     }

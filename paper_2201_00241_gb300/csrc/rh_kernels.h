@@ -176,6 +176,37 @@ struct PfState {
 // so it is fully ordered after whatever precedes it (copies, event waits).
 #ifdef __CUDACC__
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// ---- division-free elimination of dense tiles -----------------------------------
+// The diagonal tiles of the dense factorisations (the refactorisation's dense
+// tail LU, the tracking step's Cholesky) are eliminated by cross-multiplied steps
+// a_rc <- 2^-e (d a_rc - a_rj a_jc), d the current pivot and 2^-e the power of two
+// that brings it into [1, 2), instead of a reciprocal of every pivot on the
+// critical path.
+// e with 2^-e d in [1, 2) for a positive normal pivot d (e <= 1022, so 2^-e is
+// normal too); 0 for any other value, where the factorisation has failed.
+__device__ __forceinline__ int pivot_shift(double d) {
+    const int f = (int)((__double_as_longlong(d) >> 52) & 0x7ff);
+    return (d > 0.0 && f != 0 && f != 0x7ff) ? min(f - 1023, 1022) : 0;
+}
+
+// v * 2^-sh for |sh| <= 1022 by an integer update of the exponent field, with
+// the bits of the IEEE multiplication whenever v and the result are normal
+// numbers; zero, subnormal, infinite and NaN v are returned as they are, a
+// result below the normal range is flushed to a signed zero and one above it
+// becomes a signed infinity.  Selects only, no branch: the update sits on the
+// critical path of every elimination step.
+__device__ __forceinline__ double scale_pow2(double v, int sh) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned long long sign = b & 0x8000000000000000ull;
+    const int f = (int)((b >> 52) & 0x7ffu);
+    const int nf = f - sh;
+    unsigned long long r = b - ((unsigned long long)(long long)sh << 52);
+    r = nf < 1 ? sign : r;
+    r = nf > 0x7fe ? (sign | 0x7ff0000000000000ull) : r;
+    r = (f == 0 || f == 0x7ff) ? b : r;
+    return __longlong_as_double((long long)r);
+}
 #endif
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,

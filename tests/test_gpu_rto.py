@@ -4,7 +4,9 @@
   span one tile, several tiles and ragged tails of both tile widths (16 up to
   n = 2048, 32 above), with padded leading dimensions; the strictly upper
   triangle must come back untouched (bit-exact); the first bad pivot of an
-  indefinite matrix must be the oracle's (bit-exact integer).
+  indefinite matrix must be the oracle's (bit-exact integer); matrices scaled
+  by powers of two far beyond the square root of the FP64 range factor to the
+  scaled oracle factor.
 * rh_potrs against the oracle's solve for 1 to 17 right-hand sides.
 * rh_rto_step on the 1354-bus grid (the paper's Table 3 workload) against the
   oracle's tracking step, the applied form against rh_set_state with the same
@@ -61,6 +63,28 @@ def test_potrf_matches_oracle(n, pad):
         assert bool((buf[:, n:] == 7.0).all())              # padding rows of every column untouched
     tol = 8 * n * EPS * np.linalg.cond(H)
     assert np.abs(np.tril(got) - L_ref).max() <= tol * np.abs(L_ref).max()
+
+
+@pytest.mark.parametrize("n,spread", [(100, 0), (519, 1000), (2100, 600)])
+def test_potrf_under_extreme_power_of_two_scaling(n, spread):
+    # P H P with P = diag(2^k): L = P L(H) up to rounding.  Uniform 2^450 puts the
+    # entries near 2^900, whose products leave the FP64 range; the spreads put the
+    # diagonal between 2^-spread and 2^spread.  The kernels equilibrate each
+    # diagonal tile by powers of two before their cross-multiplied eliminations.
+    from paper_2201_00241_gb300 import rh
+    H = spd(n, 500 + n)
+    rng = np.random.default_rng(n)
+    k = rng.integers(-spread // 2, spread // 2 + 1, n) if spread else np.full(n, 450)
+    P = np.ldexp(1.0, k)
+    Ad, _ = to_device(H * P[:, None] * P[None, :])
+    info = rh.potrf(Ad)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    got = np.tril(Ad.cpu().numpy())
+    assert np.all(np.isfinite(got))
+    L_ref, _ = cholesky(H)
+    tol = 8 * n * EPS * np.linalg.cond(H)
+    assert np.abs(got / P[:, None] - L_ref).max() <= tol * np.abs(L_ref).max()
 
 
 @pytest.mark.parametrize("n,bad", [(4, 2), (50, 37), (2100, 2050)])

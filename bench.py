@@ -19,6 +19,7 @@ out over the host cores) on the same workload.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -595,10 +596,15 @@ def measure_serving(factors=(0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 2.0), n_req=600, w
         drained.wait(60)
         sat_req, sat_hvp = n_done / dt, hvp_done / dt
         rows = []
-        for f in factors:
-            rate = f * sat_req
-            stream = [draw(1000 * int(100 * f) + j) for j in range(n_req)]
-            gaps = rng.exponential(1.0 / rate, n_req)
+        # an unrecorded pass of the sweep's pattern at the first rate (allocator growth,
+        # first-use costs), and a collection before each rate, so that a one-time host
+        # stall does not land in the first rate's window
+        for f in (None,) + tuple(factors):
+            rate = (f if f is not None else factors[0]) * sat_req
+            n_f = n_req if f is not None else 200
+            stream = [draw(1000 * int(100 * (f if f is not None else 99)) + j) for j in range(n_f)]
+            gaps = rng.exponential(1.0 / rate, n_f)
+            gc.collect()
             srv.reset_latencies()
             h0 = dict(srv.host_s)
             t0 = _t.perf_counter()
@@ -613,6 +619,8 @@ def measure_serving(factors=(0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 2.0), n_req=600, w
             for fu in futs:
                 fu.result()
             dt = _t.perf_counter() - t0
+            if f is None:
+                continue
             st = srv.stats(skip=warm_req)
             rows.append({"rate_factor": f, "offered_req_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                          "throughput_req_per_s": n_req / dt,
@@ -623,7 +631,8 @@ def measure_serving(factors=(0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 2.0), n_req=600, w
                 "saturated_req_per_s": sat_req, "saturated_hvp_per_s": sat_hvp,
                 "saturation": f"closed loop, {outstanding} requests outstanding for {t_sat:.0f} s, each "
                               "completion submitting the next from its callback",
-                "sweep": rows, "sweep_requests": f"{n_req} per rate, percentiles over all but the first {warm_req}",
+                "sweep": rows, "sweep_requests": f"{n_req} per rate, percentiles over all but the first {warm_req}; an "
+                                                  "unrecorded pass of 200 at the first rate before the sweep",
                 "alone_n256_ms": solo,
                 "batches": srv.batches, "waited_for_budget": srv.waited_for_budget,
                 "tuned": {k: tuned[k] for k in ("width", "threads", "ctas_per_sm", "split_lanes", "max_tail", "ms")},

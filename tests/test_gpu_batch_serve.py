@@ -125,7 +125,7 @@ def test_reduced_objective_autograd_against_finite_differences():
     F = reduced_objective(p0, lg)
     grad = torch.autograd.grad(F, p0, create_graph=True)[0]
     lam, grad_ref, F_ref = lg.adjoint()
-    assert float(F) == pytest.approx(F_ref, rel=1e-14)
+    assert float(F.detach()) == pytest.approx(F_ref, rel=1e-14)
     assert rel(grad.detach().numpy(), grad_ref) <= 1e-14
     W = gg.random_directions(lg.n_p, 32, 1354)
     h = 1e-6
@@ -144,6 +144,33 @@ def test_reduced_objective_autograd_against_finite_differences():
             worst_hv = max(worst_hv, rel(hv, hv_ref))
     assert worst_fd <= 1e-5
     assert worst_hv <= 1e-12
+
+
+def test_autograd_on_the_device_and_in_blocks():
+    # p on the GPU: the double backward runs rh_hessvec on device pointers; a block of
+    # directions is one launch; both equal the host-buffer products
+    from paper_2201_00241_gb300.autograd import reduced_objective, reduced_hessian_vector_products
+    from paper_2201_00241_gb300 import rh
+    g = gg.make_case("case1354")
+    lg = rh.Grid(g)
+    st = lg.plant()
+    lg.set_state(st.p, st.pd, st.qd)
+    lg.powerflow(st.x)
+    lg._ad_x = st.x
+    p0 = torch.tensor(st.p, dtype=torch.float64, device="cuda", requires_grad=True)
+    F = reduced_objective(p0, lg)
+    grad = torch.autograd.grad(F, p0, create_graph=True)[0]
+    assert grad.is_cuda
+    W = gg.random_directions(lg.n_p, 24, 2024)
+    ref = lg.hessvec(W)                                       # host buffers, one call
+    for j in (0, 7, 23):
+        hv = torch.autograd.grad(grad, p0, grad_outputs=torch.tensor(W[:, j], device="cuda"),
+                                 retain_graph=True)[0]
+        assert hv.is_cuda
+        assert rel(hv.cpu().numpy(), ref[:, j]) <= 1e-12
+    HW = reduced_hessian_vector_products(p0, lg, torch.tensor(W, device="cuda"))
+    assert HW.is_cuda and tuple(HW.shape) == (lg.n_p, 24)
+    assert rel(HW.cpu().numpy(), ref) <= 1e-12
 
 
 def test_server_result_alone_equals_in_the_mix(grids):

@@ -134,6 +134,9 @@ struct rh_grid {
     double *bstat_d = nullptr, *bstat_h = nullptr;
     cudaGraphExec_t adj_exec = nullptr;   // captured device work of rh_adjoint
     int adj_kernels = 0;                  // kernel nodes in that graph
+    // rh_powerflow: a Newton iteration's device work as two graphs (the refactorisation
+    // with its factor copies; the step, the update and the next assembly)
+    cudaGraphExec_t nt_fac_exec = nullptr, nt_step_exec = nullptr;
     cudaEvent_t apply_done = nullptr;     // orders a tracking step's parameter update before later grid work
 
     // rh_reduced_hessian: its captured graph (for one H pointer, leading dimension and
@@ -151,10 +154,9 @@ struct rh_grid {
     cudaEvent_t ev_pf0 = nullptr, ev_pf1 = nullptr;   // fork / join of the L2 prefetch beside the assembly
 
     void drop_graphs() {
-        if (adj_exec) cudaGraphExecDestroy(adj_exec);
-        if (hess_exec) cudaGraphExecDestroy(hess_exec);
-        adj_exec = nullptr;
-        hess_exec = nullptr;
+        for (cudaGraphExec_t e : {adj_exec, hess_exec, nt_fac_exec, nt_step_exec})
+            if (e) cudaGraphExecDestroy(e);
+        adj_exec = hess_exec = nt_fac_exec = nt_step_exec = nullptr;
         for (auto& kv : pf_graphs) cudaGraphExecDestroy(kv.second);
         pf_graphs.clear();
     }
@@ -327,6 +329,33 @@ rh_status check_err_flag(rh_grid* g) {
     RH_CUDA(cudaMemcpyAsync(&e, g->err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
     RH_CUDA(cudaStreamSynchronize(g->stream));
     if (e & 1) return fail(RH_ESINGULAR, "LU refactorisation: a static pivot is below 1e-14 max|J_x|");
+    return RH_OK;
+}
+
+// Captures what `enqueue` puts on g->stream (and on streams it joins) into an
+// executable graph, counting its kernel nodes.
+template <class F>
+rh_status capture_graph(rh_grid* g, F&& enqueue, cudaGraphExec_t* exec, int* kernels) {
+    cudaGraph_t graph = nullptr;
+    RH_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    rh_status st = enqueue();
+    cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
+    if (st) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (ce != cudaSuccess) return fail(RH_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    size_t n_nodes = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &n_nodes) == cudaSuccess) {
+        std::vector<cudaGraphNode_t> nodes(n_nodes);
+        int k = 0;
+        if (n_nodes && cudaGraphGetNodes(graph, nodes.data(), &n_nodes) == cudaSuccess)
+            for (auto nd : nodes) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) k++;
+            }
+        *kernels = k;
+    }
+    ce = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) { *exec = nullptr; return fail(RH_ECUDA, std::string("graph: ") + cudaGetErrorString(ce)); }
     return RH_OK;
 }
 
@@ -1012,28 +1041,63 @@ rh_status rh_powerflow(rh_grid* g, const double* x0, double tol, int32_t max_ite
         RH_CUDA(cudaMemcpyAsync(g->xbuf, x0, nx * sizeof(double), cudaMemcpyHostToDevice, s));
         k_set_x<<<nblk(nb, 128), 128, 0, s>>>(nb, g->ix_th, g->ix_v, g->xbuf, g->vm, g->va);
     }
-    int it = 0;
-    double res = INFINITY;
-    rh_status out = RH_ENOCONV;
-    for (;;) {
-        st = assemble(g, g->jac_method, g->gres, s);
+    // An iteration's device work is replayed from two graphs captured once per grid
+    // (a few dozen launches on the host otherwise): the refactorisation with its factor
+    // copies, after which the host reads the pivot flag, and the Newton step, the update
+    // and the next assembly, after which it reads the residual.  The assembly clears the
+    // pivot flag, so the flag is read between the two.
+    if (!g->nt_fac_exec) {
+        int nk = 0;
+        st = capture_graph(
+            g,
+            [&]() -> rh_status {
+                RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_tgt_lev_ptr.data(),
+                                            S.rf_piv_lev_ptr.data(), S.rf_n_lev, g->stream));
+                enqueue_factor_copies(g, g->stream);
+                RH_CUDA(cudaGetLastError());
+                return RH_OK;
+            },
+            &g->nt_fac_exec, &nk);
         if (st) return st;
+    }
+    if (!g->nt_step_exec) {
+        int nk = 0;
+        st = capture_graph(
+            g,
+            [&]() -> rh_status {
+                RH_CUDA(cudaMemcpyAsync(g->v1, g->gres, nx * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+                rh_status ss = solve_one(g, rh::PH_L | rh::PH_U, g->stream);
+                if (ss) return ss;
+                rh::launch_newton_update(g->pf(), g->st(), g->v1, g->stream);
+                return assemble(g, g->jac_method, g->gres, g->stream);
+            },
+            &g->nt_step_exec, &nk);
+        if (st) return st;
+    }
+    auto read_residual = [&](double* r) -> rh_status {
         unsigned long long bits = 0;
         RH_CUDA(cudaMemcpyAsync(&bits, g->umax, sizeof(bits), cudaMemcpyDeviceToHost, s));
         RH_CUDA(cudaStreamSynchronize(s));
-        std::memcpy(&res, &bits, sizeof(res));
-        if (nx == 0) res = 0.0;
+        std::memcpy(r, &bits, sizeof(*r));
+        if (nx == 0) *r = 0.0;
+        return RH_OK;
+    };
+    int it = 0;
+    double res = INFINITY;
+    rh_status out = RH_ENOCONV;
+    st = assemble(g, g->jac_method, g->gres, s);
+    if (st) return st;
+    st = read_residual(&res);
+    if (st) return st;
+    for (;;) {
         if (res <= tol) { out = RH_OK; break; }
         if (it >= max_iter || !std::isfinite(res)) break;
-        RH_CUDA(rh::launch_refactor(g->rf(), S.rf_lev_ptr.data(), S.rf_tgt_lev_ptr.data(), S.rf_piv_lev_ptr.data(), S.rf_n_lev, s));
-        enqueue_factor_copies(g, s);
+        RH_CUDA(cudaGraphLaunch(g->nt_fac_exec, s));
         st = check_err_flag(g);
         if (st) return st;
-        RH_CUDA(cudaMemcpyAsync(g->v1, g->gres, nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        st = solve_one(g, rh::PH_L | rh::PH_U, s);
+        RH_CUDA(cudaGraphLaunch(g->nt_step_exec, s));
+        st = read_residual(&res);
         if (st) return st;
-        rh::launch_newton_update(g->pf(), g->st(), g->v1, s);
-        RH_CUDA(cudaGetLastError());
         it++;
     }
     if (iters) *iters = it;
@@ -1095,32 +1159,6 @@ rh_status enqueue_adjoint(rh_grid* g) {
     return enqueue_adjoint_chain(g, g->stream, false);
 }
 
-// Captures what `enqueue` puts on g->stream (and on streams it joins) into an
-// executable graph, counting its kernel nodes.
-template <class F>
-rh_status capture_graph(rh_grid* g, F&& enqueue, cudaGraphExec_t* exec, int* kernels) {
-    cudaGraph_t graph = nullptr;
-    RH_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
-    rh_status st = enqueue();
-    cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
-    if (st) { if (graph) cudaGraphDestroy(graph); return st; }
-    if (ce != cudaSuccess) return fail(RH_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
-    size_t n_nodes = 0;
-    if (cudaGraphGetNodes(graph, nullptr, &n_nodes) == cudaSuccess) {
-        std::vector<cudaGraphNode_t> nodes(n_nodes);
-        int k = 0;
-        if (n_nodes && cudaGraphGetNodes(graph, nodes.data(), &n_nodes) == cudaSuccess)
-            for (auto nd : nodes) {
-                cudaGraphNodeType ty;
-                if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) k++;
-            }
-        *kernels = k;
-    }
-    ce = cudaGraphInstantiate(exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) { *exec = nullptr; return fail(RH_ECUDA, std::string("graph: ") + cudaGetErrorString(ce)); }
-    return RH_OK;
-}
 
 // CTAs of rh_reduced_hessian's first direction launch: the fewest with the directions
 // per CTA of a launch one slot short of full; the slots left over (7 SMs' worth for the

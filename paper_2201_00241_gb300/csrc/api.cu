@@ -517,11 +517,22 @@ rh_status reach_schedule(rh_grid* g, int n_cta, rh::ReachSched** out) {
     return RH_OK;
 }
 
+// CTAs of a direction launch: the fewest that keep the default grid's largest number of
+// directions per CTA, so that every CTA holds the same number (all but the last).  On the
+// 9241-bus grid, 304 CTAs of 9 or 10 directions left a few CTAs 10 % behind the rest every
+// time, whatever their directions or workspace addresses; 289 CTAs of 10 did not, and
+// ended the launch 0.1-0.3 ms sooner.
+int balanced_ctas(int N) {
+    const int grid = rh::dirs_default_ctas(N);
+    const int per = (N + grid - 1) / grid;
+    return std::max(1, (N + per - 1) / per);
+}
+
 rh_status dirs(rh_grid* g, int N, int64_t ld, double* V, double* T, const double* W, int64_t ldw, int col0,
                double* HW, int64_t ldhw, unsigned phases, cudaStream_t s, int n_cta = 0) {
     rh::DirLaunch L;
     L.N = N;
-    L.n_cta = rh::dirs_default_ctas(N);
+    L.n_cta = balanced_ctas(N);
     if (n_cta > 0 && n_cta < L.n_cta) L.n_cta = n_cta;
     L.ld = ld;
     L.cta_stride = 0;
@@ -1190,13 +1201,9 @@ rh_status enqueue_reduced_hessian(rh_grid* g, double* Hd, int64_t lh) {
     RH_CUDA(cudaEventRecordWithFlags(g->ev_c, g->stream2, cudaEventRecordExternal));
     RH_CUDA(cudaEventRecord(g->ev_join, g->stream2));
     RH_CUDA(cudaStreamWaitEvent(g->stream, g->ev_join, 0));
-    // the second launch on the fewest CTAs with the full grid's directions per CTA, so that
-    // every CTA holds the same number (measured on the 9241-bus grid: 289 CTAs of 10 end
-    // 0.1-0.3 ms sooner than 304 CTAs of 9 or 10, whose slowest few ran 10 % behind the rest)
-    const int slots2 = rh::dirs_default_ctas(np);
-    const int per2 = (np + slots2 - 1) / slots2;
+    // the second launch on balanced CTAs (every CTA the same number of directions)
     st = dirs(g, np, np, g->V, g->T, nullptr, 0, 0, Hd, lh, rh::PH_TPROJ | rh::PH_UT | rh::PH_LT | rh::PH_MULADD,
-              g->stream, (np + per2 - 1) / per2);
+              g->stream);
     if (st) return st;
     RH_CUDA(cudaEventRecordWithFlags(g->ev_d1, g->stream, cudaEventRecordExternal));
     return RH_OK;
@@ -1915,7 +1922,7 @@ rh_status rh_hessvec_noalloc(rh_grid* g, const double* W, int64_t ldw, int32_t N
     // call (W rows, the zero row, -B, the projection), so nothing is cleared.
     rh::DirLaunch L;
     L.N = N;
-    L.n_cta = rh::dirs_default_ctas(N);
+    L.n_cta = balanced_ctas(N);
     L.ld = N;
     L.cta_stride = 0;
     L.V = scratch;
